@@ -1,0 +1,338 @@
+#!/usr/bin/env python3
+"""Throughput of binned photon-number distributions on the GPU.
+
+Metric: generating-function points per second (every point of the roots-of-unity grid
+counts; conjugate symmetry means about half are evaluated) and binned P(b) tables per
+second, for the FP32 + refinement path (``value``) next to the FP64 path, both held to
+|P - P_oracle| <= 1e-10.
+
+Workload: M = 16 spatial modes, K = 1, r ~ U(0.5, 1.2), T = diag(sqrt(eta)) U with
+eta ~ U(0.4, 0.9) and Haar U, 4 detector groups of 4, N_l = 8: 9^4 = 6561 grid points of
+32 x 32 complex matrices per table.  One step = one table: every device stage of the path
+(grid phases, K(w) formed on chip, unpivoted LU, refinement, log det / exponent epilogue,
+inverse DFT, diagnostics) with the state (XA, gamma) resident in HBM.  ``e2e`` times the
+public C ABI from host buffers: per step the host FP64 state algebra and upload
+(gbsbin_plan_set_state) plus execute and the copy of the table back (gbsbin_execute_host).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+WORKLOAD_INDEX = 1
+WORKLOAD_NAME = "M16_K1_L4_N8_n32_6561pts"
+L2_FLUSH_BYTES = 256 << 20   # > 129 MB L2
+SMS = 152
+SM_MAX_MHZ = 2070.0
+FP32_LANES_PER_SM = 128
+FP64_FMA_PER_SM_CLK = 2      # 1.25 TFLOP/s nominal / (152 SMs x 2.07 GHz x 2 flops)
+METRIC = "generating-function points/s (binned P(b) tables/s alongside), FP32+refine vs FP64"
+
+
+def algorithmic_flops(n: int, has_gamma: bool, precision: int) -> float:
+    """Per evaluated point.  FP64: complex LU (8/3) n^3 real flops + 8 n^2 for the two
+    triangular solves.  FP32R: FMA-equivalent flops (2 x FP32 pipe instructions) of the
+    algorithm: LU 4 FMA per complex MAC (n^3/3 MACs); residual E by Dot2, 10 pipe
+    instructions per real product, 4 per complex MAC (n^3/3 MACs) plus 12 products per
+    entry for D XA; Z = L^-1 E (n^3/2 MACs) and diag(U^-1 Z) (n^3/6 MACs) at 4 FMA per MAC;
+    refined solve: 4 triangular solves (4 n^2 MAC-FMA... counted as 16 n^2) and the residual
+    by Dot2 (8 n^2 products)."""
+    n = float(n)
+    if precision == 0:
+        return (8.0 / 3.0) * n ** 3 + (8.0 * n * n if has_gamma else 0.0)
+    slots = (4.0 / 3.0) * n ** 3 + (40.0 / 3.0) * n ** 3 + 120.0 * n * n + 2.0 * n ** 3 + (2.0 / 3.0) * n ** 3
+    if has_gamma:
+        slots += 16.0 * n * n + 80.0 * n * n
+    return 2.0 * slots
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "50"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for name, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows),
+                "power_w_max": max([num(r[3]) for r in rows if num(r[3]) is not None], default=None)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def run_reference(args):
+    """CPU oracle as the reference arm: same workload and metric, each step a bounded
+    sample of grid points evaluated by the oracle on the host cores."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    prob = synth.config(WORKLOAD_INDEX)
+    XA, gamma, labels = oracle.plan(prob)
+    radix = prob.radix
+    npts = prob.n_points
+    rng = np.random.default_rng(0)
+    all_digits = np.stack(np.unravel_index(np.arange(npts), tuple(radix)), axis=1)
+    # size the sample so the whole run stays within about two minutes
+    t0 = time.perf_counter()
+    oracle.logq_points(XA, gamma, labels, radix, all_digits[:512])
+    per_point = (time.perf_counter() - t0) / 512
+    budget = 120.0 / max(1, args.steps + args.warmup)
+    sample = int(max(64, min(npts, budget / per_point)))
+    for _ in range(args.warmup):
+        oracle.logq_points(XA, gamma, labels, radix, all_digits[rng.choice(npts, sample, replace=False)])
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.logq_points(XA, gamma, labels, radix, all_digits[rng.choice(npts, sample, replace=False)])
+    dt = time.perf_counter() - t0
+    value = sample * args.steps / dt
+    cores = os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD_NAME, "n": prob.n, "grid_points": npts},
+            "cpu_baseline": {"value": value, "unit": "points/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{sample} random grid points of the {npts}-point grid per step"},
+            "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=200)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    import paper_2412_17742_gb300 as gb
+    if rank == 0:
+        from paper_2412_17742_gb300 import build as libbuild
+        libbuild.build()
+    if world > 1:
+        torch.distributed.barrier()
+    gb.load()
+
+    prob = synth.config(WORKLOAD_INDEX)
+    npts = prob.n_points
+    stream = torch.cuda.current_stream()
+    plans = {p: gb.Plan(prob, precision=p, want_timing=True) for p in (1, 0)}
+    tables = {p: torch.empty(plans[p].shape, dtype=torch.float64, device="cuda") for p in plans}
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    launches_per_step = 1 + 1 + (prob.L - 1) + 1 + 1   # points, normalise, L-1 axes, last axis, diag
+
+    peaks_meas = {"fp64_tflops": gb.gbsbin_alu_peak(0, SMS * 8), "fp32_tflops": gb.gbsbin_alu_peak(1, SMS * 8)}
+
+    for p in plans:
+        for _ in range(args.warmup):
+            gb.gbsbin_execute(plans[p].handle, tables[p], stream)
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    results = {}
+    for p in (1, 0):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        kms = []
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter()
+        for s in range(args.steps):
+            flush.zero_()
+            ev[s][0].record(stream)
+            gb.gbsbin_execute(plans[p].handle, tables[p], stream)
+            ev[s][1].record(stream)
+            st, d = gb.gbsbin_diagnostics(plans[p].handle, stream)   # syncs; reads kernel time
+            kms.append(d["point_kernel_ms"])
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall
+        gpu_ms = sum(a.elapsed_time(b) for a, b in ev)
+        if world > 1:
+            t = torch.tensor([gpu_ms], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            gpu_ms = float(t.item())
+        results[p] = {"gpu_ms": gpu_ms, "ms_per_step": gpu_ms / args.steps, "kernel_ms": float(np.mean(kms)),
+                      "status": st, "diag": d, "wall_s": t_wall}
+    clocks = sampler.stop()
+
+    # end to end through the C ABI with host buffers
+    host_out = torch.empty(plans[1].shape, dtype=torch.float64).pin_memory()
+    args_prob = gb.ProblemArgs(prob)
+    n = prob.n
+    h2d = n * n * (16 + 8 + 8) + n * (16 + 16 + 4 * 8)
+    d2h = int(np.prod(plans[1].shape)) * 8
+    for _ in range(3):
+        gb.gbsbin_plan_set_state(plans[1].handle, args_prob, stream)
+        gb.gbsbin_execute_host(plans[1].handle, host_out, stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        gb.gbsbin_plan_set_state(plans[1].handle, args_prob, stream)
+        gb.gbsbin_execute_host(plans[1].handle, host_out, stream)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e_value = world * npts * args.e2e_steps / e2e_s
+
+    d1 = results[1]["diag"]
+    has_gamma = prob.alpha is not None
+    out_points = {p: world * npts * args.steps / (results[p]["gpu_ms"] * 1e-3) for p in results}
+    flops_pt = {p: algorithmic_flops(n, has_gamma, p) for p in results}
+    achieved = flops_pt[1] * d1["n_evaluated"] / (results[1]["kernel_ms"] * 1e-3) / 1e12
+    peak32 = SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    peak64 = SMS * FP64_FMA_PER_SM_CLK * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    achieved64 = flops_pt[0] * d1["n_evaluated"] / (results[0]["kernel_ms"] * 1e-3) / 1e12
+    traffic = None
+    prof_traffic = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(prof_traffic):
+        try:
+            tj = json.load(open(prof_traffic))
+            if tj.get("kernel_source_hash") == _kernel_hash():
+                traffic = tj.get("bytes_per_launch")
+        except (ValueError, OSError):
+            traffic = None
+
+    line = {
+        "metric": METRIC, "value": out_points[1], "unit": "points/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": results[1]["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64refine", "data": "synthetic",
+        "config": {"workload": WORKLOAD_NAME, "n": n, "grid_points": npts, "evaluated_points": d1["n_evaluated"],
+                   "bins": prob.L, "cutoff": int(prob.cutoff[0]), "precision": "fp32_refine",
+                   "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas{world}"},
+        "tables_per_s": world * args.steps / (results[1]["gpu_ms"] * 1e-3),
+        "fp64": {"value": out_points[0], "unit": "points/s", "ms_per_step": results[0]["ms_per_step"],
+                 "tables_per_s": world * args.steps / (results[0]["gpu_ms"] * 1e-3),
+                 "point_kernel_ms": results[0]["kernel_ms"],
+                 "roofline": {"bound": "alu", "achieved": achieved64, "peak": peak64, "unit": "TFLOP/s",
+                              "frac": achieved64 / peak64, "traffic": None}},
+        "speedup_fp32r_vs_fp64": out_points[1] / out_points[0],
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak32, "unit": "TFLOP/s",
+                     "frac": achieved / peak32, "traffic": traffic,
+                     "kernel": "k_points_fp32r", "kernel_ms": results[1]["kernel_ms"],
+                     "flops_per_point": flops_pt[1],
+                     "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
+                     "measured_fma_chain_tflops": peaks_meas},
+        "e2e": {"value": e2e_value, "unit": "points/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clocks,
+        "diagnostics": {"sum_P": d1["sum_P"], "min_pivot_re": d1["min_pivot_re"],
+                        "bad_points": d1["n_bad_points"], "fp64_sum_P": results[0]["diag"]["sum_P"]},
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"], errs = cpu_baseline(prob, args.cpu_seconds, tables)
+        line["max_abs_err_vs_oracle"] = errs
+    for p in plans.values():
+        p.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def _kernel_hash():
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2412_17742_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".h", ".cpp")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def cpu_baseline(prob, seconds, tables):
+    """The oracle as it stands, whole tables on all host cores, for ~`seconds`; also the
+    error of the benchmarked GPU tables against the oracle table."""
+    import oracle
+    ref = None
+    count = 0
+    t0 = time.perf_counter()
+    while True:
+        ref = oracle.binned(prob)["P"]
+        count += 1
+        if time.perf_counter() - t0 > seconds:
+            break
+    dt = time.perf_counter() - t0
+    errs = {("fp32_refine" if p == 1 else "fp64"): float(np.abs(tables[p].cpu().numpy() - ref).max())
+            for p in tables}
+    return ({"value": prob.n_points * count / dt, "unit": "points/s", "cores": os.cpu_count(), "kind": "oracle",
+             "sample": f"{count} whole {prob.n_points}-point tables in {dt:.1f} s"}, errs)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,202 @@
+/*
+ * gbsbin - binned photon-number distributions of Gaussian states on GB300 (sm_103a).
+ *
+ * C ABI of the library.  Plain C types only; no exceptions cross it; every call returns
+ * a gbsbin_status (0 = GBSBIN_OK) unless stated otherwise.
+ *
+ * What it computes (arXiv:2412.17742):
+ *   A Gaussian state on n' = M*K modes (M external ports x K internal modes) with
+ *   normally ordered covariance Sigma^(1) and mean z-bar (Sec. II) has adjacency data
+ *   XA = I - Sigma^{-1}, gamma = X Sigma^{-1} z-bar, Sigma = I + Sigma^(1)
+ *   (Eqs. defA, defgamma, x_matrix_husimi_cov).  The detectors are grouped by a set
+ *   partition Lambda_1..Lambda_L of the M ports (Sec. VI, Eq. coarse_grained_subset).
+ *   The probability generating function of the binned counts b is
+ *     G(w) = q(A, gamma, D(w)) / q(A, gamma, 1),   D(w) = diag(w_label(i)) (+) same,
+ *     q = exp(1/2 gamma^T [I - D XA]^{-1} D X gamma) / sqrt(det[I - D XA])
+ *   (Sec. III, Eq. q_d; Sec. VI, Eq. Lamb_lhaf_master).  On the grid of roots of unity
+ *   w_l = exp(2 pi i k_l / (N_l + 1)) the library evaluates G at every point (one
+ *   unpivoted LU of the complex n x n matrix I - D(w) XA per point, n = 2 M K) and
+ *   returns the folded table
+ *     P~(b) = (1/N_pts) sum_k G(omega^k) omega^{-k.b},  0 <= b_l <= N_l,
+ *   which equals sum over b' = b mod (N+1) of the binned probability P(b')
+ *   (Sec. VI, Eq. coarse_grained_prob).  With options.oversample = s > 1 the grid has
+ *   s (N_l + 1) points per axis and the returned table is its first N_l + 1 entries per
+ *   axis, i.e. P(b) itself up to the probability mass beyond s (N_l + 1) - 1.
+ *
+ * Memory: a plan owns its device workspaces.  Table buffers passed to *_execute are
+ * owned by the caller; device pointers unless the function name says _host.
+ * Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ * Thread safety: one plan per thread/stream; distinct plans are independent.
+ */
+#ifndef GBSBIN_H
+#define GBSBIN_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+  double re, im;
+} gbsbin_complex;
+
+typedef enum {
+  GBSBIN_OK = 0,
+  GBSBIN_ERR_ARG = 1,          /* null pointer, M <= 0, K <= 0, L not in [1, M], bad option */
+  GBSBIN_ERR_PARTITION = 2,    /* a detector group is empty or a label is out of [0, L)     */
+  GBSBIN_ERR_CUTOFF = 3,       /* N_l < 0, or the grid exceeds GBSBIN_MAX_POINTS            */
+  GBSBIN_ERR_NONPHYSICAL = 4,  /* Sigma not Hermitian, or Sigma - I/2 not positive definite
+                                  (then ||XA||_2 >= 1 and the pivots lose Re > 0)           */
+  GBSBIN_ERR_CUDA = 5,         /* a CUDA runtime call failed                                */
+  GBSBIN_ERR_NOMEM = 6,        /* host or device allocation failed                          */
+  GBSBIN_ERR_NUMERIC = 7,      /* a pivot with Re u_ii <= 0 or a non-finite value at some
+                                  grid point (see gbsbin_diagnostics)                      */
+  GBSBIN_ERR_UNSUPPORTED = 8,  /* size beyond what this build supports (n > GBSBIN_MAX_N)   */
+  GBSBIN_ERR_TIMEOUT = 9       /* a bounded device-side wait gave up                        */
+} gbsbin_status;
+
+#define GBSBIN_MAX_N 512                 /* largest matrix size n = 2 M K            */
+#define GBSBIN_MAX_POINTS (1LL << 26)    /* largest grid prod(oversample (N_l + 1))   */
+
+typedef enum {
+  GBSBIN_FP64 = 0,          /* every step in FP64 (DFMA pipe)                               */
+  GBSBIN_FP32_REFINE = 1    /* FP32 LU, one refinement step of log det and of the exponent
+                               solve whose residual is formed with error-free FP32
+                               transformations; FP64 epilogue and DFT                        */
+} gbsbin_precision;
+
+typedef struct {
+  int precision;          /* gbsbin_precision; default GBSBIN_FP64                          */
+  int oversample;         /* >= 1; default 1 (folded table on the N_l + 1 grid)             */
+  int want_diagnostics;   /* nonzero: gbsbin_execute also reduces sum/imag diagnostics     */
+  int tile_override;      /* 0 = automatic kernel choice; otherwise a gbsbin_kernel id      */
+  int want_timing;        /* nonzero: execute records CUDA events around the point kernel on
+                             its stream; gbsbin_diagnostics reports the elapsed time         */
+} gbsbin_options;
+
+/*
+ * One problem.  Give EITHER the physical description (r, T, optional alpha and V) OR the
+ * state directly (sigma1, optional zbar); sigma1 != NULL selects the latter.
+ *
+ * Physical description (Sec. II; output covariance as in Sec. VIII,
+ * Eq. output_cov_internal; internal modes as in Sec. VI and App. B):
+ *   r[i*K + k]     real squeezing of internal mode k of input port i
+ *   T[j*M + i]     M x M transfer matrix, output j <- input i, ||T||_2 <= 1 (loss allowed)
+ *   alpha[i*K + k] displacement of internal mode k of input port i (NULL = none)
+ *   V[(i*K + l)*K + k]  K x K unitary per input port: column k is the internal state of
+ *                  squeezer k of port i in the detector's internal basis (NULL = identity)
+ *   The full transfer on the M*K modes is T_full[(j,l),(i,k)] = T[j,i] V_i[l,k]; then
+ *   Sigma^(1) = W Sigma^(1)_in W^dag with W = T_full (+) T_full^*, z-bar = (T_full alpha,
+ *   conj), mode order zeta = (a_(0,0) .. a_(M-1,K-1), a^dag_(0,0) ..) (external-major).
+ * Direct description:
+ *   sigma1[p*n + q] n x n Hermitian, the s = 1 (normally ordered) covariance in the mode
+ *   order above; zbar[n] the mean vector (NULL = zero), n = 2 M K.
+ * Grouping:
+ *   bin_of_mode[j] in [0, L): detector group of output port j (every group non-empty);
+ *   cutoff[l] = N_l >= 0.
+ * All arrays are host memory, read during the call only.
+ */
+typedef struct {
+  int M;
+  int K;
+  const double* r;
+  const gbsbin_complex* T;
+  const gbsbin_complex* alpha;
+  const gbsbin_complex* V;
+  const gbsbin_complex* sigma1;
+  const gbsbin_complex* zbar;
+  const int* bin_of_mode;
+  int L;
+  const int* cutoff;
+} gbsbin_problem;
+
+typedef struct gbsbin_plan gbsbin_plan;
+
+typedef struct {
+  double sum_P;              /* sum of the returned table (1 up to rounding on the folded grid) */
+  double max_imag;           /* max |Im P~| before the real part is taken (round-off probe)    */
+  double min_pivot_re;       /* min over evaluated points of min_i Re u_ii (> 0 in theory)     */
+  long long n_bad_points;    /* evaluated points with a pivot Re <= 0 or a non-finite value    */
+  long long n_points;        /* grid points prod(oversample (N_l + 1))                         */
+  long long n_evaluated;     /* points evaluated: conjugate symmetry halves the last axis      */
+  long long table_size;      /* doubles written to P_out: prod(N_l + 1)                        */
+  int n;                     /* matrix size 2 M K                                              */
+  int kernel;                /* gbsbin_kernel id used by the last execute                      */
+  double log_q1_re;          /* log q(A, gamma, 1) = -log Pr(0), from the w = 1 grid point    */
+  double point_kernel_ms;    /* duration of the last point-kernel launch (want_timing), else 0 */
+} gbsbin_diag;
+
+typedef enum {
+  GBSBIN_KERNEL_AUTO = 0,
+  GBSBIN_KERNEL_SMEM_FP64 = 1,     /* CTA per point, matrix in shared memory, FP64          */
+  GBSBIN_KERNEL_SMEM_FP32R = 2,    /* CTA per point, shared memory, FP32 LU + refinement    */
+  GBSBIN_KERNEL_GMEM_FP64 = 3,     /* CTA per point, matrix in an L2-resident workspace     */
+  GBSBIN_KERNEL_GMEM_FP32R = 4
+} gbsbin_kernel;
+
+/* Fill *o with defaults: FP64, oversample 1, diagnostics on, automatic kernel. */
+void gbsbin_default_options(gbsbin_options* o);
+
+/*
+ * Validate the problem, build Sigma^(1), z-bar, Sigma^{-1}, XA and gamma on the host in
+ * FP64 (Sec. II), upload them and allocate device workspaces.  Synchronous.
+ * Errors: ERR_ARG, ERR_PARTITION, ERR_CUTOFF, ERR_NONPHYSICAL, ERR_UNSUPPORTED,
+ * ERR_NOMEM, ERR_CUDA.  On error *out is NULL.
+ */
+int gbsbin_plan_create(const gbsbin_problem* p, const gbsbin_options* o, gbsbin_plan** out);
+
+/*
+ * Replace the state of an existing plan (same M, K, L, cutoffs and grouping; new r, T,
+ * alpha, V or sigma1/zbar): redo the host FP64 algebra and enqueue the upload on
+ * `stream`.  Same errors as plan_create; ERR_ARG if a shape differs.
+ */
+int gbsbin_plan_set_state(gbsbin_plan* plan, const gbsbin_problem* p, void* stream);
+
+/* Free the plan and its device workspaces (synchronises the device first). */
+int gbsbin_plan_destroy(gbsbin_plan* plan);
+
+/* Number of doubles in the output table, prod(N_l + 1); -1 if plan is NULL. */
+long long gbsbin_plan_table_size(const gbsbin_plan* plan);
+
+/*
+ * Evaluate G on the grid and write the table to P_out (device, table_size doubles,
+ * row-major over l = 0..L-1, last group fastest).  Asynchronous on `stream`.  Numeric
+ * failures (ERR_NUMERIC) are reported by gbsbin_diagnostics, not here.
+ */
+int gbsbin_execute(gbsbin_plan* plan, double* P_out, void* stream);
+
+/*
+ * Same as gbsbin_execute but P_out is host memory; the device-to-host copy is enqueued
+ * on `stream` and the call synchronises it before returning.
+ */
+int gbsbin_execute_host(gbsbin_plan* plan, double* P_out_host, void* stream);
+
+/*
+ * Diagnostics of the last execute on this plan.  Synchronises `stream`.  Returns
+ * GBSBIN_ERR_NUMERIC if any evaluated point had a non-positive or non-finite pivot.
+ */
+int gbsbin_diagnostics(gbsbin_plan* plan, gbsbin_diag* out, void* stream);
+
+/*
+ * Copy the per-point results of the last execute to host memory: logq_host receives
+ * n_evaluated complex values log q(A, gamma, D(omega^k)) (interleaved re, im) and
+ * minpiv_host (may be NULL) n_evaluated doubles min_i Re u_ii.  Evaluated point e has
+ * digits k_{L-1} = e mod half, then the other axes in mixed radix (last fastest), where
+ * half = radix_{L-1}/2 + 1 and radix_l = oversample (N_l + 1).  Synchronises `stream`.
+ */
+int gbsbin_read_points(gbsbin_plan* plan, double* logq_host, double* minpiv_host, void* stream);
+
+/* Static description of a status code. */
+const char* gbsbin_strerror(int status);
+
+/*
+ * Measurement utility (no counterpart in the paper): device throughput of dependent
+ * fused multiply-add chains in FP64 (precision = GBSBIN_FP64) or FP32 (otherwise), in
+ * TFLOP/s (2 flops per FMA), from one launch of `blocks` x 256 threads.  Synchronous.
+ */
+int gbsbin_alu_peak(int precision, int blocks, double* tflops, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBSBIN_H */

@@ -56,6 +56,10 @@ def _load():
         lib.oracle_logq_grid.argtypes = [ctypes.c_int, dp, dp, ip, ctypes.c_int, ip, dp, dp, ip,
                                          ctypes.c_int]
         lib.oracle_logq_grid.restype = ctypes.c_int
+        lib.oracle_logq_points.argtypes = [ctypes.c_int, dp, dp, ip, ctypes.c_int, ip,
+                                           ctypes.POINTER(ctypes.c_longlong), ctypes.c_long, dp, dp, ip,
+                                           ctypes.c_int]
+        lib.oracle_logq_points.restype = ctypes.c_int
         lib.oracle_dft.argtypes = [ctypes.c_int, ip, dp, dp]
         lib.oracle_dft.restype = ctypes.c_int
         _lib = lib
@@ -92,6 +96,29 @@ def logq_grid(XA, gamma, labels, radix, nthreads: int = 0):
     lib.oracle_logq_grid(XA.shape[0], _dp(XA.view(np.float64)), _dp(gamma.view(np.float64)),
                          _ip(labels), len(radix), _ip(radix), _dp(logq.view(np.float64)),
                          _dp(minre), _ip(st), int(nthreads))
+    return logq, minre, st
+
+
+def logq_points(XA, gamma, labels, radix, digits, nthreads: int = 0):
+    """log q at the grid points whose digits are the rows of ``digits`` (count, L)
+    (same per-point algorithm as :func:`logq_grid`).  Returns (logq, min pivot, status)."""
+    lib = _load()
+    XA = np.ascontiguousarray(XA, dtype=np.complex128)
+    gamma = np.ascontiguousarray(gamma, dtype=np.complex128)
+    labels = np.ascontiguousarray(labels, dtype=np.int32)
+    radix = np.ascontiguousarray(radix, dtype=np.int32)
+    digits = np.atleast_2d(np.asarray(digits, dtype=np.int64))
+    strides = np.ones(len(radix), dtype=np.int64)
+    for l in range(len(radix) - 2, -1, -1):
+        strides[l] = strides[l + 1] * radix[l + 1]
+    idx = np.ascontiguousarray(digits @ strides, dtype=np.int64)
+    cnt = len(idx)
+    logq = np.zeros(cnt, dtype=np.complex128)
+    minre = np.zeros(cnt, dtype=np.float64)
+    st = np.zeros(cnt, dtype=np.int32)
+    lib.oracle_logq_points(XA.shape[0], _dp(XA.view(np.float64)), _dp(gamma.view(np.float64)), _ip(labels),
+                           len(radix), _ip(radix), idx.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)), cnt,
+                           _dp(logq.view(np.float64)), _dp(minre), _ip(st), int(nthreads))
     return logq, minre, st
 
 

@@ -150,6 +150,50 @@ int oracle_logq_grid(int n, const double *XA_, const double *gamma_, const int *
   return nerr ? OR_ERR_NUMERIC : OR_OK;
 }
 
+/*
+ * log q at selected points only: idx[c] are flattened indices into the grid prod(radix)
+ * (last axis fastest); outputs as in oracle_logq_grid, one entry per selected point.
+ */
+int oracle_logq_points(int n, const double *XA_, const double *gamma_, const int *label, int L,
+                       const int *radix, const long long *idx, long count, double *logq_,
+                       double *minre, int *status, int nthreads) {
+  if (n <= 0 || L <= 0 || !XA_ || !gamma_ || !label || !radix || !idx || !logq_) return OR_ERR_ARG;
+  const cplx *XA = (const cplx *)XA_;
+  const cplx *gamma = (const cplx *)gamma_;
+  cplx *logq = (cplx *)logq_;
+  cplx *Xgamma = (cplx *)malloc(sizeof(cplx) * n);
+  if (!Xgamma) return OR_ERR_NOMEM;
+  int h = n / 2;
+  for (int i = 0; i < n; ++i) Xgamma[i] = gamma[i < h ? i + h : i - h];
+  int nerr = 0;
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#endif
+#pragma omp parallel reduction(+ : nerr)
+  {
+    cplx *Kw = (cplx *)malloc(sizeof(cplx) * (size_t)n * n);
+    cplx *x = (cplx *)malloc(sizeof(cplx) * n);
+    cplx *d = (cplx *)malloc(sizeof(cplx) * n);
+    int *k = (int *)malloc(sizeof(int) * L);
+#pragma omp for schedule(dynamic, 1)
+    for (long c = 0; c < count; ++c) {
+      point_digits((long)idx[c], L, radix, k);
+      for (int i = 0; i < n; ++i) d[i] = unit_root(k[label[i]], radix[label[i]]);
+      double mr;
+      int st = point_logq(n, XA, gamma, Xgamma, d, Kw, x, &logq[c], &mr);
+      if (minre) minre[c] = mr;
+      if (status) status[c] = st;
+      if (st) nerr += 1;
+    }
+    free(Kw);
+    free(x);
+    free(d);
+    free(k);
+  }
+  free(Xgamma);
+  return nerr ? OR_ERR_NUMERIC : OR_OK;
+}
+
 /* Neumaier-compensated accumulation of one real sum. */
 typedef struct {
   double s, c;

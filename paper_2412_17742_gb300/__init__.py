@@ -1,0 +1,270 @@
+"""Python binding of the gbsbin C ABI (``include/gbsbin.h``).
+
+Argument marshalling only: every step of the computation runs in the CUDA library
+``lib/libgbsbin.so``; there is no CPU fallback.  If the library is missing, :func:`load`
+raises.  Functions carry the names of the C entry points; PyTorch is used only for device
+buffers and the current stream.
+
+Binned photon-number distributions of Gaussian states by evaluating the generating
+function q(A, gamma, D(w)) / q(A, gamma, 1) on a roots-of-unity grid and taking an
+inverse DFT (arXiv:2412.17742, Sec. III Eq. q_d, Sec. VI Eqs. Lamb_lhaf_master and
+coarse_grained_prob).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libgbsbin.so")
+_lib = None
+
+GBSBIN_FP64 = 0
+GBSBIN_FP32_REFINE = 1
+KERNELS = {1: "smem_fp64", 2: "smem_fp32r", 3: "gmem_fp64", 4: "gmem_fp32r"}
+EXPORTED = ["gbsbin_default_options", "gbsbin_plan_create", "gbsbin_plan_set_state", "gbsbin_plan_destroy",
+            "gbsbin_plan_table_size", "gbsbin_execute", "gbsbin_execute_host", "gbsbin_diagnostics",
+            "gbsbin_strerror", "gbsbin_alu_peak", "gbsbin_read_points"]
+
+
+class GbsbinError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__(f"{where}: status {status} ({gbsbin_strerror(status)})")
+
+
+class gbsbin_complex(ctypes.Structure):
+    _fields_ = [("re", ctypes.c_double), ("im", ctypes.c_double)]
+
+
+class gbsbin_options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("oversample", ctypes.c_int),
+                ("want_diagnostics", ctypes.c_int), ("tile_override", ctypes.c_int),
+                ("want_timing", ctypes.c_int)]
+
+
+_cp = ctypes.POINTER(gbsbin_complex)
+_ip = ctypes.POINTER(ctypes.c_int)
+_dp = ctypes.POINTER(ctypes.c_double)
+
+
+class gbsbin_problem(ctypes.Structure):
+    _fields_ = [("M", ctypes.c_int), ("K", ctypes.c_int), ("r", _dp), ("T", _cp), ("alpha", _cp), ("V", _cp),
+                ("sigma1", _cp), ("zbar", _cp), ("bin_of_mode", _ip), ("L", ctypes.c_int), ("cutoff", _ip)]
+
+
+class gbsbin_diag(ctypes.Structure):
+    _fields_ = [("sum_P", ctypes.c_double), ("max_imag", ctypes.c_double), ("min_pivot_re", ctypes.c_double),
+                ("n_bad_points", ctypes.c_longlong), ("n_points", ctypes.c_longlong),
+                ("n_evaluated", ctypes.c_longlong), ("table_size", ctypes.c_longlong), ("n", ctypes.c_int),
+                ("kernel", ctypes.c_int), ("log_q1_re", ctypes.c_double), ("point_kernel_ms", ctypes.c_double)]
+
+
+def load():
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"gbsbin CUDA library not built: {LIB_PATH} is missing "
+                           "(run paper_2412_17742_gb300/build.py)")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp = ctypes.c_void_p
+    lib.gbsbin_default_options.argtypes = [ctypes.POINTER(gbsbin_options)]
+    lib.gbsbin_default_options.restype = None
+    lib.gbsbin_plan_create.argtypes = [ctypes.POINTER(gbsbin_problem), ctypes.POINTER(gbsbin_options),
+                                       ctypes.POINTER(vp)]
+    lib.gbsbin_plan_set_state.argtypes = [vp, ctypes.POINTER(gbsbin_problem), vp]
+    lib.gbsbin_plan_destroy.argtypes = [vp]
+    lib.gbsbin_plan_table_size.argtypes = [vp]
+    lib.gbsbin_plan_table_size.restype = ctypes.c_longlong
+    lib.gbsbin_execute.argtypes = [vp, vp, vp]
+    lib.gbsbin_execute_host.argtypes = [vp, vp, vp]
+    lib.gbsbin_diagnostics.argtypes = [vp, ctypes.POINTER(gbsbin_diag), vp]
+    lib.gbsbin_strerror.argtypes = [ctypes.c_int]
+    lib.gbsbin_strerror.restype = ctypes.c_char_p
+    lib.gbsbin_alu_peak.argtypes = [ctypes.c_int, ctypes.c_int, _dp, vp]
+    lib.gbsbin_read_points.argtypes = [vp, vp, vp, vp]
+    for f in ("gbsbin_plan_create", "gbsbin_plan_set_state", "gbsbin_plan_destroy", "gbsbin_execute",
+              "gbsbin_execute_host", "gbsbin_diagnostics", "gbsbin_alu_peak", "gbsbin_read_points"):
+        getattr(lib, f).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(status, where):
+    if status != 0:
+        raise GbsbinError(status, where)
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(buf):
+    if isinstance(buf, int):
+        return ctypes.c_void_p(buf)
+    if isinstance(buf, np.ndarray):
+        return ctypes.c_void_p(buf.ctypes.data)
+    return ctypes.c_void_p(buf.data_ptr())
+
+
+class ProblemArgs:
+    """Marshals a problem description (any object with M, K, r, T, bin_of_mode, cutoff and
+    optional alpha, V, sigma1, zbar attributes) into a gbsbin_problem; keeps the arrays alive."""
+
+    def __init__(self, prob):
+        def carr(a):
+            if a is None:
+                return None, None
+            arr = np.ascontiguousarray(np.asarray(a, dtype=np.complex128).reshape(-1))
+            return arr, arr.ctypes.data_as(_cp)
+
+        self.M, self.K = int(prob.M), int(prob.K)
+        self._keep = []
+        sig = getattr(prob, "sigma1", None)
+        self.r = None if getattr(prob, "r", None) is None else \
+            np.ascontiguousarray(np.asarray(prob.r, dtype=np.float64).reshape(-1))
+        T, Tp = carr(getattr(prob, "T", None))
+        al, alp = carr(getattr(prob, "alpha", None))
+        V, Vp = carr(getattr(prob, "V", None))
+        S, Sp = carr(sig)
+        Z, Zp = carr(getattr(prob, "zbar", None))
+        self.bins = np.ascontiguousarray(np.asarray(prob.bin_of_mode, dtype=np.int32))
+        self.cut = np.ascontiguousarray(np.asarray(prob.cutoff, dtype=np.int32))
+        self._keep += [T, al, V, S, Z]
+        self.c = gbsbin_problem(
+            self.M, self.K, None if self.r is None else self.r.ctypes.data_as(_dp), Tp, alp, Vp, Sp, Zp,
+            self.bins.ctypes.data_as(_ip), int(len(self.cut)), self.cut.ctypes.data_as(_ip))
+
+
+def gbsbin_default_options():
+    o = gbsbin_options()
+    load().gbsbin_default_options(ctypes.byref(o))
+    return o
+
+
+def make_options(precision=GBSBIN_FP64, oversample=1, want_diagnostics=True, tile_override=0,
+                 want_timing=False):
+    o = gbsbin_default_options()
+    o.precision, o.oversample = int(precision), int(oversample)
+    o.want_diagnostics, o.tile_override = int(bool(want_diagnostics)), int(tile_override)
+    o.want_timing = int(bool(want_timing))
+    return o
+
+
+def gbsbin_plan_create(prob, options=None):
+    """Returns an opaque plan handle (ctypes.c_void_p)."""
+    lib = load()
+    args = prob if isinstance(prob, ProblemArgs) else ProblemArgs(prob)
+    opt = options if options is not None else gbsbin_default_options()
+    h = ctypes.c_void_p()
+    _check(lib.gbsbin_plan_create(ctypes.byref(args.c), ctypes.byref(opt), ctypes.byref(h)), "gbsbin_plan_create")
+    return h
+
+
+def gbsbin_plan_set_state(plan, prob, stream=None):
+    args = prob if isinstance(prob, ProblemArgs) else ProblemArgs(prob)
+    _check(load().gbsbin_plan_set_state(plan, ctypes.byref(args.c), _stream_handle(stream)),
+           "gbsbin_plan_set_state")
+
+
+def gbsbin_plan_destroy(plan):
+    _check(load().gbsbin_plan_destroy(plan), "gbsbin_plan_destroy")
+
+
+def gbsbin_plan_table_size(plan):
+    return int(load().gbsbin_plan_table_size(plan))
+
+
+def gbsbin_execute(plan, P_out, stream=None):
+    """P_out: device buffer (torch CUDA float64 tensor or raw pointer) of table_size doubles."""
+    _check(load().gbsbin_execute(plan, _ptr(P_out), _stream_handle(stream)), "gbsbin_execute")
+
+
+def gbsbin_execute_host(plan, P_out_host, stream=None):
+    """P_out_host: host float64 buffer (numpy array, pinned torch tensor or pointer)."""
+    _check(load().gbsbin_execute_host(plan, _ptr(P_out_host), _stream_handle(stream)), "gbsbin_execute_host")
+
+
+def gbsbin_diagnostics(plan, stream=None):
+    """Returns (status, dict); status is GBSBIN_ERR_NUMERIC (7) if any point had a bad pivot."""
+    d = gbsbin_diag()
+    st = load().gbsbin_diagnostics(plan, ctypes.byref(d), _stream_handle(stream))
+    out = {f: getattr(d, f) for f, _ in gbsbin_diag._fields_}
+    out["kernel_name"] = KERNELS.get(out["kernel"], "?")
+    if st not in (0, 7):
+        raise GbsbinError(st, "gbsbin_diagnostics")
+    return st, out
+
+
+def gbsbin_read_points(plan, n_evaluated, stream=None):
+    """Returns (logq complex128 (n_evaluated,), min pivot float64 (n_evaluated,))."""
+    lq = np.zeros(int(n_evaluated), dtype=np.complex128)
+    mp = np.zeros(int(n_evaluated), dtype=np.float64)
+    _check(load().gbsbin_read_points(plan, _ptr(lq), _ptr(mp), _stream_handle(stream)), "gbsbin_read_points")
+    return lq, mp
+
+
+def evaluated_point_digits(cutoff, oversample=1):
+    """Digits k (n_evaluated, L) of the evaluated half grid, in the library's order."""
+    radix = [oversample * (int(c) + 1) for c in cutoff]
+    half = radix[-1] // 2 + 1
+    axes = [np.arange(r) for r in radix[:-1]] + [np.arange(half)]
+    mesh = np.meshgrid(*axes, indexing="ij")
+    return np.stack([m.reshape(-1) for m in mesh], axis=1)
+
+
+def gbsbin_strerror(status):
+    return load().gbsbin_strerror(int(status)).decode()
+
+
+def gbsbin_alu_peak(precision, blocks, stream=None):
+    v = ctypes.c_double()
+    _check(load().gbsbin_alu_peak(int(precision), int(blocks), ctypes.byref(v), _stream_handle(stream)),
+           "gbsbin_alu_peak")
+    return v.value
+
+
+class Plan:
+    """Owning wrapper: ``with Plan(prob, precision=...) as p: P = p.table()``."""
+
+    def __init__(self, prob, precision=GBSBIN_FP64, oversample=1, want_diagnostics=True, tile_override=0,
+                 want_timing=False):
+        self.options = make_options(precision, oversample, want_diagnostics, tile_override, want_timing)
+        self.handle = gbsbin_plan_create(prob, self.options)
+        self.shape = tuple(int(c) + 1 for c in prob.cutoff)
+
+    def table(self, stream=None):
+        """Execute into a new CUDA float64 tensor shaped (N_1+1, ..., N_L+1)."""
+        import torch
+        out = torch.empty(self.shape, dtype=torch.float64, device="cuda")
+        gbsbin_execute(self.handle, out, stream)
+        return out
+
+    def diagnostics(self, stream=None):
+        return gbsbin_diagnostics(self.handle, stream)
+
+    def close(self):
+        if self.handle is not None:
+            gbsbin_plan_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,181 @@
+// Inverse multidimensional DFT of the generating function on the roots-of-unity grid:
+//
+//   P~(b) = (1/N_pts) sum_k G(omega^k) prod_l omega_l^{-k_l b_l},   omega_l = exp(2 pi i / R_l)
+//
+// (the coefficient extraction that replaces the finite-difference sieve of
+// arXiv:2412.17742, Sec. V/VI: on R_l-th roots of unity it returns the folded table
+// sum_{b' = b mod R} P(b') exactly).  G(omega^k) = exp(log q_k - log q_0): point 0 is
+// w = 1, so dividing by q(1) applies Pr(0) = 1/q(1) (Sec. III, Eq. sum_lhafs).
+//
+// Only half of the last axis was evaluated (G(omega^-k) = conj G(omega^k) since P is
+// real).  The transform runs axis by axis in FP64: axes 0..L-2 as complex DFTs on the
+// half array, keeping only the N_l + 1 outputs the table needs, then the last axis as a
+// Hermitian (real-output) transform.  For any partial transform Y along the other axes
+// Y(b', R - k) = conj Y(b', k), so the last axis needs only the stored half.
+#include <cuda_runtime.h>
+
+#include "gbsbin_internal.h"
+
+namespace gbsbin {
+
+__device__ __forceinline__ double2 cfma2(double2 a, double2 b, double2 c) {  // c + a b
+  return make_double2(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));
+}
+
+// G = exp(log q - log q_0) on the evaluated half grid
+__global__ void k_normalise(const double2* __restrict__ logq, long long n, double2* __restrict__ G) {
+  const double2 l0 = logq[0];
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x) {
+    double2 v = logq[e];
+    double m = exp(v.x - l0.x);
+    double s, c;
+    sincos(v.y - l0.y, &s, &c);
+    G[e] = make_double2(m * c, m * s);
+  }
+}
+
+// out[o, b, s] = sum_{k < R} in[o, k, s] tw[(k b) mod R],  b < nout
+__global__ void k_dft_axis(const double2* __restrict__ in, double2* __restrict__ out, long long outer,
+                           int R, int nout, long long inner, const double2* __restrict__ tw) {
+  const long long total = outer * nout * inner;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    long long s = t % inner;
+    long long rest = t / inner;
+    int b = (int)(rest % nout);
+    long long o = rest / nout;
+    const double2* src = in + o * R * inner + s;
+    double2 acc = make_double2(0.0, 0.0);
+    int idx = 0;
+    for (int k = 0; k < R; ++k) {
+      acc = cfma2(src[(long long)k * inner], tw[idx], acc);
+      idx += b;
+      if (idx >= R) idx -= R;
+    }
+    out[t] = acc;
+  }
+}
+
+// P[o, b] = scale (Re Y[o,0] + sum_{k=1}^{H-1} c_k Re(Y[o,k] tw[(k b) mod R])),
+// c_k = 2, except c = 1 for the self-conjugate k = R/2 when R is even.
+__global__ void k_dft_last_real(const double2* __restrict__ Y, double* __restrict__ P, long long outer,
+                                int R, int H, int nout, double scale, const double2* __restrict__ tw) {
+  const long long total = outer * nout;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    int b = (int)(t % nout);
+    long long o = t / nout;
+    const double2* row = Y + o * H;
+    double acc = row[0].x;
+    int idx = b;
+    if (idx >= R) idx -= R;
+    for (int k = 1; k < H; ++k) {
+      double2 y = row[k], w = tw[idx];
+      double re = fma(y.x, w.x, -y.y * w.y);
+      acc += ((2 * k == R) ? 1.0 : 2.0) * re;
+      idx += b;
+      if (idx >= R) idx -= R;
+    }
+    P[t] = acc * scale;
+  }
+}
+
+// diag[0] = sum P, diag[1] = max |Im| of the self-conjugate entries Y[o,0] (and Y[o,R/2]),
+// diag[2] = min pivot Re, diag[3] = count of bad points, diag[4] = Re log q_0
+__global__ void k_diag(const double* __restrict__ P, long long table, const double2* __restrict__ Y,
+                       long long outer, int H, int R, const double* __restrict__ minpiv,
+                       const double2* __restrict__ logq, long long n_eval, double* __restrict__ diag) {
+  __shared__ double s_sum[32], s_im[32], s_min[32], s_bad[32];
+  double sum = 0.0, im = 0.0, mn = 1.0e300, bad = 0.0;
+  for (long long t = threadIdx.x; t < table; t += blockDim.x) sum += P[t];
+  for (long long o = threadIdx.x; o < outer; o += blockDim.x) {
+    im = fmax(im, fabs(Y[o * H].y));
+    if ((R & 1) == 0) im = fmax(im, fabs(Y[o * H + H - 1].y));
+  }
+  for (long long e = threadIdx.x; e < n_eval; e += blockDim.x) {
+    double m = minpiv[e];
+    double2 l = logq[e];
+    bool ok = (m > 0.0) && isfinite(l.x) && isfinite(l.y);
+    if (!ok) bad += 1.0;
+    mn = fmin(mn, m);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    im = fmax(im, __shfl_xor_sync(0xffffffffu, im, o));
+    mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+    bad += __shfl_xor_sync(0xffffffffu, bad, o);
+  }
+  int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    s_sum[w] = sum;
+    s_im[w] = im;
+    s_min[w] = mn;
+    s_bad[w] = bad;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int nw = blockDim.x >> 5;
+    for (int i = 1; i < nw; ++i) {
+      sum += s_sum[i];
+      im = fmax(im, s_im[i]);
+      mn = fmin(mn, s_min[i]);
+      bad += s_bad[i];
+    }
+    diag[0] = sum;
+    diag[1] = im;
+    diag[2] = mn;
+    diag[3] = bad;
+    diag[4] = logq[0].x;
+  }
+}
+
+static unsigned blocks_for(long long work) {
+  long long b = (work + 255) / 256;
+  if (b > 4096) b = 4096;
+  if (b < 1) b = 1;
+  return (unsigned)b;
+}
+
+cudaError_t launch_dft(const DftArgs& a, cudaStream_t s) {
+  const GridDesc& g = a.grid;
+  const int L = g.L;
+  k_normalise<<<blocks_for(g.n_eval), 256, 0, s>>>(a.logq, g.n_eval, a.bufA);
+  cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) return err;
+  long long dims[GBSBIN_MAX_L];
+  for (int l = 0; l < L - 1; ++l) dims[l] = g.radix[l];
+  dims[L - 1] = g.half;
+  double2* cur = a.bufA;
+  double2* nxt = a.bufB;
+  long long twoff = 0;
+  for (int l = 0; l < L - 1; ++l) {
+    long long outer = 1, inner = 1;
+    for (int m = 0; m < l; ++m) outer *= dims[m];
+    for (int m = l + 1; m < L; ++m) inner *= dims[m];
+    k_dft_axis<<<blocks_for(outer * g.nout[l] * inner), 256, 0, s>>>(cur, nxt, outer, g.radix[l], g.nout[l],
+                                                                      inner, a.tw + twoff);
+    err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+    dims[l] = g.nout[l];
+    twoff += g.radix[l];
+    double2* t = cur;
+    cur = nxt;
+    nxt = t;
+  }
+  long long outer = 1;
+  for (int m = 0; m < L - 1; ++m) outer *= dims[m];
+  const double scale = 1.0 / (double)g.npts;
+  k_dft_last_real<<<blocks_for(outer * g.nout[L - 1]), 256, 0, s>>>(cur, a.P, outer, g.radix[L - 1], g.half,
+                                                                    g.nout[L - 1], scale, a.tw + twoff);
+  err = cudaGetLastError();
+  if (err != cudaSuccess) return err;
+  if (a.diag) {
+    k_diag<<<1, 1024, 0, s>>>(a.P, a.table_size, cur, outer, g.half, g.radix[L - 1], a.minpiv, a.logq,
+                              g.n_eval, a.diag);
+    err = cudaGetLastError();
+  }
+  return err;
+}
+
+}  // namespace gbsbin

@@ -1,0 +1,628 @@
+// Host side of the library: validation, the FP64 Gaussian-state algebra of a problem
+// (arXiv:2412.17742, Sec. II; output covariance as in Sec. VIII, Eq. output_cov_internal;
+// internal modes as in Sec. VI and App. B), device workspaces and launch orchestration.
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "gbsbin_internal.h"
+
+using cd = std::complex<double>;
+using namespace gbsbin;
+
+struct gbsbin_plan {
+  int M = 0, K = 0, L = 0, n = 0;
+  gbsbin_options opt{};
+  std::vector<int> cutoff, bin_of_mode, label;
+  GridDesc grid{};
+  long long table_size = 0;
+  int kernel = 0;
+  int num_sms = 0;
+  int device = 0;
+  int has_gamma = 0;
+  // host copies of the state (FP64)
+  std::vector<cd> XA, gamma, Xgamma;
+  // device buffers
+  double2 *d_XA = nullptr, *d_gamma = nullptr, *d_Xgamma = nullptr;
+  float2 *d_XA_hi = nullptr, *d_XA_lo = nullptr, *d_Xg_hi = nullptr, *d_Xg_lo = nullptr;
+  float2 *d_g_hi = nullptr, *d_g_lo = nullptr;
+  int* d_label = nullptr;
+  double2* d_logq = nullptr;
+  double* d_minpiv = nullptr;
+  double2 *d_bufA = nullptr, *d_bufB = nullptr;
+  double2* d_tw = nullptr;
+  double* d_diag = nullptr;
+  double* d_table = nullptr;  // device copy of the table for execute_host
+  void* d_gws = nullptr;
+  long long gws_slot_bytes = 0;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // pinned staging for uploads
+  void* h_stage = nullptr;
+  size_t h_stage_bytes = 0;
+};
+
+namespace {
+
+const double kHermTol = 1e-10;
+
+int check_cuda(cudaError_t e) { return e == cudaSuccess ? GBSBIN_OK : GBSBIN_ERR_CUDA; }
+
+// ---------------------------------------------------------------- validation
+int validate_shape(const gbsbin_problem* p, const gbsbin_options* o) {
+  if (!p || !o) return GBSBIN_ERR_ARG;
+  if (p->M <= 0 || p->K <= 0) return GBSBIN_ERR_ARG;
+  if (p->L < 1 || p->L > p->M || p->L > GBSBIN_MAX_L) return GBSBIN_ERR_ARG;
+  if (!p->bin_of_mode || !p->cutoff) return GBSBIN_ERR_ARG;
+  if (!p->sigma1 && (!p->r || !p->T)) return GBSBIN_ERR_ARG;
+  if (o->precision != GBSBIN_FP64 && o->precision != GBSBIN_FP32_REFINE) return GBSBIN_ERR_ARG;
+  if (o->oversample < 1) return GBSBIN_ERR_ARG;
+  if (o->tile_override < 0 || o->tile_override > GBSBIN_KERNEL_GMEM_FP32R) return GBSBIN_ERR_ARG;
+  long long n = 2LL * p->M * p->K;
+  if (n > GBSBIN_MAX_N) return GBSBIN_ERR_UNSUPPORTED;
+  std::vector<int> count(p->L, 0);
+  for (int j = 0; j < p->M; ++j) {
+    int b = p->bin_of_mode[j];
+    if (b < 0 || b >= p->L) return GBSBIN_ERR_PARTITION;
+    count[b]++;
+  }
+  for (int l = 0; l < p->L; ++l)
+    if (count[l] == 0) return GBSBIN_ERR_PARTITION;
+  long long npts = 1;
+  for (int l = 0; l < p->L; ++l) {
+    if (p->cutoff[l] < 0) return GBSBIN_ERR_CUTOFF;
+    long long R = (long long)o->oversample * (p->cutoff[l] + 1LL);
+    if (R > (1LL << 26)) return GBSBIN_ERR_CUTOFF;
+    npts *= R;
+    if (npts > GBSBIN_MAX_POINTS) return GBSBIN_ERR_CUTOFF;
+  }
+  return GBSBIN_OK;
+}
+
+// ------------------------------------------------------- Gaussian-state algebra
+// Normally ordered covariance Sigma^(1) (n x n) and mean z-bar of the output state.
+// Sigma^(1)_in = [[N^T, Mm], [Mm^*, N]] with N = diag(sinh^2 r), Mm = diag(sinh r cosh r);
+// Sigma^(1)_out = W Sigma^(1)_in W^dag, W = T_full (+) T_full^*.
+int physical_state(const gbsbin_problem* p, std::vector<cd>& S1, std::vector<cd>& zbar) {
+  const int M = p->M, K = p->K, MK = M * K, n = 2 * MK;
+  for (int q = 0; q < MK; ++q)
+    if (!std::isfinite(p->r[q])) return GBSBIN_ERR_ARG;
+  std::vector<cd> Tf((size_t)MK * MK, 0.0);
+  for (int j = 0; j < M; ++j)
+    for (int i = 0; i < M; ++i) {
+      cd t(p->T[j * M + i].re, p->T[j * M + i].im);
+      if (!std::isfinite(t.real()) || !std::isfinite(t.imag())) return GBSBIN_ERR_ARG;
+      for (int l = 0; l < K; ++l)
+        for (int k = 0; k < K; ++k) {
+          cd v = (l == k) ? cd(1.0) : cd(0.0);
+          if (p->V) v = cd(p->V[(i * K + l) * K + k].re, p->V[(i * K + l) * K + k].im);
+          Tf[(size_t)(j * K + l) * MK + (i * K + k)] = t * v;
+        }
+    }
+  std::vector<double> nn(MK), mm(MK);
+  for (int q = 0; q < MK; ++q) {
+    double sh = std::sinh(p->r[q]), ch = std::cosh(p->r[q]);
+    nn[q] = sh * sh;
+    mm[q] = sh * ch;
+  }
+  // N_out[a][b] = sum_q conj(Tf[a][q]) n_q Tf[b][q];  Mm_out[a][b] = sum_q Tf[a][q] m_q Tf[b][q]
+  S1.assign((size_t)n * n, 0.0);
+  for (int a = 0; a < MK; ++a)
+    for (int b = 0; b < MK; ++b) {
+      cd N = 0.0, Mo = 0.0;
+      for (int q = 0; q < MK; ++q) {
+        cd ta = Tf[(size_t)a * MK + q], tb = Tf[(size_t)b * MK + q];
+        N += std::conj(ta) * nn[q] * tb;
+        Mo += ta * mm[q] * tb;
+      }
+      S1[(size_t)b * n + a] = N;                     // top-left: N^T
+      S1[(size_t)a * n + (MK + b)] = Mo;             // top-right: Mm
+      S1[(size_t)(MK + a) * n + b] = std::conj(Mo);  // bottom-left: Mm^*
+      S1[(size_t)(MK + a) * n + (MK + b)] = N;       // bottom-right: N
+    }
+  zbar.assign(n, 0.0);
+  if (p->alpha) {
+    for (int a = 0; a < MK; ++a) {
+      cd s = 0.0;
+      for (int q = 0; q < MK; ++q) s += Tf[(size_t)a * MK + q] * cd(p->alpha[q].re, p->alpha[q].im);
+      zbar[a] = s;
+      zbar[MK + a] = std::conj(s);
+    }
+  }
+  return GBSBIN_OK;
+}
+
+// In-place Cholesky of a Hermitian matrix (lower factor); false if not positive definite.
+bool cholesky(std::vector<cd>& A, int n) {
+  for (int j = 0; j < n; ++j) {
+    double d = A[(size_t)j * n + j].real();
+    for (int k = 0; k < j; ++k) d -= std::norm(A[(size_t)j * n + k]);
+    if (!(d > 0.0) || !std::isfinite(d)) return false;
+    double ljj = std::sqrt(d);
+    A[(size_t)j * n + j] = ljj;
+    for (int i = j + 1; i < n; ++i) {
+      cd s = A[(size_t)i * n + j];
+      for (int k = 0; k < j; ++k) s -= A[(size_t)i * n + k] * std::conj(A[(size_t)j * n + k]);
+      A[(size_t)i * n + j] = s / ljj;
+    }
+  }
+  return true;
+}
+
+// XA = I - Sigma^{-1}, Xgamma = Sigma^{-1} z-bar, gamma = X Xgamma, Sigma = I + Sigma^(1).
+int adjacency(const std::vector<cd>& S1, const std::vector<cd>& zbar, int n, std::vector<cd>& XA,
+              std::vector<cd>& gamma, std::vector<cd>& Xgamma) {
+  double scale = 1.0;
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      cd a = S1[(size_t)i * n + j], b = S1[(size_t)j * n + i];
+      if (!std::isfinite(a.real()) || !std::isfinite(a.imag())) return GBSBIN_ERR_ARG;
+      scale = std::fmax(scale, std::abs(a));
+      if (std::abs(a - std::conj(b)) > kHermTol * scale) return GBSBIN_ERR_NONPHYSICAL;
+    }
+  // physicality: Sigma - I/2 = Sigma^(1) + I/2 positive definite <=> ||I - Sigma^{-1}|| < 1
+  std::vector<cd> C(S1);
+  for (int i = 0; i < n; ++i) C[(size_t)i * n + i] += 0.5;
+  if (!cholesky(C, n)) return GBSBIN_ERR_NONPHYSICAL;
+  // Sigma = C C^H; Sigma^{-1} = C^{-H} C^{-1}
+  C = S1;
+  for (int i = 0; i < n; ++i) C[(size_t)i * n + i] += 1.0;
+  if (!cholesky(C, n)) return GBSBIN_ERR_NONPHYSICAL;
+  std::vector<cd> Ci((size_t)n * n, 0.0);  // C^{-1}, lower triangular
+  for (int j = 0; j < n; ++j) {
+    Ci[(size_t)j * n + j] = 1.0 / C[(size_t)j * n + j];
+    for (int i = j + 1; i < n; ++i) {
+      cd s = 0.0;
+      for (int k = j; k < i; ++k) s += C[(size_t)i * n + k] * Ci[(size_t)k * n + j];
+      Ci[(size_t)i * n + j] = -s / C[(size_t)i * n + i];
+    }
+  }
+  XA.assign((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j <= i; ++j) {
+      cd s = 0.0;  // (C^{-H} C^{-1})_ij = sum_k conj(Ci[k][i]) Ci[k][j], k >= max(i, j) = i
+      for (int k = i; k < n; ++k) s += std::conj(Ci[(size_t)k * n + i]) * Ci[(size_t)k * n + j];
+      XA[(size_t)i * n + j] = (i == j ? 1.0 : 0.0) - s;
+      if (i != j) XA[(size_t)j * n + i] = -std::conj(s);
+    }
+  Xgamma.assign(n, 0.0);
+  gamma.assign(n, 0.0);
+  for (int i = 0; i < n; ++i) {
+    cd s = 0.0;
+    for (int j = 0; j < n; ++j) {
+      cd sij = (i == j ? 1.0 : 0.0) - XA[(size_t)i * n + j];  // Sigma^{-1}
+      s += sij * zbar[j];
+    }
+    Xgamma[i] = s;
+  }
+  const int h = n / 2;
+  for (int i = 0; i < n; ++i) gamma[i] = Xgamma[i < h ? i + h : i - h];
+  return GBSBIN_OK;
+}
+
+int build_state(const gbsbin_problem* p, int n, std::vector<cd>& XA, std::vector<cd>& gamma,
+                std::vector<cd>& Xgamma, int* has_gamma) {
+  std::vector<cd> S1, zbar;
+  if (p->sigma1) {
+    S1.resize((size_t)n * n);
+    for (size_t q = 0; q < S1.size(); ++q) S1[q] = cd(p->sigma1[q].re, p->sigma1[q].im);
+    zbar.assign(n, 0.0);
+    if (p->zbar)
+      for (int q = 0; q < n; ++q) zbar[q] = cd(p->zbar[q].re, p->zbar[q].im);
+  } else {
+    int st = physical_state(p, S1, zbar);
+    if (st) return st;
+  }
+  int st = adjacency(S1, zbar, n, XA, gamma, Xgamma);
+  if (st) return st;
+  *has_gamma = 0;
+  for (int i = 0; i < n; ++i)
+    if (gamma[i] != cd(0.0)) *has_gamma = 1;
+  return GBSBIN_OK;
+}
+
+void free_device(gbsbin_plan* P) {
+  void* ptrs[] = {P->d_XA,   P->d_gamma, P->d_Xgamma, P->d_XA_hi, P->d_XA_lo, P->d_Xg_hi,
+                  P->d_Xg_lo, P->d_g_hi, P->d_g_lo,   P->d_label, P->d_logq,  P->d_minpiv,
+                  P->d_bufA, P->d_bufB,  P->d_tw,     P->d_diag,  P->d_gws,   P->d_table};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  if (P->h_stage) cudaFreeHost(P->h_stage);
+  if (P->ev0) cudaEventDestroy(P->ev0);
+  if (P->ev1) cudaEventDestroy(P->ev1);
+}
+
+template <typename T>
+int dalloc(T** p, size_t count) {
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return GBSBIN_ERR_NOMEM;
+  }
+  return check_cuda(e);
+}
+
+// Layout of the pinned staging buffer for one state upload.
+struct Stage {
+  size_t off_XA, off_g, off_Xg, off_XAhi, off_XAlo, off_Xghi, off_Xglo, off_ghi, off_glo, total;
+};
+Stage stage_layout(int n) {
+  Stage s{};
+  size_t nn = (size_t)n * n, o = 0;
+  s.off_XA = o;   o += nn * sizeof(double2);
+  s.off_g = o;    o += n * sizeof(double2);
+  s.off_Xg = o;   o += n * sizeof(double2);
+  s.off_XAhi = o; o += nn * sizeof(float2);
+  s.off_XAlo = o; o += nn * sizeof(float2);
+  s.off_Xghi = o; o += n * sizeof(float2);
+  s.off_Xglo = o; o += n * sizeof(float2);
+  s.off_ghi = o;  o += n * sizeof(float2);
+  s.off_glo = o;  o += n * sizeof(float2);
+  s.total = o;
+  return s;
+}
+
+void split(cd v, float2* hi, float2* lo) {
+  float hr = (float)v.real(), hi_ = (float)v.imag();
+  *hi = make_float2(hr, hi_);
+  *lo = make_float2((float)(v.real() - (double)hr), (float)(v.imag() - (double)hi_));
+}
+
+// Stage the state and enqueue its upload on `stream`.
+int upload_state(gbsbin_plan* P, cudaStream_t stream) {
+  const int n = P->n;
+  Stage s = stage_layout(n);
+  // a previous upload may still be reading the staging buffer
+  cudaError_t e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess) return GBSBIN_ERR_CUDA;
+  char* h = (char*)P->h_stage;
+  double2* XA = (double2*)(h + s.off_XA);
+  double2* g = (double2*)(h + s.off_g);
+  double2* Xg = (double2*)(h + s.off_Xg);
+  float2* XAhi = (float2*)(h + s.off_XAhi);
+  float2* XAlo = (float2*)(h + s.off_XAlo);
+  float2* Xghi = (float2*)(h + s.off_Xghi);
+  float2* Xglo = (float2*)(h + s.off_Xglo);
+  float2* ghi = (float2*)(h + s.off_ghi);
+  float2* glo = (float2*)(h + s.off_glo);
+  for (size_t q = 0; q < (size_t)n * n; ++q) {
+    XA[q] = make_double2(P->XA[q].real(), P->XA[q].imag());
+    split(P->XA[q], &XAhi[q], &XAlo[q]);
+  }
+  for (int i = 0; i < n; ++i) {
+    g[i] = make_double2(P->gamma[i].real(), P->gamma[i].imag());
+    Xg[i] = make_double2(P->Xgamma[i].real(), P->Xgamma[i].imag());
+    split(P->Xgamma[i], &Xghi[i], &Xglo[i]);
+    split(P->gamma[i], &ghi[i], &glo[i]);
+  }
+  struct {
+    void* dst;
+    size_t off, bytes;
+  } cp[] = {
+      {P->d_XA, s.off_XA, (size_t)n * n * sizeof(double2)},   {P->d_gamma, s.off_g, n * sizeof(double2)},
+      {P->d_Xgamma, s.off_Xg, n * sizeof(double2)},           {P->d_XA_hi, s.off_XAhi, (size_t)n * n * sizeof(float2)},
+      {P->d_XA_lo, s.off_XAlo, (size_t)n * n * sizeof(float2)}, {P->d_Xg_hi, s.off_Xghi, n * sizeof(float2)},
+      {P->d_Xg_lo, s.off_Xglo, n * sizeof(float2)},           {P->d_g_hi, s.off_ghi, n * sizeof(float2)},
+      {P->d_g_lo, s.off_glo, n * sizeof(float2)},
+  };
+  for (auto& c : cp) {
+    e = cudaMemcpyAsync(c.dst, h + c.off, c.bytes, cudaMemcpyHostToDevice, stream);
+    if (e != cudaSuccess) return GBSBIN_ERR_CUDA;
+  }
+  return GBSBIN_OK;
+}
+
+int choose_kernel(int n, int precision, int override_id) {
+  if (override_id) return override_id;
+  if (precision == GBSBIN_FP64) return n <= GBSBIN_SMEM_MAX_N ? GBSBIN_KERNEL_SMEM_FP64 : GBSBIN_KERNEL_GMEM_FP64;
+  return n <= GBSBIN_SMEM_MAX_N ? GBSBIN_KERNEL_SMEM_FP32R : GBSBIN_KERNEL_GMEM_FP32R;
+}
+
+}  // namespace
+
+extern "C" {
+
+void gbsbin_default_options(gbsbin_options* o) {
+  if (!o) return;
+  o->precision = GBSBIN_FP64;
+  o->oversample = 1;
+  o->want_diagnostics = 1;
+  o->tile_override = 0;
+  o->want_timing = 0;
+}
+
+const char* gbsbin_strerror(int status) {
+  switch (status) {
+    case GBSBIN_OK: return "ok";
+    case GBSBIN_ERR_ARG: return "invalid argument";
+    case GBSBIN_ERR_PARTITION: return "detector grouping is not a set partition of the ports";
+    case GBSBIN_ERR_CUTOFF: return "invalid cutoff or grid too large";
+    case GBSBIN_ERR_NONPHYSICAL: return "covariance is not Hermitian or Sigma - I/2 is not positive definite";
+    case GBSBIN_ERR_CUDA: return "CUDA runtime error";
+    case GBSBIN_ERR_NOMEM: return "out of memory";
+    case GBSBIN_ERR_NUMERIC: return "non-positive or non-finite pivot at some grid point";
+    case GBSBIN_ERR_UNSUPPORTED: return "size not supported by this build";
+    case GBSBIN_ERR_TIMEOUT: return "bounded device wait timed out";
+  }
+  return "unknown status";
+}
+
+int gbsbin_plan_create(const gbsbin_problem* p, const gbsbin_options* o, gbsbin_plan** out) {
+  if (!out) return GBSBIN_ERR_ARG;
+  *out = nullptr;
+  gbsbin_options opt;
+  gbsbin_default_options(&opt);
+  if (o) opt = *o;
+  int st = validate_shape(p, &opt);
+  if (st) return st;
+  gbsbin_plan* P = new (std::nothrow) gbsbin_plan();
+  if (!P) return GBSBIN_ERR_NOMEM;
+  P->M = p->M;
+  P->K = p->K;
+  P->L = p->L;
+  P->n = 2 * p->M * p->K;
+  P->opt = opt;
+  P->cutoff.assign(p->cutoff, p->cutoff + p->L);
+  P->bin_of_mode.assign(p->bin_of_mode, p->bin_of_mode + p->M);
+  const int n = P->n, MK = p->M * p->K;
+  P->label.resize(n);
+  for (int q = 0; q < MK; ++q) P->label[q] = P->label[MK + q] = p->bin_of_mode[q / p->K];
+  // grid
+  GridDesc& g = P->grid;
+  g.L = p->L;
+  g.npts = 1;
+  P->table_size = 1;
+  for (int l = 0; l < p->L; ++l) {
+    g.radix[l] = opt.oversample * (p->cutoff[l] + 1);
+    g.nout[l] = p->cutoff[l] + 1;
+    g.npts *= g.radix[l];
+    P->table_size *= g.nout[l];
+  }
+  g.half = g.radix[p->L - 1] / 2 + 1;
+  g.n_eval = g.npts / g.radix[p->L - 1] * g.half;
+  st = build_state(p, n, P->XA, P->gamma, P->Xgamma, &P->has_gamma);
+  if (st) {
+    delete P;
+    return st;
+  }
+  P->kernel = choose_kernel(n, opt.precision, opt.tile_override);
+  if ((P->kernel == GBSBIN_KERNEL_SMEM_FP64 || P->kernel == GBSBIN_KERNEL_SMEM_FP32R) && n > GBSBIN_SMEM_MAX_N) {
+    delete P;
+    return GBSBIN_ERR_UNSUPPORTED;
+  }
+  if (cudaGetDevice(&P->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, P->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete P;
+    return GBSBIN_ERR_CUDA;
+  }
+  const size_t nn = (size_t)n * n;
+  Stage sl = stage_layout(n);
+  if ((st = dalloc(&P->d_XA, nn)) || (st = dalloc(&P->d_gamma, n)) || (st = dalloc(&P->d_Xgamma, n)) ||
+      (st = dalloc(&P->d_XA_hi, nn)) || (st = dalloc(&P->d_XA_lo, nn)) || (st = dalloc(&P->d_Xg_hi, n)) ||
+      (st = dalloc(&P->d_Xg_lo, n)) || (st = dalloc(&P->d_g_hi, n)) || (st = dalloc(&P->d_g_lo, n)) ||
+      (st = dalloc(&P->d_label, n)) || (st = dalloc(&P->d_logq, g.n_eval)) ||
+      (st = dalloc(&P->d_minpiv, g.n_eval)) || (st = dalloc(&P->d_bufA, g.n_eval)) ||
+      (st = dalloc(&P->d_bufB, g.n_eval)) || (st = dalloc(&P->d_diag, 8)) ||
+      (st = dalloc(&P->d_table, (size_t)P->table_size))) {
+    free_device(P);
+    delete P;
+    return st;
+  }
+  long long twn = 0;
+  for (int l = 0; l < p->L; ++l) twn += g.radix[l];
+  if ((st = dalloc(&P->d_tw, (size_t)twn))) {
+    free_device(P);
+    delete P;
+    return st;
+  }
+  if (P->kernel == GBSBIN_KERNEL_GMEM_FP64 || P->kernel == GBSBIN_KERNEL_GMEM_FP32R) {
+    P->gws_slot_bytes = (long long)((P->kernel == GBSBIN_KERNEL_GMEM_FP64 ? 16 : 16) * nn);
+    P->gws_slot_bytes = (P->gws_slot_bytes + 255) / 256 * 256;
+    size_t bytes = (size_t)P->gws_slot_bytes * (size_t)P->num_sms;
+    cudaError_t e = cudaMalloc(&P->d_gws, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      free_device(P);
+      delete P;
+      return e == cudaErrorMemoryAllocation ? GBSBIN_ERR_NOMEM : GBSBIN_ERR_CUDA;
+    }
+  }
+  if (cudaMallocHost(&P->h_stage, sl.total) != cudaSuccess) {
+    cudaGetLastError();
+    free_device(P);
+    delete P;
+    return GBSBIN_ERR_NOMEM;
+  }
+  P->h_stage_bytes = sl.total;
+  if (opt.want_timing &&
+      (cudaEventCreate(&P->ev0) != cudaSuccess || cudaEventCreate(&P->ev1) != cudaSuccess)) {
+    cudaGetLastError();
+    free_device(P);
+    delete P;
+    return GBSBIN_ERR_CUDA;
+  }
+  // twiddles exp(-2 pi i m / R) and labels: synchronous one-off uploads
+  std::vector<double2> tw((size_t)twn);
+  long long off = 0;
+  const double TWO_PI = 6.283185307179586476925286766559;
+  for (int l = 0; l < p->L; ++l) {
+    int R = g.radix[l];
+    for (int m = 0; m < R; ++m) {
+      double a = -TWO_PI * (double)m / (double)R;
+      tw[off + m] = make_double2(std::cos(a), std::sin(a));
+    }
+    off += R;
+  }
+  if (cudaMemcpy(P->d_tw, tw.data(), tw.size() * sizeof(double2), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(P->d_label, P->label.data(), n * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaGetLastError();
+    free_device(P);
+    delete P;
+    return GBSBIN_ERR_CUDA;
+  }
+  st = upload_state(P, 0);
+  if (!st && cudaStreamSynchronize(0) != cudaSuccess) st = GBSBIN_ERR_CUDA;
+  if (st) {
+    cudaGetLastError();
+    free_device(P);
+    delete P;
+    return st;
+  }
+  *out = P;
+  return GBSBIN_OK;
+}
+
+int gbsbin_plan_set_state(gbsbin_plan* P, const gbsbin_problem* p, void* stream) {
+  if (!P || !p) return GBSBIN_ERR_ARG;
+  if (p->M != P->M || p->K != P->K || p->L != P->L) return GBSBIN_ERR_ARG;
+  int st = validate_shape(p, &P->opt);
+  if (st) return st;
+  for (int l = 0; l < P->L; ++l)
+    if (p->cutoff[l] != P->cutoff[l]) return GBSBIN_ERR_ARG;
+  for (int j = 0; j < P->M; ++j)
+    if (p->bin_of_mode[j] != P->bin_of_mode[j]) return GBSBIN_ERR_ARG;
+  std::vector<cd> XA, gamma, Xgamma;
+  int has_gamma = 0;
+  st = build_state(p, P->n, XA, gamma, Xgamma, &has_gamma);
+  if (st) return st;
+  P->XA.swap(XA);
+  P->gamma.swap(gamma);
+  P->Xgamma.swap(Xgamma);
+  P->has_gamma = has_gamma;
+  return upload_state(P, (cudaStream_t)stream);
+}
+
+int gbsbin_plan_destroy(gbsbin_plan* P) {
+  if (!P) return GBSBIN_ERR_ARG;
+  cudaDeviceSynchronize();
+  free_device(P);
+  delete P;
+  return GBSBIN_OK;
+}
+
+long long gbsbin_plan_table_size(const gbsbin_plan* P) { return P ? P->table_size : -1; }
+
+int gbsbin_execute(gbsbin_plan* P, double* P_out, void* stream) {
+  if (!P || !P_out) return GBSBIN_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  PointArgs a{};
+  a.n = P->n;
+  a.has_gamma = P->has_gamma;
+  a.XA = P->d_XA;
+  a.Xgamma = P->d_Xgamma;
+  a.gamma = P->d_gamma;
+  a.XA_hi = P->d_XA_hi;
+  a.XA_lo = P->d_XA_lo;
+  a.Xg_hi = P->d_Xg_hi;
+  a.Xg_lo = P->d_Xg_lo;
+  a.g_hi = P->d_g_hi;
+  a.g_lo = P->d_g_lo;
+  a.label = P->d_label;
+  a.grid = P->grid;
+  a.logq = P->d_logq;
+  a.minpiv = P->d_minpiv;
+  a.gws = P->d_gws;
+  a.gws_slot_bytes = P->gws_slot_bytes;
+  if (P->ev0 && cudaEventRecord(P->ev0, s) != cudaSuccess) return GBSBIN_ERR_CUDA;
+  cudaError_t e = launch_points(a, P->kernel, P->num_sms, s);
+  if (e != cudaSuccess) return GBSBIN_ERR_CUDA;
+  if (P->ev1 && cudaEventRecord(P->ev1, s) != cudaSuccess) return GBSBIN_ERR_CUDA;
+  DftArgs d{};
+  d.grid = P->grid;
+  d.logq = P->d_logq;
+  d.tw = P->d_tw;
+  d.bufA = P->d_bufA;
+  d.bufB = P->d_bufB;
+  d.P = P_out;
+  d.diag = P->opt.want_diagnostics ? P->d_diag : nullptr;
+  d.minpiv = P->d_minpiv;
+  d.table_size = P->table_size;
+  e = launch_dft(d, s);
+  return e == cudaSuccess ? GBSBIN_OK : GBSBIN_ERR_CUDA;
+}
+
+int gbsbin_execute_host(gbsbin_plan* P, double* P_out_host, void* stream) {
+  if (!P || !P_out_host) return GBSBIN_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  int st = gbsbin_execute(P, P->d_table, stream);
+  if (!st && cudaMemcpyAsync(P_out_host, P->d_table, (size_t)P->table_size * sizeof(double),
+                             cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    st = GBSBIN_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess && !st) st = GBSBIN_ERR_CUDA;
+  return st;
+}
+
+int gbsbin_diagnostics(gbsbin_plan* P, gbsbin_diag* out, void* stream) {
+  if (!P || !out) return GBSBIN_ERR_ARG;
+  double h[8] = {0};
+  if (P->opt.want_diagnostics) {
+    if (cudaMemcpyAsync(h, P->d_diag, sizeof(h), cudaMemcpyDeviceToHost, (cudaStream_t)stream) != cudaSuccess ||
+        cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess)
+      return GBSBIN_ERR_CUDA;
+  }
+  out->sum_P = h[0];
+  out->max_imag = h[1];
+  out->min_pivot_re = h[2];
+  out->n_bad_points = (long long)h[3];
+  out->log_q1_re = h[4];
+  out->n_points = P->grid.npts;
+  out->n_evaluated = P->grid.n_eval;
+  out->table_size = P->table_size;
+  out->n = P->n;
+  out->kernel = P->kernel;
+  out->point_kernel_ms = 0.0;
+  if (P->ev1) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(P->ev1) != cudaSuccess || cudaEventElapsedTime(&ms, P->ev0, P->ev1) != cudaSuccess) {
+      cudaGetLastError();
+      return GBSBIN_ERR_CUDA;
+    }
+    out->point_kernel_ms = ms;
+  }
+  if (!P->opt.want_diagnostics) return GBSBIN_OK;
+  return out->n_bad_points > 0 ? GBSBIN_ERR_NUMERIC : GBSBIN_OK;
+}
+
+int gbsbin_read_points(gbsbin_plan* P, double* logq_host, double* minpiv_host, void* stream) {
+  if (!P || !logq_host) return GBSBIN_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t ne = (size_t)P->grid.n_eval;
+  if (cudaMemcpyAsync(logq_host, P->d_logq, ne * sizeof(double2), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return GBSBIN_ERR_CUDA;
+  if (minpiv_host &&
+      cudaMemcpyAsync(minpiv_host, P->d_minpiv, ne * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return GBSBIN_ERR_CUDA;
+  return cudaStreamSynchronize(s) == cudaSuccess ? GBSBIN_OK : GBSBIN_ERR_CUDA;
+}
+
+int gbsbin_alu_peak(int precision, int blocks, double* tflops, void* stream) {
+  if (!tflops || blocks <= 0) return GBSBIN_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  float* sink = nullptr;
+  if (cudaMalloc(&sink, sizeof(float)) != cudaSuccess) return GBSBIN_ERR_NOMEM;
+  const int fp64 = precision == GBSBIN_FP64;
+  const int iters = fp64 ? 256 : 8192;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  int st = GBSBIN_OK;
+  if (launch_alu_peak(fp64, blocks, sink, iters, s) != cudaSuccess) st = GBSBIN_ERR_CUDA;  // warm-up
+  cudaEventRecord(e0, s);
+  if (!st && launch_alu_peak(fp64, blocks, sink, iters, s) != cudaSuccess) st = GBSBIN_ERR_CUDA;
+  cudaEventRecord(e1, s);
+  if (cudaEventSynchronize(e1) != cudaSuccess) st = GBSBIN_ERR_CUDA;
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  double flops = 2.0 * 8.0 * 8.0 * (double)iters * 256.0 * (double)blocks;
+  *tflops = ms > 0.f ? flops / (ms * 1e-3) / 1e12 : 0.0;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(sink);
+  return st;
+}
+
+}  // extern "C"

@@ -1,0 +1,67 @@
+// Internal interface between the host plan (gbsbin_host.cpp) and the kernels
+// (gbsbin_points.cu, gbsbin_dft.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "../../include/gbsbin.h"
+
+#define GBSBIN_MAX_L 16
+// Largest n whose n x n complex matrix (and, for the FP32 path, its residual) fits in
+// one CTA's shared memory next to the small vectors.
+#define GBSBIN_SMEM_MAX_N 112
+
+namespace gbsbin {
+
+// Roots-of-unity grid.  Axis l has radix[l] = oversample (N_l + 1) points; by conjugate
+// symmetry G(omega^-k) = conj G(omega^k) only half = radix[L-1]/2 + 1 values of the
+// last axis are evaluated (all values of the other axes).
+struct GridDesc {
+  int L;
+  int radix[GBSBIN_MAX_L];
+  int nout[GBSBIN_MAX_L];   // N_l + 1: table extent per axis
+  int half;
+  long long n_eval;         // (npts / radix[L-1]) * half
+  long long npts;
+};
+
+struct PointArgs {
+  int n;
+  int has_gamma;
+  const double2* XA;        // n*n FP64, row-major
+  const double2* Xgamma;    // n: X gamma = Sigma^{-1} z-bar
+  const double2* gamma;     // n
+  const float2* XA_hi;      // n*n: XA rounded to FP32
+  const float2* XA_lo;      // n*n: XA - XA_hi rounded to FP32
+  const float2* Xg_hi;      // n
+  const float2* Xg_lo;      // n
+  const float2* g_hi;       // n
+  const float2* g_lo;       // n
+  const int* label;         // n: detector group of each row
+  GridDesc grid;
+  double2* logq;            // n_eval outputs: log q at each evaluated point
+  double* minpiv;           // n_eval outputs: min_i Re u_ii
+  void* gws;                // L2-resident workspace for the global-memory variants
+  long long gws_slot_bytes; // bytes of one CTA's slot
+};
+
+struct DftArgs {
+  GridDesc grid;
+  const double2* logq;      // n_eval
+  const double2* tw;        // concatenated exp(-2 pi i m / radix[l]), m < radix[l]
+  double2* bufA;            // n_eval complex scratch
+  double2* bufB;            // n_eval complex scratch
+  double* P;                // table out (prod nout doubles)
+  double* diag;             // 8 doubles of reductions, or nullptr
+  const double* minpiv;     // n_eval
+  long long table_size;
+};
+
+// Kernel launchers (return the launch error).
+cudaError_t launch_points(const PointArgs& a, int kernel, int num_sms, cudaStream_t s);
+size_t points_smem_bytes(int kernel, int n);
+int points_threads(int kernel, int n);
+cudaError_t launch_dft(const DftArgs& a, cudaStream_t s);
+cudaError_t launch_alu_peak(int fp64, int blocks, float* out_sink, int iters, cudaStream_t s);
+
+}  // namespace gbsbin

@@ -1,0 +1,115 @@
+"""C ABI of the CUDA library without a GPU: it builds, loads, exports every declared entry
+point, and its host-side validation rejects bad problems before touching the device."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def gb():
+    from paper_2412_17742_gb300 import build
+    build.build()
+    import paper_2412_17742_gb300 as gb
+    gb.load()
+    return gb
+
+
+def declared_functions():
+    names = []
+    inc = os.path.join(ROOT, "include")
+    for f in os.listdir(inc):
+        if f.endswith(".h"):
+            txt = open(os.path.join(inc, f)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names += re.findall(r"\b(gbsbin_\w+)\s*\(", txt)
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_is_exported(gb):
+    names = declared_functions()
+    assert len(names) >= 10
+    lib = ctypes.CDLL(gb.LIB_PATH)
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(gb.EXPORTED) <= set(names)
+
+
+def test_strerror_and_defaults(gb):
+    assert gb.gbsbin_strerror(0) == "ok"
+    assert "partition" in gb.gbsbin_strerror(2)
+    o = gb.gbsbin_default_options()
+    assert (o.precision, o.oversample, o.want_diagnostics, o.tile_override) == (0, 1, 1, 0)
+
+
+def _status(gb, prob, **opt):
+    args = gb.ProblemArgs(prob)
+    o = gb.make_options(**opt)
+    h = ctypes.c_void_p()
+    return gb.load().gbsbin_plan_create(ctypes.byref(args.c), ctypes.byref(o), ctypes.byref(h))
+
+
+def test_host_validation(gb):
+    base = synth.config(0)
+    p = synth.config(0)
+    p.bin_of_mode = np.array([0, 0, 0, 0], np.int32)
+    assert _status(gb, p) == 2                       # empty group
+    p = synth.config(0)
+    p.bin_of_mode = np.array([0, 1, 2, 1], np.int32)
+    assert _status(gb, p) == 2                       # label out of range
+    p = synth.config(0)
+    p.cutoff = np.array([3, -2], np.int32)
+    assert _status(gb, p) == 3
+    p = synth.config(0)
+    p.cutoff = np.array([9000, 9000], np.int32)
+    assert _status(gb, p) == 3                       # grid beyond the limit
+    p = synth.config(0)
+    p.T = p.T * 2.0
+    assert _status(gb, p) == 4                       # amplifying map is not physical
+    assert _status(gb, base, oversample=0) == 1
+    assert _status(gb, base, precision=7) == 1
+    big = synth.random_problem(np.random.default_rng(0), 200, 2, 2, 1)
+    assert _status(gb, big) == 8                     # n = 800 > 512
+    # nonzero L > M
+    p = synth.config(0)
+    p.cutoff = np.array([1, 1, 1, 1, 1], np.int32)
+    assert _status(gb, p) == 1
+
+
+def test_nonhermitian_covariance_rejected(gb):
+    class Direct:
+        pass
+    d = Direct()
+    d.M, d.K, d.r, d.T = 1, 1, None, None
+    d.sigma1 = np.array([[0.5, 0.2], [0.1, 0.5]], complex)
+    d.zbar = None
+    d.bin_of_mode = np.array([0], np.int32)
+    d.cutoff = np.array([4], np.int32)
+    assert _status(gb, d) == 4
+
+
+def test_missing_library_fails_loudly(monkeypatch):
+    import paper_2412_17742_gb300 as gb
+    monkeypatch.setattr(gb, "_lib", None)
+    monkeypatch.setattr(gb, "LIB_PATH", "/nonexistent/libgbsbin.so")
+    with pytest.raises(RuntimeError):
+        gb.load()
+
+
+def test_evaluated_digits_cover_half_grid(gb):
+    for cut in ([6, 6], [8], [3, 2, 5], [0, 7]):
+        dig = gb.evaluated_point_digits(cut)
+        radix = [c + 1 for c in cut]
+        half = radix[-1] // 2 + 1
+        assert len(dig) == int(np.prod(radix[:-1])) * half
+        # every grid point is an evaluated point or the conjugate partner of one
+        seen = set(map(tuple, dig))
+        for k in np.ndindex(*radix):
+            neg = tuple((-np.array(k)) % np.array(radix))
+            assert k in seen or neg in seen
