@@ -185,6 +185,35 @@ int gbsbin_diagnostics(gbsbin_plan* plan, gbsbin_diag* out, void* stream);
  */
 int gbsbin_read_points(gbsbin_plan* plan, double* logq_host, double* minpiv_host, void* stream);
 
+/*
+ * Binned table from per-point log q without allocating device memory.  The paper has no
+ * counterpart: this is a library-level convenience for callers that must not call
+ * cudaMalloc, such as code running under a device-memory budget owned by another
+ * framework's pool allocator (where an extra allocation can fail or fragment the pool), or
+ * latency-critical loops where cudaMalloc/cudaFree would synchronise the device and stall
+ * work on other streams.
+ *
+ * It performs the inverse DFT stage of gbsbin_execute: logq (device, n_eval complex values,
+ * interleaved re, im, in the evaluated-point order described at gbsbin_read_points, for
+ * the grid radix_l = oversample (N_l + 1)) -> P_out (device, prod(N_l + 1) doubles).
+ * The caller passes inputs and outputs; cutoff (L ints) is host memory.
+ *
+ * Scratch: one fixed array of GBSBIN_NOALLOC_MAX_TWIDDLES + 2 GBSBIN_NOALLOC_MAX_EVAL
+ * complex doubles (about 4.25 MB) held by every GPU that loads the library until the
+ * process exits.  Grids with n_eval > GBSBIN_NOALLOC_MAX_EVAL or sum of radices >
+ * GBSBIN_NOALLOC_MAX_TWIDDLES are rejected with GBSBIN_ERR_UNSUPPORTED; other errors:
+ * ERR_ARG, ERR_CUTOFF, ERR_CUDA.  The first call on each device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Every call on a device shares the same array and leaves its
+ * contents behind (nothing in it has to start at zero), so calls whose kernels overlap
+ * on the GPU - on different streams or from different threads - race with each other;
+ * serialise them.  Asynchronous on `stream`.
+ */
+#define GBSBIN_NOALLOC_MAX_EVAL (1LL << 17)
+#define GBSBIN_NOALLOC_MAX_TWIDDLES (1LL << 14)
+int gbsbin_table_from_logq_noalloc(int L, const int* cutoff, int oversample, const double* logq,
+                                   double* P_out, void* stream);
+
 /* Static description of a status code. */
 const char* gbsbin_strerror(int status);
 

@@ -26,7 +26,7 @@ GBSBIN_FP32_REFINE = 1
 KERNELS = {1: "smem_fp64", 2: "smem_fp32r", 3: "gmem_fp64", 4: "gmem_fp32r"}
 EXPORTED = ["gbsbin_default_options", "gbsbin_plan_create", "gbsbin_plan_set_state", "gbsbin_plan_destroy",
             "gbsbin_plan_table_size", "gbsbin_execute", "gbsbin_execute_host", "gbsbin_diagnostics",
-            "gbsbin_strerror", "gbsbin_alu_peak", "gbsbin_read_points"]
+            "gbsbin_strerror", "gbsbin_alu_peak", "gbsbin_read_points", "gbsbin_table_from_logq_noalloc"]
 
 
 class GbsbinError(RuntimeError):
@@ -87,8 +87,10 @@ def load():
     lib.gbsbin_strerror.restype = ctypes.c_char_p
     lib.gbsbin_alu_peak.argtypes = [ctypes.c_int, ctypes.c_int, _dp, vp]
     lib.gbsbin_read_points.argtypes = [vp, vp, vp, vp]
+    lib.gbsbin_table_from_logq_noalloc.argtypes = [ctypes.c_int, _ip, ctypes.c_int, vp, vp, vp]
     for f in ("gbsbin_plan_create", "gbsbin_plan_set_state", "gbsbin_plan_destroy", "gbsbin_execute",
-              "gbsbin_execute_host", "gbsbin_diagnostics", "gbsbin_alu_peak", "gbsbin_read_points"):
+              "gbsbin_execute_host", "gbsbin_diagnostics", "gbsbin_alu_peak", "gbsbin_read_points",
+              "gbsbin_table_from_logq_noalloc"):
         getattr(lib, f).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -220,6 +222,15 @@ def evaluated_point_digits(cutoff, oversample=1):
     axes = [np.arange(r) for r in radix[:-1]] + [np.arange(half)]
     mesh = np.meshgrid(*axes, indexing="ij")
     return np.stack([m.reshape(-1) for m in mesh], axis=1)
+
+
+def gbsbin_table_from_logq_noalloc(cutoff, oversample, logq_dev, P_out, stream=None):
+    """Table from per-point log q (device buffer of n_evaluated complex values) into P_out
+    (device), using the library's fixed scratch instead of allocating."""
+    cut = np.ascontiguousarray(np.asarray(cutoff, dtype=np.int32))
+    _check(load().gbsbin_table_from_logq_noalloc(int(len(cut)), cut.ctypes.data_as(_ip), int(oversample),
+                                                 _ptr(logq_dev), _ptr(P_out), _stream_handle(stream)),
+           "gbsbin_table_from_logq_noalloc")
 
 
 def gbsbin_strerror(status):
