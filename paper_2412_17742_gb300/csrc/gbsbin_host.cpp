@@ -26,8 +26,9 @@ struct gbsbin_plan {
   // host copies of the state (FP64)
   std::vector<cd> XA, gamma, Xgamma;
   // device buffers
-  double2 *d_XA = nullptr, *d_gamma = nullptr, *d_Xgamma = nullptr;
-  float2 *d_XA_hi = nullptr, *d_XA_lo = nullptr, *d_Xg_hi = nullptr, *d_Xg_lo = nullptr;
+  int P = 1;  // grid points per CTA of the point kernel
+  double2 *d_NXA = nullptr, *d_gamma = nullptr, *d_Xgamma = nullptr;
+  float2 *d_NXA_hi = nullptr, *d_NXA_lo = nullptr, *d_Xg_hi = nullptr, *d_Xg_lo = nullptr;
   float2 *d_g_hi = nullptr, *d_g_lo = nullptr;
   int* d_label = nullptr;
   double2* d_logq = nullptr;
@@ -224,7 +225,7 @@ int build_state(const gbsbin_problem* p, int n, std::vector<cd>& XA, std::vector
 }
 
 void free_device(gbsbin_plan* P) {
-  void* ptrs[] = {P->d_XA,   P->d_gamma, P->d_Xgamma, P->d_XA_hi, P->d_XA_lo, P->d_Xg_hi,
+  void* ptrs[] = {P->d_NXA,  P->d_gamma, P->d_Xgamma, P->d_NXA_hi, P->d_NXA_lo, P->d_Xg_hi,
                   P->d_Xg_lo, P->d_g_hi, P->d_g_lo,   P->d_label, P->d_logq,  P->d_minpiv,
                   P->d_bufA, P->d_bufB,  P->d_tw,     P->d_diag,  P->d_gws,   P->d_table};
   for (void* q : ptrs)
@@ -288,9 +289,9 @@ int upload_state(gbsbin_plan* P, cudaStream_t stream) {
   float2* Xglo = (float2*)(h + s.off_Xglo);
   float2* ghi = (float2*)(h + s.off_ghi);
   float2* glo = (float2*)(h + s.off_glo);
-  for (size_t q = 0; q < (size_t)n * n; ++q) {
-    XA[q] = make_double2(P->XA[q].real(), P->XA[q].imag());
-    split(P->XA[q], &XAhi[q], &XAlo[q]);
+  for (size_t q = 0; q < (size_t)n * n; ++q) {  // the kernels use -XA
+    XA[q] = make_double2(-P->XA[q].real(), -P->XA[q].imag());
+    split(-P->XA[q], &XAhi[q], &XAlo[q]);
   }
   for (int i = 0; i < n; ++i) {
     g[i] = make_double2(P->gamma[i].real(), P->gamma[i].imag());
@@ -302,9 +303,9 @@ int upload_state(gbsbin_plan* P, cudaStream_t stream) {
     void* dst;
     size_t off, bytes;
   } cp[] = {
-      {P->d_XA, s.off_XA, (size_t)n * n * sizeof(double2)},   {P->d_gamma, s.off_g, n * sizeof(double2)},
-      {P->d_Xgamma, s.off_Xg, n * sizeof(double2)},           {P->d_XA_hi, s.off_XAhi, (size_t)n * n * sizeof(float2)},
-      {P->d_XA_lo, s.off_XAlo, (size_t)n * n * sizeof(float2)}, {P->d_Xg_hi, s.off_Xghi, n * sizeof(float2)},
+      {P->d_NXA, s.off_XA, (size_t)n * n * sizeof(double2)},   {P->d_gamma, s.off_g, n * sizeof(double2)},
+      {P->d_Xgamma, s.off_Xg, n * sizeof(double2)},           {P->d_NXA_hi, s.off_XAhi, (size_t)n * n * sizeof(float2)},
+      {P->d_NXA_lo, s.off_XAlo, (size_t)n * n * sizeof(float2)}, {P->d_Xg_hi, s.off_Xghi, n * sizeof(float2)},
       {P->d_Xg_lo, s.off_Xglo, n * sizeof(float2)},           {P->d_g_hi, s.off_ghi, n * sizeof(float2)},
       {P->d_g_lo, s.off_glo, n * sizeof(float2)},
   };
@@ -315,10 +316,11 @@ int upload_state(gbsbin_plan* P, cudaStream_t stream) {
   return GBSBIN_OK;
 }
 
-int choose_kernel(int n, int precision, int override_id) {
+int choose_kernel(int n, int L, int precision, int override_id) {
   if (override_id) return override_id;
-  if (precision == GBSBIN_FP64) return n <= GBSBIN_SMEM_MAX_N ? GBSBIN_KERNEL_SMEM_FP64 : GBSBIN_KERNEL_GMEM_FP64;
-  return n <= GBSBIN_SMEM_MAX_N ? GBSBIN_KERNEL_SMEM_FP32R : GBSBIN_KERNEL_GMEM_FP32R;
+  if (precision == GBSBIN_FP64)
+    return points_per_cta(GBSBIN_KERNEL_SMEM_FP64, n, L) > 0 ? GBSBIN_KERNEL_SMEM_FP64 : GBSBIN_KERNEL_GMEM_FP64;
+  return points_per_cta(GBSBIN_KERNEL_SMEM_FP32R, n, L) > 0 ? GBSBIN_KERNEL_SMEM_FP32R : GBSBIN_KERNEL_GMEM_FP32R;
 }
 
 }  // namespace
@@ -388,8 +390,9 @@ int gbsbin_plan_create(const gbsbin_problem* p, const gbsbin_options* o, gbsbin_
     delete P;
     return st;
   }
-  P->kernel = choose_kernel(n, opt.precision, opt.tile_override);
-  if ((P->kernel == GBSBIN_KERNEL_SMEM_FP64 || P->kernel == GBSBIN_KERNEL_SMEM_FP32R) && n > GBSBIN_SMEM_MAX_N) {
+  P->kernel = choose_kernel(n, p->L, opt.precision, opt.tile_override);
+  P->P = points_per_cta(P->kernel, n, p->L);
+  if (P->P < 1) {  // a shared-memory variant forced on a matrix that does not fit
     delete P;
     return GBSBIN_ERR_UNSUPPORTED;
   }
@@ -401,8 +404,8 @@ int gbsbin_plan_create(const gbsbin_problem* p, const gbsbin_options* o, gbsbin_
   }
   const size_t nn = (size_t)n * n;
   Stage sl = stage_layout(n);
-  if ((st = dalloc(&P->d_XA, nn)) || (st = dalloc(&P->d_gamma, n)) || (st = dalloc(&P->d_Xgamma, n)) ||
-      (st = dalloc(&P->d_XA_hi, nn)) || (st = dalloc(&P->d_XA_lo, nn)) || (st = dalloc(&P->d_Xg_hi, n)) ||
+  if ((st = dalloc(&P->d_NXA, nn)) || (st = dalloc(&P->d_gamma, n)) || (st = dalloc(&P->d_Xgamma, n)) ||
+      (st = dalloc(&P->d_NXA_hi, nn)) || (st = dalloc(&P->d_NXA_lo, nn)) || (st = dalloc(&P->d_Xg_hi, n)) ||
       (st = dalloc(&P->d_Xg_lo, n)) || (st = dalloc(&P->d_g_hi, n)) || (st = dalloc(&P->d_g_lo, n)) ||
       (st = dalloc(&P->d_label, n)) || (st = dalloc(&P->d_logq, g.n_eval)) ||
       (st = dalloc(&P->d_minpiv, g.n_eval)) || (st = dalloc(&P->d_bufA, g.n_eval)) ||
@@ -420,7 +423,7 @@ int gbsbin_plan_create(const gbsbin_problem* p, const gbsbin_options* o, gbsbin_
     return st;
   }
   if (P->kernel == GBSBIN_KERNEL_GMEM_FP64 || P->kernel == GBSBIN_KERNEL_GMEM_FP32R) {
-    P->gws_slot_bytes = (long long)((P->kernel == GBSBIN_KERNEL_GMEM_FP64 ? 16 : 16) * nn);
+    P->gws_slot_bytes = (long long)points_matrix_bytes(P->kernel, n, P->P);
     P->gws_slot_bytes = (P->gws_slot_bytes + 255) / 256 * 256;
     size_t bytes = (size_t)P->gws_slot_bytes * (size_t)P->num_sms;
     cudaError_t e = cudaMalloc(&P->d_gws, bytes);
@@ -512,11 +515,14 @@ int gbsbin_execute(gbsbin_plan* P, double* P_out, void* stream) {
   PointArgs a{};
   a.n = P->n;
   a.has_gamma = P->has_gamma;
-  a.XA = P->d_XA;
+  a.P = P->P;
+  a.logP = 0;
+  while ((1 << a.logP) < P->P) ++a.logP;
+  a.NXA = P->d_NXA;
   a.Xgamma = P->d_Xgamma;
   a.gamma = P->d_gamma;
-  a.XA_hi = P->d_XA_hi;
-  a.XA_lo = P->d_XA_lo;
+  a.NXA_hi = P->d_NXA_hi;
+  a.NXA_lo = P->d_NXA_lo;
   a.Xg_hi = P->d_Xg_hi;
   a.Xg_lo = P->d_Xg_lo;
   a.g_hi = P->d_g_hi;

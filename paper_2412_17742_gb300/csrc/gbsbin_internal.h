@@ -28,11 +28,13 @@ struct GridDesc {
 struct PointArgs {
   int n;
   int has_gamma;
-  const double2* XA;        // n*n FP64, row-major
+  int P;                    // grid points per CTA (power of two)
+  int logP;
+  const double2* NXA;       // n*n FP64, row-major: -XA (the off-diagonal part of conj(D) - XA)
   const double2* Xgamma;    // n: X gamma = Sigma^{-1} z-bar
   const double2* gamma;     // n
-  const float2* XA_hi;      // n*n: XA rounded to FP32
-  const float2* XA_lo;      // n*n: XA - XA_hi rounded to FP32
+  const float2* NXA_hi;     // n*n: -XA rounded to FP32
+  const float2* NXA_lo;     // n*n: (-XA) - NXA_hi rounded to FP32
   const float2* Xg_hi;      // n
   const float2* Xg_lo;      // n
   const float2* g_hi;       // n
@@ -59,7 +61,9 @@ struct DftArgs {
 
 // Kernel launchers (return the launch error).
 cudaError_t launch_points(const PointArgs& a, int kernel, int num_sms, cudaStream_t s);
-size_t points_smem_bytes(int kernel, int n);
+size_t points_smem_bytes(int kernel, int n, int P, int L);
+size_t points_matrix_bytes(int kernel, int n, int P);
+int points_per_cta(int kernel, int n, int L);
 int points_threads(int kernel, int n);
 cudaError_t launch_dft(const DftArgs& a, cudaStream_t s);
 cudaError_t launch_alu_peak(int fp64, int blocks, float* out_sink, int iters, cudaStream_t s);

@@ -1,21 +1,29 @@
 // Per-grid-point evaluation of log q(A, gamma, D(w)) (arXiv:2412.17742, Sec. III,
-// Eq. q_d, with one w per detector group as in Sec. VI, Eq. Lamb_lhaf_master):
+// Eq. q_d, with one w per detector group as in Sec. VI, Eq. Lamb_lhaf_master).
 //
-//   K(w)  = I - D(w) XA,  D(w) = diag(w_label(i)),  w_l = exp(2 pi i k_l / R_l)
-//   K     = L U  (unpivoted; every pivot has Re > 0 because ||XA|| < 1 and D unitary,
-//                 so K and all its Schur complements have positive-definite Hermitian part)
-//   ld    = sum_i Log u_ii  (the branch continuous from w = 0, which is the branch of the
-//                            power series of the square root in Sec. IV)
-//   x     = K^{-1} D(w) X gamma,   log q = 1/2 gamma^T x - 1/2 ld
+// With K(w) = I - D(w) XA and D = diag(w_label(i)) unitary, K = D M where
+//   M(w) = conj(D) - XA,
+// i.e. the stored matrix -XA with a new diagonal.  If M = L' U' (unit lower L') then
+// K = (D L' conj(D)) (D U') is the LU of K, so u_ii = d_i u'_ii.  Hence
+//   ld    = log det K = sum_i Log(d_i u'_ii)   (each d_i u'_ii = u_ii has Re > 0: ||XA|| < 1
+//                                              makes K and its Schur complements accretive)
+//   x     = K^{-1} D X gamma = M^{-1} X gamma  (a right-hand side shared by every point)
+//   log q = 1/2 gamma^T x - 1/2 ld.
+// The sum of principal logs is the branch continuous from w = 0 (the branch of the power
+// series of Sec. IV).  Each lane multiplies a chunk of pivots in FP64 and recovers the
+// winding of the chunk's argument from an FP32 sum of the pivot arguments (each in
+// (-pi/2, pi/2), so that sum is accurate to far better than pi).
 //
-// Two precisions share one structure (one CTA per grid point, persistent over points):
-//   FP64       every step on the FP64 pipe.
-//   FP32R      LU and solves in FP32; one refinement step: the residual E = K - L^U^ is
-//              formed with error-free FP32 transformations (exact products + compensated
-//              sums, Ogita-Rump-Oishi Dot2), then log det K = sum Log u^_ii + tr(K^^{-1} E)
-//              + O(|K^^{-1}E|^2), and x = x^ + K^^{-1}(b - K x^) with the residual formed
-//              the same way.  Only O(n) work per point touches the FP64 pipe.
-// The matrix lives in shared memory when it fits (n <= GBSBIN_SMEM_MAX_N) and otherwise
+// Two precisions share one structure: a CTA evaluates P grid points in lockstep (the
+// flat work index has the point fastest, so one warp instruction serves all P points for
+// the pivot reciprocals and every barrier is shared by P points).
+//   FP64    LU of M in FP64.
+//   FP32R   LU of fl32(M) in FP32 plus one refinement step: the residual E = M - L^U^ is
+//           formed with error-free FP32 transformations (TwoProd by FMA, Knuth TwoSum;
+//           Ogita-Rump-Oishi Dot2), log det M = sum Log u^'_ii + tr(U^^{-1} L^^{-1} E)
+//           + O(|M^^{-1}E|^2), and x = x^ + M^^{-1}(X gamma - M x^) with the residual
+//           formed the same way.  Only O(n) work per point uses the FP64 pipe.
+// Matrices live in shared memory when P of them fit (n <= GBSBIN_SMEM_MAX_N), otherwise
 // in a per-CTA slot of an L2-resident global workspace.
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -28,8 +36,7 @@ namespace gbsbin {
 __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
   return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
 }
-// a - b c
-__device__ __forceinline__ double2 cfnma(double2 a, double2 b, double2 c) {
+__device__ __forceinline__ double2 cfnma(double2 a, double2 b, double2 c) {  // a - b c
   return make_double2(fma(-b.x, c.x, fma(b.y, c.y, a.x)), fma(-b.x, c.y, fma(-b.y, c.x, a.y)));
 }
 __device__ __forceinline__ double2 crecip(double2 a) {
@@ -56,70 +63,69 @@ __device__ __forceinline__ double2 root_of_unity(long long m, int R) {
   return make_double2(c, s);
 }
 
-// Digits of evaluated point e: last axis in [0, half), the others full radix.
-__device__ void point_digits(long long e, const GridDesc& g, int* k) {
-  k[g.L - 1] = (int)(e % g.half);
+// Digit l of evaluated point e: last axis in [0, half), the others full radix.
+__device__ __forceinline__ int point_digit(long long e, const GridDesc& g, int l) {
+  int last = (int)(e % g.half);
+  if (l == g.L - 1) return last;
   long long rest = e / g.half;
-  for (int l = g.L - 2; l >= 0; --l) {
-    k[l] = (int)(rest % g.radix[l]);
-    rest /= g.radix[l];
-  }
+  for (int m = g.L - 2; m > l; --m) rest /= g.radix[m];
+  return (int)(rest % g.radix[l]);
 }
 
-// --------------------------------------------- log det from the pivots, exact branch
-// Running product of the pivots, normalised by powers of two, plus a winding count.
-// Every pivot has |Arg u| < pi/2, so the running product's argument moves by less than
-// pi/2 per factor and crosses the negative real axis only between quadrants II and III;
-// counting those crossings gives sum_i Arg u_ii exactly, with a single log and atan2.
-struct LogDetAcc {
-  double2 p;
-  int e2;
-  int wind;
-  double minre;
-};
-__device__ __forceinline__ void ldacc_init(LogDetAcc& a) {
-  a.p = make_double2(1.0, 0.0);
-  a.e2 = 0;
-  a.wind = 0;
-  a.minre = 1.0e300;
+__device__ __forceinline__ double warp_sum_d(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
 }
-__device__ __forceinline__ void ldacc_push(LogDetAcc& a, double2 u) {
-  a.minre = fmin(a.minre, u.x);
-  if (!(u.x == u.x) || !(u.y == u.y)) a.minre = -1.0e300;  // NaN marks the point bad
-  double2 q = cmul(a.p, u);
-  if (a.p.x < 0.0 && q.x < 0.0) {
-    if (a.p.y >= 0.0 && q.y < 0.0) a.wind += 1;
-    else if (a.p.y < 0.0 && q.y >= 0.0) a.wind -= 1;
-  }
-  int ex = 0;
-  double m = fmax(fabs(q.x), fabs(q.y));
-  if (m > 0.0 && m < 1.0e300) {
-    frexp(m, &ex);
-    q.x = ldexp(q.x, -ex);
-    q.y = ldexp(q.y, -ex);
-  }
-  a.e2 += ex;
-  a.p = q;
-}
-__device__ __forceinline__ double2 ldacc_log(const LogDetAcc& a) {
-  const double LN2 = 0.693147180559945309417232121458;
-  const double TWO_PI = 6.283185307179586476925286766559;
-  double re = 0.5 * log(fma(a.p.x, a.p.x, a.p.y * a.p.y)) + (double)a.e2 * LN2;
-  double im = atan2(a.p.y, a.p.x) + TWO_PI * (double)a.wind;
-  return make_double2(re, im);
-}
-
-__device__ __forceinline__ double2 warp_sum(double2 v) {
-  for (int o = 16; o > 0; o >>= 1) {
-    v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
-    v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
-  }
+__device__ __forceinline__ double warp_min_d(double v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
   return v;
 }
 
+// Sum over i of Log(d_i u'_ii) for one point, by one warp.  diag(i) returns u'_ii as
+// double2.  Returns (ld, min_i Re(d_i u'_ii)) in lane 0 (all lanes hold the sums).
+template <typename DiagFn>
+__device__ __forceinline__ void warp_logdet(int n, const double2* w, const int* lab, DiagFn diag, double2* ld,
+                                            double* minre) {
+  const int lane = threadIdx.x & 31;
+  const int chunk = (n + 31) >> 5;
+  const int i0 = lane * chunk, i1 = min(n, i0 + chunk);
+  double2 p = make_double2(1.0, 0.0);
+  int e2 = 0;
+  float argsum = 0.0f;
+  double mn = 1.0e300;
+  for (int i = i0; i < i1; ++i) {
+    double2 z = cmul(w[lab[i]], diag(i));
+    mn = fmin(mn, z.x);
+    if (!(z.x == z.x) || !(z.y == z.y)) mn = -1.0e300;
+    argsum += atan2f((float)z.y, (float)z.x);
+    p = cmul(p, z);
+    int ex;
+    double m = fmax(fabs(p.x), fabs(p.y));
+    if (m > 0.0 && m < 1.0e300) {
+      frexp(m, &ex);
+      p.x = ldexp(p.x, -ex);
+      p.y = ldexp(p.y, -ex);
+      e2 += ex;
+    }
+  }
+  const double LN2 = 0.693147180559945309417232121458;
+  const double TWO_PI = 6.283185307179586476925286766559;
+  double re = 0.0, im = 0.0;
+  if (i1 > i0) {
+    double a = atan2(p.y, p.x);
+    double wind = rint(((double)argsum - a) / TWO_PI);
+    re = 0.5 * log(fma(p.x, p.x, p.y * p.y)) + (double)e2 * LN2;
+    im = a + TWO_PI * wind;
+  }
+  re = warp_sum_d(re);
+  im = warp_sum_d(im);
+  mn = warp_min_d(mn);
+  *ld = make_double2(re, im);
+  *minre = mn;
+}
+
 // ---------------------------------------------------- error-free FP32 transformations
-// Dot2 accumulator (Ogita, Rump, Oishi, SIAM J. Sci. Comput. 26 (2005)): s is the
-// rounded running sum, c collects the exact rounding errors of every product and sum.
+// Dot2 accumulator: s is the rounded running sum, c collects the exact rounding errors.
 struct Acc2 {
   float s, c;
 };
@@ -141,92 +147,116 @@ __device__ __forceinline__ void acc2_add(Acc2& a, float v) {
 }
 __device__ __forceinline__ float acc2_value(const Acc2& a) { return a.s + a.c; }
 
+// ---------------------------------------------------------------- smem/slot layout
+// Per CTA: P matrices (stride S = n*n + 1 elements, the extra element staggers the
+// points across banks), for FP32R a second set for the residual, then small vectors.
+struct Layout {
+  int P, logP, n, S;
+};
+__host__ __device__ inline int layout_stride(int n) { return n * n + 1; }
+
 // ------------------------------------------------------------------------ FP64 path
 template <int NT, bool SMEM>
 __global__ void __launch_bounds__(NT) k_points_fp64(PointArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const int n = a.n;
-  const int tid = threadIdx.x;
-  double2* vec = (double2*)smem;
-  double2* dv = vec;            // n twiddles of the rows
-  double2* xv = vec + n;        // n right-hand side / solution
-  double2* pinv = vec + 2 * n;  // n reciprocal pivots
-  double2* A = SMEM ? (vec + 3 * n)
-                    : (double2*)((char*)a.gws + (size_t)blockIdx.x * (size_t)a.gws_slot_bytes);
-  __shared__ int kd[GBSBIN_MAX_L];
+  const int n = a.n, P = a.P, logP = a.logP, L = a.grid.L;
+  const int S = layout_stride(n);
+  const int tid = threadIdx.x, warp = tid >> 5, nwarps = NT / 32;
+  double2* A;
+  double2* vec;
+  if (SMEM) {
+    A = (double2*)smem;
+    vec = A + (size_t)P * S;
+  } else {
+    A = (double2*)((char*)a.gws + (size_t)blockIdx.x * (size_t)a.gws_slot_bytes);
+    vec = (double2*)smem;
+  }
+  double2* w = vec;                    // P x L twiddles
+  double2* pinv = w + P * L;           // P x n reciprocal pivots
+  double2* xv = pinv + (size_t)P * n;  // P x n solution
+  int* lab = (int*)(xv + (size_t)P * n);
+  for (int i = tid; i < n; i += NT) lab[i] = a.label[i];
 
-  for (long long e = blockIdx.x; e < a.grid.n_eval; e += gridDim.x) {
-    if (tid == 0) point_digits(e, a.grid, kd);
-    __syncthreads();
-    for (int i = tid; i < n; i += NT) {
-      int l = a.label[i];
-      dv[i] = root_of_unity(kd[l], a.grid.radix[l]);
+  const long long step = (long long)gridDim.x * P;
+  for (long long e0 = (long long)blockIdx.x * P; e0 < a.grid.n_eval; e0 += step) {
+    for (int t = tid; t < P * L; t += NT) {
+      int p = t / L, l = t - p * L;
+      long long e = min(e0 + p, a.grid.n_eval - 1);
+      w[t] = root_of_unity(point_digit(e, a.grid, l), a.grid.radix[l]);
     }
     __syncthreads();
-    // K = I - D(w) XA
-    for (int t = tid; t < n * n; t += NT) {
-      int i = t / n, j = t - i * n;
-      double2 dx = cmul(dv[i], a.XA[t]);
-      A[t] = make_double2((i == j ? 1.0 : 0.0) - dx.x, -dx.y);
+    // M = conj(D) - XA
+    for (int t = tid; t < P * n * n; t += NT) {
+      int p = t & (P - 1), r = t >> logP;
+      int i = r / n, j = r - i * n;
+      double2 v = a.NXA[r];
+      if (i == j) {
+        double2 d = w[p * L + lab[i]];
+        v.x += d.x;
+        v.y -= d.y;
+      }
+      A[(size_t)p * S + r] = v;
     }
     __syncthreads();
-
-    LogDetAcc acc;
-    if (tid == 0) {
-      ldacc_init(acc);
-      double2 u = A[0];
-      ldacc_push(acc, u);
-      pinv[0] = crecip(u);
-    }
+    if (tid < P) pinv[tid * n] = crecip(A[(size_t)tid * S]);
     __syncthreads();
-    // right-looking Doolittle LU without pivoting
     for (int k = 0; k < n - 1; ++k) {
       const int m = n - 1 - k;
-      const double2 inv = pinv[k];
-      for (int i = k + 1 + tid; i < n; i += NT) A[(size_t)i * n + k] = cmul(A[(size_t)i * n + k], inv);
+      for (int t = tid; t < P * m; t += NT) {
+        int p = t & (P - 1);
+        size_t i = k + 1 + (t >> logP);
+        double2* Ap = A + (size_t)p * S;
+        Ap[i * n + k] = cmul(Ap[i * n + k], pinv[p * n + k]);
+      }
       __syncthreads();
-      for (int t = tid; t < m * m; t += NT) {
-        int ii = t / m, jj = t - ii * m;
+      for (int t = tid; t < P * m * m; t += NT) {
+        int p = t & (P - 1), r = t >> logP;
+        int ii = r / m, jj = r - ii * m;
         size_t i = k + 1 + ii, j = k + 1 + jj;
-        double2 v = cfnma(A[i * n + j], A[i * n + k], A[(size_t)k * n + j]);
-        A[i * n + j] = v;
-        if (t == 0) {  // u_{k+1,k+1} is final now; thread 0 owns it in every step
-          ldacc_push(acc, v);
-          pinv[k + 1] = crecip(v);
-        }
+        double2* Ap = A + (size_t)p * S;
+        double2 v = cfnma(Ap[i * n + j], Ap[i * n + k], Ap[(size_t)k * n + j]);
+        Ap[i * n + j] = v;
+        if (r == 0) pinv[p * n + k + 1] = crecip(v);
       }
       __syncthreads();
     }
-
-    // exponent: x = U^{-1} L^{-1} D X gamma, one warp, warp-synchronous
-    double2 expo = make_double2(0.0, 0.0);
-    if (a.has_gamma && tid < 32) {
-      const int lane = tid;
-      for (int i = lane; i < n; i += 32) xv[i] = cmul(dv[i], a.Xgamma[i]);
-      __syncwarp();
-      for (int k = 0; k < n - 1; ++k) {
-        double2 yk = xv[k];
-        for (int i = k + 1 + lane; i < n; i += 32) xv[i] = cfnma(xv[i], A[(size_t)i * n + k], yk);
+    // per point: log det and exponent, one warp per point
+    for (int p = warp; p < P; p += nwarps) {
+      const long long e = e0 + p;
+      const double2* Ap = A + (size_t)p * S;
+      double2 ld;
+      double mn;
+      warp_logdet(n, w + p * L, lab, [&](int i) { return Ap[(size_t)i * n + i]; }, &ld, &mn);
+      double2 expo = make_double2(0.0, 0.0);
+      if (a.has_gamma) {
+        const int lane = tid & 31;
+        double2* x = xv + (size_t)p * n;
+        for (int i = lane; i < n; i += 32) x[i] = a.Xgamma[i];
         __syncwarp();
+        for (int k = 0; k < n - 1; ++k) {
+          double2 yk = x[k];
+          for (int i = k + 1 + lane; i < n; i += 32) x[i] = cfnma(x[i], Ap[(size_t)i * n + k], yk);
+          __syncwarp();
+        }
+        for (int k = n - 1; k >= 0; --k) {
+          double2 xk = cmul(x[k], pinv[p * n + k]);
+          __syncwarp();
+          if (lane == 0) x[k] = xk;
+          for (int i = lane; i < k; i += 32) x[i] = cfnma(x[i], Ap[(size_t)i * n + k], xk);
+          __syncwarp();
+        }
+        double sr = 0.0, si = 0.0;
+        for (int i = lane; i < n; i += 32) {
+          double2 g = a.gamma[i];
+          sr += g.x * x[i].x - g.y * x[i].y;
+          si += g.x * x[i].y + g.y * x[i].x;
+        }
+        expo = make_double2(warp_sum_d(sr), warp_sum_d(si));
       }
-      for (int k = n - 1; k >= 0; --k) {
-        double2 xk = cmul(xv[k], pinv[k]);
-        __syncwarp();
-        if (lane == 0) xv[k] = xk;
-        for (int i = lane; i < k; i += 32) xv[i] = cfnma(xv[i], A[(size_t)i * n + k], xk);
-        __syncwarp();
+      if ((tid & 31) == 0 && e < a.grid.n_eval) {
+        a.logq[e] = make_double2(0.5 * expo.x - 0.5 * ld.x, 0.5 * expo.y - 0.5 * ld.y);
+        a.minpiv[e] = mn;
       }
-      double2 s = make_double2(0.0, 0.0);
-      for (int i = lane; i < n; i += 32) {
-        double2 g = a.gamma[i];
-        s = make_double2(s.x + g.x * xv[i].x - g.y * xv[i].y, s.y + g.x * xv[i].y + g.y * xv[i].x);
-      }
-      expo = warp_sum(s);
-    }
-    if (tid == 0) {
-      double2 ld = ldacc_log(acc);
-      a.logq[e] = make_double2(0.5 * expo.x - 0.5 * ld.x, 0.5 * expo.y - 0.5 * ld.y);
-      a.minpiv[e] = acc.minre;
     }
     __syncthreads();
   }
@@ -236,237 +266,278 @@ __global__ void __launch_bounds__(NT) k_points_fp64(PointArgs a) {
 template <int NT, bool SMEM>
 __global__ void __launch_bounds__(NT) k_points_fp32r(PointArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const int n = a.n;
-  const int tid = threadIdx.x;
-  double2* dv = (double2*)smem;            // n FP64 twiddles
-  float2* dh = (float2*)(dv + n);          // n twiddles, high FP32 part
-  float2* dl = dh + n;                     // n twiddles, low FP32 part
-  float2* xv = dl + n;                     // n solution
-  float2* rv = xv + n;                     // n residual / correction
-  float2* pinv = rv + n;                   // n reciprocal pivots
+  const int n = a.n, P = a.P, logP = a.logP, L = a.grid.L;
+  const int S = layout_stride(n);
+  const int tid = threadIdx.x, warp = tid >> 5, nwarps = NT / 32;
+  const int nstrip = (n + 3) >> 2;   // 4-column strips
   float2* A;
   float2* E;
+  unsigned char* vbase;
   if (SMEM) {
-    A = pinv + n;
-    E = A + (size_t)n * n;
+    A = (float2*)smem;
+    E = A + (size_t)P * S;
+    vbase = (unsigned char*)(E + (size_t)P * S);
   } else {
     A = (float2*)((char*)a.gws + (size_t)blockIdx.x * (size_t)a.gws_slot_bytes);
-    E = A + (size_t)n * n;
+    E = A + (size_t)P * S;
+    vbase = smem;
   }
-  __shared__ int kd[GBSBIN_MAX_L];
-  __shared__ double2 red[NT / 32];
+  vbase = (unsigned char*)(((uintptr_t)vbase + 15) & ~(uintptr_t)15);
+  double2* w = (double2*)vbase;          // P x L twiddles (FP64)
+  float2* pinv = (float2*)(w + P * L);   // P x n
+  float2* xv = pinv + (size_t)P * n;     // P x n
+  float2* rv = xv + (size_t)P * n;       // P x n
+  double2* delta = (double2*)(rv + (size_t)P * n);  // P trace corrections
+  int* lab = (int*)(delta + P);
+  for (int i = tid; i < n; i += NT) lab[i] = a.label[i];
 
-  for (long long e = blockIdx.x; e < a.grid.n_eval; e += gridDim.x) {
-    if (tid == 0) point_digits(e, a.grid, kd);
-    __syncthreads();
-    for (int i = tid; i < n; i += NT) {
-      int l = a.label[i];
-      double2 w = root_of_unity(kd[l], a.grid.radix[l]);
-      dv[i] = w;
-      float2 hi = make_float2((float)w.x, (float)w.y);
-      dh[i] = hi;
-      dl[i] = make_float2((float)(w.x - (double)hi.x), (float)(w.y - (double)hi.y));
+  const long long step = (long long)gridDim.x * P;
+  for (long long e0 = (long long)blockIdx.x * P; e0 < a.grid.n_eval; e0 += step) {
+    for (int t = tid; t < P * L; t += NT) {
+      int p = t / L, l = t - p * L;
+      long long e = min(e0 + p, a.grid.n_eval - 1);
+      w[t] = root_of_unity(point_digit(e, a.grid, l), a.grid.radix[l]);
     }
     __syncthreads();
-    // K^ = fl32(I - dh XA_hi); whatever it misses of K is put back by the residual
-    for (int t = tid; t < n * n; t += NT) {
-      int i = t / n, j = t - i * n;
-      float2 dx = cmulf(dh[i], a.XA_hi[t]);
-      A[t] = make_float2((i == j ? 1.0f : 0.0f) - dx.x, -dx.y);
+    // M^ = fl32(conj(D) - XA): off-diagonal NXA_hi, diagonal rounded from FP64
+    for (int t = tid; t < P * n * n; t += NT) {
+      int p = t & (P - 1), r = t >> logP;
+      int i = r / n, j = r - i * n;
+      float2 v = a.NXA_hi[r];
+      if (i == j) {
+        double2 d = w[p * L + lab[i]];
+        double2 x = a.NXA[r];
+        v = make_float2((float)(x.x + d.x), (float)(x.y - d.y));
+      }
+      A[(size_t)p * S + r] = v;
     }
     __syncthreads();
-
-    LogDetAcc acc;
-    if (tid == 0) {
-      ldacc_init(acc);
-      float2 u = A[0];
-      ldacc_push(acc, make_double2(u.x, u.y));
-      pinv[0] = crecipf(u);
-    }
+    if (tid < P) pinv[tid * n] = crecipf(A[(size_t)tid * S]);
     __syncthreads();
     for (int k = 0; k < n - 1; ++k) {
       const int m = n - 1 - k;
-      const float2 inv = pinv[k];
-      for (int i = k + 1 + tid; i < n; i += NT) A[(size_t)i * n + k] = cmulf(A[(size_t)i * n + k], inv);
+      for (int t = tid; t < P * m; t += NT) {
+        int p = t & (P - 1);
+        size_t i = k + 1 + (t >> logP);
+        float2* Ap = A + (size_t)p * S;
+        Ap[i * n + k] = cmulf(Ap[i * n + k], pinv[p * n + k]);
+      }
       __syncthreads();
-      for (int t = tid; t < m * m; t += NT) {
-        int ii = t / m, jj = t - ii * m;
+      for (int t = tid; t < P * m * m; t += NT) {
+        int p = t & (P - 1), r = t >> logP;
+        int ii = r / m, jj = r - ii * m;
         size_t i = k + 1 + ii, j = k + 1 + jj;
-        float2 v = cfnmaf(A[i * n + j], A[i * n + k], A[(size_t)k * n + j]);
-        A[i * n + j] = v;
-        if (t == 0) {
-          ldacc_push(acc, make_double2(v.x, v.y));
-          pinv[k + 1] = crecipf(v);
-        }
+        float2* Ap = A + (size_t)p * S;
+        float2 v = cfnmaf(Ap[i * n + j], Ap[i * n + k], Ap[(size_t)k * n + j]);
+        Ap[i * n + j] = v;
+        if (r == 0) pinv[p * n + k + 1] = crecipf(v);
       }
       __syncthreads();
     }
 
-    // residual E = K - L^ U^ with K = I - (dh + dl)(XA_hi + XA_lo), by Dot2
-    for (int t = tid; t < n * n; t += NT) {
-      int i = t / n, j = t - i * n;
-      Acc2 re = {i == j ? 1.0f : 0.0f, 0.0f}, im = {0.0f, 0.0f};
-      const float2 d_h = dh[i], d_l = dl[i], x_h = a.XA_hi[t], x_l = a.XA_lo[t];
-      // - d x = -(dr xr - di xi) - i (dr xi + di xr), each real product split hi/lo
-      acc2_add_prod(re, -d_h.x, x_h.x);
-      acc2_add_prod(re, d_h.y, x_h.y);
-      acc2_add_prod(re, -d_h.x, x_l.x);
-      acc2_add_prod(re, d_h.y, x_l.y);
-      acc2_add_prod(re, -d_l.x, x_h.x);
-      acc2_add_prod(re, d_l.y, x_h.y);
-      acc2_add_prod(im, -d_h.x, x_h.y);
-      acc2_add_prod(im, -d_h.y, x_h.x);
-      acc2_add_prod(im, -d_h.x, x_l.y);
-      acc2_add_prod(im, -d_h.y, x_l.x);
-      acc2_add_prod(im, -d_l.x, x_h.y);
-      acc2_add_prod(im, -d_l.y, x_h.x);
-      // - sum_{k < min(i,j)} L_ik U_kj - (i <= j ? U_ij : L_ij U_jj)
-      const int kmax = i < j ? i : j;
-      const float2* Lrow = A + (size_t)i * n;
+    // residual E = M - L^U^, 4-column strips, Dot2 per entry
+    for (int t = tid; t < P * n * nstrip; t += NT) {
+      int p = t & (P - 1), r = t >> logP;
+      int i = r / nstrip, j0 = (r - i * nstrip) * 4;
+      const float2* Ap = A + (size_t)p * S;
+      Acc2 re[4], im[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        re[c] = Acc2{0.0f, 0.0f};
+        im[c] = Acc2{0.0f, 0.0f};
+      }
+      const int kmax = min(i, j0 + 3);
       for (int k = 0; k < kmax; ++k) {
-        float2 l = Lrow[k], u = A[(size_t)k * n + j];
-        acc2_add_prod(re, -l.x, u.x);
-        acc2_add_prod(re, l.y, u.y);
-        acc2_add_prod(im, -l.x, u.y);
-        acc2_add_prod(im, -l.y, u.x);
+        const float2 l = Ap[(size_t)i * n + k];
+        const float2* urow = Ap + (size_t)k * n + j0;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          if (k < j0 + c && j0 + c < n) {
+            const float2 u = urow[c];
+            acc2_add_prod(re[c], -l.x, u.x);
+            acc2_add_prod(re[c], l.y, u.y);
+            acc2_add_prod(im[c], -l.x, u.y);
+            acc2_add_prod(im[c], -l.y, u.x);
+          }
+        }
       }
-      if (i <= j) {
-        float2 u = A[t];
-        acc2_add(re, -u.x);
-        acc2_add(im, -u.y);
-      } else {
-        float2 l = A[t], u = A[(size_t)j * n + j];
-        acc2_add_prod(re, -l.x, u.x);
-        acc2_add_prod(re, l.y, u.y);
-        acc2_add_prod(im, -l.x, u.y);
-        acc2_add_prod(im, -l.y, u.x);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int j = j0 + c;
+        if (j >= n) break;
+        const size_t ij = (size_t)i * n + j;
+        if (i <= j) {                       // k = i term: L_ii U_ij = U_ij
+          const float2 u = Ap[ij];
+          acc2_add(re[c], -u.x);
+          acc2_add(im[c], -u.y);
+        } else {                            // k = j term: L_ij U_jj
+          const float2 l = Ap[ij], u = Ap[(size_t)j * n + j];
+          acc2_add_prod(re[c], -l.x, u.x);
+          acc2_add_prod(re[c], l.y, u.y);
+          acc2_add_prod(im[c], -l.x, u.y);
+          acc2_add_prod(im[c], -l.y, u.x);
+        }
+        // + M_ij = NXA_hi + NXA_lo (+ conj(d) on the diagonal, as dh + dl)
+        const float2 xh = a.NXA_hi[ij], xl = a.NXA_lo[ij];
+        acc2_add(re[c], xh.x);
+        acc2_add(re[c], xl.x);
+        acc2_add(im[c], xh.y);
+        acc2_add(im[c], xl.y);
+        if (i == j) {
+          const double2 d = w[p * L + lab[i]];
+          const float dhx = (float)d.x, dhy = (float)d.y;
+          acc2_add(re[c], dhx);
+          acc2_add(re[c], (float)(d.x - (double)dhx));
+          acc2_add(im[c], -dhy);
+          acc2_add(im[c], -(float)(d.y - (double)dhy));
+        }
+        E[(size_t)p * S + ij] = make_float2(acc2_value(re[c]), acc2_value(im[c]));
       }
-      E[t] = make_float2(acc2_value(re), acc2_value(im));
     }
     __syncthreads();
 
-    // Z = L^^{-1} E in place (unit lower, all columns)
+    // Z = L^^{-1} E in place (unit lower, all columns), 4-column strips
     for (int k = 0; k < n - 1; ++k) {
       const int rows = n - 1 - k;
-      for (int t = tid; t < rows * n; t += NT) {
-        int ii = t / n, j = t - ii * n;
+      for (int t = tid; t < P * rows * nstrip; t += NT) {
+        int p = t & (P - 1), r = t >> logP;
+        int ii = r / nstrip, j0 = (r - ii * nstrip) * 4;
         size_t i = k + 1 + ii;
-        E[i * n + j] = cfnmaf(E[i * n + j], A[i * n + k], E[(size_t)k * n + j]);
+        const float2 l = A[(size_t)p * S + i * n + k];
+        float2* Ei = E + (size_t)p * S + i * n;
+        const float2* Ek = E + (size_t)p * S + (size_t)k * n;
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+          if (j0 + c < n) Ei[j0 + c] = cfnmaf(Ei[j0 + c], l, Ek[j0 + c]);
       }
       __syncthreads();
     }
-    // X = U^^{-1} Z, only X[m][c] with m >= c (what diag(X) needs); row k is scaled by
-    // the thread that makes its last update, so one barrier per step suffices
-    for (int c = tid; c < n; c += NT) E[(size_t)(n - 1) * n + c] = cmulf(E[(size_t)(n - 1) * n + c], pinv[n - 1]);
+    // X = U^^{-1} Z, only X[m][c] with m >= c (what diag(X) needs).  Row k-1 receives its
+    // last update in step k, so the updater scales it at once: one barrier per step.
+    for (int t = tid; t < P * n; t += NT) {
+      int p = t & (P - 1), c = t >> logP;
+      float2* Ep = E + (size_t)p * S + (size_t)(n - 1) * n;
+      Ep[c] = cmulf(Ep[c], pinv[p * n + n - 1]);
+    }
     __syncthreads();
     for (int k = n - 1; k >= 1; --k) {
-      // rows i < k, columns c <= i: Z[i][c] -= U[i][k] X[k][c]
-      const int cnt = k * (k + 1) / 2;
-      for (int t = tid; t < cnt; t += NT) {
-        // t -> (i, c) with 0 <= c <= i < k, row-major over the triangle
-        int i = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
-        while ((i + 1) * (i + 2) / 2 <= t) ++i;
-        while (i * (i + 1) / 2 > t) --i;
-        int c = t - i * (i + 1) / 2;
-        float2 v = cfnmaf(E[(size_t)i * n + c], A[(size_t)i * n + k], E[(size_t)k * n + c]);
-        if (i == k - 1) v = cmulf(v, pinv[k - 1]);
-        E[(size_t)i * n + c] = v;
+      const int cs = (k + 3) >> 2;          // column strips over c < k
+      for (int t = tid; t < P * k * cs; t += NT) {
+        int p = t & (P - 1), r = t >> logP;
+        int i = r / cs, c0 = (r - i * cs) * 4;
+        if (c0 > i) continue;
+        const float2 u = A[(size_t)p * S + (size_t)i * n + k];
+        const float2 sc = pinv[p * n + (k - 1)];
+        float2* Ei = E + (size_t)p * S + (size_t)i * n;
+        const float2* Ek = E + (size_t)p * S + (size_t)k * n;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const int cc = c0 + c;
+          if (cc <= i) {
+            float2 v = cfnmaf(Ei[cc], u, Ek[cc]);
+            if (i == k - 1) v = cmulf(v, sc);
+            Ei[cc] = v;
+          }
+        }
       }
       __syncthreads();
     }
-    // delta = tr(U^^{-1} L^^{-1} E) in FP64
-    double2 s = make_double2(0.0, 0.0);
-    for (int c = tid; c < n; c += NT) {
-      float2 v = E[(size_t)c * n + c];
-      s.x += v.x;
-      s.y += v.y;
+    // delta_p = tr(U^^{-1} L^^{-1} E), one warp per point, FP64 sum
+    for (int p = warp; p < P; p += nwarps) {
+      double sr = 0.0, si = 0.0;
+      for (int c = (tid & 31); c < n; c += 32) {
+        float2 v = E[(size_t)p * S + (size_t)c * n + c];
+        sr += v.x;
+        si += v.y;
+      }
+      sr = warp_sum_d(sr);
+      si = warp_sum_d(si);
+      if ((tid & 31) == 0) delta[p] = make_double2(sr, si);
     }
-    s = warp_sum(s);
-    if ((tid & 31) == 0) red[tid >> 5] = s;
-    __syncthreads();
+    __syncwarp();
 
-    // exponent with one refinement step (warp 0)
-    double2 expo = make_double2(0.0, 0.0);
-    if (a.has_gamma && tid < 32) {
-      const int lane = tid;
-      // x^ = K^^{-1} fl32(d X gamma)
-      for (int i = lane; i < n; i += 32) xv[i] = cmulf(dh[i], a.Xg_hi[i]);
-      __syncwarp();
-      for (int pass = 0; pass < 2; ++pass) {
-        float2* v = pass == 0 ? xv : rv;
-        for (int k = 0; k < n - 1; ++k) {
-          float2 yk = v[k];
-          for (int i = k + 1 + lane; i < n; i += 32) v[i] = cfnmaf(v[i], A[(size_t)i * n + k], yk);
-          __syncwarp();
-        }
-        for (int k = n - 1; k >= 0; --k) {
-          float2 xk = cmulf(v[k], pinv[k]);
-          __syncwarp();
-          if (lane == 0) v[k] = xk;
-          for (int i = lane; i < k; i += 32) v[i] = cfnmaf(v[i], A[(size_t)i * n + k], xk);
-          __syncwarp();
-        }
-        if (pass == 0) {
-          // r = d X gamma - K x^ = d X gamma - x^ + d (XA x^), by Dot2 per row
-          for (int i = lane; i < n; i += 32) {
-            Acc2 sr = {0.0f, 0.0f}, si = {0.0f, 0.0f};
-            for (int j = 0; j < n; ++j) {
-              float2 xh = a.XA_hi[(size_t)i * n + j], xl = a.XA_lo[(size_t)i * n + j], y = xv[j];
-              acc2_add_prod(sr, xh.x, y.x);
-              acc2_add_prod(sr, -xh.y, y.y);
-              acc2_add_prod(sr, xl.x, y.x);
-              acc2_add_prod(sr, -xl.y, y.y);
-              acc2_add_prod(si, xh.x, y.y);
-              acc2_add_prod(si, xh.y, y.x);
-              acc2_add_prod(si, xl.x, y.y);
-              acc2_add_prod(si, xl.y, y.x);
-            }
-            // u = (XA x^)_i as a float pair (sr.s + sr.c, si.s + si.c); t = Xgamma + u
-            float2 gh = a.Xg_hi[i], gl = a.Xg_lo[i];
-            Acc2 tr = {0.0f, 0.0f}, ti = {0.0f, 0.0f};
-            float ur = sr.s, urc = sr.c, ui = si.s, uic = si.c;
-            // d * (Xgamma + u) - x^, with d = dh + dl
-            const float2 d_h = dh[i], d_l = dl[i];
-            const float pr[4] = {gh.x, gl.x, ur, urc};
-            const float pi_[4] = {gh.y, gl.y, ui, uic};
-            for (int q = 0; q < 4; ++q) {
-              acc2_add_prod(tr, d_h.x, pr[q]);
-              acc2_add_prod(tr, -d_h.y, pi_[q]);
-              acc2_add_prod(ti, d_h.x, pi_[q]);
-              acc2_add_prod(ti, d_h.y, pr[q]);
-            }
-            acc2_add_prod(tr, d_l.x, pr[0] + pr[2]);
-            acc2_add_prod(tr, -d_l.y, pi_[0] + pi_[2]);
-            acc2_add_prod(ti, d_l.x, pi_[0] + pi_[2]);
-            acc2_add_prod(ti, d_l.y, pr[0] + pr[2]);
-            acc2_add(tr, -xv[i].x);
-            acc2_add(ti, -xv[i].y);
-            rv[i] = make_float2(acc2_value(tr), acc2_value(ti));
+    for (int p = warp; p < P; p += nwarps) {
+      const long long e = e0 + p;
+      const float2* Ap = A + (size_t)p * S;
+      const int lane = tid & 31;
+      double2 ld;
+      double mn;
+      warp_logdet(n, w + p * L, lab,
+                  [&](int i) { float2 u = Ap[(size_t)i * n + i]; return make_double2(u.x, u.y); }, &ld, &mn);
+      double2 expo = make_double2(0.0, 0.0);
+      if (a.has_gamma) {
+        float2* x = xv + (size_t)p * n;
+        float2* rr = rv + (size_t)p * n;
+        const double2* wp = w + p * L;
+        for (int i = lane; i < n; i += 32) x[i] = a.Xg_hi[i];
+        __syncwarp();
+        for (int pass = 0; pass < 2; ++pass) {
+          float2* v = pass == 0 ? x : rr;
+          for (int k = 0; k < n - 1; ++k) {
+            float2 yk = v[k];
+            for (int i = k + 1 + lane; i < n; i += 32) v[i] = cfnmaf(v[i], Ap[(size_t)i * n + k], yk);
+            __syncwarp();
           }
-          __syncwarp();
+          for (int k = n - 1; k >= 0; --k) {
+            float2 xk = cmulf(v[k], pinv[p * n + k]);
+            __syncwarp();
+            if (lane == 0) v[k] = xk;
+            for (int i = lane; i < k; i += 32) v[i] = cfnmaf(v[i], Ap[(size_t)i * n + k], xk);
+            __syncwarp();
+          }
+          if (pass == 0) {
+            // r = X gamma - M x^ = X gamma - conj(d) x^ - NXA x^, Dot2 per row
+            for (int i = lane; i < n; i += 32) {
+              Acc2 sr = {0.0f, 0.0f}, si = {0.0f, 0.0f};
+              const float2 gh = a.Xg_hi[i], gl = a.Xg_lo[i];
+              acc2_add(sr, gh.x);
+              acc2_add(sr, gl.x);
+              acc2_add(si, gh.y);
+              acc2_add(si, gl.y);
+              for (int j = 0; j < n; ++j) {
+                const float2 xh = a.NXA_hi[(size_t)i * n + j], xl = a.NXA_lo[(size_t)i * n + j], y = x[j];
+                acc2_add_prod(sr, -xh.x, y.x);
+                acc2_add_prod(sr, xh.y, y.y);
+                acc2_add_prod(sr, -xl.x, y.x);
+                acc2_add_prod(sr, xl.y, y.y);
+                acc2_add_prod(si, -xh.x, y.y);
+                acc2_add_prod(si, -xh.y, y.x);
+                acc2_add_prod(si, -xl.x, y.y);
+                acc2_add_prod(si, -xl.y, y.x);
+              }
+              // - conj(d) x^ = -(dr xr + di xi) - i (dr xi - di xr), d = dh + dl
+              const double2 d = wp[lab[i]];
+              const float dhx = (float)d.x, dhy = (float)d.y;
+              const float dlx = (float)(d.x - (double)dhx), dly = (float)(d.y - (double)dhy);
+              const float2 y = x[i];
+              acc2_add_prod(sr, -dhx, y.x);
+              acc2_add_prod(sr, -dhy, y.y);
+              acc2_add_prod(si, -dhx, y.y);
+              acc2_add_prod(si, dhy, y.x);
+              acc2_add_prod(sr, -dlx, y.x);
+              acc2_add_prod(sr, -dly, y.y);
+              acc2_add_prod(si, -dlx, y.y);
+              acc2_add_prod(si, dly, y.x);
+              rr[i] = make_float2(acc2_value(sr), acc2_value(si));
+            }
+            __syncwarp();
+          }
         }
+        double sr = 0.0, si = 0.0;
+        for (int i = lane; i < n; i += 32) {
+          double xr = (double)x[i].x + (double)rr[i].x, xi = (double)x[i].y + (double)rr[i].y;
+          double gr = (double)a.g_hi[i].x + (double)a.g_lo[i].x, gi = (double)a.g_hi[i].y + (double)a.g_lo[i].y;
+          sr += gr * xr - gi * xi;
+          si += gr * xi + gi * xr;
+        }
+        expo = make_double2(warp_sum_d(sr), warp_sum_d(si));
       }
-      // x = x^ + dx; 1/2 gamma^T x in FP64 with gamma = g_hi + g_lo
-      double2 sx = make_double2(0.0, 0.0);
-      for (int i = lane; i < n; i += 32) {
-        double xr = (double)xv[i].x + (double)rv[i].x, xi = (double)xv[i].y + (double)rv[i].y;
-        double gr = (double)a.g_hi[i].x + (double)a.g_lo[i].x, gi = (double)a.g_hi[i].y + (double)a.g_lo[i].y;
-        sx.x += gr * xr - gi * xi;
-        sx.y += gr * xi + gi * xr;
+      if (lane == 0 && e < a.grid.n_eval) {
+        ld.x += delta[p].x;
+        ld.y += delta[p].y;
+        a.logq[e] = make_double2(0.5 * expo.x - 0.5 * ld.x, 0.5 * expo.y - 0.5 * ld.y);
+        a.minpiv[e] = mn;
       }
-      expo = warp_sum(sx);
-    }
-    if (tid == 0) {
-      double2 delta = make_double2(0.0, 0.0);
-      for (int w = 0; w < NT / 32; ++w) {
-        delta.x += red[w].x;
-        delta.y += red[w].y;
-      }
-      double2 ld = ldacc_log(acc);
-      ld.x += delta.x;
-      ld.y += delta.y;
-      a.logq[e] = make_double2(0.5 * expo.x - 0.5 * ld.x, 0.5 * expo.y - 0.5 * ld.y);
-      a.minpiv[e] = acc.minre;
     }
     __syncthreads();
   }
@@ -477,19 +548,37 @@ static int threads_for(int n) { return n <= 48 ? 128 : 256; }
 
 int points_threads(int kernel, int n) { return threads_for(n); }
 
-size_t points_smem_bytes(int kernel, int n) {
-  switch (kernel) {
-    case GBSBIN_KERNEL_SMEM_FP64: return (size_t)3 * n * 16 + (size_t)n * n * 16;
-    case GBSBIN_KERNEL_GMEM_FP64: return (size_t)3 * n * 16;
-    case GBSBIN_KERNEL_SMEM_FP32R: return (size_t)n * 16 + (size_t)5 * n * 8 + (size_t)2 * n * n * 8;
-    case GBSBIN_KERNEL_GMEM_FP32R: return (size_t)n * 16 + (size_t)5 * n * 8;
-  }
-  return 0;
+static size_t vec_bytes(int kernel, int n, int P, int L) {
+  bool fp64 = (kernel == GBSBIN_KERNEL_SMEM_FP64 || kernel == GBSBIN_KERNEL_GMEM_FP64);
+  if (fp64) return (size_t)P * L * 16 + (size_t)2 * P * n * 16 + (size_t)n * 4 + 16;
+  return 16 + (size_t)P * L * 16 + (size_t)3 * P * n * 8 + (size_t)P * 16 + (size_t)n * 4 + 16;
+}
+
+size_t points_matrix_bytes(int kernel, int n, int P) {
+  bool fp64 = (kernel == GBSBIN_KERNEL_SMEM_FP64 || kernel == GBSBIN_KERNEL_GMEM_FP64);
+  size_t S = (size_t)layout_stride(n);
+  return fp64 ? (size_t)P * S * 16 : (size_t)2 * P * S * 8;
+}
+
+size_t points_smem_bytes(int kernel, int n, int P, int L) {
+  bool smem = (kernel == GBSBIN_KERNEL_SMEM_FP64 || kernel == GBSBIN_KERNEL_SMEM_FP32R);
+  return (smem ? points_matrix_bytes(kernel, n, P) : 0) + vec_bytes(kernel, n, P, L);
+}
+
+int points_per_cta(int kernel, int n, int L) {
+  bool smem = (kernel == GBSBIN_KERNEL_SMEM_FP64 || kernel == GBSBIN_KERNEL_SMEM_FP32R);
+  if (!smem) return 1;
+  // largest power of two <= 8 whose shared-memory footprint leaves room for 2 CTAs per SM
+  // (or 1 CTA when even a single matrix is large)
+  const size_t budget2 = 110 * 1024, budget1 = 220 * 1024;
+  for (int P = 8; P >= 1; P >>= 1)
+    if (points_smem_bytes(kernel, n, P, L) <= budget2) return P;
+  return points_smem_bytes(kernel, n, 1, L) <= budget1 ? 1 : 0;
 }
 
 template <int NT>
 static cudaError_t launch_nt(const PointArgs& a, int kernel, int num_sms, cudaStream_t s) {
-  size_t smem = points_smem_bytes(kernel, a.n);
+  size_t smem = points_smem_bytes(kernel, a.n, a.P, a.grid.L);
   void (*fn)(PointArgs) = nullptr;
   switch (kernel) {
     case GBSBIN_KERNEL_SMEM_FP64: fn = k_points_fp64<NT, true>; break;
@@ -501,8 +590,9 @@ static cudaError_t launch_nt(const PointArgs& a, int kernel, int num_sms, cudaSt
   cudaError_t err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
   long long grid;
+  const long long groups = (a.grid.n_eval + a.P - 1) / a.P;
   if (kernel == GBSBIN_KERNEL_GMEM_FP64 || kernel == GBSBIN_KERNEL_GMEM_FP32R) {
-    grid = num_sms;  // one workspace slot per CTA, one CTA per SM
+    grid = num_sms;  // one workspace slot per CTA
   } else {
     int per_sm = 0;
     err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, NT, smem);
@@ -510,7 +600,7 @@ static cudaError_t launch_nt(const PointArgs& a, int kernel, int num_sms, cudaSt
     if (per_sm < 1) per_sm = 1;
     grid = (long long)per_sm * num_sms;
   }
-  if (grid > a.grid.n_eval) grid = a.grid.n_eval;
+  if (grid > groups) grid = groups;
   if (grid < 1) grid = 1;
   fn<<<(unsigned)grid, NT, smem, s>>>(a);
   return cudaGetLastError();
