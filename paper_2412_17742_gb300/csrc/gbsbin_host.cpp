@@ -60,7 +60,7 @@ int validate_shape(const gbsbin_problem* p, const gbsbin_options* o) {
   if (!p->sigma1 && (!p->r || !p->T)) return GBSBIN_ERR_ARG;
   if (o->precision != GBSBIN_FP64 && o->precision != GBSBIN_FP32_REFINE) return GBSBIN_ERR_ARG;
   if (o->oversample < 1) return GBSBIN_ERR_ARG;
-  if (o->tile_override < 0 || o->tile_override > GBSBIN_KERNEL_GMEM_FP32R) return GBSBIN_ERR_ARG;
+  if (o->tile_override < 0 || o->tile_override > GBSBIN_KERNEL_WARP_FP32R) return GBSBIN_ERR_ARG;
   long long n = 2LL * p->M * p->K;
   if (n > GBSBIN_MAX_N) return GBSBIN_ERR_UNSUPPORTED;
   std::vector<int> count(p->L, 0);
@@ -318,6 +318,7 @@ int upload_state(gbsbin_plan* P, cudaStream_t stream) {
 
 int choose_kernel(int n, int L, int precision, int override_id) {
   if (override_id) return override_id;
+  if (precision == GBSBIN_FP32_REFINE && n <= 32) return GBSBIN_KERNEL_WARP_FP32R;
   if (precision == GBSBIN_FP64)
     return points_per_cta(GBSBIN_KERNEL_SMEM_FP64, n, L) > 0 ? GBSBIN_KERNEL_SMEM_FP64 : GBSBIN_KERNEL_GMEM_FP64;
   return points_per_cta(GBSBIN_KERNEL_SMEM_FP32R, n, L) > 0 ? GBSBIN_KERNEL_SMEM_FP32R : GBSBIN_KERNEL_GMEM_FP32R;
@@ -391,8 +392,8 @@ int gbsbin_plan_create(const gbsbin_problem* p, const gbsbin_options* o, gbsbin_
     return st;
   }
   P->kernel = choose_kernel(n, p->L, opt.precision, opt.tile_override);
-  P->P = points_per_cta(P->kernel, n, p->L);
-  if (P->P < 1) {  // a shared-memory variant forced on a matrix that does not fit
+  P->P = P->kernel == GBSBIN_KERNEL_WARP_FP32R ? (n <= 32 ? 1 : 0) : points_per_cta(P->kernel, n, p->L);
+  if (P->P < 1) {  // a variant forced on a matrix it cannot hold
     delete P;
     return GBSBIN_ERR_UNSUPPORTED;
   }
@@ -534,7 +535,8 @@ int gbsbin_execute(gbsbin_plan* P, double* P_out, void* stream) {
   a.gws = P->d_gws;
   a.gws_slot_bytes = P->gws_slot_bytes;
   if (P->ev0 && cudaEventRecord(P->ev0, s) != cudaSuccess) return GBSBIN_ERR_CUDA;
-  cudaError_t e = launch_points(a, P->kernel, P->num_sms, s);
+  cudaError_t e = P->kernel == GBSBIN_KERNEL_WARP_FP32R ? launch_points_warp(a, P->num_sms, s)
+                                                        : launch_points(a, P->kernel, P->num_sms, s);
   if (e != cudaSuccess) return GBSBIN_ERR_CUDA;
   if (P->ev1 && cudaEventRecord(P->ev1, s) != cudaSuccess) return GBSBIN_ERR_CUDA;
   DftArgs d{};

@@ -61,6 +61,7 @@ struct DftArgs {
 
 // Kernel launchers (return the launch error).
 cudaError_t launch_points(const PointArgs& a, int kernel, int num_sms, cudaStream_t s);
+cudaError_t launch_points_warp(const PointArgs& a, int num_sms, cudaStream_t s);
 size_t points_smem_bytes(int kernel, int n, int P, int L);
 size_t points_matrix_bytes(int kernel, int n, int P);
 int points_per_cta(int kernel, int n, int L);

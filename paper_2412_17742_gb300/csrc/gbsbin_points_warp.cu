@@ -1,0 +1,388 @@
+// Warp-per-point FP32 + refinement kernel for n <= 32 (arXiv:2412.17742, Sec. III
+// Eq. q_d, Sec. VI Eq. Lamb_lhaf_master; same mathematics as k_points_fp32r).
+//
+// One warp evaluates one grid point with the whole matrix in registers.  The matrix
+// M(w) = conj(D) - XA is padded to NP x NP (NP = 8, 16 or 32) with an identity block,
+// which leaves its LU, pivots, residual and log det unchanged.  Lane (lr, lc) =
+// (lane / 4, lane % 4) owns rows lr + 8 ra and columns lc + 4 cb (block-cyclic, so every
+// lane keeps work until the last steps).  Each elimination step broadcasts column k of L
+// and row k of U with warp shuffles.  Steps run in blocks of four: the block index is
+// unrolled (so the owning register row/column is a compile-time constant), the step within
+// the block is a runtime loop, which keeps the code small enough for the instruction
+// cache.  The residual pass reads L\U from a per-warp shared tile in a runtime loop.
+//
+// Per point:
+//   1. M^ = fl32(M) in registers; unpivoted LU in FP32.
+//   2. Log det from the pivots: lane i takes Log(d_i u'_ii) in FP64 (each has Re > 0).
+//   3. Residual E = M - L^U^ with Dot2 (exact FP32 products, Knuth TwoSum), M taken as
+//      NXA_hi + NXA_lo (+ conj(d) as hi + lo on the diagonal); stored to a shared tile.
+//   4. delta = tr(U^^{-1} L^^{-1} E): forward substitution on all columns, then back
+//      substitution on the entries X[m][c], m >= c, that diag(X) needs.
+//   5. If displaced: x^ = M^^{-1} X gamma, r = X gamma - M x^ by Dot2, x = x^ + M^^{-1} r.
+//   6. log q = 1/2 gamma^T x - 1/2 (ld + delta).
+#include <cuda_runtime.h>
+
+#include "gbsbin_device.cuh"
+#include "gbsbin_internal.h"
+
+namespace gbsbin {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ float2 shfl2(float2 v, int src) {
+  return make_float2(__shfl_sync(kFull, v.x, src), __shfl_sync(kFull, v.y, src));
+}
+
+}  // namespace
+
+template <int NP, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32, 3) k_points_fp32r_warp(PointArgs a) {
+  constexpr int RA = NP / 8;     // rows per lane
+  constexpr int CB = NP / 4;     // columns per lane
+  constexpr int NKB = NP / 4;    // 4-step blocks of the elimination
+  constexpr int CH = CB / 2;     // columns per lane in one half of the residual pass
+  constexpr int ES = NP + 4;     // row stride of the shared tile (bank stagger)
+  __shared__ double2 s_w[WARPS][GBSBIN_MAX_L];
+  __shared__ float2 s_inv[WARPS][NP];
+  __shared__ __align__(16) float2 s_LU[WARPS][NP * ES];
+  __shared__ float2 s_x[WARPS][NP];
+  __shared__ float2 s_r[WARPS][NP];
+  __shared__ int s_lab[NP];
+
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int lr = lane >> 2, lc = lane & 3;
+  const int n = a.n, L = a.grid.L;
+  for (int i = threadIdx.x; i < NP; i += WARPS * 32) s_lab[i] = i < n ? a.label[i] : 0;
+  __syncthreads();
+  double2* w = s_w[warp];
+  float2* invk = s_inv[warp];
+  float2* T = s_LU[warp];
+  float2* xs = s_x[warp];
+  float2* rs = s_r[warp];
+  const float2 zero = make_float2(0.0f, 0.0f);
+
+  for (long long e = (long long)blockIdx.x * WARPS + warp; e < a.grid.n_eval;
+       e += (long long)gridDim.x * WARPS) {
+    if (lane < L) w[lane] = root_of_unity(point_digit(e, a.grid, lane), a.grid.radix[lane]);
+    __syncwarp();
+
+    // ---- 1. M^ = fl32(conj(D) - XA), padded with the identity; LU in registers.
+    // Steps run in blocks of four (k = 4 kb + kc): within a block the owning register
+    // column kb and row ka = kb / 2 are compile-time constants, kc is a runtime loop.
+    float2 A[RA][CB];
+#pragma unroll
+    for (int ra = 0; ra < RA; ++ra)
+#pragma unroll
+      for (int cb = 0; cb < CB; ++cb) {
+        const int i = lr + 8 * ra, j = lc + 4 * cb;
+        float2 v = make_float2(i == j ? 1.0f : 0.0f, 0.0f);
+        if (i < n && j < n) {
+          if (i == j) {
+            const double2 x = a.NXA[i * n + j], d = w[s_lab[i]];
+            v = make_float2((float)(x.x + d.x), (float)(x.y - d.y));
+          } else {
+            v = a.NXA_hi[i * n + j];
+          }
+        }
+        A[ra][cb] = v;
+      }
+#pragma unroll
+    for (int kb = 0; kb < NKB; ++kb) {
+      const int ka = kb >> 1;
+#pragma unroll 1
+      for (int kc = 0; kc < 4; ++kc) {
+        const int k = 4 * kb + kc, kr = k & 7;
+        const float2 inv = crecipf(shfl2(A[ka][kb], kr * 4 + kc));
+        if (lane == 0) invk[k] = inv;
+        if (k == NP - 1) break;
+#pragma unroll
+        for (int ra = 0; ra < RA; ++ra)
+          if (8 * ra + 7 >= 4 * kb && lc == kc && lr + 8 * ra > k) A[ra][kb] = cmulf(A[ra][kb], inv);
+        float2 l[RA], u[CB];
+#pragma unroll
+        for (int ra = 0; ra < RA; ++ra)
+          l[ra] = (8 * ra + 7 < 4 * kb) ? zero : shfl2(A[ra][kb], lr * 4 + kc);
+#pragma unroll
+        for (int cb = 0; cb < CB; ++cb) u[cb] = (cb < kb) ? zero : shfl2(A[ka][cb], kr * 4 + lc);
+#pragma unroll
+        for (int ra = 0; ra < RA; ++ra) {
+          if (8 * ra + 7 < 4 * kb) continue;
+          if (8 * ra + 7 <= k) continue;        // warp-uniform
+#pragma unroll
+          for (int cb = 0; cb < CB; ++cb) {
+            if (cb < kb) continue;
+            const float2 nv = cfnmaf(A[ra][cb], l[ra], u[cb]);
+            if (lr + 8 * ra > k && lc + 4 * cb > k) A[ra][cb] = nv;
+          }
+        }
+      }
+    }
+    // stage L\U to the warp's shared tile (read by the residual pass and the solves)
+#pragma unroll
+    for (int ra = 0; ra < RA; ++ra)
+#pragma unroll
+      for (int cb = 0; cb < CB; ++cb) T[(lr + 8 * ra) * ES + lc + 4 * cb] = A[ra][cb];
+    __syncwarp();
+
+    // ---- 2. log det = sum_i Log(d_i u'_ii), one pivot per lane, FP64
+    double ld_re = 0.0, ld_im = 0.0, mn = 1.0e300;
+    if (lane < n) {
+      const float2 u = T[lane * ES + lane];
+      const double2 z = cmul(w[s_lab[lane]], make_double2(u.x, u.y));
+      mn = z.x;
+      if (!(z.x == z.x) || !(z.y == z.y)) mn = -1.0e300;
+      ld_re = 0.5 * log(fma(z.x, z.x, z.y * z.y));
+      ld_im = atan2(z.y, z.x);
+    }
+    ld_re = warp_sum_d(ld_re);
+    ld_im = warp_sum_d(ld_im);
+    mn = warp_min_d(mn);
+
+    // ---- 3. residual E = M - L^U^ (Dot2), runtime loop over k reading L\U from the tile.
+    // Terms outside k < min(i, j) (and k = j for i > j) get a zero factor, which leaves the
+    // Dot2 sums exactly unchanged and keeps the accumulation branch-free.
+    float2 Z[RA][CB];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      Acc2 er[RA][CH], ei[RA][CH];
+#pragma unroll
+      for (int ra = 0; ra < RA; ++ra)
+#pragma unroll
+        for (int q = 0; q < CH; ++q) {
+          er[ra][q] = Acc2{0.0f, 0.0f};
+          ei[ra][q] = Acc2{0.0f, 0.0f};
+        }
+      const int kend = 4 * (CH * h + CH - 1) + 3;   // largest column of this half
+#pragma unroll 1
+      for (int k = 0; k < NP - 1 && k <= kend; ++k) {
+        float2 u[CH];
+#pragma unroll
+        for (int q = 0; q < CH; ++q) u[q] = T[k * ES + lc + 4 * (CH * h + q)];
+#pragma unroll
+        for (int ra = 0; ra < RA; ++ra) {
+          if (8 * ra + 7 <= k) continue;        // warp-uniform: all rows of the group <= k
+          const int i = lr + 8 * ra;
+          const float2 l = T[i * ES + k];
+          const float lx = k < i ? -l.x : 0.0f, ly = k < i ? l.y : 0.0f;
+#pragma unroll
+          for (int q = 0; q < CH; ++q) {
+            const int j = lc + 4 * (CH * h + q);
+            const float ux = k <= j ? u[q].x : 0.0f, uy = k <= j ? u[q].y : 0.0f;
+            acc2_add_prod(er[ra][q], lx, ux);
+            acc2_add_prod(er[ra][q], ly, uy);
+            acc2_add_prod(ei[ra][q], lx, uy);
+            acc2_add_prod(ei[ra][q], -ly, ux);
+          }
+        }
+      }
+#pragma unroll
+      for (int ra = 0; ra < RA; ++ra)
+#pragma unroll
+        for (int q = 0; q < CH; ++q) {
+          const int cb = CH * h + q, i = lr + 8 * ra, j = lc + 4 * cb;
+          if (i <= j) {                  // L_ii U_ij = U_ij
+            const float2 uij = T[i * ES + j];
+            acc2_add(er[ra][q], -uij.x);
+            acc2_add(ei[ra][q], -uij.y);
+          }
+          if (i < n && j < n) {
+            const float2 xh = a.NXA_hi[i * n + j], xl = a.NXA_lo[i * n + j];
+            acc2_add(er[ra][q], xh.x);
+            acc2_add(er[ra][q], xl.x);
+            acc2_add(ei[ra][q], xh.y);
+            acc2_add(ei[ra][q], xl.y);
+            if (i == j) {
+              const double2 d = w[s_lab[i]];
+              const float dhx = (float)d.x, dhy = (float)d.y;
+              acc2_add(er[ra][q], dhx);
+              acc2_add(er[ra][q], (float)(d.x - (double)dhx));
+              acc2_add(ei[ra][q], -dhy);
+              acc2_add(ei[ra][q], -(float)(d.y - (double)dhy));
+            }
+          } else if (i == j) {
+            acc2_add(er[ra][q], 1.0f);
+          }
+          Z[ra][cb] = make_float2(acc2_value(er[ra][q]), acc2_value(ei[ra][q]));
+        }
+    }
+    // L\U back into registers for the substitutions
+#pragma unroll
+    for (int ra = 0; ra < RA; ++ra)
+#pragma unroll
+      for (int cb = 0; cb < CB; ++cb) A[ra][cb] = T[(lr + 8 * ra) * ES + lc + 4 * cb];
+
+    // ---- 4. delta = tr(U^^{-1} L^^{-1} E): Z = L^^{-1} E, then X = U^^{-1} Z on m >= c
+#pragma unroll
+    for (int kb = 0; kb < NKB; ++kb) {
+      const int ka = kb >> 1;
+#pragma unroll 1
+      for (int kc = 0; kc < 4; ++kc) {
+        const int k = 4 * kb + kc, kr = k & 7;
+        if (k == NP - 1) break;
+        float2 l[RA], z[CB];
+#pragma unroll
+        for (int ra = 0; ra < RA; ++ra)
+          l[ra] = (8 * ra + 7 < 4 * kb) ? zero : shfl2(A[ra][kb], lr * 4 + kc);
+#pragma unroll
+        for (int cb = 0; cb < CB; ++cb) z[cb] = shfl2(Z[ka][cb], kr * 4 + lc);
+#pragma unroll
+        for (int ra = 0; ra < RA; ++ra) {
+          if (8 * ra + 7 < 4 * kb) continue;
+          if (8 * ra + 7 <= k) continue;
+#pragma unroll
+          for (int cb = 0; cb < CB; ++cb) {
+            const float2 nv = cfnmaf(Z[ra][cb], l[ra], z[cb]);
+            if (lr + 8 * ra > k) Z[ra][cb] = nv;
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int kb = NKB - 1; kb >= 0; --kb) {
+      const int ka = kb >> 1;
+#pragma unroll 1
+      for (int kc = 3; kc >= 0; --kc) {
+        const int k = 4 * kb + kc, kr = k & 7;
+        const float2 ik = invk[k];
+        if (lr == kr) {
+#pragma unroll
+          for (int cb = 0; cb < CB; ++cb) Z[ka][cb] = cmulf(Z[ka][cb], ik);
+        }
+        if (k == 0) break;
+        float2 uk[RA], x[CB];
+#pragma unroll
+        for (int ra = 0; ra < RA; ++ra) uk[ra] = (8 * ra > 4 * kb + 3) ? zero : shfl2(A[ra][kb], lr * 4 + kc);
+#pragma unroll
+        for (int cb = 0; cb < CB; ++cb) x[cb] = (cb > kb) ? zero : shfl2(Z[ka][cb], kr * 4 + lc);
+#pragma unroll
+        for (int ra = 0; ra < RA; ++ra) {
+          if (8 * ra > 4 * kb + 3) continue;
+          if (8 * ra >= k) continue;
+#pragma unroll
+          for (int cb = 0; cb < CB; ++cb) {
+            if (cb > kb) continue;
+            const float2 nv = cfnmaf(Z[ra][cb], uk[ra], x[cb]);
+            if (lr + 8 * ra < k) Z[ra][cb] = nv;
+          }
+        }
+      }
+    }
+    double dre = 0.0, dim = 0.0;
+#pragma unroll
+    for (int ra = 0; ra < RA; ++ra)
+#pragma unroll
+      for (int cb = 0; cb < CB; ++cb)
+        if (lr + 8 * ra == lc + 4 * cb && lr + 8 * ra < n) {
+          dre += (double)Z[ra][cb].x;
+          dim += (double)Z[ra][cb].y;
+        }
+    dre = warp_sum_d(dre);
+    dim = warp_sum_d(dim);
+
+    // ---- 5. exponent with one refinement step (triangular solves read the tile)
+    double ex_re = 0.0, ex_im = 0.0;
+    if (a.has_gamma) {
+      for (int pass = 0; pass < 2; ++pass) {
+        float2* v = pass == 0 ? xs : rs;
+        if (pass == 0) {
+          if (lane < NP) v[lane] = lane < n ? a.Xg_hi[lane] : zero;
+          __syncwarp();
+        }
+        for (int k = 0; k < NP - 1; ++k) {      // v_i -= L_ik v_k, i > k
+          const float2 vk = v[k];
+          __syncwarp();
+          for (int i = k + 1 + lane; i < NP; i += 32) v[i] = cfnmaf(v[i], T[i * ES + k], vk);
+          __syncwarp();
+        }
+        for (int k = NP - 1; k >= 0; --k) {     // v_k /= u_kk; v_i -= U_ik v_k, i < k
+          const float2 vk = cmulf(v[k], invk[k]);
+          __syncwarp();
+          if (lane == 0) v[k] = vk;
+          for (int i = lane; i < k; i += 32) v[i] = cfnmaf(v[i], T[i * ES + k], vk);
+          __syncwarp();
+        }
+        if (pass == 0) {
+          // r = X gamma - M x^ = X gamma - conj(d) x^ - NXA x^, Dot2 per row (lane = row)
+          float2 rr = zero;
+          if (lane < n) {
+            const int i = lane;
+            Acc2 sr = {0.0f, 0.0f}, si = {0.0f, 0.0f};
+            const float2 gh = a.Xg_hi[i], gl = a.Xg_lo[i];
+            acc2_add(sr, gh.x);
+            acc2_add(sr, gl.x);
+            acc2_add(si, gh.y);
+            acc2_add(si, gl.y);
+            for (int j = 0; j < n; ++j) {
+              const float2 xh = a.NXA_hi[i * n + j], xl = a.NXA_lo[i * n + j], y = xs[j];
+              acc2_add_prod(sr, -xh.x, y.x);
+              acc2_add_prod(sr, xh.y, y.y);
+              acc2_add_prod(sr, -xl.x, y.x);
+              acc2_add_prod(sr, xl.y, y.y);
+              acc2_add_prod(si, -xh.x, y.y);
+              acc2_add_prod(si, -xh.y, y.x);
+              acc2_add_prod(si, -xl.x, y.y);
+              acc2_add_prod(si, -xl.y, y.x);
+            }
+            const double2 d = w[s_lab[i]];
+            const float dhx = (float)d.x, dhy = (float)d.y;
+            const float dlx = (float)(d.x - (double)dhx), dly = (float)(d.y - (double)dhy);
+            const float2 y = xs[i];
+            acc2_add_prod(sr, -dhx, y.x);
+            acc2_add_prod(sr, -dhy, y.y);
+            acc2_add_prod(si, -dhx, y.y);
+            acc2_add_prod(si, dhy, y.x);
+            acc2_add_prod(sr, -dlx, y.x);
+            acc2_add_prod(sr, -dly, y.y);
+            acc2_add_prod(si, -dlx, y.y);
+            acc2_add_prod(si, dly, y.x);
+            rr = make_float2(acc2_value(sr), acc2_value(si));
+          }
+          __syncwarp();
+          if (lane < NP) rs[lane] = rr;
+          __syncwarp();
+        }
+      }
+      if (lane < n) {
+        const double xr = (double)xs[lane].x + (double)rs[lane].x, xi = (double)xs[lane].y + (double)rs[lane].y;
+        const double gr = (double)a.g_hi[lane].x + (double)a.g_lo[lane].x;
+        const double gi = (double)a.g_hi[lane].y + (double)a.g_lo[lane].y;
+        ex_re = gr * xr - gi * xi;
+        ex_im = gr * xi + gi * xr;
+      }
+      ex_re = warp_sum_d(ex_re);
+      ex_im = warp_sum_d(ex_im);
+    }
+
+    if (lane == 0) {
+      a.logq[e] = make_double2(0.5 * ex_re - 0.5 * (ld_re + dre), 0.5 * ex_im - 0.5 * (ld_im + dim));
+      a.minpiv[e] = mn;
+    }
+    __syncwarp();
+  }
+}
+
+template <int NP>
+static cudaError_t launch_warp_np(const PointArgs& a, int num_sms, cudaStream_t s) {
+  constexpr int WARPS = 4;
+  int per_sm = 0;
+  cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_points_fp32r_warp<NP, WARPS>,
+                                                                  WARPS * 32, 0);
+  if (err != cudaSuccess) return err;
+  if (per_sm < 1) per_sm = 1;
+  long long groups = (a.grid.n_eval + WARPS - 1) / WARPS;
+  long long grid = (long long)per_sm * num_sms;
+  if (grid > groups) grid = groups;
+  if (grid < 1) grid = 1;
+  k_points_fp32r_warp<NP, WARPS><<<(unsigned)grid, WARPS * 32, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_points_warp(const PointArgs& a, int num_sms, cudaStream_t s) {
+  if (a.n <= 8) return launch_warp_np<8>(a, num_sms, s);
+  if (a.n <= 16) return launch_warp_np<16>(a, num_sms, s);
+  if (a.n <= 32) return launch_warp_np<32>(a, num_sms, s);
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace gbsbin
