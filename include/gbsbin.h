@@ -71,6 +71,8 @@ typedef struct {
   int tile_override;      /* 0 = automatic kernel choice; otherwise a gbsbin_kernel id      */
   int want_timing;        /* nonzero: execute records CUDA events around the point kernel on
                              its stream; gbsbin_diagnostics reports the elapsed time         */
+  int want_backward;      /* nonzero: allocate what gbsbin_backward needs; FP64 executes then
+                             keep the LU factors and exponent solutions of every point      */
 } gbsbin_options;
 
 /*
@@ -214,6 +216,38 @@ int gbsbin_read_points(gbsbin_plan* plan, double* logq_host, double* minpiv_host
 #define GBSBIN_NOALLOC_MAX_TWIDDLES (1LL << 14)
 int gbsbin_table_from_logq_noalloc(int L, const int* cutoff, int oversample, const double* logq,
                                    double* P_out, void* stream);
+
+/*
+ * Gradients of a scalar loss L(P) with respect to the problem's inputs (reverse mode
+ * through the inverse DFT, the per-point log det and exponent, and the FP64 state
+ * algebra).  Complex parameters use the convention g = dL/dRe z + i dL/dIm z, entries
+ * treated as independent.  d_sigma1 and d_zbar are exact along physical directions
+ * (perturbations keeping Sigma^(1) = [[N^T, Mm], [Mm^*, N]] and z-bar = (m, conj m)), the
+ * only ones under which the table stays real; the evaluation relies on that symmetry.  Every pointer may be NULL (not wanted); all are host memory
+ * owned by the caller.  d_r, d_T, d_alpha, d_V need the physical description
+ * (r, T, alpha, V) at plan creation / set_state; d_alpha and d_V are zero-filled when the
+ * problem had no alpha / V.
+ */
+typedef struct {
+  double* d_r;                /* [M*K]                                  */
+  gbsbin_complex* d_T;        /* [M*M]                                  */
+  gbsbin_complex* d_alpha;    /* [M*K]                                  */
+  gbsbin_complex* d_V;        /* [M*K*K]                                */
+  gbsbin_complex* d_sigma1;   /* [n*n] w.r.t. Sigma^(1)                 */
+  gbsbin_complex* d_zbar;     /* [n]   w.r.t. z-bar                     */
+} gbsbin_grads;
+
+/*
+ * Reverse pass for the plan's current state (no counterpart in the paper, which leaves
+ * differentiability to future work; the adjoint follows from d log det A = tr(A^{-1} dA)).
+ * dL_dP: device, table_size doubles, dL/dP(b) for the table of the last execute.  Needs a
+ * plan created with want_backward.  It reuses the LU factors stored by the last FP64
+ * execute of the current state; otherwise (FP32R plan, or state changed since) it first
+ * re-evaluates the grid in FP64 with the factors kept.  Synchronises `stream`.
+ * Errors: ERR_ARG (NULL plan/dL_dP/g, plan without want_backward, physical gradients
+ * requested for a direct-covariance problem), ERR_CUDA, ERR_NOMEM.
+ */
+int gbsbin_backward(gbsbin_plan* plan, const double* dL_dP, gbsbin_grads* g, void* stream);
 
 /* Static description of a status code. */
 const char* gbsbin_strerror(int status);

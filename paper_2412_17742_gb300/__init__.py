@@ -26,7 +26,8 @@ GBSBIN_FP32_REFINE = 1
 KERNELS = {1: "smem_fp64", 2: "smem_fp32r", 3: "gmem_fp64", 4: "gmem_fp32r", 5: "warp_fp32r"}
 EXPORTED = ["gbsbin_default_options", "gbsbin_plan_create", "gbsbin_plan_set_state", "gbsbin_plan_destroy",
             "gbsbin_plan_table_size", "gbsbin_execute", "gbsbin_execute_host", "gbsbin_diagnostics",
-            "gbsbin_strerror", "gbsbin_alu_peak", "gbsbin_read_points", "gbsbin_table_from_logq_noalloc"]
+            "gbsbin_strerror", "gbsbin_alu_peak", "gbsbin_read_points", "gbsbin_table_from_logq_noalloc",
+            "gbsbin_backward"]
 
 
 class GbsbinError(RuntimeError):
@@ -42,7 +43,7 @@ class gbsbin_complex(ctypes.Structure):
 class gbsbin_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("oversample", ctypes.c_int),
                 ("want_diagnostics", ctypes.c_int), ("tile_override", ctypes.c_int),
-                ("want_timing", ctypes.c_int)]
+                ("want_timing", ctypes.c_int), ("want_backward", ctypes.c_int)]
 
 
 _cp = ctypes.POINTER(gbsbin_complex)
@@ -53,6 +54,10 @@ _dp = ctypes.POINTER(ctypes.c_double)
 class gbsbin_problem(ctypes.Structure):
     _fields_ = [("M", ctypes.c_int), ("K", ctypes.c_int), ("r", _dp), ("T", _cp), ("alpha", _cp), ("V", _cp),
                 ("sigma1", _cp), ("zbar", _cp), ("bin_of_mode", _ip), ("L", ctypes.c_int), ("cutoff", _ip)]
+
+
+class gbsbin_grads(ctypes.Structure):
+    _fields_ = [("d_r", _dp), ("d_T", _cp), ("d_alpha", _cp), ("d_V", _cp), ("d_sigma1", _cp), ("d_zbar", _cp)]
 
 
 class gbsbin_diag(ctypes.Structure):
@@ -88,9 +93,10 @@ def load():
     lib.gbsbin_alu_peak.argtypes = [ctypes.c_int, ctypes.c_int, _dp, vp]
     lib.gbsbin_read_points.argtypes = [vp, vp, vp, vp]
     lib.gbsbin_table_from_logq_noalloc.argtypes = [ctypes.c_int, _ip, ctypes.c_int, vp, vp, vp]
+    lib.gbsbin_backward.argtypes = [vp, vp, ctypes.POINTER(gbsbin_grads), vp]
     for f in ("gbsbin_plan_create", "gbsbin_plan_set_state", "gbsbin_plan_destroy", "gbsbin_execute",
               "gbsbin_execute_host", "gbsbin_diagnostics", "gbsbin_alu_peak", "gbsbin_read_points",
-              "gbsbin_table_from_logq_noalloc"):
+              "gbsbin_table_from_logq_noalloc", "gbsbin_backward"):
         getattr(lib, f).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -154,11 +160,12 @@ def gbsbin_default_options():
 
 
 def make_options(precision=GBSBIN_FP64, oversample=1, want_diagnostics=True, tile_override=0,
-                 want_timing=False):
+                 want_timing=False, want_backward=False):
     o = gbsbin_default_options()
     o.precision, o.oversample = int(precision), int(oversample)
     o.want_diagnostics, o.tile_override = int(bool(want_diagnostics)), int(tile_override)
     o.want_timing = int(bool(want_timing))
+    o.want_backward = int(bool(want_backward))
     return o
 
 
@@ -233,6 +240,31 @@ def gbsbin_table_from_logq_noalloc(cutoff, oversample, logq_dev, P_out, stream=N
            "gbsbin_table_from_logq_noalloc")
 
 
+def gbsbin_backward(plan, dL_dP, M, K, n, stream=None, want=("r", "T", "alpha", "V", "sigma1", "zbar")):
+    """Reverse pass: dL_dP is a device buffer of table_size doubles.  Returns a dict of
+    numpy arrays (complex gradients as dL/dRe + i dL/dIm) for the names in ``want``."""
+    shapes = {"r": (M * K,), "T": (M * M,), "alpha": (M * K,), "V": (M * K * K,), "sigma1": (n * n,),
+              "zbar": (n,)}
+    out = {k: np.zeros(shapes[k], dtype=np.float64 if k == "r" else np.complex128) for k in want}
+    g = gbsbin_grads()
+    for k, arr in out.items():
+        ptr = arr.ctypes.data_as(_dp if k == "r" else _cp)
+        setattr(g, "d_" + k, ptr)
+    _check(load().gbsbin_backward(plan, _ptr(dL_dP), ctypes.byref(g), _stream_handle(stream)), "gbsbin_backward")
+    res = {k: v for k, v in out.items()}
+    if "T" in res:
+        res["T"] = res["T"].reshape(M, M)
+    if "r" in res:
+        res["r"] = res["r"].reshape(M, K)
+    if "alpha" in res:
+        res["alpha"] = res["alpha"].reshape(M, K)
+    if "V" in res:
+        res["V"] = res["V"].reshape(M, K, K)
+    if "sigma1" in res:
+        res["sigma1"] = res["sigma1"].reshape(n, n)
+    return res
+
+
 def gbsbin_strerror(status):
     return load().gbsbin_strerror(int(status)).decode()
 
@@ -248,10 +280,17 @@ class Plan:
     """Owning wrapper: ``with Plan(prob, precision=...) as p: P = p.table()``."""
 
     def __init__(self, prob, precision=GBSBIN_FP64, oversample=1, want_diagnostics=True, tile_override=0,
-                 want_timing=False):
-        self.options = make_options(precision, oversample, want_diagnostics, tile_override, want_timing)
+                 want_timing=False, want_backward=False):
+        self.options = make_options(precision, oversample, want_diagnostics, tile_override, want_timing,
+                                    want_backward)
         self.handle = gbsbin_plan_create(prob, self.options)
         self.shape = tuple(int(c) + 1 for c in prob.cutoff)
+        self.M, self.K = int(prob.M), int(prob.K)
+        self.n = 2 * self.M * self.K
+
+    def backward(self, dL_dP, stream=None, want=("r", "T", "alpha", "V", "sigma1", "zbar")):
+        """Gradients of L for the plan's current state given dL/dP (CUDA float64 tensor)."""
+        return gbsbin_backward(self.handle, dL_dP, self.M, self.K, self.n, stream, want)
 
     def table(self, stream=None):
         """Execute into a new CUDA float64 tensor shaped (N_1+1, ..., N_L+1)."""
@@ -279,3 +318,58 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+class _State:
+    """Physical description assembled from tensors for one evaluation."""
+
+    def __init__(self, template, r, T, alpha, V):
+        self.M, self.K = template.M, template.K
+        self.bin_of_mode, self.cutoff = template.bin_of_mode, template.cutoff
+        self.r = r.detach().cpu().numpy()
+        self.T = T.detach().cpu().numpy()
+        self.alpha = None if alpha is None else alpha.detach().cpu().numpy()
+        self.V = None if V is None else V.detach().cpu().numpy()
+
+
+def _autograd_function():
+    import torch
+
+    class BinnedDistribution(torch.autograd.Function):
+        """P(b) as a differentiable function of (r, T, alpha, V) through a plan created with
+        want_backward; the reverse pass is gbsbin_backward."""
+
+        @staticmethod
+        def forward(ctx, plan, template, r, T, alpha, V):
+            gbsbin_plan_set_state(plan.handle, _State(template, r, T, alpha, V))
+            P = plan.table()
+            ctx.plan = plan
+            ctx.has = (alpha is not None, V is not None)
+            ctx.dev = (r.device, T.device)
+            return P
+
+        @staticmethod
+        def backward(ctx, grad_P):
+            g = ctx.plan.backward(grad_P.detach().contiguous().to(torch.float64),
+                                  want=("r", "T", "alpha", "V"))
+            d_r = torch.from_numpy(g["r"]).to(ctx.dev[0])
+            d_T = torch.from_numpy(g["T"]).to(ctx.dev[1])
+            d_a = torch.from_numpy(g["alpha"]).to(ctx.dev[0]) if ctx.has[0] else None
+            d_V = torch.from_numpy(g["V"]).to(ctx.dev[0]) if ctx.has[1] else None
+            return None, None, d_r, d_T, d_a, d_V
+
+    return BinnedDistribution
+
+
+_BD = None
+
+
+def binned_distribution(plan, template, r, T, alpha=None, V=None):
+    """Differentiable binned table: ``plan`` is a :class:`Plan` made with want_backward for a
+    problem with the same M, K, grouping and cutoffs as ``template``; r (float64, (M, K)),
+    T (complex128, (M, M)), alpha (complex128, (M, K)) and V (complex128, (M, K, K)) are
+    torch tensors.  Returns a CUDA float64 tensor shaped (N_1+1, ..., N_L+1)."""
+    global _BD
+    if _BD is None:
+        _BD = _autograd_function()
+    return _BD.apply(plan, template, r, T, alpha, V)

@@ -81,19 +81,23 @@ __global__ void k_dft_last_real(const double2* __restrict__ Y, double* __restric
   }
 }
 
-// diag[0] = sum P, diag[1] = max |Im| of the self-conjugate entries Y[o,0] (and Y[o,R/2]),
-// diag[2] = min pivot Re, diag[3] = count of bad points, diag[4] = Re log q_0
+// Per-block partial diagnostics (the host finishes the reduction in a fixed order):
+// part[4b + 0] = sum of P over the block's share, part[4b + 1] = max |Im| of the
+// self-conjugate entries Y[o, 0] (and Y[o, R/2]), part[4b + 2] = min pivot Re,
+// part[4b + 3] = number of bad points; part[4 GBSBIN_DIAG_BLOCKS] = Re log q_0.
 __global__ void k_diag(const double* __restrict__ P, long long table, const double2* __restrict__ Y,
                        long long outer, int H, int R, const double* __restrict__ minpiv,
-                       const double2* __restrict__ logq, long long n_eval, double* __restrict__ diag) {
+                       const double2* __restrict__ logq, long long n_eval, double* __restrict__ part) {
   __shared__ double s_sum[32], s_im[32], s_min[32], s_bad[32];
   double sum = 0.0, im = 0.0, mn = 1.0e300, bad = 0.0;
-  for (long long t = threadIdx.x; t < table; t += blockDim.x) sum += P[t];
-  for (long long o = threadIdx.x; o < outer; o += blockDim.x) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  for (long long t = t0; t < table; t += stride) sum += P[t];
+  for (long long o = t0; o < outer; o += stride) {
     im = fmax(im, fabs(Y[o * H].y));
     if ((R & 1) == 0) im = fmax(im, fabs(Y[o * H + H - 1].y));
   }
-  for (long long e = threadIdx.x; e < n_eval; e += blockDim.x) {
+  for (long long e = t0; e < n_eval; e += stride) {
     double m = minpiv[e];
     double2 l = logq[e];
     bool ok = (m > 0.0) && isfinite(l.x) && isfinite(l.y);
@@ -122,17 +126,21 @@ __global__ void k_diag(const double* __restrict__ P, long long table, const doub
       mn = fmin(mn, s_min[i]);
       bad += s_bad[i];
     }
-    diag[0] = sum;
-    diag[1] = im;
-    diag[2] = mn;
-    diag[3] = bad;
-    diag[4] = logq[0].x;
+    double* out = part + 4 * blockIdx.x;
+    out[0] = sum;
+    out[1] = im;
+    out[2] = mn;
+    out[3] = bad;
+    if (blockIdx.x == 0) part[4 * gridDim.x] = logq[0].x;
   }
 }
 
+// Small transforms use 64-thread blocks so the work spreads over many SMs (these kernels
+// run on the FP64 pipe, which is narrow per SM).
+constexpr int kDftThreads = 64;
 static unsigned blocks_for(long long work) {
-  long long b = (work + 255) / 256;
-  if (b > 4096) b = 4096;
+  long long b = (work + kDftThreads - 1) / kDftThreads;
+  if (b > 16384) b = 16384;
   if (b < 1) b = 1;
   return (unsigned)b;
 }
@@ -140,7 +148,7 @@ static unsigned blocks_for(long long work) {
 cudaError_t launch_dft(const DftArgs& a, cudaStream_t s) {
   const GridDesc& g = a.grid;
   const int L = g.L;
-  k_normalise<<<blocks_for(g.n_eval), 256, 0, s>>>(a.logq, g.n_eval, a.bufA);
+  k_normalise<<<blocks_for(g.n_eval), kDftThreads, 0, s>>>(a.logq, g.n_eval, a.bufA);
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return err;
   long long dims[GBSBIN_MAX_L];
@@ -153,7 +161,7 @@ cudaError_t launch_dft(const DftArgs& a, cudaStream_t s) {
     long long outer = 1, inner = 1;
     for (int m = 0; m < l; ++m) outer *= dims[m];
     for (int m = l + 1; m < L; ++m) inner *= dims[m];
-    k_dft_axis<<<blocks_for(outer * g.nout[l] * inner), 256, 0, s>>>(cur, nxt, outer, g.radix[l], g.nout[l],
+    k_dft_axis<<<blocks_for(outer * g.nout[l] * inner), kDftThreads, 0, s>>>(cur, nxt, outer, g.radix[l], g.nout[l],
                                                                       inner, a.tw + twoff);
     err = cudaGetLastError();
     if (err != cudaSuccess) return err;
@@ -166,13 +174,13 @@ cudaError_t launch_dft(const DftArgs& a, cudaStream_t s) {
   long long outer = 1;
   for (int m = 0; m < L - 1; ++m) outer *= dims[m];
   const double scale = 1.0 / (double)g.npts;
-  k_dft_last_real<<<blocks_for(outer * g.nout[L - 1]), 256, 0, s>>>(cur, a.P, outer, g.radix[L - 1], g.half,
+  k_dft_last_real<<<blocks_for(outer * g.nout[L - 1]), kDftThreads, 0, s>>>(cur, a.P, outer, g.radix[L - 1], g.half,
                                                                     g.nout[L - 1], scale, a.tw + twoff);
   err = cudaGetLastError();
   if (err != cudaSuccess) return err;
   if (a.diag) {
-    k_diag<<<1, 1024, 0, s>>>(a.P, a.table_size, cur, outer, g.half, g.radix[L - 1], a.minpiv, a.logq,
-                              g.n_eval, a.diag);
+    k_diag<<<GBSBIN_DIAG_BLOCKS, 256, 0, s>>>(a.P, a.table_size, cur, outer, g.half, g.radix[L - 1],
+                                              a.minpiv, a.logq, g.n_eval, a.diag);
     err = cudaGetLastError();
   }
   return err;

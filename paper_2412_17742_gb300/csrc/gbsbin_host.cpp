@@ -1,6 +1,7 @@
 // Host side of the library: validation, the FP64 Gaussian-state algebra of a problem
 // (arXiv:2412.17742, Sec. II; output covariance as in Sec. VIII, Eq. output_cov_internal;
 // internal modes as in Sec. VI and App. B), device workspaces and launch orchestration.
+#include <algorithm>
 #include <cmath>
 #include <complex>
 #include <cstdio>
@@ -40,6 +41,15 @@ struct gbsbin_plan {
   void* d_gws = nullptr;
   long long gws_slot_bytes = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // reverse pass
+  bool physical = false;              // state given as r, T (alpha, V)
+  std::vector<double> r;
+  std::vector<cd> T, alpha, V, zbar;
+  bool has_alpha = false, has_V = false;
+  double2 *d_lu = nullptr, *d_xs = nullptr, *d_adjA = nullptr, *d_adjB = nullptr, *d_bws = nullptr;
+  double2 *d_partS = nullptr, *d_partg = nullptr, *d_outS = nullptr, *d_outg = nullptr;
+  bool saved_valid = false;           // d_lu / d_xs hold the current state's factors
+  long long bws_slot_bytes = 0;       // per-SM slot of d_bws (reverse pass and FP64 workspace)
   // pinned staging for uploads
   void* h_stage = nullptr;
   size_t h_stage_bytes = 0;
@@ -204,7 +214,7 @@ int adjacency(const std::vector<cd>& S1, const std::vector<cd>& zbar, int n, std
 }
 
 int build_state(const gbsbin_problem* p, int n, std::vector<cd>& XA, std::vector<cd>& gamma,
-                std::vector<cd>& Xgamma, int* has_gamma) {
+                std::vector<cd>& Xgamma, int* has_gamma, std::vector<cd>* zbar_out = nullptr) {
   std::vector<cd> S1, zbar;
   if (p->sigma1) {
     S1.resize((size_t)n * n);
@@ -218,6 +228,7 @@ int build_state(const gbsbin_problem* p, int n, std::vector<cd>& XA, std::vector
   }
   int st = adjacency(S1, zbar, n, XA, gamma, Xgamma);
   if (st) return st;
+  if (zbar_out) *zbar_out = zbar;
   *has_gamma = 0;
   for (int i = 0; i < n; ++i)
     if (gamma[i] != cd(0.0)) *has_gamma = 1;
@@ -233,6 +244,9 @@ void free_device(gbsbin_plan* P) {
   if (P->h_stage) cudaFreeHost(P->h_stage);
   if (P->ev0) cudaEventDestroy(P->ev0);
   if (P->ev1) cudaEventDestroy(P->ev1);
+  void* bw[] = {P->d_lu, P->d_xs, P->d_adjA, P->d_adjB, P->d_bws, P->d_partS, P->d_partg, P->d_outS, P->d_outg};
+  for (void* q : bw)
+    if (q) cudaFree(q);
 }
 
 template <typename T>
@@ -316,6 +330,83 @@ int upload_state(gbsbin_plan* P, cudaStream_t stream) {
   return GBSBIN_OK;
 }
 
+void record_inputs(gbsbin_plan* P, const gbsbin_problem* p) {
+  const int M = p->M, K = p->K;
+  P->physical = p->sigma1 == nullptr;
+  if (!P->physical) return;
+  P->r.assign(p->r, p->r + M * K);
+  P->T.resize((size_t)M * M);
+  for (int q = 0; q < M * M; ++q) P->T[q] = cd(p->T[q].re, p->T[q].im);
+  P->has_alpha = p->alpha != nullptr;
+  P->alpha.assign((size_t)M * K, 0.0);
+  if (p->alpha)
+    for (int q = 0; q < M * K; ++q) P->alpha[q] = cd(p->alpha[q].re, p->alpha[q].im);
+  P->has_V = p->V != nullptr;
+  P->V.assign((size_t)M * K * K, 0.0);
+  for (int i = 0; i < M; ++i)
+    for (int l = 0; l < K; ++l)
+      for (int k = 0; k < K; ++k)
+        P->V[((size_t)i * K + l) * K + k] = p->V ? cd(p->V[(i * K + l) * K + k].re, p->V[(i * K + l) * K + k].im)
+                                                 : cd(l == k ? 1.0 : 0.0);
+}
+
+
+// ------------------------------------------------------------ reverse-pass helpers
+// C = A B for n x n row-major complex matrices (i, k, j loop order).
+void matmul(const std::vector<cd>& A, const std::vector<cd>& B, std::vector<cd>& C, int n) {
+  C.assign((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i)
+    for (int k = 0; k < n; ++k) {
+      const cd a = A[(size_t)i * n + k];
+      if (a == cd(0.0)) continue;
+      const cd* b = &B[(size_t)k * n];
+      cd* c = &C[(size_t)i * n];
+      for (int j = 0; j < n; ++j) c[j] += a * b[j];
+    }
+}
+
+std::vector<cd> transpose(const std::vector<cd>& A, int n) {
+  std::vector<cd> T((size_t)n * n);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) T[(size_t)j * n + i] = A[(size_t)i * n + j];
+  return T;
+}
+
+// Launch the FP64 point kernel for the current state with the LU factors and exponent
+// solutions kept for the reverse pass.
+int evaluate_fp64_with_factors(gbsbin_plan* P, cudaStream_t s) {
+  const int n = P->n;
+  int kernel = points_per_cta(GBSBIN_KERNEL_SMEM_FP64, n, P->L) > 0 ? GBSBIN_KERNEL_SMEM_FP64 : GBSBIN_KERNEL_GMEM_FP64;
+  PointArgs a{};
+  a.n = n;
+  a.has_gamma = P->has_gamma;
+  a.P = kernel == GBSBIN_KERNEL_GMEM_FP64 ? 1 : points_per_cta(kernel, n, P->L);
+  a.logP = 0;
+  while ((1 << a.logP) < a.P) ++a.logP;
+  a.NXA = P->d_NXA;
+  a.Xgamma = P->d_Xgamma;
+  a.gamma = P->d_gamma;
+  a.NXA_hi = P->d_NXA_hi;
+  a.NXA_lo = P->d_NXA_lo;
+  a.Xg_hi = P->d_Xg_hi;
+  a.Xg_lo = P->d_Xg_lo;
+  a.g_hi = P->d_g_hi;
+  a.g_lo = P->d_g_lo;
+  a.label = P->d_label;
+  a.grid = P->grid;
+  a.logq = P->d_logq;
+  a.minpiv = P->d_minpiv;
+  a.lu_store = P->d_lu;
+  a.x_store = P->d_xs;
+  if (kernel == GBSBIN_KERNEL_GMEM_FP64) {  // the reverse-pass slots double as the forward workspace
+    a.gws = P->d_bws;
+    a.gws_slot_bytes = P->bws_slot_bytes;
+  }
+  if (launch_points(a, kernel, P->num_sms, s) != cudaSuccess) return GBSBIN_ERR_CUDA;
+  P->saved_valid = true;
+  return GBSBIN_OK;
+}
+
 int choose_kernel(int n, int L, int precision, int override_id) {
   if (override_id) return override_id;
   if (precision == GBSBIN_FP32_REFINE && n <= 32) return GBSBIN_KERNEL_WARP_FP32R;
@@ -335,6 +426,7 @@ void gbsbin_default_options(gbsbin_options* o) {
   o->want_diagnostics = 1;
   o->tile_override = 0;
   o->want_timing = 0;
+  o->want_backward = 0;
 }
 
 const char* gbsbin_strerror(int status) {
@@ -386,11 +478,12 @@ int gbsbin_plan_create(const gbsbin_problem* p, const gbsbin_options* o, gbsbin_
   }
   g.half = g.radix[p->L - 1] / 2 + 1;
   g.n_eval = g.npts / g.radix[p->L - 1] * g.half;
-  st = build_state(p, n, P->XA, P->gamma, P->Xgamma, &P->has_gamma);
+  st = build_state(p, n, P->XA, P->gamma, P->Xgamma, &P->has_gamma, &P->zbar);
   if (st) {
     delete P;
     return st;
   }
+  record_inputs(P, p);
   P->kernel = choose_kernel(n, p->L, opt.precision, opt.tile_override);
   P->P = P->kernel == GBSBIN_KERNEL_WARP_FP32R ? (n <= 32 ? 1 : 0) : points_per_cta(P->kernel, n, p->L);
   if (P->P < 1) {  // a variant forced on a matrix it cannot hold
@@ -410,7 +503,7 @@ int gbsbin_plan_create(const gbsbin_problem* p, const gbsbin_options* o, gbsbin_
       (st = dalloc(&P->d_Xg_lo, n)) || (st = dalloc(&P->d_g_hi, n)) || (st = dalloc(&P->d_g_lo, n)) ||
       (st = dalloc(&P->d_label, n)) || (st = dalloc(&P->d_logq, g.n_eval)) ||
       (st = dalloc(&P->d_minpiv, g.n_eval)) || (st = dalloc(&P->d_bufA, g.n_eval)) ||
-      (st = dalloc(&P->d_bufB, g.n_eval)) || (st = dalloc(&P->d_diag, 8)) ||
+      (st = dalloc(&P->d_bufB, g.n_eval)) || (st = dalloc(&P->d_diag, 4 * GBSBIN_DIAG_BLOCKS + 1)) ||
       (st = dalloc(&P->d_table, (size_t)P->table_size))) {
     free_device(P);
     delete P;
@@ -442,6 +535,20 @@ int gbsbin_plan_create(const gbsbin_problem* p, const gbsbin_options* o, gbsbin_
     return GBSBIN_ERR_NOMEM;
   }
   P->h_stage_bytes = sl.total;
+  if (opt.want_backward) {
+    const size_t ne = (size_t)g.n_eval, adj = (size_t)std::max<long long>(P->table_size, g.n_eval);
+    const size_t parts = (size_t)P->num_sms;
+    P->bws_slot_bytes = ((long long)points_matrix_bytes(GBSBIN_KERNEL_GMEM_FP64, n, 1) + 255) / 256 * 256;
+    if ((st = dalloc(&P->d_lu, ne * nn)) || (st = dalloc(&P->d_xs, ne * n)) || (st = dalloc(&P->d_adjA, adj)) ||
+        (st = dalloc(&P->d_adjB, adj)) ||
+        (st = dalloc(&P->d_bws, parts * (size_t)P->bws_slot_bytes / sizeof(double2))) ||
+        (st = dalloc(&P->d_partS, parts * nn)) || (st = dalloc(&P->d_partg, parts * n)) ||
+        (st = dalloc(&P->d_outS, nn)) || (st = dalloc(&P->d_outg, (size_t)n))) {
+      free_device(P);
+      delete P;
+      return st;
+    }
+  }
   if (opt.want_timing &&
       (cudaEventCreate(&P->ev0) != cudaSuccess || cudaEventCreate(&P->ev1) != cudaSuccess)) {
     cudaGetLastError();
@@ -489,10 +596,13 @@ int gbsbin_plan_set_state(gbsbin_plan* P, const gbsbin_problem* p, void* stream)
     if (p->cutoff[l] != P->cutoff[l]) return GBSBIN_ERR_ARG;
   for (int j = 0; j < P->M; ++j)
     if (p->bin_of_mode[j] != P->bin_of_mode[j]) return GBSBIN_ERR_ARG;
-  std::vector<cd> XA, gamma, Xgamma;
+  std::vector<cd> XA, gamma, Xgamma, zbar;
   int has_gamma = 0;
-  st = build_state(p, P->n, XA, gamma, Xgamma, &has_gamma);
+  st = build_state(p, P->n, XA, gamma, Xgamma, &has_gamma, &zbar);
   if (st) return st;
+  record_inputs(P, p);
+  P->saved_valid = false;
+  P->zbar.swap(zbar);
   P->XA.swap(XA);
   P->gamma.swap(gamma);
   P->Xgamma.swap(Xgamma);
@@ -534,6 +644,10 @@ int gbsbin_execute(gbsbin_plan* P, double* P_out, void* stream) {
   a.minpiv = P->d_minpiv;
   a.gws = P->d_gws;
   a.gws_slot_bytes = P->gws_slot_bytes;
+  const bool save = P->opt.want_backward && (P->kernel == GBSBIN_KERNEL_SMEM_FP64 || P->kernel == GBSBIN_KERNEL_GMEM_FP64);
+  a.lu_store = save ? P->d_lu : nullptr;
+  a.x_store = save ? P->d_xs : nullptr;
+  P->saved_valid = save;
   if (P->ev0 && cudaEventRecord(P->ev0, s) != cudaSuccess) return GBSBIN_ERR_CUDA;
   cudaError_t e = P->kernel == GBSBIN_KERNEL_WARP_FP32R ? launch_points_warp(a, P->num_sms, s)
                                                         : launch_points(a, P->kernel, P->num_sms, s);
@@ -566,11 +680,19 @@ int gbsbin_execute_host(gbsbin_plan* P, double* P_out_host, void* stream) {
 
 int gbsbin_diagnostics(gbsbin_plan* P, gbsbin_diag* out, void* stream) {
   if (!P || !out) return GBSBIN_ERR_ARG;
-  double h[8] = {0};
+  double part[4 * GBSBIN_DIAG_BLOCKS + 1] = {0};
+  double h[5] = {0.0, 0.0, 1.0e300, 0.0, 0.0};
   if (P->opt.want_diagnostics) {
-    if (cudaMemcpyAsync(h, P->d_diag, sizeof(h), cudaMemcpyDeviceToHost, (cudaStream_t)stream) != cudaSuccess ||
+    if (cudaMemcpyAsync(part, P->d_diag, sizeof(part), cudaMemcpyDeviceToHost, (cudaStream_t)stream) != cudaSuccess ||
         cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess)
       return GBSBIN_ERR_CUDA;
+    for (int b = 0; b < GBSBIN_DIAG_BLOCKS; ++b) {  // fixed order: deterministic
+      h[0] += part[4 * b];
+      h[1] = std::fmax(h[1], part[4 * b + 1]);
+      h[2] = std::fmin(h[2], part[4 * b + 2]);
+      h[3] += part[4 * b + 3];
+    }
+    h[4] = part[4 * GBSBIN_DIAG_BLOCKS];
   }
   out->sum_P = h[0];
   out->max_imag = h[1];
@@ -605,6 +727,140 @@ int gbsbin_read_points(gbsbin_plan* P, double* logq_host, double* minpiv_host, v
       cudaMemcpyAsync(minpiv_host, P->d_minpiv, ne * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess)
     return GBSBIN_ERR_CUDA;
   return cudaStreamSynchronize(s) == cudaSuccess ? GBSBIN_OK : GBSBIN_ERR_CUDA;
+}
+
+
+int gbsbin_backward(gbsbin_plan* P, const double* dLdP, gbsbin_grads* g, void* stream) {
+  if (!P || !dLdP || !g) return GBSBIN_ERR_ARG;
+  if (!P->opt.want_backward) return GBSBIN_ERR_ARG;
+  if ((g->d_r || g->d_T || g->d_alpha || g->d_V) && !P->physical) return GBSBIN_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int n = P->n, MK = n / 2, M = P->M, K = P->K;
+  int st = GBSBIN_OK;
+  if (!P->saved_valid && (st = evaluate_fp64_with_factors(P, s))) return st;
+  BackwardArgs b{};
+  b.n = n;
+  b.grid = P->grid;
+  b.n_eval = P->grid.n_eval;
+  b.lu_store = P->d_lu;
+  b.x_store = P->d_xs;
+  b.gamma = P->d_gamma;
+  b.logq = P->d_logq;
+  b.tw = P->d_tw;
+  b.bufA = P->d_adjA;
+  b.bufB = P->d_adjB;
+  b.ws = P->d_bws;
+  b.ws_slot_bytes = P->bws_slot_bytes;
+  b.partS = P->d_partS;
+  b.partg = P->d_partg;
+  b.nparts = P->num_sms;
+  b.outS = P->d_outS;
+  b.outg = P->d_outg;
+  if (launch_backward(b, dLdP, s) != cudaSuccess) return GBSBIN_ERR_CUDA;
+  std::vector<double2> hS((size_t)n * n), hg(n);
+  if (cudaMemcpyAsync(hS.data(), P->d_outS, hS.size() * sizeof(double2), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemcpyAsync(hg.data(), P->d_outg, hg.size() * sizeof(double2), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return GBSBIN_ERR_CUDA;
+
+  // dL = Re( sum_ij S_ij dXA_ij + sum_i s_i dgamma_i ) with XA = I - Sigma^{-1},
+  // gamma = X Sigma^{-1} zbar:  dL = Re tr(B dSigma) + Re v^T dzbar, where
+  // B = Sinv S^T Sinv - (Sinv zbar)(Sinv^T X s)^T and v = Sinv^T X s.
+  std::vector<cd> S((size_t)n * n), sv(n), Sinv((size_t)n * n);
+  for (size_t q = 0; q < S.size(); ++q) S[q] = cd(hS[q].x, hS[q].y);
+  for (int i = 0; i < n; ++i) sv[i] = cd(hg[i].x, hg[i].y);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) Sinv[(size_t)i * n + j] = (i == j ? 1.0 : 0.0) - P->XA[(size_t)i * n + j];
+  std::vector<cd> T1, B;
+  matmul(Sinv, transpose(S, n), T1, n);
+  matmul(T1, Sinv, B, n);
+  std::vector<cd> u(n, 0.0), w(n, 0.0);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) u[i] += Sinv[(size_t)i * n + j] * P->zbar[j];
+  for (int i = 0; i < n; ++i)       // w = Sinv^T X s
+    for (int j = 0; j < n; ++j) w[i] += Sinv[(size_t)j * n + i] * sv[j < MK ? j + MK : j - MK];
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) B[(size_t)i * n + j] -= u[i] * w[j];
+  if (g->d_sigma1)
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) {
+        cd c = std::conj(B[(size_t)j * n + i]);
+        g->d_sigma1[(size_t)i * n + j] = gbsbin_complex{c.real(), c.imag()};
+      }
+  if (g->d_zbar)
+    for (int i = 0; i < n; ++i) g->d_zbar[i] = gbsbin_complex{w[i].real(), -w[i].imag()};
+  if (!(g->d_r || g->d_T || g->d_alpha || g->d_V)) return GBSBIN_OK;
+
+  // physical parameters: Sigma^(1) = W Sigma_in W^dag, W = Tf (+) conj(Tf),
+  // zbar = (Tf alpha, conj(Tf alpha)), Tf[(j,l),(i,k)] = T_ji V_i[l,k]
+  std::vector<cd> Tf((size_t)MK * MK);
+  for (int j = 0; j < M; ++j)
+    for (int i = 0; i < M; ++i)
+      for (int l = 0; l < K; ++l)
+        for (int k = 0; k < K; ++k)
+          Tf[(size_t)(j * K + l) * MK + (i * K + k)] = P->T[(size_t)j * M + i] * P->V[((size_t)i * K + l) * K + k];
+  std::vector<cd> W((size_t)n * n, 0.0), Wh((size_t)n * n, 0.0), Sin((size_t)n * n, 0.0);
+  for (int a = 0; a < MK; ++a)
+    for (int c = 0; c < MK; ++c) {
+      W[(size_t)a * n + c] = Tf[(size_t)a * MK + c];
+      W[(size_t)(a + MK) * n + (c + MK)] = std::conj(Tf[(size_t)a * MK + c]);
+    }
+  for (int a = 0; a < n; ++a)
+    for (int c = 0; c < n; ++c) Wh[(size_t)a * n + c] = std::conj(W[(size_t)c * n + a]);
+  for (int q = 0; q < MK; ++q) {
+    double sh = std::sinh(P->r[q]), ch = std::cosh(P->r[q]);
+    Sin[(size_t)q * n + q] = Sin[(size_t)(q + MK) * n + (q + MK)] = sh * sh;
+    Sin[(size_t)q * n + (q + MK)] = Sin[(size_t)(q + MK) * n + q] = sh * ch;
+  }
+  std::vector<cd> WhB, C, SinWhB, BW, A;
+  matmul(Wh, B, WhB, n);
+  if (g->d_r) {
+    matmul(WhB, W, C, n);
+    for (int q = 0; q < MK; ++q) {
+      const int p = q + MK;
+      double s2 = std::sinh(2.0 * P->r[q]), c2 = std::cosh(2.0 * P->r[q]);
+      cd v = s2 * (C[(size_t)q * n + q] + C[(size_t)p * n + p]) + c2 * (C[(size_t)p * n + q] + C[(size_t)q * n + p]);
+      g->d_r[q] = v.real();
+    }
+  }
+  if (!(g->d_T || g->d_alpha || g->d_V)) return GBSBIN_OK;
+  matmul(Sin, WhB, SinWhB, n);
+  matmul(B, W, BW, n);
+  matmul(BW, Sin, A, n);
+  // G_W = conj(c1) + A with c1 = (Sigma_in W^dag B)^T; G_Tf = G_W11 + conj(G_W22) + z-bar terms
+  std::vector<cd> GTf((size_t)MK * MK);
+  for (int a = 0; a < MK; ++a)
+    for (int c = 0; c < MK; ++c) {
+      cd g11 = std::conj(SinWhB[(size_t)c * n + a]) + A[(size_t)a * n + c];
+      cd g22 = std::conj(SinWhB[(size_t)(c + MK) * n + (a + MK)]) + A[(size_t)(a + MK) * n + (c + MK)];
+      cd v1a = w[a], v2a = w[a + MK], al = P->alpha[c];
+      GTf[(size_t)a * MK + c] = g11 + std::conj(g22) + std::conj(v1a * al) + v2a * std::conj(al);
+    }
+  if (g->d_alpha)
+    for (int c = 0; c < MK; ++c) {
+      cd uu = 0.0;
+      for (int a = 0; a < MK; ++a) uu += Tf[(size_t)a * MK + c] * (w[a] + std::conj(w[a + MK]));
+      g->d_alpha[c] = gbsbin_complex{uu.real(), -uu.imag()};
+    }
+  if (g->d_T)
+    for (int j = 0; j < M; ++j)
+      for (int i = 0; i < M; ++i) {
+        cd acc = 0.0;
+        for (int l = 0; l < K; ++l)
+          for (int k = 0; k < K; ++k)
+            acc += GTf[(size_t)(j * K + l) * MK + (i * K + k)] * std::conj(P->V[((size_t)i * K + l) * K + k]);
+        g->d_T[(size_t)j * M + i] = gbsbin_complex{acc.real(), acc.imag()};
+      }
+  if (g->d_V)
+    for (int i = 0; i < M; ++i)
+      for (int l = 0; l < K; ++l)
+        for (int k = 0; k < K; ++k) {
+          cd acc = 0.0;
+          for (int j = 0; j < M; ++j)
+            acc += GTf[(size_t)(j * K + l) * MK + (i * K + k)] * std::conj(P->T[(size_t)j * M + i]);
+          g->d_V[((size_t)i * K + l) * K + k] = gbsbin_complex{acc.real(), acc.imag()};
+        }
+  return GBSBIN_OK;
 }
 
 int gbsbin_alu_peak(int precision, int blocks, double* tflops, void* stream) {

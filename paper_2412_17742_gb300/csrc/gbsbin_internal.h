@@ -10,6 +10,8 @@
 // Largest n whose n x n complex matrix (and, for the FP32 path, its residual) fits in
 // one CTA's shared memory next to the small vectors.
 #define GBSBIN_SMEM_MAX_N 112
+// Blocks of the diagnostics reduction; the host finishes the sum over their partials.
+#define GBSBIN_DIAG_BLOCKS 64
 
 namespace gbsbin {
 
@@ -45,6 +47,29 @@ struct PointArgs {
   double* minpiv;           // n_eval outputs: min_i Re u_ii
   void* gws;                // L2-resident workspace for the global-memory variants
   long long gws_slot_bytes; // bytes of one CTA's slot
+  double2* lu_store;        // FP64 kernels only, or nullptr: n_eval x n*n LU factors of M
+  double2* x_store;         // n_eval x n: x = M^{-1} X gamma
+};
+
+struct BackwardArgs {
+  int n;
+  GridDesc grid;
+  long long n_eval;
+  const double2* lu_store;  // n_eval x n*n
+  const double2* x_store;   // n_eval x n
+  const double2* gamma;     // n
+  const double2* logq;      // n_eval
+  const double2* tw;        // twiddles, as for the DFT
+  double2* bufA;            // max(table, n_eval) complex scratch
+  double2* bufB;            // max(table, n_eval) complex scratch
+  const double2* beta;      // set by the launcher
+  void* ws;                 // nparts slots of n*n complex
+  long long ws_slot_bytes;
+  double2* partS;           // nparts x n*n
+  double2* partg;           // nparts x n
+  int nparts;
+  double2* outS;            // n*n: dL/dXA (bilinear)
+  double2* outg;            // n: dL/dgamma (bilinear)
 };
 
 struct DftArgs {
@@ -54,7 +79,7 @@ struct DftArgs {
   double2* bufA;            // n_eval complex scratch
   double2* bufB;            // n_eval complex scratch
   double* P;                // table out (prod nout doubles)
-  double* diag;             // 8 doubles of reductions, or nullptr
+  double* diag;             // 4 GBSBIN_DIAG_BLOCKS + 1 partial reductions, or nullptr
   const double* minpiv;     // n_eval
   long long table_size;
 };
@@ -67,6 +92,7 @@ size_t points_matrix_bytes(int kernel, int n, int P);
 int points_per_cta(int kernel, int n, int L);
 int points_threads(int kernel, int n);
 cudaError_t launch_dft(const DftArgs& a, cudaStream_t s);
+cudaError_t launch_backward(const BackwardArgs& b, const double* dLdP, cudaStream_t s);
 cudaError_t launch_alu_peak(int fp64, int blocks, float* out_sink, int iters, cudaStream_t s);
 
 }  // namespace gbsbin
