@@ -249,6 +249,38 @@ typedef struct {
  */
 int gbsbin_backward(gbsbin_plan* plan, const double* dL_dP, gbsbin_grads* g, void* stream);
 
+/*
+ * Measured autotuning of the point kernel (no counterpart in the paper): for matrix size
+ * n (even, <= GBSBIN_MAX_N) and a precision, times the candidate kernels (warp per point
+ * for FP32R n <= 32; shared-memory CTA kernel with 1, 2, 4 or 8 points per CTA where they
+ * fit; L2-workspace kernel) on a synthetic state with ~1024 evaluated points and returns the
+ * fastest as a gbsbin_kernel id, points per CTA and microseconds per evaluated point.
+ * Results are cached per (n rounded up to a multiple of 16, precision) for the process.
+ * Synchronous; uses the current device.
+ */
+int gbsbin_autotune(int n, int precision, int* kernel, int* points_per_cta, double* us_per_point);
+
+/*
+ * Batches of independent problems (uneven sizes, groupings and cutoffs) evaluated
+ * together: one persistent point-kernel launch per kernel class takes (problem, point
+ * group) jobs from a device work queue, largest first; the inverse DFT then runs per
+ * problem.  Options apply to every problem (want_backward and want_timing are not
+ * supported: ERR_ARG); autotune != 0 picks each size's kernel with gbsbin_autotune.
+ * gbsbin_batch_capture_graph records one execute (into the given outputs) as a CUDA
+ * graph on a non-default stream; gbsbin_batch_replay relaunches it.  P_out is a host
+ * array of nprob device pointers, P_out[i] holding gbsbin_batch_table_size(b, i) doubles.
+ */
+typedef struct gbsbin_batch gbsbin_batch;
+int gbsbin_batch_create(const gbsbin_problem* probs, int nprob, const gbsbin_options* o, int autotune,
+                        gbsbin_batch** out);
+int gbsbin_batch_execute(gbsbin_batch* b, double* const* P_out, void* stream);
+int gbsbin_batch_capture_graph(gbsbin_batch* b, double* const* P_out, void* stream);
+int gbsbin_batch_replay(gbsbin_batch* b, void* stream);
+long long gbsbin_batch_table_size(const gbsbin_batch* b, int i);
+int gbsbin_batch_diagnostics(gbsbin_batch* b, int i, gbsbin_diag* out, void* stream);
+int gbsbin_batch_read_points(gbsbin_batch* b, int i, double* logq_host, double* minpiv_host, void* stream);
+int gbsbin_batch_destroy(gbsbin_batch* b);
+
 /* Static description of a status code. */
 const char* gbsbin_strerror(int status);
 

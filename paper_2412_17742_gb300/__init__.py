@@ -27,7 +27,9 @@ KERNELS = {1: "smem_fp64", 2: "smem_fp32r", 3: "gmem_fp64", 4: "gmem_fp32r", 5: 
 EXPORTED = ["gbsbin_default_options", "gbsbin_plan_create", "gbsbin_plan_set_state", "gbsbin_plan_destroy",
             "gbsbin_plan_table_size", "gbsbin_execute", "gbsbin_execute_host", "gbsbin_diagnostics",
             "gbsbin_strerror", "gbsbin_alu_peak", "gbsbin_read_points", "gbsbin_table_from_logq_noalloc",
-            "gbsbin_backward"]
+            "gbsbin_backward", "gbsbin_autotune", "gbsbin_batch_create", "gbsbin_batch_execute",
+            "gbsbin_batch_capture_graph", "gbsbin_batch_replay", "gbsbin_batch_table_size",
+            "gbsbin_batch_diagnostics", "gbsbin_batch_read_points", "gbsbin_batch_destroy"]
 
 
 class GbsbinError(RuntimeError):
@@ -94,9 +96,22 @@ def load():
     lib.gbsbin_read_points.argtypes = [vp, vp, vp, vp]
     lib.gbsbin_table_from_logq_noalloc.argtypes = [ctypes.c_int, _ip, ctypes.c_int, vp, vp, vp]
     lib.gbsbin_backward.argtypes = [vp, vp, ctypes.POINTER(gbsbin_grads), vp]
+    lib.gbsbin_autotune.argtypes = [ctypes.c_int, ctypes.c_int, _ip, _ip, _dp]
+    lib.gbsbin_batch_create.argtypes = [ctypes.POINTER(gbsbin_problem), ctypes.c_int, ctypes.POINTER(gbsbin_options),
+                                        ctypes.c_int, ctypes.POINTER(vp)]
+    lib.gbsbin_batch_execute.argtypes = [vp, ctypes.POINTER(vp), vp]
+    lib.gbsbin_batch_capture_graph.argtypes = [vp, ctypes.POINTER(vp), vp]
+    lib.gbsbin_batch_replay.argtypes = [vp, vp]
+    lib.gbsbin_batch_table_size.argtypes = [vp, ctypes.c_int]
+    lib.gbsbin_batch_table_size.restype = ctypes.c_longlong
+    lib.gbsbin_batch_diagnostics.argtypes = [vp, ctypes.c_int, ctypes.POINTER(gbsbin_diag), vp]
+    lib.gbsbin_batch_read_points.argtypes = [vp, ctypes.c_int, vp, vp, vp]
+    lib.gbsbin_batch_destroy.argtypes = [vp]
     for f in ("gbsbin_plan_create", "gbsbin_plan_set_state", "gbsbin_plan_destroy", "gbsbin_execute",
               "gbsbin_execute_host", "gbsbin_diagnostics", "gbsbin_alu_peak", "gbsbin_read_points",
-              "gbsbin_table_from_logq_noalloc", "gbsbin_backward"):
+              "gbsbin_table_from_logq_noalloc", "gbsbin_backward", "gbsbin_autotune", "gbsbin_batch_create",
+              "gbsbin_batch_execute", "gbsbin_batch_capture_graph", "gbsbin_batch_replay",
+              "gbsbin_batch_diagnostics", "gbsbin_batch_read_points", "gbsbin_batch_destroy"):
         getattr(lib, f).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -265,6 +280,14 @@ def gbsbin_backward(plan, dL_dP, M, K, n, stream=None, want=("r", "T", "alpha", 
     return res
 
 
+def gbsbin_autotune(n, precision):
+    """Returns (kernel id, points per CTA, microseconds per evaluated point)."""
+    k, p, us = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    _check(load().gbsbin_autotune(int(n), int(precision), ctypes.byref(k), ctypes.byref(p), ctypes.byref(us)),
+           "gbsbin_autotune")
+    return k.value, p.value, us.value
+
+
 def gbsbin_strerror(status):
     return load().gbsbin_strerror(int(status)).decode()
 
@@ -373,3 +396,78 @@ def binned_distribution(plan, template, r, T, alpha=None, V=None):
     if _BD is None:
         _BD = _autograd_function()
     return _BD.apply(plan, template, r, T, alpha, V)
+
+
+class Batch:
+    """Owning wrapper of a gbsbin batch: ``Batch(problems, precision=..., autotune=True)``."""
+
+    def __init__(self, problems, precision=GBSBIN_FP64, oversample=1, want_diagnostics=True, tile_override=0,
+                 autotune=False):
+        self._args = [ProblemArgs(p) for p in problems]
+        arr = (gbsbin_problem * len(self._args))(*[a.c for a in self._args])
+        self.options = make_options(precision, oversample, want_diagnostics, tile_override)
+        h = ctypes.c_void_p()
+        _check(load().gbsbin_batch_create(arr, len(self._args), ctypes.byref(self.options), int(bool(autotune)),
+                                          ctypes.byref(h)), "gbsbin_batch_create")
+        self.handle = h
+        self.shapes = [tuple(int(c) + 1 for c in p.cutoff) for p in problems]
+        self.outputs = None
+
+    def _out_array(self, outs):
+        return (ctypes.c_void_p * len(outs))(*[o.data_ptr() for o in outs])
+
+    def allocate(self):
+        import torch
+        self.outputs = [torch.empty(s, dtype=torch.float64, device="cuda") for s in self.shapes]
+        return self.outputs
+
+    def execute(self, stream=None):
+        """Evaluate every table into self.outputs (allocated on first use)."""
+        if self.outputs is None:
+            self.allocate()
+        _check(load().gbsbin_batch_execute(self.handle, self._out_array(self.outputs), _stream_handle(stream)),
+               "gbsbin_batch_execute")
+        return self.outputs
+
+    def capture(self, stream):
+        if self.outputs is None:
+            self.allocate()
+        _check(load().gbsbin_batch_capture_graph(self.handle, self._out_array(self.outputs), _stream_handle(stream)),
+               "gbsbin_batch_capture_graph")
+
+    def replay(self, stream):
+        _check(load().gbsbin_batch_replay(self.handle, _stream_handle(stream)), "gbsbin_batch_replay")
+        return self.outputs
+
+    def diagnostics(self, i, stream=None):
+        d = gbsbin_diag()
+        st = load().gbsbin_batch_diagnostics(self.handle, int(i), ctypes.byref(d), _stream_handle(stream))
+        if st not in (0, 7):
+            raise GbsbinError(st, "gbsbin_batch_diagnostics")
+        out = {f: getattr(d, f) for f, _ in gbsbin_diag._fields_}
+        out["kernel_name"] = KERNELS.get(out["kernel"], "?")
+        return st, out
+
+    def read_points(self, i, n_evaluated, stream=None):
+        lq = np.zeros(int(n_evaluated), dtype=np.complex128)
+        mp = np.zeros(int(n_evaluated), dtype=np.float64)
+        _check(load().gbsbin_batch_read_points(self.handle, int(i), _ptr(lq), _ptr(mp), _stream_handle(stream)),
+               "gbsbin_batch_read_points")
+        return lq, mp
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            _check(load().gbsbin_batch_destroy(self.handle), "gbsbin_batch_destroy")
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -2,6 +2,7 @@
 // (arXiv:2412.17742, Sec. II; output covariance as in Sec. VIII, Eq. output_cov_internal;
 // internal modes as in Sec. VI and App. B), device workspaces and launch orchestration.
 #include <algorithm>
+#include <tuple>
 #include <cmath>
 #include <complex>
 #include <cstdio>
@@ -445,7 +446,17 @@ const char* gbsbin_strerror(int status) {
   return "unknown status";
 }
 
+static int plan_create_impl(const gbsbin_problem* p, const gbsbin_options* o, gbsbin_plan** out, int p_override,
+                            bool alloc_gws);
+
 int gbsbin_plan_create(const gbsbin_problem* p, const gbsbin_options* o, gbsbin_plan** out) {
+  return plan_create_impl(p, o, out, 0, true);
+}
+
+// p_override > 0 forces the points per CTA (autotuning); alloc_gws = false leaves the
+// workspace to a batch that shares one across its problems.
+static int plan_create_impl(const gbsbin_problem* p, const gbsbin_options* o, gbsbin_plan** out, int p_override,
+                            bool alloc_gws) {
   if (!out) return GBSBIN_ERR_ARG;
   *out = nullptr;
   gbsbin_options opt;
@@ -486,6 +497,13 @@ int gbsbin_plan_create(const gbsbin_problem* p, const gbsbin_options* o, gbsbin_
   record_inputs(P, p);
   P->kernel = choose_kernel(n, p->L, opt.precision, opt.tile_override);
   P->P = P->kernel == GBSBIN_KERNEL_WARP_FP32R ? (n <= 32 ? 1 : 0) : points_per_cta(P->kernel, n, p->L);
+  if (p_override > 0 && P->P > 0 && (P->kernel == GBSBIN_KERNEL_SMEM_FP64 || P->kernel == GBSBIN_KERNEL_SMEM_FP32R)) {
+    if (points_smem_bytes(P->kernel, n, p_override, p->L) > 225 * 1024) {
+      delete P;
+      return GBSBIN_ERR_UNSUPPORTED;
+    }
+    P->P = p_override;
+  }
   if (P->P < 1) {  // a variant forced on a matrix it cannot hold
     delete P;
     return GBSBIN_ERR_UNSUPPORTED;
@@ -516,7 +534,7 @@ int gbsbin_plan_create(const gbsbin_problem* p, const gbsbin_options* o, gbsbin_
     delete P;
     return st;
   }
-  if (P->kernel == GBSBIN_KERNEL_GMEM_FP64 || P->kernel == GBSBIN_KERNEL_GMEM_FP32R) {
+  if (alloc_gws && (P->kernel == GBSBIN_KERNEL_GMEM_FP64 || P->kernel == GBSBIN_KERNEL_GMEM_FP32R)) {
     P->gws_slot_bytes = (long long)points_matrix_bytes(P->kernel, n, P->P);
     P->gws_slot_bytes = (P->gws_slot_bytes + 255) / 256 * 256;
     size_t bytes = (size_t)P->gws_slot_bytes * (size_t)P->num_sms;
@@ -620,9 +638,7 @@ int gbsbin_plan_destroy(gbsbin_plan* P) {
 
 long long gbsbin_plan_table_size(const gbsbin_plan* P) { return P ? P->table_size : -1; }
 
-int gbsbin_execute(gbsbin_plan* P, double* P_out, void* stream) {
-  if (!P || !P_out) return GBSBIN_ERR_ARG;
-  cudaStream_t s = (cudaStream_t)stream;
+static PointArgs make_point_args(gbsbin_plan* P) {
   PointArgs a{};
   a.n = P->n;
   a.has_gamma = P->has_gamma;
@@ -647,12 +663,10 @@ int gbsbin_execute(gbsbin_plan* P, double* P_out, void* stream) {
   const bool save = P->opt.want_backward && (P->kernel == GBSBIN_KERNEL_SMEM_FP64 || P->kernel == GBSBIN_KERNEL_GMEM_FP64);
   a.lu_store = save ? P->d_lu : nullptr;
   a.x_store = save ? P->d_xs : nullptr;
-  P->saved_valid = save;
-  if (P->ev0 && cudaEventRecord(P->ev0, s) != cudaSuccess) return GBSBIN_ERR_CUDA;
-  cudaError_t e = P->kernel == GBSBIN_KERNEL_WARP_FP32R ? launch_points_warp(a, P->num_sms, s)
-                                                        : launch_points(a, P->kernel, P->num_sms, s);
-  if (e != cudaSuccess) return GBSBIN_ERR_CUDA;
-  if (P->ev1 && cudaEventRecord(P->ev1, s) != cudaSuccess) return GBSBIN_ERR_CUDA;
+  return a;
+}
+
+static DftArgs make_dft_args(gbsbin_plan* P, double* P_out) {
   DftArgs d{};
   d.grid = P->grid;
   d.logq = P->d_logq;
@@ -663,7 +677,20 @@ int gbsbin_execute(gbsbin_plan* P, double* P_out, void* stream) {
   d.diag = P->opt.want_diagnostics ? P->d_diag : nullptr;
   d.minpiv = P->d_minpiv;
   d.table_size = P->table_size;
-  e = launch_dft(d, s);
+  return d;
+}
+
+int gbsbin_execute(gbsbin_plan* P, double* P_out, void* stream) {
+  if (!P || !P_out) return GBSBIN_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  PointArgs a = make_point_args(P);
+  P->saved_valid = a.lu_store != nullptr;
+  if (P->ev0 && cudaEventRecord(P->ev0, s) != cudaSuccess) return GBSBIN_ERR_CUDA;
+  cudaError_t e = P->kernel == GBSBIN_KERNEL_WARP_FP32R ? launch_points_warp(a, P->num_sms, s)
+                                                        : launch_points(a, P->kernel, P->num_sms, s);
+  if (e != cudaSuccess) return GBSBIN_ERR_CUDA;
+  if (P->ev1 && cudaEventRecord(P->ev1, s) != cudaSuccess) return GBSBIN_ERR_CUDA;
+  e = launch_dft(make_dft_args(P, P_out), s);
   return e == cudaSuccess ? GBSBIN_OK : GBSBIN_ERR_CUDA;
 }
 
@@ -887,6 +914,352 @@ int gbsbin_alu_peak(int precision, int blocks, double* tflops, void* stream) {
   cudaEventDestroy(e1);
   cudaFree(sink);
   return st;
+}
+
+}  // extern "C"
+
+// =============================================================== autotuning
+// Measured choice of the point-kernel variant and points per CTA for a matrix size.
+// Candidates (per precision): the warp kernel (FP32R, n <= 32), the shared-memory CTA
+// kernel with P = 1, 2, 4, 8 where the footprint fits, and the workspace kernel.  Each is
+// timed with CUDA events on a synthetic state of that size (the unpivoted LU does the same
+// arithmetic for any values) over a one-group grid of ~1024 evaluated points; results are
+// cached per (size bucket of 16, precision) for the life of the process.
+#include <map>
+#include <mutex>
+
+namespace {
+
+struct TuneKey {
+  int nb, precision;
+  bool operator<(const TuneKey& o) const { return nb != o.nb ? nb < o.nb : precision < o.precision; }
+};
+struct TuneVal {
+  int kernel, P;
+  double us_per_point;
+};
+std::map<TuneKey, TuneVal> g_tune;
+std::mutex g_tune_mu;
+
+int tune_size(int n, int precision, TuneVal* best) {
+  const int M = n / 2;
+  std::vector<double> r(M, 0.7);
+  std::vector<gbsbin_complex> T((size_t)M * M);
+  const double TWO_PI = 6.283185307179586476925286766559;
+  for (int j = 0; j < M; ++j)  // 0.8 x unitary DFT matrix: dense, ||T|| < 1
+    for (int i = 0; i < M; ++i) {
+      double a = TWO_PI * (double)i * (double)j / (double)M;
+      T[(size_t)j * M + i] = gbsbin_complex{0.8 * std::cos(a) / std::sqrt((double)M), 0.8 * std::sin(a) / std::sqrt((double)M)};
+    }
+  std::vector<int> bins(M, 0);
+  int cutoff = 2047;  // one axis, half = 1025 evaluated points
+  gbsbin_problem pr{};
+  pr.M = M;
+  pr.K = 1;
+  pr.r = r.data();
+  pr.T = T.data();
+  pr.bin_of_mode = bins.data();
+  pr.L = 1;
+  pr.cutoff = &cutoff;
+  struct Cand {
+    int kernel, P;
+  };
+  std::vector<Cand> cands;
+  if (precision == GBSBIN_FP32_REFINE && n <= 32) cands.push_back({GBSBIN_KERNEL_WARP_FP32R, 1});
+  const int smem_k = precision == GBSBIN_FP64 ? GBSBIN_KERNEL_SMEM_FP64 : GBSBIN_KERNEL_SMEM_FP32R;
+  const int gmem_k = precision == GBSBIN_FP64 ? GBSBIN_KERNEL_GMEM_FP64 : GBSBIN_KERNEL_GMEM_FP32R;
+  for (int Pc = 1; Pc <= 8; Pc *= 2)
+    if (points_smem_bytes(smem_k, n, Pc, 1) <= 225 * 1024) cands.push_back({smem_k, Pc});
+  cands.push_back({gmem_k, 1});
+  best->us_per_point = 1e300;
+  best->kernel = 0;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return GBSBIN_ERR_CUDA;
+  double* table = nullptr;
+  if (cudaMalloc(&table, sizeof(double) * (cutoff + 1)) != cudaSuccess) return GBSBIN_ERR_NOMEM;
+  int status = GBSBIN_OK;
+  for (const Cand& c : cands) {
+    gbsbin_options o;
+    gbsbin_default_options(&o);
+    o.precision = precision;
+    o.tile_override = c.kernel;
+    o.want_diagnostics = 0;
+    gbsbin_plan* P = nullptr;
+    if (plan_create_impl(&pr, &o, &P, c.P, true) != GBSBIN_OK) continue;
+    PointArgs a = make_point_args(P);
+    float best_ms = 1e30f;
+    for (int rep = 0; rep < 3; ++rep) {
+      cudaEventRecord(e0, 0);
+      cudaError_t err = P->kernel == GBSBIN_KERNEL_WARP_FP32R ? launch_points_warp(a, P->num_sms, 0)
+                                                              : launch_points(a, P->kernel, P->num_sms, 0);
+      cudaEventRecord(e1, 0);
+      if (err != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+        status = GBSBIN_ERR_CUDA;
+        break;
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep > 0 && ms < best_ms) best_ms = ms;  // first launch is a warm-up
+    }
+    const double us = 1e3 * best_ms / (double)P->grid.n_eval;
+    if (status == GBSBIN_OK && us < best->us_per_point) *best = TuneVal{c.kernel, P->P, us};
+    gbsbin_plan_destroy(P);
+    if (status) break;
+  }
+  cudaFree(table);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return best->kernel ? status : (status ? status : GBSBIN_ERR_UNSUPPORTED);
+}
+
+int autotune_lookup(int n, int precision, TuneVal* out) {
+  const int nb = (n + 15) / 16 * 16;
+  const int ntune = std::min(std::max(nb, 16), GBSBIN_MAX_N);
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tune.find(TuneKey{nb, precision});
+    if (it != g_tune.end()) {
+      *out = it->second;
+      return GBSBIN_OK;
+    }
+  }
+  TuneVal v{};
+  int st = tune_size(ntune, precision, &v);
+  if (st) return st;
+  // a choice tuned at the bucket's top size must still be legal for n itself
+  if (v.kernel == GBSBIN_KERNEL_WARP_FP32R && n > 32) v = TuneVal{GBSBIN_KERNEL_SMEM_FP32R, 1, v.us_per_point};
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tune[TuneKey{nb, precision}] = v;
+  *out = v;
+  return GBSBIN_OK;
+}
+
+}  // namespace
+
+// ================================================================== batches
+struct gbsbin_batch {
+  std::vector<gbsbin_plan*> plans;
+  struct Class {
+    int kernel = 0, threads = 0, np = 0;
+    size_t smem = 0;
+    std::vector<PointJob> jobs;
+    PointJob* d_jobs = nullptr;
+  };
+  std::vector<Class> classes;
+  PointArgs* d_probs = nullptr;
+  unsigned long long* d_queue = nullptr;
+  void* d_gws = nullptr;
+  long long gws_slot = 0;
+  int num_sms = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+};
+
+namespace {
+
+void batch_free(gbsbin_batch* B) {
+  if (B->graph_exec) cudaGraphExecDestroy(B->graph_exec);
+  if (B->graph) cudaGraphDestroy(B->graph);
+  for (auto& c : B->classes)
+    if (c.d_jobs) cudaFree(c.d_jobs);
+  if (B->d_probs) cudaFree(B->d_probs);
+  if (B->d_queue) cudaFree(B->d_queue);
+  if (B->d_gws) cudaFree(B->d_gws);
+  for (gbsbin_plan* P : B->plans)
+    if (P) gbsbin_plan_destroy(P);
+  delete B;
+}
+
+int batch_launch(gbsbin_batch* B, double* const* P_out, cudaStream_t s) {
+  for (size_t c = 0; c < B->classes.size(); ++c) {
+    auto& C = B->classes[c];
+    if (C.jobs.empty()) continue;
+    if (cudaMemsetAsync(B->d_queue + c, 0, sizeof(unsigned long long), s) != cudaSuccess) return GBSBIN_ERR_CUDA;
+    PointBatch pb{B->d_probs, C.d_jobs, (long long)C.jobs.size(), B->d_queue + c};
+    cudaError_t e = C.kernel == GBSBIN_KERNEL_WARP_FP32R
+                        ? launch_points_warp_batch(pb, C.np, B->num_sms, s)
+                        : launch_points_batch(pb, C.kernel, C.threads, C.smem, B->num_sms, s);
+    if (e != cudaSuccess) return GBSBIN_ERR_CUDA;
+  }
+  for (size_t i = 0; i < B->plans.size(); ++i) {
+    if (!P_out[i]) return GBSBIN_ERR_ARG;
+    if (launch_dft(make_dft_args(B->plans[i], P_out[i]), s) != cudaSuccess) return GBSBIN_ERR_CUDA;
+  }
+  return GBSBIN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int gbsbin_autotune(int n, int precision, int* kernel, int* points_per_cta_out, double* us_per_point) {
+  if (n < 2 || n > GBSBIN_MAX_N || (n & 1)) return GBSBIN_ERR_ARG;
+  if (precision != GBSBIN_FP64 && precision != GBSBIN_FP32_REFINE) return GBSBIN_ERR_ARG;
+  TuneVal v{};
+  int st = autotune_lookup(n, precision, &v);
+  if (st) return st;
+  if (kernel) *kernel = v.kernel;
+  if (points_per_cta_out) *points_per_cta_out = v.P;
+  if (us_per_point) *us_per_point = v.us_per_point;
+  return GBSBIN_OK;
+}
+
+int gbsbin_batch_create(const gbsbin_problem* probs, int nprob, const gbsbin_options* o, int autotune,
+                        gbsbin_batch** out) {
+  if (!out || !probs || nprob <= 0) return GBSBIN_ERR_ARG;
+  *out = nullptr;
+  gbsbin_options opt;
+  gbsbin_default_options(&opt);
+  if (o) opt = *o;
+  if (opt.want_backward || opt.want_timing) return GBSBIN_ERR_ARG;  // per-plan features only
+  gbsbin_batch* B = new (std::nothrow) gbsbin_batch();
+  if (!B) return GBSBIN_ERR_NOMEM;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&B->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    delete B;
+    return GBSBIN_ERR_CUDA;
+  }
+  B->plans.assign(nprob, nullptr);
+  std::vector<PointArgs> args(nprob);
+  std::map<std::tuple<int, int, int>, int> class_of;
+  for (int i = 0; i < nprob; ++i) {
+    gbsbin_options oi = opt;
+    int p_override = 0;
+    const int n = 2 * probs[i].M * probs[i].K;
+    if (autotune && !opt.tile_override && n <= GBSBIN_MAX_N) {
+      TuneVal v{};
+      int st = autotune_lookup(n, opt.precision, &v);
+      if (st) {
+        batch_free(B);
+        return st;
+      }
+      oi.tile_override = v.kernel;
+      p_override = v.P;
+    }
+    int st = plan_create_impl(&probs[i], &oi, &B->plans[i], p_override, false);
+    if (st == GBSBIN_ERR_UNSUPPORTED && p_override) st = plan_create_impl(&probs[i], &opt, &B->plans[i], 0, false);
+    if (st) {
+      batch_free(B);
+      return st;
+    }
+    gbsbin_plan* P = B->plans[i];
+    args[i] = make_point_args(P);
+    const int threads = P->kernel == GBSBIN_KERNEL_WARP_FP32R ? 128 : points_threads(P->kernel, P->n);
+    const int np = P->kernel == GBSBIN_KERNEL_WARP_FP32R ? (P->n <= 8 ? 8 : P->n <= 16 ? 16 : 32) : 0;
+    auto key = std::make_tuple(P->kernel, threads, np);
+    if (!class_of.count(key)) {
+      class_of[key] = (int)B->classes.size();
+      B->classes.emplace_back();
+      B->classes.back().kernel = P->kernel;
+      B->classes.back().threads = threads;
+      B->classes.back().np = np;
+    }
+    auto& C = B->classes[class_of[key]];
+    const int group = P->kernel == GBSBIN_KERNEL_WARP_FP32R ? 4 : P->P;
+    for (long long e0 = 0; e0 < P->grid.n_eval; e0 += group) C.jobs.push_back(PointJob{i, 0, e0});
+    if (P->kernel == GBSBIN_KERNEL_SMEM_FP64 || P->kernel == GBSBIN_KERNEL_SMEM_FP32R ||
+        P->kernel == GBSBIN_KERNEL_GMEM_FP64 || P->kernel == GBSBIN_KERNEL_GMEM_FP32R)
+      C.smem = std::max(C.smem, points_smem_bytes(P->kernel, P->n, P->P, P->L));
+    if (P->kernel == GBSBIN_KERNEL_GMEM_FP64 || P->kernel == GBSBIN_KERNEL_GMEM_FP32R)
+      B->gws_slot = std::max(B->gws_slot, ((long long)points_matrix_bytes(P->kernel, P->n, 1) + 255) / 256 * 256);
+  }
+  if (B->gws_slot > 0) {
+    if (cudaMalloc(&B->d_gws, (size_t)B->gws_slot * B->num_sms) != cudaSuccess) {
+      cudaGetLastError();
+      batch_free(B);
+      return GBSBIN_ERR_NOMEM;
+    }
+    for (auto& a : args) {
+      a.gws = B->d_gws;
+      a.gws_slot_bytes = B->gws_slot;
+    }
+  }
+  // largest jobs first: cost ~ n^3 x points per job, so the queue ends on small jobs
+  for (auto& C : B->classes) {
+    std::stable_sort(C.jobs.begin(), C.jobs.end(), [&](const PointJob& x, const PointJob& y) {
+      double cx = std::pow((double)B->plans[x.prob]->n, 3) * B->plans[x.prob]->P;
+      double cy = std::pow((double)B->plans[y.prob]->n, 3) * B->plans[y.prob]->P;
+      return cx > cy;
+    });
+    if (cudaMalloc(&C.d_jobs, C.jobs.size() * sizeof(PointJob)) != cudaSuccess ||
+        cudaMemcpy(C.d_jobs, C.jobs.data(), C.jobs.size() * sizeof(PointJob), cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaGetLastError();
+      batch_free(B);
+      return GBSBIN_ERR_NOMEM;
+    }
+  }
+  if (cudaMalloc(&B->d_probs, sizeof(PointArgs) * nprob) != cudaSuccess ||
+      cudaMemcpy(B->d_probs, args.data(), sizeof(PointArgs) * nprob, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMalloc(&B->d_queue, sizeof(unsigned long long) * std::max<size_t>(1, B->classes.size())) != cudaSuccess) {
+    cudaGetLastError();
+    batch_free(B);
+    return GBSBIN_ERR_NOMEM;
+  }
+  *out = B;
+  return GBSBIN_OK;
+}
+
+int gbsbin_batch_destroy(gbsbin_batch* B) {
+  if (!B) return GBSBIN_ERR_ARG;
+  cudaDeviceSynchronize();
+  batch_free(B);
+  return GBSBIN_OK;
+}
+
+long long gbsbin_batch_table_size(const gbsbin_batch* B, int i) {
+  if (!B || i < 0 || i >= (int)B->plans.size()) return -1;
+  return B->plans[i]->table_size;
+}
+
+int gbsbin_batch_execute(gbsbin_batch* B, double* const* P_out, void* stream) {
+  if (!B || !P_out) return GBSBIN_ERR_ARG;
+  return batch_launch(B, P_out, (cudaStream_t)stream);
+}
+
+int gbsbin_batch_capture_graph(gbsbin_batch* B, double* const* P_out, void* stream) {
+  if (!B || !P_out) return GBSBIN_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!s) return GBSBIN_ERR_ARG;  // the legacy default stream cannot be captured
+  if (B->graph_exec) {
+    cudaGraphExecDestroy(B->graph_exec);
+    B->graph_exec = nullptr;
+  }
+  if (B->graph) {
+    cudaGraphDestroy(B->graph);
+    B->graph = nullptr;
+  }
+  if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return GBSBIN_ERR_CUDA;
+  int st = batch_launch(B, P_out, s);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(s, &g);
+  if (st) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  if (e != cudaSuccess || !g) return GBSBIN_ERR_CUDA;
+  B->graph = g;
+  if (cudaGraphInstantiate(&B->graph_exec, g, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return GBSBIN_ERR_CUDA;
+  }
+  return GBSBIN_OK;
+}
+
+int gbsbin_batch_replay(gbsbin_batch* B, void* stream) {
+  if (!B || !B->graph_exec) return GBSBIN_ERR_ARG;
+  return cudaGraphLaunch(B->graph_exec, (cudaStream_t)stream) == cudaSuccess ? GBSBIN_OK : GBSBIN_ERR_CUDA;
+}
+
+int gbsbin_batch_diagnostics(gbsbin_batch* B, int i, gbsbin_diag* out, void* stream) {
+  if (!B || i < 0 || i >= (int)B->plans.size()) return GBSBIN_ERR_ARG;
+  return gbsbin_diagnostics(B->plans[i], out, stream);
+}
+
+int gbsbin_batch_read_points(gbsbin_batch* B, int i, double* logq_host, double* minpiv_host, void* stream) {
+  if (!B || i < 0 || i >= (int)B->plans.size()) return GBSBIN_ERR_ARG;
+  return gbsbin_read_points(B->plans[i], logq_host, minpiv_host, stream);
 }
 
 }  // extern "C"

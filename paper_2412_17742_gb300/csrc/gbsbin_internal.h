@@ -51,6 +51,20 @@ struct PointArgs {
   double2* x_store;         // n_eval x n: x = M^{-1} X gamma
 };
 
+// A batch of problems for one point-kernel launch: jobs are (problem, first point) groups
+// taken in order from an atomic counter (reset to 0 before every launch).
+struct PointJob {
+  int prob;
+  int pad;
+  long long e0;
+};
+struct PointBatch {
+  const PointArgs* probs;   // device array of per-problem descriptors (nullptr: single problem)
+  const PointJob* jobs;     // device array
+  long long njobs;
+  unsigned long long* queue;
+};
+
 struct BackwardArgs {
   int n;
   GridDesc grid;
@@ -87,6 +101,9 @@ struct DftArgs {
 // Kernel launchers (return the launch error).
 cudaError_t launch_points(const PointArgs& a, int kernel, int num_sms, cudaStream_t s);
 cudaError_t launch_points_warp(const PointArgs& a, int num_sms, cudaStream_t s);
+cudaError_t launch_points_batch(const PointBatch& batch, int kernel, int threads, size_t smem, int num_sms,
+                                cudaStream_t s);
+cudaError_t launch_points_warp_batch(const PointBatch& batch, int np, int num_sms, cudaStream_t s);
 size_t points_smem_bytes(int kernel, int n, int P, int L);
 size_t points_matrix_bytes(int kernel, int n, int P);
 int points_per_cta(int kernel, int n, int L);

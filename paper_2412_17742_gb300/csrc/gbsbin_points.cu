@@ -43,8 +43,7 @@ __host__ __device__ inline int layout_stride(int n) { return n * n + 1; }
 
 // ------------------------------------------------------------------------ FP64 path
 template <int NT, bool SMEM>
-__global__ void __launch_bounds__(NT) k_points_fp64(PointArgs a) {
-  extern __shared__ __align__(16) unsigned char smem[];
+__device__ __forceinline__ void group_fp64(const PointArgs& a, const long long e0, unsigned char* smem) {
   const int n = a.n, P = a.P, logP = a.logP, L = a.grid.L;
   const int S = layout_stride(n);
   const int tid = threadIdx.x, warp = tid >> 5, nwarps = NT / 32;
@@ -62,9 +61,7 @@ __global__ void __launch_bounds__(NT) k_points_fp64(PointArgs a) {
   double2* xv = pinv + (size_t)P * n;  // P x n solution
   int* lab = (int*)(xv + (size_t)P * n);
   for (int i = tid; i < n; i += NT) lab[i] = a.label[i];
-
-  const long long step = (long long)gridDim.x * P;
-  for (long long e0 = (long long)blockIdx.x * P; e0 < a.grid.n_eval; e0 += step) {
+  {
     for (int t = tid; t < P * L; t += NT) {
       int p = t / L, l = t - p * L;
       long long e = min(e0 + p, a.grid.n_eval - 1);
@@ -159,10 +156,37 @@ __global__ void __launch_bounds__(NT) k_points_fp64(PointArgs a) {
   }
 }
 
+// One problem: CTAs stride over its point groups.  A batch: CTAs take (problem, group)
+// jobs from an atomic queue, so uneven problems balance dynamically; every job writes only
+// its own outputs, so results do not depend on the order.
+template <int NT, bool SMEM>
+__global__ void __launch_bounds__(NT) k_points_fp64(PointArgs a0, PointBatch batch) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  if (!batch.probs) {
+    const long long step = (long long)gridDim.x * a0.P;
+    for (long long e0 = (long long)blockIdx.x * a0.P; e0 < a0.grid.n_eval; e0 += step)
+      group_fp64<NT, SMEM>(a0, e0, smem);
+    return;
+  }
+  __shared__ PointArgs sa;
+  __shared__ long long sj;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const unsigned long long j = atomicAdd(batch.queue, 1ull);
+      sj = (long long)j;
+      if ((long long)j < batch.njobs) sa = batch.probs[batch.jobs[j].prob];
+    }
+    __syncthreads();
+    const long long j = sj;
+    if (j >= batch.njobs) break;
+    group_fp64<NT, SMEM>(sa, batch.jobs[j].e0, smem);
+    __syncthreads();
+  }
+}
+
 // -------------------------------------------------------------- FP32 + refinement path
 template <int NT, bool SMEM>
-__global__ void __launch_bounds__(NT) k_points_fp32r(PointArgs a) {
-  extern __shared__ __align__(16) unsigned char smem[];
+__device__ __forceinline__ void group_fp32r(const PointArgs& a, const long long e0, unsigned char* smem) {
   const int n = a.n, P = a.P, logP = a.logP, L = a.grid.L;
   const int S = layout_stride(n);
   const int tid = threadIdx.x, warp = tid >> 5, nwarps = NT / 32;
@@ -187,9 +211,7 @@ __global__ void __launch_bounds__(NT) k_points_fp32r(PointArgs a) {
   double2* delta = (double2*)(rv + (size_t)P * n);  // P trace corrections
   int* lab = (int*)(delta + P);
   for (int i = tid; i < n; i += NT) lab[i] = a.label[i];
-
-  const long long step = (long long)gridDim.x * P;
-  for (long long e0 = (long long)blockIdx.x * P; e0 < a.grid.n_eval; e0 += step) {
+  {
     for (int t = tid; t < P * L; t += NT) {
       int p = t / L, l = t - p * L;
       long long e = min(e0 + p, a.grid.n_eval - 1);
@@ -440,6 +462,31 @@ __global__ void __launch_bounds__(NT) k_points_fp32r(PointArgs a) {
   }
 }
 
+template <int NT, bool SMEM>
+__global__ void __launch_bounds__(NT) k_points_fp32r(PointArgs a0, PointBatch batch) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  if (!batch.probs) {
+    const long long step = (long long)gridDim.x * a0.P;
+    for (long long e0 = (long long)blockIdx.x * a0.P; e0 < a0.grid.n_eval; e0 += step)
+      group_fp32r<NT, SMEM>(a0, e0, smem);
+    return;
+  }
+  __shared__ PointArgs sa;
+  __shared__ long long sj;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const unsigned long long j = atomicAdd(batch.queue, 1ull);
+      sj = (long long)j;
+      if ((long long)j < batch.njobs) sa = batch.probs[batch.jobs[j].prob];
+    }
+    __syncthreads();
+    const long long j = sj;
+    if (j >= batch.njobs) break;
+    group_fp32r<NT, SMEM>(sa, batch.jobs[j].e0, smem);
+    __syncthreads();
+  }
+}
+
 // ----------------------------------------------------------------------- launchers
 static int threads_for(int n) { return n <= 48 ? 128 : 256; }
 
@@ -474,9 +521,10 @@ int points_per_cta(int kernel, int n, int L) {
 }
 
 template <int NT>
-static cudaError_t launch_nt(const PointArgs& a, int kernel, int num_sms, cudaStream_t s) {
-  size_t smem = points_smem_bytes(kernel, a.n, a.P, a.grid.L);
-  void (*fn)(PointArgs) = nullptr;
+static cudaError_t launch_nt(const PointArgs& a, const PointBatch& batch, size_t smem_batch, int kernel, int num_sms,
+                             cudaStream_t s) {
+  size_t smem = batch.probs ? smem_batch : points_smem_bytes(kernel, a.n, a.P, a.grid.L);
+  void (*fn)(PointArgs, PointBatch) = nullptr;
   switch (kernel) {
     case GBSBIN_KERNEL_SMEM_FP64: fn = k_points_fp64<NT, true>; break;
     case GBSBIN_KERNEL_GMEM_FP64: fn = k_points_fp64<NT, false>; break;
@@ -487,7 +535,7 @@ static cudaError_t launch_nt(const PointArgs& a, int kernel, int num_sms, cudaSt
   cudaError_t err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
   long long grid;
-  const long long groups = (a.grid.n_eval + a.P - 1) / a.P;
+  const long long groups = batch.probs ? batch.njobs : (a.grid.n_eval + a.P - 1) / a.P;
   if (kernel == GBSBIN_KERNEL_GMEM_FP64 || kernel == GBSBIN_KERNEL_GMEM_FP32R) {
     grid = num_sms;  // one workspace slot per CTA
   } else {
@@ -499,14 +547,24 @@ static cudaError_t launch_nt(const PointArgs& a, int kernel, int num_sms, cudaSt
   }
   if (grid > groups) grid = groups;
   if (grid < 1) grid = 1;
-  fn<<<(unsigned)grid, NT, smem, s>>>(a);
+  fn<<<(unsigned)grid, NT, smem, s>>>(a, batch);
   return cudaGetLastError();
 }
 
 cudaError_t launch_points(const PointArgs& a, int kernel, int num_sms, cudaStream_t s) {
+  PointBatch none{};
   int nt = threads_for(a.n);
-  if (nt == 128) return launch_nt<128>(a, kernel, num_sms, s);
-  return launch_nt<256>(a, kernel, num_sms, s);
+  if (nt == 128) return launch_nt<128>(a, none, 0, kernel, num_sms, s);
+  return launch_nt<256>(a, none, 0, kernel, num_sms, s);
+}
+
+cudaError_t launch_points_batch(const PointBatch& batch, int kernel, int threads, size_t smem, int num_sms,
+                                cudaStream_t s) {
+  PointArgs dummy{};
+  dummy.P = 1;
+  dummy.grid.n_eval = 1;
+  if (threads == 128) return launch_nt<128>(dummy, batch, smem, kernel, num_sms, s);
+  return launch_nt<256>(dummy, batch, smem, kernel, num_sms, s);
 }
 
 // ------------------------------------------------------------- ALU throughput probe

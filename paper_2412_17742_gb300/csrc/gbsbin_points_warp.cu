@@ -37,33 +37,34 @@ __device__ __forceinline__ float2 shfl2(float2 v, int src) {
 }  // namespace
 
 template <int NP, int WARPS>
-__global__ void __launch_bounds__(WARPS * 32, 3) k_points_fp32r_warp(PointArgs a) {
+struct WarpShared {
+  double2 w[WARPS][GBSBIN_MAX_L];
+  float2 inv[WARPS][NP];
+  float2 LU[WARPS][NP * (NP + 4)];
+  float2 x[WARPS][NP];
+  float2 r[WARPS][NP];
+  int lab[NP];
+};
+
+// One grid point per warp: point e of problem a (e >= n_eval: idle warp).
+template <int NP, int WARPS>
+__device__ __forceinline__ void warp_point(const PointArgs& a, const long long e, WarpShared<NP, WARPS>& sh) {
   constexpr int RA = NP / 8;     // rows per lane
   constexpr int CB = NP / 4;     // columns per lane
   constexpr int NKB = NP / 4;    // 4-step blocks of the elimination
   constexpr int CH = CB / 2;     // columns per lane in one half of the residual pass
   constexpr int ES = NP + 4;     // row stride of the shared tile (bank stagger)
-  __shared__ double2 s_w[WARPS][GBSBIN_MAX_L];
-  __shared__ float2 s_inv[WARPS][NP];
-  __shared__ __align__(16) float2 s_LU[WARPS][NP * ES];
-  __shared__ float2 s_x[WARPS][NP];
-  __shared__ float2 s_r[WARPS][NP];
-  __shared__ int s_lab[NP];
-
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int lr = lane >> 2, lc = lane & 3;
   const int n = a.n, L = a.grid.L;
-  for (int i = threadIdx.x; i < NP; i += WARPS * 32) s_lab[i] = i < n ? a.label[i] : 0;
-  __syncthreads();
-  double2* w = s_w[warp];
-  float2* invk = s_inv[warp];
-  float2* T = s_LU[warp];
-  float2* xs = s_x[warp];
-  float2* rs = s_r[warp];
+  const int* s_lab = sh.lab;
+  double2* w = sh.w[warp];
+  float2* invk = sh.inv[warp];
+  float2* T = sh.LU[warp];
+  float2* xs = sh.x[warp];
+  float2* rs = sh.r[warp];
   const float2 zero = make_float2(0.0f, 0.0f);
-
-  for (long long e = (long long)blockIdx.x * WARPS + warp; e < a.grid.n_eval;
-       e += (long long)gridDim.x * WARPS) {
+  if (e < a.grid.n_eval) {
     if (lane < L) w[lane] = root_of_unity(point_digit(e, a.grid, lane), a.grid.radix[lane]);
     __syncwarp();
 
@@ -362,26 +363,66 @@ __global__ void __launch_bounds__(WARPS * 32, 3) k_points_fp32r_warp(PointArgs a
   }
 }
 
+template <int NP, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32, 3) k_points_fp32r_warp(PointArgs a0, PointBatch batch) {
+  __shared__ __align__(16) WarpShared<NP, WARPS> sh;
+  const int warp = threadIdx.x >> 5;
+  if (!batch.probs) {
+    for (int i = threadIdx.x; i < NP; i += WARPS * 32) sh.lab[i] = i < a0.n ? a0.label[i] : 0;
+    __syncthreads();
+    for (long long e = (long long)blockIdx.x * WARPS + warp; e < a0.grid.n_eval; e += (long long)gridDim.x * WARPS)
+      warp_point<NP, WARPS>(a0, e, sh);
+    return;
+  }
+  __shared__ PointArgs sa;
+  __shared__ long long sj;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const unsigned long long j = atomicAdd(batch.queue, 1ull);
+      sj = (long long)j;
+      if ((long long)j < batch.njobs) sa = batch.probs[batch.jobs[j].prob];
+    }
+    __syncthreads();
+    const long long j = sj;
+    if (j >= batch.njobs) break;
+    for (int i = threadIdx.x; i < NP; i += WARPS * 32) sh.lab[i] = i < sa.n ? sa.label[i] : 0;
+    __syncthreads();
+    warp_point<NP, WARPS>(sa, batch.jobs[j].e0 + warp, sh);
+    __syncthreads();
+  }
+}
+
 template <int NP>
-static cudaError_t launch_warp_np(const PointArgs& a, int num_sms, cudaStream_t s) {
+static cudaError_t launch_warp_np(const PointArgs& a, const PointBatch& batch, int num_sms, cudaStream_t s) {
   constexpr int WARPS = 4;
   int per_sm = 0;
   cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_points_fp32r_warp<NP, WARPS>,
                                                                   WARPS * 32, 0);
   if (err != cudaSuccess) return err;
   if (per_sm < 1) per_sm = 1;
-  long long groups = (a.grid.n_eval + WARPS - 1) / WARPS;
+  long long groups = batch.probs ? batch.njobs : (a.grid.n_eval + WARPS - 1) / WARPS;
   long long grid = (long long)per_sm * num_sms;
   if (grid > groups) grid = groups;
   if (grid < 1) grid = 1;
-  k_points_fp32r_warp<NP, WARPS><<<(unsigned)grid, WARPS * 32, 0, s>>>(a);
+  k_points_fp32r_warp<NP, WARPS><<<(unsigned)grid, WARPS * 32, 0, s>>>(a, batch);
   return cudaGetLastError();
 }
 
 cudaError_t launch_points_warp(const PointArgs& a, int num_sms, cudaStream_t s) {
-  if (a.n <= 8) return launch_warp_np<8>(a, num_sms, s);
-  if (a.n <= 16) return launch_warp_np<16>(a, num_sms, s);
-  if (a.n <= 32) return launch_warp_np<32>(a, num_sms, s);
+  PointBatch none{};
+  if (a.n <= 8) return launch_warp_np<8>(a, none, num_sms, s);
+  if (a.n <= 16) return launch_warp_np<16>(a, none, num_sms, s);
+  if (a.n <= 32) return launch_warp_np<32>(a, none, num_sms, s);
+  return cudaErrorInvalidValue;
+}
+
+// Batch: jobs of WARPS consecutive points of one problem; np is the padded size class.
+cudaError_t launch_points_warp_batch(const PointBatch& batch, int np, int num_sms, cudaStream_t s) {
+  PointArgs dummy{};
+  dummy.grid.n_eval = 1;
+  if (np == 8) return launch_warp_np<8>(dummy, batch, num_sms, s);
+  if (np == 16) return launch_warp_np<16>(dummy, batch, num_sms, s);
+  if (np == 32) return launch_warp_np<32>(dummy, batch, num_sms, s);
   return cudaErrorInvalidValue;
 }
 
