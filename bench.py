@@ -46,18 +46,18 @@ METRIC = "generating-function points/s (binned P(b) tables/s alongside), FP32+re
 
 def algorithmic_flops(n: int, has_gamma: bool, precision: int) -> float:
     """Per evaluated point.  FP64: complex LU (8/3) n^3 real flops + 8 n^2 for the two
-    triangular solves.  FP32R: FMA-equivalent flops (2 x FP32 pipe instructions) of the
-    algorithm: LU 4 FMA per complex MAC (n^3/3 MACs); residual E by Dot2, 10 pipe
-    instructions per real product, 4 per complex MAC (n^3/3 MACs) plus 12 products per
-    entry for D XA; Z = L^-1 E (n^3/2 MACs) and diag(U^-1 Z) (n^3/6 MACs) at 4 FMA per MAC;
-    refined solve: 4 triangular solves (4 n^2 MAC-FMA... counted as 16 n^2) and the residual
-    by Dot2 (8 n^2 products)."""
+    triangular solves of the exponent.  FP32R: FMA-equivalent flops, i.e. 2 x the FP32 pipe
+    instructions the algorithm needs: LU 4 per complex MAC over n^3/3 MACs; residual
+    E = M - L^U^ by Dot2 at 10 per real product, 4 real products per complex MAC over n^3/3
+    MACs, plus ~30 per entry for the terms of M; Z = L^^-1 E (n^3/2 complex MACs) and
+    diag(U^^-1 Z) (n^3/6) at 4 per MAC; if displaced, four triangular solves (8 n^2) and
+    the solve residual by Dot2 (8 real products per matrix entry, 80 n^2)."""
     n = float(n)
     if precision == 0:
         return (8.0 / 3.0) * n ** 3 + (8.0 * n * n if has_gamma else 0.0)
-    slots = (4.0 / 3.0) * n ** 3 + (40.0 / 3.0) * n ** 3 + 120.0 * n * n + 2.0 * n ** 3 + (2.0 / 3.0) * n ** 3
+    slots = (4.0 / 3.0 + 40.0 / 3.0 + 2.0 + 2.0 / 3.0) * n ** 3 + 30.0 * n * n
     if has_gamma:
-        slots += 16.0 * n * n + 80.0 * n * n
+        slots += 8.0 * n * n + 80.0 * n * n
     return 2.0 * slots
 
 
@@ -170,6 +170,9 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the other workloads (n=192 grid, 256-problem batch, n=200 gradient)")
+    ap.add_argument("--extra-steps", type=int, default=3)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -293,16 +296,91 @@ def main():
         "diagnostics": {"sum_P": d1["sum_P"], "min_pivot_re": d1["min_pivot_re"],
                         "bad_points": d1["n_bad_points"], "fp64_sum_P": results[0]["diag"]["sum_P"]},
     }
+    for p in plans.values():
+        p.close()
+    if not args.no_extras:
+        line["workloads"] = extra_workloads(gb, torch, stream, flush, args.extra_steps, world)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"], errs = cpu_baseline(prob, args.cpu_seconds, tables)
         line["max_abs_err_vs_oracle"] = errs
-    for p in plans.values():
-        p.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def _timed(torch, stream, flush, steps, fn):
+    """Sum of CUDA-event durations of `steps` calls of fn on `stream`, L2 flushed between."""
+    total = 0.0
+    for _ in range(steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        b.synchronize()
+        total += a.elapsed_time(b)
+    return total
+
+
+def extra_workloads(gb, torch, stream, flush, steps, world):
+    """The other workloads, a few steps each: per-table and per-point rates, FP32R next to
+    FP64 where both apply."""
+    out = {}
+    # n = 192: 24 modes x 4 internal, displaced, 3 groups, 9261 points
+    prob = synth.config(2)
+    res = {}
+    for name, prec in (("fp32_refine", 1), ("fp64", 0)):
+        with gb.Plan(prob, precision=prec, want_timing=True) as p:
+            t = torch.empty(p.shape, dtype=torch.float64, device="cuda")
+            gb.gbsbin_execute(p.handle, t, stream)
+            ms = _timed(torch, stream, flush, steps, lambda: gb.gbsbin_execute(p.handle, t, stream))
+            st, d = p.diagnostics(stream)
+            res[name] = {"ms_per_table": ms / steps, "points_per_s": world * prob.n_points * steps / (ms * 1e-3),
+                         "point_kernel_ms": d["point_kernel_ms"], "kernel": d["kernel_name"]}
+    out["M24_K4_L3_N20_n192_9261pts"] = res
+    # 256 uneven problems, one persistent launch per kernel class, autotuned, graph replay
+    probs = synth.batch_config()
+    npts = sum(p.n_points for p in probs)
+    res = {}
+    for name, prec in (("fp32_refine", 1), ("fp64", 0)):
+        with gb.Batch(probs, precision=prec, autotune=True) as b:
+            b.execute(stream)
+            s2 = torch.cuda.Stream()
+            torch.cuda.synchronize()
+            b.capture(s2)
+            b.replay(s2)
+            s2.synchronize()
+            ms = _timed(torch, s2, flush, steps, lambda: b.replay(s2))
+            res[name] = {"ms_per_batch": ms / steps, "tables_per_s": world * len(probs) * steps / (ms * 1e-3),
+                         "points_per_s": world * npts * steps / (ms * 1e-3)}
+    out["batch256_uneven"] = {"problems": len(probs), "grid_points": npts, **res}
+    # n = 200: 100 modes, 2 groups of 50, 81 x 81 grid; NLL of a count table, forward + gradient
+    prob = synth.config(4)
+    with gb.Plan(prob, precision=0, want_backward=True) as p:
+        t = torch.empty(p.shape, dtype=torch.float64, device="cuda")
+        gb.gbsbin_execute(p.handle, t, stream)
+        torch.cuda.synchronize()
+        rng = np.random.default_rng(0)
+        Pn = np.clip(t.cpu().numpy(), 1e-300, None)
+        counts = torch.from_numpy(rng.multinomial(10 ** 6, (Pn / Pn.sum()).reshape(-1)).reshape(Pn.shape)
+                                  .astype(np.float64)).cuda()
+
+        def step():
+            gb.gbsbin_execute(p.handle, t, stream)
+            dLdP = -counts / t
+            p.backward(dLdP, stream, want=("r", "T"))
+        step()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            step()
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        out["M100_K1_L2_N80_n200_gradient"] = {"ms_per_forward_backward": dt / steps * 1e3,
+                                               "points_per_s": world * prob.n_points * steps / dt,
+                                               "precision": "fp64", "timer": "wall clock (backward syncs)"}
+    return out
 
 
 def _kernel_hash():
