@@ -71,7 +71,7 @@ int validate_shape(const gbsbin_problem* p, const gbsbin_options* o) {
   if (!p->sigma1 && (!p->r || !p->T)) return GBSBIN_ERR_ARG;
   if (o->precision != GBSBIN_FP64 && o->precision != GBSBIN_FP32_REFINE) return GBSBIN_ERR_ARG;
   if (o->oversample < 1) return GBSBIN_ERR_ARG;
-  if (o->tile_override < 0 || o->tile_override > GBSBIN_KERNEL_WARP_FP32R) return GBSBIN_ERR_ARG;
+  if (o->tile_override < 0 || o->tile_override > GBSBIN_KERNEL_BLK_FP32R) return GBSBIN_ERR_ARG;
   long long n = 2LL * p->M * p->K;
   if (n > GBSBIN_MAX_N) return GBSBIN_ERR_UNSUPPORTED;
   std::vector<int> count(p->L, 0);
@@ -411,6 +411,7 @@ int evaluate_fp64_with_factors(gbsbin_plan* P, cudaStream_t s) {
 int choose_kernel(int n, int L, int precision, int override_id) {
   if (override_id) return override_id;
   if (precision == GBSBIN_FP32_REFINE && n <= 32) return GBSBIN_KERNEL_WARP_FP32R;
+  if (precision == GBSBIN_FP32_REFINE && n > GBSBIN_SMEM_MAX_N && n <= GBSBIN_BLK_MAX_N) return GBSBIN_KERNEL_BLK_FP32R;
   if (precision == GBSBIN_FP64)
     return points_per_cta(GBSBIN_KERNEL_SMEM_FP64, n, L) > 0 ? GBSBIN_KERNEL_SMEM_FP64 : GBSBIN_KERNEL_GMEM_FP64;
   return points_per_cta(GBSBIN_KERNEL_SMEM_FP32R, n, L) > 0 ? GBSBIN_KERNEL_SMEM_FP32R : GBSBIN_KERNEL_GMEM_FP32R;
@@ -496,7 +497,9 @@ static int plan_create_impl(const gbsbin_problem* p, const gbsbin_options* o, gb
   }
   record_inputs(P, p);
   P->kernel = choose_kernel(n, p->L, opt.precision, opt.tile_override);
-  P->P = P->kernel == GBSBIN_KERNEL_WARP_FP32R ? (n <= 32 ? 1 : 0) : points_per_cta(P->kernel, n, p->L);
+  P->P = P->kernel == GBSBIN_KERNEL_WARP_FP32R ? (n <= 32 ? 1 : 0)
+         : P->kernel == GBSBIN_KERNEL_BLK_FP32R ? (n <= GBSBIN_BLK_MAX_N ? 1 : 0)
+                                                 : points_per_cta(P->kernel, n, p->L);
   if (p_override > 0 && P->P > 0 && (P->kernel == GBSBIN_KERNEL_SMEM_FP64 || P->kernel == GBSBIN_KERNEL_SMEM_FP32R)) {
     if (points_smem_bytes(P->kernel, n, p_override, p->L) > 225 * 1024) {
       delete P;
@@ -534,8 +537,10 @@ static int plan_create_impl(const gbsbin_problem* p, const gbsbin_options* o, gb
     delete P;
     return st;
   }
-  if (alloc_gws && (P->kernel == GBSBIN_KERNEL_GMEM_FP64 || P->kernel == GBSBIN_KERNEL_GMEM_FP32R)) {
-    P->gws_slot_bytes = (long long)points_matrix_bytes(P->kernel, n, P->P);
+  if (alloc_gws && (P->kernel == GBSBIN_KERNEL_GMEM_FP64 || P->kernel == GBSBIN_KERNEL_GMEM_FP32R ||
+                    P->kernel == GBSBIN_KERNEL_BLK_FP32R)) {
+    P->gws_slot_bytes = (long long)points_matrix_bytes(
+        P->kernel == GBSBIN_KERNEL_BLK_FP32R ? GBSBIN_KERNEL_GMEM_FP32R : P->kernel, n, P->P);
     P->gws_slot_bytes = (P->gws_slot_bytes + 255) / 256 * 256;
     size_t bytes = (size_t)P->gws_slot_bytes * (size_t)P->num_sms;
     cudaError_t e = cudaMalloc(&P->d_gws, bytes);
@@ -686,8 +691,9 @@ int gbsbin_execute(gbsbin_plan* P, double* P_out, void* stream) {
   PointArgs a = make_point_args(P);
   P->saved_valid = a.lu_store != nullptr;
   if (P->ev0 && cudaEventRecord(P->ev0, s) != cudaSuccess) return GBSBIN_ERR_CUDA;
-  cudaError_t e = P->kernel == GBSBIN_KERNEL_WARP_FP32R ? launch_points_warp(a, P->num_sms, s)
-                                                        : launch_points(a, P->kernel, P->num_sms, s);
+  cudaError_t e = P->kernel == GBSBIN_KERNEL_WARP_FP32R  ? launch_points_warp(a, P->num_sms, s)
+                  : P->kernel == GBSBIN_KERNEL_BLK_FP32R ? launch_points_blk(a, PointBatch{}, 0, P->num_sms, s)
+                                                         : launch_points(a, P->kernel, P->num_sms, s);
   if (e != cudaSuccess) return GBSBIN_ERR_CUDA;
   if (P->ev1 && cudaEventRecord(P->ev1, s) != cudaSuccess) return GBSBIN_ERR_CUDA;
   e = launch_dft(make_dft_args(P, P_out), s);
@@ -970,6 +976,7 @@ int tune_size(int n, int precision, TuneVal* best) {
   const int gmem_k = precision == GBSBIN_FP64 ? GBSBIN_KERNEL_GMEM_FP64 : GBSBIN_KERNEL_GMEM_FP32R;
   for (int Pc = 1; Pc <= 8; Pc *= 2)
     if (points_smem_bytes(smem_k, n, Pc, 1) <= 225 * 1024) cands.push_back({smem_k, Pc});
+  if (precision == GBSBIN_FP32_REFINE && n > 32 && n <= GBSBIN_BLK_MAX_N) cands.push_back({GBSBIN_KERNEL_BLK_FP32R, 1});
   cands.push_back({gmem_k, 1});
   best->us_per_point = 1e300;
   best->kernel = 0;
@@ -990,8 +997,9 @@ int tune_size(int n, int precision, TuneVal* best) {
     float best_ms = 1e30f;
     for (int rep = 0; rep < 3; ++rep) {
       cudaEventRecord(e0, 0);
-      cudaError_t err = P->kernel == GBSBIN_KERNEL_WARP_FP32R ? launch_points_warp(a, P->num_sms, 0)
-                                                              : launch_points(a, P->kernel, P->num_sms, 0);
+      cudaError_t err = P->kernel == GBSBIN_KERNEL_WARP_FP32R  ? launch_points_warp(a, P->num_sms, 0)
+                        : P->kernel == GBSBIN_KERNEL_BLK_FP32R ? launch_points_blk(a, PointBatch{}, 0, P->num_sms, 0)
+                                                               : launch_points(a, P->kernel, P->num_sms, 0);
       cudaEventRecord(e1, 0);
       if (err != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
         status = GBSBIN_ERR_CUDA;
@@ -1076,9 +1084,9 @@ int batch_launch(gbsbin_batch* B, double* const* P_out, cudaStream_t s) {
     if (C.jobs.empty()) continue;
     if (cudaMemsetAsync(B->d_queue + c, 0, sizeof(unsigned long long), s) != cudaSuccess) return GBSBIN_ERR_CUDA;
     PointBatch pb{B->d_probs, C.d_jobs, (long long)C.jobs.size(), B->d_queue + c};
-    cudaError_t e = C.kernel == GBSBIN_KERNEL_WARP_FP32R
-                        ? launch_points_warp_batch(pb, C.np, B->num_sms, s)
-                        : launch_points_batch(pb, C.kernel, C.threads, C.smem, B->num_sms, s);
+    cudaError_t e = C.kernel == GBSBIN_KERNEL_WARP_FP32R  ? launch_points_warp_batch(pb, C.np, B->num_sms, s)
+                    : C.kernel == GBSBIN_KERNEL_BLK_FP32R ? launch_points_blk(PointArgs{}, pb, C.smem, B->num_sms, s)
+                                                          : launch_points_batch(pb, C.kernel, C.threads, C.smem, B->num_sms, s);
     if (e != cudaSuccess) return GBSBIN_ERR_CUDA;
   }
   for (size_t i = 0; i < B->plans.size(); ++i) {
@@ -1146,7 +1154,9 @@ int gbsbin_batch_create(const gbsbin_problem* probs, int nprob, const gbsbin_opt
     }
     gbsbin_plan* P = B->plans[i];
     args[i] = make_point_args(P);
-    const int threads = P->kernel == GBSBIN_KERNEL_WARP_FP32R ? 128 : points_threads(P->kernel, P->n);
+    const int threads = P->kernel == GBSBIN_KERNEL_WARP_FP32R ? 128
+                        : P->kernel == GBSBIN_KERNEL_BLK_FP32R ? 256
+                                                               : points_threads(P->kernel, P->n);
     const int np = P->kernel == GBSBIN_KERNEL_WARP_FP32R ? (P->n <= 8 ? 8 : P->n <= 16 ? 16 : 32) : 0;
     auto key = std::make_tuple(P->kernel, threads, np);
     if (!class_of.count(key)) {
@@ -1162,8 +1172,13 @@ int gbsbin_batch_create(const gbsbin_problem* probs, int nprob, const gbsbin_opt
     if (P->kernel == GBSBIN_KERNEL_SMEM_FP64 || P->kernel == GBSBIN_KERNEL_SMEM_FP32R ||
         P->kernel == GBSBIN_KERNEL_GMEM_FP64 || P->kernel == GBSBIN_KERNEL_GMEM_FP32R)
       C.smem = std::max(C.smem, points_smem_bytes(P->kernel, P->n, P->P, P->L));
-    if (P->kernel == GBSBIN_KERNEL_GMEM_FP64 || P->kernel == GBSBIN_KERNEL_GMEM_FP32R)
-      B->gws_slot = std::max(B->gws_slot, ((long long)points_matrix_bytes(P->kernel, P->n, 1) + 255) / 256 * 256);
+    if (P->kernel == GBSBIN_KERNEL_BLK_FP32R) C.smem = std::max(C.smem, points_blk_smem_bytes(P->n));
+    if (P->kernel == GBSBIN_KERNEL_GMEM_FP64 || P->kernel == GBSBIN_KERNEL_GMEM_FP32R ||
+        P->kernel == GBSBIN_KERNEL_BLK_FP32R)
+      B->gws_slot = std::max(
+          B->gws_slot,
+          ((long long)points_matrix_bytes(P->kernel == GBSBIN_KERNEL_BLK_FP32R ? GBSBIN_KERNEL_GMEM_FP32R : P->kernel,
+                                          P->n, 1) + 255) / 256 * 256);
   }
   if (B->gws_slot > 0) {
     if (cudaMalloc(&B->d_gws, (size_t)B->gws_slot * B->num_sms) != cudaSuccess) {

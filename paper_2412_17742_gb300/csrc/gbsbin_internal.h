@@ -104,6 +104,11 @@ cudaError_t launch_points_warp(const PointArgs& a, int num_sms, cudaStream_t s);
 cudaError_t launch_points_batch(const PointBatch& batch, int kernel, int threads, size_t smem, int num_sms,
                                 cudaStream_t s);
 cudaError_t launch_points_warp_batch(const PointBatch& batch, int np, int num_sms, cudaStream_t s);
+// Blocked large-n FP32 + refinement kernel (gbsbin_points_blk.cu); n <= GBSBIN_BLK_MAX_N.
+#define GBSBIN_BLK_MAX_N 384
+size_t points_blk_smem_bytes(int n);
+cudaError_t launch_points_blk(const PointArgs& a, const PointBatch& batch, size_t smem_batch, int num_sms,
+                              cudaStream_t s);
 size_t points_smem_bytes(int kernel, int n, int P, int L);
 size_t points_matrix_bytes(int kernel, int n, int P);
 int points_per_cta(int kernel, int n, int L);

@@ -93,10 +93,10 @@ def test_oversampled_table_is_unfolded(cuda_lib, precision):
 
 @pytest.mark.parametrize("precision", PRECISIONS)
 def test_global_workspace_kernel_matches(cuda_lib, precision):
-    # n = 120 > shared-memory limit: the L2-resident workspace variant runs by default
+    # n = 120 > shared-memory limit: the L2-resident workspace variants run by default
     prob = synth.random_problem(np.random.default_rng(111), 60, 1, 2, [4, 3], displaced=True)
     P, st, d, lq, mp = gpu_table(cuda_lib, prob, precision)
-    assert d["kernel_name"].startswith("gmem")
+    assert d["kernel_name"] == ("gmem_fp64" if precision == 0 else "blk_fp32r")
     ref, _ = oracle_table(prob)
     assert np.abs(P - ref).max() <= TOL[precision]
     # forcing the workspace variant on a small problem gives the shared-memory result
@@ -108,7 +108,7 @@ def test_global_workspace_kernel_matches(cuda_lib, precision):
     assert np.abs(Pf - Ps).max() < 1e-13
 
 
-@pytest.mark.parametrize("kernel", [2, 4, 5])
+@pytest.mark.parametrize("kernel", [2, 4, 5, 6])
 def test_fp32r_kernel_variants_agree(cuda_lib, kernel):
     # every FP32 + refinement variant (CTA/shared memory, CTA/workspace, warp/registers)
     # meets the bound on the same small problems
@@ -119,6 +119,22 @@ def test_fp32r_kernel_variants_agree(cuda_lib, kernel):
         ref, _ = oracle_table(prob)
         assert d["kernel"] == kernel
         assert np.abs(P - ref).max() <= TOL[1]
+
+
+@pytest.mark.parametrize("M,K,displaced", [(17, 1, True), (32, 1, False), (49, 1, True), (48, 3, True),
+                                           (192, 1, True)])
+def test_blocked_kernel_sizes(cuda_lib, M, K, displaced):
+    # the blocked kernel (32-wide panels, 64 x 64 residual blocks) at n = 34 (one panel and a
+    # 2-row tail), 64 (exact panels), 98 (ragged panel and residual block), 288 (largest n
+    # of the batched workload, internal modes) and 384 (its largest supported n)
+    rng = np.random.default_rng(140 + M + K)
+    prob = synth.random_problem(rng, M, K, 2, [2, 1], displaced=displaced, internal_basis=K > 1)
+    P, st, d, lq, mp = gpu_table(cuda_lib, prob, 1, tile_override=6)
+    assert st == 0 and d["kernel_name"] == "blk_fp32r" and d["n_bad_points"] == 0
+    ref, res = oracle_table(prob)
+    assert np.abs(P - ref).max() <= TOL[1]
+    dig = cuda_lib.evaluated_point_digits(prob.cutoff)
+    assert np.abs(lq - res["logq"][_flat_index(dig, prob.radix)]).max() < LOGQ_TOL[1]
 
 
 def test_precisions_agree_and_repeatable(cuda_lib):
