@@ -172,6 +172,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the other workloads (n=192 grid, 256-problem batch, n=200 gradient)")
+    ap.add_argument("--extras", default="n192,batch,n200",
+                    help="comma list of the other workloads to time: n192, batch, n200")
     ap.add_argument("--extra-steps", type=int, default=3)
     args = ap.parse_args()
     if args.impl == "reference":
@@ -199,7 +201,8 @@ def main():
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     launches_per_step = 1 + 1 + (prob.L - 1) + 1 + 1   # points, normalise, L-1 axes, last axis, diag
 
-    peaks_meas = {"fp64_tflops": gb.gbsbin_alu_peak(0, SMS * 8), "fp32_tflops": gb.gbsbin_alu_peak(1, SMS * 8)}
+    peaks_meas = {"fp64_tflops": gb.gbsbin_alu_peak(0, SMS * 8), "fp32_tflops": gb.gbsbin_alu_peak(1, SMS * 8),
+                  "int64_mad_wide_tops": gb.gbsbin_alu_peak(2, SMS * 8)}
 
     for p in plans:
         for _ in range(args.warmup):
@@ -238,7 +241,7 @@ def main():
     host_out = torch.empty(plans[1].shape, dtype=torch.float64).pin_memory()
     args_prob = gb.ProblemArgs(prob)
     n = prob.n
-    h2d = n * n * (16 + 8 + 8) + n * (16 + 16 + 4 * 8)
+    h2d = n * n * (16 + 8 + 8 + 16) + n * (16 + 16 + 4 * 8)
     d2h = int(np.prod(plans[1].shape)) * 8
     for _ in range(3):
         gb.gbsbin_plan_set_state(plans[1].handle, args_prob, stream)
@@ -299,7 +302,8 @@ def main():
     for p in plans.values():
         p.close()
     if not args.no_extras:
-        line["workloads"] = extra_workloads(gb, torch, stream, flush, args.extra_steps, world)
+        which = {w.strip() for w in args.extras.split(",") if w.strip()}
+        line["workloads"] = extra_workloads(gb, torch, stream, flush, args.extra_steps, world, which)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"], errs = cpu_baseline(prob, args.cpu_seconds, tables)
         line["max_abs_err_vs_oracle"] = errs
@@ -324,9 +328,20 @@ def _timed(torch, stream, flush, steps, fn):
     return total
 
 
-def extra_workloads(gb, torch, stream, flush, steps, world):
+def extra_workloads(gb, torch, stream, flush, steps, world, which=("n192", "batch", "n200")):
     """The other workloads, a few steps each: per-table and per-point rates, FP32R next to
     FP64 where both apply."""
+    out = {}
+    if "n192" in which:
+        out.update(_extra_n192(gb, torch, stream, flush, steps, world))
+    if "batch" in which:
+        out.update(_extra_batch(gb, torch, stream, flush, steps, world))
+    if "n200" in which:
+        out.update(_extra_n200(gb, torch, stream, flush, steps, world))
+    return out
+
+
+def _extra_n192(gb, torch, stream, flush, steps, world):
     out = {}
     # n = 192: 24 modes x 4 internal, displaced, 3 groups, 9261 points
     prob = synth.config(2)
@@ -340,6 +355,11 @@ def extra_workloads(gb, torch, stream, flush, steps, world):
             res[name] = {"ms_per_table": ms / steps, "points_per_s": world * prob.n_points * steps / (ms * 1e-3),
                          "point_kernel_ms": d["point_kernel_ms"], "kernel": d["kernel_name"]}
     out["M24_K4_L3_N20_n192_9261pts"] = res
+    return out
+
+
+def _extra_batch(gb, torch, stream, flush, steps, world):
+    out = {}
     # 256 uneven problems, one persistent launch per kernel class, autotuned, graph replay
     probs = synth.batch_config()
     npts = sum(p.n_points for p in probs)
@@ -356,6 +376,11 @@ def extra_workloads(gb, torch, stream, flush, steps, world):
             res[name] = {"ms_per_batch": ms / steps, "tables_per_s": world * len(probs) * steps / (ms * 1e-3),
                          "points_per_s": world * npts * steps / (ms * 1e-3)}
     out["batch256_uneven"] = {"problems": len(probs), "grid_points": npts, **res}
+    return out
+
+
+def _extra_n200(gb, torch, stream, flush, steps, world):
+    out = {}
     # n = 200: 100 modes, 2 groups of 50, 81 x 81 grid; NLL of a count table, forward + gradient
     prob = synth.config(4)
     with gb.Plan(prob, precision=0, want_backward=True) as p:

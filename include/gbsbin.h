@@ -288,9 +288,11 @@ const char* gbsbin_strerror(int status);
 
 /*
  * Measurement utility (no counterpart in the paper): device throughput of dependent
- * fused multiply-add chains in FP64 (precision = GBSBIN_FP64) or FP32 (otherwise), in
- * TFLOP/s (2 flops per FMA), from one launch of `blocks` x 256 threads.  Synchronous.
+ * multiply-add chains in FP64 (precision = GBSBIN_FP64), 32 x 32 -> 64-bit integer
+ * (precision = GBSBIN_ALU_INT64, PTX mad.wide.s32) or FP32 (otherwise), in tera-ops/s
+ * (2 per multiply-add), from one launch of `blocks` x 256 threads.  Synchronous.
  */
+#define GBSBIN_ALU_INT64 2
 int gbsbin_alu_peak(int precision, int blocks, double* tflops, void* stream);
 
 #ifdef __cplusplus

@@ -32,6 +32,7 @@ struct gbsbin_plan {
   double2 *d_NXA = nullptr, *d_gamma = nullptr, *d_Xgamma = nullptr;
   float2 *d_NXA_hi = nullptr, *d_NXA_lo = nullptr, *d_Xg_hi = nullptr, *d_Xg_lo = nullptr;
   float2 *d_g_hi = nullptr, *d_g_lo = nullptr;
+  longlong2* d_NXA_fix = nullptr;
   int* d_label = nullptr;
   double2* d_logq = nullptr;
   double* d_minpiv = nullptr;
@@ -239,7 +240,8 @@ int build_state(const gbsbin_problem* p, int n, std::vector<cd>& XA, std::vector
 void free_device(gbsbin_plan* P) {
   void* ptrs[] = {P->d_NXA,  P->d_gamma, P->d_Xgamma, P->d_NXA_hi, P->d_NXA_lo, P->d_Xg_hi,
                   P->d_Xg_lo, P->d_g_hi, P->d_g_lo,   P->d_label, P->d_logq,  P->d_minpiv,
-                  P->d_bufA, P->d_bufB,  P->d_tw,     P->d_diag,  P->d_gws,   P->d_table};
+                  P->d_bufA, P->d_bufB,  P->d_tw,     P->d_diag,  P->d_gws,   P->d_table,
+                  P->d_NXA_fix};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (P->h_stage) cudaFreeHost(P->h_stage);
@@ -263,7 +265,7 @@ int dalloc(T** p, size_t count) {
 
 // Layout of the pinned staging buffer for one state upload.
 struct Stage {
-  size_t off_XA, off_g, off_Xg, off_XAhi, off_XAlo, off_Xghi, off_Xglo, off_ghi, off_glo, total;
+  size_t off_XA, off_g, off_Xg, off_XAhi, off_XAlo, off_Xghi, off_Xglo, off_ghi, off_glo, off_XAfix, total;
 };
 Stage stage_layout(int n) {
   Stage s{};
@@ -277,6 +279,7 @@ Stage stage_layout(int n) {
   s.off_Xglo = o; o += n * sizeof(float2);
   s.off_ghi = o;  o += n * sizeof(float2);
   s.off_glo = o;  o += n * sizeof(float2);
+  s.off_XAfix = o; o += nn * sizeof(longlong2);
   s.total = o;
   return s;
 }
@@ -304,9 +307,13 @@ int upload_state(gbsbin_plan* P, cudaStream_t stream) {
   float2* Xglo = (float2*)(h + s.off_Xglo);
   float2* ghi = (float2*)(h + s.off_ghi);
   float2* glo = (float2*)(h + s.off_glo);
+  longlong2* XAfix = (longlong2*)(h + s.off_XAfix);
   for (size_t q = 0; q < (size_t)n * n; ++q) {  // the kernels use -XA
     XA[q] = make_double2(-P->XA[q].real(), -P->XA[q].imag());
     split(-P->XA[q], &XAhi[q], &XAlo[q]);
+    // |XA_ij| <= ||XA||_2 < 1 for a physical state, so the scaled value fits in 63 bits
+    XAfix[q] = make_longlong2(std::llrint(std::ldexp(-P->XA[q].real(), GBSBIN_FIX_BITS)),
+                              std::llrint(std::ldexp(-P->XA[q].imag(), GBSBIN_FIX_BITS)));
   }
   for (int i = 0; i < n; ++i) {
     g[i] = make_double2(P->gamma[i].real(), P->gamma[i].imag());
@@ -322,7 +329,7 @@ int upload_state(gbsbin_plan* P, cudaStream_t stream) {
       {P->d_Xgamma, s.off_Xg, n * sizeof(double2)},           {P->d_NXA_hi, s.off_XAhi, (size_t)n * n * sizeof(float2)},
       {P->d_NXA_lo, s.off_XAlo, (size_t)n * n * sizeof(float2)}, {P->d_Xg_hi, s.off_Xghi, n * sizeof(float2)},
       {P->d_Xg_lo, s.off_Xglo, n * sizeof(float2)},           {P->d_g_hi, s.off_ghi, n * sizeof(float2)},
-      {P->d_g_lo, s.off_glo, n * sizeof(float2)},
+      {P->d_g_lo, s.off_glo, n * sizeof(float2)},             {P->d_NXA_fix, s.off_XAfix, (size_t)n * n * sizeof(longlong2)},
   };
   for (auto& c : cp) {
     e = cudaMemcpyAsync(c.dst, h + c.off, c.bytes, cudaMemcpyHostToDevice, stream);
@@ -389,6 +396,7 @@ int evaluate_fp64_with_factors(gbsbin_plan* P, cudaStream_t s) {
   a.gamma = P->d_gamma;
   a.NXA_hi = P->d_NXA_hi;
   a.NXA_lo = P->d_NXA_lo;
+  a.NXA_fix = P->d_NXA_fix;
   a.Xg_hi = P->d_Xg_hi;
   a.Xg_lo = P->d_Xg_lo;
   a.g_hi = P->d_g_hi;
@@ -521,6 +529,7 @@ static int plan_create_impl(const gbsbin_problem* p, const gbsbin_options* o, gb
   Stage sl = stage_layout(n);
   if ((st = dalloc(&P->d_NXA, nn)) || (st = dalloc(&P->d_gamma, n)) || (st = dalloc(&P->d_Xgamma, n)) ||
       (st = dalloc(&P->d_NXA_hi, nn)) || (st = dalloc(&P->d_NXA_lo, nn)) || (st = dalloc(&P->d_Xg_hi, n)) ||
+      (st = dalloc(&P->d_NXA_fix, nn)) ||
       (st = dalloc(&P->d_Xg_lo, n)) || (st = dalloc(&P->d_g_hi, n)) || (st = dalloc(&P->d_g_lo, n)) ||
       (st = dalloc(&P->d_label, n)) || (st = dalloc(&P->d_logq, g.n_eval)) ||
       (st = dalloc(&P->d_minpiv, g.n_eval)) || (st = dalloc(&P->d_bufA, g.n_eval)) ||
@@ -539,10 +548,11 @@ static int plan_create_impl(const gbsbin_problem* p, const gbsbin_options* o, gb
   }
   if (alloc_gws && (P->kernel == GBSBIN_KERNEL_GMEM_FP64 || P->kernel == GBSBIN_KERNEL_GMEM_FP32R ||
                     P->kernel == GBSBIN_KERNEL_BLK_FP32R)) {
-    P->gws_slot_bytes = (long long)points_matrix_bytes(
-        P->kernel == GBSBIN_KERNEL_BLK_FP32R ? GBSBIN_KERNEL_GMEM_FP32R : P->kernel, n, P->P);
+    P->gws_slot_bytes = P->kernel == GBSBIN_KERNEL_BLK_FP32R ? (long long)points_blk_slot_bytes(n)
+                                                             : (long long)points_matrix_bytes(P->kernel, n, P->P);
     P->gws_slot_bytes = (P->gws_slot_bytes + 255) / 256 * 256;
-    size_t bytes = (size_t)P->gws_slot_bytes * (size_t)P->num_sms;
+    size_t bytes = (size_t)P->gws_slot_bytes * (size_t)P->num_sms *
+                   (P->kernel == GBSBIN_KERNEL_BLK_FP32R ? GBSBIN_BLK_CTAS_PER_SM : 1);
     cudaError_t e = cudaMalloc(&P->d_gws, bytes);
     if (e != cudaSuccess) {
       cudaGetLastError();
@@ -655,6 +665,7 @@ static PointArgs make_point_args(gbsbin_plan* P) {
   a.gamma = P->d_gamma;
   a.NXA_hi = P->d_NXA_hi;
   a.NXA_lo = P->d_NXA_lo;
+  a.NXA_fix = P->d_NXA_fix;
   a.Xg_hi = P->d_Xg_hi;
   a.Xg_lo = P->d_Xg_lo;
   a.g_hi = P->d_g_hi;
@@ -901,8 +912,8 @@ int gbsbin_alu_peak(int precision, int blocks, double* tflops, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
   float* sink = nullptr;
   if (cudaMalloc(&sink, sizeof(float)) != cudaSuccess) return GBSBIN_ERR_NOMEM;
-  const int fp64 = precision == GBSBIN_FP64;
-  const int iters = fp64 ? 256 : 8192;
+  const int fp64 = precision == GBSBIN_FP64 ? 1 : precision == GBSBIN_ALU_INT64 ? 2 : 0;
+  const int iters = fp64 == 1 ? 256 : fp64 == 2 ? 2048 : 8192;
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
@@ -1175,13 +1186,13 @@ int gbsbin_batch_create(const gbsbin_problem* probs, int nprob, const gbsbin_opt
     if (P->kernel == GBSBIN_KERNEL_BLK_FP32R) C.smem = std::max(C.smem, points_blk_smem_bytes(P->n));
     if (P->kernel == GBSBIN_KERNEL_GMEM_FP64 || P->kernel == GBSBIN_KERNEL_GMEM_FP32R ||
         P->kernel == GBSBIN_KERNEL_BLK_FP32R)
-      B->gws_slot = std::max(
-          B->gws_slot,
-          ((long long)points_matrix_bytes(P->kernel == GBSBIN_KERNEL_BLK_FP32R ? GBSBIN_KERNEL_GMEM_FP32R : P->kernel,
-                                          P->n, 1) + 255) / 256 * 256);
+      B->gws_slot = std::max(B->gws_slot, ((long long)(P->kernel == GBSBIN_KERNEL_BLK_FP32R
+                                                               ? points_blk_slot_bytes(P->n)
+                                                               : points_matrix_bytes(P->kernel, P->n, 1)) + 255) /
+                                              256 * 256);
   }
   if (B->gws_slot > 0) {
-    if (cudaMalloc(&B->d_gws, (size_t)B->gws_slot * B->num_sms) != cudaSuccess) {
+    if (cudaMalloc(&B->d_gws, (size_t)B->gws_slot * B->num_sms * GBSBIN_BLK_CTAS_PER_SM) != cudaSuccess) {
       cudaGetLastError();
       batch_free(B);
       return GBSBIN_ERR_NOMEM;

@@ -12,6 +12,8 @@
 #define GBSBIN_SMEM_MAX_N 112
 // Blocks of the diagnostics reduction; the host finishes the sum over their partials.
 #define GBSBIN_DIAG_BLOCKS 64
+// Fixed-point scale of the integer copy of -XA used by the exact integer residual.
+#define GBSBIN_FIX_BITS 62
 
 namespace gbsbin {
 
@@ -37,6 +39,7 @@ struct PointArgs {
   const double2* gamma;     // n
   const float2* NXA_hi;     // n*n: -XA rounded to FP32
   const float2* NXA_lo;     // n*n: (-XA) - NXA_hi rounded to FP32
+  const longlong2* NXA_fix; // n*n: -XA in fixed point, round(-XA * 2^GBSBIN_FIX_BITS) (|XA_ij| < 1)
   const float2* Xg_hi;      // n
   const float2* Xg_lo;      // n
   const float2* g_hi;       // n
@@ -106,7 +109,9 @@ cudaError_t launch_points_batch(const PointBatch& batch, int kernel, int threads
 cudaError_t launch_points_warp_batch(const PointBatch& batch, int np, int num_sms, cudaStream_t s);
 // Blocked large-n FP32 + refinement kernel (gbsbin_points_blk.cu); n <= GBSBIN_BLK_MAX_N.
 #define GBSBIN_BLK_MAX_N 384
+#define GBSBIN_BLK_CTAS_PER_SM 2
 size_t points_blk_smem_bytes(int n);
+size_t points_blk_slot_bytes(int n);
 cudaError_t launch_points_blk(const PointArgs& a, const PointBatch& batch, size_t smem_batch, int num_sms,
                               cudaStream_t s);
 size_t points_smem_bytes(int kernel, int n, int P, int L);

@@ -584,8 +584,34 @@ __global__ void __launch_bounds__(256) k_fma_chain(float* sink, int iters) {
   if (r == (T)-12345.0) sink[0] = (float)r;  // keeps the chains live
 }
 
+// 32 x 32 -> 64-bit integer multiply-add chains (mad.wide.s32), eight independent per thread.
+__global__ void __launch_bounds__(256) k_imad_wide_chain(float* sink, int iters) {
+  long long x[8];
+  int m[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    x[c] = threadIdx.x + c;
+    m[c] = 1000003 + 2 * c + (int)threadIdx.x;
+  }
+  const int b = 77;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        asm volatile("mad.wide.s32 %0, %1, %2, %0;" : "+l"(x[c]) : "r"(m[c]), "r"(b));
+      }
+  }
+  long long r = 0;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) r += x[c];
+  if (r == -12345) sink[0] = (float)r;
+}
+
 cudaError_t launch_alu_peak(int fp64, int blocks, float* sink, int iters, cudaStream_t s) {
-  if (fp64)
+  if (fp64 == 2)
+    k_imad_wide_chain<<<blocks, 256, 0, s>>>(sink, iters);
+  else if (fp64)
     k_fma_chain<double><<<blocks, 256, 0, s>>>(sink, iters);
   else
     k_fma_chain<float><<<blocks, 256, 0, s>>>(sink, iters);

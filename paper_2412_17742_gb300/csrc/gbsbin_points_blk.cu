@@ -8,7 +8,14 @@
 // shared memory:
 //   LU        right-looking: panel LU in shared memory, U12 = L11^{-1} A12 column by
 //             column, A22 -= L21 U12 as a tiled rank-32 update;
-//   residual  E = M - L^U^ by Dot2 over 64 x 64 output blocks, L/U chunks staged;
+//   rounding  each row of L^ and each column of U^ is rounded onto a 24-bit fixed-point
+//             grid (scale 2^(24 - e) with |entries| < 2^e), which moves an entry by at most
+//             the FP32 rounding of the largest one; the LU in use from here on is the rounded
+//             one, exactly representable both as FP32 and as int32 digits;
+//   residual  E = M - L^U^ exactly: the products of digits are summed in int64 (three
+//             32 x 32 -> 64-bit multiply-adds per complex term, Karatsuba), M enters as a
+//             fixed-point copy of -XA (2^62 scale) shifted to the entry's scale, and the
+//             difference is rounded to FP32 once; 64 x 64 output blocks, digit chunks staged;
 //   trace     Z = L^^{-1} E (blocked forward substitution on all columns) and the entries
 //             X[m][c], m >= c, of X = U^^{-1} Z (blocked back substitution), delta =
 //             sum_c X[c][c];
@@ -25,7 +32,9 @@ namespace {
 constexpr int NT = 256;
 constexpr int NB = 32;                  // panel width
 constexpr int LDP = NB + 1;             // leading dimension of staged panels (bank stagger)
-constexpr int EB = 64;                  // residual output block
+constexpr int EB = 64;                  // residual output block rows
+constexpr int EBJ = 32;                 // residual output block columns
+constexpr int CTAS_PER_SM = GBSBIN_BLK_CTAS_PER_SM;   // resident CTAs per SM where shared memory allows
 
 // shared-memory plan (float2 units): panel [n x LDP], row block [NB x (n + 1)], vectors
 struct BlkSmem {
@@ -37,7 +46,11 @@ struct BlkSmem {
   float2* xv;      // n
   float2* rv;      // n
   double2* red;    // NT / 32
+  double2* red2;   // NT / 32
   int* lab;        // n
+  int* erow;       // n: exponent bound of row i of L^ (|L^_ik| < 2^erow[i])
+  int* fcol;       // n: exponent bound of column j of U^
+  int* bad;        // 1: a factor fell outside the fixed-point range
 };
 
 __device__ __forceinline__ BlkSmem carve(unsigned char* smem, int n, int L) {
@@ -58,7 +71,11 @@ __device__ __forceinline__ BlkSmem carve(unsigned char* smem, int n, int L) {
   uintptr_t p = ((uintptr_t)f + 15) & ~(uintptr_t)15;
   s.w = (double2*)p;
   s.red = s.w + GBSBIN_MAX_L;
-  s.lab = (int*)(s.red + NT / 32);
+  s.red2 = s.red + NT / 32;
+  s.lab = (int*)(s.red2 + NT / 32);
+  s.erow = s.lab + n;
+  s.fcol = s.erow + n;
+  s.bad = s.fcol + n;
   return s;
 }
 
@@ -108,6 +125,68 @@ __device__ __forceinline__ void tile_update(float2* C, int ldc, int r0, int c0, 
 struct NoMask {
   __device__ bool operator()(int, int) const { return true; }
 };
+
+// 2^s as FP32 for -126 <= s <= 127.
+__device__ __forceinline__ float pow2f(int s) { return __int_as_float((127 + s) << 23); }
+
+// Smallest e with m < 2^e for finite m > 0 (-126 for m = 0 or subnormal, 129 for inf/NaN).
+__device__ __forceinline__ int exponent_bound(float m) { return ((__float_as_int(m) >> 23) & 0xff) - 126; }
+
+// v <- U^^{-1} L^^{-1} v for one right-hand side v (shared memory, n entries), with L\U
+// in global memory (unit lower L) and pinv[k] = 1 / u_kk, by the whole CTA: per 32-row
+// block, warp 0 solves the diagonal block with shuffles and all threads apply the
+// off-diagonal rows.  Ends with __syncthreads().
+__device__ __forceinline__ void cta_solve_lu(const float2* A, int n, const float2* pinv, float2* v) {
+  const int tid = threadIdx.x, lane = tid & 31;
+  for (int k0 = 0; k0 < n; k0 += NB) {           // forward: L y = v
+    const int nb = min(NB, n - k0);
+    if (tid < 32) {
+      float2 row[NB];
+#pragma unroll
+      for (int q = 0; q < NB; ++q)
+        row[q] = (lane < nb && q < lane) ? A[(size_t)(k0 + lane) * n + k0 + q] : make_float2(0.f, 0.f);
+      float2 vr = lane < nb ? v[k0 + lane] : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int q = 0; q < NB - 1; ++q) {
+        const float2 vq = make_float2(__shfl_sync(0xffffffffu, vr.x, q), __shfl_sync(0xffffffffu, vr.y, q));
+        if (lane > q) vr = cfnmaf(vr, row[q], vq);
+      }
+      if (lane < nb) v[k0 + lane] = vr;
+    }
+    __syncthreads();
+    for (int i = k0 + nb + tid; i < n; i += NT) {
+      float2 acc = v[i];
+      for (int q = 0; q < nb; ++q) acc = cfnmaf(acc, A[(size_t)i * n + k0 + q], v[k0 + q]);
+      v[i] = acc;
+    }
+    __syncthreads();
+  }
+  for (int k0 = ((n - 1) / NB) * NB; k0 >= 0; k0 -= NB) {   // backward: U x = y
+    const int nb = min(NB, n - k0);
+    if (tid < 32) {
+      float2 row[NB];
+#pragma unroll
+      for (int q = 0; q < NB; ++q)
+        row[q] = (lane < nb && q > lane && q < nb) ? A[(size_t)(k0 + lane) * n + k0 + q] : make_float2(0.f, 0.f);
+      float2 vr = lane < nb ? v[k0 + lane] : make_float2(0.f, 0.f);
+      const float2 ip = lane < nb ? pinv[k0 + lane] : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int q = NB - 1; q >= 0; --q) {
+        if (lane == q) vr = cmulf(vr, ip);
+        const float2 xq = make_float2(__shfl_sync(0xffffffffu, vr.x, q), __shfl_sync(0xffffffffu, vr.y, q));
+        if (lane < q) vr = cfnmaf(vr, row[q], xq);
+      }
+      if (lane < nb) v[k0 + lane] = vr;
+    }
+    __syncthreads();
+    for (int i = tid; i < k0; i += NT) {
+      float2 acc = v[i];
+      for (int q = 0; q < nb; ++q) acc = cfnmaf(acc, A[(size_t)i * n + k0 + q], v[k0 + q]);
+      v[i] = acc;
+    }
+    __syncthreads();
+  }
+}
 
 }  // namespace
 
@@ -181,88 +260,143 @@ __device__ void group_fp32r_blk(const PointArgs& a, const long long e, unsigned 
     __syncthreads();
   }
 
-  // ------------------------------------------- residual E = M - L^U^ by Dot2
-  // (uses panel / rowb as the L and U chunk stages: L chunk EB x NB, U chunk NB x EB)
-  const int nblk = (n + EB - 1) / EB;
-  for (int bi = 0; bi < nblk; ++bi)
-    for (int bj = 0; bj < nblk; ++bj) {
-      const int i0 = bi * EB, j0 = bj * EB;
-      const int ni = min(EB, n - i0), nj = min(EB, n - j0);
-      // this thread's 4 x 4 entries of the 64 x 64 block: rows ti .. ti+3, columns tj + 16 q
-      const int ti = (tid >> 4) * 4, tj = tid & 15;
-      Acc2 er[4][4], ei[4][4];
-#pragma unroll
-      for (int p = 0; p < 4; ++p)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          er[p][q] = Acc2{0.0f, 0.0f};
-          ei[p][q] = Acc2{0.0f, 0.0f};
-        }
-      const int kmax = min(i0 + ni, j0 + nj);   // terms need k < i and k <= j
-      for (int kc = 0; kc < kmax; kc += NB) {
-        const int kd = min(NB, kmax - kc);
-        __syncthreads();
-        for (int t = tid; t < EB * NB; t += NT) {
-          const int r = t / NB, c = t - r * NB;
-          sm.panel[r * LDP + c] = (r < ni && c < kd) ? A[(size_t)(i0 + r) * n + kc + c] : make_float2(0.f, 0.f);
-          const int rr = t / EB, cc = t - rr * EB;
-          sm.rowb[rr * sm.ldr + cc] = (rr < kd && cc < nj) ? A[(size_t)(kc + rr) * n + j0 + cc] : make_float2(0.f, 0.f);
-        }
-        __syncthreads();
-        for (int k = 0; k < kd; ++k) {
-          const int kg = kc + k;
-          float2 l[4], u[4];
-#pragma unroll
-          for (int p = 0; p < 4; ++p) {
-            const float2 v = sm.panel[(ti + p) * LDP + k];
-            const bool ok = kg < i0 + ti + p;    // k < i: L_ik is a multiplier
-            l[p] = ok ? make_float2(-v.x, v.y) : make_float2(0.f, 0.f);
-          }
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const float2 v = sm.rowb[k * sm.ldr + tj + 16 * q];
-            const bool ok = kg <= j0 + tj + 16 * q;   // k <= j: U_kj is in the upper factor
-            u[q] = ok ? v : make_float2(0.f, 0.f);
-          }
-#pragma unroll
-          for (int p = 0; p < 4; ++p)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              acc2_add_prod(er[p][q], l[p].x, u[q].x);
-              acc2_add_prod(er[p][q], l[p].y, u[q].y);
-              acc2_add_prod(ei[p][q], l[p].x, u[q].y);
-              acc2_add_prod(ei[p][q], -l[p].y, u[q].x);
-            }
-        }
-      }
-#pragma unroll
-      for (int p = 0; p < 4; ++p)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int i = i0 + ti + p, j = j0 + tj + 16 * q;
-          if (ti + p >= ni || tj + 16 * q >= nj) continue;
-          const size_t ij = (size_t)i * n + j;
-          if (i <= j) {                      // L_ii U_ij = U_ij
-            const float2 u = A[ij];
-            acc2_add(er[p][q], -u.x);
-            acc2_add(ei[p][q], -u.y);
-          }
-          const float2 xh = a.NXA_hi[ij], xl = a.NXA_lo[ij];
-          acc2_add(er[p][q], xh.x);
-          acc2_add(er[p][q], xl.x);
-          acc2_add(ei[p][q], xh.y);
-          acc2_add(ei[p][q], xl.y);
-          if (i == j) {
-            const double2 d = sm.w[sm.lab[i]];
-            const float dhx = (float)d.x, dhy = (float)d.y;
-            acc2_add(er[p][q], dhx);
-            acc2_add(er[p][q], (float)(d.x - (double)dhx));
-            acc2_add(ei[p][q], -dhy);
-            acc2_add(ei[p][q], -(float)(d.y - (double)dhy));
-          }
-          E[ij] = make_float2(acc2_value(er[p][q]), acc2_value(ei[p][q]));
-        }
+  // --------------------------------------- rounding of L^ and U^ onto fixed-point grids
+  // The integer digits share memory with E: the residual pass below visits its output
+  // blocks in reverse order, and every digit of block (bi, bj) is read only by blocks
+  // (bi, bj' >= bj) (an L digit) or (bi' >= bi, bj) (a U digit), which come earlier.
+  int2* Q = (int2*)E;
+  if (tid == 0) *sm.bad = 0;
+  for (int i = warp; i < n; i += NT / 32) {      // row bound of L^ (k < i), warp per row
+    float m = 0.0f;
+    for (int k = lane; k < i; k += 32) {
+      const float2 v = A[(size_t)i * n + k];
+      m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
     }
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) {
+      int ex = exponent_bound(m);
+      if (ex < 0) ex = 0;
+      if (ex > 20) {                              // L^ entries this large: not a physical state
+        ex = 20;
+        *sm.bad = 1;
+      }
+      sm.erow[i] = ex;
+    }
+  }
+  for (int j = tid; j < n; j += NT) {             // column bound of U^ (k <= j), thread per column
+    float m = 0.0f;
+    for (int k = 0; k <= j; ++k) {
+      const float2 v = A[(size_t)k * n + j];
+      m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
+    }
+    int ex = exponent_bound(m);
+    if (ex < -14) ex = -14;
+    if (ex > 29) {                                // keeps the shift below 64
+      ex = 29;
+      *sm.bad = 1;
+    }
+    sm.fcol[j] = ex;
+  }
+  __syncthreads();
+  for (int t = tid; t < n * n; t += NT) {
+    const int i = t / n, j = t - i * n;
+    const int sc = 24 - (i > j ? sm.erow[i] : sm.fcol[j]);
+    const float2 v = A[t];
+    const float qx = rintf(v.x * pow2f(sc)), qy = rintf(v.y * pow2f(sc));
+    A[t] = make_float2(qx * pow2f(-sc), qy * pow2f(-sc));
+    Q[t] = make_int2((int)qx, (int)qy);
+  }
+  __syncthreads();
+  for (int k = tid; k < n; k += NT) sm.pinv[k] = crecipf(A[(size_t)k * n + k]);
+
+  // ------------------------------------------- residual E = M - L^U^, exact in int64
+  // (panel / rowb stage the digits: L chunk EB x NB, U chunk NB x EBJ, int2)
+  {
+    int2* Ls = (int2*)sm.panel;
+    int2* Us = (int2*)sm.rowb;
+    const int nbi = (n + EB - 1) / EB, nbj = (n + EBJ - 1) / EBJ;
+    // this thread's 4 x 2 entries of a 64 x 32 block: rows ti .. ti+3, columns tj, tj + 16
+    const int ti = (tid >> 4) * 4, tj = tid & 15;
+    for (int bi = nbi - 1; bi >= 0; --bi)
+      for (int bj = nbj - 1; bj >= 0; --bj) {
+        const int i0 = bi * EB, j0 = bj * EBJ;
+        const int ni = min(EB, n - i0), nj = min(EBJ, n - j0);
+        long long sa[4][2], sb[4][2], sc[4][2];   // sum lr ur, sum li ui, sum (lr+li)(ur+ui)
+#pragma unroll
+        for (int p = 0; p < 4; ++p)
+#pragma unroll
+          for (int q = 0; q < 2; ++q) sa[p][q] = sb[p][q] = sc[p][q] = 0;
+        const int kmax = min(i0 + ni, j0 + nj);   // terms need k < i and k <= j
+        for (int kc = 0; kc < kmax; kc += NB) {
+          const int kd = min(NB, kmax - kc);
+          __syncthreads();
+          for (int t = tid; t < EB * NB; t += NT) {
+            const int r = t / NB, c = t - r * NB;
+            Ls[r * LDP + c] = (r < ni && c < kd) ? Q[(size_t)(i0 + r) * n + kc + c] : make_int2(0, 0);
+          }
+          for (int t = tid; t < NB * EBJ; t += NT) {
+            const int rr = t / EBJ, cc = t - rr * EBJ;
+            Us[rr * sm.ldr + cc] = (rr < kd && cc < nj) ? Q[(size_t)(kc + rr) * n + j0 + cc] : make_int2(0, 0);
+          }
+          __syncthreads();
+#pragma unroll 2
+          for (int k = 0; k < kd; ++k) {
+            const int kg = kc + k;
+            int lx[4], ly[4], ls[4], ux[2], uy[2], us[2];
+#pragma unroll
+            for (int p = 0; p < 4; ++p) {
+              const int2 v = Ls[(ti + p) * LDP + k];
+              const bool ok = kg < i0 + ti + p;    // k < i: L_ik is a multiplier
+              lx[p] = ok ? v.x : 0;
+              ly[p] = ok ? v.y : 0;
+              ls[p] = lx[p] + ly[p];
+            }
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+              const int2 v = Us[k * sm.ldr + tj + 16 * q];
+              const bool ok = kg <= j0 + tj + 16 * q;   // k <= j: U_kj is in the upper factor
+              ux[q] = ok ? v.x : 0;
+              uy[q] = ok ? v.y : 0;
+              us[q] = ux[q] + uy[q];
+            }
+#pragma unroll
+            for (int p = 0; p < 4; ++p)
+#pragma unroll
+              for (int q = 0; q < 2; ++q) {
+                sa[p][q] += (long long)lx[p] * ux[q];
+                sb[p][q] += (long long)ly[p] * uy[q];
+                sc[p][q] += (long long)ls[p] * us[q];
+              }
+          }
+        }
+        // every read of this block's digits by other threads happened in the staging above
+#pragma unroll
+        for (int p = 0; p < 4; ++p)
+#pragma unroll
+          for (int q = 0; q < 2; ++q) {
+            const int i = i0 + ti + p, j = j0 + tj + 16 * q;
+            if (ti + p >= ni || tj + 16 * q >= nj) continue;
+            const size_t ij = (size_t)i * n + j;
+            const int ei = sm.erow[i], fj = sm.fcol[j];
+            const int sh = GBSBIN_FIX_BITS - 48 + ei + fj;   // 2^62 scale -> 2^(48 - ei - fj)
+            const longlong2 mf = a.NXA_fix[ij];
+            long long er = (mf.x >> sh) - (sa[p][q] - sb[p][q]);
+            long long eim = (mf.y >> sh) - (sc[p][q] - sa[p][q] - sb[p][q]);
+            if (i <= j) {                      // L_ii U_ij = U_ij (this thread's own digit)
+              const int2 u = Q[ij];
+              er -= (long long)u.x << (24 - ei);
+              eim -= (long long)u.y << (24 - ei);
+            }
+            if (i == j) {                      // conj(d_i) on the diagonal of M
+              const double2 d = sm.w[sm.lab[i]];
+              er += __double2ll_rn(d.x * 4611686018427387904.0) >> sh;    // 2^62
+              eim -= __double2ll_rn(d.y * 4611686018427387904.0) >> sh;
+            }
+            const float s = pow2f(ei + fj - 48);     // value of one unit of the products
+            E[ij] = make_float2(__ll2float_rn(er) * s, __ll2float_rn(eim) * s);
+          }
+      }
+  }
   __syncthreads();
 
   // ------------------------------------------- Z = L^^{-1} E, all columns, blocked
@@ -353,77 +487,70 @@ __device__ void group_fp32r_blk(const PointArgs& a, const long long e, unsigned 
   __syncthreads();
 
   // ------------------------------------------------------------- FP64 epilogue
+  double2 expo = make_double2(0.0, 0.0);
+  if (a.has_gamma) {                  // x = M^{-1} X gamma with one refinement step
+    float2* x = sm.xv;
+    float2* rr = sm.rv;
+    for (int i = tid; i < n; i += NT) x[i] = a.Xg_hi[i];
+    __syncthreads();
+    cta_solve_lu(A, n, sm.pinv, x);
+    // r = X gamma - M x^ by Dot2, a thread per row
+    for (int i = tid; i < n; i += NT) {
+      Acc2 sr = {0.0f, 0.0f}, si = {0.0f, 0.0f};
+      const float2 gh = a.Xg_hi[i], gl = a.Xg_lo[i];
+      acc2_add(sr, gh.x);
+      acc2_add(sr, gl.x);
+      acc2_add(si, gh.y);
+      acc2_add(si, gl.y);
+      for (int j = 0; j < n; ++j) {
+        const float2 xh = a.NXA_hi[(size_t)i * n + j], xl = a.NXA_lo[(size_t)i * n + j], y = x[j];
+        acc2_add_prod(sr, -xh.x, y.x);
+        acc2_add_prod(sr, xh.y, y.y);
+        acc2_add_prod(sr, -xl.x, y.x);
+        acc2_add_prod(sr, xl.y, y.y);
+        acc2_add_prod(si, -xh.x, y.y);
+        acc2_add_prod(si, -xh.y, y.x);
+        acc2_add_prod(si, -xl.x, y.y);
+        acc2_add_prod(si, -xl.y, y.x);
+      }
+      const double2 d = sm.w[sm.lab[i]];
+      const float dhx = (float)d.x, dhy = (float)d.y;
+      const float dlx = (float)(d.x - (double)dhx), dly = (float)(d.y - (double)dhy);
+      const float2 y = x[i];
+      acc2_add_prod(sr, -dhx, y.x);
+      acc2_add_prod(sr, -dhy, y.y);
+      acc2_add_prod(si, -dhx, y.y);
+      acc2_add_prod(si, dhy, y.x);
+      acc2_add_prod(sr, -dlx, y.x);
+      acc2_add_prod(sr, -dly, y.y);
+      acc2_add_prod(si, -dlx, y.y);
+      acc2_add_prod(si, dly, y.x);
+      rr[i] = make_float2(acc2_value(sr), acc2_value(si));
+    }
+    __syncthreads();
+    cta_solve_lu(A, n, sm.pinv, rr);
+    double sr = 0.0, si = 0.0;
+    for (int i = tid; i < n; i += NT) {
+      const double xr = (double)x[i].x + (double)rr[i].x, xi = (double)x[i].y + (double)rr[i].y;
+      const double gr = (double)a.g_hi[i].x + (double)a.g_lo[i].x, gi = (double)a.g_hi[i].y + (double)a.g_lo[i].y;
+      sr += gr * xr - gi * xi;
+      si += gr * xi + gi * xr;
+    }
+    sr = warp_sum_d(sr);
+    si = warp_sum_d(si);
+    if (lane == 0) sm.red2[warp] = make_double2(sr, si);
+    __syncthreads();
+    if (tid == 0)
+      for (int q = 0; q < NT / 32; ++q) {
+        expo.x += sm.red2[q].x;
+        expo.y += sm.red2[q].y;
+      }
+  }
   if (warp == 0) {
     double2 ld;
     double mn;
     warp_logdet(n, sm.w, sm.lab, [&](int i) { float2 u = A[(size_t)i * n + i]; return make_double2(u.x, u.y); },
                 &ld, &mn);
-    double2 expo = make_double2(0.0, 0.0);
-    if (a.has_gamma) {
-      float2* x = sm.xv;
-      float2* rr = sm.rv;
-      for (int i = lane; i < n; i += 32) x[i] = a.Xg_hi[i];
-      __syncwarp();
-      for (int pass = 0; pass < 2; ++pass) {
-        float2* v = pass == 0 ? x : rr;
-        for (int k = 0; k < n - 1; ++k) {
-          const float2 yk = v[k];
-          __syncwarp();
-          for (int i = k + 1 + lane; i < n; i += 32) v[i] = cfnmaf(v[i], A[(size_t)i * n + k], yk);
-          __syncwarp();
-        }
-        for (int k = n - 1; k >= 0; --k) {
-          const float2 xk = cmulf(v[k], sm.pinv[k]);
-          __syncwarp();
-          if (lane == 0) v[k] = xk;
-          for (int i = lane; i < k; i += 32) v[i] = cfnmaf(v[i], A[(size_t)i * n + k], xk);
-          __syncwarp();
-        }
-        if (pass == 0) {
-          for (int i = lane; i < n; i += 32) {
-            Acc2 sr = {0.0f, 0.0f}, si = {0.0f, 0.0f};
-            const float2 gh = a.Xg_hi[i], gl = a.Xg_lo[i];
-            acc2_add(sr, gh.x);
-            acc2_add(sr, gl.x);
-            acc2_add(si, gh.y);
-            acc2_add(si, gl.y);
-            for (int j = 0; j < n; ++j) {
-              const float2 xh = a.NXA_hi[(size_t)i * n + j], xl = a.NXA_lo[(size_t)i * n + j], y = x[j];
-              acc2_add_prod(sr, -xh.x, y.x);
-              acc2_add_prod(sr, xh.y, y.y);
-              acc2_add_prod(sr, -xl.x, y.x);
-              acc2_add_prod(sr, xl.y, y.y);
-              acc2_add_prod(si, -xh.x, y.y);
-              acc2_add_prod(si, -xh.y, y.x);
-              acc2_add_prod(si, -xl.x, y.y);
-              acc2_add_prod(si, -xl.y, y.x);
-            }
-            const double2 d = sm.w[sm.lab[i]];
-            const float dhx = (float)d.x, dhy = (float)d.y;
-            const float dlx = (float)(d.x - (double)dhx), dly = (float)(d.y - (double)dhy);
-            const float2 y = x[i];
-            acc2_add_prod(sr, -dhx, y.x);
-            acc2_add_prod(sr, -dhy, y.y);
-            acc2_add_prod(si, -dhx, y.y);
-            acc2_add_prod(si, dhy, y.x);
-            acc2_add_prod(sr, -dlx, y.x);
-            acc2_add_prod(sr, -dly, y.y);
-            acc2_add_prod(si, -dlx, y.y);
-            acc2_add_prod(si, dly, y.x);
-            rr[i] = make_float2(acc2_value(sr), acc2_value(si));
-          }
-          __syncwarp();
-        }
-      }
-      double sr = 0.0, si = 0.0;
-      for (int i = lane; i < n; i += 32) {
-        const double xr = (double)x[i].x + (double)rr[i].x, xi = (double)x[i].y + (double)rr[i].y;
-        const double gr = (double)a.g_hi[i].x + (double)a.g_lo[i].x, gi = (double)a.g_hi[i].y + (double)a.g_lo[i].y;
-        sr += gr * xr - gi * xi;
-        si += gr * xi + gi * xr;
-      }
-      expo = make_double2(warp_sum_d(sr), warp_sum_d(si));
-    }
     if (lane == 0) {
       double2 delta = make_double2(0.0, 0.0);
       for (int q = 0; q < NT / 32; ++q) {
@@ -431,13 +558,13 @@ __device__ void group_fp32r_blk(const PointArgs& a, const long long e, unsigned 
         delta.y += sm.red[q].y;
       }
       a.logq[e] = make_double2(0.5 * expo.x - 0.5 * (ld.x + delta.x), 0.5 * expo.y - 0.5 * (ld.y + delta.y));
-      a.minpiv[e] = mn;
+      a.minpiv[e] = *sm.bad ? -1.0e300 : mn;
     }
   }
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(NT) k_points_fp32r_blk(PointArgs a0, PointBatch batch) {
+__global__ void __launch_bounds__(NT, CTAS_PER_SM) k_points_fp32r_blk(PointArgs a0, PointBatch batch) {
   extern __shared__ __align__(16) unsigned char smem[];
   if (!batch.probs) {
     for (long long e = blockIdx.x; e < a0.grid.n_eval; e += gridDim.x) group_fp32r_blk(a0, e, smem);
@@ -462,15 +589,24 @@ __global__ void __launch_bounds__(NT) k_points_fp32r_blk(PointArgs a0, PointBatc
 size_t points_blk_smem_bytes(int n) {
   const size_t R = n > EB ? n : EB;
   return R * LDP * 8 + (size_t)NB * (R + 1) * 8 + (size_t)3 * n * 8 + 16 + (size_t)GBSBIN_MAX_L * 16 +
-         (size_t)(NT / 32) * 16 + (size_t)n * 4 + 16;
+         (size_t)(NT / 32) * 32 + (size_t)3 * n * 4 + 16;
 }
+
+// One CTA's workspace slot: L\U (float2) and the residual (float2; the integer digits of
+// the rounded factors before it), n x n each.  The workspace holds
+// GBSBIN_BLK_CTAS_PER_SM slots per SM.
+size_t points_blk_slot_bytes(int n) { return ((size_t)16 * n * n + 255) / 256 * 256; }
 
 cudaError_t launch_points_blk(const PointArgs& a, const PointBatch& batch, size_t smem_batch, int num_sms,
                               cudaStream_t s) {
   const size_t smem = batch.probs ? smem_batch : points_blk_smem_bytes(a.n);
   cudaError_t err = cudaFuncSetAttribute(k_points_fp32r_blk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
-  long long grid = num_sms;  // one workspace slot per CTA
+  int per_sm = 0;
+  err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_points_fp32r_blk, NT, smem);
+  if (err != cudaSuccess) return err;
+  per_sm = per_sm < 1 ? 1 : per_sm > GBSBIN_BLK_CTAS_PER_SM ? GBSBIN_BLK_CTAS_PER_SM : per_sm;
+  long long grid = (long long)num_sms * per_sm;  // one workspace slot per CTA
   const long long work = batch.probs ? batch.njobs : a.grid.n_eval;
   if (grid > work) grid = work;
   if (grid < 1) grid = 1;
