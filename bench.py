@@ -44,18 +44,26 @@ FP64_FMA_PER_SM_CLK = 2      # 1.25 TFLOP/s nominal / (152 SMs x 2.07 GHz x 2 fl
 METRIC = "generating-function points/s (binned P(b) tables/s alongside), FP32+refine vs FP64"
 
 
-def algorithmic_flops(n: int, has_gamma: bool, precision: int) -> float:
-    """Per evaluated point.  FP64: complex LU (8/3) n^3 real flops + 8 n^2 for the two
-    triangular solves of the exponent.  FP32R: FMA-equivalent flops, i.e. 2 x the FP32 pipe
-    instructions the algorithm needs: LU 4 per complex MAC over n^3/3 MACs; residual
-    E = M - L^U^ by Dot2 at 10 per real product, 4 real products per complex MAC over n^3/3
-    MACs, plus ~30 per entry for the terms of M; Z = L^^-1 E (n^3/2 complex MACs) and
-    diag(U^^-1 Z) (n^3/6) at 4 per MAC; if displaced, four triangular solves (8 n^2) and
-    the solve residual by Dot2 (8 real products per matrix entry, 80 n^2)."""
+def algorithmic_flops(n: int, has_gamma: bool) -> float:
+    """Per evaluated point, the work the method needs whatever the precision: the complex
+    unpivoted LU, (8/3) n^3 real flops, plus 8 n^2 for the two triangular solves of the
+    exponent when the state is displaced."""
+    n = float(n)
+    return (8.0 / 3.0) * n ** 3 + (8.0 * n * n if has_gamma else 0.0)
+
+
+def pipe_flops(n: int, has_gamma: bool, precision: int) -> float:
+    """Per evaluated point, the arithmetic-pipe work the kernel issues, in FP32-FMA
+    equivalents x 2 (so that it compares with a flop peak).  FP64: as algorithmic_flops.
+    FP32R: LU 4 FMA per complex MAC over n^3/3 MACs; exact residual 3 mad.wide.s32 per
+    complex MAC over n^3/3 MACs, each worth 2 FMA slots (it issues at half the FP32 FMA
+    rate), plus ~30 integer operations per entry; Z = L^^-1 E (n^3/2 complex MACs) and
+    diag(U^^-1 Z) (n^3/6) at 4 FMA per MAC; if displaced, four triangular solves (8 n^2)
+    and the solve residual by Dot2 (80 n^2)."""
     n = float(n)
     if precision == 0:
-        return (8.0 / 3.0) * n ** 3 + (8.0 * n * n if has_gamma else 0.0)
-    slots = (4.0 / 3.0 + 40.0 / 3.0 + 2.0 + 2.0 / 3.0) * n ** 3 + 30.0 * n * n
+        return algorithmic_flops(n, has_gamma)
+    slots = (4.0 / 3.0 + 2.0 + 2.0 + 2.0 / 3.0) * n ** 3 + 30.0 * n * n
     if has_gamma:
         slots += 8.0 * n * n + 80.0 * n * n
     return 2.0 * slots
@@ -258,11 +266,13 @@ def main():
     d1 = results[1]["diag"]
     has_gamma = prob.alpha is not None
     out_points = {p: world * npts * args.steps / (results[p]["gpu_ms"] * 1e-3) for p in results}
-    flops_pt = {p: algorithmic_flops(n, has_gamma, p) for p in results}
-    achieved = flops_pt[1] * d1["n_evaluated"] / (results[1]["kernel_ms"] * 1e-3) / 1e12
+    flops_pt = algorithmic_flops(n, has_gamma)
+    achieved = flops_pt * d1["n_evaluated"] / (results[1]["kernel_ms"] * 1e-3) / 1e12
+    pipe_pt = pipe_flops(n, has_gamma, 1)
+    pipe_achieved = pipe_pt * d1["n_evaluated"] / (results[1]["kernel_ms"] * 1e-3) / 1e12
     peak32 = SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
     peak64 = SMS * FP64_FMA_PER_SM_CLK * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    achieved64 = flops_pt[0] * d1["n_evaluated"] / (results[0]["kernel_ms"] * 1e-3) / 1e12
+    achieved64 = flops_pt * d1["n_evaluated"] / (results[0]["kernel_ms"] * 1e-3) / 1e12
     traffic = None
     prof_traffic = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(prof_traffic):
@@ -289,10 +299,12 @@ def main():
         "speedup_fp32r_vs_fp64": out_points[1] / out_points[0],
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak32, "unit": "TFLOP/s",
                      "frac": achieved / peak32, "traffic": traffic,
-                     "kernel": "k_points_fp32r", "kernel_ms": results[1]["kernel_ms"],
-                     "flops_per_point": flops_pt[1],
-                     "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
-                     "measured_fma_chain_tflops": peaks_meas},
+                     "kernel": d1["kernel_name"], "kernel_ms": results[1]["kernel_ms"],
+                     "flops_per_point": flops_pt, "flops": "complex LU (8/3) n^3 per evaluated point",
+                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
+                     "pipe_flops_per_point": pipe_pt, "pipe_achieved": pipe_achieved,
+                     "pipe_frac": pipe_achieved / peak32,
+                     "measured_alu_chains": peaks_meas},
         "e2e": {"value": e2e_value, "unit": "points/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,

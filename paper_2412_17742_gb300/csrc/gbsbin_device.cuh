@@ -124,4 +124,17 @@ __device__ __forceinline__ void acc2_add(Acc2& a, float v) {
 }
 __device__ __forceinline__ float acc2_value(const Acc2& a) { return a.s + a.c; }
 
+// ------------------------------------------------- fixed-point digits of the FP32 factors
+// 2^s as FP32 for -126 <= s <= 127.
+__device__ __forceinline__ float pow2f(int s) { return __int_as_float((127 + s) << 23); }
+
+// Smallest e with m < 2^e for finite m > 0 (-126 for m = 0 or subnormal, 129 for inf/NaN).
+__device__ __forceinline__ int exponent_bound(float m) { return ((__float_as_int(m) >> 23) & 0xff) - 126; }
+
+// conj(d) on the diagonal of M in the fixed-point scale 2^GBSBIN_FIX_BITS of -XA.
+__device__ __forceinline__ longlong2 conj_fix(double2 d) {
+  const double s = 4611686018427387904.0;   // 2^62
+  return make_longlong2(__double2ll_rn(d.x * s), -__double2ll_rn(d.y * s));
+}
+
 }  // namespace gbsbin

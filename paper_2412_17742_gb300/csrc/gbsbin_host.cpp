@@ -1168,7 +1168,11 @@ int gbsbin_batch_create(const gbsbin_problem* probs, int nprob, const gbsbin_opt
     const int threads = P->kernel == GBSBIN_KERNEL_WARP_FP32R ? 128
                         : P->kernel == GBSBIN_KERNEL_BLK_FP32R ? 256
                                                                : points_threads(P->kernel, P->n);
-    const int np = P->kernel == GBSBIN_KERNEL_WARP_FP32R ? (P->n <= 8 ? 8 : P->n <= 16 ? 16 : 32) : 0;
+    // warp kernel: padded size class; blocked kernel: problems whose shared memory allows
+    // two CTAs per SM run apart from the larger ones (a class launches with its largest need)
+    const int np = P->kernel == GBSBIN_KERNEL_WARP_FP32R ? (P->n <= 8 ? 8 : P->n <= 16 ? 16 : 32)
+                   : P->kernel == GBSBIN_KERNEL_BLK_FP32R ? points_blk_ctas_per_sm(P->n)
+                                                          : 0;
     auto key = std::make_tuple(P->kernel, threads, np);
     if (!class_of.count(key)) {
       class_of[key] = (int)B->classes.size();

@@ -112,6 +112,7 @@ cudaError_t launch_points_warp_batch(const PointBatch& batch, int np, int num_sm
 #define GBSBIN_BLK_CTAS_PER_SM 2
 size_t points_blk_smem_bytes(int n);
 size_t points_blk_slot_bytes(int n);
+int points_blk_ctas_per_sm(int n);   // resident CTAs per SM that the shared memory allows (1 or 2)
 cudaError_t launch_points_blk(const PointArgs& a, const PointBatch& batch, size_t smem_batch, int num_sms,
                               cudaStream_t s);
 size_t points_smem_bytes(int kernel, int n, int P, int L);

@@ -126,11 +126,6 @@ struct NoMask {
   __device__ bool operator()(int, int) const { return true; }
 };
 
-// 2^s as FP32 for -126 <= s <= 127.
-__device__ __forceinline__ float pow2f(int s) { return __int_as_float((127 + s) << 23); }
-
-// Smallest e with m < 2^e for finite m > 0 (-126 for m = 0 or subnormal, 129 for inf/NaN).
-__device__ __forceinline__ int exponent_bound(float m) { return ((__float_as_int(m) >> 23) & 0xff) - 126; }
 
 // v <- U^^{-1} L^^{-1} v for one right-hand side v (shared memory, n entries), with L\U
 // in global memory (unit lower L) and pinv[k] = 1 / u_kk, by the whole CTA: per 32-row
@@ -388,9 +383,9 @@ __device__ void group_fp32r_blk(const PointArgs& a, const long long e, unsigned 
               eim -= (long long)u.y << (24 - ei);
             }
             if (i == j) {                      // conj(d_i) on the diagonal of M
-              const double2 d = sm.w[sm.lab[i]];
-              er += __double2ll_rn(d.x * 4611686018427387904.0) >> sh;    // 2^62
-              eim -= __double2ll_rn(d.y * 4611686018427387904.0) >> sh;
+              const longlong2 dc = conj_fix(sm.w[sm.lab[i]]);
+              er += dc.x >> sh;
+              eim += dc.y >> sh;
             }
             const float s = pow2f(ei + fj - 48);     // value of one unit of the products
             E[ij] = make_float2(__ll2float_rn(er) * s, __ll2float_rn(eim) * s);
@@ -595,6 +590,11 @@ size_t points_blk_smem_bytes(int n) {
 // One CTA's workspace slot: L\U (float2) and the residual (float2; the integer digits of
 // the rounded factors before it), n x n each.  The workspace holds
 // GBSBIN_BLK_CTAS_PER_SM slots per SM.
+int points_blk_ctas_per_sm(int n) {
+  // 228 KB of shared memory per SM, 1 KB of it reserved per resident CTA
+  return 2 * (points_blk_smem_bytes(n) + 1024) <= 228 * 1024 ? GBSBIN_BLK_CTAS_PER_SM : 1;
+}
+
 size_t points_blk_slot_bytes(int n) { return ((size_t)16 * n * n + 255) / 256 * 256; }
 
 cudaError_t launch_points_blk(const PointArgs& a, const PointBatch& batch, size_t smem_batch, int num_sms,

@@ -9,17 +9,20 @@
 // and row k of U with warp shuffles.  Steps run in blocks of four: the block index is
 // unrolled (so the owning register row/column is a compile-time constant), the step within
 // the block is a runtime loop, which keeps the code small enough for the instruction
-// cache.  The residual pass reads L\U from a per-warp shared tile in a runtime loop.
+// cache.  The residual pass reads the digits of L\U from a per-warp shared tile in a
+// runtime loop.
 //
 // Per point:
 //   1. M^ = fl32(M) in registers; unpivoted LU in FP32.
-//   2. Log det from the pivots: lane i takes Log(d_i u'_ii) in FP64 (each has Re > 0).
-//   3. Residual E = M - L^U^ with Dot2 (exact FP32 products, Knuth TwoSum), M taken as
-//      NXA_hi + NXA_lo (+ conj(d) as hi + lo on the diagonal); stored to a shared tile.
-//   4. delta = tr(U^^{-1} L^^{-1} E): forward substitution on all columns, then back
+//   2. Rounding of each row of L^ and column of U^ onto a 24-bit fixed-point grid (at most
+//      the FP32 rounding of the row's / column's largest entry); int32 digits to the tile.
+//   3. Log det from the rounded pivots: lane i takes Log(d_i u'_ii) in FP64 (Re > 0).
+//   4. Residual E = M - L^U^ exactly in int64 (Karatsuba digit products, M as fixed-point
+//      -XA shifted to each entry's scale), rounded to FP32 once.
+//   5. delta = tr(U^^{-1} L^^{-1} E): forward substitution on all columns, then back
 //      substitution on the entries X[m][c], m >= c, that diag(X) needs.
-//   5. If displaced: x^ = M^^{-1} X gamma, r = X gamma - M x^ by Dot2, x = x^ + M^^{-1} r.
-//   6. log q = 1/2 gamma^T x - 1/2 (ld + delta).
+//   6. If displaced: x^ = M^^{-1} X gamma, r = X gamma - M x^ by Dot2, x = x^ + M^^{-1} r.
+//   7. log q = 1/2 gamma^T x - 1/2 (ld + delta).
 #include <cuda_runtime.h>
 
 #include "gbsbin_device.cuh"
@@ -40,6 +43,7 @@ template <int NP, int WARPS>
 struct WarpShared {
   double2 w[WARPS][GBSBIN_MAX_L];
   float2 inv[WARPS][NP];
+  float2 piv[WARPS][NP];
   float2 LU[WARPS][NP * (NP + 4)];
   float2 x[WARPS][NP];
   float2 r[WARPS][NP];
@@ -60,6 +64,7 @@ __device__ __forceinline__ void warp_point(const PointArgs& a, const long long e
   const int* s_lab = sh.lab;
   double2* w = sh.w[warp];
   float2* invk = sh.inv[warp];
+  float2* pv = sh.piv[warp];
   float2* T = sh.LU[warp];
   float2* xs = sh.x[warp];
   float2* rs = sh.r[warp];
@@ -119,17 +124,60 @@ __device__ __forceinline__ void warp_point(const PointArgs& a, const long long e
         }
       }
     }
-    // stage L\U to the warp's shared tile (read by the residual pass and the solves)
+    // ---- 2. rounding: row i of L^ onto the grid 2^(erow_i - 24), column j of U^ onto
+    // 2^(fcol_j - 24), all entries below 2^erow_i (2^fcol_j); the rounded factors are used
+    // from here on.  Their int32 digits go to the warp's tile, the exponents to sh.ex.
+    int erow[RA], fcol[CB];
+    bool bad = false;
+#pragma unroll
+    for (int ra = 0; ra < RA; ++ra) {
+      const int i = lr + 8 * ra;
+      float m = 0.0f;
+#pragma unroll
+      for (int cb = 0; cb < CB; ++cb)
+        if (lc + 4 * cb < i) m = fmaxf(m, fmaxf(fabsf(A[ra][cb].x), fabsf(A[ra][cb].y)));
+      m = fmaxf(m, __shfl_xor_sync(kFull, m, 1));
+      m = fmaxf(m, __shfl_xor_sync(kFull, m, 2));
+      const int ex = exponent_bound(m);
+      bad |= ex > 20;
+      erow[ra] = min(max(ex, 0), 20);
+    }
+#pragma unroll
+    for (int cb = 0; cb < CB; ++cb) {
+      const int j = lc + 4 * cb;
+      float m = 0.0f;
+#pragma unroll
+      for (int ra = 0; ra < RA; ++ra)
+        if (lr + 8 * ra <= j) m = fmaxf(m, fmaxf(fabsf(A[ra][cb].x), fabsf(A[ra][cb].y)));
+      m = fmaxf(m, __shfl_xor_sync(kFull, m, 4));
+      m = fmaxf(m, __shfl_xor_sync(kFull, m, 8));
+      m = fmaxf(m, __shfl_xor_sync(kFull, m, 16));
+      const int ex = exponent_bound(m);
+      bad |= ex > 29;
+      fcol[cb] = min(max(ex, -14), 29);
+    }
+    int2* Tq = reinterpret_cast<int2*>(T);
+    __syncwarp();                       // the LU's writes of invk (lane 0) come first
 #pragma unroll
     for (int ra = 0; ra < RA; ++ra)
 #pragma unroll
-      for (int cb = 0; cb < CB; ++cb) T[(lr + 8 * ra) * ES + lc + 4 * cb] = A[ra][cb];
+      for (int cb = 0; cb < CB; ++cb) {
+        const int i = lr + 8 * ra, j = lc + 4 * cb;
+        const int sc = 24 - (i > j ? erow[ra] : fcol[cb]);
+        const float qx = rintf(A[ra][cb].x * pow2f(sc)), qy = rintf(A[ra][cb].y * pow2f(sc));
+        Tq[i * ES + j] = make_int2((int)qx, (int)qy);
+        if (i == j) {
+          const float2 u = make_float2(qx * pow2f(-sc), qy * pow2f(-sc));
+          pv[i] = u;
+          invk[i] = crecipf(u);
+        }
+      }
     __syncwarp();
 
-    // ---- 2. log det = sum_i Log(d_i u'_ii), one pivot per lane, FP64
+    // ---- 3. log det = sum_i Log(d_i u'_ii), one pivot per lane, FP64
     double ld_re = 0.0, ld_im = 0.0, mn = 1.0e300;
     if (lane < n) {
-      const float2 u = T[lane * ES + lane];
+      const float2 u = pv[lane];
       const double2 z = cmul(w[s_lab[lane]], make_double2(u.x, u.y));
       mn = z.x;
       if (!(z.x == z.x) || !(z.y == z.y)) mn = -1.0e300;
@@ -139,81 +187,89 @@ __device__ __forceinline__ void warp_point(const PointArgs& a, const long long e
     ld_re = warp_sum_d(ld_re);
     ld_im = warp_sum_d(ld_im);
     mn = warp_min_d(mn);
+    if (__any_sync(kFull, bad)) mn = -1.0e300;
 
-    // ---- 3. residual E = M - L^U^ (Dot2), runtime loop over k reading L\U from the tile.
-    // Terms outside k < min(i, j) (and k = j for i > j) get a zero factor, which leaves the
-    // Dot2 sums exactly unchanged and keeps the accumulation branch-free.
+    // ---- 4. residual E = M - L^U^ exactly: digit products summed in int64 (Karatsuba,
+    // three 32 x 32 -> 64-bit multiply-adds per complex term), M from the fixed-point
+    // -XA shifted to the entry's scale 2^(erow_i + fcol_j - 48), one rounding to FP32.
+    // Two columns per pass; terms outside k < min(i, j + 1) get a zero digit.
     float2 Z[RA][CB];
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      Acc2 er[RA][CH], ei[RA][CH];
+    for (int h = 0; h < CB / 2; ++h) {
+      long long sa[RA][2], sb[RA][2], sc[RA][2];
 #pragma unroll
       for (int ra = 0; ra < RA; ++ra)
 #pragma unroll
-        for (int q = 0; q < CH; ++q) {
-          er[ra][q] = Acc2{0.0f, 0.0f};
-          ei[ra][q] = Acc2{0.0f, 0.0f};
-        }
-      const int kend = 4 * (CH * h + CH - 1) + 3;   // largest column of this half
+        for (int q = 0; q < 2; ++q) sa[ra][q] = sb[ra][q] = sc[ra][q] = 0;
+      const int kend = 4 * (2 * h + 1) + 3;   // largest column of this pass
 #pragma unroll 1
       for (int k = 0; k < NP - 1 && k <= kend; ++k) {
-        float2 u[CH];
+        int ux[2], uy[2], us[2];
 #pragma unroll
-        for (int q = 0; q < CH; ++q) u[q] = T[k * ES + lc + 4 * (CH * h + q)];
+        for (int q = 0; q < 2; ++q) {
+          const int j = lc + 4 * (2 * h + q);
+          const int2 u = Tq[k * ES + j];
+          ux[q] = k <= j ? u.x : 0;
+          uy[q] = k <= j ? u.y : 0;
+          us[q] = ux[q] + uy[q];
+        }
 #pragma unroll
         for (int ra = 0; ra < RA; ++ra) {
           if (8 * ra + 7 <= k) continue;        // warp-uniform: all rows of the group <= k
           const int i = lr + 8 * ra;
-          const float2 l = T[i * ES + k];
-          const float lx = k < i ? -l.x : 0.0f, ly = k < i ? l.y : 0.0f;
+          const int2 l = Tq[i * ES + k];
+          const int lx = k < i ? l.x : 0, ly = k < i ? l.y : 0, ls = lx + ly;
 #pragma unroll
-          for (int q = 0; q < CH; ++q) {
-            const int j = lc + 4 * (CH * h + q);
-            const float ux = k <= j ? u[q].x : 0.0f, uy = k <= j ? u[q].y : 0.0f;
-            acc2_add_prod(er[ra][q], lx, ux);
-            acc2_add_prod(er[ra][q], ly, uy);
-            acc2_add_prod(ei[ra][q], lx, uy);
-            acc2_add_prod(ei[ra][q], -ly, ux);
+          for (int q = 0; q < 2; ++q) {
+            sa[ra][q] += (long long)lx * ux[q];
+            sb[ra][q] += (long long)ly * uy[q];
+            sc[ra][q] += (long long)ls * us[q];
           }
         }
       }
 #pragma unroll
       for (int ra = 0; ra < RA; ++ra)
 #pragma unroll
-        for (int q = 0; q < CH; ++q) {
-          const int cb = CH * h + q, i = lr + 8 * ra, j = lc + 4 * cb;
+        for (int q = 0; q < 2; ++q) {
+          const int cb = 2 * h + q, i = lr + 8 * ra, j = lc + 4 * cb;
+          const int sh = GBSBIN_FIX_BITS - 48 + erow[ra] + fcol[cb];
+          longlong2 mf = make_longlong2(i == j ? (1ll << GBSBIN_FIX_BITS) : 0ll, 0ll);   // identity padding
+          if (i < n && j < n) mf = a.NXA_fix[i * n + j];
+          long long er = (mf.x >> sh) - (sa[ra][q] - sb[ra][q]);
+          long long ei = (mf.y >> sh) - (sc[ra][q] - sa[ra][q] - sb[ra][q]);
           if (i <= j) {                  // L_ii U_ij = U_ij
-            const float2 uij = T[i * ES + j];
-            acc2_add(er[ra][q], -uij.x);
-            acc2_add(ei[ra][q], -uij.y);
+            const int2 u = Tq[i * ES + j];
+            er -= (long long)u.x << (24 - erow[ra]);
+            ei -= (long long)u.y << (24 - erow[ra]);
           }
-          if (i < n && j < n) {
-            const float2 xh = a.NXA_hi[i * n + j], xl = a.NXA_lo[i * n + j];
-            acc2_add(er[ra][q], xh.x);
-            acc2_add(er[ra][q], xl.x);
-            acc2_add(ei[ra][q], xh.y);
-            acc2_add(ei[ra][q], xl.y);
-            if (i == j) {
-              const double2 d = w[s_lab[i]];
-              const float dhx = (float)d.x, dhy = (float)d.y;
-              acc2_add(er[ra][q], dhx);
-              acc2_add(er[ra][q], (float)(d.x - (double)dhx));
-              acc2_add(ei[ra][q], -dhy);
-              acc2_add(ei[ra][q], -(float)(d.y - (double)dhy));
-            }
-          } else if (i == j) {
-            acc2_add(er[ra][q], 1.0f);
+          if (i == j && i < n) {
+            const longlong2 dc = conj_fix(w[s_lab[i]]);
+            er += dc.x >> sh;
+            ei += dc.y >> sh;
           }
-          Z[ra][cb] = make_float2(acc2_value(er[ra][q]), acc2_value(ei[ra][q]));
+          const float s = pow2f(erow[ra] + fcol[cb] - 48);
+          Z[ra][cb] = make_float2(__ll2float_rn(er) * s, __ll2float_rn(ei) * s);
         }
     }
-    // L\U back into registers for the substitutions
+    // the rounded L\U back into registers (from the digits) and, as FP32, into the tile
+    // for the exponent's substitutions
 #pragma unroll
     for (int ra = 0; ra < RA; ++ra)
 #pragma unroll
-      for (int cb = 0; cb < CB; ++cb) A[ra][cb] = T[(lr + 8 * ra) * ES + lc + 4 * cb];
+      for (int cb = 0; cb < CB; ++cb) {
+        const int i = lr + 8 * ra, j = lc + 4 * cb;
+        const int sc = (i > j ? erow[ra] : fcol[cb]) - 24;
+        const int2 q = Tq[i * ES + j];
+        A[ra][cb] = make_float2((float)q.x * pow2f(sc), (float)q.y * pow2f(sc));
+      }
+    __syncwarp();
+#pragma unroll
+    for (int ra = 0; ra < RA; ++ra)
+#pragma unroll
+      for (int cb = 0; cb < CB; ++cb) T[(lr + 8 * ra) * ES + lc + 4 * cb] = A[ra][cb];
+    __syncwarp();
 
-    // ---- 4. delta = tr(U^^{-1} L^^{-1} E): Z = L^^{-1} E, then X = U^^{-1} Z on m >= c
+    // ---- 5. delta = tr(U^^{-1} L^^{-1} E): Z = L^^{-1} E, then X = U^^{-1} Z on m >= c
 #pragma unroll
     for (int kb = 0; kb < NKB; ++kb) {
       const int ka = kb >> 1;
@@ -281,7 +337,7 @@ __device__ __forceinline__ void warp_point(const PointArgs& a, const long long e
     dre = warp_sum_d(dre);
     dim = warp_sum_d(dim);
 
-    // ---- 5. exponent with one refinement step (triangular solves read the tile)
+    // ---- 6. exponent with one refinement step (triangular solves read the tile)
     double ex_re = 0.0, ex_im = 0.0;
     if (a.has_gamma) {
       for (int pass = 0; pass < 2; ++pass) {
