@@ -131,6 +131,13 @@ __device__ __forceinline__ float pow2f(int s) { return __int_as_float((127 + s) 
 // Smallest e with m < 2^e for finite m > 0 (-126 for m = 0 or subnormal, 129 for inf/NaN).
 __device__ __forceinline__ int exponent_bound(float m) { return ((__float_as_int(m) >> 23) & 0xff) - 126; }
 
+// int64 -> FP32, rounded to nearest: the 32-bit conversion (a full-rate instruction) when
+// the value fits, the 64-bit one (on the FP64 pipe) otherwise.
+__device__ __forceinline__ float ll2f(long long v) {
+  const int lo = (int)v;
+  return (long long)lo == v ? __int2float_rn(lo) : __ll2float_rn(v);
+}
+
 // conj(d) on the diagonal of M in the fixed-point scale 2^GBSBIN_FIX_BITS of -XA.
 __device__ __forceinline__ longlong2 conj_fix(double2 d) {
   const double s = 4611686018427387904.0;   // 2^62

@@ -22,12 +22,35 @@ __device__ __forceinline__ double2 cfma2(double2 a, double2 b, double2 c) {  // 
   return make_double2(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));
 }
 
-// G = exp(log q - log q_0) on the evaluated half grid
-__global__ void k_normalise(const double2* __restrict__ logq, long long n, double2* __restrict__ G) {
-  const double2 l0 = logq[0];
+// log q from the warp kernel's unfinished form f = (P re, P im, A, r re, r im): P is the
+// product of the factors d_i u'_ii of det K (each with Re > 0), A the FP32 sum of their
+// arguments (within far less than pi of the exact sum), r the rest of log q.  Log det K =
+// log|P| + i (Arg P + 2 pi m) with m the winding that brings Arg P to A.
+__device__ __forceinline__ double2 finish_logq(const double* f) {
+  const double TWO_PI = 6.283185307179586476925286766559;
+  const double a0 = atan2(f[1], f[0]);
+  const double re = 0.5 * log(fma(f[0], f[0], f[1] * f[1]));
+  const double im = a0 + TWO_PI * rint((f[2] - a0) / TWO_PI);
+  return make_double2(f[3] - 0.5 * re, f[4] - 0.5 * im);
+}
+
+// G = exp(log q - log q_0) on the evaluated half grid (finishing log q first when the point
+// kernel left it unfinished)
+__global__ void k_normalise(const double2* logq, long long n, double2* __restrict__ G,
+                            const double* __restrict__ ldfin, double2* logq_fin) {
+  __shared__ double2 s_l0;
+  if (threadIdx.x == 0) s_l0 = ldfin ? finish_logq(ldfin) : logq[0];
+  __syncthreads();
+  const double2 l0 = s_l0;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
        e += (long long)gridDim.x * blockDim.x) {
-    double2 v = logq[e];
+    double2 v;
+    if (ldfin) {
+      v = finish_logq(ldfin + 6 * e);
+      logq_fin[e] = v;
+    } else {
+      v = logq[e];
+    }
     double m = exp(v.x - l0.x);
     double s, c;
     sincos(v.y - l0.y, &s, &c);
@@ -148,7 +171,7 @@ static unsigned blocks_for(long long work) {
 cudaError_t launch_dft(const DftArgs& a, cudaStream_t s) {
   const GridDesc& g = a.grid;
   const int L = g.L;
-  k_normalise<<<blocks_for(g.n_eval), kDftThreads, 0, s>>>(a.logq, g.n_eval, a.bufA);
+  k_normalise<<<blocks_for(g.n_eval), kDftThreads, 0, s>>>(a.logq, g.n_eval, a.bufA, a.ldfin, a.logq_fin);
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return err;
   long long dims[GBSBIN_MAX_L];

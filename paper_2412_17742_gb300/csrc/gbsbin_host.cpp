@@ -33,6 +33,7 @@ struct gbsbin_plan {
   float2 *d_NXA_hi = nullptr, *d_NXA_lo = nullptr, *d_Xg_hi = nullptr, *d_Xg_lo = nullptr;
   float2 *d_g_hi = nullptr, *d_g_lo = nullptr;
   longlong2* d_NXA_fix = nullptr;
+  double* d_ldfin = nullptr;          // warp kernel: unfinished log det per evaluated point
   int* d_label = nullptr;
   double2* d_logq = nullptr;
   double* d_minpiv = nullptr;
@@ -241,7 +242,7 @@ void free_device(gbsbin_plan* P) {
   void* ptrs[] = {P->d_NXA,  P->d_gamma, P->d_Xgamma, P->d_NXA_hi, P->d_NXA_lo, P->d_Xg_hi,
                   P->d_Xg_lo, P->d_g_hi, P->d_g_lo,   P->d_label, P->d_logq,  P->d_minpiv,
                   P->d_bufA, P->d_bufB,  P->d_tw,     P->d_diag,  P->d_gws,   P->d_table,
-                  P->d_NXA_fix};
+                  P->d_NXA_fix, P->d_ldfin};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (P->h_stage) cudaFreeHost(P->h_stage);
@@ -546,6 +547,11 @@ static int plan_create_impl(const gbsbin_problem* p, const gbsbin_options* o, gb
     delete P;
     return st;
   }
+  if (P->kernel == GBSBIN_KERNEL_WARP_FP32R && (st = dalloc(&P->d_ldfin, (size_t)6 * g.n_eval))) {
+    free_device(P);
+    delete P;
+    return st;
+  }
   if (alloc_gws && (P->kernel == GBSBIN_KERNEL_GMEM_FP64 || P->kernel == GBSBIN_KERNEL_GMEM_FP32R ||
                     P->kernel == GBSBIN_KERNEL_BLK_FP32R)) {
     P->gws_slot_bytes = P->kernel == GBSBIN_KERNEL_BLK_FP32R ? (long long)points_blk_slot_bytes(n)
@@ -676,6 +682,7 @@ static PointArgs make_point_args(gbsbin_plan* P) {
   a.minpiv = P->d_minpiv;
   a.gws = P->d_gws;
   a.gws_slot_bytes = P->gws_slot_bytes;
+  a.ldfin = P->d_ldfin;
   const bool save = P->opt.want_backward && (P->kernel == GBSBIN_KERNEL_SMEM_FP64 || P->kernel == GBSBIN_KERNEL_GMEM_FP64);
   a.lu_store = save ? P->d_lu : nullptr;
   a.x_store = save ? P->d_xs : nullptr;
@@ -686,6 +693,8 @@ static DftArgs make_dft_args(gbsbin_plan* P, double* P_out) {
   DftArgs d{};
   d.grid = P->grid;
   d.logq = P->d_logq;
+  d.ldfin = P->d_ldfin;
+  d.logq_fin = P->d_logq;
   d.tw = P->d_tw;
   d.bufA = P->d_bufA;
   d.bufB = P->d_bufB;

@@ -52,6 +52,9 @@ struct PointArgs {
   long long gws_slot_bytes; // bytes of one CTA's slot
   double2* lu_store;        // FP64 kernels only, or nullptr: n_eval x n*n LU factors of M
   double2* x_store;         // n_eval x n: x = M^{-1} X gamma
+  double* ldfin;            // warp kernel only: n_eval x 6 doubles (the product of the
+                            // pivots d_i u'_ii re/im, the FP32 sum of their arguments, the
+                            // rest of log q re/im, unused); log q is finished by the DFT
 };
 
 // A batch of problems for one point-kernel launch: jobs are (problem, first point) groups
@@ -92,6 +95,8 @@ struct BackwardArgs {
 struct DftArgs {
   GridDesc grid;
   const double2* logq;      // n_eval
+  const double* ldfin;      // nullptr, or the warp kernel's unfinished log det (see PointArgs)
+  double2* logq_fin;        // with ldfin: where the finished log q go (n_eval)
   const double2* tw;        // concatenated exp(-2 pi i m / radix[l]), m < radix[l]
   double2* bufA;            // n_eval complex scratch
   double2* bufB;            // n_eval complex scratch

@@ -388,7 +388,7 @@ __device__ void group_fp32r_blk(const PointArgs& a, const long long e, unsigned 
               eim += dc.y >> sh;
             }
             const float s = pow2f(ei + fj - 48);     // value of one unit of the products
-            E[ij] = make_float2(__ll2float_rn(er) * s, __ll2float_rn(eim) * s);
+            E[ij] = make_float2(ll2f(er) * s, ll2f(eim) * s);
           }
       }
   }

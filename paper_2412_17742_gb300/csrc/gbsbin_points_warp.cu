@@ -16,13 +16,14 @@
 //   1. M^ = fl32(M) in registers; unpivoted LU in FP32.
 //   2. Rounding of each row of L^ and column of U^ onto a 24-bit fixed-point grid (at most
 //      the FP32 rounding of the row's / column's largest entry); int32 digits to the tile.
-//   3. Log det from the rounded pivots: lane i takes Log(d_i u'_ii) in FP64 (Re > 0).
+//   3. Log det from the rounded pivots: product of d_i u'_ii (each Re > 0) and the FP32 sum
+//      of their arguments; the DFT's first kernel takes the Log (one point per thread).
 //   4. Residual E = M - L^U^ exactly in int64 (Karatsuba digit products, M as fixed-point
 //      -XA shifted to each entry's scale), rounded to FP32 once.
 //   5. delta = tr(U^^{-1} L^^{-1} E): forward substitution on all columns, then back
 //      substitution on the entries X[m][c], m >= c, that diag(X) needs.
 //   6. If displaced: x^ = M^^{-1} X gamma, r = X gamma - M x^ by Dot2, x = x^ + M^^{-1} r.
-//   7. log q = 1/2 gamma^T x - 1/2 (ld + delta).
+//   7. log q = 1/2 gamma^T x - 1/2 (ld + delta), finished by the DFT's first kernel.
 #include <cuda_runtime.h>
 
 #include "gbsbin_device.cuh"
@@ -174,18 +175,36 @@ __device__ __forceinline__ void warp_point(const PointArgs& a, const long long e
       }
     __syncwarp();
 
-    // ---- 3. log det = sum_i Log(d_i u'_ii), one pivot per lane, FP64
-    double ld_re = 0.0, ld_im = 0.0, mn = 1.0e300;
-    if (lane < n) {
-      const float2 u = pv[lane];
-      const double2 z = cmul(w[s_lab[lane]], make_double2(u.x, u.y));
-      mn = z.x;
-      if (!(z.x == z.x) || !(z.y == z.y)) mn = -1.0e300;
-      ld_re = 0.5 * log(fma(z.x, z.x, z.y * z.y));
-      ld_im = atan2(z.y, z.x);
+    // ---- 3. log det = sum_i Log(d_i u'_ii) (each factor has Re > 0): the product of the
+    // factors by a butterfly over the lanes in FP64 and the FP32 sum of their arguments
+    // (each in (-pi/2, pi/2), so the sum is far closer to the exact one than pi, which
+    // fixes the winding).  The Log of the product is taken by the DFT's first kernel,
+    // one point per thread, off this kernel's FP64 pipe.
+    double mn = 1.0e300;
+    {
+      double2 z = make_double2(1.0, 0.0);
+      float arg = 0.0f;
+      if (lane < n) {
+        const float2 u = pv[lane];
+        z = cmul(w[s_lab[lane]], make_double2(u.x, u.y));
+        mn = z.x;
+        if (!(z.x == z.x) || !(z.y == z.y)) mn = -1.0e300;
+        arg = atan2f((float)z.y, (float)z.x);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double2 y = make_double2(__shfl_xor_sync(kFull, z.x, o), __shfl_xor_sync(kFull, z.y, o));
+        z = cmul(z, y);
+        arg += __shfl_xor_sync(kFull, arg, o);
+      }
+      if (lane == 0) {
+        double* f = a.ldfin + 6 * e;
+        f[0] = z.x;
+        f[1] = z.y;
+        f[2] = (double)arg;
+        f[5] = 0.0;
+      }
     }
-    ld_re = warp_sum_d(ld_re);
-    ld_im = warp_sum_d(ld_im);
     mn = warp_min_d(mn);
     if (__any_sync(kFull, bad)) mn = -1.0e300;
 
@@ -202,7 +221,7 @@ __device__ __forceinline__ void warp_point(const PointArgs& a, const long long e
 #pragma unroll
         for (int q = 0; q < 2; ++q) sa[ra][q] = sb[ra][q] = sc[ra][q] = 0;
       const int kend = 4 * (2 * h + 1) + 3;   // largest column of this pass
-#pragma unroll 1
+#pragma unroll 4
       for (int k = 0; k < NP - 1 && k <= kend; ++k) {
         int ux[2], uy[2], us[2];
 #pragma unroll
@@ -248,7 +267,7 @@ __device__ __forceinline__ void warp_point(const PointArgs& a, const long long e
             ei += dc.y >> sh;
           }
           const float s = pow2f(erow[ra] + fcol[cb] - 48);
-          Z[ra][cb] = make_float2(__ll2float_rn(er) * s, __ll2float_rn(ei) * s);
+          Z[ra][cb] = make_float2(ll2f(er) * s, ll2f(ei) * s);
         }
     }
     // the rounded L\U back into registers (from the digits) and, as FP32, into the tile
@@ -412,7 +431,10 @@ __device__ __forceinline__ void warp_point(const PointArgs& a, const long long e
     }
 
     if (lane == 0) {
-      a.logq[e] = make_double2(0.5 * ex_re - 0.5 * (ld_re + dre), 0.5 * ex_im - 0.5 * (ld_im + dim));
+      // unfinished log q: log det is completed from (product, argument sum) by the DFT
+      double* f = a.ldfin + 6 * e;
+      f[3] = 0.5 * ex_re - 0.5 * dre;
+      f[4] = 0.5 * ex_im - 0.5 * dim;
       a.minpiv[e] = mn;
     }
     __syncwarp();
