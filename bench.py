@@ -207,7 +207,7 @@ def main():
     plans = {p: gb.Plan(prob, precision=p, want_timing=True) for p in (1, 0)}
     tables = {p: torch.empty(plans[p].shape, dtype=torch.float64, device="cuda") for p in plans}
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
-    launches_per_step = 1 + 1 + (prob.L - 1) + 1 + 1   # points, normalise, L-1 axes, last axis, diag
+    launches_per_step = 2   # point kernel, fused DFT + diagnostics (one cooperative launch)
 
     peaks_meas = {"fp64_tflops": gb.gbsbin_alu_peak(0, SMS * 8), "fp32_tflops": gb.gbsbin_alu_peak(1, SMS * 8),
                   "int64_mad_wide_tops": gb.gbsbin_alu_peak(2, SMS * 8)}
@@ -273,15 +273,7 @@ def main():
     peak32 = SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
     peak64 = SMS * FP64_FMA_PER_SM_CLK * 2 * SM_MAX_MHZ * 1e6 / 1e12
     achieved64 = flops_pt * d1["n_evaluated"] / (results[0]["kernel_ms"] * 1e-3) / 1e12
-    traffic = None
-    prof_traffic = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(prof_traffic):
-        try:
-            tj = json.load(open(prof_traffic))
-            if tj.get("kernel_source_hash") == _kernel_hash():
-                traffic = tj.get("bytes_per_launch")
-        except (ValueError, OSError):
-            traffic = None
+    traffic = _profiled_traffic(d1["kernel_name"])
 
     line = {
         "metric": METRIC, "value": out_points[1], "unit": "points/s", "n_gpus": world, "steps": args.steps,
@@ -420,14 +412,32 @@ def _extra_n200(gb, torch, stream, flush, steps, world):
     return out
 
 
-def _kernel_hash():
+def _sources_hash(paths):
+    """Hash of the source files a profiled kernel is built from (its own .cu and headers)."""
     import hashlib
     h = hashlib.sha256()
-    csrc = os.path.join(ROOT, "paper_2412_17742_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".h", ".cpp")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    for rel in paths:
+        h.update(open(os.path.join(ROOT, rel), "rb").read())
     return h.hexdigest()[:16]
+
+
+def _profiled_traffic(kernel_name):
+    """DRAM bytes per launch of the point kernel from the committed ncu summary, or None
+    when no summary exists for this kernel or its sources changed since the capture."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        tj = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    entry = tj.get(kernel_name)
+    if not entry:
+        return None
+    try:
+        if _sources_hash(entry["sources"]) != entry["sources_hash"]:
+            return None
+    except (OSError, KeyError):
+        return None
+    return entry["dram_bytes_per_launch"]
 
 
 def cpu_baseline(prob, seconds, tables):

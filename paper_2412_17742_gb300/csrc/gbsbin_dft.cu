@@ -35,15 +35,11 @@ __device__ __forceinline__ double2 finish_logq(const double* f) {
 }
 
 // G = exp(log q - log q_0) on the evaluated half grid (finishing log q first when the point
-// kernel left it unfinished)
-__global__ void k_normalise(const double2* logq, long long n, double2* __restrict__ G,
-                            const double* __restrict__ ldfin, double2* logq_fin) {
-  __shared__ double2 s_l0;
-  if (threadIdx.x == 0) s_l0 = ldfin ? finish_logq(ldfin) : logq[0];
-  __syncthreads();
-  const double2 l0 = s_l0;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
-       e += (long long)gridDim.x * blockDim.x) {
+// kernel left it unfinished).  Items t0, t0 + stride, ...; l0 = log q_0.
+__device__ __forceinline__ void stage_normalise(const double2* logq, long long n, double2* __restrict__ G,
+                                                const double* __restrict__ ldfin, double2* logq_fin, double2 l0,
+                                                long long t0, long long stride) {
+  for (long long e = t0; e < n; e += stride) {
     double2 v;
     if (ldfin) {
       v = finish_logq(ldfin + 6 * e);
@@ -58,12 +54,21 @@ __global__ void k_normalise(const double2* logq, long long n, double2* __restric
   }
 }
 
+__global__ void k_normalise(const double2* logq, long long n, double2* __restrict__ G,
+                            const double* __restrict__ ldfin, double2* logq_fin) {
+  __shared__ double2 s_l0;
+  if (threadIdx.x == 0) s_l0 = ldfin ? finish_logq(ldfin) : logq[0];
+  __syncthreads();
+  stage_normalise(logq, n, G, ldfin, logq_fin, s_l0, blockIdx.x * (long long)blockDim.x + threadIdx.x,
+                  (long long)gridDim.x * blockDim.x);
+}
+
 // out[o, b, s] = sum_{k < R} in[o, k, s] tw[(k b) mod R],  b < nout
-__global__ void k_dft_axis(const double2* __restrict__ in, double2* __restrict__ out, long long outer,
-                           int R, int nout, long long inner, const double2* __restrict__ tw) {
+__device__ __forceinline__ void stage_axis(const double2* __restrict__ in, double2* __restrict__ out, long long outer,
+                                           int R, int nout, long long inner, const double2* __restrict__ tw,
+                                           long long t0, long long stride) {
   const long long total = outer * nout * inner;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
+  for (long long t = t0; t < total; t += stride) {
     long long s = t % inner;
     long long rest = t / inner;
     int b = (int)(rest % nout);
@@ -80,13 +85,19 @@ __global__ void k_dft_axis(const double2* __restrict__ in, double2* __restrict__
   }
 }
 
+__global__ void k_dft_axis(const double2* __restrict__ in, double2* __restrict__ out, long long outer,
+                           int R, int nout, long long inner, const double2* __restrict__ tw) {
+  stage_axis(in, out, outer, R, nout, inner, tw, blockIdx.x * (long long)blockDim.x + threadIdx.x,
+             (long long)gridDim.x * blockDim.x);
+}
+
 // P[o, b] = scale (Re Y[o,0] + sum_{k=1}^{H-1} c_k Re(Y[o,k] tw[(k b) mod R])),
 // c_k = 2, except c = 1 for the self-conjugate k = R/2 when R is even.
-__global__ void k_dft_last_real(const double2* __restrict__ Y, double* __restrict__ P, long long outer,
-                                int R, int H, int nout, double scale, const double2* __restrict__ tw) {
+__device__ __forceinline__ void stage_last_real(const double2* __restrict__ Y, double* __restrict__ P,
+                                                long long outer, int R, int H, int nout, double scale,
+                                                const double2* __restrict__ tw, long long t0, long long stride) {
   const long long total = outer * nout;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
+  for (long long t = t0; t < total; t += stride) {
     int b = (int)(t % nout);
     long long o = t / nout;
     const double2* row = Y + o * H;
@@ -104,17 +115,25 @@ __global__ void k_dft_last_real(const double2* __restrict__ Y, double* __restric
   }
 }
 
+__global__ void k_dft_last_real(const double2* __restrict__ Y, double* __restrict__ P, long long outer,
+                                int R, int H, int nout, double scale, const double2* __restrict__ tw) {
+  stage_last_real(Y, P, outer, R, H, nout, scale, tw, blockIdx.x * (long long)blockDim.x + threadIdx.x,
+                  (long long)gridDim.x * blockDim.x);
+}
+
 // Per-block partial diagnostics (the host finishes the reduction in a fixed order):
 // part[4b + 0] = sum of P over the block's share, part[4b + 1] = max |Im| of the
 // self-conjugate entries Y[o, 0] (and Y[o, R/2]), part[4b + 2] = min pivot Re,
-// part[4b + 3] = number of bad points; part[4 GBSBIN_DIAG_BLOCKS] = Re log q_0.
-__global__ void k_diag(const double* __restrict__ P, long long table, const double2* __restrict__ Y,
-                       long long outer, int H, int R, const double* __restrict__ minpiv,
-                       const double2* __restrict__ logq, long long n_eval, double* __restrict__ part) {
+// part[4b + 3] = number of bad points; part[4 nblocks] = Re log q_0.  Block vb of nvb
+// blocks of blockDim.x threads; the whole CTA calls it.
+__device__ __forceinline__ void stage_diag(const double* __restrict__ P, long long table, const double2* __restrict__ Y,
+                                           long long outer, int H, int R, const double* __restrict__ minpiv,
+                                           const double2* logq, long long n_eval, double* __restrict__ part,
+                                           int vb, int nvb) {
   __shared__ double s_sum[32], s_im[32], s_min[32], s_bad[32];
   double sum = 0.0, im = 0.0, mn = 1.0e300, bad = 0.0;
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long stride = (long long)nvb * blockDim.x;
+  const long long t0 = (long long)vb * blockDim.x + threadIdx.x;
   for (long long t = t0; t < table; t += stride) sum += P[t];
   for (long long o = t0; o < outer; o += stride) {
     im = fmax(im, fabs(Y[o * H].y));
@@ -149,12 +168,91 @@ __global__ void k_diag(const double* __restrict__ P, long long table, const doub
       mn = fmin(mn, s_min[i]);
       bad += s_bad[i];
     }
-    double* out = part + 4 * blockIdx.x;
+    double* out = part + 4 * vb;
     out[0] = sum;
     out[1] = im;
     out[2] = mn;
     out[3] = bad;
-    if (blockIdx.x == 0) part[4 * gridDim.x] = logq[0].x;
+    if (vb == 0) part[4 * nvb] = logq[0].x;
+  }
+}
+
+__global__ void k_diag(const double* __restrict__ P, long long table, const double2* __restrict__ Y,
+                       long long outer, int H, int R, const double* __restrict__ minpiv,
+                       const double2* __restrict__ logq, long long n_eval, double* __restrict__ part) {
+  stage_diag(P, table, Y, outer, H, R, minpiv, logq, n_eval, part, blockIdx.x, gridDim.x);
+}
+
+// ------------------------------------------------------- one cooperative launch, all stages
+// The stages above run in sequence in one launch of co-resident CTAs (cooperative launch),
+// separated by a grid barrier: bar[0] counts arrivals, bar[1] is the generation, bar[2]
+// records a barrier that gave up waiting (after ~1 s), which the host reports as a CUDA
+// error.  Items are dealt to the CTAs cyclically (item t to CTA t mod gridDim), so the
+// FP64 work of every stage spreads over all SMs.  Every table entry is summed in the same order as in the multi-launch path, so
+// the table is bit-identical to it (the diagnostics' partial sums are split differently).
+struct DftStage {
+  long long outer, inner, twoff;
+  int R, nout;
+};
+struct DftFused {
+  DftArgs a;
+  int naxes;                         // complex axes 0 .. L-2
+  DftStage ax[GBSBIN_MAX_L];
+  long long last_outer, last_twoff;
+  int last_R, H, last_nout;
+  double scale;
+  unsigned* bar;
+};
+
+__device__ __forceinline__ void grid_barrier(unsigned* bar) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned g, old, cur;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(g) : "l"(bar + 1) : "memory");
+    asm volatile("atom.add.release.gpu.global.u32 %0, [%1], 1;" : "=r"(old) : "l"(bar) : "memory");
+    if (old == gridDim.x - 1) {
+      bar[0] = 0;
+      asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar + 1) : "memory");
+    } else {
+      long long it = 0;
+      do {
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(cur) : "l"(bar + 1) : "memory");
+        if (++it > (1ll << 23)) {          // ~1 s of L2 polls: give up, record it
+          atomicExch(bar + 2, 1u);
+          break;
+        }
+      } while (cur == g);
+    }
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(128) k_dft_fused(DftFused f) {
+  const DftArgs& a = f.a;
+  const long long t0 = threadIdx.x * (long long)gridDim.x + blockIdx.x;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  __shared__ double2 s_l0;
+  if (threadIdx.x == 0) s_l0 = a.ldfin ? finish_logq(a.ldfin) : a.logq[0];
+  __syncthreads();
+  stage_normalise(a.logq, a.grid.n_eval, a.bufA, a.ldfin, a.logq_fin, s_l0, t0, stride);
+  double2* cur = a.bufA;
+  double2* nxt = a.bufB;
+  for (int l = 0; l < f.naxes; ++l) {
+    grid_barrier(f.bar);
+    const DftStage& st = f.ax[l];
+    stage_axis(cur, nxt, st.outer, st.R, st.nout, st.inner, a.tw + st.twoff, t0, stride);
+    double2* t = cur;
+    cur = nxt;
+    nxt = t;
+  }
+  grid_barrier(f.bar);
+  stage_last_real(cur, a.P, f.last_outer, f.last_R, f.H, f.last_nout, f.scale, a.tw + f.last_twoff, t0, stride);
+  if (a.diag) {
+    grid_barrier(f.bar);
+    if ((int)blockIdx.x < GBSBIN_DIAG_BLOCKS)
+      stage_diag(a.P, a.table_size, cur, f.last_outer, f.H, f.last_R, a.minpiv, a.ldfin ? a.logq_fin : a.logq,
+                 a.grid.n_eval, a.diag, blockIdx.x, GBSBIN_DIAG_BLOCKS);
+    if (t0 == 0) a.diag[4 * GBSBIN_DIAG_BLOCKS + 1] = (double)*(volatile unsigned*)(f.bar + 2);
   }
 }
 
@@ -207,6 +305,49 @@ cudaError_t launch_dft(const DftArgs& a, cudaStream_t s) {
     err = cudaGetLastError();
   }
   return err;
+}
+
+cudaError_t launch_dft_fused(const DftArgs& a, unsigned* bar, int num_sms, cudaStream_t s) {
+  const GridDesc& g = a.grid;
+  const int L = g.L;
+  DftFused f{};
+  f.a = a;
+  f.bar = bar;
+  f.naxes = L - 1;
+  long long dims[GBSBIN_MAX_L];
+  for (int l = 0; l < L - 1; ++l) dims[l] = g.radix[l];
+  dims[L - 1] = g.half;
+  long long twoff = 0;
+  for (int l = 0; l < L - 1; ++l) {
+    long long outer = 1, inner = 1;
+    for (int m = 0; m < l; ++m) outer *= dims[m];
+    for (int m = l + 1; m < L; ++m) inner *= dims[m];
+    f.ax[l] = DftStage{outer, inner, twoff, g.radix[l], g.nout[l]};
+    dims[l] = g.nout[l];
+    twoff += g.radix[l];
+  }
+  long long outer = 1;
+  for (int m = 0; m < L - 1; ++m) outer *= dims[m];
+  f.last_outer = outer;
+  f.last_twoff = twoff;
+  f.last_R = g.radix[L - 1];
+  f.H = g.half;
+  f.last_nout = g.nout[L - 1];
+  f.scale = 1.0 / (double)g.npts;
+  int per_sm = 0;
+  cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dft_fused, 128, 0);
+  if (err != cudaSuccess) return err;
+  if (per_sm > 4) per_sm = 4;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  // one CTA per SM (the stages are FP64-latency-bound: spreading beats packing), more only
+  // for grids with more than 128 items per SM; at least the diagnostics' blocks
+  long long blocks = num_sms;
+  const long long need = (g.n_eval + 127) / 128;
+  if (need > blocks) blocks = need < (long long)per_sm * num_sms ? need : (long long)per_sm * num_sms;
+  if (blocks < GBSBIN_DIAG_BLOCKS) blocks = GBSBIN_DIAG_BLOCKS;
+  if (blocks > (long long)per_sm * num_sms) return cudaErrorInvalidConfiguration;
+  void* params[] = {&f};
+  return cudaLaunchCooperativeKernel((const void*)k_dft_fused, dim3((unsigned)blocks), dim3(128), params, 0, s);
 }
 
 }  // namespace gbsbin

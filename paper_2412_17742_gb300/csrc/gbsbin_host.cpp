@@ -34,6 +34,7 @@ struct gbsbin_plan {
   float2 *d_g_hi = nullptr, *d_g_lo = nullptr;
   longlong2* d_NXA_fix = nullptr;
   double* d_ldfin = nullptr;          // warp kernel: unfinished log det per evaluated point
+  unsigned* d_bar = nullptr;          // grid-barrier state of the fused DFT launch
   int* d_label = nullptr;
   double2* d_logq = nullptr;
   double* d_minpiv = nullptr;
@@ -242,7 +243,7 @@ void free_device(gbsbin_plan* P) {
   void* ptrs[] = {P->d_NXA,  P->d_gamma, P->d_Xgamma, P->d_NXA_hi, P->d_NXA_lo, P->d_Xg_hi,
                   P->d_Xg_lo, P->d_g_hi, P->d_g_lo,   P->d_label, P->d_logq,  P->d_minpiv,
                   P->d_bufA, P->d_bufB,  P->d_tw,     P->d_diag,  P->d_gws,   P->d_table,
-                  P->d_NXA_fix, P->d_ldfin};
+                  P->d_NXA_fix, P->d_ldfin, P->d_bar};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (P->h_stage) cudaFreeHost(P->h_stage);
@@ -534,11 +535,18 @@ static int plan_create_impl(const gbsbin_problem* p, const gbsbin_options* o, gb
       (st = dalloc(&P->d_Xg_lo, n)) || (st = dalloc(&P->d_g_hi, n)) || (st = dalloc(&P->d_g_lo, n)) ||
       (st = dalloc(&P->d_label, n)) || (st = dalloc(&P->d_logq, g.n_eval)) ||
       (st = dalloc(&P->d_minpiv, g.n_eval)) || (st = dalloc(&P->d_bufA, g.n_eval)) ||
-      (st = dalloc(&P->d_bufB, g.n_eval)) || (st = dalloc(&P->d_diag, 4 * GBSBIN_DIAG_BLOCKS + 1)) ||
+      (st = dalloc(&P->d_bufB, g.n_eval)) || (st = dalloc(&P->d_diag, 4 * GBSBIN_DIAG_BLOCKS + 2)) ||
+      (st = dalloc(&P->d_bar, 4)) ||
       (st = dalloc(&P->d_table, (size_t)P->table_size))) {
     free_device(P);
     delete P;
     return st;
+  }
+  if (cudaMemset(P->d_bar, 0, 4 * sizeof(unsigned)) != cudaSuccess ||
+      cudaMemset(P->d_diag, 0, (4 * GBSBIN_DIAG_BLOCKS + 2) * sizeof(double)) != cudaSuccess) {
+    free_device(P);
+    delete P;
+    return GBSBIN_ERR_CUDA;
   }
   long long twn = 0;
   for (int l = 0; l < p->L; ++l) twn += g.radix[l];
@@ -716,7 +724,7 @@ int gbsbin_execute(gbsbin_plan* P, double* P_out, void* stream) {
                                                          : launch_points(a, P->kernel, P->num_sms, s);
   if (e != cudaSuccess) return GBSBIN_ERR_CUDA;
   if (P->ev1 && cudaEventRecord(P->ev1, s) != cudaSuccess) return GBSBIN_ERR_CUDA;
-  e = launch_dft(make_dft_args(P, P_out), s);
+  e = launch_dft_fused(make_dft_args(P, P_out), P->d_bar, P->num_sms, s);
   return e == cudaSuccess ? GBSBIN_OK : GBSBIN_ERR_CUDA;
 }
 
@@ -733,7 +741,7 @@ int gbsbin_execute_host(gbsbin_plan* P, double* P_out_host, void* stream) {
 
 int gbsbin_diagnostics(gbsbin_plan* P, gbsbin_diag* out, void* stream) {
   if (!P || !out) return GBSBIN_ERR_ARG;
-  double part[4 * GBSBIN_DIAG_BLOCKS + 1] = {0};
+  double part[4 * GBSBIN_DIAG_BLOCKS + 2] = {0};
   double h[5] = {0.0, 0.0, 1.0e300, 0.0, 0.0};
   if (P->opt.want_diagnostics) {
     if (cudaMemcpyAsync(part, P->d_diag, sizeof(part), cudaMemcpyDeviceToHost, (cudaStream_t)stream) != cudaSuccess ||
@@ -767,6 +775,7 @@ int gbsbin_diagnostics(gbsbin_plan* P, gbsbin_diag* out, void* stream) {
     out->point_kernel_ms = ms;
   }
   if (!P->opt.want_diagnostics) return GBSBIN_OK;
+  if (part[4 * GBSBIN_DIAG_BLOCKS + 1] != 0.0) return GBSBIN_ERR_CUDA;   // a grid barrier gave up waiting
   return out->n_bad_points > 0 ? GBSBIN_ERR_NUMERIC : GBSBIN_OK;
 }
 
@@ -1111,7 +1120,8 @@ int batch_launch(gbsbin_batch* B, double* const* P_out, cudaStream_t s) {
   }
   for (size_t i = 0; i < B->plans.size(); ++i) {
     if (!P_out[i]) return GBSBIN_ERR_ARG;
-    if (launch_dft(make_dft_args(B->plans[i], P_out[i]), s) != cudaSuccess) return GBSBIN_ERR_CUDA;
+    if (launch_dft_fused(make_dft_args(B->plans[i], P_out[i]), B->plans[i]->d_bar, B->num_sms, s) != cudaSuccess)
+      return GBSBIN_ERR_CUDA;
   }
   return GBSBIN_OK;
 }

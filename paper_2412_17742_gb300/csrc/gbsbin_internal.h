@@ -125,6 +125,9 @@ size_t points_matrix_bytes(int kernel, int n, int P);
 int points_per_cta(int kernel, int n, int L);
 int points_threads(int kernel, int n);
 cudaError_t launch_dft(const DftArgs& a, cudaStream_t s);
+// All DFT stages and the diagnostics in one cooperative launch; bar: 4 zeroed unsigned ints
+// of grid-barrier state owned by the caller; needs diag to hold 4 GBSBIN_DIAG_BLOCKS + 2.
+cudaError_t launch_dft_fused(const DftArgs& a, unsigned* bar, int num_sms, cudaStream_t s);
 cudaError_t launch_backward(const BackwardArgs& b, const double* dLdP, cudaStream_t s);
 cudaError_t launch_alu_peak(int fp64, int blocks, float* out_sink, int iters, cudaStream_t s);
 
