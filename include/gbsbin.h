@@ -73,6 +73,12 @@ typedef struct {
                              its stream; gbsbin_diagnostics reports the elapsed time         */
   int want_backward;      /* nonzero: allocate what gbsbin_backward needs; FP64 executes then
                              keep the LU factors and exponent solutions of every point      */
+  long long shard_begin;  /* shard_end > 0: this plan evaluates only the evaluated points    */
+  long long shard_end;    /* e in [shard_begin, shard_end) of the half grid (plus point 0,
+                             w = 1, for the normalisation) and returns the PARTIAL table of
+                             their terms; the tables of shards that partition [0, n_evaluated)
+                             sum to the whole table (the DFT is linear).  0, 0 = whole grid.
+                             Not for batches or gbsbin_backward (ERR_UNSUPPORTED).          */
 } gbsbin_options;
 
 /*

@@ -45,7 +45,8 @@ class gbsbin_complex(ctypes.Structure):
 class gbsbin_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("oversample", ctypes.c_int),
                 ("want_diagnostics", ctypes.c_int), ("tile_override", ctypes.c_int),
-                ("want_timing", ctypes.c_int), ("want_backward", ctypes.c_int)]
+                ("want_timing", ctypes.c_int), ("want_backward", ctypes.c_int),
+                ("shard_begin", ctypes.c_longlong), ("shard_end", ctypes.c_longlong)]
 
 
 _cp = ctypes.POINTER(gbsbin_complex)
@@ -175,12 +176,14 @@ def gbsbin_default_options():
 
 
 def make_options(precision=GBSBIN_FP64, oversample=1, want_diagnostics=True, tile_override=0,
-                 want_timing=False, want_backward=False):
+                 want_timing=False, want_backward=False, shard=None):
     o = gbsbin_default_options()
     o.precision, o.oversample = int(precision), int(oversample)
     o.want_diagnostics, o.tile_override = int(bool(want_diagnostics)), int(tile_override)
     o.want_timing = int(bool(want_timing))
     o.want_backward = int(bool(want_backward))
+    if shard is not None:
+        o.shard_begin, o.shard_end = int(shard[0]), int(shard[1])
     return o
 
 
@@ -303,9 +306,11 @@ class Plan:
     """Owning wrapper: ``with Plan(prob, precision=...) as p: P = p.table()``."""
 
     def __init__(self, prob, precision=GBSBIN_FP64, oversample=1, want_diagnostics=True, tile_override=0,
-                 want_timing=False, want_backward=False):
+                 want_timing=False, want_backward=False, shard=None):
+        """shard = (begin, end): evaluate only points [begin, end) of the evaluated half grid
+        (plus point 0 for the normalisation); table() then returns their partial table."""
         self.options = make_options(precision, oversample, want_diagnostics, tile_override, want_timing,
-                                    want_backward)
+                                    want_backward, shard)
         self.handle = gbsbin_plan_create(prob, self.options)
         self.shape = tuple(int(c) + 1 for c in prob.cutoff)
         self.M, self.K = int(prob.M), int(prob.K)

@@ -40,8 +40,15 @@ __device__ __forceinline__ double2 root_of_unity(long long m, int R) {
   return make_double2(c, s);
 }
 
+// Half-grid index of a plan's evaluated point e: a shard evaluates point 0 first, then its
+// slice [e_lo, e_hi).
+__device__ __forceinline__ long long global_point(long long e, const GridDesc& g) {
+  return g.e_lo > 0 ? (e == 0 ? 0 : e - 1 + g.e_lo) : e;
+}
+
 // Digit l of evaluated point e: last axis in [0, half), the others full radix.
 __device__ __forceinline__ int point_digit(long long e, const GridDesc& g, int l) {
+  e = global_point(e, g);
   int last = (int)(e % g.half);
   if (l == g.L - 1) return last;
   long long rest = e / g.half;

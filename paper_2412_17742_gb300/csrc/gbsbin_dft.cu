@@ -34,32 +34,45 @@ __device__ __forceinline__ double2 finish_logq(const double* f) {
   return make_double2(f[3] - 0.5 * re, f[4] - 0.5 * im);
 }
 
-// G = exp(log q - log q_0) on the evaluated half grid (finishing log q first when the point
-// kernel left it unfinished).  Items t0, t0 + stride, ...; l0 = log q_0.
-__device__ __forceinline__ void stage_normalise(const double2* logq, long long n, double2* __restrict__ G,
+// G = exp(log q - log q_0) on the whole evaluated half grid (finishing log q first when the
+// point kernel left it unfinished).  A shard's plan evaluated point 0 and its slice
+// [e_lo, e_hi) only: G is zero off the slice, so the transform gives the slice's partial
+// table.  Items t0, t0 + stride, ... of the half grid; l0 = log q_0.
+__device__ __forceinline__ void stage_normalise(const double2* logq, const GridDesc& g, double2* __restrict__ G,
                                                 const double* __restrict__ ldfin, double2* logq_fin, double2 l0,
                                                 long long t0, long long stride) {
-  for (long long e = t0; e < n; e += stride) {
+  for (long long t = t0; t < g.n_full; t += stride) {
+    const bool in_slice = t >= g.e_lo && t < g.e_hi;
+    // this plan's index of half-grid point t (-1: not evaluated here)
+    const long long loc = in_slice ? (g.e_lo > 0 ? t - g.e_lo + 1 : t) : (t == 0 ? 0 : -1);
+    if (loc < 0) {
+      G[t] = make_double2(0.0, 0.0);
+      continue;
+    }
     double2 v;
     if (ldfin) {
-      v = finish_logq(ldfin + 6 * e);
-      logq_fin[e] = v;
+      v = finish_logq(ldfin + 6 * loc);
+      logq_fin[loc] = v;
     } else {
-      v = logq[e];
+      v = logq[loc];
+    }
+    if (!in_slice) {                   // point 0 of a later shard: normalisation only
+      G[t] = make_double2(0.0, 0.0);
+      continue;
     }
     double m = exp(v.x - l0.x);
     double s, c;
     sincos(v.y - l0.y, &s, &c);
-    G[e] = make_double2(m * c, m * s);
+    G[t] = make_double2(m * c, m * s);
   }
 }
 
-__global__ void k_normalise(const double2* logq, long long n, double2* __restrict__ G,
+__global__ void k_normalise(const double2* logq, GridDesc g, double2* __restrict__ G,
                             const double* __restrict__ ldfin, double2* logq_fin) {
   __shared__ double2 s_l0;
   if (threadIdx.x == 0) s_l0 = ldfin ? finish_logq(ldfin) : logq[0];
   __syncthreads();
-  stage_normalise(logq, n, G, ldfin, logq_fin, s_l0, blockIdx.x * (long long)blockDim.x + threadIdx.x,
+  stage_normalise(logq, g, G, ldfin, logq_fin, s_l0, blockIdx.x * (long long)blockDim.x + threadIdx.x,
                   (long long)gridDim.x * blockDim.x);
 }
 
@@ -234,7 +247,7 @@ __global__ void __launch_bounds__(128) k_dft_fused(DftFused f) {
   __shared__ double2 s_l0;
   if (threadIdx.x == 0) s_l0 = a.ldfin ? finish_logq(a.ldfin) : a.logq[0];
   __syncthreads();
-  stage_normalise(a.logq, a.grid.n_eval, a.bufA, a.ldfin, a.logq_fin, s_l0, t0, stride);
+  stage_normalise(a.logq, a.grid, a.bufA, a.ldfin, a.logq_fin, s_l0, t0, stride);
   double2* cur = a.bufA;
   double2* nxt = a.bufB;
   for (int l = 0; l < f.naxes; ++l) {
@@ -269,7 +282,7 @@ static unsigned blocks_for(long long work) {
 cudaError_t launch_dft(const DftArgs& a, cudaStream_t s) {
   const GridDesc& g = a.grid;
   const int L = g.L;
-  k_normalise<<<blocks_for(g.n_eval), kDftThreads, 0, s>>>(a.logq, g.n_eval, a.bufA, a.ldfin, a.logq_fin);
+  k_normalise<<<blocks_for(g.n_full), kDftThreads, 0, s>>>(a.logq, g, a.bufA, a.ldfin, a.logq_fin);
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return err;
   long long dims[GBSBIN_MAX_L];
@@ -342,7 +355,7 @@ cudaError_t launch_dft_fused(const DftArgs& a, unsigned* bar, int num_sms, cudaS
   // one CTA per SM (the stages are FP64-latency-bound: spreading beats packing), more only
   // for grids with more than 128 items per SM; at least the diagnostics' blocks
   long long blocks = num_sms;
-  const long long need = (g.n_eval + 127) / 128;
+  const long long need = (g.n_full + 127) / 128;
   if (need > blocks) blocks = need < (long long)per_sm * num_sms ? need : (long long)per_sm * num_sms;
   if (blocks < GBSBIN_DIAG_BLOCKS) blocks = GBSBIN_DIAG_BLOCKS;
   if (blocks > (long long)per_sm * num_sms) return cudaErrorInvalidConfiguration;

@@ -439,6 +439,8 @@ void gbsbin_default_options(gbsbin_options* o) {
   o->tile_override = 0;
   o->want_timing = 0;
   o->want_backward = 0;
+  o->shard_begin = 0;
+  o->shard_end = 0;
 }
 
 const char* gbsbin_strerror(int status) {
@@ -499,7 +501,23 @@ static int plan_create_impl(const gbsbin_problem* p, const gbsbin_options* o, gb
     P->table_size *= g.nout[l];
   }
   g.half = g.radix[p->L - 1] / 2 + 1;
-  g.n_eval = g.npts / g.radix[p->L - 1] * g.half;
+  g.n_full = g.npts / g.radix[p->L - 1] * g.half;
+  g.e_lo = 0;
+  g.e_hi = g.n_full;
+  g.n_eval = g.n_full;
+  if (opt.shard_end != 0 || opt.shard_begin != 0) {   // a shard: point 0, then [begin, end)
+    if (opt.shard_begin < 0 || opt.shard_end <= opt.shard_begin || opt.shard_end > g.n_full) {
+      delete P;
+      return GBSBIN_ERR_ARG;
+    }
+    if (opt.want_backward) {
+      delete P;
+      return GBSBIN_ERR_UNSUPPORTED;
+    }
+    g.e_lo = opt.shard_begin;
+    g.e_hi = opt.shard_end;
+    g.n_eval = (g.e_hi - g.e_lo) + (g.e_lo > 0 ? 1 : 0);
+  }
   st = build_state(p, n, P->XA, P->gamma, P->Xgamma, &P->has_gamma, &P->zbar);
   if (st) {
     delete P;
@@ -534,8 +552,8 @@ static int plan_create_impl(const gbsbin_problem* p, const gbsbin_options* o, gb
       (st = dalloc(&P->d_NXA_fix, nn)) ||
       (st = dalloc(&P->d_Xg_lo, n)) || (st = dalloc(&P->d_g_hi, n)) || (st = dalloc(&P->d_g_lo, n)) ||
       (st = dalloc(&P->d_label, n)) || (st = dalloc(&P->d_logq, g.n_eval)) ||
-      (st = dalloc(&P->d_minpiv, g.n_eval)) || (st = dalloc(&P->d_bufA, g.n_eval)) ||
-      (st = dalloc(&P->d_bufB, g.n_eval)) || (st = dalloc(&P->d_diag, 4 * GBSBIN_DIAG_BLOCKS + 2)) ||
+      (st = dalloc(&P->d_minpiv, g.n_eval)) || (st = dalloc(&P->d_bufA, g.n_full)) ||
+      (st = dalloc(&P->d_bufB, g.n_full)) || (st = dalloc(&P->d_diag, 4 * GBSBIN_DIAG_BLOCKS + 2)) ||
       (st = dalloc(&P->d_bar, 4)) ||
       (st = dalloc(&P->d_table, (size_t)P->table_size))) {
     free_device(P);
@@ -1150,6 +1168,7 @@ int gbsbin_batch_create(const gbsbin_problem* probs, int nprob, const gbsbin_opt
   gbsbin_default_options(&opt);
   if (o) opt = *o;
   if (opt.want_backward || opt.want_timing) return GBSBIN_ERR_ARG;  // per-plan features only
+  if (opt.shard_begin || opt.shard_end) return GBSBIN_ERR_UNSUPPORTED;
   gbsbin_batch* B = new (std::nothrow) gbsbin_batch();
   if (!B) return GBSBIN_ERR_NOMEM;
   int dev = 0;

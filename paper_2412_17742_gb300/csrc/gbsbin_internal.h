@@ -25,8 +25,11 @@ struct GridDesc {
   int radix[GBSBIN_MAX_L];
   int nout[GBSBIN_MAX_L];   // N_l + 1: table extent per axis
   int half;
-  long long n_eval;         // (npts / radix[L-1]) * half
+  long long n_eval;         // points this plan evaluates: (npts / radix[L-1]) * half, or for a
+                            // shard 1 + (e_hi - e_lo) (point 0 first, then the slice)
   long long npts;
+  long long n_full;         // (npts / radix[L-1]) * half: the whole evaluated half grid
+  long long e_lo, e_hi;     // the shard [e_lo, e_hi) of the half grid (0, n_full: no shard)
 };
 
 struct PointArgs {

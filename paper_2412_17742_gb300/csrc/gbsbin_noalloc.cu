@@ -89,6 +89,9 @@ extern "C" int gbsbin_table_from_logq_noalloc(int L, const int* cutoff, int over
   }
   g.half = g.radix[L - 1] / 2 + 1;
   g.n_eval = g.npts / g.radix[L - 1] * g.half;
+  g.n_full = g.n_eval;   // the whole half grid: no shard
+  g.e_lo = 0;
+  g.e_hi = g.n_eval;
   if (g.n_eval > kMaxEval || twiddles > kMaxTwiddles) return GBSBIN_ERR_UNSUPPORTED;
 
   double2* base = nullptr;

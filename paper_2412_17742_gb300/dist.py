@@ -1,0 +1,58 @@
+"""Several GPUs (one process per GPU, torch.distributed) on the binned distribution.
+
+Two ways to share the work, both without a collective on the point path:
+
+* independent tables or problems: ``shard_range(n_units, rank, world)`` deals each rank a
+  contiguous block of units (tables of a parameter sweep, problems of a batch); nothing is
+  exchanged;
+* one table: the grid points are independent (each is one determinant, Sec. III Eq. q_d),
+  and the inverse DFT that turns the grid into P(b) is linear, so rank r evaluates the slice
+  ``shard_range(n_evaluated, r, world)`` of the evaluated half grid into a partial table and
+  one all-reduce (sum) of prod(N_l + 1) doubles gives the whole table
+  (``sharded_table``).
+
+Slices of the half grid keep every conjugate pair G(w^-k) = conj G(w^k) on one rank: the
+half grid holds one representative of each pair.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def shard_range(n_units: int, rank: int, world: int):
+    """Contiguous block [begin, end) of units for ``rank`` of ``world``; the blocks of all
+    ranks partition [0, n_units) and differ in size by at most one."""
+    if world < 1 or not 0 <= rank < world or n_units < 0:
+        raise ValueError("need 0 <= rank < world and n_units >= 0")
+    return rank * n_units // world, (rank + 1) * n_units // world
+
+
+def evaluated_points(cutoff, oversample: int = 1) -> int:
+    """Points of the half grid a whole-table plan evaluates: prod over the axes but the last
+    of R_l, times floor(R_last / 2) + 1, with R_l = oversample (N_l + 1)."""
+    radix = [oversample * (int(c) + 1) for c in cutoff]
+    return int(np.prod(radix[:-1], dtype=np.int64)) * (radix[-1] // 2 + 1)
+
+
+def allreduce_table(table, group=None):
+    """Sum the ranks' partial tables in place (one all-reduce of prod(N_l + 1) doubles)."""
+    import torch.distributed as dist
+    dist.all_reduce(table, op=dist.ReduceOp.SUM, group=group)
+    return table
+
+
+def sharded_table(prob, precision: int = 0, oversample: int = 1, group=None, stream=None):
+    """The whole table P(b) of ``prob``, its grid shared by the ranks of ``group``: this rank
+    evaluates its slice on its current CUDA device, then the partial tables are summed."""
+    import torch.distributed as dist
+
+    from . import Plan
+    rank, world = dist.get_rank(group), dist.get_world_size(group)
+    begin, end = shard_range(evaluated_points(prob.cutoff, oversample), rank, world)
+    if end <= begin:                       # more ranks than points: contribute zeros
+        import torch
+        table = torch.zeros(tuple(int(c) + 1 for c in prob.cutoff), dtype=torch.float64, device="cuda")
+    else:
+        with Plan(prob, precision=precision, oversample=oversample, shard=(begin, end)) as p:
+            table = p.table(stream)
+    return allreduce_table(table, group)

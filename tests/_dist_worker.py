@@ -1,0 +1,41 @@
+"""One rank of the world-size-2 gloo test (run as a subprocess by tests/test_dist.py).
+
+Each rank builds the partial table of its shard of the evaluated half grid on the CPU from
+the oracle's per-point log q (standing in for the device's partial table), the ranks sum
+them with paper_2412_17742_gb300.dist.allreduce_table, and rank 0 saves the result.
+"""
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+
+import numpy as np  # noqa: E402
+import torch  # noqa: E402
+import torch.distributed as dist  # noqa: E402
+
+import oracle  # noqa: E402
+import synth  # noqa: E402
+from paper_2412_17742_gb300 import dist as gdist  # noqa: E402
+from shard_tables import partial_table_cpu  # noqa: E402
+
+
+def main():
+    rank, world = int(os.environ["RANK"]), int(os.environ["WORLD_SIZE"])
+    out = sys.argv[1]
+    dist.init_process_group("gloo", init_method="env://", rank=rank, world_size=world)
+    prob = synth.config(0)
+    logq = oracle.binned(prob)["logq"]
+    n_eval = gdist.evaluated_points(prob.cutoff)
+    begin, end = gdist.shard_range(n_eval, rank, world)
+    part = torch.from_numpy(partial_table_cpu(prob, logq, begin, end))
+    total = gdist.allreduce_table(part)
+    if rank == 0:
+        np.save(out, total.numpy())
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
