@@ -350,8 +350,8 @@ def _extra_n192(gb, torch, stream, flush, steps, world):
     # n = 192: 24 modes x 4 internal, displaced, 3 groups, 9261 points
     prob = synth.config(2)
     res = {}
-    for name, prec in (("fp32_refine", 1), ("fp64", 0)):
-        with gb.Plan(prob, precision=prec, want_timing=True) as p:
+    for name, prec, tile in (("fp32_refine", 1, 0), ("fp32_refine_tensor_core_trace", 1, 7), ("fp64", 0, 0)):
+        with gb.Plan(prob, precision=prec, want_timing=True, tile_override=tile) as p:
             t = torch.empty(p.shape, dtype=torch.float64, device="cuda")
             gb.gbsbin_execute(p.handle, t, stream)
             ms = _timed(torch, stream, flush, steps, lambda: gb.gbsbin_execute(p.handle, t, stream))

@@ -140,8 +140,10 @@ typedef enum {
   GBSBIN_KERNEL_GMEM_FP64 = 3,     /* CTA per point, matrix in an L2-resident workspace     */
   GBSBIN_KERNEL_GMEM_FP32R = 4,
   GBSBIN_KERNEL_WARP_FP32R = 5,    /* warp per point, matrix in registers (n <= 32)        */
-  GBSBIN_KERNEL_BLK_FP32R = 6      /* CTA per point, blocked (NB = 32) on an L2-resident
+  GBSBIN_KERNEL_BLK_FP32R = 6,     /* CTA per point, blocked (NB = 32) on an L2-resident
                                       slot, register-tiled updates (n <= 384)              */
+  GBSBIN_KERNEL_BLK_TC_FP32R = 7   /* as 6, the trace-correction updates on the tensor
+                                      cores (tcgen05, 3 x TF32, TMEM accumulator)         */
 } gbsbin_kernel;
 
 /* Fill *o with defaults: FP64, oversample 1, diagnostics on, automatic kernel. */

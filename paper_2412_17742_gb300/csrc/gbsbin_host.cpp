@@ -74,7 +74,7 @@ int validate_shape(const gbsbin_problem* p, const gbsbin_options* o) {
   if (!p->sigma1 && (!p->r || !p->T)) return GBSBIN_ERR_ARG;
   if (o->precision != GBSBIN_FP64 && o->precision != GBSBIN_FP32_REFINE) return GBSBIN_ERR_ARG;
   if (o->oversample < 1) return GBSBIN_ERR_ARG;
-  if (o->tile_override < 0 || o->tile_override > GBSBIN_KERNEL_BLK_FP32R) return GBSBIN_ERR_ARG;
+  if (o->tile_override < 0 || o->tile_override > GBSBIN_KERNEL_BLK_TC_FP32R) return GBSBIN_ERR_ARG;
   long long n = 2LL * p->M * p->K;
   if (n > GBSBIN_MAX_N) return GBSBIN_ERR_UNSUPPORTED;
   std::vector<int> count(p->L, 0);
@@ -418,6 +418,10 @@ int evaluate_fp64_with_factors(gbsbin_plan* P, cudaStream_t s) {
   return GBSBIN_OK;
 }
 
+// The blocked FP32 + refinement kernel, with its trace updates on the CUDA cores or on the
+// tensor cores.
+inline bool is_blk(int kernel) { return kernel == GBSBIN_KERNEL_BLK_FP32R || kernel == GBSBIN_KERNEL_BLK_TC_FP32R; }
+
 int choose_kernel(int n, int L, int precision, int override_id) {
   if (override_id) return override_id;
   if (precision == GBSBIN_FP32_REFINE && n <= 32) return GBSBIN_KERNEL_WARP_FP32R;
@@ -526,7 +530,7 @@ static int plan_create_impl(const gbsbin_problem* p, const gbsbin_options* o, gb
   record_inputs(P, p);
   P->kernel = choose_kernel(n, p->L, opt.precision, opt.tile_override);
   P->P = P->kernel == GBSBIN_KERNEL_WARP_FP32R ? (n <= 32 ? 1 : 0)
-         : P->kernel == GBSBIN_KERNEL_BLK_FP32R ? (n <= GBSBIN_BLK_MAX_N ? 1 : 0)
+         : is_blk(P->kernel) ? (n <= GBSBIN_BLK_MAX_N ? 1 : 0)
                                                  : points_per_cta(P->kernel, n, p->L);
   if (p_override > 0 && P->P > 0 && (P->kernel == GBSBIN_KERNEL_SMEM_FP64 || P->kernel == GBSBIN_KERNEL_SMEM_FP32R)) {
     if (points_smem_bytes(P->kernel, n, p_override, p->L) > 225 * 1024) {
@@ -579,12 +583,12 @@ static int plan_create_impl(const gbsbin_problem* p, const gbsbin_options* o, gb
     return st;
   }
   if (alloc_gws && (P->kernel == GBSBIN_KERNEL_GMEM_FP64 || P->kernel == GBSBIN_KERNEL_GMEM_FP32R ||
-                    P->kernel == GBSBIN_KERNEL_BLK_FP32R)) {
-    P->gws_slot_bytes = P->kernel == GBSBIN_KERNEL_BLK_FP32R ? (long long)points_blk_slot_bytes(n)
+                    is_blk(P->kernel))) {
+    P->gws_slot_bytes = is_blk(P->kernel) ? (long long)points_blk_slot_bytes(n)
                                                              : (long long)points_matrix_bytes(P->kernel, n, P->P);
     P->gws_slot_bytes = (P->gws_slot_bytes + 255) / 256 * 256;
     size_t bytes = (size_t)P->gws_slot_bytes * (size_t)P->num_sms *
-                   (P->kernel == GBSBIN_KERNEL_BLK_FP32R ? GBSBIN_BLK_CTAS_PER_SM : 1);
+                   (is_blk(P->kernel) ? GBSBIN_BLK_CTAS_PER_SM : 1);
     cudaError_t e = cudaMalloc(&P->d_gws, bytes);
     if (e != cudaSuccess) {
       cudaGetLastError();
@@ -738,7 +742,7 @@ int gbsbin_execute(gbsbin_plan* P, double* P_out, void* stream) {
   P->saved_valid = a.lu_store != nullptr;
   if (P->ev0 && cudaEventRecord(P->ev0, s) != cudaSuccess) return GBSBIN_ERR_CUDA;
   cudaError_t e = P->kernel == GBSBIN_KERNEL_WARP_FP32R  ? launch_points_warp(a, P->num_sms, s)
-                  : P->kernel == GBSBIN_KERNEL_BLK_FP32R ? launch_points_blk(a, PointBatch{}, 0, P->num_sms, s)
+                  : is_blk(P->kernel) ? launch_points_blk(a, PointBatch{}, 0, P->num_sms, s, P->kernel == GBSBIN_KERNEL_BLK_TC_FP32R)
                                                          : launch_points(a, P->kernel, P->num_sms, s);
   if (e != cudaSuccess) return GBSBIN_ERR_CUDA;
   if (P->ev1 && cudaEventRecord(P->ev1, s) != cudaSuccess) return GBSBIN_ERR_CUDA;
@@ -1023,7 +1027,10 @@ int tune_size(int n, int precision, TuneVal* best) {
   const int gmem_k = precision == GBSBIN_FP64 ? GBSBIN_KERNEL_GMEM_FP64 : GBSBIN_KERNEL_GMEM_FP32R;
   for (int Pc = 1; Pc <= 8; Pc *= 2)
     if (points_smem_bytes(smem_k, n, Pc, 1) <= 225 * 1024) cands.push_back({smem_k, Pc});
-  if (precision == GBSBIN_FP32_REFINE && n > 32 && n <= GBSBIN_BLK_MAX_N) cands.push_back({GBSBIN_KERNEL_BLK_FP32R, 1});
+  if (precision == GBSBIN_FP32_REFINE && n > 32 && n <= GBSBIN_BLK_MAX_N) {
+    cands.push_back({GBSBIN_KERNEL_BLK_FP32R, 1});
+    cands.push_back({GBSBIN_KERNEL_BLK_TC_FP32R, 1});
+  }
   cands.push_back({gmem_k, 1});
   best->us_per_point = 1e300;
   best->kernel = 0;
@@ -1045,7 +1052,7 @@ int tune_size(int n, int precision, TuneVal* best) {
     for (int rep = 0; rep < 3; ++rep) {
       cudaEventRecord(e0, 0);
       cudaError_t err = P->kernel == GBSBIN_KERNEL_WARP_FP32R  ? launch_points_warp(a, P->num_sms, 0)
-                        : P->kernel == GBSBIN_KERNEL_BLK_FP32R ? launch_points_blk(a, PointBatch{}, 0, P->num_sms, 0)
+                        : is_blk(P->kernel) ? launch_points_blk(a, PointBatch{}, 0, P->num_sms, 0, P->kernel == GBSBIN_KERNEL_BLK_TC_FP32R)
                                                                : launch_points(a, P->kernel, P->num_sms, 0);
       cudaEventRecord(e1, 0);
       if (err != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
@@ -1132,7 +1139,7 @@ int batch_launch(gbsbin_batch* B, double* const* P_out, cudaStream_t s) {
     if (cudaMemsetAsync(B->d_queue + c, 0, sizeof(unsigned long long), s) != cudaSuccess) return GBSBIN_ERR_CUDA;
     PointBatch pb{B->d_probs, C.d_jobs, (long long)C.jobs.size(), B->d_queue + c};
     cudaError_t e = C.kernel == GBSBIN_KERNEL_WARP_FP32R  ? launch_points_warp_batch(pb, C.np, B->num_sms, s)
-                    : C.kernel == GBSBIN_KERNEL_BLK_FP32R ? launch_points_blk(PointArgs{}, pb, C.smem, B->num_sms, s)
+                    : is_blk(C.kernel) ? launch_points_blk(PointArgs{}, pb, C.smem, B->num_sms, s, C.kernel == GBSBIN_KERNEL_BLK_TC_FP32R)
                                                           : launch_points_batch(pb, C.kernel, C.threads, C.smem, B->num_sms, s);
     if (e != cudaSuccess) return GBSBIN_ERR_CUDA;
   }
@@ -1204,12 +1211,12 @@ int gbsbin_batch_create(const gbsbin_problem* probs, int nprob, const gbsbin_opt
     gbsbin_plan* P = B->plans[i];
     args[i] = make_point_args(P);
     const int threads = P->kernel == GBSBIN_KERNEL_WARP_FP32R ? 128
-                        : P->kernel == GBSBIN_KERNEL_BLK_FP32R ? 256
+                        : is_blk(P->kernel) ? 256
                                                                : points_threads(P->kernel, P->n);
     // warp kernel: padded size class; blocked kernel: problems whose shared memory allows
     // two CTAs per SM run apart from the larger ones (a class launches with its largest need)
     const int np = P->kernel == GBSBIN_KERNEL_WARP_FP32R ? (P->n <= 8 ? 8 : P->n <= 16 ? 16 : 32)
-                   : P->kernel == GBSBIN_KERNEL_BLK_FP32R ? points_blk_ctas_per_sm(P->n)
+                   : is_blk(P->kernel) ? points_blk_ctas_per_sm(P->n)
                                                           : 0;
     auto key = std::make_tuple(P->kernel, threads, np);
     if (!class_of.count(key)) {
@@ -1225,10 +1232,10 @@ int gbsbin_batch_create(const gbsbin_problem* probs, int nprob, const gbsbin_opt
     if (P->kernel == GBSBIN_KERNEL_SMEM_FP64 || P->kernel == GBSBIN_KERNEL_SMEM_FP32R ||
         P->kernel == GBSBIN_KERNEL_GMEM_FP64 || P->kernel == GBSBIN_KERNEL_GMEM_FP32R)
       C.smem = std::max(C.smem, points_smem_bytes(P->kernel, P->n, P->P, P->L));
-    if (P->kernel == GBSBIN_KERNEL_BLK_FP32R) C.smem = std::max(C.smem, points_blk_smem_bytes(P->n));
+    if (is_blk(P->kernel)) C.smem = std::max(C.smem, points_blk_smem_bytes(P->n));
     if (P->kernel == GBSBIN_KERNEL_GMEM_FP64 || P->kernel == GBSBIN_KERNEL_GMEM_FP32R ||
-        P->kernel == GBSBIN_KERNEL_BLK_FP32R)
-      B->gws_slot = std::max(B->gws_slot, ((long long)(P->kernel == GBSBIN_KERNEL_BLK_FP32R
+        is_blk(P->kernel))
+      B->gws_slot = std::max(B->gws_slot, ((long long)(is_blk(P->kernel)
                                                                ? points_blk_slot_bytes(P->n)
                                                                : points_matrix_bytes(P->kernel, P->n, 1)) + 255) /
                                               256 * 256);

@@ -122,7 +122,7 @@ size_t points_blk_smem_bytes(int n);
 size_t points_blk_slot_bytes(int n);
 int points_blk_ctas_per_sm(int n);   // resident CTAs per SM that the shared memory allows (1 or 2)
 cudaError_t launch_points_blk(const PointArgs& a, const PointBatch& batch, size_t smem_batch, int num_sms,
-                              cudaStream_t s);
+                              cudaStream_t s, bool tensor_cores);
 size_t points_smem_bytes(int kernel, int n, int P, int L);
 size_t points_matrix_bytes(int kernel, int n, int P);
 int points_per_cta(int kernel, int n, int L);

@@ -18,7 +18,12 @@
 //             difference is rounded to FP32 once; 64 x 64 output blocks, digit chunks staged;
 //   trace     Z = L^^{-1} E (blocked forward substitution on all columns) and the entries
 //             X[m][c], m >= c, of X = U^^{-1} Z (blocked back substitution), delta =
-//             sum_c X[c][c];
+//             sum_c X[c][c]; the rank-32 updates of both substitutions run either on the
+//             CUDA cores (register tiles, the default) or, in the tensor-core variant, on
+//             the tensor cores (tcgen05, 3 x TF32, TMEM accumulator): they only feed the
+//             correction delta, which needs ~1e-6 relative accuracy, while the LU's own
+//             updates stay in exact FP32 on the CUDA cores (its rounding sets the
+//             refinement's remainder);
 // then the FP64 epilogue: log det = sum Log(d_i u'_ii) + delta and the refined exponent.
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -53,6 +58,16 @@ struct BlkSmem {
   int* bad;        // 1: a factor fell outside the fixed-point range
 };
 
+// Bytes of the tensor-core operand stage (A hi/lo 128 x 64 and B hi/lo 64 x 64, FP32) and
+// of the region at the start of shared memory that holds either it or panel + rowb.
+constexpr int TC_STAGE_BYTES = (2 * 128 * 64 + 2 * 64 * 64) * 4;
+__host__ __device__ __forceinline__ size_t region0_bytes(int n) {
+  const size_t R = n > EB ? n : EB;
+  const size_t pr = R * LDP * 8 + (size_t)NB * (R + 1) * 8;
+  const size_t tc = (size_t)TC_STAGE_BYTES + 128;
+  return pr > tc ? pr : tc;
+}
+
 __device__ __forceinline__ BlkSmem carve(unsigned char* smem, int n, int L) {
   BlkSmem s;
   const int R = n > EB ? n : EB;        // the residual pass stages EB-row chunks
@@ -61,7 +76,7 @@ __device__ __forceinline__ BlkSmem carve(unsigned char* smem, int n, int L) {
   f += (size_t)R * LDP;
   s.ldr = R + 1;
   s.rowb = f;
-  f += (size_t)NB * s.ldr;
+  f = (float2*)(smem + region0_bytes(n));
   s.pinv = f;
   f += n;
   s.xv = f;
@@ -127,6 +142,160 @@ struct NoMask {
 };
 
 
+// ------------------------------------------------------------ tensor cores (tcgen05)
+// C -= A B for complex A (nr x kd), B (kd x nc), kd <= 32, on the 5th-generation tensor
+// cores: realified to a real GEMM with K = 64 (A row i = [Re A_i., Im A_i.]; output column
+// 2c from B column [Re B_.c, -Im B_.c], 2c + 1 from [Im B_.c, Re B_.c]), each operand split
+// into hi + lo TF32 parts and the three products hi.hi + hi.lo + lo.hi accumulated in FP32 in
+// tensor memory (about 2^-21 relative).  Tiles: 128 rows x 64 real columns, operands staged
+// in shared memory in the K-major no-swizzle layout (8-row x 16-byte core matrices; 128 B
+// between cores along K, 2048 B between 8-row groups), one thread issues the MMAs and
+// commits them to an mbarrier that all threads wait on (bounded), tcgen05.ld brings the tile
+// back (warp w reads TMEM lanes 32 (w mod 4) .. + 31, column half w / 4).
+struct TcCtx {
+  uint32_t tmem;        // base of this CTA's 64 TMEM columns
+  uint32_t mbar;        // shared address of the completion mbarrier
+  uint32_t phase;       // parity of the next completion
+  float* stage;         // TC_STAGE_BYTES of shared memory, 128-byte aligned
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t kmajor_desc(uint32_t addr) {   // LBO 128 B, SBO 2048 B, no swizzle
+  return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(2048 >> 4) << 32) |
+         (1ull << 46);
+}
+
+__device__ __forceinline__ void tf32_split(float v, float& hi, float& lo) {
+  uint32_t h;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(v));
+  hi = __uint_as_float(h);
+  lo = v - hi;
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase) {
+  for (long long it = 0; it < (1ll << 26); ++it) {
+    uint32_t done;
+    asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(done) : "r"(mbar), "r"(phase) : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// C[i * ldc + j] -= sum_k Ag[i * lda + k] Bg[k * ldb + j], i < nr, j < nc, k < kd <= 32.
+// Called by the whole CTA; returns false if a completion wait gave up.
+__device__ bool tc_sub_gemm(float2* C, int ldc, int nr, int nc, const float2* Ag, int lda, const float2* Bg, int ldb,
+                            int kd, TcCtx& tc) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  float* Ahi = tc.stage;
+  float* Alo = Ahi + 128 * 64;
+  float* Bhi = Alo + 128 * 64;
+  float* Blo = Bhi + 64 * 64;
+  const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(64 >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+  bool ok = true;
+  for (int i0 = 0; i0 < nr; i0 += 128) {
+    // A tile: complex element (r, k) -> real (r, k) = Re, (r, k + 32) = Im.  A warp takes one
+    // 8 x 4 block of complex elements (eight 32-byte row segments), so its stores fill whole
+    // 128-byte core matrices; every thread issues its 16 loads before any store.
+    {
+      float2 v[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const int e = tid + NT * q, cc = e >> 5, w = e & 31;
+        const int r = (cc >> 3) * 8 + (w >> 2), k = (cc & 7) * 4 + (w & 3);
+        v[q] = (i0 + r < nr && k < kd) ? Ag[(size_t)(i0 + r) * lda + k] : make_float2(0.0f, 0.0f);
+      }
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const int e = tid + NT * q, cc = e >> 5, w = e & 31;
+        const int fre = (((cc >> 3) * 16 + (cc & 7)) << 5) + w;   // float index of (r, k)
+        tf32_split(v[q].x, Ahi[fre], Alo[fre]);
+        tf32_split(v[q].y, Ahi[fre + 8 * 32], Alo[fre + 8 * 32]);  // (r, k + 32): 8 cores on
+      }
+    }
+    for (int j0 = 0; j0 < 2 * nc; j0 += 64) {
+      // B tile (real rows jr = 2c' + part of the 32 complex columns c' of this tile):
+      // B(k, c) -> (2c', k) = Re, (2c', k + 32) = -Im, (2c' + 1, k) = Im, (2c' + 1, k + 32) = Re.
+      // A warp takes 8 k x 4 columns; loads first, then stores.
+      {
+        float2 v[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int e = tid + NT * q, grp = e >> 5, w = e & 31;
+          const int cp = (grp & 7) * 4 + (w >> 3), k = (grp >> 3) * 8 + (w & 7), c = (j0 >> 1) + cp;
+          v[q] = (c < nc && k < kd) ? Bg[(size_t)k * ldb + c] : make_float2(0.0f, 0.0f);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int e = tid + NT * q, grp = e >> 5, w = e & 31;
+          const int cp = (grp & 7) * 4 + (w >> 3), k = (grp >> 3) * 8 + (w & 7);
+#pragma unroll
+          for (int part = 0; part < 2; ++part) {
+            const int jr = 2 * cp + part;
+            const int f0 = (((jr >> 3) * 16 + (k >> 2)) << 5) + ((jr & 7) << 2) + (k & 3);   // (jr, k)
+            const float lo_k = part ? v[q].y : v[q].x;        // K index k
+            const float hi_k = part ? v[q].x : -v[q].y;       // K index k + 32
+            tf32_split(lo_k, Bhi[f0], Blo[f0]);
+            tf32_split(hi_k, Bhi[f0 + 8 * 32], Blo[f0 + 8 * 32]);
+          }
+        }
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncthreads();
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      if (tid == 0) {
+        const float* As[3] = {Ahi, Ahi, Alo};
+        const float* Bs[3] = {Bhi, Blo, Bhi};
+        uint32_t acc = 0;
+#pragma unroll
+        for (int p = 0; p < 3; ++p)
+#pragma unroll
+          for (int ks = 0; ks < 8; ++ks) {        // K = 8 per instruction: two cores along K
+            const uint64_t da = kmajor_desc(smem_u32(As[p]) + ks * 256);
+            const uint64_t db = kmajor_desc(smem_u32(Bs[p]) + ks * 256);
+            asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                         "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(tc.tmem),
+                         "l"(da), "l"(db), "r"(idesc), "r"(acc));
+            acc = 1;
+          }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(tc.mbar)
+                     : "memory");
+      }
+      ok &= mbar_wait(tc.mbar, tc.phase);
+      tc.phase ^= 1u;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int row = i0 + 32 * (warp & 3) + lane;
+      const int cbase = (j0 >> 1) + (warp >> 2) * 16;   // complex column of this warp's half
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        uint32_t r[16];
+        const uint32_t ta = tc.tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)((warp >> 2) * 32 + 16 * h);
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                     : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                       "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                       "=r"(r[15])
+                     : "r"(ta));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (row < nr) {
+          float2* crow = C + (size_t)row * ldc + cbase + 8 * h;
+          const int nv = min(8, nc - (cbase + 8 * h));
+          float2 cv[8];
+#pragma unroll
+          for (int q = 0; q < 8; ++q) cv[q] = q < nv ? crow[q] : make_float2(0.0f, 0.0f);
+#pragma unroll
+          for (int q = 0; q < 8; ++q)
+            if (q < nv) crow[q] = make_float2(cv[q].x - __uint_as_float(r[2 * q]), cv[q].y - __uint_as_float(r[2 * q + 1]));
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncthreads();
+    }
+  }
+  return ok;
+}
+
 // v <- U^^{-1} L^^{-1} v for one right-hand side v (shared memory, n entries), with L\U
 // in global memory (unit lower L) and pinv[k] = 1 / u_kk, by the whole CTA: per 32-row
 // block, warp 0 solves the diagonal block with shuffles and all threads apply the
@@ -185,7 +354,8 @@ __device__ __forceinline__ void cta_solve_lu(const float2* A, int n, const float
 
 }  // namespace
 
-__device__ void group_fp32r_blk(const PointArgs& a, const long long e, unsigned char* smem) {
+template <bool TC>
+__device__ void group_fp32r_blk(const PointArgs& a, const long long e, unsigned char* smem, TcCtx& tc) {
   const int n = a.n, L = a.grid.L, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   BlkSmem sm = carve(smem, n, L);
   float2* A = (float2*)((char*)a.gws + (size_t)blockIdx.x * (size_t)a.gws_slot_bytes);
@@ -419,13 +589,19 @@ __device__ void group_fp32r_blk(const PointArgs& a, const long long e, unsigned 
         }
     }
     __syncthreads();
-    if (m > 0) {
-      for (int t = tid; t < m * nb; t += NT) {     // L21 into the panel stage
-        const int r = t / nb, c = t - r * nb;
-        sm.panel[r * LDP + c] = A[(size_t)(k0 + nb + r) * n + k0 + c];
+    if (m > 0) {                                   // E[rows below] -= L21 Z1
+      if constexpr (TC) {
+        const bool ok = tc_sub_gemm(E + (size_t)(k0 + nb) * n, n, m, n, A + (size_t)(k0 + nb) * n + k0, n,
+                                    E + (size_t)k0 * n, n, nb, tc);
+        if (!ok) *sm.bad = 1;
+      } else {
+        for (int t = tid; t < m * nb; t += NT) {   // L21 into the panel stage
+          const int r = t / nb, c = t - r * nb;
+          sm.panel[r * LDP + c] = A[(size_t)(k0 + nb + r) * n + k0 + c];
+        }
+        __syncthreads();
+        tile_update(E, n, k0 + nb, 0, m, n, sm.panel, sm.rowb, sm.ldr, nb, NoMask());
       }
-      __syncthreads();
-      tile_update(E, n, k0 + nb, 0, m, n, sm.panel, sm.rowb, sm.ldr, nb, NoMask());
     }
     __syncthreads();
   }
@@ -459,14 +635,20 @@ __device__ void group_fp32r_blk(const PointArgs& a, const long long e, unsigned 
         }
     }
     __syncthreads();
-    if (k0 > 0) {
-      for (int t = tid; t < k0 * nb; t += NT) {     // U01 (rows above the block) into the stage
-        const int r = t / nb, c = t - r * nb;
-        sm.panel[r * LDP + c] = A[(size_t)r * n + k0 + c];
+    if (k0 > 0) {                                   // E[rows above][c < k0] -= U01 X1
+      if constexpr (TC) {
+        // only the entries c <= row are needed (the others are never read): the tensor
+        // cores update the whole square
+        const bool ok = tc_sub_gemm(E, n, k0, k0, A + k0, n, E + (size_t)k0 * n, n, nb, tc);
+        if (!ok) *sm.bad = 1;
+      } else {
+        for (int t = tid; t < k0 * nb; t += NT) {   // U01 (rows above the block) into the stage
+          const int r = t / nb, c = t - r * nb;
+          sm.panel[r * LDP + c] = A[(size_t)r * n + k0 + c];
+        }
+        __syncthreads();
+        tile_update(E, n, 0, 0, k0, k0, sm.panel, sm.rowb, sm.ldr, nb, [](int i, int j) { return j <= i; });
       }
-      __syncthreads();
-      // rows i < k0 need columns c <= i only
-      tile_update(E, n, 0, 0, k0, k0, sm.panel, sm.rowb, sm.ldr, nb, [](int i, int j) { return j <= i; });
     }
     __syncthreads();
   }
@@ -559,58 +741,86 @@ __device__ void group_fp32r_blk(const PointArgs& a, const long long e, unsigned 
   __syncthreads();
 }
 
+template <bool TC>
 __global__ void __launch_bounds__(NT, CTAS_PER_SM) k_points_fp32r_blk(PointArgs a0, PointBatch batch) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  if (!batch.probs) {
-    for (long long e = blockIdx.x; e < a0.grid.n_eval; e += gridDim.x) group_fp32r_blk(a0, e, smem);
-    return;
-  }
-  __shared__ PointArgs sa;
-  __shared__ long long sj;
-  for (;;) {
-    if (threadIdx.x == 0) {
-      const unsigned long long j = atomicAdd(batch.queue, 1ull);
-      sj = (long long)j;
-      if ((long long)j < batch.njobs) sa = batch.probs[batch.jobs[j].prob];
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) unsigned long long s_mbar;
+  __shared__ uint32_t s_tmem;
+  TcCtx tc{0u, 0u, 0u, nullptr};
+  if constexpr (TC) {
+    // 64 columns of tensor memory for the accumulator and the completion mbarrier, per CTA;
+    // the allocation permit is given up at once so that the SM's other CTA can allocate too
+    if (threadIdx.x < 32) {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(smem_u32(&s_tmem)));
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
+    if (threadIdx.x == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_mbar)));
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    const long long j = sj;
-    if (j >= batch.njobs) break;
-    group_fp32r_blk(sa, batch.jobs[j].e0, smem);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    tc = TcCtx{s_tmem, smem_u32(&s_mbar), 0u, (float*)(((uintptr_t)smem + 127) & ~(uintptr_t)127)};
+  }
+  if (!batch.probs) {
+    for (long long e = blockIdx.x; e < a0.grid.n_eval; e += gridDim.x) group_fp32r_blk<TC>(a0, e, smem, tc);
+  } else {
+    __shared__ PointArgs sa;
+    __shared__ long long sj;
+    for (;;) {
+      if (threadIdx.x == 0) {
+        const unsigned long long j = atomicAdd(batch.queue, 1ull);
+        sj = (long long)j;
+        if ((long long)j < batch.njobs) sa = batch.probs[batch.jobs[j].prob];
+      }
+      __syncthreads();
+      const long long j = sj;
+      if (j >= batch.njobs) break;
+      group_fp32r_blk<TC>(sa, batch.jobs[j].e0, smem, tc);
+      __syncthreads();
+    }
+  }
+  if constexpr (TC) {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
+    if (threadIdx.x < 32) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(s_tmem));
   }
 }
 
 size_t points_blk_smem_bytes(int n) {
-  const size_t R = n > EB ? n : EB;
-  return R * LDP * 8 + (size_t)NB * (R + 1) * 8 + (size_t)3 * n * 8 + 16 + (size_t)GBSBIN_MAX_L * 16 +
-         (size_t)(NT / 32) * 32 + (size_t)3 * n * 4 + 16;
+  return region0_bytes(n) + (size_t)3 * n * 8 + 16 + (size_t)GBSBIN_MAX_L * 16 + (size_t)(NT / 32) * 32 +
+         (size_t)3 * n * 4 + 16;
 }
 
 // One CTA's workspace slot: L\U (float2) and the residual (float2; the integer digits of
 // the rounded factors before it), n x n each.  The workspace holds
 // GBSBIN_BLK_CTAS_PER_SM slots per SM.
-int points_blk_ctas_per_sm(int n) {
-  // 228 KB of shared memory per SM, 1 KB of it reserved per resident CTA
-  return 2 * (points_blk_smem_bytes(n) + 1024) <= 228 * 1024 ? GBSBIN_BLK_CTAS_PER_SM : 1;
+// Resident CTAs per SM for a dynamic shared-memory size: 228 KB per SM, 1 KB reserved per
+// CTA, ~1 KB of static shared memory; registers allow two (__launch_bounds__(256, 2)), and
+// two CTAs hold 2 x 64 of the 512 TMEM columns.  (The occupancy calculator answers 1 for
+// any kernel with tcgen05 instructions, so it is not used here; measured on GB300: two such
+// CTAs per SM, each holding TMEM after relinquishing the allocation permit, run together.)
+static int blk_ctas_for_smem(size_t smem) {
+  return 2 * (smem + 2048) <= 228 * 1024 ? GBSBIN_BLK_CTAS_PER_SM : 1;
 }
+
+int points_blk_ctas_per_sm(int n) { return blk_ctas_for_smem(points_blk_smem_bytes(n)); }
 
 size_t points_blk_slot_bytes(int n) { return ((size_t)16 * n * n + 255) / 256 * 256; }
 
 cudaError_t launch_points_blk(const PointArgs& a, const PointBatch& batch, size_t smem_batch, int num_sms,
-                              cudaStream_t s) {
+                              cudaStream_t s, bool tensor_cores) {
   const size_t smem = batch.probs ? smem_batch : points_blk_smem_bytes(a.n);
-  cudaError_t err = cudaFuncSetAttribute(k_points_fp32r_blk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const void* fn = tensor_cores ? (const void*)k_points_fp32r_blk<true> : (const void*)k_points_fp32r_blk<false>;
+  cudaError_t err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
-  int per_sm = 0;
-  err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_points_fp32r_blk, NT, smem);
-  if (err != cudaSuccess) return err;
-  per_sm = per_sm < 1 ? 1 : per_sm > GBSBIN_BLK_CTAS_PER_SM ? GBSBIN_BLK_CTAS_PER_SM : per_sm;
+  const int per_sm = blk_ctas_for_smem(smem);
   long long grid = (long long)num_sms * per_sm;  // one workspace slot per CTA
   const long long work = batch.probs ? batch.njobs : a.grid.n_eval;
   if (grid > work) grid = work;
   if (grid < 1) grid = 1;
-  k_points_fp32r_blk<<<(unsigned)grid, NT, smem, s>>>(a, batch);
+  if (tensor_cores)
+    k_points_fp32r_blk<true><<<(unsigned)grid, NT, smem, s>>>(a, batch);
+  else
+    k_points_fp32r_blk<false><<<(unsigned)grid, NT, smem, s>>>(a, batch);
   return cudaGetLastError();
 }
 

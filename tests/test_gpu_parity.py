@@ -108,7 +108,7 @@ def test_global_workspace_kernel_matches(cuda_lib, precision):
     assert np.abs(Pf - Ps).max() < 1e-13
 
 
-@pytest.mark.parametrize("kernel", [2, 4, 5, 6])
+@pytest.mark.parametrize("kernel", [2, 4, 5, 6, 7])
 def test_fp32r_kernel_variants_agree(cuda_lib, kernel):
     # every FP32 + refinement variant (CTA/shared memory, CTA/workspace, warp/registers)
     # meets the bound on the same small problems
@@ -121,16 +121,18 @@ def test_fp32r_kernel_variants_agree(cuda_lib, kernel):
         assert np.abs(P - ref).max() <= TOL[1]
 
 
+@pytest.mark.parametrize("kernel", [6, 7])
 @pytest.mark.parametrize("M,K,displaced", [(17, 1, True), (32, 1, False), (49, 1, True), (48, 3, True),
-                                           (192, 1, True)])
-def test_blocked_kernel_sizes(cuda_lib, M, K, displaced):
-    # the blocked kernel (32-wide panels, 64 x 64 residual blocks) at n = 34 (one panel and a
-    # 2-row tail), 64 (exact panels), 98 (ragged panel and residual block), 288 (largest n
-    # of the batched workload, internal modes) and 384 (its largest supported n)
+                                           (70, 1, True), (192, 1, True)])
+def test_blocked_kernel_sizes(cuda_lib, M, K, displaced, kernel):
+    # the blocked kernel (32-wide panels, 64 x 32 residual blocks), trace updates on the CUDA
+    # cores (6) or the tensor cores (7, 128 x 64 tiles), at n = 34 (one panel and a 2-row
+    # tail), 64 (exact panels), 98 (ragged panel and residual block), 140 (two tensor M-tiles),
+    # 288 (largest n of the batched workload, internal modes) and 384 (largest supported n)
     rng = np.random.default_rng(140 + M + K)
     prob = synth.random_problem(rng, M, K, 2, [2, 1], displaced=displaced, internal_basis=K > 1)
-    P, st, d, lq, mp = gpu_table(cuda_lib, prob, 1, tile_override=6)
-    assert st == 0 and d["kernel_name"] == "blk_fp32r" and d["n_bad_points"] == 0
+    P, st, d, lq, mp = gpu_table(cuda_lib, prob, 1, tile_override=kernel)
+    assert st == 0 and d["kernel"] == kernel and d["n_bad_points"] == 0
     ref, res = oracle_table(prob)
     assert np.abs(P - ref).max() <= TOL[1]
     dig = cuda_lib.evaluated_point_digits(prob.cutoff)
@@ -227,3 +229,15 @@ def test_errors_are_reported(cuda_lib):
     assert e.value.status == 3
     with gb.Plan(prob) as p:
         assert gb.gbsbin_plan_table_size(p.handle) == 49
+
+
+def test_tensor_core_trace_full_size(cuda_lib):
+    # n = 192 (displaced, internal modes): the trace updates on the tensor cores (3 x TF32)
+    # give the same table as on the CUDA cores and as the FP64 path
+    prob = synth.config(2)
+    P6, st6, *_ = gpu_table(cuda_lib, prob, 1, tile_override=6)
+    P7, st7, d7, *_ = gpu_table(cuda_lib, prob, 1, tile_override=7)
+    P64, *_ = gpu_table(cuda_lib, prob, 0)
+    assert st6 == 0 and st7 == 0 and d7["kernel_name"] == "blk_tc_fp32r"
+    assert np.abs(P7 - P6).max() < 1e-10
+    assert np.abs(P7 - P64).max() < 1e-10
