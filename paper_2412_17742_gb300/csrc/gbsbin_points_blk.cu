@@ -495,33 +495,33 @@ __device__ void group_fp32r_blk(const PointArgs& a, const long long e, unsigned 
         for (int kc = 0; kc < kmax; kc += NB) {
           const int kd = min(NB, kmax - kc);
           __syncthreads();
+          // the stages hold zero digits off the factors' triangles (L_ik needs k < i, U_kj
+          // needs k <= j), so the multiply-add loop below needs no masks
           for (int t = tid; t < EB * NB; t += NT) {
             const int r = t / NB, c = t - r * NB;
-            Ls[r * LDP + c] = (r < ni && c < kd) ? Q[(size_t)(i0 + r) * n + kc + c] : make_int2(0, 0);
+            Ls[r * LDP + c] = (r < ni && c < kd && kc + c < i0 + r) ? Q[(size_t)(i0 + r) * n + kc + c] : make_int2(0, 0);
           }
           for (int t = tid; t < NB * EBJ; t += NT) {
             const int rr = t / EBJ, cc = t - rr * EBJ;
-            Us[rr * sm.ldr + cc] = (rr < kd && cc < nj) ? Q[(size_t)(kc + rr) * n + j0 + cc] : make_int2(0, 0);
+            Us[rr * sm.ldr + cc] =
+                (rr < kd && cc < nj && kc + rr <= j0 + cc) ? Q[(size_t)(kc + rr) * n + j0 + cc] : make_int2(0, 0);
           }
           __syncthreads();
 #pragma unroll 2
           for (int k = 0; k < kd; ++k) {
-            const int kg = kc + k;
             int lx[4], ly[4], ls[4], ux[2], uy[2], us[2];
 #pragma unroll
             for (int p = 0; p < 4; ++p) {
               const int2 v = Ls[(ti + p) * LDP + k];
-              const bool ok = kg < i0 + ti + p;    // k < i: L_ik is a multiplier
-              lx[p] = ok ? v.x : 0;
-              ly[p] = ok ? v.y : 0;
+              lx[p] = v.x;
+              ly[p] = v.y;
               ls[p] = lx[p] + ly[p];
             }
 #pragma unroll
             for (int q = 0; q < 2; ++q) {
               const int2 v = Us[k * sm.ldr + tj + 16 * q];
-              const bool ok = kg <= j0 + tj + 16 * q;   // k <= j: U_kj is in the upper factor
-              ux[q] = ok ? v.x : 0;
-              uy[q] = ok ? v.y : 0;
+              ux[q] = v.x;
+              uy[q] = v.y;
               us[q] = ux[q] + uy[q];
             }
 #pragma unroll
@@ -622,8 +622,10 @@ __device__ void group_fp32r_blk(const PointArgs& a, const long long e, unsigned 
 #pragma unroll
       for (int r = NB - 1; r >= 0; --r) {
         if (r >= nb) continue;
+        // q descending: the terms of the longest-finished unknowns first, so the chain of
+        // col[r] does not start on col[r + 1], which was finished just before
 #pragma unroll
-        for (int q = r + 1; q < NB; ++q)
+        for (int q = NB - 1; q > r; --q)
           if (q < nb) col[r] = cfnmaf(col[r], sm.panel[r * LDP + q], col[q]);
         col[r] = cmulf(col[r], sm.pinv[k0 + r]);
       }
@@ -671,25 +673,43 @@ __device__ void group_fp32r_blk(const PointArgs& a, const long long e, unsigned 
     for (int i = tid; i < n; i += NT) x[i] = a.Xg_hi[i];
     __syncthreads();
     cta_solve_lu(A, n, sm.pinv, x);
-    // r = X gamma - M x^ by Dot2, a thread per row
+    // r = X gamma - M x^ by Dot2, a thread per row; four independent accumulator pairs over
+    // interleaved j keep the dependent chains a quarter as long
     for (int i = tid; i < n; i += NT) {
-      Acc2 sr = {0.0f, 0.0f}, si = {0.0f, 0.0f};
+      Acc2 ar[4], ai[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) ar[u] = ai[u] = Acc2{0.0f, 0.0f};
+      for (int j0 = 0; j0 < n; j0 += 4) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int j = j0 + u;
+          if (j < n) {
+            const float2 xh = a.NXA_hi[(size_t)i * n + j], xl = a.NXA_lo[(size_t)i * n + j], y = x[j];
+            acc2_add_prod(ar[u], -xh.x, y.x);
+            acc2_add_prod(ar[u], xh.y, y.y);
+            acc2_add_prod(ar[u], -xl.x, y.x);
+            acc2_add_prod(ar[u], xl.y, y.y);
+            acc2_add_prod(ai[u], -xh.x, y.y);
+            acc2_add_prod(ai[u], -xh.y, y.x);
+            acc2_add_prod(ai[u], -xl.x, y.y);
+            acc2_add_prod(ai[u], -xl.y, y.x);
+          }
+        }
+      }
+      // combine the pairs (each partial sum s + c exactly as accumulated)
+      Acc2 sr = ar[0], si = ai[0];
+#pragma unroll
+      for (int u = 1; u < 4; ++u) {
+        acc2_add(sr, ar[u].s);
+        sr.c += ar[u].c;
+        acc2_add(si, ai[u].s);
+        si.c += ai[u].c;
+      }
       const float2 gh = a.Xg_hi[i], gl = a.Xg_lo[i];
       acc2_add(sr, gh.x);
       acc2_add(sr, gl.x);
       acc2_add(si, gh.y);
       acc2_add(si, gl.y);
-      for (int j = 0; j < n; ++j) {
-        const float2 xh = a.NXA_hi[(size_t)i * n + j], xl = a.NXA_lo[(size_t)i * n + j], y = x[j];
-        acc2_add_prod(sr, -xh.x, y.x);
-        acc2_add_prod(sr, xh.y, y.y);
-        acc2_add_prod(sr, -xl.x, y.x);
-        acc2_add_prod(sr, xl.y, y.y);
-        acc2_add_prod(si, -xh.x, y.y);
-        acc2_add_prod(si, -xh.y, y.x);
-        acc2_add_prod(si, -xl.x, y.y);
-        acc2_add_prod(si, -xl.y, y.x);
-      }
       const double2 d = sm.w[sm.lab[i]];
       const float dhx = (float)d.x, dhy = (float)d.y;
       const float dlx = (float)(d.x - (double)dhx), dly = (float)(d.y - (double)dhy);
