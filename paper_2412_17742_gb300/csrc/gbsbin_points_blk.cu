@@ -384,19 +384,41 @@ __device__ void group_fp32r_blk(const PointArgs& a, const long long e, unsigned 
       sm.panel[i * LDP + c] = A[(size_t)(k0 + i) * n + k0 + c];
     }
     __syncthreads();
-    for (int kk = 0; kk < nb; ++kk) {          // unblocked LU of the panel
-      const float2 inv = crecipf(sm.panel[kk * LDP + kk]);
-      if (tid == 0) sm.pinv[k0 + kk] = inv;
-      for (int i = kk + 1 + tid; i < rows; i += NT) sm.panel[i * LDP + kk] = cmulf(sm.panel[i * LDP + kk], inv);
-      __syncthreads();
-      const int cols = nb - kk - 1;
-      if (cols > 0)
-        for (int t = tid; t < (rows - kk - 1) * cols; t += NT) {
-          const int i = kk + 1 + t / cols, c = kk + 1 + (t - (t / cols) * cols);
-          sm.panel[i * LDP + c] = cfnmaf(sm.panel[i * LDP + c], sm.panel[i * LDP + kk], sm.panel[kk * LDP + c]);
+    // panel LU in two steps with two CTA barriers instead of two per column: warp 0
+    // factorizes the nb x nb diagonal block (lane i owns row i, warp syncs only), then each
+    // thread takes one row i below it and solves l_ik = (a_ik - sum_{q<k} l_iq u_qk) / u_kk
+    // in registers against U11 (the same elimination, left-looking for L21)
+    if (warp == 0) {
+      for (int kk = 0; kk < nb; ++kk) {
+        const float2 inv = crecipf(sm.panel[kk * LDP + kk]);
+        if (lane == 0) sm.pinv[k0 + kk] = inv;
+        if (lane > kk && lane < nb) {
+          const float2 l = cmulf(sm.panel[lane * LDP + kk], inv);
+          sm.panel[lane * LDP + kk] = l;
+          for (int c = kk + 1; c < nb; ++c)
+            sm.panel[lane * LDP + c] = cfnmaf(sm.panel[lane * LDP + c], l, sm.panel[kk * LDP + c]);
         }
-      __syncthreads();
+        __syncwarp();
+      }
     }
+    __syncthreads();
+    for (int i = nb + tid; i < rows; i += NT) {
+      float2 row[NB];
+#pragma unroll
+      for (int c = 0; c < NB; ++c) row[c] = c < nb ? sm.panel[i * LDP + c] : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int k = 0; k < NB; ++k) {
+        if (k >= nb) continue;
+        float2 acc = row[k];
+#pragma unroll
+        for (int q = 0; q < k; ++q) acc = cfnmaf(acc, row[q], sm.panel[q * LDP + k]);
+        row[k] = cmulf(acc, sm.pinv[k0 + k]);
+      }
+#pragma unroll
+      for (int c = 0; c < NB; ++c)
+        if (c < nb) sm.panel[i * LDP + c] = row[c];
+    }
+    __syncthreads();
     for (int t = tid; t < rows * nb; t += NT) {
       const int i = t / nb, c = t - i * nb;
       A[(size_t)(k0 + i) * n + k0 + c] = sm.panel[i * LDP + c];
