@@ -27,7 +27,7 @@ __device__ __forceinline__ float2 cfnmaf(float2 a, float2 b, float2 c) {
   return make_float2(fmaf(-b.x, c.x, fmaf(b.y, c.y, a.x)), fmaf(-b.x, c.y, fmaf(-b.y, c.x, a.y)));
 }
 __device__ __forceinline__ float2 crecipf(float2 a) {
-  float s = 1.0f / fmaf(a.x, a.x, a.y * a.y);
+  float s = __frcp_rn(fmaf(a.x, a.x, a.y * a.y));   // correctly rounded, as 1.0f / x
   return make_float2(a.x * s, -a.y * s);
 }
 

@@ -106,12 +106,20 @@ __device__ __forceinline__ void warp_point(const PointArgs& a, const long long e
 #pragma unroll
         for (int ra = 0; ra < RA; ++ra)
           if (8 * ra + 7 >= 4 * kb && lc == kc && lr + 8 * ra > k) A[ra][kb] = cmulf(A[ra][kb], inv);
+        // the multipliers of rows <= k and the pivot-row entries of columns <= k are
+        // broadcast as zero, which leaves those entries exactly unchanged (a - 0 u = a):
+        // one select per broadcast value instead of one per updated entry
         float2 l[RA], u[CB];
 #pragma unroll
-        for (int ra = 0; ra < RA; ++ra)
-          l[ra] = (8 * ra + 7 < 4 * kb) ? zero : shfl2(A[ra][kb], lr * 4 + kc);
+        for (int ra = 0; ra < RA; ++ra) {
+          const float2 v = (8 * ra + 7 < 4 * kb) ? zero : shfl2(A[ra][kb], lr * 4 + kc);
+          l[ra] = lr + 8 * ra > k ? v : zero;
+        }
 #pragma unroll
-        for (int cb = 0; cb < CB; ++cb) u[cb] = (cb < kb) ? zero : shfl2(A[ka][cb], kr * 4 + lc);
+        for (int cb = 0; cb < CB; ++cb) {
+          const float2 v = (cb < kb) ? zero : shfl2(A[ka][cb], kr * 4 + lc);
+          u[cb] = lc + 4 * cb > k ? v : zero;
+        }
 #pragma unroll
         for (int ra = 0; ra < RA; ++ra) {
           if (8 * ra + 7 < 4 * kb) continue;
@@ -119,8 +127,7 @@ __device__ __forceinline__ void warp_point(const PointArgs& a, const long long e
 #pragma unroll
           for (int cb = 0; cb < CB; ++cb) {
             if (cb < kb) continue;
-            const float2 nv = cfnmaf(A[ra][cb], l[ra], u[cb]);
-            if (lr + 8 * ra > k && lc + 4 * cb > k) A[ra][cb] = nv;
+            A[ra][cb] = cfnmaf(A[ra][cb], l[ra], u[cb]);
           }
         }
       }
@@ -298,8 +305,10 @@ __device__ __forceinline__ void warp_point(const PointArgs& a, const long long e
         if (k == NP - 1) break;
         float2 l[RA], z[CB];
 #pragma unroll
-        for (int ra = 0; ra < RA; ++ra)
-          l[ra] = (8 * ra + 7 < 4 * kb) ? zero : shfl2(A[ra][kb], lr * 4 + kc);
+        for (int ra = 0; ra < RA; ++ra) {       // zero multiplier for rows <= k
+          const float2 v = (8 * ra + 7 < 4 * kb) ? zero : shfl2(A[ra][kb], lr * 4 + kc);
+          l[ra] = lr + 8 * ra > k ? v : zero;
+        }
 #pragma unroll
         for (int cb = 0; cb < CB; ++cb) z[cb] = shfl2(Z[ka][cb], kr * 4 + lc);
 #pragma unroll
@@ -307,10 +316,7 @@ __device__ __forceinline__ void warp_point(const PointArgs& a, const long long e
           if (8 * ra + 7 < 4 * kb) continue;
           if (8 * ra + 7 <= k) continue;
 #pragma unroll
-          for (int cb = 0; cb < CB; ++cb) {
-            const float2 nv = cfnmaf(Z[ra][cb], l[ra], z[cb]);
-            if (lr + 8 * ra > k) Z[ra][cb] = nv;
-          }
+          for (int cb = 0; cb < CB; ++cb) Z[ra][cb] = cfnmaf(Z[ra][cb], l[ra], z[cb]);
         }
       }
     }
@@ -328,7 +334,10 @@ __device__ __forceinline__ void warp_point(const PointArgs& a, const long long e
         if (k == 0) break;
         float2 uk[RA], x[CB];
 #pragma unroll
-        for (int ra = 0; ra < RA; ++ra) uk[ra] = (8 * ra > 4 * kb + 3) ? zero : shfl2(A[ra][kb], lr * 4 + kc);
+        for (int ra = 0; ra < RA; ++ra) {       // zero U entry for rows >= k
+          const float2 v = (8 * ra > 4 * kb + 3) ? zero : shfl2(A[ra][kb], lr * 4 + kc);
+          uk[ra] = lr + 8 * ra < k ? v : zero;
+        }
 #pragma unroll
         for (int cb = 0; cb < CB; ++cb) x[cb] = (cb > kb) ? zero : shfl2(Z[ka][cb], kr * 4 + lc);
 #pragma unroll
@@ -338,8 +347,7 @@ __device__ __forceinline__ void warp_point(const PointArgs& a, const long long e
 #pragma unroll
           for (int cb = 0; cb < CB; ++cb) {
             if (cb > kb) continue;
-            const float2 nv = cfnmaf(Z[ra][cb], uk[ra], x[cb]);
-            if (lr + 8 * ra < k) Z[ra][cb] = nv;
+            Z[ra][cb] = cfnmaf(Z[ra][cb], uk[ra], x[cb]);
           }
         }
       }
