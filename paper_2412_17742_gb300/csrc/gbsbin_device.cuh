@@ -31,29 +31,32 @@ __device__ __forceinline__ float2 crecipf(float2 a) {
   return make_float2(a.x * s, -a.y * s);
 }
 
-// exp(2 pi i m / R) from the exact integer index m (no accumulated angle).
-__device__ __forceinline__ double2 root_of_unity(long long m, int R) {
-  long long r = m % R;
-  if (r < 0) r += R;
-  double s, c;
-  sincospi(2.0 * (double)r / (double)R, &s, &c);
-  return make_double2(c, s);
-}
-
 // Half-grid index of a plan's evaluated point e: a shard evaluates point 0 first, then its
 // slice [e_lo, e_hi).
 __device__ __forceinline__ long long global_point(long long e, const GridDesc& g) {
   return g.e_lo > 0 ? (e == 0 ? 0 : e - 1 + g.e_lo) : e;
 }
 
-// Digit l of evaluated point e: last axis in [0, half), the others full radix.
-__device__ __forceinline__ int point_digit(long long e, const GridDesc& g, int l) {
-  e = global_point(e, g);
-  int last = (int)(e % g.half);
+// Digit l of evaluated point e: last axis in [0, half), the others full radix.  32-bit
+// arithmetic (grids hold at most GBSBIN_MAX_POINTS = 2^26 points): 64-bit division would
+// expand to a long instruction sequence.
+__device__ __forceinline__ int point_digit(long long e64, const GridDesc& g, int l) {
+  const int e = (int)global_point(e64, g);
+  const int last = e % g.half;
   if (l == g.L - 1) return last;
-  long long rest = e / g.half;
+  int rest = e / g.half;
   for (int m = g.L - 2; m > l; --m) rest /= g.radix[m];
-  return (int)(rest % g.radix[l]);
+  return rest % g.radix[l];
+}
+
+// w_l = exp(2 pi i k / R_l) for digit k of axis l, from the plan's twiddle table tw (the
+// exact-index values exp(-2 pi i m / R_l), m < R_l, axis after axis): a load instead of an
+// FP64 sincospi per point.
+__device__ __forceinline__ double2 grid_root(const double2* tw, const GridDesc& g, int l, int k) {
+  int off = 0;
+  for (int m = 0; m < l; ++m) off += g.radix[m];
+  const double2 t = tw[off + k];
+  return make_double2(t.x, -t.y);
 }
 
 __device__ __forceinline__ double warp_sum_d(double v) {

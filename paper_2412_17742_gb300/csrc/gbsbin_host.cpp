@@ -404,6 +404,7 @@ int evaluate_fp64_with_factors(gbsbin_plan* P, cudaStream_t s) {
   a.g_hi = P->d_g_hi;
   a.g_lo = P->d_g_lo;
   a.label = P->d_label;
+  a.tw = P->d_tw;
   a.grid = P->grid;
   a.logq = P->d_logq;
   a.minpiv = P->d_minpiv;
@@ -707,6 +708,7 @@ static PointArgs make_point_args(gbsbin_plan* P) {
   a.g_hi = P->d_g_hi;
   a.g_lo = P->d_g_lo;
   a.label = P->d_label;
+  a.tw = P->d_tw;
   a.grid = P->grid;
   a.logq = P->d_logq;
   a.minpiv = P->d_minpiv;

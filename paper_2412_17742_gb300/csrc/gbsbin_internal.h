@@ -48,6 +48,7 @@ struct PointArgs {
   const float2* g_hi;       // n
   const float2* g_lo;       // n
   const int* label;         // n: detector group of each row
+  const double2* tw;        // twiddles exp(-2 pi i m / radix[l]), m < radix[l], axis after axis
   GridDesc grid;
   double2* logq;            // n_eval outputs: log q at each evaluated point
   double* minpiv;           // n_eval outputs: min_i Re u_ii

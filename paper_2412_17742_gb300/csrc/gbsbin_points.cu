@@ -65,7 +65,7 @@ __device__ __forceinline__ void group_fp64(const PointArgs& a, const long long e
     for (int t = tid; t < P * L; t += NT) {
       int p = t / L, l = t - p * L;
       long long e = min(e0 + p, a.grid.n_eval - 1);
-      w[t] = root_of_unity(point_digit(e, a.grid, l), a.grid.radix[l]);
+      w[t] = grid_root(a.tw, a.grid, l, point_digit(e, a.grid, l));
     }
     __syncthreads();
     // M = conj(D) - XA
@@ -215,7 +215,7 @@ __device__ __forceinline__ void group_fp32r(const PointArgs& a, const long long 
     for (int t = tid; t < P * L; t += NT) {
       int p = t / L, l = t - p * L;
       long long e = min(e0 + p, a.grid.n_eval - 1);
-      w[t] = root_of_unity(point_digit(e, a.grid, l), a.grid.radix[l]);
+      w[t] = grid_root(a.tw, a.grid, l, point_digit(e, a.grid, l));
     }
     __syncthreads();
     // M^ = fl32(conj(D) - XA): off-diagonal NXA_hi, diagonal rounded from FP64

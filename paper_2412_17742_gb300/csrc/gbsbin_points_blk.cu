@@ -361,7 +361,7 @@ __device__ void group_fp32r_blk(const PointArgs& a, const long long e, unsigned 
   float2* A = (float2*)((char*)a.gws + (size_t)blockIdx.x * (size_t)a.gws_slot_bytes);
   float2* E = A + (size_t)n * n;
   for (int i = tid; i < n; i += NT) sm.lab[i] = a.label[i];
-  if (tid < L) sm.w[tid] = root_of_unity(point_digit(e, a.grid, tid), a.grid.radix[tid]);
+  if (tid < L) sm.w[tid] = grid_root(a.tw, a.grid, tid, point_digit(e, a.grid, tid));
   __syncthreads();
 
   // M^ = fl32(conj(D) - XA)

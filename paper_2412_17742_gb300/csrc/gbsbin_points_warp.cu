@@ -71,7 +71,7 @@ __device__ __forceinline__ void warp_point(const PointArgs& a, const long long e
   float2* rs = sh.r[warp];
   const float2 zero = make_float2(0.0f, 0.0f);
   if (e < a.grid.n_eval) {
-    if (lane < L) w[lane] = root_of_unity(point_digit(e, a.grid, lane), a.grid.radix[lane]);
+    if (lane < L) w[lane] = grid_root(a.tw, a.grid, lane, point_digit(e, a.grid, lane));
     __syncwarp();
 
     // ---- 1. M^ = fl32(conj(D) - XA), padded with the identity; LU in registers.
