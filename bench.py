@@ -180,8 +180,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the other workloads (n=192 grid, 256-problem batch, n=200 gradient)")
-    ap.add_argument("--extras", default="n192,batch,n200",
-                    help="comma list of the other workloads to time: n192, batch, n200")
+    ap.add_argument("--extras", default="n192,batch,n200,e3",
+                    help="comma list of the other workloads to time: n192, batch, n200, e3")
     ap.add_argument("--extra-steps", type=int, default=3)
     args = ap.parse_args()
     if args.impl == "reference":
@@ -332,7 +332,7 @@ def _timed(torch, stream, flush, steps, fn):
     return total
 
 
-def extra_workloads(gb, torch, stream, flush, steps, world, which=("n192", "batch", "n200")):
+def extra_workloads(gb, torch, stream, flush, steps, world, which=("n192", "batch", "n200", "e3")):
     """The other workloads, a few steps each: per-table and per-point rates, FP32R next to
     FP64 where both apply."""
     out = {}
@@ -342,7 +342,33 @@ def extra_workloads(gb, torch, stream, flush, steps, world, which=("n192", "batc
         out.update(_extra_batch(gb, torch, stream, flush, steps, world))
     if "n200" in which:
         out.update(_extra_n200(gb, torch, stream, flush, steps, world))
+    if "e3" in which:
+        out.update(_extra_e3(gb, torch, stream, flush, steps, world))
     return out
+
+
+def _extra_e3(gb, torch, stream, flush, steps, world):
+    """Total photon number of the largest uniform-loss setup of Sec. VIII: M = 256 (n = 512),
+    xi = 0.89, eta = 0.36, Haar U, one detector group, N_max = 170: the one-group Hessenberg
+    path against the general FP64 LU kernel on the same table."""
+    M, Nmax, xi, eta = 256, 170, 0.89, 0.36
+    prob = synth.Problem(M, 1, np.full((M, 1), xi), np.sqrt(eta) * synth.haar_unitary(M, np.random.default_rng(61)),
+                         np.zeros(M, np.int32), np.array([Nmax], np.int32))
+    res = {}
+    tables = {}
+    for name, tile in (("hessenberg_fp64", 0), ("general_lu_fp64", 3)):
+        t0 = time.perf_counter()
+        with gb.Plan(prob, precision=0, want_timing=True, tile_override=tile) as p:
+            plan_s = time.perf_counter() - t0
+            t = torch.empty(p.shape, dtype=torch.float64, device="cuda")
+            gb.gbsbin_execute(p.handle, t, stream)
+            ms = _timed(torch, stream, flush, steps, lambda: gb.gbsbin_execute(p.handle, t, stream))
+            st, d = p.diagnostics(stream)
+            tables[name] = t.cpu().numpy()
+            res[name] = {"ms_per_table": ms / steps, "point_kernel_ms": d["point_kernel_ms"],
+                         "kernel": d["kernel_name"], "plan_create_s": plan_s, "status": st}
+    res["max_abs_diff"] = float(np.abs(tables["hessenberg_fp64"] - tables["general_lu_fp64"]).max())
+    return {"E3_M256_n512_L1_N170": res}
 
 
 def _extra_n192(gb, torch, stream, flush, steps, world):

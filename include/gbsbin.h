@@ -142,8 +142,13 @@ typedef enum {
   GBSBIN_KERNEL_WARP_FP32R = 5,    /* warp per point, matrix in registers (n <= 32)        */
   GBSBIN_KERNEL_BLK_FP32R = 6,     /* CTA per point, blocked (NB = 32) on an L2-resident
                                       slot, register-tiled updates (n <= 384)              */
-  GBSBIN_KERNEL_BLK_TC_FP32R = 7   /* as 6, the trace-correction updates on the tensor
+  GBSBIN_KERNEL_BLK_TC_FP32R = 7,  /* as 6, the trace-correction updates on the tensor
                                       cores (tcgen05, 3 x TF32, TMEM accumulator)         */
+  GBSBIN_KERNEL_HESS_FP64 = 8      /* one detector group (L = 1, the total photon number of
+                                      Sec. VIII) and no displacement: D(w) = w I, so one
+                                      Hessenberg reduction XA = Q H Q^H per state serves
+                                      every point, O(n^2) per point (warp per point, FP64);
+                                      chosen automatically for such problems              */
 } gbsbin_kernel;
 
 /* Fill *o with defaults: FP64, oversample 1, diagnostics on, automatic kernel. */

@@ -35,6 +35,7 @@ struct gbsbin_plan {
   longlong2* d_NXA_fix = nullptr;
   double* d_ldfin = nullptr;          // warp kernel: unfinished log det per evaluated point
   unsigned* d_bar = nullptr;          // grid-barrier state of the fused DFT launch
+  double2* d_H = nullptr;             // Hessenberg form of XA (one-group, undisplaced plans)
   int* d_label = nullptr;
   double2* d_logq = nullptr;
   double* d_minpiv = nullptr;
@@ -74,7 +75,7 @@ int validate_shape(const gbsbin_problem* p, const gbsbin_options* o) {
   if (!p->sigma1 && (!p->r || !p->T)) return GBSBIN_ERR_ARG;
   if (o->precision != GBSBIN_FP64 && o->precision != GBSBIN_FP32_REFINE) return GBSBIN_ERR_ARG;
   if (o->oversample < 1) return GBSBIN_ERR_ARG;
-  if (o->tile_override < 0 || o->tile_override > GBSBIN_KERNEL_BLK_TC_FP32R) return GBSBIN_ERR_ARG;
+  if (o->tile_override < 0 || o->tile_override > GBSBIN_KERNEL_HESS_FP64) return GBSBIN_ERR_ARG;
   long long n = 2LL * p->M * p->K;
   if (n > GBSBIN_MAX_N) return GBSBIN_ERR_UNSUPPORTED;
   std::vector<int> count(p->L, 0);
@@ -243,7 +244,7 @@ void free_device(gbsbin_plan* P) {
   void* ptrs[] = {P->d_NXA,  P->d_gamma, P->d_Xgamma, P->d_NXA_hi, P->d_NXA_lo, P->d_Xg_hi,
                   P->d_Xg_lo, P->d_g_hi, P->d_g_lo,   P->d_label, P->d_logq,  P->d_minpiv,
                   P->d_bufA, P->d_bufB,  P->d_tw,     P->d_diag,  P->d_gws,   P->d_table,
-                  P->d_NXA_fix, P->d_ldfin, P->d_bar};
+                  P->d_NXA_fix, P->d_ldfin, P->d_bar, P->d_H};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (P->h_stage) cudaFreeHost(P->h_stage);
@@ -292,6 +293,8 @@ void split(cd v, float2* hi, float2* lo) {
   *lo = make_float2((float)(v.real() - (double)hr), (float)(v.imag() - (double)hi_));
 }
 
+int upload_hessenberg(gbsbin_plan* P, cudaStream_t stream);
+
 // Stage the state and enqueue its upload on `stream`.
 int upload_state(gbsbin_plan* P, cudaStream_t stream) {
   const int n = P->n;
@@ -337,6 +340,64 @@ int upload_state(gbsbin_plan* P, cudaStream_t stream) {
     e = cudaMemcpyAsync(c.dst, h + c.off, c.bytes, cudaMemcpyHostToDevice, stream);
     if (e != cudaSuccess) return GBSBIN_ERR_CUDA;
   }
+  if (P->kernel == GBSBIN_KERNEL_HESS_FP64) return upload_hessenberg(P, stream);
+  return GBSBIN_OK;
+}
+
+// In place: A (n x n, row-major) <- Q^H A Q upper Hessenberg, Q a product of Householder
+// reflectors (FP64).  Similar matrices share det(I - w A) for every w, which is all the
+// one-group evaluation needs; the reflectors are not kept.
+void hessenberg(std::vector<cd>& A, int n) {
+  std::vector<cd> v(n), sv(n);
+  for (int k = 0; k + 2 < n; ++k) {
+    double nrm2 = 0.0;
+    for (int i = k + 1; i < n; ++i) nrm2 += std::norm(A[(size_t)i * n + k]);
+    if (nrm2 == 0.0) continue;
+    const double nrm = std::sqrt(nrm2);
+    const cd x0 = A[(size_t)(k + 1) * n + k];
+    const double ax0 = std::abs(x0);
+    const cd alpha = (ax0 > 0.0 ? -x0 / ax0 : cd(-1.0, 0.0)) * nrm;   // -e^{i arg x0} ||x||
+    for (int i = k + 1; i < n; ++i) v[i] = A[(size_t)i * n + k];
+    v[k + 1] -= alpha;
+    double vn2 = 0.0;
+    for (int i = k + 1; i < n; ++i) vn2 += std::norm(v[i]);
+    if (vn2 == 0.0) continue;
+    const double beta = 2.0 / vn2;
+    // rows k+1.. : A <- (I - beta v v^H) A
+    for (int j = 0; j < n; ++j) sv[j] = 0.0;
+    for (int i = k + 1; i < n; ++i) {
+      const cd vc = std::conj(v[i]);
+      const cd* row = &A[(size_t)i * n];
+      for (int j = 0; j < n; ++j) sv[j] += vc * row[j];
+    }
+    for (int i = k + 1; i < n; ++i) {
+      const cd vi = beta * v[i];
+      cd* row = &A[(size_t)i * n];
+      for (int j = 0; j < n; ++j) row[j] -= vi * sv[j];
+    }
+    // columns k+1.. : A <- A (I - beta v v^H)
+    for (int i = 0; i < n; ++i) {
+      cd* row = &A[(size_t)i * n];
+      cd t = 0.0;
+      for (int j = k + 1; j < n; ++j) t += row[j] * v[j];
+      t *= beta;
+      for (int j = k + 1; j < n; ++j) row[j] -= t * std::conj(v[j]);
+    }
+    A[(size_t)(k + 1) * n + k] = alpha;
+    for (int i = k + 2; i < n; ++i) A[(size_t)i * n + k] = 0.0;
+  }
+}
+
+// The one-group plans' Hessenberg form of the current XA, uploaded on `stream`.
+int upload_hessenberg(gbsbin_plan* P, cudaStream_t stream) {
+  const int n = P->n;
+  std::vector<cd> H(P->XA);
+  hessenberg(H, n);
+  std::vector<double2> h((size_t)n * n);
+  for (size_t q = 0; q < h.size(); ++q) h[q] = make_double2(H[q].real(), H[q].imag());
+  // a pageable source: the call returns once the data are staged, so h may go out of scope
+  if (cudaMemcpyAsync(P->d_H, h.data(), h.size() * sizeof(double2), cudaMemcpyHostToDevice, stream) != cudaSuccess)
+    return GBSBIN_ERR_CUDA;
   return GBSBIN_OK;
 }
 
@@ -423,8 +484,9 @@ int evaluate_fp64_with_factors(gbsbin_plan* P, cudaStream_t s) {
 // tensor cores.
 inline bool is_blk(int kernel) { return kernel == GBSBIN_KERNEL_BLK_FP32R || kernel == GBSBIN_KERNEL_BLK_TC_FP32R; }
 
-int choose_kernel(int n, int L, int precision, int override_id) {
+int choose_kernel(int n, int L, int precision, int override_id, int has_gamma) {
   if (override_id) return override_id;
+  if (L == 1 && !has_gamma) return GBSBIN_KERNEL_HESS_FP64;   // one group, undisplaced
   if (precision == GBSBIN_FP32_REFINE && n <= 32) return GBSBIN_KERNEL_WARP_FP32R;
   if (precision == GBSBIN_FP32_REFINE && n > GBSBIN_SMEM_MAX_N && n <= GBSBIN_BLK_MAX_N) return GBSBIN_KERNEL_BLK_FP32R;
   if (precision == GBSBIN_FP64)
@@ -529,8 +591,13 @@ static int plan_create_impl(const gbsbin_problem* p, const gbsbin_options* o, gb
     return st;
   }
   record_inputs(P, p);
-  P->kernel = choose_kernel(n, p->L, opt.precision, opt.tile_override);
-  P->P = P->kernel == GBSBIN_KERNEL_WARP_FP32R ? (n <= 32 ? 1 : 0)
+  P->kernel = choose_kernel(n, p->L, opt.precision, opt.tile_override, P->has_gamma);
+  if (P->kernel == GBSBIN_KERNEL_HESS_FP64 && (p->L != 1 || P->has_gamma)) {
+    delete P;
+    return GBSBIN_ERR_UNSUPPORTED;
+  }
+  P->P = P->kernel == GBSBIN_KERNEL_HESS_FP64 ? 1
+         : P->kernel == GBSBIN_KERNEL_WARP_FP32R ? (n <= 32 ? 1 : 0)
          : is_blk(P->kernel) ? (n <= GBSBIN_BLK_MAX_N ? 1 : 0)
                                                  : points_per_cta(P->kernel, n, p->L);
   if (p_override > 0 && P->P > 0 && (P->kernel == GBSBIN_KERNEL_SMEM_FP64 || P->kernel == GBSBIN_KERNEL_SMEM_FP32R)) {
@@ -578,7 +645,13 @@ static int plan_create_impl(const gbsbin_problem* p, const gbsbin_options* o, gb
     delete P;
     return st;
   }
-  if (P->kernel == GBSBIN_KERNEL_WARP_FP32R && (st = dalloc(&P->d_ldfin, (size_t)6 * g.n_eval))) {
+  if ((P->kernel == GBSBIN_KERNEL_WARP_FP32R || P->kernel == GBSBIN_KERNEL_HESS_FP64) &&
+      (st = dalloc(&P->d_ldfin, (size_t)6 * g.n_eval))) {
+    free_device(P);
+    delete P;
+    return st;
+  }
+  if (P->kernel == GBSBIN_KERNEL_HESS_FP64 && (st = dalloc(&P->d_H, nn))) {
     free_device(P);
     delete P;
     return st;
@@ -670,6 +743,7 @@ int gbsbin_plan_set_state(gbsbin_plan* P, const gbsbin_problem* p, void* stream)
   int has_gamma = 0;
   st = build_state(p, P->n, XA, gamma, Xgamma, &has_gamma, &zbar);
   if (st) return st;
+  if (P->kernel == GBSBIN_KERNEL_HESS_FP64 && has_gamma) return GBSBIN_ERR_UNSUPPORTED;  // one-group path: undisplaced only
   record_inputs(P, p);
   P->saved_valid = false;
   P->zbar.swap(zbar);
@@ -715,6 +789,7 @@ static PointArgs make_point_args(gbsbin_plan* P) {
   a.gws = P->d_gws;
   a.gws_slot_bytes = P->gws_slot_bytes;
   a.ldfin = P->d_ldfin;
+  a.H = P->d_H;
   const bool save = P->opt.want_backward && (P->kernel == GBSBIN_KERNEL_SMEM_FP64 || P->kernel == GBSBIN_KERNEL_GMEM_FP64);
   a.lu_store = save ? P->d_lu : nullptr;
   a.x_store = save ? P->d_xs : nullptr;
@@ -744,6 +819,7 @@ int gbsbin_execute(gbsbin_plan* P, double* P_out, void* stream) {
   P->saved_valid = a.lu_store != nullptr;
   if (P->ev0 && cudaEventRecord(P->ev0, s) != cudaSuccess) return GBSBIN_ERR_CUDA;
   cudaError_t e = P->kernel == GBSBIN_KERNEL_WARP_FP32R  ? launch_points_warp(a, P->num_sms, s)
+                  : P->kernel == GBSBIN_KERNEL_HESS_FP64 ? launch_points_hess(a, PointBatch{}, P->num_sms, s)
                   : is_blk(P->kernel) ? launch_points_blk(a, PointBatch{}, 0, P->num_sms, s, P->kernel == GBSBIN_KERNEL_BLK_TC_FP32R)
                                                          : launch_points(a, P->kernel, P->num_sms, s);
   if (e != cudaSuccess) return GBSBIN_ERR_CUDA;
@@ -1141,6 +1217,7 @@ int batch_launch(gbsbin_batch* B, double* const* P_out, cudaStream_t s) {
     if (cudaMemsetAsync(B->d_queue + c, 0, sizeof(unsigned long long), s) != cudaSuccess) return GBSBIN_ERR_CUDA;
     PointBatch pb{B->d_probs, C.d_jobs, (long long)C.jobs.size(), B->d_queue + c};
     cudaError_t e = C.kernel == GBSBIN_KERNEL_WARP_FP32R  ? launch_points_warp_batch(pb, C.np, B->num_sms, s)
+                    : C.kernel == GBSBIN_KERNEL_HESS_FP64 ? launch_points_hess(PointArgs{}, pb, B->num_sms, s)
                     : is_blk(C.kernel) ? launch_points_blk(PointArgs{}, pb, C.smem, B->num_sms, s, C.kernel == GBSBIN_KERNEL_BLK_TC_FP32R)
                                                           : launch_points_batch(pb, C.kernel, C.threads, C.smem, B->num_sms, s);
     if (e != cudaSuccess) return GBSBIN_ERR_CUDA;
@@ -1194,7 +1271,9 @@ int gbsbin_batch_create(const gbsbin_problem* probs, int nprob, const gbsbin_opt
     gbsbin_options oi = opt;
     int p_override = 0;
     const int n = 2 * probs[i].M * probs[i].K;
-    if (autotune && !opt.tile_override && n <= GBSBIN_MAX_N) {
+    // one-group undisplaced problems keep the Hessenberg path whatever the size's tuning
+    const bool one_group = probs[i].L == 1 && !probs[i].alpha && !(probs[i].sigma1 && probs[i].zbar);
+    if (autotune && !opt.tile_override && n <= GBSBIN_MAX_N && !one_group) {
       TuneVal v{};
       int st = autotune_lookup(n, opt.precision, &v);
       if (st) {
@@ -1212,7 +1291,7 @@ int gbsbin_batch_create(const gbsbin_problem* probs, int nprob, const gbsbin_opt
     }
     gbsbin_plan* P = B->plans[i];
     args[i] = make_point_args(P);
-    const int threads = P->kernel == GBSBIN_KERNEL_WARP_FP32R ? 128
+    const int threads = (P->kernel == GBSBIN_KERNEL_WARP_FP32R || P->kernel == GBSBIN_KERNEL_HESS_FP64) ? 128
                         : is_blk(P->kernel) ? 256
                                                                : points_threads(P->kernel, P->n);
     // warp kernel: padded size class; blocked kernel: problems whose shared memory allows
@@ -1229,7 +1308,7 @@ int gbsbin_batch_create(const gbsbin_problem* probs, int nprob, const gbsbin_opt
       B->classes.back().np = np;
     }
     auto& C = B->classes[class_of[key]];
-    const int group = P->kernel == GBSBIN_KERNEL_WARP_FP32R ? 4 : P->P;
+    const int group = (P->kernel == GBSBIN_KERNEL_WARP_FP32R || P->kernel == GBSBIN_KERNEL_HESS_FP64) ? 4 : P->P;
     for (long long e0 = 0; e0 < P->grid.n_eval; e0 += group) C.jobs.push_back(PointJob{i, 0, e0});
     if (P->kernel == GBSBIN_KERNEL_SMEM_FP64 || P->kernel == GBSBIN_KERNEL_SMEM_FP32R ||
         P->kernel == GBSBIN_KERNEL_GMEM_FP64 || P->kernel == GBSBIN_KERNEL_GMEM_FP32R)

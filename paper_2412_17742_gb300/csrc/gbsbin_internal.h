@@ -49,6 +49,7 @@ struct PointArgs {
   const float2* g_lo;       // n
   const int* label;         // n: detector group of each row
   const double2* tw;        // twiddles exp(-2 pi i m / radix[l]), m < radix[l], axis after axis
+  const double2* H;         // one-group plans: Hessenberg form of XA, n*n FP64 (else nullptr)
   GridDesc grid;
   double2* logq;            // n_eval outputs: log q at each evaluated point
   double* minpiv;           // n_eval outputs: min_i Re u_ii
@@ -124,6 +125,9 @@ size_t points_blk_slot_bytes(int n);
 int points_blk_ctas_per_sm(int n);   // resident CTAs per SM that the shared memory allows (1 or 2)
 cudaError_t launch_points_blk(const PointArgs& a, const PointBatch& batch, size_t smem_batch, int num_sms,
                               cudaStream_t s, bool tensor_cores);
+// One-group (L = 1) undisplaced kernel (gbsbin_points_hess.cu): warp per point, four
+// points per CTA; batch jobs are groups of four consecutive points of one problem.
+cudaError_t launch_points_hess(const PointArgs& a, const PointBatch& batch, int num_sms, cudaStream_t s);
 size_t points_smem_bytes(int kernel, int n, int P, int L);
 size_t points_matrix_bytes(int kernel, int n, int P);
 int points_per_cta(int kernel, int n, int L);

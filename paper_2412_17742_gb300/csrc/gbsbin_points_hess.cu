@@ -1,0 +1,147 @@
+// One detector group, no displacement (arXiv:2412.17742, Sec. VIII, total photon-number
+// distribution; Sec. III Eq. q_d with a single group): D(w) = w I, so
+//
+//   K(w) = I - w XA = Q (I - w H) Q^H,   XA = Q H Q^H with H upper Hessenberg,
+//
+// and det K(w) = det(I - w H).  The host reduces XA once per state; per grid point the
+// unpivoted LU of the Hessenberg matrix B = I - w H costs O(n^2): each elimination step
+// subtracts a multiple of the current pivot row from the next row only.  Since
+// B = -w (H - conj(w) I), the steps run on H - conj(w) I (no multiplication per entry) and
+// the pivots of B are -w times its pivots; every pivot of B has Re > 0 (||w H|| =
+// ||XA|| < 1, so B has a positive-definite Hermitian part, as do its Schur complements), so
+// sum_i Log p_i is the branch of log det K continuous from w = 0.
+//
+// One warp per point, FP64: lane t holds entries j = lane + 32 s of the current pivot row
+// in registers (s < 16, n <= 512); row i + 1 of H - conj(w) I is read from the L2-resident
+// H.  log q = -1/2 log det K is left unfinished as (product of pivots with its power of two,
+// FP32 sum of their arguments), finished one point per thread by the DFT's first stage.
+#include <cuda_runtime.h>
+
+#include "gbsbin_device.cuh"
+#include "gbsbin_internal.h"
+
+namespace gbsbin {
+namespace {
+
+constexpr int HW = 4;                         // warps (points) per CTA
+constexpr int SMAX = GBSBIN_MAX_N / 32;       // row slots per lane
+
+__device__ __forceinline__ double2 shfl_d2(double2 v, int src) {
+  return make_double2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
+}
+
+// 2^-ex scaling of z with ex the binary exponent of max(|re|, |im|); returns ex.
+__device__ __forceinline__ int renormalise(double2& z) {
+  const double m = fmax(fabs(z.x), fabs(z.y));
+  if (!(m > 0.0) || !(m < 1.0e300)) return 0;
+  const int ex = ((__double2hiint(m) >> 20) & 0x7ff) - 1022;   // m in [2^(ex-1), 2^ex)
+  const double sc = __hiloint2double((1023 - ex) << 20, 0);    // 2^-ex
+  z.x *= sc;
+  z.y *= sc;
+  return ex;
+}
+
+__device__ void hess_point(const PointArgs& a, long long e) {
+  const int n = a.n, lane = threadIdx.x & 31;
+  const int S = (n + 31) >> 5;
+  const double2 w = grid_root(a.tw, a.grid, 0, point_digit(e, a.grid, 0));
+  const double2 sg = make_double2(w.x, -w.y);                  // conj(w)
+  const double2 mw = make_double2(-w.x, -w.y);                 // pivots of B = -w x pivots here
+  const double2* H = a.H;
+  // row 0 of H - conj(w) I
+  double2 r[SMAX];
+#pragma unroll
+  for (int s = 0; s < SMAX; ++s) {
+    const int j = lane + 32 * s;
+    double2 v = make_double2(0.0, 0.0);
+    if (s < S && j < n) {
+      v = H[j];
+      if (j == 0) v = make_double2(v.x - sg.x, v.y - sg.y);
+    }
+    r[s] = v;
+  }
+  double2 prod = make_double2(1.0, 0.0);
+  int e2 = 0;
+  float args = 0.0f;
+  double mn = 1.0e300;
+#pragma unroll
+  for (int sb = 0; sb < SMAX; ++sb) {           // pivot i = 32 sb + il sits in slot sb of lane il
+    if (sb >= S) break;
+    for (int il = 0; il < 32; ++il) {
+      const int i = 32 * sb + il;
+      if (i >= n) break;
+      const double2 q = shfl_d2(r[sb], il);     // pivot of H - conj(w) I
+      const double2 p = cmul(mw, q);            // pivot of B = I - w H
+      mn = fmin(mn, p.x);
+      if (!(p.x == p.x) || !(p.y == p.y)) mn = -1.0e300;
+      args += atan2f((float)p.y, (float)p.x);
+      prod = cmul(prod, p);
+      if (i == n - 1) break;
+      // row i + 1: its only entry left of the diagonal is H[i+1][i]; l = that / q
+      const double2* hrow = H + (size_t)(i + 1) * n;
+      const double2 l = cmul(hrow[i], crecip(q));
+#pragma unroll
+      for (int s = 0; s < SMAX; ++s) {
+        const int j = lane + 32 * s;
+        if (s < S && j > i && j < n) {
+          double2 h = hrow[j];
+          if (j == i + 1) h = make_double2(h.x - sg.x, h.y - sg.y);
+          r[s] = cfnma(h, l, r[s]);
+        }
+      }
+    }
+    e2 += renormalise(prod);                    // every 32 pivots: |prod| stays in range
+  }
+  if (lane == 0) {
+    const double LN2 = 0.693147180559945309417232121458;
+    double* f = a.ldfin + 6 * e;
+    f[0] = prod.x;
+    f[1] = prod.y;
+    f[2] = (double)args;
+    f[3] = -0.5 * (double)e2 * LN2;             // log q = -1/2 log det K (no exponent term)
+    f[4] = 0.0;
+    f[5] = 0.0;
+    a.minpiv[e] = mn;
+  }
+}
+
+__global__ void __launch_bounds__(HW * 32) k_points_hess(PointArgs a0, PointBatch batch) {
+  const int warp = threadIdx.x >> 5;
+  if (!batch.probs) {
+    for (long long e = (long long)blockIdx.x * HW + warp; e < a0.grid.n_eval; e += (long long)gridDim.x * HW)
+      hess_point(a0, e);
+    return;
+  }
+  __shared__ PointArgs sa;
+  __shared__ long long sj;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const unsigned long long j = atomicAdd(batch.queue, 1ull);
+      sj = (long long)j;
+      if ((long long)j < batch.njobs) sa = batch.probs[batch.jobs[j].prob];
+    }
+    __syncthreads();
+    const long long j = sj;
+    if (j >= batch.njobs) break;
+    const long long e = batch.jobs[j].e0 + warp;
+    if (e < sa.grid.n_eval) hess_point(sa, e);
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_points_hess(const PointArgs& a, const PointBatch& batch, int num_sms, cudaStream_t s) {
+  int per_sm = 0;
+  cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_points_hess, HW * 32, 0);
+  if (err != cudaSuccess) return err;
+  if (per_sm < 1) per_sm = 1;
+  const long long groups = batch.probs ? batch.njobs : (a.grid.n_eval + HW - 1) / HW;
+  long long grid = (long long)per_sm * num_sms;
+  if (grid > groups) grid = groups;
+  if (grid < 1) grid = 1;
+  k_points_hess<<<(unsigned)grid, HW * 32, 0, s>>>(a, batch);
+  return cudaGetLastError();
+}
+
+}  // namespace gbsbin

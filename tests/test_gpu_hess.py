@@ -1,0 +1,100 @@
+"""One detector group without displacement (the total photon number of Sec. VIII): the
+Hessenberg path (one reduction per state, O(n^2) per point) against the oracle's LU, the
+general kernels, and the closed form of the uniform-loss setup of Sec. VIII up to n = 512."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+CASES = [  # (M, K, cutoff, internal basis)
+    (4, 1, 12, False),      # n = 8
+    (15, 1, 30, False),     # n = 30: one ragged row block
+    (32, 1, 20, False),     # n = 64
+    (25, 2, 16, True),      # n = 100, internal modes
+    (100, 1, 9, False),     # n = 200
+]
+
+
+def _flat(digits, radix):
+    strides = np.ones(len(radix), dtype=np.int64)
+    for l in range(len(radix) - 2, -1, -1):
+        strides[l] = strides[l + 1] * radix[l + 1]
+    return digits @ strides
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("M,K,cut,basis", CASES)
+def test_one_group_matches_oracle(cuda_lib, M, K, cut, basis, precision):
+    gb = cuda_lib
+    prob = synth.random_problem(np.random.default_rng(500 + M + K), M, K, 1, cut, internal_basis=basis)
+    with gb.Plan(prob, precision=precision) as p:
+        P = p.table().cpu().numpy()
+        st, d = p.diagnostics()
+        lq, mp = gb.gbsbin_read_points(p.handle, d["n_evaluated"])
+    assert st == 0 and d["kernel_name"] == "hess_fp64" and d["n_bad_points"] == 0
+    res = oracle.binned(prob)
+    assert np.abs(P - res["P"]).max() <= 1e-10
+    dig = gb.evaluated_point_digits(prob.cutoff)
+    assert np.abs(lq - res["logq"][_flat(dig, prob.radix)]).max() < 1e-9
+    assert d["min_pivot_re"] > 0
+    # the general FP64 kernel on the same problem gives the same table
+    with gb.Plan(prob, precision=0, tile_override=3) as p:
+        Pg = p.table().cpu().numpy()
+    assert np.abs(P - Pg).max() < 1e-12
+
+
+@pytest.mark.parametrize("row", [0, 2, 4])
+def test_uniform_loss_total_number_closed_form(cuda_lib, row):
+    # Sec. VIII setup (xi = 0.89, eta = 0.36, Haar U; M = 16, 64, 256 and the paper's N_max):
+    # the total count is M independent lossy squeezed vacua, so log q(w) - log q(1) =
+    # -(M/2) log[(1 - x(n+m))(1 - x(n-m))], x = w - 1, n = eta sinh^2 xi, m = eta sinh xi cosh xi
+    gb = cuda_lib
+    rows = [ln.split() for ln in open(__file__.replace("test_gpu_hess.py", "golden/e3_total_photon_setup.txt"))
+            if ln.strip() and not ln.startswith("#")]
+    M, Nmax = int(rows[row][0]), int(rows[row][1])
+    xi, eta = 0.89, 0.36
+    rng = np.random.default_rng(61 + row)
+    prob = synth.Problem(M, 1, np.full((M, 1), xi), np.sqrt(eta) * synth.haar_unitary(M, rng),
+                         np.zeros(M, np.int32), np.array([Nmax], np.int32))
+    with gb.Plan(prob) as p:
+        P = p.table().cpu().numpy()
+        st, d = p.diagnostics()
+        lq, mp = gb.gbsbin_read_points(p.handle, d["n_evaluated"])
+    assert st == 0 and d["kernel_name"] == "hess_fp64" and d["n"] == 2 * M
+    w = np.exp(2j * np.pi * np.arange(Nmax + 1) / (Nmax + 1))
+    n_, m_ = eta * np.sinh(xi) ** 2, eta * np.sinh(xi) * np.cosh(xi)
+    x = w - 1
+    G = ((1 - x * (n_ + m_)) * (1 - x * (n_ - m_))) ** (-M / 2.0)
+    half = (Nmax + 1) // 2 + 1
+    Gk = np.exp(lq - lq[0])
+    assert np.abs(Gk - G[:half]).max() < 1e-11
+    assert np.abs(P - (np.fft.fft(G) / (Nmax + 1)).real).max() < 1e-12
+    assert abs(P.sum() - 1.0) < 1e-12
+
+
+def test_one_group_fallbacks_and_errors(cuda_lib):
+    gb = cuda_lib
+    rng = np.random.default_rng(520)
+    disp = synth.random_problem(rng, 6, 1, 1, 10, displaced=True)
+    with gb.Plan(disp) as p:                      # displaced: the general path
+        P = p.table().cpu().numpy()
+        st, d = p.diagnostics()
+    assert d["kernel_name"] != "hess_fp64"
+    assert np.abs(P - oracle.binned(disp)["P"]).max() <= 1e-10
+    two = synth.random_problem(rng, 6, 1, 2, [3, 4])
+    for bad in (disp, two):                       # forcing the one-group path where it does not apply
+        with pytest.raises(gb.GbsbinError):
+            gb.Plan(bad, tile_override=8)
+    # a new undisplaced state on a one-group plan; a displaced one is refused
+    a = synth.random_problem(np.random.default_rng(521), 10, 1, 1, 14)
+    b = synth.random_problem(np.random.default_rng(522), 10, 1, 1, 14)
+    with gb.Plan(a) as p:
+        gb.gbsbin_plan_set_state(p.handle, b)
+        Pb = p.table().cpu().numpy()
+        assert np.abs(Pb - oracle.binned(b)["P"]).max() <= 1e-10
+        b.alpha = 0.3 * np.ones((10, 1), complex)
+        with pytest.raises(gb.GbsbinError):
+            gb.gbsbin_plan_set_state(p.handle, b)
