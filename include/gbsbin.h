@@ -296,6 +296,22 @@ int gbsbin_batch_diagnostics(gbsbin_batch* b, int i, gbsbin_diag* out, void* str
 int gbsbin_batch_read_points(gbsbin_batch* b, int i, double* logq_host, double* minpiv_host, void* stream);
 int gbsbin_batch_destroy(gbsbin_batch* b);
 
+/*
+ * Exact mean and covariance of the binned counts (Sec. VI, coarse-grained moments and
+ * cumulants): with G(e^t) the moment generating function of b, they are the first and
+ * second derivatives of log G(e^t) at t = 0, where log G = 1/2 gamma^T (I - D XA)^{-1} D X
+ * gamma - 1/2 log det(I - D XA) + const and D = diag(e^{t_l(i)}).  Written out with
+ * R = (I - XA)^{-1}, W = XA R, u = R X gamma, v = R^T gamma:
+ *   mean_l   = 1/2 sum_{i in l} (v_i u_i + W_ii)
+ *   cov_lm   = 1/2 [sum_{i in m, j in l} v_i W_ij u_j + sum_{i in l, j in m} v_i W_ij u_j
+ *                   + d_lm sum_{i in l} v_i u_i + sum_{i in m, j in l} W_ij W_ji
+ *                   + d_lm sum_{i in l} W_ii].
+ * Unfolded (no cutoff enters: p->cutoff is validated but unused).  Host only, FP64, O(n^3);
+ * no device is used.  mean: L doubles, cov: L x L doubles row-major, caller-owned host.
+ * Errors: ERR_ARG / ERR_PARTITION / ERR_NONPHYSICAL as for gbsbin_plan_create.
+ */
+int gbsbin_moments(const gbsbin_problem* p, double* mean, double* cov);
+
 /* Static description of a status code. */
 const char* gbsbin_strerror(int status);
 

@@ -30,7 +30,7 @@ EXPORTED = ["gbsbin_default_options", "gbsbin_plan_create", "gbsbin_plan_set_sta
             "gbsbin_strerror", "gbsbin_alu_peak", "gbsbin_read_points", "gbsbin_table_from_logq_noalloc",
             "gbsbin_backward", "gbsbin_autotune", "gbsbin_batch_create", "gbsbin_batch_execute",
             "gbsbin_batch_capture_graph", "gbsbin_batch_replay", "gbsbin_batch_table_size",
-            "gbsbin_batch_diagnostics", "gbsbin_batch_read_points", "gbsbin_batch_destroy"]
+            "gbsbin_batch_diagnostics", "gbsbin_batch_read_points", "gbsbin_batch_destroy", "gbsbin_moments"]
 
 
 class GbsbinError(RuntimeError):
@@ -95,6 +95,7 @@ def load():
     lib.gbsbin_strerror.argtypes = [ctypes.c_int]
     lib.gbsbin_strerror.restype = ctypes.c_char_p
     lib.gbsbin_alu_peak.argtypes = [ctypes.c_int, ctypes.c_int, _dp, vp]
+    lib.gbsbin_moments.argtypes = [ctypes.POINTER(gbsbin_problem), vp, vp]
     lib.gbsbin_read_points.argtypes = [vp, vp, vp, vp]
     lib.gbsbin_table_from_logq_noalloc.argtypes = [ctypes.c_int, _ip, ctypes.c_int, vp, vp, vp]
     lib.gbsbin_backward.argtypes = [vp, vp, ctypes.POINTER(gbsbin_grads), vp]
@@ -294,6 +295,17 @@ def gbsbin_autotune(n, precision):
 
 def gbsbin_strerror(status):
     return load().gbsbin_strerror(int(status)).decode()
+
+
+def gbsbin_moments(prob):
+    """Exact mean (L,) and covariance (L, L) of the binned counts (host, FP64, no device)."""
+    args = prob if isinstance(prob, ProblemArgs) else ProblemArgs(prob)
+    L = len(np.asarray(prob.cutoff))
+    mean = np.zeros(L)
+    cov = np.zeros((L, L))
+    _check(load().gbsbin_moments(ctypes.byref(args.c), mean.ctypes.data_as(ctypes.c_void_p),
+                                 cov.ctypes.data_as(ctypes.c_void_p)), "gbsbin_moments")
+    return mean, cov
 
 
 def gbsbin_alu_peak(precision, blocks, stream=None):

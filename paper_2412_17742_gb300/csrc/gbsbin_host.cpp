@@ -1025,6 +1025,92 @@ int gbsbin_backward(gbsbin_plan* P, const double* dLdP, gbsbin_grads* g, void* s
   return GBSBIN_OK;
 }
 
+// ---------------------------------------------------------------- binned moments
+// Inverse of a general complex n x n matrix (row-major) by Gauss-Jordan with partial
+// pivoting, FP64; returns false if a pivot vanishes.
+static bool invert(std::vector<cd>& A, int n) {
+  std::vector<cd> I((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) I[(size_t)i * n + i] = 1.0;
+  for (int k = 0; k < n; ++k) {
+    int piv = k;
+    for (int i = k + 1; i < n; ++i)
+      if (std::abs(A[(size_t)i * n + k]) > std::abs(A[(size_t)piv * n + k])) piv = i;
+    if (std::abs(A[(size_t)piv * n + k]) == 0.0) return false;
+    if (piv != k)
+      for (int j = 0; j < n; ++j) {
+        std::swap(A[(size_t)k * n + j], A[(size_t)piv * n + j]);
+        std::swap(I[(size_t)k * n + j], I[(size_t)piv * n + j]);
+      }
+    const cd inv = 1.0 / A[(size_t)k * n + k];
+    for (int j = 0; j < n; ++j) {
+      A[(size_t)k * n + j] *= inv;
+      I[(size_t)k * n + j] *= inv;
+    }
+    for (int i = 0; i < n; ++i) {
+      if (i == k) continue;
+      const cd f = A[(size_t)i * n + k];
+      if (f == cd(0.0)) continue;
+      for (int j = 0; j < n; ++j) {
+        A[(size_t)i * n + j] -= f * A[(size_t)k * n + j];
+        I[(size_t)i * n + j] -= f * I[(size_t)k * n + j];
+      }
+    }
+  }
+  A.swap(I);
+  return true;
+}
+
+int gbsbin_moments(const gbsbin_problem* p, double* mean, double* cov) {
+  if (!p || !mean || !cov) return GBSBIN_ERR_ARG;
+  gbsbin_options o;
+  gbsbin_default_options(&o);
+  int st = validate_shape(p, &o);
+  if (st) return st;
+  const int MK = p->M * p->K, n = 2 * MK, L = p->L;
+  std::vector<cd> C, gamma, Xgamma;
+  int has_gamma = 0;
+  if ((st = build_state(p, n, C, gamma, Xgamma, &has_gamma))) return st;
+  std::vector<int> lab(n);
+  for (int q = 0; q < MK; ++q) lab[q] = lab[MK + q] = p->bin_of_mode[q / p->K];
+  // R = (I - XA)^{-1}, W = XA R, u = R X gamma, v = R^T gamma
+  std::vector<cd> R((size_t)n * n);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) R[(size_t)i * n + j] = (i == j ? 1.0 : 0.0) - C[(size_t)i * n + j];
+  if (!invert(R, n)) return GBSBIN_ERR_NONPHYSICAL;
+  std::vector<cd> W((size_t)n * n, 0.0), u(n, 0.0), v(n, 0.0);
+  for (int i = 0; i < n; ++i)
+    for (int k = 0; k < n; ++k) {
+      const cd c = C[(size_t)i * n + k];
+      if (c == cd(0.0)) continue;
+      const cd* rrow = &R[(size_t)k * n];
+      cd* wrow = &W[(size_t)i * n];
+      for (int j = 0; j < n; ++j) wrow[j] += c * rrow[j];
+    }
+  for (int i = 0; i < n; ++i)
+    for (int k = 0; k < n; ++k) {
+      u[i] += R[(size_t)i * n + k] * Xgamma[k];
+      v[i] += R[(size_t)k * n + i] * gamma[k];
+    }
+  // mean_l = 1/2 sum_{i in l} (v_i u_i + W_ii)
+  std::vector<cd> mu(L, 0.0), s(L * L, 0.0);
+  for (int i = 0; i < n; ++i) mu[lab[i]] += 0.5 * (v[i] * u[i] + W[(size_t)i * n + i]);
+  // cov_lm = 1/2 [sum_{i in m, j in l} v_i W_ij u_j + sum_{i in l, j in m} v_i W_ij u_j
+  //               + d_lm sum_{i in l} v_i u_i + sum_{i in m, j in l} W_ij W_ji + d_lm sum_{i in l} W_ii]
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      const cd t = v[i] * W[(size_t)i * n + j] * u[j];
+      const cd ww = W[(size_t)i * n + j] * W[(size_t)j * n + i];
+      const int li = lab[i], lj = lab[j];
+      s[lj * L + li] += 0.5 * t;                 // i in m = li, j in l = lj: entry (l, m)
+      s[li * L + lj] += 0.5 * t;                 // i in l = li, j in m = lj
+      s[lj * L + li] += 0.5 * ww;
+    }
+  for (int i = 0; i < n; ++i) s[lab[i] * L + lab[i]] += 0.5 * (v[i] * u[i] + W[(size_t)i * n + i]);
+  for (int l = 0; l < L; ++l) mean[l] = mu[l].real();
+  for (int q = 0; q < L * L; ++q) cov[q] = s[q].real();
+  return GBSBIN_OK;
+}
+
 int gbsbin_alu_peak(int precision, int blocks, double* tflops, void* stream) {
   if (!tflops || blocks <= 0) return GBSBIN_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;

@@ -1,0 +1,77 @@
+"""Exact binned means and covariances (gbsbin_moments, host FP64, no GPU) against textbook
+single-mode results and against the moments of the oracle's unfolded (oversampled) tables."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from oracle import state
+
+
+@pytest.fixture(scope="module")
+def gb():
+    import paper_2412_17742_gb300 as gb
+    try:
+        gb.load()
+    except RuntimeError:
+        pytest.skip("library not built")
+    return gb
+
+
+def _one_mode(r, alpha=None, eta=1.0):
+    return synth.Problem(1, 1, np.array([[r]]), np.array([[np.sqrt(eta)]], complex), np.zeros(1, np.int32),
+                         np.array([5], np.int32), alpha=None if alpha is None else np.array([[alpha]], complex))
+
+
+def test_squeezed_vacuum_and_coherent_state(gb):
+    r = 0.7
+    m, c = gb.gbsbin_moments(_one_mode(r))
+    assert abs(m[0] - np.sinh(r) ** 2) < 1e-14
+    assert abs(c[0, 0] - 2 * np.sinh(r) ** 2 * np.cosh(r) ** 2) < 1e-13   # variance of a squeezed vacuum
+    a = 0.9 - 0.4j
+    m, c = gb.gbsbin_moments(_one_mode(0.0, a))
+    assert abs(m[0] - abs(a) ** 2) < 1e-14 and abs(c[0, 0] - abs(a) ** 2) < 1e-13   # Poisson
+    # loss eta on a squeezed vacuum: mean eta sinh^2 r; the variance against the oracle's
+    # unfolded table (its 400-point DFT carries ~1e-12 of rounding)
+    m, c = gb.gbsbin_moments(_one_mode(r, eta=0.6))
+    assert abs(m[0] - 0.6 * np.sinh(r) ** 2) < 1e-14
+    P = oracle.binned(_one_mode(r, eta=0.6), radix=[400])["P"]
+    k = np.arange(len(P))
+    mu = (P * k).sum()
+    assert abs(m[0] - mu) < 1e-10 and abs(c[0, 0] - ((P * k * k).sum() - mu * mu)) < 1e-9
+
+
+@pytest.mark.parametrize("M,K,L,cut,disp,basis", [(4, 1, 2, 6, True, False), (3, 2, 2, 5, False, True),
+                                                  (3, 2, 3, 4, True, True), (5, 1, 3, 4, True, False)])
+def test_against_unfolded_tables(gb, M, K, L, cut, disp, basis):
+    rng = np.random.default_rng(900 + M + K + L)
+    prob = synth.random_problem(rng, M, K, L, cut, displaced=disp, internal_basis=basis, r_range=(0.1, 0.5))
+    m, c = gb.gbsbin_moments(prob)
+    P = oracle.binned(prob, radix=prob.radix * (12 if L <= 2 else 8))["P"]
+    grids = np.meshgrid(*[np.arange(s) for s in P.shape], indexing="ij")
+    assert abs(P.sum() - 1) < 1e-12
+    mu = np.array([(P * g).sum() for g in grids])
+    cov = np.array([[(P * gi * gj).sum() - mu[i] * mu[j] for j, gj in enumerate(grids)] for i, gi in enumerate(grids)])
+    assert np.abs(m - mu).max() < 1e-10, (m, mu)
+    assert np.abs(c - cov).max() < 1e-9, (c, cov)
+    assert np.abs(c - c.T).max() < 1e-13
+
+
+def test_means_match_closed_form(gb):
+    # first moment per bin: sum_{j in group} (Sigma^(1)_jj + |zbar_j|^2), no table involved
+    rng = np.random.default_rng(931)
+    prob = synth.random_problem(rng, 12, 2, 3, 3, displaced=True, internal_basis=True, r_range=(0.5, 1.2))
+    m, c = gb.gbsbin_moments(prob)
+    s1, zbar = state.sigma1_zbar(prob)
+    MK = prob.M * prob.K
+    labels = np.repeat(prob.bin_of_mode, prob.K)
+    expect = [sum((s1[i, i] + abs(zbar[i]) ** 2).real for i in range(MK) if labels[i] == l) for l in range(prob.L)]
+    assert np.abs(m - np.array(expect)).max() < 1e-11
+    assert np.all(np.linalg.eigvalsh(c) > 0)
+
+
+def test_rejects_bad_input(gb):
+    bad = synth.config(0)
+    bad.bin_of_mode = np.array([0, 0, 0, 0], np.int32)
+    with pytest.raises(gb.GbsbinError):
+        gb.gbsbin_moments(bad)
