@@ -145,10 +145,11 @@ typedef enum {
   GBSBIN_KERNEL_BLK_TC_FP32R = 7,  /* as 6, the trace-correction updates on the tensor
                                       cores (tcgen05, 3 x TF32, TMEM accumulator)         */
   GBSBIN_KERNEL_HESS_FP64 = 8      /* one detector group (L = 1, the total photon number of
-                                      Sec. VIII) and no displacement: D(w) = w I, so one
-                                      Hessenberg reduction XA = Q H Q^H per state serves
-                                      every point, O(n^2) per point (warp per point, FP64);
-                                      chosen automatically for such problems              */
+                                      Sec. VIII): D(w) = w I, so one Hessenberg reduction
+                                      XA = Q H Q^H per state (host) serves every point,
+                                      O(n^2) per point (warp per point, FP64), displacement
+                                      through Q^T gamma and Q^H X gamma; chosen
+                                      automatically for L = 1                              */
 } gbsbin_kernel;
 
 /* Fill *o with defaults: FP64, oversample 1, diagnostics on, automatic kernel. */

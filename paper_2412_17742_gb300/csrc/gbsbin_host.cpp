@@ -345,9 +345,9 @@ int upload_state(gbsbin_plan* P, cudaStream_t stream) {
 }
 
 // In place: A (n x n, row-major) <- Q^H A Q upper Hessenberg, Q a product of Householder
-// reflectors (FP64).  Similar matrices share det(I - w A) for every w, which is all the
-// one-group evaluation needs; the reflectors are not kept.
-void hessenberg(std::vector<cd>& A, int n) {
+// reflectors (FP64); each reflector is also applied to the vectors in `vecs` (which become
+// Q^H vec).  Similar matrices share det(I - w A) for every w.
+void hessenberg(std::vector<cd>& A, int n, std::vector<std::vector<cd>*> vecs = {}) {
   std::vector<cd> v(n), sv(n);
   for (int k = 0; k + 2 < n; ++k) {
     double nrm2 = 0.0;
@@ -383,18 +383,31 @@ void hessenberg(std::vector<cd>& A, int n) {
       t *= beta;
       for (int j = k + 1; j < n; ++j) row[j] -= t * std::conj(v[j]);
     }
+    for (std::vector<cd>* x : vecs) {           // x <- (I - beta v v^H) x
+      cd t = 0.0;
+      for (int i = k + 1; i < n; ++i) t += std::conj(v[i]) * (*x)[i];
+      t *= beta;
+      for (int i = k + 1; i < n; ++i) (*x)[i] -= t * v[i];
+    }
     A[(size_t)(k + 1) * n + k] = alpha;
     for (int i = k + 2; i < n; ++i) A[(size_t)i * n + k] = 0.0;
   }
 }
 
-// The one-group plans' Hessenberg form of the current XA, uploaded on `stream`.
+// The one-group plans' Hessenberg form of the current XA, followed by a = Q^T gamma and
+// c = Q^H X gamma (the exponent gamma^T (conj(w) - XA)^{-1} X gamma = a^T (conj(w) - H)^{-1} c),
+// uploaded on `stream`.
 int upload_hessenberg(gbsbin_plan* P, cudaStream_t stream) {
   const int n = P->n;
-  std::vector<cd> H(P->XA);
-  hessenberg(H, n);
-  std::vector<double2> h((size_t)n * n);
-  for (size_t q = 0; q < h.size(); ++q) h[q] = make_double2(H[q].real(), H[q].imag());
+  std::vector<cd> H(P->XA), ga(n), c(P->Xgamma);
+  for (int i = 0; i < n; ++i) ga[i] = std::conj(P->gamma[i]);     // Q^T g = conj(Q^H conj(g))
+  hessenberg(H, n, {&ga, &c});
+  std::vector<double2> h((size_t)n * n + 2 * (size_t)n);
+  for (size_t q = 0; q < (size_t)n * n; ++q) h[q] = make_double2(H[q].real(), H[q].imag());
+  for (int i = 0; i < n; ++i) {
+    h[(size_t)n * n + i] = make_double2(ga[i].real(), -ga[i].imag());
+    h[(size_t)n * n + n + i] = make_double2(c[i].real(), c[i].imag());
+  }
   // a pageable source: the call returns once the data are staged, so h may go out of scope
   if (cudaMemcpyAsync(P->d_H, h.data(), h.size() * sizeof(double2), cudaMemcpyHostToDevice, stream) != cudaSuccess)
     return GBSBIN_ERR_CUDA;
@@ -486,7 +499,7 @@ inline bool is_blk(int kernel) { return kernel == GBSBIN_KERNEL_BLK_FP32R || ker
 
 int choose_kernel(int n, int L, int precision, int override_id, int has_gamma) {
   if (override_id) return override_id;
-  if (L == 1 && !has_gamma) return GBSBIN_KERNEL_HESS_FP64;   // one group, undisplaced
+  if (L == 1) return GBSBIN_KERNEL_HESS_FP64;   // one group
   if (precision == GBSBIN_FP32_REFINE && n <= 32) return GBSBIN_KERNEL_WARP_FP32R;
   if (precision == GBSBIN_FP32_REFINE && n > GBSBIN_SMEM_MAX_N && n <= GBSBIN_BLK_MAX_N) return GBSBIN_KERNEL_BLK_FP32R;
   if (precision == GBSBIN_FP64)
@@ -592,7 +605,7 @@ static int plan_create_impl(const gbsbin_problem* p, const gbsbin_options* o, gb
   }
   record_inputs(P, p);
   P->kernel = choose_kernel(n, p->L, opt.precision, opt.tile_override, P->has_gamma);
-  if (P->kernel == GBSBIN_KERNEL_HESS_FP64 && (p->L != 1 || P->has_gamma)) {
+  if (P->kernel == GBSBIN_KERNEL_HESS_FP64 && p->L != 1) {
     delete P;
     return GBSBIN_ERR_UNSUPPORTED;
   }
@@ -651,7 +664,7 @@ static int plan_create_impl(const gbsbin_problem* p, const gbsbin_options* o, gb
     delete P;
     return st;
   }
-  if (P->kernel == GBSBIN_KERNEL_HESS_FP64 && (st = dalloc(&P->d_H, nn))) {
+  if (P->kernel == GBSBIN_KERNEL_HESS_FP64 && (st = dalloc(&P->d_H, nn + 2 * (size_t)n))) {
     free_device(P);
     delete P;
     return st;
@@ -743,7 +756,6 @@ int gbsbin_plan_set_state(gbsbin_plan* P, const gbsbin_problem* p, void* stream)
   int has_gamma = 0;
   st = build_state(p, P->n, XA, gamma, Xgamma, &has_gamma, &zbar);
   if (st) return st;
-  if (P->kernel == GBSBIN_KERNEL_HESS_FP64 && has_gamma) return GBSBIN_ERR_UNSUPPORTED;  // one-group path: undisplaced only
   record_inputs(P, p);
   P->saved_valid = false;
   P->zbar.swap(zbar);
@@ -1357,8 +1369,8 @@ int gbsbin_batch_create(const gbsbin_problem* probs, int nprob, const gbsbin_opt
     gbsbin_options oi = opt;
     int p_override = 0;
     const int n = 2 * probs[i].M * probs[i].K;
-    // one-group undisplaced problems keep the Hessenberg path whatever the size's tuning
-    const bool one_group = probs[i].L == 1 && !probs[i].alpha && !(probs[i].sigma1 && probs[i].zbar);
+    // one-group problems keep the Hessenberg path whatever the size's tuning
+    const bool one_group = probs[i].L == 1;
     if (autotune && !opt.tile_override && n <= GBSBIN_MAX_N && !one_group) {
       TuneVal v{};
       int st = autotune_lookup(n, opt.precision, &v);

@@ -1,5 +1,5 @@
-// One detector group, no displacement (arXiv:2412.17742, Sec. VIII, total photon-number
-// distribution; Sec. III Eq. q_d with a single group): D(w) = w I, so
+// One detector group (arXiv:2412.17742, Sec. VIII, total photon-number distribution;
+// Sec. III Eq. q_d with a single group): D(w) = w I, so
 //
 //   K(w) = I - w XA = Q (I - w H) Q^H,   XA = Q H Q^H with H upper Hessenberg,
 //
@@ -11,10 +11,18 @@
 // ||XA|| < 1, so B has a positive-definite Hermitian part, as do its Schur complements), so
 // sum_i Log p_i is the branch of log det K continuous from w = 0.
 //
+// Displacement: the exponent gamma^T (conj(w) - XA)^{-1} X gamma = -a^T N^{-1} c with
+// N = H - conj(w) I, a = Q^T gamma, c = Q^H X gamma (reflectors applied on the host).  With
+// N = L_N U_N from the same sweep, y = L_N^{-1} c is a scalar recurrence (L_N is bidiagonal:
+// y_{i+1} = c_{i+1} - l_i y_i) and z^T = a^T U_N^{-1} follows row by row as the rows of U_N
+// appear (z_i = (a_i - s_i) / u_ii, then s_j += z_i u_ij for j > i), so a^T N^{-1} c =
+// sum_i z_i y_i needs no stored factors.
+//
 // One warp per point, FP64: lane t holds entries j = lane + 32 s of the current pivot row
-// in registers (s < 16, n <= 512); row i + 1 of H - conj(w) I is read from the L2-resident
-// H.  log q = -1/2 log det K is left unfinished as (product of pivots with its power of two,
-// FP32 sum of their arguments), finished one point per thread by the DFT's first stage.
+// (and of the running sums s) in registers (s < 16, n <= 512); row i + 1 of H - conj(w) I is
+// read from the L2-resident H.  log q = 1/2 gamma^T x - 1/2 log det K is left unfinished as
+// (product of pivots with its power of two, FP32 sum of their arguments, the rest), finished
+// one point per thread by the DFT's first stage.
 #include <cuda_runtime.h>
 
 #include "gbsbin_device.cuh"
@@ -41,6 +49,7 @@ __device__ __forceinline__ int renormalise(double2& z) {
   return ex;
 }
 
+template <bool DISP>
 __device__ void hess_point(const PointArgs& a, long long e) {
   const int n = a.n, lane = threadIdx.x & 31;
   const int S = (n + 31) >> 5;
@@ -48,8 +57,11 @@ __device__ void hess_point(const PointArgs& a, long long e) {
   const double2 sg = make_double2(w.x, -w.y);                  // conj(w)
   const double2 mw = make_double2(-w.x, -w.y);                 // pivots of B = -w x pivots here
   const double2* H = a.H;
-  // row 0 of H - conj(w) I
-  double2 r[SMAX];
+  const double2* av = H + (size_t)n * n;        // a = Q^T gamma
+  const double2* cv = av + n;                   // c = Q^H X gamma
+  constexpr bool disp = DISP;
+  // row 0 of H - conj(w) I (the running sums only for displaced states)
+  double2 r[SMAX], sacc[DISP ? SMAX : 1];
 #pragma unroll
   for (int s = 0; s < SMAX; ++s) {
     const int j = lane + 32 * s;
@@ -59,7 +71,10 @@ __device__ void hess_point(const PointArgs& a, long long e) {
       if (j == 0) v = make_double2(v.x - sg.x, v.y - sg.y);
     }
     r[s] = v;
+    if constexpr (DISP) sacc[s] = make_double2(0.0, 0.0);
   }
+  double2 y = disp ? cv[0] : make_double2(0.0, 0.0);
+  double2 zy = make_double2(0.0, 0.0);          // sum_i z_i y_i
   double2 prod = make_double2(1.0, 0.0);
   int e2 = 0;
   float args = 0.0f;
@@ -72,6 +87,19 @@ __device__ void hess_point(const PointArgs& a, long long e) {
       if (i >= n) break;
       const double2 q = shfl_d2(r[sb], il);     // pivot of H - conj(w) I
       const double2 p = cmul(mw, q);            // pivot of B = I - w H
+      const double2 iq = crecip(q);
+      if constexpr (DISP) {                     // z_i, then the running sums of later columns
+        const double2 si = shfl_d2(sacc[sb], il);
+        const double2 ai = av[i];
+        const double2 zi = cmul(make_double2(ai.x - si.x, ai.y - si.y), iq);
+        zy = make_double2(zy.x + (zi.x * y.x - zi.y * y.y), zy.y + (zi.x * y.y + zi.y * y.x));
+#pragma unroll
+        for (int s = 0; s < SMAX; ++s) {
+          const int j = lane + 32 * s;
+          if (s < S && j > i && j < n) sacc[s] = make_double2(sacc[s].x + (zi.x * r[s].x - zi.y * r[s].y),
+                                                              sacc[s].y + (zi.x * r[s].y + zi.y * r[s].x));
+        }
+      }
       mn = fmin(mn, p.x);
       if (!(p.x == p.x) || !(p.y == p.y)) mn = -1.0e300;
       args += atan2f((float)p.y, (float)p.x);
@@ -79,7 +107,8 @@ __device__ void hess_point(const PointArgs& a, long long e) {
       if (i == n - 1) break;
       // row i + 1: its only entry left of the diagonal is H[i+1][i]; l = that / q
       const double2* hrow = H + (size_t)(i + 1) * n;
-      const double2 l = cmul(hrow[i], crecip(q));
+      const double2 l = cmul(hrow[i], iq);
+      if constexpr (DISP) y = cfnma(cv[i + 1], l, y);   // y_{i+1} = c_{i+1} - l_i y_i
 #pragma unroll
       for (int s = 0; s < SMAX; ++s) {
         const int j = lane + 32 * s;
@@ -98,50 +127,60 @@ __device__ void hess_point(const PointArgs& a, long long e) {
     f[0] = prod.x;
     f[1] = prod.y;
     f[2] = (double)args;
-    f[3] = -0.5 * (double)e2 * LN2;             // log q = -1/2 log det K (no exponent term)
-    f[4] = 0.0;
+    // log q = 1/2 gamma^T x - 1/2 log det K, gamma^T x = -sum_i z_i y_i
+    f[3] = -0.5 * (double)e2 * LN2 - 0.5 * zy.x;
+    f[4] = -0.5 * zy.y;
     f[5] = 0.0;
     a.minpiv[e] = mn;
   }
 }
 
+// MODE 0 / 1: one problem, undisplaced / displaced (each with its own register budget);
+// MODE 2: a batch job queue, displacement decided per problem.
+template <int MODE>
 __global__ void __launch_bounds__(HW * 32) k_points_hess(PointArgs a0, PointBatch batch) {
   const int warp = threadIdx.x >> 5;
-  if (!batch.probs) {
+  if constexpr (MODE < 2) {
     for (long long e = (long long)blockIdx.x * HW + warp; e < a0.grid.n_eval; e += (long long)gridDim.x * HW)
-      hess_point(a0, e);
-    return;
-  }
-  __shared__ PointArgs sa;
-  __shared__ long long sj;
-  for (;;) {
-    if (threadIdx.x == 0) {
-      const unsigned long long j = atomicAdd(batch.queue, 1ull);
-      sj = (long long)j;
-      if ((long long)j < batch.njobs) sa = batch.probs[batch.jobs[j].prob];
+      hess_point<MODE == 1>(a0, e);
+  } else {
+    __shared__ PointArgs sa;
+    __shared__ long long sj;
+    for (;;) {
+      if (threadIdx.x == 0) {
+        const unsigned long long j = atomicAdd(batch.queue, 1ull);
+        sj = (long long)j;
+        if ((long long)j < batch.njobs) sa = batch.probs[batch.jobs[j].prob];
+      }
+      __syncthreads();
+      const long long j = sj;
+      if (j >= batch.njobs) break;
+      const long long e = batch.jobs[j].e0 + warp;
+      if (e < sa.grid.n_eval) sa.has_gamma ? hess_point<true>(sa, e) : hess_point<false>(sa, e);
+      __syncthreads();
     }
-    __syncthreads();
-    const long long j = sj;
-    if (j >= batch.njobs) break;
-    const long long e = batch.jobs[j].e0 + warp;
-    if (e < sa.grid.n_eval) hess_point(sa, e);
-    __syncthreads();
   }
 }
 
-}  // namespace
-
-cudaError_t launch_points_hess(const PointArgs& a, const PointBatch& batch, int num_sms, cudaStream_t s) {
+template <int MODE>
+cudaError_t launch_hess_mode(const PointArgs& a, const PointBatch& batch, int num_sms, cudaStream_t s) {
   int per_sm = 0;
-  cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_points_hess, HW * 32, 0);
+  cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_points_hess<MODE>, HW * 32, 0);
   if (err != cudaSuccess) return err;
   if (per_sm < 1) per_sm = 1;
   const long long groups = batch.probs ? batch.njobs : (a.grid.n_eval + HW - 1) / HW;
   long long grid = (long long)per_sm * num_sms;
   if (grid > groups) grid = groups;
   if (grid < 1) grid = 1;
-  k_points_hess<<<(unsigned)grid, HW * 32, 0, s>>>(a, batch);
+  k_points_hess<MODE><<<(unsigned)grid, HW * 32, 0, s>>>(a, batch);
   return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_points_hess(const PointArgs& a, const PointBatch& batch, int num_sms, cudaStream_t s) {
+  if (batch.probs) return launch_hess_mode<2>(a, batch, num_sms, s);
+  return a.has_gamma ? launch_hess_mode<1>(a, batch, num_sms, s) : launch_hess_mode<0>(a, batch, num_sms, s);
 }
 
 }  // namespace gbsbin

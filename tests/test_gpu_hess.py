@@ -1,6 +1,7 @@
-"""One detector group without displacement (the total photon number of Sec. VIII): the
-Hessenberg path (one reduction per state, O(n^2) per point) against the oracle's LU, the
-general kernels, and the closed form of the uniform-loss setup of Sec. VIII up to n = 512."""
+"""One detector group (the total photon number of Sec. VIII): the Hessenberg path (one
+reduction per state, O(n^2) per point, displacement through the reflected vectors) against
+the oracle's LU, the general kernels, and the closed form of the uniform-loss setup of
+Sec. VIII up to n = 512."""
 import numpy as np
 import pytest
 
@@ -9,12 +10,14 @@ import synth
 
 pytestmark = pytest.mark.gpu
 
-CASES = [  # (M, K, cutoff, internal basis)
-    (4, 1, 12, False),      # n = 8
-    (15, 1, 30, False),     # n = 30: one ragged row block
-    (32, 1, 20, False),     # n = 64
-    (25, 2, 16, True),      # n = 100, internal modes
-    (100, 1, 9, False),     # n = 200
+CASES = [  # (M, K, cutoff, internal basis, displaced)
+    (4, 1, 12, False, False),      # n = 8
+    (4, 1, 12, False, True),
+    (15, 1, 30, False, True),      # n = 30: one ragged row block
+    (32, 1, 20, False, False),     # n = 64
+    (25, 2, 16, True, True),       # n = 100, internal modes
+    (100, 1, 9, False, False),     # n = 200
+    (100, 1, 9, False, True),
 ]
 
 
@@ -26,10 +29,11 @@ def _flat(digits, radix):
 
 
 @pytest.mark.parametrize("precision", [0, 1])
-@pytest.mark.parametrize("M,K,cut,basis", CASES)
-def test_one_group_matches_oracle(cuda_lib, M, K, cut, basis, precision):
+@pytest.mark.parametrize("M,K,cut,basis,disp", CASES)
+def test_one_group_matches_oracle(cuda_lib, M, K, cut, basis, disp, precision):
     gb = cuda_lib
-    prob = synth.random_problem(np.random.default_rng(500 + M + K), M, K, 1, cut, internal_basis=basis)
+    prob = synth.random_problem(np.random.default_rng(500 + M + K), M, K, 1, cut, internal_basis=basis,
+                                displaced=disp)
     with gb.Plan(prob, precision=precision) as p:
         P = p.table().cpu().numpy()
         st, d = p.diagnostics()
@@ -75,26 +79,20 @@ def test_uniform_loss_total_number_closed_form(cuda_lib, row):
     assert abs(P.sum() - 1.0) < 1e-12
 
 
-def test_one_group_fallbacks_and_errors(cuda_lib):
+def test_one_group_state_changes_and_errors(cuda_lib):
     gb = cuda_lib
     rng = np.random.default_rng(520)
-    disp = synth.random_problem(rng, 6, 1, 1, 10, displaced=True)
-    with gb.Plan(disp) as p:                      # displaced: the general path
-        P = p.table().cpu().numpy()
-        st, d = p.diagnostics()
-    assert d["kernel_name"] != "hess_fp64"
-    assert np.abs(P - oracle.binned(disp)["P"]).max() <= 1e-10
     two = synth.random_problem(rng, 6, 1, 2, [3, 4])
-    for bad in (disp, two):                       # forcing the one-group path where it does not apply
-        with pytest.raises(gb.GbsbinError):
-            gb.Plan(bad, tile_override=8)
-    # a new undisplaced state on a one-group plan; a displaced one is refused
+    with pytest.raises(gb.GbsbinError):          # forcing the one-group path on two groups
+        gb.Plan(two, tile_override=8)
+    # new states on a one-group plan: undisplaced, then displaced
     a = synth.random_problem(np.random.default_rng(521), 10, 1, 1, 14)
     b = synth.random_problem(np.random.default_rng(522), 10, 1, 1, 14)
+    c = synth.random_problem(np.random.default_rng(523), 10, 1, 1, 14, displaced=True)
     with gb.Plan(a) as p:
-        gb.gbsbin_plan_set_state(p.handle, b)
-        Pb = p.table().cpu().numpy()
-        assert np.abs(Pb - oracle.binned(b)["P"]).max() <= 1e-10
-        b.alpha = 0.3 * np.ones((10, 1), complex)
-        with pytest.raises(gb.GbsbinError):
-            gb.gbsbin_plan_set_state(p.handle, b)
+        for new in (b, c):
+            gb.gbsbin_plan_set_state(p.handle, new)
+            Pn = p.table().cpu().numpy()
+            st, d = p.diagnostics()
+            assert st == 0 and d["kernel_name"] == "hess_fp64"
+            assert np.abs(Pn - oracle.binned(new)["P"]).max() <= 1e-10
