@@ -29,6 +29,9 @@ struct gbsbin_plan {
   std::vector<cd> XA, gamma, Xgamma;
   // device buffers
   int P = 1;  // grid points per CTA of the point kernel
+  // the state arrays below live in one device block laid out like the pinned staging
+  // buffer, so an upload is a single copy
+  unsigned char* d_state = nullptr;
   double2 *d_NXA = nullptr, *d_gamma = nullptr, *d_Xgamma = nullptr;
   float2 *d_NXA_hi = nullptr, *d_NXA_lo = nullptr, *d_Xg_hi = nullptr, *d_Xg_lo = nullptr;
   float2 *d_g_hi = nullptr, *d_g_lo = nullptr;
@@ -241,10 +244,8 @@ int build_state(const gbsbin_problem* p, int n, std::vector<cd>& XA, std::vector
 }
 
 void free_device(gbsbin_plan* P) {
-  void* ptrs[] = {P->d_NXA,  P->d_gamma, P->d_Xgamma, P->d_NXA_hi, P->d_NXA_lo, P->d_Xg_hi,
-                  P->d_Xg_lo, P->d_g_hi, P->d_g_lo,   P->d_label, P->d_logq,  P->d_minpiv,
-                  P->d_bufA, P->d_bufB,  P->d_tw,     P->d_diag,  P->d_gws,   P->d_table,
-                  P->d_NXA_fix, P->d_ldfin, P->d_bar, P->d_H};
+  void* ptrs[] = {P->d_state, P->d_label, P->d_logq,  P->d_minpiv, P->d_bufA, P->d_bufB,
+                  P->d_tw,    P->d_diag,  P->d_gws,   P->d_table,  P->d_ldfin, P->d_bar,  P->d_H};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (P->h_stage) cudaFreeHost(P->h_stage);
@@ -326,20 +327,9 @@ int upload_state(gbsbin_plan* P, cudaStream_t stream) {
     split(P->Xgamma[i], &Xghi[i], &Xglo[i]);
     split(P->gamma[i], &ghi[i], &glo[i]);
   }
-  struct {
-    void* dst;
-    size_t off, bytes;
-  } cp[] = {
-      {P->d_NXA, s.off_XA, (size_t)n * n * sizeof(double2)},   {P->d_gamma, s.off_g, n * sizeof(double2)},
-      {P->d_Xgamma, s.off_Xg, n * sizeof(double2)},           {P->d_NXA_hi, s.off_XAhi, (size_t)n * n * sizeof(float2)},
-      {P->d_NXA_lo, s.off_XAlo, (size_t)n * n * sizeof(float2)}, {P->d_Xg_hi, s.off_Xghi, n * sizeof(float2)},
-      {P->d_Xg_lo, s.off_Xglo, n * sizeof(float2)},           {P->d_g_hi, s.off_ghi, n * sizeof(float2)},
-      {P->d_g_lo, s.off_glo, n * sizeof(float2)},             {P->d_NXA_fix, s.off_XAfix, (size_t)n * n * sizeof(longlong2)},
-  };
-  for (auto& c : cp) {
-    e = cudaMemcpyAsync(c.dst, h + c.off, c.bytes, cudaMemcpyHostToDevice, stream);
-    if (e != cudaSuccess) return GBSBIN_ERR_CUDA;
-  }
+  // the device block has the staging layout: one copy
+  e = cudaMemcpyAsync(P->d_state, h, s.total, cudaMemcpyHostToDevice, stream);
+  if (e != cudaSuccess) return GBSBIN_ERR_CUDA;
   if (P->kernel == GBSBIN_KERNEL_HESS_FP64) return upload_hessenberg(P, stream);
   return GBSBIN_OK;
 }
@@ -632,11 +622,8 @@ static int plan_create_impl(const gbsbin_problem* p, const gbsbin_options* o, gb
   }
   const size_t nn = (size_t)n * n;
   Stage sl = stage_layout(n);
-  if ((st = dalloc(&P->d_NXA, nn)) || (st = dalloc(&P->d_gamma, n)) || (st = dalloc(&P->d_Xgamma, n)) ||
-      (st = dalloc(&P->d_NXA_hi, nn)) || (st = dalloc(&P->d_NXA_lo, nn)) || (st = dalloc(&P->d_Xg_hi, n)) ||
-      (st = dalloc(&P->d_NXA_fix, nn)) ||
-      (st = dalloc(&P->d_Xg_lo, n)) || (st = dalloc(&P->d_g_hi, n)) || (st = dalloc(&P->d_g_lo, n)) ||
-      (st = dalloc(&P->d_label, n)) || (st = dalloc(&P->d_logq, g.n_eval)) ||
+  (void)nn;
+  if ((st = dalloc(&P->d_state, sl.total)) || (st = dalloc(&P->d_label, n)) || (st = dalloc(&P->d_logq, g.n_eval)) ||
       (st = dalloc(&P->d_minpiv, g.n_eval)) || (st = dalloc(&P->d_bufA, g.n_full)) ||
       (st = dalloc(&P->d_bufB, g.n_full)) || (st = dalloc(&P->d_diag, 4 * GBSBIN_DIAG_BLOCKS + 2)) ||
       (st = dalloc(&P->d_bar, 4)) ||
@@ -645,6 +632,16 @@ static int plan_create_impl(const gbsbin_problem* p, const gbsbin_options* o, gb
     delete P;
     return st;
   }
+  P->d_NXA = (double2*)(P->d_state + sl.off_XA);          // all offsets are multiples of 16
+  P->d_gamma = (double2*)(P->d_state + sl.off_g);
+  P->d_Xgamma = (double2*)(P->d_state + sl.off_Xg);
+  P->d_NXA_hi = (float2*)(P->d_state + sl.off_XAhi);
+  P->d_NXA_lo = (float2*)(P->d_state + sl.off_XAlo);
+  P->d_Xg_hi = (float2*)(P->d_state + sl.off_Xghi);
+  P->d_Xg_lo = (float2*)(P->d_state + sl.off_Xglo);
+  P->d_g_hi = (float2*)(P->d_state + sl.off_ghi);
+  P->d_g_lo = (float2*)(P->d_state + sl.off_glo);
+  P->d_NXA_fix = (longlong2*)(P->d_state + sl.off_XAfix);
   if (cudaMemset(P->d_bar, 0, 4 * sizeof(unsigned)) != cudaSuccess ||
       cudaMemset(P->d_diag, 0, (4 * GBSBIN_DIAG_BLOCKS + 2) * sizeof(double)) != cudaSuccess) {
     free_device(P);
