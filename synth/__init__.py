@@ -164,3 +164,61 @@ def random_problem(rng: np.random.Generator, M: int, K: int, L: int, cutoff,
         alpha = 0.4 * (rng.standard_normal((M, K)) + 1j * rng.standard_normal((M, K)))
     V = np.stack([haar_unitary(K, rng) for _ in range(M)]) if internal_basis else None
     return Problem(M, K, r, T, lab, cut, alpha=alpha, V=V, name=f"rand_m{M}_k{K}_l{L}")
+
+
+# ---------------------------------------------------------------- Fock inputs (App. C)
+@dataclass
+class FockProblem:
+    """Photon-number (Fock) inputs through a lossy linear circuit, binned outputs.
+
+    ``photons[j]`` photons enter input port ``j`` of the ``M x M`` transfer matrix ``T``
+    (row = output port, ``||T|| <= 1``); ``bin_of_mode[i]`` groups output port ``i``;
+    ``cutoff[l]`` is ``N_l``."""
+
+    M: int
+    T: np.ndarray                      # (M, M) complex128, row = output port
+    photons: np.ndarray                # (M,) int32 >= 0
+    bin_of_mode: np.ndarray            # (M,) int32, values in [0, L)
+    cutoff: np.ndarray                 # (L,) int32
+    name: str = ""
+
+    @property
+    def L(self) -> int:
+        return int(self.cutoff.shape[0])
+
+    @property
+    def N(self) -> int:
+        return int(np.sum(self.photons))
+
+    @property
+    def radix(self) -> np.ndarray:
+        return (self.cutoff + 1).astype(np.int64)
+
+
+FOCK_SEED_INDEX = 50
+
+
+def fock_config(N: int = 16, M: int = 32, L: int = 3) -> FockProblem:
+    """Fock boson-sampling validation workload: single photons in input ports 0..N-1 of
+    an M-port interferometer T = diag(sqrt(eta_i)) U (Haar U, output loss eta_i ~
+    U(0.4, 0.9)), L contiguous detector groups, cutoff N_l = N (the whole table: no
+    group can see more than N photons)."""
+    rng = np.random.default_rng(SEED_BASE + FOCK_SEED_INDEX + N)
+    eta = rng.uniform(0.4, 0.9, M)
+    T = np.sqrt(eta)[:, None] * haar_unitary(M, rng)
+    photons = np.zeros(M, dtype=np.int32)
+    photons[:N] = 1
+    return FockProblem(M, T, photons, contiguous_bins(M, L), np.full(L, N, dtype=np.int32),
+                       name=f"fock_m{M}_n{N}_l{L}")
+
+
+def random_fock_problem(rng: np.random.Generator, M: int, photons, L: int, cutoff,
+                        eta_range=(0.3, 0.95), shuffle_bins: bool = False) -> FockProblem:
+    """Small random Fock-input problem for tests (photons: a length-M sequence)."""
+    eta = rng.uniform(*eta_range, M)
+    T = np.sqrt(eta)[:, None] * haar_unitary(M, rng)
+    lab = contiguous_bins(M, L)
+    if shuffle_bins:
+        lab = rng.permutation(lab).astype(np.int32)
+    cut = np.array(np.broadcast_to(np.asarray(cutoff, dtype=np.int32), (L,)), dtype=np.int32)
+    return FockProblem(M, T, np.asarray(photons, dtype=np.int32), lab, cut, name=f"fock_rand_m{M}_l{L}")
