@@ -144,12 +144,15 @@ typedef enum {
                                       slot, register-tiled updates (n <= 384)              */
   GBSBIN_KERNEL_BLK_TC_FP32R = 7,  /* as 6, the trace-correction updates on the tensor
                                       cores (tcgen05, 3 x TF32, TMEM accumulator)         */
-  GBSBIN_KERNEL_HESS_FP64 = 8      /* one detector group (L = 1, the total photon number of
+  GBSBIN_KERNEL_HESS_FP64 = 8,     /* one detector group (L = 1, the total photon number of
                                       Sec. VIII): D(w) = w I, so one Hessenberg reduction
                                       XA = Q H Q^H per state (host) serves every point,
                                       O(n^2) per point (warp per point, FP64), displacement
                                       through Q^T gamma and Q^H X gamma; chosen
                                       automatically for L = 1                              */
+  GBSBIN_KERNEL_FOCK_FP64 = 9,     /* Fock inputs (gbsbin_fock_*): FP64 throughout           */
+  GBSBIN_KERNEL_FOCK_DF32 = 10     /* Fock inputs: pairs of FP32 (hi + lo, ~46 bits) on the
+                                      FMA pipe, running sums flushed to FP64               */
 } gbsbin_kernel;
 
 /* Fill *o with defaults: FP64, oversample 1, diagnostics on, automatic kernel. */
@@ -313,6 +316,56 @@ int gbsbin_batch_destroy(gbsbin_batch* b);
  */
 int gbsbin_moments(const gbsbin_problem* p, double* mean, double* cov);
 
+/*
+ * Fock inputs through a lossy linear circuit (App. C of the paper).  photons[j] >= 0
+ * photons enter input port j of the M x M transfer matrix T (T[i*M + j]: output i <- input
+ * j, ||T||_2 <= 1), the output ports are grouped as for Gaussian states, and the library
+ * returns the binned output table.  The generating function of the binned counts is
+ *   G(z) = perm(B(z)[p, p]) / prod_j p_j!,   B(z) = I - T^dag (I - Z) T,  Z = diag(z_label(i)),
+ * the generating function of the diagonal elements of Eq. probs_fock_circuit over the
+ * output patterns.  The permanent is taken as the coefficient of x^p in
+ * prod_j (B(z) x)_j^{p_j} on roots-of-unity nodes x_k = exp(2 pi i g_k / (p_k + 1)) (exact:
+ * the polynomial is homogeneous of degree N = sum p, so with one occupied input of
+ * smallest p held at x = 1 nothing aliases), and the table is the inverse DFT of G over
+ * the grid z_l = exp(2 pi i k_l / R_l), R_l = oversample (N_l + 1), exactly as for
+ * gbsbin_execute: the folded table P~(b), 0 <= b_l <= N_l, which is P(b) itself when every
+ * N_l >= N (no group sees more than N photons).
+ * Work: prod over the other occupied inputs of (p_k + 1) nodes x (half the output grid)
+ * points, each factor O(L).  Options: precision GBSBIN_FP64 (kernel 9) or
+ * GBSBIN_FP32_REFINE, which here selects pairs of FP32 (kernel 10); oversample,
+ * want_diagnostics, want_timing and tile_override (9 or 10) as for gbsbin_plan_create;
+ * want_backward and shards are not supported (ERR_UNSUPPORTED).
+ * Limits: at most GBSBIN_FOCK_MAX_INPUTS occupied inputs, GBSBIN_FOCK_MAX_PER_INPUT photons
+ * in one input, GBSBIN_FOCK_MAX_GROUPS groups, GBSBIN_FOCK_MAX_NODES nodes, the output grid as for Gaussian states (ERR_UNSUPPORTED /
+ * ERR_CUTOFF).  ERR_NONPHYSICAL if ||T||_2 > 1.  All arrays are host memory read during
+ * the call.  gbsbin_fock_diagnostics fills sum_P and max_imag as gbsbin_diagnostics does,
+ * n_points (output grid), n_evaluated (half-grid points), n = occupied inputs, kernel and
+ * point_kernel_ms; min_pivot_re = 1, n_bad_points = 0 and log_q1_re = 0 do not apply.
+ */
+#define GBSBIN_FOCK_MAX_INPUTS 32
+#define GBSBIN_FOCK_MAX_GROUPS 8
+#define GBSBIN_FOCK_MAX_NODES (1LL << 40)
+#define GBSBIN_FOCK_MAX_PER_INPUT (1 << 20)   /* photons in one input port */
+typedef struct {
+  int M;
+  const gbsbin_complex* T;
+  const int* photons;
+  const int* bin_of_mode;
+  int L;
+  const int* cutoff;
+} gbsbin_fock_problem;
+typedef struct gbsbin_fock_plan gbsbin_fock_plan;
+int gbsbin_fock_plan_create(const gbsbin_fock_problem* p, const gbsbin_options* o, gbsbin_fock_plan** out);
+/* New transfer matrix T (same M, photons, grouping, cutoffs): host FP64 algebra, one
+ * upload enqueued on `stream`.  ERR_ARG / ERR_NONPHYSICAL as for plan creation. */
+int gbsbin_fock_plan_set_transfer(gbsbin_fock_plan* plan, const gbsbin_complex* T, void* stream);
+long long gbsbin_fock_plan_table_size(const gbsbin_fock_plan* plan);
+/* Table to P_out (device, table_size doubles, last group fastest); asynchronous. */
+int gbsbin_fock_execute(gbsbin_fock_plan* plan, double* P_out, void* stream);
+/* The same into host memory; synchronises `stream`. */
+int gbsbin_fock_execute_host(gbsbin_fock_plan* plan, double* P_out_host, void* stream);
+int gbsbin_fock_diagnostics(gbsbin_fock_plan* plan, gbsbin_diag* out, void* stream);
+int gbsbin_fock_plan_destroy(gbsbin_fock_plan* plan);
 /* Static description of a status code. */
 const char* gbsbin_strerror(int status);
 

@@ -24,13 +24,16 @@ _lib = None
 GBSBIN_FP64 = 0
 GBSBIN_FP32_REFINE = 1
 KERNELS = {1: "smem_fp64", 2: "smem_fp32r", 3: "gmem_fp64", 4: "gmem_fp32r", 5: "warp_fp32r", 6: "blk_fp32r",
-           7: "blk_tc_fp32r", 8: "hess_fp64"}
+           7: "blk_tc_fp32r", 8: "hess_fp64", 9: "fock_fp64", 10: "fock_df32"}
 EXPORTED = ["gbsbin_default_options", "gbsbin_plan_create", "gbsbin_plan_set_state", "gbsbin_plan_destroy",
             "gbsbin_plan_table_size", "gbsbin_execute", "gbsbin_execute_host", "gbsbin_diagnostics",
             "gbsbin_strerror", "gbsbin_alu_peak", "gbsbin_read_points", "gbsbin_table_from_logq_noalloc",
             "gbsbin_backward", "gbsbin_autotune", "gbsbin_batch_create", "gbsbin_batch_execute",
             "gbsbin_batch_capture_graph", "gbsbin_batch_replay", "gbsbin_batch_table_size",
-            "gbsbin_batch_diagnostics", "gbsbin_batch_read_points", "gbsbin_batch_destroy", "gbsbin_moments"]
+            "gbsbin_batch_diagnostics", "gbsbin_batch_read_points", "gbsbin_batch_destroy", "gbsbin_moments",
+            "gbsbin_fock_plan_create", "gbsbin_fock_plan_set_transfer", "gbsbin_fock_plan_table_size",
+            "gbsbin_fock_execute", "gbsbin_fock_execute_host", "gbsbin_fock_diagnostics",
+            "gbsbin_fock_plan_destroy"]
 
 
 class GbsbinError(RuntimeError):
@@ -69,6 +72,11 @@ class gbsbin_diag(ctypes.Structure):
                 ("n_bad_points", ctypes.c_longlong), ("n_points", ctypes.c_longlong),
                 ("n_evaluated", ctypes.c_longlong), ("table_size", ctypes.c_longlong), ("n", ctypes.c_int),
                 ("kernel", ctypes.c_int), ("log_q1_re", ctypes.c_double), ("point_kernel_ms", ctypes.c_double)]
+
+
+class gbsbin_fock_problem(ctypes.Structure):
+    _fields_ = [("M", ctypes.c_int), ("T", _cp), ("photons", _ip), ("bin_of_mode", _ip), ("L", ctypes.c_int),
+                ("cutoff", _ip)]
 
 
 def load():
@@ -110,11 +118,22 @@ def load():
     lib.gbsbin_batch_diagnostics.argtypes = [vp, ctypes.c_int, ctypes.POINTER(gbsbin_diag), vp]
     lib.gbsbin_batch_read_points.argtypes = [vp, ctypes.c_int, vp, vp, vp]
     lib.gbsbin_batch_destroy.argtypes = [vp]
+    lib.gbsbin_fock_plan_create.argtypes = [ctypes.POINTER(gbsbin_fock_problem), ctypes.POINTER(gbsbin_options),
+                                            ctypes.POINTER(vp)]
+    lib.gbsbin_fock_plan_set_transfer.argtypes = [vp, _cp, vp]
+    lib.gbsbin_fock_plan_table_size.argtypes = [vp]
+    lib.gbsbin_fock_plan_table_size.restype = ctypes.c_longlong
+    lib.gbsbin_fock_execute.argtypes = [vp, vp, vp]
+    lib.gbsbin_fock_execute_host.argtypes = [vp, vp, vp]
+    lib.gbsbin_fock_diagnostics.argtypes = [vp, ctypes.POINTER(gbsbin_diag), vp]
+    lib.gbsbin_fock_plan_destroy.argtypes = [vp]
     for f in ("gbsbin_plan_create", "gbsbin_plan_set_state", "gbsbin_plan_destroy", "gbsbin_execute",
               "gbsbin_execute_host", "gbsbin_diagnostics", "gbsbin_alu_peak", "gbsbin_read_points",
               "gbsbin_table_from_logq_noalloc", "gbsbin_backward", "gbsbin_autotune", "gbsbin_batch_create",
               "gbsbin_batch_execute", "gbsbin_batch_capture_graph", "gbsbin_batch_replay",
-              "gbsbin_batch_diagnostics", "gbsbin_batch_read_points", "gbsbin_batch_destroy"):
+              "gbsbin_batch_diagnostics", "gbsbin_batch_read_points", "gbsbin_batch_destroy",
+              "gbsbin_fock_plan_create", "gbsbin_fock_plan_set_transfer", "gbsbin_fock_execute",
+              "gbsbin_fock_execute_host", "gbsbin_fock_diagnostics", "gbsbin_fock_plan_destroy"):
         getattr(lib, f).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -476,6 +495,109 @@ class Batch:
     def close(self):
         if getattr(self, "handle", None) is not None:
             _check(load().gbsbin_batch_destroy(self.handle), "gbsbin_batch_destroy")
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------------ Fock inputs (App. C)
+class FockProblemArgs:
+    """Marshals a Fock-input problem (M, T, photons, bin_of_mode, cutoff) into a
+    gbsbin_fock_problem; keeps the arrays alive."""
+
+    def __init__(self, prob):
+        self.M = int(prob.M)
+        self.T = np.ascontiguousarray(np.asarray(prob.T, dtype=np.complex128).reshape(-1))
+        self.photons = np.ascontiguousarray(np.asarray(prob.photons, dtype=np.int32))
+        self.bins = np.ascontiguousarray(np.asarray(prob.bin_of_mode, dtype=np.int32))
+        self.cut = np.ascontiguousarray(np.asarray(prob.cutoff, dtype=np.int32))
+        self.c = gbsbin_fock_problem(self.M, self.T.ctypes.data_as(_cp), self.photons.ctypes.data_as(_ip),
+                                     self.bins.ctypes.data_as(_ip), int(len(self.cut)), self.cut.ctypes.data_as(_ip))
+
+
+def gbsbin_fock_plan_create(prob, options=None):
+    lib = load()
+    args = FockProblemArgs(prob)
+    opts = options if options is not None else gbsbin_default_options()
+    h = ctypes.c_void_p()
+    _check(lib.gbsbin_fock_plan_create(ctypes.byref(args.c), ctypes.byref(opts), ctypes.byref(h)),
+           "gbsbin_fock_plan_create")
+    return h
+
+
+def gbsbin_fock_plan_set_transfer(plan, T, stream=None):
+    arr = np.ascontiguousarray(np.asarray(T, dtype=np.complex128).reshape(-1))
+    _check(load().gbsbin_fock_plan_set_transfer(plan, arr.ctypes.data_as(_cp), _stream_handle(stream)),
+           "gbsbin_fock_plan_set_transfer")
+
+
+def gbsbin_fock_plan_table_size(plan):
+    return int(load().gbsbin_fock_plan_table_size(plan))
+
+
+def gbsbin_fock_execute(plan, P_out, stream=None):
+    _check(load().gbsbin_fock_execute(plan, _ptr(P_out), _stream_handle(stream)), "gbsbin_fock_execute")
+
+
+def gbsbin_fock_execute_host(plan, P_out_host, stream=None):
+    _check(load().gbsbin_fock_execute_host(plan, _ptr(P_out_host), _stream_handle(stream)),
+           "gbsbin_fock_execute_host")
+
+
+def gbsbin_fock_diagnostics(plan, stream=None):
+    d = gbsbin_diag()
+    st = load().gbsbin_fock_diagnostics(plan, ctypes.byref(d), _stream_handle(stream))
+    out = {f: getattr(d, f) for f, _ in gbsbin_diag._fields_}
+    out["status"] = st
+    return out
+
+
+def gbsbin_fock_plan_destroy(plan):
+    _check(load().gbsbin_fock_plan_destroy(plan), "gbsbin_fock_plan_destroy")
+
+
+class FockPlan:
+    """Owning wrapper for Fock inputs: ``with FockPlan(prob) as p: P = p.table()``.
+
+    precision GBSBIN_FP64 runs the FP64 kernel, GBSBIN_FP32_REFINE the FP32-pair kernel."""
+
+    def __init__(self, prob, precision=GBSBIN_FP64, oversample=1, want_diagnostics=True, tile_override=0,
+                 want_timing=False):
+        self.options = make_options(precision, oversample, want_diagnostics, tile_override, want_timing)
+        self.handle = gbsbin_fock_plan_create(prob, self.options)
+        self.shape = tuple(int(c) + 1 for c in prob.cutoff)
+
+    def set_transfer(self, T, stream=None):
+        gbsbin_fock_plan_set_transfer(self.handle, T, stream)
+
+    def table(self, stream=None):
+        """Execute into a new CUDA float64 tensor shaped (N_1+1, ..., N_L+1)."""
+        import torch
+        out = torch.empty(self.shape, dtype=torch.float64, device="cuda")
+        gbsbin_fock_execute(self.handle, out, stream)
+        return out
+
+    def table_host(self, stream=None):
+        out = np.empty(self.shape, dtype=np.float64)
+        gbsbin_fock_execute_host(self.handle, out, stream)
+        return out
+
+    def diagnostics(self, stream=None):
+        return gbsbin_fock_diagnostics(self.handle, stream)
+
+    def close(self):
+        if self.handle is not None:
+            gbsbin_fock_plan_destroy(self.handle)
             self.handle = None
 
     def __enter__(self):

@@ -67,12 +67,34 @@ __device__ __forceinline__ void stage_normalise(const double2* logq, const GridD
   }
 }
 
+// G given as partial sums over nparts ranges of some inner sum (Fock inputs: node ranges
+// of the input-side extraction): G[t] = pscale sum_r parts[r n_full + t], r ascending.
+__device__ __forceinline__ void stage_sum_parts(const double2* __restrict__ parts, long long nparts, double pscale,
+                                                const GridDesc& g, double2* __restrict__ G, long long t0,
+                                                long long stride) {
+  for (long long t = t0; t < g.n_full; t += stride) {
+    double2 acc = make_double2(0.0, 0.0);
+    for (long long r = 0; r < nparts; ++r) {
+      const double2 v = parts[r * g.n_full + t];
+      acc.x += v.x;
+      acc.y += v.y;
+    }
+    G[t] = make_double2(acc.x * pscale, acc.y * pscale);
+  }
+}
+
 __global__ void k_normalise(const double2* logq, GridDesc g, double2* __restrict__ G,
                             const double* __restrict__ ldfin, double2* logq_fin) {
   __shared__ double2 s_l0;
   if (threadIdx.x == 0) s_l0 = ldfin ? finish_logq(ldfin) : logq[0];
   __syncthreads();
   stage_normalise(logq, g, G, ldfin, logq_fin, s_l0, blockIdx.x * (long long)blockDim.x + threadIdx.x,
+                  (long long)gridDim.x * blockDim.x);
+}
+
+__global__ void k_sum_parts(const double2* parts, long long nparts, double pscale, GridDesc g,
+                            double2* __restrict__ G) {
+  stage_sum_parts(parts, nparts, pscale, g, G, blockIdx.x * (long long)blockDim.x + threadIdx.x,
                   (long long)gridDim.x * blockDim.x);
 }
 
@@ -152,7 +174,7 @@ __device__ __forceinline__ void stage_diag(const double* __restrict__ P, long lo
     im = fmax(im, fabs(Y[o * H].y));
     if ((R & 1) == 0) im = fmax(im, fabs(Y[o * H + H - 1].y));
   }
-  for (long long e = t0; e < n_eval; e += stride) {
+  for (long long e = t0; minpiv && e < n_eval; e += stride) {
     double m = minpiv[e];
     double2 l = logq[e];
     bool ok = (m > 0.0) && isfinite(l.x) && isfinite(l.y);
@@ -186,7 +208,7 @@ __device__ __forceinline__ void stage_diag(const double* __restrict__ P, long lo
     out[1] = im;
     out[2] = mn;
     out[3] = bad;
-    if (vb == 0) part[4 * nvb] = logq[0].x;
+    if (vb == 0) part[4 * nvb] = logq ? logq[0].x : 0.0;
   }
 }
 
@@ -200,8 +222,9 @@ __global__ void k_diag(const double* __restrict__ P, long long table, const doub
 // The stages above run in sequence in one launch of co-resident CTAs (cooperative launch),
 // separated by a grid barrier: bar[0] counts arrivals, bar[1] is the generation, bar[2]
 // records a barrier that gave up waiting (after ~1 s), which the host reports as a CUDA
-// error.  Items are dealt to the CTAs cyclically (item t to CTA t mod gridDim), so the
-// FP64 work of every stage spreads over all SMs.  Every table entry is summed in the same order as in the multi-launch path, so
+// error.  Items are dealt to the CTAs cyclically (item t to CTA t mod gridDim), and within
+// a CTA across its warps, so the FP64 work of every stage spreads over all SMs and all
+// their schedulers.  Every table entry is summed in the same order as in the multi-launch path, so
 // the table is bit-identical to it (the diagnostics' partial sums are split differently).
 struct DftStage {
   long long outer, inner, twoff;
@@ -242,12 +265,19 @@ __device__ __forceinline__ void grid_barrier(unsigned* bar) {
 
 __global__ void __launch_bounds__(128) k_dft_fused(DftFused f) {
   const DftArgs& a = f.a;
-  const long long t0 = threadIdx.x * (long long)gridDim.x + blockIdx.x;
+  // the CTA's k-th item goes to lane k / 4 of warp k mod 4: a CTA's few items use all
+  // four schedulers' FP64 units instead of one warp's
+  const int tid = ((threadIdx.x & 31) << 2) | (threadIdx.x >> 5);
+  const long long t0 = tid * (long long)gridDim.x + blockIdx.x;
   const long long stride = (long long)gridDim.x * blockDim.x;
-  __shared__ double2 s_l0;
-  if (threadIdx.x == 0) s_l0 = a.ldfin ? finish_logq(a.ldfin) : a.logq[0];
-  __syncthreads();
-  stage_normalise(a.logq, a.grid, a.bufA, a.ldfin, a.logq_fin, s_l0, t0, stride);
+  if (a.parts) {
+    stage_sum_parts(a.parts, a.nparts, a.pscale, a.grid, a.bufA, t0, stride);
+  } else {
+    __shared__ double2 s_l0;
+    if (threadIdx.x == 0) s_l0 = a.ldfin ? finish_logq(a.ldfin) : a.logq[0];
+    __syncthreads();
+    stage_normalise(a.logq, a.grid, a.bufA, a.ldfin, a.logq_fin, s_l0, t0, stride);
+  }
   double2* cur = a.bufA;
   double2* nxt = a.bufB;
   for (int l = 0; l < f.naxes; ++l) {
@@ -282,7 +312,10 @@ static unsigned blocks_for(long long work) {
 cudaError_t launch_dft(const DftArgs& a, cudaStream_t s) {
   const GridDesc& g = a.grid;
   const int L = g.L;
-  k_normalise<<<blocks_for(g.n_full), kDftThreads, 0, s>>>(a.logq, g, a.bufA, a.ldfin, a.logq_fin);
+  if (a.parts)
+    k_sum_parts<<<blocks_for(g.n_full), kDftThreads, 0, s>>>(a.parts, a.nparts, a.pscale, g, a.bufA);
+  else
+    k_normalise<<<blocks_for(g.n_full), kDftThreads, 0, s>>>(a.logq, g, a.bufA, a.ldfin, a.logq_fin);
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return err;
   long long dims[GBSBIN_MAX_L];

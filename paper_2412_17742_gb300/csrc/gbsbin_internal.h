@@ -99,6 +99,11 @@ struct BackwardArgs {
 
 struct DftArgs {
   GridDesc grid;
+  const double2* parts;     // non-null: G is given as nparts partial sums per half-grid point
+                            // (parts[r * n_full + t]); the transform uses pscale * their sum
+                            // (summed in order r = 0, 1, ...) instead of exp(log q - log q_0)
+  long long nparts;
+  double pscale;
   const double2* logq;      // n_eval
   const double* ldfin;      // nullptr, or the warp kernel's unfinished log det (see PointArgs)
   double2* logq_fin;        // with ldfin: where the finished log q go (n_eval)
@@ -110,6 +115,39 @@ struct DftArgs {
   const double* minpiv;     // n_eval
   long long table_size;
 };
+
+// Fock inputs through a lossy circuit (gbsbin_fock.cu).  nin occupied inputs in position
+// order (position 0 is the held input, x = 1; positions 1..nd are the Gray digits); per
+// node x of the roots-of-unity grid the state is st_m = coef_m x (m = 0: I - T^dag T,
+// m = 1 + l: T_l^dag T_l, all restricted to the occupied inputs), and at output-group
+// point z the node contributes w(x) prod_j (st_0 + sum_l z_l st_{1+l})_j^{p_j}.
+#define GBSBIN_FOCK_MAX_IN 32
+#define GBSBIN_FOCK_MAX_L 8
+struct FockArgs {
+  int nin, L, nd;
+  int rsum;                          // sum of the group radices
+  int pw[GBSBIN_FOCK_MAX_IN];        // photons per position
+  int drad[GBSBIN_FOCK_MAX_IN];      // radix p + 1 of digit d (position d + 1)
+  int doff[GBSBIN_FOCK_MAX_IN];      // offset of digit d's roots in xtw
+  long long dstride[GBSBIN_FOCK_MAX_IN + 1];   // prod_{d' < d} drad[d']
+  int roff[GBSBIN_FOCK_MAX_L + 1];   // offset of group l's rows in the table (sum of radices)
+  long long S;                       // nodes: dstride[nd]
+  long long chunk, nchunks;          // Gray steps per restart, restarts
+  const double2* coef;               // (L + 1) x nin x nin, [m][k][j] (column k contiguous)
+  const float4* coef_df;             // the same as (hi re, hi im, lo re, lo im)
+  const double2* xtw;                // exp(2 pi i g / drad[d]), g < drad[d], digit after digit
+  const float4* xtw_df;
+  const float4* zr_df;               // exp(2 pi i c / radix[l]), c < radix[l], group after group
+  const double2* zr;
+  GridDesc grid;                     // output-group grid (half of the last axis)
+  int xr;                            // CTAs along the nodes (restarts dealt cyclically)
+  double2* parts;                    // xr x n_full partial sums
+};
+#define GBSBIN_FOCK_THREADS 128
+int fock_points_per_thread(bool df);                 // output-group points per thread
+size_t fock_smem_bytes(int nin, int L, int rsum);
+int fock_ctas_per_sm(bool df, size_t smem);          // 0: does not fit
+cudaError_t launch_fock(const FockArgs& a, bool df, cudaStream_t s);
 
 // Kernel launchers (return the launch error).
 cudaError_t launch_points(const PointArgs& a, int kernel, int num_sms, cudaStream_t s);

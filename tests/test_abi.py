@@ -113,3 +113,39 @@ def test_evaluated_digits_cover_half_grid(gb):
         for k in np.ndindex(*radix):
             neg = tuple((-np.array(k)) % np.array(radix))
             assert k in seen or neg in seen
+
+
+def _fock_status(gb, prob, **opt):
+    args = gb.FockProblemArgs(prob)
+    o = gb.make_options(**opt)
+    h = ctypes.c_void_p()
+    return gb.load().gbsbin_fock_plan_create(ctypes.byref(args.c), ctypes.byref(o), ctypes.byref(h))
+
+
+def test_fock_host_validation(gb):
+    rng = np.random.default_rng(3)
+
+    def fp(**kw):
+        p = synth.random_fock_problem(rng, 4, [1, 1, 0, 2], 2, 4)
+        for k, v in kw.items():
+            setattr(p, k, v)
+        return p
+
+    assert _fock_status(gb, fp(bin_of_mode=np.array([0, 0, 0, 0], np.int32))) == 2   # empty group
+    assert _fock_status(gb, fp(bin_of_mode=np.array([0, 1, 2, 1], np.int32))) == 2   # label out of range
+    assert _fock_status(gb, fp(cutoff=np.array([3, -1], np.int32))) == 3
+    assert _fock_status(gb, fp(cutoff=np.array([9000, 9000], np.int32))) == 3         # grid beyond the limit
+    assert _fock_status(gb, fp(photons=np.array([1, -1, 0, 0], np.int32))) == 1
+    p = fp()
+    p.T = p.T * 1.5
+    assert _fock_status(gb, p) == 4                                                   # amplifying T
+    assert _fock_status(gb, fp(), want_backward=True) == 8
+    assert _fock_status(gb, fp(), shard=(0, 3)) == 8
+    assert _fock_status(gb, fp(), tile_override=5) == 1
+    assert _fock_status(gb, fp(), oversample=0) == 1
+    big = synth.random_fock_problem(rng, 40, [1] * 33 + [0] * 7, 2, 2)
+    assert _fock_status(gb, big) == 8                                                 # 33 occupied inputs
+    many = synth.random_fock_problem(rng, 9, [1] * 9, 9, 1)
+    assert _fock_status(gb, many) == 8                                                # 9 groups > 8
+    nodes = synth.random_fock_problem(rng, 31, [3] * 31, 1, 4)
+    assert _fock_status(gb, nodes) == 8                                               # 4^30 nodes
