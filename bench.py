@@ -179,9 +179,10 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip the other workloads (n=192 grid, 256-problem batch, n=200 gradient)")
-    ap.add_argument("--extras", default="n192,batch,n200,e3",
-                    help="comma list of the other workloads to time: n192, batch, n200, e3")
+                    help="skip the other workloads (n=192 grid, 256-problem batch, n=200 gradient, "
+                         "M=256 total photon number, Fock inputs)")
+    ap.add_argument("--extras", default="n192,batch,n200,e3,fock",
+                    help="comma list of the other workloads to time: n192, batch, n200, e3, fock")
     ap.add_argument("--extra-steps", type=int, default=3)
     args = ap.parse_args()
     if args.impl == "reference":
@@ -344,7 +345,54 @@ def extra_workloads(gb, torch, stream, flush, steps, world, which=("n192", "batc
         out.update(_extra_n200(gb, torch, stream, flush, steps, world))
     if "e3" in which:
         out.update(_extra_e3(gb, torch, stream, flush, steps, world))
+    if "fock" in which:
+        out.update(_extra_fock(gb, torch, stream, flush, steps, world))
     return out
+
+
+def _extra_fock(gb, torch, stream, flush, steps, world):
+    """Fock inputs through a lossy circuit (App. C): 16 single photons in 32 ports, output
+    loss eta_i ~ U(0.4, 0.9), three detector groups, the whole table (N_l = 16): 2^15 input
+    nodes x 2601 output-group points.  FP64 kernel against FP32 pairs; the pipe operations
+    per (node, point) pair are counted from the kernels' inner loop (FP64: 2L additions and
+    4 multiply-adds per photon plus 2; FP32 pairs: 4L additions, 12 for the renormalisation
+    and 38 per product per photon, plus 16)."""
+    fp = synth.fock_config()
+    nin = int(np.count_nonzero(fp.photons))
+    L = fp.L
+    nodes = 1
+    for c in sorted(fp.photons[fp.photons > 0])[1:]:
+        nodes *= int(c) + 1
+    radix = [int(c) + 1 for c in fp.cutoff]
+    half = radix[-1] // 2 + 1
+    points = int(np.prod(radix[:-1])) * half
+    pairs = nodes * points
+    N = int(fp.photons.sum())
+    ops = {"fp64": nin * 2 * L + 4 * N + 2, "df32": nin * (4 * L + 12) + 38 * N + 16}
+    peaks = {"fp64": (0.5 * 1.05e12, "FP64 pipe: measured 1.05 TFLOP/s dependent-FMA rate / 2"),
+             "df32": (152 * 128 * 2.07e9, "FP32 pipe: 152 SMs x 128 lanes x 2070 MHz")}
+    res = {"nodes": nodes, "points": points, "occupied_inputs": nin}
+    tables = {}
+    for name, prec in (("fp64", 0), ("df32", 1)):
+        with gb.FockPlan(fp, precision=prec, want_timing=True) as p:
+            t = torch.empty(p.shape, dtype=torch.float64, device="cuda")
+            gb.gbsbin_fock_execute(p.handle, t, stream)
+            ms = _timed(torch, stream, flush, steps, lambda: gb.gbsbin_fock_execute(p.handle, t, stream))
+            d = p.diagnostics(stream)
+            tables[name] = t.cpu().numpy()
+        kms = d["point_kernel_ms"]
+        achieved = pairs * ops[name] / (kms * 1e-3)
+        res[name] = {"ms_per_table": ms / steps, "tables_per_s": 1e3 * steps / ms, "kernel_ms": kms,
+                     "pairs_per_s": pairs / (kms * 1e-3), "pipe_ops_per_pair": ops[name],
+                     "pipe_ops_per_s": achieved, "pipe_peak": peaks[name][0], "pipe_peak_source": peaks[name][1],
+                     "pipe_frac": achieved / peaks[name][0], "sum_P": d["sum_P"], "status": d["status"]}
+    res["max_abs_diff_fp64_df32"] = float(np.abs(tables["fp64"] - tables["df32"]).max())
+    P = tables["df32"]
+    means = [float(np.dot(np.arange(P.shape[l]), P.sum(axis=tuple(m for m in range(L) if m != l)))) for l in range(L)]
+    exact = (np.abs(fp.T) ** 2) @ fp.photons.astype(np.float64)
+    exact_g = [float(exact[fp.bin_of_mode == l].sum()) for l in range(L)]
+    res["group_mean_err_df32"] = float(np.max(np.abs(np.array(means) - np.array(exact_g))))
+    return {fp.name: res}
 
 
 def _extra_e3(gb, torch, stream, flush, steps, world):

@@ -20,7 +20,9 @@
 // node to the next a single coordinate moves by one root, so a and v change by one column
 // of the coefficient matrices; every `chunk` nodes the state is recomputed directly.
 //
-// CTA = (tile of output-group points, node range): 128 threads with ZT points each; node
+// CTA = (tile of output-group points, node range): 128 threads with ZT points each (1 or 2
+// for FP64, 2 or 4 for FP32 pairs, by how well the grid fills the tiles: independent
+// product chains, one shared-memory read of a_j per photon); node
 // restarts c = blockIdx.y, blockIdx.y + gridDim.y, ...; each point's sum over the CTA's
 // nodes goes to parts[blockIdx.y][point], summed in order by the inverse DFT's first stage.
 //
@@ -141,16 +143,21 @@ __global__ void __launch_bounds__(FT) k_fock(const FockArgs a) {
   E* ws = reinterpret_cast<E*>(xs + nin);        // weight w(x) of the current node
   const long long nfull = a.grid.n_full;
 
-  // this thread's output-group points: their table row per group
-  int zrow[ZT][GBSBIN_FOCK_MAX_L];
+  // this thread's output-group points: their table row per group, two 16-bit rows per word
+  // (rsum < 2^16: the table fits in shared memory)
+  unsigned zrow[ZT][GBSBIN_FOCK_MAX_L / 2];
   bool zok[ZT];
 #pragma unroll
   for (int zt = 0; zt < ZT; ++zt) {
     const long long e = ((long long)blockIdx.x * ZT + zt) * FT + tid;
     zok[zt] = e < nfull;
 #pragma unroll
-    for (int l = 0; l < GBSBIN_FOCK_MAX_L; ++l)
-      zrow[zt][l] = (zok[zt] && l < L) ? a.roff[l] + point_digit(e, a.grid, l) : 0;
+    for (int l2 = 0; l2 < GBSBIN_FOCK_MAX_L / 2; ++l2) {
+      const int l0 = 2 * l2, l1 = 2 * l2 + 1;
+      const unsigned r0 = (zok[zt] && l0 < L) ? (unsigned)(a.roff[l0] + point_digit(e, a.grid, l0)) : 0u;
+      const unsigned r1 = (zok[zt] && l1 < L) ? (unsigned)(a.roff[l1] + point_digit(e, a.grid, l1)) : 0u;
+      zrow[zt][l2] = r0 | (r1 << 16);
+    }
   }
   double2 acc[ZT];
   float4 accd[ZT];
@@ -211,40 +218,52 @@ __global__ void __launch_bounds__(FT) k_fock(const FockArgs a) {
       if (tid == 0) *ws = w;
       __syncthreads();                           // table of node i complete
 
-      const E wv = *ws;
+      // points: photon by photon, the thread's ZT products side by side (independent
+      // chains); a point off the grid computes on row 0 and is not accumulated
+      E F[ZT];
 #pragma unroll
-      for (int zt = 0; zt < ZT; ++zt) {
-        if (!zok[zt]) continue;
-        E F = wv;
-        for (int j = 0; j < nin; ++j) {
-          const E* row = tab + j * rsum;
-          E s = ta[j];
+      for (int zt = 0; zt < ZT; ++zt) F[zt] = *ws;
+      for (int j = 0; j < nin; ++j) {
+        const E* row = tab + j * rsum;
+        const E aj = ta[j];
+        E s[ZT];
+#pragma unroll
+        for (int zt = 0; zt < ZT; ++zt) {
+          s[zt] = aj;
 #pragma unroll
           for (int l = 0; l < GBSBIN_FOCK_MAX_L; ++l) {
             if (l >= L) break;
-            const E t = row[zrow[zt][l]];
+            const E t = row[(zrow[zt][l >> 1] >> ((l & 1) * 16)) & 0xffffu];
             if constexpr (DF) {                  // hi parts exact, lo parts plain
-              s.x = __fadd_rn(s.x, t.x);
-              s.y = __fadd_rn(s.y, t.y);
-              s.z = __fadd_rn(s.z, t.z);
-              s.w = __fadd_rn(s.w, t.w);
+              s[zt].x = __fadd_rn(s[zt].x, t.x);
+              s[zt].y = __fadd_rn(s[zt].y, t.y);
+              s[zt].z = __fadd_rn(s[zt].z, t.z);
+              s[zt].w = __fadd_rn(s[zt].w, t.w);
             } else {
-              s = zadd(s, t);
+              s[zt] = zadd(s[zt], t);
             }
           }
           if constexpr (DF) {                    // renormalise (TwoSum: lo may exceed hi)
             float4 u;
-            two_sum(s.x, s.z, u.x, u.z);
-            two_sum(s.y, s.w, u.y, u.w);
-            s = u;
-          }
-          for (int rep = 0; rep < a.pw[j]; ++rep) {
-            if constexpr (DF) F = df_mul(F, s);
-            else F = zmul(F, s);
+            two_sum(s[zt].x, s[zt].z, u.x, u.z);
+            two_sum(s[zt].y, s[zt].w, u.y, u.w);
+            s[zt] = u;
           }
         }
-        if constexpr (DF) df_acc(accd[zt], F);
-        else acc[zt] = zadd(acc[zt], F);
+        const int pj = a.pw[j];
+        for (int rep = 0; rep < pj; ++rep) {
+#pragma unroll
+          for (int zt = 0; zt < ZT; ++zt) {
+            if constexpr (DF) F[zt] = df_mul(F[zt], s[zt]);
+            else F[zt] = zmul(F[zt], s[zt]);
+          }
+        }
+      }
+#pragma unroll
+      for (int zt = 0; zt < ZT; ++zt) {
+        if (!zok[zt]) continue;
+        if constexpr (DF) df_acc(accd[zt], F[zt]);
+        else acc[zt] = zadd(acc[zt], F[zt]);
       }
       if constexpr (DF) {
         if (++since_flush == FLUSH) {
@@ -330,17 +349,29 @@ int ctas_one(size_t smem) {
 
 }  // namespace
 
-int fock_points_per_thread(bool df) { return df ? 2 : 1; }
+int fock_points_per_thread(bool df, long long n_full) {
+  // the larger count gives more independent chains and shares each node's table among more
+  // points; the smaller one wastes fewer slots of a CTA's last tile on small grids
+  const int small = df ? 2 : 1, big = 2 * small;
+  const double per = (double)FT;
+  const double eff_small = (double)n_full / (per * small * (double)((n_full + FT * small - 1) / (FT * small)));
+  const double eff_big = (double)n_full / (per * big * (double)((n_full + FT * big - 1) / (FT * big)));
+  return eff_big >= 0.9 * eff_small ? big : small;
+}
 
 size_t fock_smem_bytes(int nin, int L, int rsum) {
   return 16 * ((size_t)(L + 3) * nin + (size_t)nin * rsum + 1);
 }
 
-int fock_ctas_per_sm(bool df, size_t smem) { return df ? ctas_one<true, 2>(smem) : ctas_one<false, 1>(smem); }
+int fock_ctas_per_sm(bool df, int zt, size_t smem) {
+  if (df) return zt == 4 ? ctas_one<true, 4>(smem) : ctas_one<true, 2>(smem);
+  return zt == 2 ? ctas_one<false, 2>(smem) : ctas_one<false, 1>(smem);
+}
 
-cudaError_t launch_fock(const FockArgs& a, bool df, cudaStream_t s) {
+cudaError_t launch_fock(const FockArgs& a, bool df, int zt, cudaStream_t s) {
   const size_t smem = fock_smem_bytes(a.nin, a.L, a.rsum);
-  return df ? launch_one<true, 2>(a, smem, s) : launch_one<false, 1>(a, smem, s);
+  if (df) return zt == 4 ? launch_one<true, 4>(a, smem, s) : launch_one<true, 2>(a, smem, s);
+  return zt == 2 ? launch_one<false, 2>(a, smem, s) : launch_one<false, 1>(a, smem, s);
 }
 
 }  // namespace gbsbin

@@ -19,6 +19,7 @@ struct gbsbin_fock_plan {
   std::vector<int> photons, bin_of_mode, cutoff;
   std::vector<int> pos_input;            // input port of each position (position 0: held)
   bool df = false;
+  int zt = 1;                            // output-group points per thread
   int kernel = 0;
   int num_sms = 0;
   long long table_size = 0;
@@ -229,8 +230,7 @@ int gbsbin_fock_plan_create(const gbsbin_fock_problem* p, const gbsbin_options* 
                                 : (opt.precision == GBSBIN_FP32_REFINE ? GBSBIN_KERNEL_FOCK_DF32 : GBSBIN_KERNEL_FOCK_FP64);
   P->df = P->kernel == GBSBIN_KERNEL_FOCK_DF32;
   // restarts bound the drift of the incrementally updated state (FP32 pairs drift faster)
-  a.chunk = P->df ? 256 : 1024;
-  a.nchunks = (a.S + a.chunk - 1) / a.chunk;
+  const long long chunk_max = P->df ? 256 : 1024;
   int device = 0;
   if (cudaGetDevice(&device) != cudaSuccess ||
       cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
@@ -239,19 +239,28 @@ int gbsbin_fock_plan_create(const gbsbin_fock_problem* p, const gbsbin_options* 
     return GBSBIN_ERR_CUDA;
   }
   const size_t smem = fock_smem_bytes(a.nin, L, a.rsum);
-  const int per_sm = smem <= 200 * 1024 ? fock_ctas_per_sm(P->df, smem) : 0;
+  P->zt = fock_points_per_thread(P->df, g.n_full);
+  const int per_sm = smem <= 200 * 1024 ? fock_ctas_per_sm(P->df, P->zt, smem) : 0;
   if (per_sm < 1) {
     delete P;
     return GBSBIN_ERR_UNSUPPORTED;
   }
-  const long long per_cta = (long long)GBSBIN_FOCK_THREADS * fock_points_per_thread(P->df);
+  const long long per_cta = (long long)GBSBIN_FOCK_THREADS * P->zt;
   const long long tiles = (g.n_full + per_cta - 1) / per_cta;
-  long long xr = (2LL * per_sm * P->num_sms + tiles - 1) / tiles;   // about two waves of CTAs
-  if (xr > a.nchunks) xr = a.nchunks;
-  if (xr > 65535) xr = 65535;
+  // node ranges: two whole waves of resident CTAs where the nodes allow (a partial last wave
+  // idles SMs), each range at least 32 nodes; ranges longer than chunk_max are walked as
+  // several restarts dealt cyclically
+  const long long slots = (long long)per_sm * P->num_sms;
+  long long xr = 2 * slots / tiles;
   const long long cap = (512LL << 20) / (16 * g.n_full);            // parts <= 512 MB
   if (xr > cap) xr = cap;
+  if (xr > 65535) xr = 65535;
+  if (xr > (a.S + 31) / 32) xr = (a.S + 31) / 32;
   if (xr < 1) xr = 1;
+  a.chunk = (a.S + xr - 1) / xr;
+  if (a.chunk > chunk_max) a.chunk = chunk_max;
+  a.nchunks = (a.S + a.chunk - 1) / a.chunk;
+  if (xr > a.nchunks) xr = a.nchunks;
   a.xr = (int)xr;
   P->coef_count = (size_t)(L + 1) * a.nin * a.nin;
   P->state_bytes = P->coef_count * (sizeof(double2) + sizeof(float4));
@@ -346,7 +355,7 @@ int gbsbin_fock_execute(gbsbin_fock_plan* P, double* P_out, void* stream) {
   if (!P || !P_out) return GBSBIN_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   if (P->ev0 && cudaEventRecord(P->ev0, s) != cudaSuccess) return GBSBIN_ERR_CUDA;
-  if (launch_fock(P->args, P->df, s) != cudaSuccess) return GBSBIN_ERR_CUDA;
+  if (launch_fock(P->args, P->df, P->zt, s) != cudaSuccess) return GBSBIN_ERR_CUDA;
   if (P->ev1 && cudaEventRecord(P->ev1, s) != cudaSuccess) return GBSBIN_ERR_CUDA;
   DftArgs d{};
   d.grid = P->args.grid;

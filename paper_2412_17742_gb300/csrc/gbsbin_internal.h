@@ -144,10 +144,10 @@ struct FockArgs {
   double2* parts;                    // xr x n_full partial sums
 };
 #define GBSBIN_FOCK_THREADS 128
-int fock_points_per_thread(bool df);                 // output-group points per thread
+int fock_points_per_thread(bool df, long long n_full);   // output-group points per thread
 size_t fock_smem_bytes(int nin, int L, int rsum);
-int fock_ctas_per_sm(bool df, size_t smem);          // 0: does not fit
-cudaError_t launch_fock(const FockArgs& a, bool df, cudaStream_t s);
+int fock_ctas_per_sm(bool df, int zt, size_t smem);      // 0: does not fit
+cudaError_t launch_fock(const FockArgs& a, bool df, int zt, cudaStream_t s);
 
 // Kernel launchers (return the launch error).
 cudaError_t launch_points(const PointArgs& a, int kernel, int num_sms, cudaStream_t s);
