@@ -61,7 +61,9 @@ typedef enum {
   GBSBIN_FP64 = 0,          /* every step in FP64 (DFMA pipe)                               */
   GBSBIN_FP32_REFINE = 1    /* FP32 LU, one refinement step of log det and of the exponent
                                solve whose residual is formed with error-free FP32
-                               transformations; FP64 epilogue and DFT                        */
+                               transformations; FP64 epilogue and DFT.  Where the tree of
+                               block eliminations applies (GBSBIN_KERNEL_TREE_DF32), pairs
+                               of FP32 instead of the refinement                            */
 } gbsbin_precision;
 
 typedef struct {
@@ -151,8 +153,18 @@ typedef enum {
                                       through Q^T gamma and Q^H X gamma; chosen
                                       automatically for L = 1                              */
   GBSBIN_KERNEL_FOCK_FP64 = 9,     /* Fock inputs (gbsbin_fock_*): FP64 throughout           */
-  GBSBIN_KERNEL_FOCK_DF32 = 10     /* Fock inputs: pairs of FP32 (hi + lo, ~46 bits) on the
+  GBSBIN_KERNEL_FOCK_DF32 = 10,    /* Fock inputs: pairs of FP32 (hi + lo, ~46 bits) on the
                                       FMA pipe, running sums flushed to FP64               */
+  GBSBIN_KERNEL_TREE_DF32 = 11     /* L >= 2: rows ordered by group, the grid evaluated as a
+                                      tree of block eliminations - depth l holds one reduced
+                                      matrix I - D'A' per combination of the first l axes'
+                                      roots (the Schur complement after eliminating groups
+                                      0..l-1 depends on their phases only), every grid point
+                                      a leaf; the same pivots as the per-point unpivoted LU
+                                      of the permuted matrix; pairs of FP32 (~46 bits) on
+                                      the FMA pipe, FP64 results; chosen automatically for
+                                      GBSBIN_FP32_REFINE plans with n <= 64, last group <= 16
+                                      rows, no shard and no want_backward                */
 } gbsbin_kernel;
 
 /* Fill *o with defaults: FP64, oversample 1, diagnostics on, automatic kernel. */

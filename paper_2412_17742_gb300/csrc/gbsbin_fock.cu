@@ -37,6 +37,7 @@
 #include <type_traits>
 
 #include "gbsbin_device.cuh"
+#include "gbsbin_df.cuh"
 #include "gbsbin_internal.h"
 
 namespace gbsbin {
@@ -54,62 +55,6 @@ __device__ __forceinline__ double2 zfma(double2 a, double2 b, double2 c) {   // 
   return make_double2(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));
 }
 
-// ------------------------------------------- pairs of FP32: (hi re, hi im, lo re, lo im)
-// The intrinsics keep the compiler from contracting or reassociating these sequences.
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {   // Knuth: a + b = s + e
-  s = __fadd_rn(a, b);
-  const float bb = __fsub_rn(s, a);
-  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-}
-__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {  // Dekker, |a| >= |b|
-  s = __fadd_rn(a, b);
-  e = __fsub_rn(b, __fsub_rn(s, a));
-}
-__device__ __forceinline__ float4 df_from(double2 v) {
-  const float hr = __double2float_rn(v.x), hi = __double2float_rn(v.y);
-  return make_float4(hr, hi, __double2float_rn(v.x - (double)hr), __double2float_rn(v.y - (double)hi));
-}
-__device__ __forceinline__ double2 df_to(float4 v) {
-  return make_double2((double)v.x + (double)v.z, (double)v.y + (double)v.w);
-}
-// a b of normalised pairs: the hi x hi products exactly (TwoProduct by FMA), the cross
-// terms in FP32, one renormalisation per component
-__device__ __forceinline__ float4 df_mul(float4 a, float4 b) {
-  const float p1 = __fmul_rn(a.x, b.x), e1 = fmaf(a.x, b.x, -p1);
-  const float p2 = __fmul_rn(a.y, b.y), e2 = fmaf(a.y, b.y, -p2);
-  float sr, er;
-  two_sum(p1, -p2, sr, er);
-  er = __fadd_rn(er, __fsub_rn(e1, e2));
-  er = fmaf(a.x, b.z, er);
-  er = fmaf(a.z, b.x, er);
-  er = fmaf(-a.y, b.w, er);
-  er = fmaf(-a.w, b.y, er);
-  const float p3 = __fmul_rn(a.x, b.y), e3 = fmaf(a.x, b.y, -p3);
-  const float p4 = __fmul_rn(a.y, b.x), e4 = fmaf(a.y, b.x, -p4);
-  float si, ei;
-  two_sum(p3, p4, si, ei);
-  ei = __fadd_rn(ei, __fadd_rn(e3, e4));
-  ei = fmaf(a.x, b.w, ei);
-  ei = fmaf(a.z, b.y, ei);
-  ei = fmaf(a.y, b.z, ei);
-  ei = fmaf(a.w, b.x, ei);
-  float4 r;
-  fast_two_sum(sr, er, r.x, r.z);
-  fast_two_sum(si, ei, r.y, r.w);
-  return r;
-}
-__device__ __forceinline__ float4 df_add(float4 a, float4 b) {
-  float sr, er, si, ei;
-  two_sum(a.x, b.x, sr, er);
-  two_sum(a.y, b.y, si, ei);
-  er = __fadd_rn(er, __fadd_rn(a.z, b.z));
-  ei = __fadd_rn(ei, __fadd_rn(a.w, b.w));
-  float4 r;
-  fast_two_sum(sr, er, r.x, r.z);
-  fast_two_sum(si, ei, r.y, r.w);
-  return r;
-}
-__device__ __forceinline__ float4 df_conj(float4 a) { return make_float4(a.x, -a.y, a.z, -a.w); }
 // (hi, lo) with hi = a rounded to a multiple of 2^-18 (|a| < 16: x + 48 lies in [32, 64),
 // whose FP32 spacing is 2^-18) and lo = a - hi
 __device__ __forceinline__ float4 df_split(float4 a) {

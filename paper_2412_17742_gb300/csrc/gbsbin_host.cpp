@@ -39,6 +39,11 @@ struct gbsbin_plan {
   double* d_ldfin = nullptr;          // warp kernel: unfinished log det per evaluated point
   unsigned* d_bar = nullptr;          // grid-barrier state of the fused DFT launch
   double2* d_H = nullptr;             // Hessenberg form of XA (one-group, undisplaced plans)
+  // tree plans: rows ordered by group (tree_perm[new] = old), depth-0 arrays in d_state,
+  // depths 1 .. L-1 in d_tree
+  std::vector<int> tree_perm;
+  TreeArgs tree{};
+  unsigned char* d_tree = nullptr;
   int* d_label = nullptr;
   double2* d_logq = nullptr;
   double* d_minpiv = nullptr;
@@ -78,7 +83,8 @@ int validate_shape(const gbsbin_problem* p, const gbsbin_options* o) {
   if (!p->sigma1 && (!p->r || !p->T)) return GBSBIN_ERR_ARG;
   if (o->precision != GBSBIN_FP64 && o->precision != GBSBIN_FP32_REFINE) return GBSBIN_ERR_ARG;
   if (o->oversample < 1) return GBSBIN_ERR_ARG;
-  if (o->tile_override < 0 || o->tile_override > GBSBIN_KERNEL_HESS_FP64) return GBSBIN_ERR_ARG;
+  if (o->tile_override < 0 || (o->tile_override > GBSBIN_KERNEL_HESS_FP64 && o->tile_override != GBSBIN_KERNEL_TREE_DF32))
+    return GBSBIN_ERR_ARG;
   long long n = 2LL * p->M * p->K;
   if (n > GBSBIN_MAX_N) return GBSBIN_ERR_UNSUPPORTED;
   std::vector<int> count(p->L, 0);
@@ -244,8 +250,8 @@ int build_state(const gbsbin_problem* p, int n, std::vector<cd>& XA, std::vector
 }
 
 void free_device(gbsbin_plan* P) {
-  void* ptrs[] = {P->d_state, P->d_label, P->d_logq,  P->d_minpiv, P->d_bufA, P->d_bufB,
-                  P->d_tw,    P->d_diag,  P->d_gws,   P->d_table,  P->d_ldfin, P->d_bar,  P->d_H};
+  void* ptrs[] = {P->d_state, P->d_label, P->d_logq,  P->d_minpiv, P->d_bufA, P->d_bufB, P->d_tw,
+                  P->d_diag,  P->d_gws,   P->d_table, P->d_ldfin,  P->d_bar,  P->d_H,    P->d_tree};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (P->h_stage) cudaFreeHost(P->h_stage);
@@ -269,9 +275,11 @@ int dalloc(T** p, size_t count) {
 
 // Layout of the pinned staging buffer for one state upload.
 struct Stage {
-  size_t off_XA, off_g, off_Xg, off_XAhi, off_XAlo, off_Xghi, off_Xglo, off_ghi, off_glo, off_XAfix, total;
+  size_t off_XA, off_g, off_Xg, off_XAhi, off_XAlo, off_Xghi, off_Xglo, off_ghi, off_glo, off_XAfix;
+  size_t off_tree;   // tree plans: permuted XA (n x n), X gamma, gamma as FP32 pairs, root path record
+  size_t total;
 };
-Stage stage_layout(int n) {
+Stage stage_layout(int n, bool tree) {
   Stage s{};
   size_t nn = (size_t)n * n, o = 0;
   s.off_XA = o;   o += nn * sizeof(double2);
@@ -284,8 +292,16 @@ Stage stage_layout(int n) {
   s.off_ghi = o;  o += n * sizeof(float2);
   s.off_glo = o;  o += n * sizeof(float2);
   s.off_XAfix = o; o += nn * sizeof(longlong2);
+  s.off_tree = o;
+  if (tree) o += (nn + 2 * (size_t)n + 3) * sizeof(float4);
   s.total = o;
   return s;
+}
+
+// v as a pair of FP32 per component: (hi re, hi im, lo re, lo im)
+float4 split4(cd v) {
+  const float hr = (float)v.real(), hi = (float)v.imag();
+  return make_float4(hr, hi, (float)(v.real() - (double)hr), (float)(v.imag() - (double)hi));
 }
 
 void split(cd v, float2* hi, float2* lo) {
@@ -299,7 +315,8 @@ int upload_hessenberg(gbsbin_plan* P, cudaStream_t stream);
 // Stage the state and enqueue its upload on `stream`.
 int upload_state(gbsbin_plan* P, cudaStream_t stream) {
   const int n = P->n;
-  Stage s = stage_layout(n);
+  const bool tree = P->kernel == GBSBIN_KERNEL_TREE_DF32;
+  Stage s = stage_layout(n, tree);
   // a previous upload may still be reading the staging buffer
   cudaError_t e = cudaStreamSynchronize(stream);
   if (e != cudaSuccess) return GBSBIN_ERR_CUDA;
@@ -326,6 +343,21 @@ int upload_state(gbsbin_plan* P, cudaStream_t stream) {
     Xg[i] = make_double2(P->Xgamma[i].real(), P->Xgamma[i].imag());
     split(P->Xgamma[i], &Xghi[i], &Xglo[i]);
     split(P->gamma[i], &ghi[i], &glo[i]);
+  }
+  if (tree) {                                     // depth 0 of the tree: the permuted state
+    float4* A0 = (float4*)(h + s.off_tree);
+    float4* c0 = A0 + (size_t)n * n;
+    float4* u0 = c0 + n;
+    float4* path = u0 + n;
+    const std::vector<int>& pm = P->tree_perm;
+    for (int i = 0; i < n; ++i) {
+      for (int j = 0; j < n; ++j) A0[(size_t)i * n + j] = split4(P->XA[(size_t)pm[i] * n + pm[j]]);
+      c0[i] = split4(P->Xgamma[pm[i]]);
+      u0[i] = split4(P->gamma[pm[i]]);
+    }
+    path[0] = make_float4(1.f, 0.f, 0.f, 0.f);        // pivot product
+    path[1] = make_float4(0.f, 0.f, 3.0e38f, 0.f);    // argument sum, power of two, min Re pivot
+    path[2] = make_float4(0.f, 0.f, 0.f, 0.f);        // exponent sum
   }
   // the device block has the staging layout: one copy
   e = cudaMemcpyAsync(P->d_state, h, s.total, cudaMemcpyHostToDevice, stream);
@@ -487,6 +519,64 @@ int evaluate_fp64_with_factors(gbsbin_plan* P, cudaStream_t s) {
 // tensor cores.
 inline bool is_blk(int kernel) { return kernel == GBSBIN_KERNEL_BLK_FP32R || kernel == GBSBIN_KERNEL_BLK_TC_FP32R; }
 
+// Tree plans: rows ordered by group (stable within a group), the block sizes, and the
+// reduced-matrix sizes and node counts per depth.  Returns the scratch bytes of depths
+// 1 .. L-1, or 0 when the problem does not suit the tree (one group, a level block or the
+// last group too large for the kernels' shared memory, scratch beyond 2 GB).
+size_t tree_layout(gbsbin_plan* P) {
+  const int L = P->L, n = P->n;
+  if (L < 2 || n > 64) return 0;
+  TreeArgs& t = P->tree;
+  P->tree_perm.clear();
+  for (int l = 0; l < L; ++l) {
+    t.nb[l] = 0;
+    for (int q = 0; q < n; ++q)
+      if (P->label[q] == l) {
+        P->tree_perm.push_back(q);
+        ++t.nb[l];
+      }
+  }
+  int rem = n;
+  for (int l = 0; l < L; ++l) {
+    t.m[l] = rem;
+    rem -= t.nb[l];
+  }
+  if (tree_leaf_threads(t.m[L - 1]) == 0) return 0;
+  size_t bytes = 0;
+  long long nodes = 1;
+  for (int l = 0; l + 1 < L; ++l) {
+    if (tree_level_smem_bytes(t.nb[l], t.m[l]) > 200 * 1024) return 0;
+    nodes *= P->grid.radix[l];
+    const size_t mc = (size_t)t.m[l + 1];
+    bytes += (size_t)nodes * (mc * mc + 2 * mc + 3) * sizeof(float4);
+  }
+  return bytes <= (2ull << 30) ? bytes : 0;
+}
+
+void tree_pointers(gbsbin_plan* P, const Stage& sl) {
+  TreeArgs& t = P->tree;
+  const int n = P->n;
+  float4* A0 = (float4*)(P->d_state + sl.off_tree);
+  t.A[0] = A0;
+  t.c[0] = A0 + (size_t)n * n;
+  t.u[0] = t.c[0] + n;
+  t.path[0] = t.u[0] + n;
+  float4* q = (float4*)P->d_tree;
+  long long nodes = 1;
+  for (int l = 0; l + 1 < P->L; ++l) {
+    nodes *= P->grid.radix[l];
+    const size_t mc = (size_t)t.m[l + 1];
+    t.A[l + 1] = q;
+    q += (size_t)nodes * mc * mc;
+    t.c[l + 1] = q;
+    q += (size_t)nodes * mc;
+    t.u[l + 1] = q;
+    q += (size_t)nodes * mc;
+    t.path[l + 1] = q;
+    q += (size_t)nodes * 3;
+  }
+}
+
 int choose_kernel(int n, int L, int precision, int override_id, int has_gamma) {
   if (override_id) return override_id;
   if (L == 1) return GBSBIN_KERNEL_HESS_FP64;   // one group
@@ -599,7 +689,21 @@ static int plan_create_impl(const gbsbin_problem* p, const gbsbin_options* o, gb
     delete P;
     return GBSBIN_ERR_UNSUPPORTED;
   }
-  P->P = P->kernel == GBSBIN_KERNEL_HESS_FP64 ? 1
+  // the tree: asked for, or by default for standalone FP32 + refinement plans it suits
+  // (batches run their own per-point launches)
+  const bool sharded = opt.shard_end != 0 || opt.shard_begin != 0;
+  size_t tree_bytes = 0;
+  if (P->kernel == GBSBIN_KERNEL_TREE_DF32 ||
+      (alloc_gws && !opt.tile_override && opt.precision == GBSBIN_FP32_REFINE && p->L >= 2)) {
+    tree_bytes = (!sharded && !opt.want_backward) ? tree_layout(P) : 0;
+    if (tree_bytes) {
+      P->kernel = GBSBIN_KERNEL_TREE_DF32;
+    } else if (P->kernel == GBSBIN_KERNEL_TREE_DF32) {
+      delete P;
+      return GBSBIN_ERR_UNSUPPORTED;
+    }
+  }
+  P->P = P->kernel == GBSBIN_KERNEL_HESS_FP64 || P->kernel == GBSBIN_KERNEL_TREE_DF32 ? 1
          : P->kernel == GBSBIN_KERNEL_WARP_FP32R ? (n <= 32 ? 1 : 0)
          : is_blk(P->kernel) ? (n <= GBSBIN_BLK_MAX_N ? 1 : 0)
                                                  : points_per_cta(P->kernel, n, p->L);
@@ -621,7 +725,7 @@ static int plan_create_impl(const gbsbin_problem* p, const gbsbin_options* o, gb
     return GBSBIN_ERR_CUDA;
   }
   const size_t nn = (size_t)n * n;
-  Stage sl = stage_layout(n);
+  Stage sl = stage_layout(n, P->kernel == GBSBIN_KERNEL_TREE_DF32);
   (void)nn;
   if ((st = dalloc(&P->d_state, sl.total)) || (st = dalloc(&P->d_label, n)) || (st = dalloc(&P->d_logq, g.n_eval)) ||
       (st = dalloc(&P->d_minpiv, g.n_eval)) || (st = dalloc(&P->d_bufA, g.n_full)) ||
@@ -655,11 +759,20 @@ static int plan_create_impl(const gbsbin_problem* p, const gbsbin_options* o, gb
     delete P;
     return st;
   }
-  if ((P->kernel == GBSBIN_KERNEL_WARP_FP32R || P->kernel == GBSBIN_KERNEL_HESS_FP64) &&
+  if ((P->kernel == GBSBIN_KERNEL_WARP_FP32R || P->kernel == GBSBIN_KERNEL_HESS_FP64 ||
+       P->kernel == GBSBIN_KERNEL_TREE_DF32) &&
       (st = dalloc(&P->d_ldfin, (size_t)6 * g.n_eval))) {
     free_device(P);
     delete P;
     return st;
+  }
+  if (P->kernel == GBSBIN_KERNEL_TREE_DF32) {
+    if ((st = dalloc(&P->d_tree, tree_bytes))) {
+      free_device(P);
+      delete P;
+      return st;
+    }
+    tree_pointers(P, sl);
   }
   if (P->kernel == GBSBIN_KERNEL_HESS_FP64 && (st = dalloc(&P->d_H, nn + 2 * (size_t)n))) {
     free_device(P);
@@ -827,6 +940,18 @@ int gbsbin_execute(gbsbin_plan* P, double* P_out, void* stream) {
   PointArgs a = make_point_args(P);
   P->saved_valid = a.lu_store != nullptr;
   if (P->ev0 && cudaEventRecord(P->ev0, s) != cudaSuccess) return GBSBIN_ERR_CUDA;
+  if (P->kernel == GBSBIN_KERNEL_TREE_DF32) {
+    TreeArgs t = P->tree;
+    t.has_gamma = P->has_gamma;
+    t.tw = P->d_tw;
+    t.grid = P->grid;
+    t.ldfin = P->d_ldfin;
+    t.minpiv = P->d_minpiv;
+    if (launch_points_tree(t, s) != cudaSuccess) return GBSBIN_ERR_CUDA;
+    if (P->ev1 && cudaEventRecord(P->ev1, s) != cudaSuccess) return GBSBIN_ERR_CUDA;
+    return launch_dft_fused(make_dft_args(P, P_out), P->d_bar, P->num_sms, s) == cudaSuccess ? GBSBIN_OK
+                                                                                          : GBSBIN_ERR_CUDA;
+  }
   cudaError_t e = P->kernel == GBSBIN_KERNEL_WARP_FP32R  ? launch_points_warp(a, P->num_sms, s)
                   : P->kernel == GBSBIN_KERNEL_HESS_FP64 ? launch_points_hess(a, PointBatch{}, P->num_sms, s)
                   : is_blk(P->kernel) ? launch_points_blk(a, PointBatch{}, 0, P->num_sms, s, P->kernel == GBSBIN_KERNEL_BLK_TC_FP32R)

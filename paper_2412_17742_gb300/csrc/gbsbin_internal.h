@@ -116,6 +116,29 @@ struct DftArgs {
   long long table_size;
 };
 
+// Tree of block eliminations over the grid (gbsbin_points_tree.cu), in pairs of FP32
+// (float4 = hi re, hi im, lo re, lo im): rows ordered by group; depth l holds one reduced
+// matrix A' per combination of the first l axes' roots (A[l]: nodes x m[l] x m[l],
+// row-major; c, u: the displacement vectors; path: 3 float4 per node).  Depth 0 is the
+// permuted state.  Leaves (depth L - 1, last axis halved) write the unfinished log q of
+// every evaluated point to ldfin (FP64).
+struct TreeArgs {
+  int has_gamma;
+  int nb[GBSBIN_MAX_L];     // rows of group l
+  int m[GBSBIN_MAX_L];      // size of the reduced matrices at depth l (m[0] = n)
+  float4* A[GBSBIN_MAX_L];
+  float4* c[GBSBIN_MAX_L];
+  float4* u[GBSBIN_MAX_L];
+  float4* path[GBSBIN_MAX_L];
+  const double2* tw;
+  GridDesc grid;
+  double* ldfin;
+  double* minpiv;
+};
+size_t tree_level_smem_bytes(int nb, int m);
+int tree_leaf_threads(int n);   // lanes per leaf (0: no kernel for a last group of n rows)
+cudaError_t launch_points_tree(const TreeArgs& a, cudaStream_t s);
+
 // Fock inputs through a lossy circuit (gbsbin_fock.cu).  nin occupied inputs in position
 // order (position 0 is the held input, x = 1; positions 1..nd are the Gray digits); per
 // node x of the roots-of-unity grid the state is st_m = coef_m x (m = 0: I - T^dag T,

@@ -1,0 +1,282 @@
+// Grid points by a tree of block eliminations (arXiv:2412.17742, Sec. III Eq. q_d on the
+// roots-of-unity grid of Sec. VI), in pairs of FP32.
+//
+// Order the rows and columns of K(w) = I - D(w) A (A = XA) by detector group, group 0
+// first (a symmetric permutation: det and the bilinear form below are unchanged, and
+// every unpivoted pivot keeps Re > 0, so the branch of log det is the one of the
+// per-point LU).  The leading block of group 0 is B = I - w_0 A_00, and eliminating it
+// leaves the Schur complement
+//
+//   K_rr - K_r0 B^-1 K_0r = I - D_r (A_rr + A_r0 W),   W = w_0 B^-1 A_0r,
+//
+// again of the form I - D' A' with A' depending on w_0 only.  So every point with the same
+// phases w_0..w_l shares the first l + 1 eliminations: depth l of the tree holds one
+// reduced matrix per combination of the first l axes' roots, and a grid point is a leaf
+// (the last group's block, last axis halved by conjugate symmetry).  The displacement term
+// u^T K^-1 v, u = gamma, v = D X gamma, splits the same way: each elimination adds
+// u_0^T y with y = w_0 B^-1 c_0 (v = D c), and leaves c' = c_r + A_r0 y, u' = u_r + W^T u_0.
+//
+// A level CTA runs one Gauss-Jordan sweep over the first nb columns of
+//
+//   [ B      | w A_0r | w c_0 ]        ->   [ I | W  | y  ]
+//   [ -A_r0  | A_rr   | c_r   ]             [ . | A' | c' ],
+//
+// whose pivots are those of B's unpivoted LU.  log q = 1/2 sum(u_0^T y) - 1/2 sum Log(pivots).
+// Each node carries a path record - the pivot product (scaled by a power of two), the FP32
+// sum of the pivots' arguments, the exponent sum and the smallest pivot real part - and
+// leaves write the unfinished form that the inverse DFT's first stage finishes in FP64.
+//
+// Arithmetic: pairs of FP32 (about 46 bits, gbsbin_df.cuh) on the FMA pipe.  The chains
+// here are short and dependent; the FP64 pipe of this GPU issues one 32-lane instruction
+// per ~64 cycles per scheduler, the FMA pipe one per cycle.
+#include <cuda_runtime.h>
+
+#include "gbsbin_device.cuh"
+#include "gbsbin_df.cuh"
+#include "gbsbin_internal.h"
+
+namespace gbsbin {
+namespace {
+
+constexpr int LT_MAX = 512;      // threads of a level CTA (at most)
+
+// path record (3 float4): [0] pivot product; [1] = (argument sum, power of two, smallest
+// pivot real part, -); [2] exponent sum
+__device__ __forceinline__ void path_pivot(float4* pr, float4 p) {
+  float4 r = df_mul(pr[0], p);
+  const float mx = fmaxf(fabsf(r.x), fabsf(r.y));
+  float e2 = pr[1].y;
+  if (mx > 0.f && mx < 1.0e30f) {
+    int ex;
+    frexpf(mx, &ex);
+    r = make_float4(ldexpf(r.x, -ex), ldexpf(r.y, -ex), ldexpf(r.z, -ex), ldexpf(r.w, -ex));
+    e2 += (float)ex;
+  }
+  pr[0] = r;
+  float mn = fminf(pr[1].z, p.x);
+  if (!(p.x == p.x) || !(p.y == p.y)) mn = -3.0e38f;
+  pr[1] = make_float4(__fadd_rn(pr[1].x, atan2f(p.y, p.x)), e2, mn, 0.f);
+}
+
+// Level l: one CTA per child (parent, k) of depth l.
+__global__ void __launch_bounds__(LT_MAX) k_tree_level(TreeArgs a, int l) {
+  extern __shared__ __align__(16) float4 gsm[];
+  const int nb = a.nb[l], m = a.m[l], mc = m - nb, cols = m + 1;
+  float4* G = gsm;                                   // m x cols, the augmented matrix
+  float4* pv = G + (size_t)m * cols;                 // nb pivots
+  __shared__ float4 s_inv;
+  const long long child = blockIdx.x;
+  const int R = a.grid.radix[l];
+  const long long parent = child / R;
+  const int k = (int)(child - parent * R);
+  const float4 w = df_from(grid_root(a.tw, a.grid, l, k));
+  const float4* Ap = a.A[l] + parent * (long long)m * m;
+  const float4* cp = a.c[l] + parent * (long long)m;
+  const float4* up = a.u[l] + parent * (long long)m;
+  const int tid = threadIdx.x, LT = blockDim.x;
+  const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int idx = tid; idx < m * cols; idx += LT) {
+    const int i = idx / cols, s = idx - (idx / cols) * cols;
+    const float4 v = s < m ? Ap[(long long)i * m + s] : (a.has_gamma ? cp[i] : zero);
+    float4 g;
+    if (i < nb) {
+      g = df_mul(w, v);
+      if (s < nb) {
+        g = df_neg(g);
+        if (s == i) g = df_add(g, make_float4(1.f, 0.f, 0.f, 0.f));
+      }
+    } else {
+      g = s < nb ? df_neg(v) : v;
+    }
+    G[idx] = g;
+  }
+  for (int kk = 0; kk < nb; ++kk) {
+    __syncthreads();
+    if (tid == 0) {
+      const float4 piv = G[kk * cols + kk];
+      pv[kk] = piv;
+      s_inv = df_recip(piv);
+    }
+    __syncthreads();
+    const float4 r = s_inv;
+    for (int s = kk + 1 + tid; s < cols; s += LT) G[kk * cols + s] = df_mul(G[kk * cols + s], r);
+    __syncthreads();
+    // columns right of kk, rows other than kk; two independent entries per pass.  The row
+    // of entry idx is floor(idx / w_) from a float reciprocal: idx < 2^14 and w_ <= 65, so
+    // (idx + 1/2) / w_ stays more than 1/(2 w_) from an integer, far above its rounding
+    const int w_ = cols - kk - 1, total = (m - 1) * w_;
+    const float rw = 1.0f / (float)w_;
+    for (int idx = tid; idx < total; idx += 2 * LT) {
+      const int idx2 = idx + LT;
+      int i = (int)(((float)idx + 0.5f) * rw);
+      const int s = kk + 1 + (idx - i * w_);
+      if (i >= kk) ++i;
+      const float4 g1 = df_fms(G[i * cols + s], G[i * cols + kk], G[kk * cols + s]);
+      if (idx2 < total) {
+        int i2 = (int)(((float)idx2 + 0.5f) * rw);
+        const int s2 = kk + 1 + (idx2 - i2 * w_);
+        if (i2 >= kk) ++i2;
+        G[i2 * cols + s2] = df_fms(G[i2 * cols + s2], G[i2 * cols + kk], G[kk * cols + s2]);
+      }
+      G[i * cols + s] = g1;
+    }
+  }
+  __syncthreads();
+  float4* Ac = a.A[l + 1] + child * (long long)mc * mc;
+  for (int idx = tid; idx < mc * mc; idx += LT) {
+    const int i = idx / mc, j = idx - (idx / mc) * mc;
+    Ac[idx] = G[(nb + i) * cols + nb + j];
+  }
+  if (a.has_gamma) {
+    float4* cc = a.c[l + 1] + child * (long long)mc;
+    float4* uc = a.u[l + 1] + child * (long long)mc;
+    for (int j = tid; j < mc; j += LT) {
+      cc[j] = G[(nb + j) * cols + m];
+      float4 uv = up[nb + j];
+      for (int t = 0; t < nb; ++t) uv = df_fma(G[t * cols + nb + j], up[t], uv);
+      uc[j] = uv;
+    }
+  }
+  if (tid == 0) {
+    const float4* pp = a.path[l] + parent * 3;
+    float4 pr[3] = {pp[0], pp[1], pp[2]};
+    for (int t = 0; t < nb; ++t) path_pivot(pr, pv[t]);
+    if (a.has_gamma)
+      for (int t = 0; t < nb; ++t) pr[2] = df_fma(up[t], G[t * cols + m], pr[2]);
+    float4* pc = a.path[l + 1] + child * 3;
+    pc[0] = pr[0];
+    pc[1] = pr[1];
+    pc[2] = pr[2];
+  }
+}
+
+__device__ __forceinline__ float4 shfl4(float4 v, int src) {
+  return make_float4(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src),
+                     __shfl_sync(0xffffffffu, v.z, src), __shfl_sync(0xffffffffu, v.w, src));
+}
+
+// Leaves: a team of NL lanes per evaluated point (32 / NL teams per warp), lane r holding
+// row r of B = I - w A_leaf and of the right-hand side w c in registers.  Step kk
+// broadcasts row kk from its lane; the rows below subtract their multiple of it (the
+// right-hand side with them), so U and L^-1 (w c) come out together; the back substitution
+// then broadcasts one solution entry per step.  Every lane sees every pivot and keeps the
+// path record; the team's first lane writes the point.
+template <int NL>
+__global__ void __launch_bounds__(128) k_tree_leaf(TreeArgs a) {
+  constexpr int TEAMS = 32 / NL;
+  const int lane = threadIdx.x & 31;
+  const int team = lane / NL, r = lane - team * NL;
+  const int base = team * NL;
+  const long long leaf = ((long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * TEAMS + team;
+  const bool live = team < TEAMS && leaf < a.grid.n_eval;
+  const int l = a.grid.L - 1;
+  const int H = a.grid.half;
+  const long long parent = live ? leaf / H : 0;
+  const int k = live ? (int)(leaf - parent * H) : 0;
+  const float4 w = df_from(grid_root(a.tw, a.grid, l, k));
+  const float4* Ap = a.A[l] + parent * (long long)NL * NL + (long long)(live ? r : 0) * NL;
+  const float4 one = make_float4(1.f, 0.f, 0.f, 0.f), zero = make_float4(0.f, 0.f, 0.f, 0.f);
+  float4 b[NL];
+#pragma unroll
+  for (int j = 0; j < NL; ++j) {
+    b[j] = df_neg(df_mul(w, Ap[j]));
+    if (j == r) b[j] = df_add(b[j], one);
+  }
+  float4 y = zero, u = zero;
+  if (a.has_gamma) {
+    y = df_mul(w, a.c[l][parent * NL + (live ? r : 0)]);
+    u = a.u[l][parent * NL + (live ? r : 0)];
+  }
+  const float4* pp = a.path[l] + parent * 3;
+  float4 pr[3] = {pp[0], pp[1], pp[2]};
+  float4 myinv = one;
+#pragma unroll
+  for (int kk = 0; kk < NL; ++kk) {
+    const int src = base + kk;
+    const float4 piv = shfl4(b[kk], src);
+    const float4 ykk = shfl4(y, src);
+    path_pivot(pr, piv);
+    const float4 inv = df_recip(piv);
+    if (r == kk) myinv = inv;
+    const bool below = r > kk;
+    const float4 li = df_mul(b[kk], inv);            // used by the rows below only
+#pragma unroll
+    for (int j = kk + 1; j < NL; ++j) {
+      const float4 rj = shfl4(b[j], src);
+      if (below) b[j] = df_fms(b[j], li, rj);
+    }
+    if (below) y = df_fms(y, li, ykk);
+  }
+  float4 ex = pr[2];
+  if (a.has_gamma) {                                  // x = U^-1 y, ex += u^T x
+    float4 acc = y, x = zero;
+#pragma unroll
+    for (int t = NL - 1; t >= 0; --t) {
+      if (r == t) x = df_mul(acc, myinv);
+      const float4 xt = shfl4(x, base + t);
+      if (r < t) acc = df_fms(acc, b[t], xt);
+    }
+    float4 part = df_mul(u, x);
+#pragma unroll
+    for (int t = 0; t < NL; ++t) ex = df_add(ex, shfl4(part, base + t));
+  }
+  if (!live || r != 0) return;
+  const double LN2 = 0.693147180559945309417232121458;
+  const double2 P = df_to(pr[0]), X = df_to(ex);
+  double* f = a.ldfin + 6 * leaf;
+  f[0] = P.x;
+  f[1] = P.y;
+  f[2] = (double)pr[1].x;
+  f[3] = -0.5 * (double)pr[1].y * LN2 + 0.5 * X.x;
+  f[4] = 0.5 * X.y;
+  f[5] = 0.0;
+  a.minpiv[leaf] = (double)pr[1].z;
+}
+
+template <int NL>
+cudaError_t launch_leaf(const TreeArgs& a, cudaStream_t s) {
+  constexpr int TEAMS = 32 / NL;
+  const long long warps = (a.grid.n_eval + TEAMS - 1) / TEAMS;
+  const long long blocks = (warps + 3) / 4;
+  k_tree_leaf<NL><<<(unsigned)blocks, 128, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t tree_level_smem_bytes(int nb, int m) { return sizeof(float4) * ((size_t)m * (m + 1) + nb); }
+
+// Leaf blocks of 2, 4, ..., 16 rows have a kernel instance (0: not supported).
+int tree_leaf_threads(int n) { return (n >= 2 && n <= 16 && n % 2 == 0) ? n : 0; }
+
+cudaError_t launch_points_tree(const TreeArgs& a, cudaStream_t s) {
+  cudaError_t err = cudaSuccess;
+  long long nodes = 1;
+  for (int l = 0; l + 1 < a.grid.L; ++l) {
+    const long long children = nodes * a.grid.radix[l];
+    const size_t smem = tree_level_smem_bytes(a.nb[l], a.m[l]);
+    if (smem > 48 * 1024) {
+      err = cudaFuncSetAttribute(k_tree_level, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (err != cudaSuccess) return err;
+    }
+    const int m = a.m[l], width = (m - 1) * m;        // entries of the first elimination step
+    const int threads = width >= 1024 ? 512 : width >= 256 ? 256 : 128;
+    k_tree_level<<<(unsigned)children, threads, smem, s>>>(a, l);
+    err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+    nodes = children;
+  }
+  switch (a.m[a.grid.L - 1]) {
+    case 2: return launch_leaf<2>(a, s);
+    case 4: return launch_leaf<4>(a, s);
+    case 6: return launch_leaf<6>(a, s);
+    case 8: return launch_leaf<8>(a, s);
+    case 10: return launch_leaf<10>(a, s);
+    case 12: return launch_leaf<12>(a, s);
+    case 14: return launch_leaf<14>(a, s);
+    case 16: return launch_leaf<16>(a, s);
+    default: return cudaErrorInvalidConfiguration;
+  }
+}
+
+}  // namespace gbsbin

@@ -149,3 +149,13 @@ def test_fock_host_validation(gb):
     assert _fock_status(gb, many) == 8                                                # 9 groups > 8
     nodes = synth.random_fock_problem(rng, 31, [3] * 31, 1, 4)
     assert _fock_status(gb, nodes) == 8                                               # 4^30 nodes
+
+
+def test_tree_kernel_validation(gb):
+    one_group = synth.random_problem(np.random.default_rng(7), 4, 1, 1, 3)
+    assert _status(gb, one_group, tile_override=11) == 8                 # the tree needs L >= 2
+    big = synth.random_problem(np.random.default_rng(8), 40, 1, 2, 2)    # n = 80 > 64
+    assert _status(gb, big, tile_override=11) == 8
+    assert _status(gb, synth.config(1), tile_override=11, want_backward=True) == 8
+    assert _status(gb, synth.config(1), tile_override=11, shard=(0, 10)) == 8
+    assert _status(gb, synth.config(1), tile_override=9) == 1            # a Fock kernel id
