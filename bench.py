@@ -3,14 +3,16 @@
 
 Metric: generating-function points per second (every point of the roots-of-unity grid
 counts; conjugate symmetry means about half are evaluated) and binned P(b) tables per
-second, for the FP32 + refinement path (``value``) next to the FP64 path, both held to
-|P - P_oracle| <= 1e-10.
+second, for the FP32-arithmetic path (``value``: on this grid the tree of block
+eliminations in pairs of FP32, kernel 11) next to the per-point FP32 + refinement warp
+kernel and the per-point FP64 path, all held to |P - P_oracle| <= 1e-10.
 
 Workload: M = 16 spatial modes, K = 1, r ~ U(0.5, 1.2), T = diag(sqrt(eta)) U with
 eta ~ U(0.4, 0.9) and Haar U, 4 detector groups of 4, N_l = 8: 9^4 = 6561 grid points of
 32 x 32 complex matrices per table.  One step = one table: every device stage of the path
-(grid phases, K(w) formed on chip, unpivoted LU, refinement, log det / exponent epilogue,
-inverse DFT, diagnostics) with the state (XA, gamma) resident in HBM.  ``e2e`` times the
+(grid phases, the per-point factorisation - shared Schur complements down the tree, or one
+LU per point - log det / exponent epilogue, inverse DFT, diagnostics) with the state
+resident in HBM.  ``e2e`` times the
 public C ABI from host buffers: per step the host FP64 state algebra and upload
 (gbsbin_plan_set_state) plus execute and the copy of the table back (gbsbin_execute_host).
 
@@ -50,6 +52,29 @@ def algorithmic_flops(n: int, has_gamma: bool) -> float:
     exponent when the state is displaced."""
     n = float(n)
     return (8.0 / 3.0) * n ** 3 + (8.0 * n * n if has_gamma else 0.0)
+
+
+def tree_work(prob, n_eval: int, has_gamma: bool):
+    """The tree of block eliminations (kernel 11): complex multiply-adds per table.  Level l
+    (one node per combination of the first l axes' roots) runs a Gauss-Jordan sweep over nb
+    pivot columns of its m x (m + 1) augmented matrix: step kk scales row kk right of the
+    pivot and updates the other m - 1 rows there, (m - kk)(m + 1 - kk - 1) multiply-adds,
+    plus the fill (nb (m + 1) products) and the u update (nb (m - nb)); each leaf runs an
+    unpivoted LU of its NL x NL block with the right-hand side, sum (NL - kk)^2, and, if
+    displaced, the back substitution (NL^2 / 2).  Returns (complex MACs, level launches)."""
+    rows = [2 * prob.K * int(np.sum(prob.bin_of_mode == l)) for l in range(prob.L)]
+    m, nodes, macs = prob.n, 1, 0.0
+    for l in range(prob.L - 1):
+        nodes *= int(prob.radix[l])
+        nb, cols = rows[l], m + 1
+        per = nb * cols + sum((m - kk) * (cols - kk - 1) for kk in range(nb))
+        if has_gamma:
+            per += nb * (m - nb)
+        macs += nodes * per
+        m -= nb
+    per_leaf = sum((m - kk) ** 2 for kk in range(m)) + (m * m / 2.0 if has_gamma else 0.0)
+    macs += n_eval * per_leaf
+    return macs, prob.L - 1
 
 
 def pipe_flops(n: int, has_gamma: bool, precision: int) -> float:
@@ -205,10 +230,12 @@ def main():
     prob = synth.config(WORKLOAD_INDEX)
     npts = prob.n_points
     stream = torch.cuda.current_stream()
-    plans = {p: gb.Plan(prob, precision=p, want_timing=True) for p in (1, 0)}
+    # precision 1 on this grid runs the tree of block eliminations (FP32 pairs); the per-point
+    # FP32 + refinement warp kernel and the per-point FP64 kernel are timed beside it
+    plans = {1: gb.Plan(prob, precision=1, want_timing=True), 0: gb.Plan(prob, precision=0, want_timing=True),
+             "warp": gb.Plan(prob, precision=1, want_timing=True, tile_override=5)}
     tables = {p: torch.empty(plans[p].shape, dtype=torch.float64, device="cuda") for p in plans}
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
-    launches_per_step = 2   # point kernel, fused DFT + diagnostics (one cooperative launch)
 
     peaks_meas = {"fp64_tflops": gb.gbsbin_alu_peak(0, SMS * 8), "fp32_tflops": gb.gbsbin_alu_peak(1, SMS * 8),
                   "int64_mad_wide_tops": gb.gbsbin_alu_peak(2, SMS * 8)}
@@ -221,7 +248,7 @@ def main():
     sampler = ClockSampler(local)
     sampler.start()
     results = {}
-    for p in (1, 0):
+    for p in (1, 0, "warp"):
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
         kms = []
         if world > 1:
@@ -251,6 +278,8 @@ def main():
     args_prob = gb.ProblemArgs(prob)
     n = prob.n
     h2d = n * n * (16 + 8 + 8 + 16) + n * (16 + 16 + 4 * 8)
+    if plans[1].diagnostics(stream)[1]["kernel_name"] == "tree_df32":
+        h2d += (n * n + 2 * n + 3) * 16     # the permuted state as FP32 pairs
     d2h = int(np.prod(plans[1].shape)) * 8
     for _ in range(3):
         gb.gbsbin_plan_set_state(plans[1].handle, args_prob, stream)
@@ -265,23 +294,42 @@ def main():
     e2e_value = world * npts * args.e2e_steps / e2e_s
 
     d1 = results[1]["diag"]
+    dw = results["warp"]["diag"]
     has_gamma = prob.alpha is not None
     out_points = {p: world * npts * args.steps / (results[p]["gpu_ms"] * 1e-3) for p in results}
     flops_pt = algorithmic_flops(n, has_gamma)
-    achieved = flops_pt * d1["n_evaluated"] / (results[1]["kernel_ms"] * 1e-3) / 1e12
-    pipe_pt = pipe_flops(n, has_gamma, 1)
-    pipe_achieved = pipe_pt * d1["n_evaluated"] / (results[1]["kernel_ms"] * 1e-3) / 1e12
     peak32 = SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
     peak64 = SMS * FP64_FMA_PER_SM_CLK * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    issue32 = SMS * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12    # FP32-pipe operations (T/s)
     achieved64 = flops_pt * d1["n_evaluated"] / (results[0]["kernel_ms"] * 1e-3) / 1e12
+    tree = d1["kernel_name"] == "tree_df32"
+    if tree:
+        macs, levels = tree_work(prob, d1["n_evaluated"], has_gamma)
+        launches_per_step = levels + 2        # level sweeps, leaves, fused DFT + diagnostics
+        achieved = 8.0 * macs / (results[1]["kernel_ms"] * 1e-3) / 1e12
+        # one complex multiply-add in FP32 pairs: product 38, sum 22, negation 4 operations
+        pipe_achieved = 64.0 * macs / (results[1]["kernel_ms"] * 1e-3) / 1e12
+        roof_extra = {"flops": "tree of block eliminations: 8 x complex multiply-adds per table",
+                      "flops_per_table": 8.0 * macs, "pipe_ops_per_table": 64.0 * macs,
+                      "pipe_unit": "FP32-pipe operations / s (T)", "pipe_peak": issue32,
+                      "pipe_frac": pipe_achieved / issue32}
+    else:
+        launches_per_step = 2                  # point kernel, fused DFT + diagnostics
+        achieved = flops_pt * d1["n_evaluated"] / (results[1]["kernel_ms"] * 1e-3) / 1e12
+        pipe_achieved = pipe_flops(n, has_gamma, 1) * d1["n_evaluated"] / (results[1]["kernel_ms"] * 1e-3) / 1e12
+        roof_extra = {"flops": "complex LU (8/3) n^3 per evaluated point", "flops_per_point": flops_pt,
+                      "pipe_flops_per_point": pipe_flops(n, has_gamma, 1), "pipe_frac": pipe_achieved / peak32}
+    achieved_w = flops_pt * dw["n_evaluated"] / (results["warp"]["kernel_ms"] * 1e-3) / 1e12
+    pipe_w = pipe_flops(n, has_gamma, 1) * dw["n_evaluated"] / (results["warp"]["kernel_ms"] * 1e-3) / 1e12
     traffic = _profiled_traffic(d1["kernel_name"])
 
     line = {
         "metric": METRIC, "value": out_points[1], "unit": "points/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": results[1]["ms_per_step"], "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64refine", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32x2" if tree else "f32+f64refine", "data": "synthetic",
         "config": {"workload": WORKLOAD_NAME, "n": n, "grid_points": npts, "evaluated_points": d1["n_evaluated"],
                    "bins": prob.L, "cutoff": int(prob.cutoff[0]), "precision": "fp32_refine",
+                   "kernel": d1["kernel_name"],
                    "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas{world}"},
         "tables_per_s": world * args.steps / (results[1]["gpu_ms"] * 1e-3),
         "fp64": {"value": out_points[0], "unit": "points/s", "ms_per_step": results[0]["ms_per_step"],
@@ -289,15 +337,19 @@ def main():
                  "point_kernel_ms": results[0]["kernel_ms"],
                  "roofline": {"bound": "alu", "achieved": achieved64, "peak": peak64, "unit": "TFLOP/s",
                               "frac": achieved64 / peak64, "traffic": None}},
+        "per_point_fp32_refine": {"kernel": dw["kernel_name"], "value": out_points["warp"], "unit": "points/s",
+                                  "ms_per_step": results["warp"]["ms_per_step"],
+                                  "point_kernel_ms": results["warp"]["kernel_ms"],
+                                  "roofline": {"bound": "alu", "achieved": achieved_w, "peak": peak32,
+                                               "unit": "TFLOP/s", "frac": achieved_w / peak32,
+                                               "pipe_achieved": pipe_w, "pipe_frac": pipe_w / peak32,
+                                               "traffic": _profiled_traffic(dw["kernel_name"])}},
         "speedup_fp32r_vs_fp64": out_points[1] / out_points[0],
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak32, "unit": "TFLOP/s",
-                     "frac": achieved / peak32, "traffic": traffic,
-                     "kernel": d1["kernel_name"], "kernel_ms": results[1]["kernel_ms"],
-                     "flops_per_point": flops_pt, "flops": "complex LU (8/3) n^3 per evaluated point",
-                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
-                     "pipe_flops_per_point": pipe_pt, "pipe_achieved": pipe_achieved,
-                     "pipe_frac": pipe_achieved / peak32,
-                     "measured_alu_chains": peaks_meas},
+        "roofline": dict({"bound": "alu", "achieved": achieved, "peak": peak32, "unit": "TFLOP/s",
+                          "frac": achieved / peak32, "traffic": traffic,
+                          "kernel": d1["kernel_name"], "kernel_ms": results[1]["kernel_ms"],
+                          "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
+                          "pipe_achieved": pipe_achieved, "measured_alu_chains": peaks_meas}, **roof_extra),
         "e2e": {"value": e2e_value, "unit": "points/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
@@ -527,8 +579,8 @@ def cpu_baseline(prob, seconds, tables):
         if time.perf_counter() - t0 > seconds:
             break
     dt = time.perf_counter() - t0
-    errs = {("fp32_refine" if p == 1 else "fp64"): float(np.abs(tables[p].cpu().numpy() - ref).max())
-            for p in tables}
+    names = {1: "fp32_refine", 0: "fp64", "warp": "per_point_fp32_refine"}
+    errs = {names.get(p, str(p)): float(np.abs(tables[p].cpu().numpy() - ref).max()) for p in tables}
     return ({"value": prob.n_points * count / dt, "unit": "points/s", "cores": os.cpu_count(), "kind": "oracle",
              "sample": f"{count} whole {prob.n_points}-point tables in {dt:.1f} s"}, errs)
 
