@@ -58,13 +58,76 @@ __device__ __forceinline__ void path_pivot(float4* pr, float4 p) {
   pr[1] = make_float4(__fadd_rn(pr[1].x, atan2f(p.y, p.x)), e2, mn, 0.f);
 }
 
-// Level l: one CTA per child (parent, k) of depth l.
+__device__ __forceinline__ float4 shfl4(float4 v, int src) {
+  return make_float4(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src),
+                     __shfl_sync(0xffffffffu, v.z, src), __shfl_sync(0xffffffffu, v.w, src));
+}
+__device__ __forceinline__ float4 shfl4_xor(float4 v, int mask) {
+  return make_float4(__shfl_xor_sync(0xffffffffu, v.x, mask), __shfl_xor_sync(0xffffffffu, v.y, mask),
+                     __shfl_xor_sync(0xffffffffu, v.z, mask), __shfl_xor_sync(0xffffffffu, v.w, mask));
+}
+
+// The path record after a set of pivots, by one full warp: lane t holds pivot t of the set
+// (count <= 32; lanes beyond hold 1).  Product by a butterfly of pair products (each level
+// rescaled by a power of two), argument sum and smallest real part by butterflies too.
+// pr: the parent's record on input, the child's on output (every lane).
+__device__ __forceinline__ void path_warp(float4* pr, float4 piv, bool real) {
+  const int lane = threadIdx.x & 31;
+  float4 p = real ? piv : make_float4(1.f, 0.f, 0.f, 0.f);
+  float arg = real ? atan2f(piv.y, piv.x) : 0.f;
+  float mn = real ? piv.x : 3.0e38f;
+  if (real && (!(piv.x == piv.x) || !(piv.y == piv.y))) mn = -3.0e38f;
+  float e2 = 0.f;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    p = df_mul(p, shfl4_xor(p, o));
+    const float mx = fmaxf(fabsf(p.x), fabsf(p.y));
+    float eo = __shfl_xor_sync(0xffffffffu, e2, o);
+    e2 += eo;
+    if (mx > 0.f && mx < 1.0e30f) {
+      int ex;
+      frexpf(mx, &ex);
+      p = make_float4(ldexpf(p.x, -ex), ldexpf(p.y, -ex), ldexpf(p.z, -ex), ldexpf(p.w, -ex));
+      e2 += (float)ex;
+    }
+    arg = __fadd_rn(arg, __shfl_xor_sync(0xffffffffu, arg, o));
+    mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+  }
+  (void)lane;
+  // every lane now holds the same product, exponent, sum and minimum; fold in the parent
+  float4 q = df_mul(pr[0], p);
+  float e = pr[1].y + e2;
+  const float mx = fmaxf(fabsf(q.x), fabsf(q.y));
+  if (mx > 0.f && mx < 1.0e30f) {
+    int ex;
+    frexpf(mx, &ex);
+    q = make_float4(ldexpf(q.x, -ex), ldexpf(q.y, -ex), ldexpf(q.z, -ex), ldexpf(q.w, -ex));
+    e += (float)ex;
+  }
+  pr[0] = q;
+  pr[1] = make_float4(__fadd_rn(pr[1].x, arg), e, fminf(pr[1].z, mn), 0.f);
+}
+
+// Level l: one CTA per child (parent, k) of depth l.  Forward elimination of the nb pivot
+// columns of the (m + 1) x (m + 1) augmented matrix
+//
+//   [ B      | w A_0r | w c_0 ]
+//   [ -A_r0  | A_rr   | c_r   ]
+//   [ -u_0^T | u_r^T  | 0     ]
+//
+// leaves the child's A' and c' in the middle rows and (u'^T | u_0^T y) in the last row:
+// eliminating block 0 from a row [a_0 | a_r] gives a_r - a_0 B^-1 [w A_0r | w c_0].  Rows
+// are never scaled (only the Schur complement is needed): step kk subtracts
+// (G[i][kk] / G[kk][kk]) row kk from every row i > kk: one thread forms the pivot's
+// reciprocal, the rows below their multipliers, then every entry one fused multiply-subtract.
 __global__ void __launch_bounds__(LT_MAX) k_tree_level(TreeArgs a, int l) {
   extern __shared__ __align__(16) float4 gsm[];
   const int nb = a.nb[l], m = a.m[l], mc = m - nb, cols = m + 1;
-  float4* G = gsm;                                   // m x cols, the augmented matrix
-  float4* pv = G + (size_t)m * cols;                 // nb pivots
-  __shared__ float4 s_inv;
+  const int rows = a.has_gamma ? m + 1 : m;
+  float4* G = gsm;                                   // rows x cols
+  float4* pv = G + (size_t)rows * cols;              // nb pivots
+  float4* Lm = pv + nb;                              // rows: multipliers of the current step
+  __shared__ float4 s_inv[1];
   const long long child = blockIdx.x;
   const int R = a.grid.radix[l];
   const long long parent = child / R;
@@ -75,50 +138,52 @@ __global__ void __launch_bounds__(LT_MAX) k_tree_level(TreeArgs a, int l) {
   const float4* up = a.u[l] + parent * (long long)m;
   const int tid = threadIdx.x, LT = blockDim.x;
   const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
-  for (int idx = tid; idx < m * cols; idx += LT) {
+  for (int idx = tid; idx < rows * cols; idx += LT) {
     const int i = idx / cols, s = idx - (idx / cols) * cols;
-    const float4 v = s < m ? Ap[(long long)i * m + s] : (a.has_gamma ? cp[i] : zero);
     float4 g;
-    if (i < nb) {
-      g = df_mul(w, v);
-      if (s < nb) {
-        g = df_neg(g);
-        if (s == i) g = df_add(g, make_float4(1.f, 0.f, 0.f, 0.f));
-      }
+    if (i == m) {                                   // the u row
+      g = s < nb ? df_neg(up[s]) : s < m ? up[s] : zero;
     } else {
-      g = s < nb ? df_neg(v) : v;
+      const float4 v = s < m ? Ap[(long long)i * m + s] : (a.has_gamma ? cp[i] : zero);
+      if (i < nb) {
+        g = df_mul(w, v);
+        if (s < nb) {
+          g = df_neg(g);
+          if (s == i) g = df_add(g, make_float4(1.f, 0.f, 0.f, 0.f));
+        }
+      } else {
+        g = s < nb ? df_neg(v) : v;
+      }
     }
     G[idx] = g;
   }
   for (int kk = 0; kk < nb; ++kk) {
-    __syncthreads();
+    __syncthreads();                                 // row kk final
     if (tid == 0) {
       const float4 piv = G[kk * cols + kk];
       pv[kk] = piv;
-      s_inv = df_recip(piv);
+      s_inv[0] = df_recip(piv);
     }
     __syncthreads();
-    const float4 r = s_inv;
-    for (int s = kk + 1 + tid; s < cols; s += LT) G[kk * cols + s] = df_mul(G[kk * cols + s], r);
+    const float4 r = s_inv[0];
+    for (int i = kk + 1 + tid; i < rows; i += LT) Lm[i] = df_mul(G[i * cols + kk], r);
     __syncthreads();
-    // columns right of kk, rows other than kk; two independent entries per pass.  The row
-    // of entry idx is floor(idx / w_) from a float reciprocal: idx < 2^14 and w_ <= 65, so
-    // (idx + 1/2) / w_ stays more than 1/(2 w_) from an integer, far above its rounding
-    const int w_ = cols - kk - 1, total = (m - 1) * w_;
+    // entries (i, s), i in (kk, rows), s in (kk, cols); two independent entries per pass.
+    // floor(idx / w_) from a float reciprocal: idx < 2^14 and w_ <= 65, so (idx + 1/2) / w_
+    // stays more than 1/(2 w_) from an integer, far above its rounding
+    const int w_ = cols - kk - 1, total = (rows - kk - 1) * w_;
     const float rw = 1.0f / (float)w_;
     for (int idx = tid; idx < total; idx += 2 * LT) {
       const int idx2 = idx + LT;
-      int i = (int)(((float)idx + 0.5f) * rw);
-      const int s = kk + 1 + (idx - i * w_);
-      if (i >= kk) ++i;
-      const float4 g1 = df_fms(G[i * cols + s], G[i * cols + kk], G[kk * cols + s]);
+      const int i = kk + 1 + (int)(((float)idx + 0.5f) * rw);
+      const int sc = kk + 1 + (idx - (i - kk - 1) * w_);
+      const float4 g1 = df_fms(G[i * cols + sc], Lm[i], G[kk * cols + sc]);
       if (idx2 < total) {
-        int i2 = (int)(((float)idx2 + 0.5f) * rw);
-        const int s2 = kk + 1 + (idx2 - i2 * w_);
-        if (i2 >= kk) ++i2;
-        G[i2 * cols + s2] = df_fms(G[i2 * cols + s2], G[i2 * cols + kk], G[kk * cols + s2]);
+        const int i2 = kk + 1 + (int)(((float)idx2 + 0.5f) * rw);
+        const int s2 = kk + 1 + (idx2 - (i2 - kk - 1) * w_);
+        G[i2 * cols + s2] = df_fms(G[i2 * cols + s2], Lm[i2], G[kk * cols + s2]);
       }
-      G[i * cols + s] = g1;
+      G[i * cols + sc] = g1;
     }
   }
   __syncthreads();
@@ -132,28 +197,26 @@ __global__ void __launch_bounds__(LT_MAX) k_tree_level(TreeArgs a, int l) {
     float4* uc = a.u[l + 1] + child * (long long)mc;
     for (int j = tid; j < mc; j += LT) {
       cc[j] = G[(nb + j) * cols + m];
-      float4 uv = up[nb + j];
-      for (int t = 0; t < nb; ++t) uv = df_fma(G[t * cols + nb + j], up[t], uv);
-      uc[j] = uv;
+      uc[j] = G[m * cols + nb + j];
     }
   }
-  if (tid == 0) {
+  if (tid < 32) {                                    // the child's path record (warp 0)
     const float4* pp = a.path[l] + parent * 3;
     float4 pr[3] = {pp[0], pp[1], pp[2]};
-    for (int t = 0; t < nb; ++t) path_pivot(pr, pv[t]);
-    if (a.has_gamma)
-      for (int t = 0; t < nb; ++t) pr[2] = df_fma(up[t], G[t * cols + m], pr[2]);
-    float4* pc = a.path[l + 1] + child * 3;
-    pc[0] = pr[0];
-    pc[1] = pr[1];
-    pc[2] = pr[2];
+    for (int t0 = 0; t0 < nb; t0 += 32) {
+      const int t = t0 + tid;
+      path_warp(pr, t < nb ? pv[t] : zero, t < nb);
+    }
+    if (a.has_gamma) pr[2] = df_add(pr[2], G[m * cols + m]);
+    if (tid == 0) {
+      float4* pc = a.path[l + 1] + child * 3;
+      pc[0] = pr[0];
+      pc[1] = pr[1];
+      pc[2] = pr[2];
+    }
   }
 }
 
-__device__ __forceinline__ float4 shfl4(float4 v, int src) {
-  return make_float4(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src),
-                     __shfl_sync(0xffffffffu, v.z, src), __shfl_sync(0xffffffffu, v.w, src));
-}
 
 // Leaves: a team of NL lanes per evaluated point (32 / NL teams per warp), lane r holding
 // row r of B = I - w A_leaf and of the right-hand side w c in registers.  Step kk
@@ -190,18 +253,25 @@ __global__ void __launch_bounds__(128) k_tree_leaf(TreeArgs a) {
   const float4* pp = a.path[l] + parent * 3;
   float4 pr[3] = {pp[0], pp[1], pp[2]};
   float4 myinv = one;
-#pragma unroll
+  // the step loop stays rolled (an unrolled copy per step overflows the instruction
+  // cache); the row stays in registers, entries left of the step skipped by a uniform test
+#pragma unroll 1
   for (int kk = 0; kk < NL; ++kk) {
     const int src = base + kk;
-    const float4 piv = shfl4(b[kk], src);
+    float4 bk = b[0];
+#pragma unroll
+    for (int j = 1; j < NL; ++j)
+      if (j == kk) bk = b[j];
+    const float4 piv = shfl4(bk, src);
     const float4 ykk = shfl4(y, src);
     path_pivot(pr, piv);
     const float4 inv = df_recip(piv);
     if (r == kk) myinv = inv;
     const bool below = r > kk;
-    const float4 li = df_mul(b[kk], inv);            // used by the rows below only
+    const float4 li = df_mul(bk, inv);               // used by the rows below only
 #pragma unroll
-    for (int j = kk + 1; j < NL; ++j) {
+    for (int j = 1; j < NL; ++j) {
+      if (j <= kk) continue;
       const float4 rj = shfl4(b[j], src);
       if (below) b[j] = df_fms(b[j], li, rj);
     }
@@ -244,7 +314,7 @@ cudaError_t launch_leaf(const TreeArgs& a, cudaStream_t s) {
 
 }  // namespace
 
-size_t tree_level_smem_bytes(int nb, int m) { return sizeof(float4) * ((size_t)m * (m + 1) + nb); }
+size_t tree_level_smem_bytes(int nb, int m) { return sizeof(float4) * ((size_t)(m + 1) * (m + 1) + nb + m + 1); }
 
 // Leaf blocks of 2, 4, ..., 16 rows have a kernel instance (0: not supported).
 int tree_leaf_threads(int n) { return (n >= 2 && n <= 16 && n % 2 == 0) ? n : 0; }
@@ -259,7 +329,7 @@ cudaError_t launch_points_tree(const TreeArgs& a, cudaStream_t s) {
       err = cudaFuncSetAttribute(k_tree_level, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (err != cudaSuccess) return err;
     }
-    const int m = a.m[l], width = (m - 1) * m;        // entries of the first elimination step
+    const int m = a.m[l], width = m * m;              // entries of the first elimination step
     const int threads = width >= 1024 ? 512 : width >= 256 ? 256 : 128;
     k_tree_level<<<(unsigned)children, threads, smem, s>>>(a, l);
     err = cudaGetLastError();
