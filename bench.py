@@ -548,8 +548,9 @@ def _sources_hash(paths):
 
 
 def _profiled_traffic(kernel_name):
-    """DRAM bytes per launch of the point kernel from the committed ncu summary, or None
-    when no summary exists for this kernel or its sources changed since the capture."""
+    """DRAM bytes per launch of the point kernel (per table for the tree's four launches)
+    from the committed ncu summary, or None when no summary exists for this kernel or its
+    sources changed since the capture."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         tj = json.load(open(path))
@@ -563,7 +564,7 @@ def _profiled_traffic(kernel_name):
             return None
     except (OSError, KeyError):
         return None
-    return entry["dram_bytes_per_launch"]
+    return entry.get("dram_bytes_per_launch", entry.get("dram_bytes_per_table"))
 
 
 def cpu_baseline(prob, seconds, tables):

@@ -559,6 +559,7 @@ def gbsbin_fock_diagnostics(plan, stream=None):
     d = gbsbin_diag()
     st = load().gbsbin_fock_diagnostics(plan, ctypes.byref(d), _stream_handle(stream))
     out = {f: getattr(d, f) for f, _ in gbsbin_diag._fields_}
+    out["kernel_name"] = KERNELS.get(out["kernel"], "?")
     out["status"] = st
     return out
 
