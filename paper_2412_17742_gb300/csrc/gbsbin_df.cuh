@@ -92,4 +92,40 @@ __device__ __forceinline__ float4 df_recip(float4 a) {
   return df_mul(df_conj(a), make_float4(sh, 0.f, sl, 0.f));
 }
 
+// Real pairs (hi, lo) in the x and z components of a float4 (y = w = 0).
+// 1 / a by one Newton step on the FP32 seed (as in df_recip).
+__device__ __forceinline__ float4 df_rrecip(float4 a) {
+  const float s0 = __frcp_rn(a.x);
+  const float r = __fsub_rn(fmaf(-a.x, s0, 1.0f), __fmul_rn(a.z, s0));   // 1 - a s0
+  float sh, sl;
+  fast_two_sum(s0, __fmul_rn(s0, r), sh, sl);
+  return make_float4(sh, 0.f, sl, 0.f);
+}
+// sqrt(a), a >= 0, by one Newton (Heron) step on the FP32 seed t = sqrt(hi):
+// sqrt(a) = t + (a - t^2) / (2 t), the residual a - t^2 formed with an FMA.
+__device__ __forceinline__ float4 df_rsqrt_root(float4 a) {
+  if (!(a.x > 0.f)) return make_float4(0.f, 0.f, 0.f, 0.f);
+  const float t = __fsqrt_rn(a.x);
+  const float res = __fadd_rn(fmaf(-t, t, a.x), a.z);                      // a - t^2
+  const float corr = __fdiv_rn(res, __fmul_rn(2.0f, t));
+  float h, l;
+  fast_two_sum(t, corr, h, l);
+  return make_float4(h, 0.f, l, 0.f);
+}
+// Principal square root of a complex pair z = x + i y: r = |z|, s = sqrt((r + |x|) / 2),
+// then (s, y / (2 s)) for x >= 0 and (|y| / (2 s), sign(y) s) otherwise.
+__device__ __forceinline__ float4 df_csqrt(float4 z) {
+  const float4 x = make_float4(z.x, 0.f, z.z, 0.f), y = make_float4(z.y, 0.f, z.w, 0.f);
+  const float4 r = df_rsqrt_root(df_add(df_mul(x, x), df_mul(y, y)));
+  const bool neg = z.x < 0.f;
+  const float4 ax = neg ? df_neg(x) : x;
+  const float4 half = make_float4(0.5f, 0.f, 0.f, 0.f);
+  const float4 s = df_rsqrt_root(df_mul(df_add(r, ax), half));
+  if (!(s.x > 0.f)) return make_float4(0.f, 0.f, 0.f, 0.f);
+  const float4 q = df_mul(y, df_rrecip(df_mul(s, make_float4(2.f, 0.f, 0.f, 0.f))));   // y / (2 s)
+  if (!neg) return make_float4(s.x, q.x, s.z, q.z);
+  const float sg = z.y < 0.f ? -1.f : 1.f;
+  return make_float4(fabsf(q.x), sg * s.x, q.x < 0.f ? -q.z : q.z, sg * s.z);
+}
+
 }  // namespace gbsbin

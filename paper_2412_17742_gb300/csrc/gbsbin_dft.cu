@@ -176,7 +176,7 @@ __device__ __forceinline__ void stage_diag(const double* __restrict__ P, long lo
   }
   for (long long e = t0; minpiv && e < n_eval; e += stride) {
     double m = minpiv[e];
-    double2 l = logq[e];
+    double2 l = logq ? logq[e] : make_double2(0.0, 0.0);
     bool ok = (m > 0.0) && isfinite(l.x) && isfinite(l.y);
     if (!ok) bad += 1.0;
     mn = fmin(mn, m);
@@ -270,7 +270,10 @@ __global__ void __launch_bounds__(128) k_dft_fused(DftFused f) {
   const int tid = ((threadIdx.x & 31) << 2) | (threadIdx.x >> 5);
   const long long t0 = tid * (long long)gridDim.x + blockIdx.x;
   const long long stride = (long long)gridDim.x * blockDim.x;
-  if (a.parts) {
+  const bool first = !a.g_ready;
+  if (a.g_ready) {
+    // G already in bufA (written by the point kernel)
+  } else if (a.parts) {
     stage_sum_parts(a.parts, a.nparts, a.pscale, a.grid, a.bufA, t0, stride);
   } else {
     __shared__ double2 s_l0;
@@ -281,22 +284,28 @@ __global__ void __launch_bounds__(128) k_dft_fused(DftFused f) {
   double2* cur = a.bufA;
   double2* nxt = a.bufB;
   for (int l = 0; l < f.naxes; ++l) {
-    grid_barrier(f.bar);
+    if (l > 0 || first) grid_barrier(f.bar);
     const DftStage& st = f.ax[l];
     stage_axis(cur, nxt, st.outer, st.R, st.nout, st.inner, a.tw + st.twoff, t0, stride);
     double2* t = cur;
     cur = nxt;
     nxt = t;
   }
-  grid_barrier(f.bar);
+  if (f.naxes > 0 || first) grid_barrier(f.bar);
   stage_last_real(cur, a.P, f.last_outer, f.last_R, f.H, f.last_nout, f.scale, a.tw + f.last_twoff, t0, stride);
   if (a.diag) {
     grid_barrier(f.bar);
     if ((int)blockIdx.x < GBSBIN_DIAG_BLOCKS)
-      stage_diag(a.P, a.table_size, cur, f.last_outer, f.H, f.last_R, a.minpiv, a.ldfin ? a.logq_fin : a.logq,
+      stage_diag(a.P, a.table_size, cur, f.last_outer, f.H, f.last_R, a.minpiv,
+                 a.g_ready ? nullptr : a.ldfin ? a.logq_fin : a.logq,
                  a.grid.n_eval, a.diag, blockIdx.x, GBSBIN_DIAG_BLOCKS);
     if (t0 == 0) a.diag[4 * GBSBIN_DIAG_BLOCKS + 1] = (double)*(volatile unsigned*)(f.bar + 2);
   }
+}
+
+__global__ void k_finish_logq(const double* __restrict__ ldfin, double2* __restrict__ logq, long long n) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    logq[e] = finish_logq(ldfin + 6 * e);
 }
 
 // Small transforms use 64-thread blocks so the work spreads over many SMs (these kernels
@@ -351,6 +360,11 @@ cudaError_t launch_dft(const DftArgs& a, cudaStream_t s) {
     err = cudaGetLastError();
   }
   return err;
+}
+
+cudaError_t launch_finish_logq(const double* ldfin, double2* logq, long long n, cudaStream_t s) {
+  k_finish_logq<<<blocks_for(n), kDftThreads, 0, s>>>(ldfin, logq, n);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_dft_fused(const DftArgs& a, unsigned* bar, int num_sms, cudaStream_t s) {

@@ -43,6 +43,8 @@ struct gbsbin_plan {
   // depths 1 .. L-1 in d_tree
   std::vector<int> tree_perm;
   TreeArgs tree{};
+  bool tree_g = false;                // undisplaced tree plan: leaves write G, the DFT skips a stage
+  double tree_logq0 = 0.0;            // Re log q(1) from the host LU (diagnostics)
   unsigned char* d_tree = nullptr;
   int* d_label = nullptr;
   double2* d_logq = nullptr;
@@ -358,6 +360,38 @@ int upload_state(gbsbin_plan* P, cudaStream_t stream) {
     path[0] = make_float4(1.f, 0.f, 0.f, 0.f);        // pivot product
     path[1] = make_float4(0.f, 0.f, 3.0e38f, 0.f);    // argument sum, power of two, min Re pivot
     path[2] = make_float4(0.f, 0.f, 0.f, 0.f);        // exponent sum
+    // the w = 1 point on the host: unpivoted LU of I - XA in the tree's row order, its pivot
+    // product p0 2^e0, argument and winding (each pivot has Re > 0)
+    P->tree_g = !P->has_gamma;
+    if (P->tree_g) {
+      std::vector<cd> K((size_t)n * n);
+      for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) K[(size_t)i * n + j] = (i == j ? 1.0 : 0.0) - P->XA[(size_t)pm[i] * n + pm[j]];
+      cd prod = 1.0;
+      int e0 = 0;
+      double args = 0.0;
+      for (int k = 0; k < n; ++k) {
+        const cd piv = K[(size_t)k * n + k];
+        prod *= piv;
+        int ex;
+        std::frexp(std::max(std::fabs(prod.real()), std::fabs(prod.imag())), &ex);
+        prod = cd(std::ldexp(prod.real(), -ex), std::ldexp(prod.imag(), -ex));
+        e0 += ex;
+        args += std::atan2(piv.imag(), piv.real());
+        for (int i = k + 1; i < n; ++i) {
+          const cd li = K[(size_t)i * n + k] / piv;
+          for (int j = k + 1; j < n; ++j) K[(size_t)i * n + j] -= li * K[(size_t)k * n + j];
+        }
+      }
+      const double TWO_PI = 6.283185307179586476925286766559;
+      const double arg0 = std::atan2(prod.imag(), prod.real());
+      P->tree.p0re = prod.real();
+      P->tree.p0im = prod.imag();
+      P->tree.p0arg = (float)arg0;
+      P->tree.e0 = (float)e0;
+      P->tree.m0 = (float)std::nearbyint((args - arg0) / TWO_PI);
+      P->tree_logq0 = -0.5 * (std::log(std::abs(prod)) + e0 * 0.693147180559945309417232121458);
+    }
   }
   // the device block has the staging layout: one copy
   e = cudaMemcpyAsync(P->d_state, h, s.total, cudaMemcpyHostToDevice, stream);
@@ -947,10 +981,12 @@ int gbsbin_execute(gbsbin_plan* P, double* P_out, void* stream) {
     t.grid = P->grid;
     t.ldfin = P->d_ldfin;
     t.minpiv = P->d_minpiv;
+    t.gout = P->tree_g ? P->d_bufA : nullptr;
     if (launch_points_tree(t, s) != cudaSuccess) return GBSBIN_ERR_CUDA;
     if (P->ev1 && cudaEventRecord(P->ev1, s) != cudaSuccess) return GBSBIN_ERR_CUDA;
-    return launch_dft_fused(make_dft_args(P, P_out), P->d_bar, P->num_sms, s) == cudaSuccess ? GBSBIN_OK
-                                                                                          : GBSBIN_ERR_CUDA;
+    DftArgs d = make_dft_args(P, P_out);
+    d.g_ready = P->tree_g ? 1 : 0;
+    return launch_dft_fused(d, P->d_bar, P->num_sms, s) == cudaSuccess ? GBSBIN_OK : GBSBIN_ERR_CUDA;
   }
   cudaError_t e = P->kernel == GBSBIN_KERNEL_WARP_FP32R  ? launch_points_warp(a, P->num_sms, s)
                   : P->kernel == GBSBIN_KERNEL_HESS_FP64 ? launch_points_hess(a, PointBatch{}, P->num_sms, s)
@@ -993,7 +1029,7 @@ int gbsbin_diagnostics(gbsbin_plan* P, gbsbin_diag* out, void* stream) {
   out->max_imag = h[1];
   out->min_pivot_re = h[2];
   out->n_bad_points = (long long)h[3];
-  out->log_q1_re = h[4];
+  out->log_q1_re = (P->kernel == GBSBIN_KERNEL_TREE_DF32 && P->tree_g) ? P->tree_logq0 : h[4];
   out->n_points = P->grid.npts;
   out->n_evaluated = P->grid.n_eval;
   out->table_size = P->table_size;
@@ -1017,6 +1053,10 @@ int gbsbin_read_points(gbsbin_plan* P, double* logq_host, double* minpiv_host, v
   if (!P || !logq_host) return GBSBIN_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   const size_t ne = (size_t)P->grid.n_eval;
+  // plans whose DFT took G directly left log q unfinished
+  if (P->kernel == GBSBIN_KERNEL_TREE_DF32 && P->tree_g &&
+      launch_finish_logq(P->d_ldfin, P->d_logq, (long long)ne, s) != cudaSuccess)
+    return GBSBIN_ERR_CUDA;
   if (cudaMemcpyAsync(logq_host, P->d_logq, ne * sizeof(double2), cudaMemcpyDeviceToHost, s) != cudaSuccess)
     return GBSBIN_ERR_CUDA;
   if (minpiv_host &&

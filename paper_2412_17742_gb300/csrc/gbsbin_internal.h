@@ -99,6 +99,7 @@ struct BackwardArgs {
 
 struct DftArgs {
   GridDesc grid;
+  int g_ready;              // bufA already holds G on the evaluated half grid: no first stage
   const double2* parts;     // non-null: G is given as nparts partial sums per half-grid point
                             // (parts[r * n_full + t]); the transform uses pscale * their sum
                             // (summed in order r = 0, 1, ...) instead of exp(log q - log q_0)
@@ -134,6 +135,12 @@ struct TreeArgs {
   GridDesc grid;
   double* ldfin;
   double* minpiv;
+  // undisplaced plans: the leaves also write G = q / q(1) per evaluated point to gout, from
+  // the pivot product P0 = p0 2^e0 of I - XA (host FP64, same row order), its argument
+  // p0arg and winding m0 (log det(I - XA) = log|P0| + e0 log 2 + i (p0arg + 2 pi m0))
+  double2* gout;
+  double p0re, p0im;
+  float p0arg, e0, m0;
 };
 size_t tree_level_smem_bytes(int nb, int m);
 int tree_leaf_threads(int n);   // lanes per leaf (0: no kernel for a last group of n rows)
@@ -194,6 +201,9 @@ size_t points_matrix_bytes(int kernel, int n, int P);
 int points_per_cta(int kernel, int n, int L);
 int points_threads(int kernel, int n);
 cudaError_t launch_dft(const DftArgs& a, cudaStream_t s);
+// log q of n evaluated points from the unfinished form (ldfin) - for plans whose DFT took G
+// directly and did not finish them.
+cudaError_t launch_finish_logq(const double* ldfin, double2* logq, long long n, cudaStream_t s);
 // All DFT stages and the diagnostics in one cooperative launch; bar: 4 zeroed unsigned ints
 // of grid-barrier state owned by the caller; needs diag to hold 4 GBSBIN_DIAG_BLOCKS + 2.
 cudaError_t launch_dft_fused(const DftArgs& a, unsigned* bar, int num_sms, cudaStream_t s);

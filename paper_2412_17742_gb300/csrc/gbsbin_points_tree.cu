@@ -301,6 +301,23 @@ __global__ void __launch_bounds__(128) k_tree_leaf(TreeArgs a) {
   f[4] = 0.5 * X.y;
   f[5] = 0.0;
   a.minpiv[leaf] = (double)pr[1].z;
+  if (a.gout) {                                      // G = q / q(1) = (P0 / P)^(1/2) 2^((e0 - e)/2) (-1)^w
+    const float TWO_PI = 6.28318530717958647692f;
+    const float argP = atan2f(pr[0].y, pr[0].x);
+    const float m = rintf((pr[1].x - argP) / TWO_PI);           // winding of log det at this point
+    const float4 Z = df_mul(df_from(make_double2(a.p0re, a.p0im)), df_recip(pr[0]));
+    const float kz = rintf((atan2f(Z.y, Z.x) - (a.p0arg - argP)) / TWO_PI);
+    const int wind = (int)(kz + m - a.m0);
+    double2 g = df_to(df_csqrt(Z));
+    const int d = (int)(a.e0 - pr[1].y);
+    if (d & 1) {
+      g.x *= 1.41421356237309504880;
+      g.y *= 1.41421356237309504880;
+    }
+    const int hexp = (d - (d & 1)) / 2;
+    const double sg = (wind & 1) ? -1.0 : 1.0;
+    a.gout[leaf] = make_double2(sg * ldexp(g.x, hexp), sg * ldexp(g.y, hexp));
+  }
 }
 
 template <int NL>
