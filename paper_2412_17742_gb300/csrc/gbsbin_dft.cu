@@ -399,11 +399,12 @@ cudaError_t launch_dft_fused(const DftArgs& a, unsigned* bar, int num_sms, cudaS
   if (err != cudaSuccess) return err;
   if (per_sm > 4) per_sm = 4;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  // one CTA per SM (the stages are FP64-latency-bound: spreading beats packing), more only
-  // for grids with more than 128 items per SM; at least the diagnostics' blocks
-  long long blocks = num_sms;
-  const long long need = (g.n_full + 127) / 128;
-  if (need > blocks) blocks = need < (long long)per_sm * num_sms ? need : (long long)per_sm * num_sms;
+  // one item per thread in the largest stage (the stages are FP64-latency-bound chains, so
+  // more CTAs than that only add arrivals at every grid barrier); at least the diagnostics'
+  // blocks
+  const long long items = g.n_full > a.table_size ? g.n_full : a.table_size;
+  long long blocks = (items + 127) / 128;
+  if (blocks > (long long)per_sm * num_sms) blocks = (long long)per_sm * num_sms;
   if (blocks < GBSBIN_DIAG_BLOCKS) blocks = GBSBIN_DIAG_BLOCKS;
   if (blocks > (long long)per_sm * num_sms) return cudaErrorInvalidConfiguration;
   void* params[] = {&f};
