@@ -128,14 +128,23 @@ __global__ void k_dft_axis(const double2* __restrict__ in, double2* __restrict__
 
 // P[o, b] = scale (Re Y[o,0] + sum_{k=1}^{H-1} c_k Re(Y[o,k] tw[(k b) mod R])),
 // c_k = 2, except c = 1 for the self-conjugate k = R/2 when R is even.
+struct DiagAcc {
+  double sum, im, mn, bad;
+};
+
 __device__ __forceinline__ void stage_last_real(const double2* __restrict__ Y, double* __restrict__ P,
                                                 long long outer, int R, int H, int nout, double scale,
-                                                const double2* __restrict__ tw, long long t0, long long stride) {
+                                                const double2* __restrict__ tw, long long t0, long long stride,
+                                                DiagAcc* acc_out = nullptr) {
   const long long total = outer * nout;
   for (long long t = t0; t < total; t += stride) {
     int b = (int)(t % nout);
     long long o = t / nout;
     const double2* row = Y + o * H;
+    if (acc_out && b == 0) {                          // the row's self-conjugate entries
+      acc_out->im = fmax(acc_out->im, fabs(row[0].y));
+      if ((R & 1) == 0) acc_out->im = fmax(acc_out->im, fabs(row[H - 1].y));
+    }
     double acc = row[0].x;
     int idx = b;
     if (idx >= R) idx -= R;
@@ -147,6 +156,38 @@ __device__ __forceinline__ void stage_last_real(const double2* __restrict__ Y, d
       if (idx >= R) idx -= R;
     }
     P[t] = acc * scale;
+    if (acc_out) acc_out->sum += acc * scale;
+  }
+}
+
+// Block reduction of the per-thread diagnostics into partial vb (the whole CTA calls it).
+__device__ __forceinline__ void block_diag(DiagAcc a, double* __restrict__ part, int vb) {
+  __shared__ double s_d[4][32];
+  for (int o = 16; o > 0; o >>= 1) {
+    a.sum += __shfl_xor_sync(0xffffffffu, a.sum, o);
+    a.im = fmax(a.im, __shfl_xor_sync(0xffffffffu, a.im, o));
+    a.mn = fmin(a.mn, __shfl_xor_sync(0xffffffffu, a.mn, o));
+    a.bad += __shfl_xor_sync(0xffffffffu, a.bad, o);
+  }
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    s_d[0][w] = a.sum;
+    s_d[1][w] = a.im;
+    s_d[2][w] = a.mn;
+    s_d[3][w] = a.bad;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int i = 1; i < (int)(blockDim.x >> 5); ++i) {
+      a.sum += s_d[0][i];
+      a.im = fmax(a.im, s_d[1][i]);
+      a.mn = fmin(a.mn, s_d[2][i]);
+      a.bad += s_d[3][i];
+    }
+    part[4 * vb] = a.sum;
+    part[4 * vb + 1] = a.im;
+    part[4 * vb + 2] = a.mn;
+    part[4 * vb + 3] = a.bad;
   }
 }
 
@@ -208,7 +249,10 @@ __device__ __forceinline__ void stage_diag(const double* __restrict__ P, long lo
     out[1] = im;
     out[2] = mn;
     out[3] = bad;
-    if (vb == 0) part[4 * nvb] = logq ? logq[0].x : 0.0;
+    if (vb == 0) {
+      part[4 * GBSBIN_DIAG_SLOTS] = logq ? logq[0].x : 0.0;
+      part[4 * GBSBIN_DIAG_SLOTS + 2] = (double)nvb;
+    }
   }
 }
 
@@ -292,14 +336,25 @@ __global__ void __launch_bounds__(128) k_dft_fused(DftFused f) {
     nxt = t;
   }
   if (f.naxes > 0 || first) grid_barrier(f.bar);
-  stage_last_real(cur, a.P, f.last_outer, f.last_R, f.H, f.last_nout, f.scale, a.tw + f.last_twoff, t0, stride);
+  // the diagnostics ride along: every CTA reduces what its threads wrote or read into its
+  // own partial (no barrier after the last stage)
+  DiagAcc acc{0.0, 0.0, 1.0e300, 0.0};
+  stage_last_real(cur, a.P, f.last_outer, f.last_R, f.H, f.last_nout, f.scale, a.tw + f.last_twoff, t0, stride,
+                  a.diag ? &acc : nullptr);
   if (a.diag) {
-    grid_barrier(f.bar);
-    if ((int)blockIdx.x < GBSBIN_DIAG_BLOCKS)
-      stage_diag(a.P, a.table_size, cur, f.last_outer, f.H, f.last_R, a.minpiv,
-                 a.g_ready ? nullptr : a.ldfin ? a.logq_fin : a.logq,
-                 a.grid.n_eval, a.diag, blockIdx.x, GBSBIN_DIAG_BLOCKS);
-    if (t0 == 0) a.diag[4 * GBSBIN_DIAG_BLOCKS + 1] = (double)*(volatile unsigned*)(f.bar + 2);
+    const double2* lq = a.g_ready ? nullptr : a.ldfin ? a.logq_fin : a.logq;
+    for (long long e = t0; a.minpiv && e < a.grid.n_eval; e += stride) {
+      const double m = a.minpiv[e];
+      const double2 l = lq ? lq[e] : make_double2(0.0, 0.0);
+      if (!((m > 0.0) && isfinite(l.x) && isfinite(l.y))) acc.bad += 1.0;
+      acc.mn = fmin(acc.mn, m);
+    }
+    block_diag(acc, a.diag, blockIdx.x);
+    if (t0 == 0) {
+      a.diag[4 * GBSBIN_DIAG_SLOTS] = lq ? lq[0].x : 0.0;
+      a.diag[4 * GBSBIN_DIAG_SLOTS + 1] = (double)*(volatile unsigned*)(f.bar + 2);
+      a.diag[4 * GBSBIN_DIAG_SLOTS + 2] = (double)gridDim.x;
+    }
   }
 }
 
@@ -406,6 +461,7 @@ cudaError_t launch_dft_fused(const DftArgs& a, unsigned* bar, int num_sms, cudaS
   long long blocks = (items + 127) / 128;
   if (blocks > (long long)per_sm * num_sms) blocks = (long long)per_sm * num_sms;
   if (blocks < GBSBIN_DIAG_BLOCKS) blocks = GBSBIN_DIAG_BLOCKS;
+  if (blocks > GBSBIN_DIAG_SLOTS) blocks = GBSBIN_DIAG_SLOTS;
   if (blocks > (long long)per_sm * num_sms) return cudaErrorInvalidConfiguration;
   void* params[] = {&f};
   return cudaLaunchCooperativeKernel((const void*)k_dft_fused, dim3((unsigned)blocks), dim3(128), params, 0, s);

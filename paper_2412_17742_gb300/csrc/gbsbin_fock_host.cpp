@@ -269,7 +269,7 @@ int gbsbin_fock_plan_create(const gbsbin_fock_problem* p, const gbsbin_options* 
       (st = dalloc(&P->d_xtw_df, (size_t)xoff)) || (st = dalloc(&P->d_zr, (size_t)a.rsum)) ||
       (st = dalloc(&P->d_zr_df, (size_t)a.rsum)) || (st = dalloc(&P->d_tw, (size_t)a.rsum)) ||
       (st = dalloc(&P->d_parts, (size_t)xr * g.n_full)) || (st = dalloc(&P->d_bufA, (size_t)g.n_full)) ||
-      (st = dalloc(&P->d_bufB, (size_t)g.n_full)) || (st = dalloc(&P->d_diag, 4 * GBSBIN_DIAG_BLOCKS + 2)) ||
+      (st = dalloc(&P->d_bufB, (size_t)g.n_full)) || (st = dalloc(&P->d_diag, GBSBIN_DIAG_DOUBLES)) ||
       (st = dalloc(&P->d_bar, 4)) || (st = dalloc(&P->d_table, (size_t)P->table_size))) {
     free_all(P);
     delete P;
@@ -322,7 +322,7 @@ int gbsbin_fock_plan_create(const gbsbin_fock_problem* p, const gbsbin_options* 
         cudaMemcpy(P->d_tw, tw.data(), tw.size() * sizeof(double2), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(P->d_state, P->h_stage, P->state_bytes, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemset(P->d_bar, 0, 4 * sizeof(unsigned)) != cudaSuccess ||
-        cudaMemset(P->d_diag, 0, (4 * GBSBIN_DIAG_BLOCKS + 2) * sizeof(double)) != cudaSuccess) {
+        cudaMemset(P->d_diag, 0, GBSBIN_DIAG_DOUBLES * sizeof(double)) != cudaSuccess) {
       cudaGetLastError();
       st = GBSBIN_ERR_CUDA;
     }
@@ -384,13 +384,15 @@ int gbsbin_fock_execute_host(gbsbin_fock_plan* P, double* P_out_host, void* stre
 
 int gbsbin_fock_diagnostics(gbsbin_fock_plan* P, gbsbin_diag* out, void* stream) {
   if (!P || !out) return GBSBIN_ERR_ARG;
-  double part[4 * GBSBIN_DIAG_BLOCKS + 2] = {0};
+  std::vector<double> part(GBSBIN_DIAG_DOUBLES, 0.0);
   double sum = 0.0, im = 0.0;
   if (P->opt.want_diagnostics) {
-    if (cudaMemcpyAsync(part, P->d_diag, sizeof(part), cudaMemcpyDeviceToHost, (cudaStream_t)stream) != cudaSuccess ||
+    if (cudaMemcpyAsync(part.data(), P->d_diag, part.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                        (cudaStream_t)stream) != cudaSuccess ||
         cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess)
       return GBSBIN_ERR_CUDA;
-    for (int b = 0; b < GBSBIN_DIAG_BLOCKS; ++b) {   // fixed order: deterministic
+    const int nblk = std::min(GBSBIN_DIAG_SLOTS, std::max(0, (int)part[4 * GBSBIN_DIAG_SLOTS + 2]));
+    for (int b = 0; b < nblk; ++b) {   // fixed order: deterministic
       sum += part[4 * b];
       im = std::fmax(im, part[4 * b + 1]);
     }
@@ -414,7 +416,7 @@ int gbsbin_fock_diagnostics(gbsbin_fock_plan* P, gbsbin_diag* out, void* stream)
     }
     out->point_kernel_ms = ms;
   }
-  if (P->opt.want_diagnostics && part[4 * GBSBIN_DIAG_BLOCKS + 1] != 0.0) return GBSBIN_ERR_CUDA;
+  if (P->opt.want_diagnostics && part[4 * GBSBIN_DIAG_SLOTS + 1] != 0.0) return GBSBIN_ERR_CUDA;
   if (P->opt.want_diagnostics && !(std::isfinite(sum))) return GBSBIN_ERR_NUMERIC;
   return GBSBIN_OK;
 }

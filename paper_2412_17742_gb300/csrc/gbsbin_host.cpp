@@ -763,7 +763,7 @@ static int plan_create_impl(const gbsbin_problem* p, const gbsbin_options* o, gb
   (void)nn;
   if ((st = dalloc(&P->d_state, sl.total)) || (st = dalloc(&P->d_label, n)) || (st = dalloc(&P->d_logq, g.n_eval)) ||
       (st = dalloc(&P->d_minpiv, g.n_eval)) || (st = dalloc(&P->d_bufA, g.n_full)) ||
-      (st = dalloc(&P->d_bufB, g.n_full)) || (st = dalloc(&P->d_diag, 4 * GBSBIN_DIAG_BLOCKS + 2)) ||
+      (st = dalloc(&P->d_bufB, g.n_full)) || (st = dalloc(&P->d_diag, GBSBIN_DIAG_DOUBLES)) ||
       (st = dalloc(&P->d_bar, 4)) ||
       (st = dalloc(&P->d_table, (size_t)P->table_size))) {
     free_device(P);
@@ -781,7 +781,7 @@ static int plan_create_impl(const gbsbin_problem* p, const gbsbin_options* o, gb
   P->d_g_lo = (float2*)(P->d_state + sl.off_glo);
   P->d_NXA_fix = (longlong2*)(P->d_state + sl.off_XAfix);
   if (cudaMemset(P->d_bar, 0, 4 * sizeof(unsigned)) != cudaSuccess ||
-      cudaMemset(P->d_diag, 0, (4 * GBSBIN_DIAG_BLOCKS + 2) * sizeof(double)) != cudaSuccess) {
+      cudaMemset(P->d_diag, 0, GBSBIN_DIAG_DOUBLES * sizeof(double)) != cudaSuccess) {
     free_device(P);
     delete P;
     return GBSBIN_ERR_CUDA;
@@ -1011,19 +1011,21 @@ int gbsbin_execute_host(gbsbin_plan* P, double* P_out_host, void* stream) {
 
 int gbsbin_diagnostics(gbsbin_plan* P, gbsbin_diag* out, void* stream) {
   if (!P || !out) return GBSBIN_ERR_ARG;
-  double part[4 * GBSBIN_DIAG_BLOCKS + 2] = {0};
+  std::vector<double> part(GBSBIN_DIAG_DOUBLES, 0.0);
   double h[5] = {0.0, 0.0, 1.0e300, 0.0, 0.0};
   if (P->opt.want_diagnostics) {
-    if (cudaMemcpyAsync(part, P->d_diag, sizeof(part), cudaMemcpyDeviceToHost, (cudaStream_t)stream) != cudaSuccess ||
+    if (cudaMemcpyAsync(part.data(), P->d_diag, part.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                        (cudaStream_t)stream) != cudaSuccess ||
         cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess)
       return GBSBIN_ERR_CUDA;
-    for (int b = 0; b < GBSBIN_DIAG_BLOCKS; ++b) {  // fixed order: deterministic
+    const int nblk = std::min(GBSBIN_DIAG_SLOTS, std::max(0, (int)part[4 * GBSBIN_DIAG_SLOTS + 2]));
+    for (int b = 0; b < nblk; ++b) {  // fixed order: deterministic
       h[0] += part[4 * b];
       h[1] = std::fmax(h[1], part[4 * b + 1]);
       h[2] = std::fmin(h[2], part[4 * b + 2]);
       h[3] += part[4 * b + 3];
     }
-    h[4] = part[4 * GBSBIN_DIAG_BLOCKS];
+    h[4] = part[4 * GBSBIN_DIAG_SLOTS];
   }
   out->sum_P = h[0];
   out->max_imag = h[1];
@@ -1045,7 +1047,7 @@ int gbsbin_diagnostics(gbsbin_plan* P, gbsbin_diag* out, void* stream) {
     out->point_kernel_ms = ms;
   }
   if (!P->opt.want_diagnostics) return GBSBIN_OK;
-  if (part[4 * GBSBIN_DIAG_BLOCKS + 1] != 0.0) return GBSBIN_ERR_CUDA;   // a grid barrier gave up waiting
+  if (part[4 * GBSBIN_DIAG_SLOTS + 1] != 0.0) return GBSBIN_ERR_CUDA;   // a grid barrier gave up waiting
   return out->n_bad_points > 0 ? GBSBIN_ERR_NUMERIC : GBSBIN_OK;
 }
 

@@ -10,8 +10,13 @@
 // Largest n whose n x n complex matrix (and, for the FP32 path, its residual) fits in
 // one CTA's shared memory next to the small vectors.
 #define GBSBIN_SMEM_MAX_N 112
-// Blocks of the diagnostics reduction; the host finishes the sum over their partials.
+// Blocks of the diagnostics reduction of the multi-launch DFT; the host finishes the sum
+// over the partials.  The diagnostics array holds GBSBIN_DIAG_SLOTS partials of 4 doubles
+// (sum of P, max |Im| of the self-conjugate entries, min pivot real part, bad points), then
+// Re log q(1), the grid-barrier error flag and the number of partials written.
 #define GBSBIN_DIAG_BLOCKS 64
+#define GBSBIN_DIAG_SLOTS 1024
+#define GBSBIN_DIAG_DOUBLES (4 * GBSBIN_DIAG_SLOTS + 4)
 // Fixed-point scale of the integer copy of -XA used by the exact integer residual.
 #define GBSBIN_FIX_BITS 62
 
@@ -112,7 +117,7 @@ struct DftArgs {
   double2* bufA;            // n_eval complex scratch
   double2* bufB;            // n_eval complex scratch
   double* P;                // table out (prod nout doubles)
-  double* diag;             // 4 GBSBIN_DIAG_BLOCKS + 1 partial reductions, or nullptr
+  double* diag;             // GBSBIN_DIAG_DOUBLES: partial reductions (see above), or nullptr
   const double* minpiv;     // n_eval
   long long table_size;
 };
@@ -205,7 +210,7 @@ cudaError_t launch_dft(const DftArgs& a, cudaStream_t s);
 // directly and did not finish them.
 cudaError_t launch_finish_logq(const double* ldfin, double2* logq, long long n, cudaStream_t s);
 // All DFT stages and the diagnostics in one cooperative launch; bar: 4 zeroed unsigned ints
-// of grid-barrier state owned by the caller; needs diag to hold 4 GBSBIN_DIAG_BLOCKS + 2.
+// of grid-barrier state owned by the caller; diag (if any) holds GBSBIN_DIAG_DOUBLES.
 cudaError_t launch_dft_fused(const DftArgs& a, unsigned* bar, int num_sms, cudaStream_t s);
 cudaError_t launch_backward(const BackwardArgs& b, const double* dLdP, cudaStream_t s);
 cudaError_t launch_alu_peak(int fp64, int blocks, float* out_sink, int iters, cudaStream_t s);
