@@ -327,6 +327,22 @@ int gbsbin_batch_destroy(gbsbin_batch* b);
  * Errors: ERR_ARG / ERR_PARTITION / ERR_NONPHYSICAL as for gbsbin_plan_create.
  */
 int gbsbin_moments(const gbsbin_problem* p, double* mean, double* cov);
+/*
+ * Exact third cumulants of the binned counts (Sec. VI, coarse-grained moments and
+ * cumulants): kappa_lmn = third derivative of log G(e^t) at t = 0.  With e_l = e^{t_l} - 1,
+ * log G = sum_l c_l e_l + sum_lm a_lm e_l e_m + sum_lmn b_lmn e_l e_m e_n + O(e^4), where
+ * (R, W, u, v as for gbsbin_moments; i in l means row i belongs to group l)
+ *   c_l   = 1/2 sum_{i in l} (W_ii + v_i u_i)
+ *   a_lm  = sum_{i in l, j in m} (1/4 W_ij W_ji + 1/2 v_i W_ij u_j)
+ *   b_lmn = sum_{i in l, j in m, k in n} (1/6 W_ij W_jk W_ki + 1/2 v_i W_ij W_jk u_k),
+ * from -1/2 log det(I - D XA) = const + 1/2 sum_k tr((E W)^k) / k and the exponent's
+ * Neumann series, E = diag(e_label(i)).  Then
+ *   kappa_lmn = sum over the 6 orders of (l, m, n) of b
+ *               + d_lm Q_ln + d_ln Q_lm + d_mn Q_ml + d_lm d_mn c_l,   Q = a + a^T.
+ * Unfolded (no cutoff enters).  Host only, FP64, O(n^3); k3: L x L x L doubles, row-major,
+ * caller-owned host memory.  Errors: as gbsbin_moments.
+ */
+int gbsbin_cumulants3(const gbsbin_problem* p, double* k3);
 
 /*
  * Fock inputs through a lossy linear circuit (App. C of the paper).  photons[j] >= 0

@@ -1236,24 +1236,31 @@ static bool invert(std::vector<cd>& A, int n) {
   return true;
 }
 
-int gbsbin_moments(const gbsbin_problem* p, double* mean, double* cov) {
-  if (!p || !mean || !cov) return GBSBIN_ERR_ARG;
+}  // extern "C"
+
+// The algebra both moment calls share (Sec. VI, coarse-grained moments and cumulants):
+// R = (I - XA)^{-1}, W = XA R, u = R X gamma, v = R^T gamma and the group label of each
+// row of the state.
+static int moment_algebra(const gbsbin_problem* p, int& n, std::vector<int>& lab, std::vector<cd>& W,
+                          std::vector<cd>& u, std::vector<cd>& v) {
   gbsbin_options o;
   gbsbin_default_options(&o);
   int st = validate_shape(p, &o);
   if (st) return st;
-  const int MK = p->M * p->K, n = 2 * MK, L = p->L;
+  const int MK = p->M * p->K;
+  n = 2 * MK;
   std::vector<cd> C, gamma, Xgamma;
   int has_gamma = 0;
   if ((st = build_state(p, n, C, gamma, Xgamma, &has_gamma))) return st;
-  std::vector<int> lab(n);
+  lab.assign(n, 0);
   for (int q = 0; q < MK; ++q) lab[q] = lab[MK + q] = p->bin_of_mode[q / p->K];
-  // R = (I - XA)^{-1}, W = XA R, u = R X gamma, v = R^T gamma
   std::vector<cd> R((size_t)n * n);
   for (int i = 0; i < n; ++i)
     for (int j = 0; j < n; ++j) R[(size_t)i * n + j] = (i == j ? 1.0 : 0.0) - C[(size_t)i * n + j];
   if (!invert(R, n)) return GBSBIN_ERR_NONPHYSICAL;
-  std::vector<cd> W((size_t)n * n, 0.0), u(n, 0.0), v(n, 0.0);
+  W.assign((size_t)n * n, 0.0);
+  u.assign(n, 0.0);
+  v.assign(n, 0.0);
   for (int i = 0; i < n; ++i)
     for (int k = 0; k < n; ++k) {
       const cd c = C[(size_t)i * n + k];
@@ -1267,6 +1274,19 @@ int gbsbin_moments(const gbsbin_problem* p, double* mean, double* cov) {
       u[i] += R[(size_t)i * n + k] * Xgamma[k];
       v[i] += R[(size_t)k * n + i] * gamma[k];
     }
+  return GBSBIN_OK;
+}
+
+extern "C" {
+
+int gbsbin_moments(const gbsbin_problem* p, double* mean, double* cov) {
+  if (!p || !mean || !cov) return GBSBIN_ERR_ARG;
+  int n = 0;
+  std::vector<int> lab;
+  std::vector<cd> W, u, v;
+  int st = moment_algebra(p, n, lab, W, u, v);
+  if (st) return st;
+  const int L = p->L;
   // mean_l = 1/2 sum_{i in l} (v_i u_i + W_ii)
   std::vector<cd> mu(L, 0.0), s(L * L, 0.0);
   for (int i = 0; i < n; ++i) mu[lab[i]] += 0.5 * (v[i] * u[i] + W[(size_t)i * n + i]);
@@ -1284,6 +1304,63 @@ int gbsbin_moments(const gbsbin_problem* p, double* mean, double* cov) {
   for (int i = 0; i < n; ++i) s[lab[i] * L + lab[i]] += 0.5 * (v[i] * u[i] + W[(size_t)i * n + i]);
   for (int l = 0; l < L; ++l) mean[l] = mu[l].real();
   for (int q = 0; q < L * L; ++q) cov[q] = s[q].real();
+  return GBSBIN_OK;
+}
+
+int gbsbin_cumulants3(const gbsbin_problem* p, double* k3) {
+  if (!p || !k3) return GBSBIN_ERR_ARG;
+  int n = 0;
+  std::vector<int> lab;
+  std::vector<cd> W, u, v;
+  int st = moment_algebra(p, n, lab, W, u, v);
+  if (st) return st;
+  const int L = p->L;
+  // log G(e^t) in e_l = e^{t_l} - 1: sum_l c1_l e_l + sum_lm a_lm e_l e_m + sum_lmn b_lmn e_l e_m e_n
+  std::vector<cd> c1(L, 0.0), a((size_t)L * L, 0.0), b((size_t)L * L * L, 0.0);
+  for (int i = 0; i < n; ++i) c1[lab[i]] += 0.5 * (W[(size_t)i * n + i] + v[i] * u[i]);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j)
+      a[(size_t)lab[i] * L + lab[j]] +=
+          0.25 * W[(size_t)i * n + j] * W[(size_t)j * n + i] + 0.5 * v[i] * W[(size_t)i * n + j] * u[j];
+  // b_lmn = 1/6 sum_{i in l, j in m, k in n} W_ij W_jk W_ki + 1/2 sum v_i W_ij W_jk u_k; the second
+  // sum is sum_{j in m} x^(l)_j y^(n)_j with x^(l)_j = sum_{i in l} v_i W_ij, y^(n)_j = sum_{k in n} W_jk u_k
+  std::vector<cd> Wt((size_t)n * n), acc(L);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) Wt[(size_t)j * n + i] = W[(size_t)i * n + j];
+  for (int i = 0; i < n; ++i) {
+    const cd* wcol_i = &Wt[(size_t)i * n];          // W_ki over k
+    for (int j = 0; j < n; ++j) {
+      const cd* wrow_j = &W[(size_t)j * n];         // W_jk over k
+      std::fill(acc.begin(), acc.end(), cd(0.0));
+      for (int k = 0; k < n; ++k) acc[lab[k]] += wrow_j[k] * wcol_i[k];
+      const cd wij = W[(size_t)i * n + j] / 6.0;
+      cd* brow = &b[((size_t)lab[i] * L + lab[j]) * L];
+      for (int l = 0; l < L; ++l) brow[l] += wij * acc[l];
+    }
+  }
+  std::vector<cd> x((size_t)L * n, 0.0), y((size_t)L * n, 0.0);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      x[(size_t)lab[i] * n + j] += v[i] * W[(size_t)i * n + j];
+      y[(size_t)lab[j] * n + i] += W[(size_t)i * n + j] * u[j];
+    }
+  for (int l = 0; l < L; ++l)
+    for (int j = 0; j < n; ++j)
+      for (int m = 0; m < L; ++m) b[((size_t)l * L + lab[j]) * L + m] += 0.5 * x[(size_t)l * n + j] * y[(size_t)m * n + j];
+  // kappa_lmn = sum over the 6 orders of (l, m, n) of b + the chain-rule terms of e(t):
+  // d_lm Q_ln + d_ln Q_lm + d_mn Q_ml + d_lm d_mn c1_l, Q = a + a^T
+  auto B = [&](int i, int j, int k) { return b[((size_t)i * L + j) * L + k]; };
+  auto Q = [&](int i, int j) { return a[(size_t)i * L + j] + a[(size_t)j * L + i]; };
+  for (int l = 0; l < L; ++l)
+    for (int m = 0; m < L; ++m)
+      for (int q = 0; q < L; ++q) {
+        cd kap = B(l, m, q) + B(l, q, m) + B(m, l, q) + B(m, q, l) + B(q, l, m) + B(q, m, l);
+        if (l == m) kap += Q(l, q);
+        if (l == q) kap += Q(l, m);
+        if (m == q) kap += Q(m, l);
+        if (l == m && m == q) kap += c1[l];
+        k3[((size_t)l * L + m) * L + q] = kap.real();
+      }
   return GBSBIN_OK;
 }
 

@@ -75,3 +75,35 @@ def test_rejects_bad_input(gb):
     bad.bin_of_mode = np.array([0, 0, 0, 0], np.int32)
     with pytest.raises(gb.GbsbinError):
         gb.gbsbin_moments(bad)
+
+
+# ------------------------------------------------------------------ third cumulants
+def test_third_cumulant_single_modes(gb):
+    # squeezed vacuum: log G(e^t) = -1/2 log(cosh^2 r - e^{2t} sinh^2 r), whose third
+    # derivative at 0 is 4 s + 12 s^2 + 8 s^3 with s = sinh^2 r; coherent state: Poisson
+    # (every cumulant is the mean)
+    r = 0.6
+    s = np.sinh(r) ** 2
+    k3 = gb.gbsbin_cumulants3(_one_mode(r))
+    assert abs(k3[0, 0, 0] - (4 * s + 12 * s * s + 8 * s ** 3)) < 1e-12
+    a = 0.7 + 0.5j
+    k3 = gb.gbsbin_cumulants3(_one_mode(0.0, a))
+    assert abs(k3[0, 0, 0] - abs(a) ** 2) < 1e-13
+
+
+@pytest.mark.parametrize("M,K,L,cut,disp,basis", [(4, 1, 2, 6, True, False), (3, 2, 2, 5, False, True),
+                                                  (3, 1, 3, 4, True, False)])
+def test_third_cumulants_against_unfolded_tables(gb, M, K, L, cut, disp, basis):
+    # third cumulants are the third central moments of the unfolded table
+    rng = np.random.default_rng(950 + M + K + L)
+    prob = synth.random_problem(rng, M, K, L, cut, displaced=disp, internal_basis=basis, r_range=(0.1, 0.45))
+    k3 = gb.gbsbin_cumulants3(prob)
+    P = oracle.binned(prob, radix=prob.radix * (12 if L <= 2 else 8))["P"]
+    grids = np.meshgrid(*[np.arange(sz) for sz in P.shape], indexing="ij")
+    mu = [(P * g).sum() for g in grids]
+    d = [g - m for g, m in zip(grids, mu)]
+    ref = np.array([[[(P * d[i] * d[j] * d[k]).sum() for k in range(L)] for j in range(L)] for i in range(L)])
+    assert np.abs(k3 - ref).max() < 1e-8, np.abs(k3 - ref).max()
+    # symmetric in its three indices
+    for perm in [(0, 2, 1), (1, 0, 2), (2, 1, 0)]:
+        assert np.abs(k3 - k3.transpose(perm)).max() < 1e-12
