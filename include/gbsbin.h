@@ -362,7 +362,18 @@ int gbsbin_cumulants3(const gbsbin_problem* p, double* k3);
  * points, each factor O(L).  Options: precision GBSBIN_FP64 (kernel 9) or
  * GBSBIN_FP32_REFINE, which here selects pairs of FP32 (kernel 10); oversample,
  * want_diagnostics, want_timing and tile_override (9 or 10) as for gbsbin_plan_create;
- * want_backward and shards are not supported (ERR_UNSUPPORTED).
+ * want_backward is not supported (ERR_UNSUPPORTED).  shard_begin/shard_end select a range
+ * [begin, end) of the input nodes in the order the kernel walks them: node i has digits
+ * g_d (one per occupied input other than the held one, which is the occupied input with the
+ * fewest photons, lowest port on ties; the others in port order, the first the fastest)
+ * given by the reflected mixed-radix Gray code: with n_d = floor(i / s_d) mod R_d,
+ * s_d = prod_{d' < d} R_d', R_d = p + 1, g_d = n_d if floor(i / s_{d+1}) is even, else
+ * R_d - 1 - n_d.  gbsbin_fock_plan_nodes gives the count.  The plan then returns the
+ * PARTIAL table of those nodes' share G_p of G (normalised by the whole node count) in the
+ * half-grid form every plan's inverse DFT takes - last axis k <= R/2 only, weight 1 at
+ * k = 0 (and R/2 for even R) and 2 elsewhere, real part - exact for the whole G, whose
+ * conjugate symmetry a share lacks: the tables of shards that partition [0, nodes) sum to
+ * the whole table, and one shard's table alone is not a distribution.
  * Limits: at most GBSBIN_FOCK_MAX_INPUTS occupied inputs, GBSBIN_FOCK_MAX_PER_INPUT photons
  * in one input, GBSBIN_FOCK_MAX_GROUPS groups, GBSBIN_FOCK_MAX_NODES nodes, the output grid as for Gaussian states (ERR_UNSUPPORTED /
  * ERR_CUTOFF).  ERR_NONPHYSICAL if ||T||_2 > 1.  All arrays are host memory read during
@@ -388,6 +399,9 @@ int gbsbin_fock_plan_create(const gbsbin_fock_problem* p, const gbsbin_options* 
  * upload enqueued on `stream`.  ERR_ARG / ERR_NONPHYSICAL as for plan creation. */
 int gbsbin_fock_plan_set_transfer(gbsbin_fock_plan* plan, const gbsbin_complex* T, void* stream);
 long long gbsbin_fock_plan_table_size(const gbsbin_fock_plan* plan);
+/* Input nodes of the whole problem, prod over the occupied inputs but the held one of
+ * (p_k + 1); -1 if plan is NULL. */
+long long gbsbin_fock_plan_nodes(const gbsbin_fock_plan* plan);
 /* Table to P_out (device, table_size doubles, last group fastest); asynchronous. */
 int gbsbin_fock_execute(gbsbin_fock_plan* plan, double* P_out, void* stream);
 /* The same into host memory; synchronises `stream`. */

@@ -34,7 +34,9 @@ generating function of App. C's diagonal elements):
   no other monomial aliases onto x^p; the weight x^{-p} equals prod_k x_k on these nodes.
 * ``table`` - G on the roots-of-unity grid of the output groups by ``pgf_extract``, then the
   inverse DFT of :func:`oracle.dft` (Sec. VI, Eq. coarse_grained_prob): the folded table,
-  exact (unfolded) when every N_l >= N.
+  exact (unfolded) when every N_l >= N.  For a range of the input nodes (in the reflected
+  mixed-radix Gray order of ``gray_digits``) the partial table of their share of G, in the
+  half-grid form of the DFT (see ``table``).
 
 Pinned by ``tests/test_fock_oracle.py``: brute force through the Hafnian definition, the
 two independent generating-function routes against each other, and closed forms (Hong-Ou-
@@ -186,8 +188,54 @@ def extraction_nodes(photons):
     return J, k0, others, np.array(X, dtype=np.complex128), np.array(W, dtype=np.complex128)
 
 
-def pgf_extract(fp, z, nodes=None) -> complex:
-    """G(z) = [x^p] prod_j (B(z) x)_j^{p_j} by the roots-of-unity nodes (mean over them)."""
+def gray_digits(index: int, radices):
+    """Digits of node ``index`` in the reflected mixed-radix Gray code over ``radices``
+    (first digit fastest): n_d = floor(index / s_d) mod R_d, reflected (R_d - 1 - n_d) when
+    floor(index / s_{d+1}) is odd, s_d = prod_{d' < d} R_d'."""
+    g, stride = [], 1
+    for R in radices:
+        n = (index // stride) % R
+        g.append(n if (index // (stride * R)) % 2 == 0 else R - 1 - n)
+        stride *= R
+    return g
+
+
+def extraction_nodes_range(photons, begin: int, end: int):
+    """As extraction_nodes, for the nodes [begin, end) in Gray-code order: the held input is
+    the occupied one with the fewest photons (lowest port on ties), the digits run over the
+    other occupied inputs in port order."""
+    p = np.asarray(photons)
+    J = [j for j in range(len(p)) if p[j] > 0]
+    if not J:
+        return J, None, [], np.zeros((1, 0), dtype=np.complex128), np.ones(1, dtype=np.complex128)
+    k0 = min(J, key=lambda j: (p[j], j))
+    others = [j for j in J if j != k0]
+    radices = [int(p[j]) + 1 for j in others]
+    X, W = [], []
+    for i in range(begin, end):
+        g = gray_digits(i, radices)
+        x = {k0: 1.0 + 0j}
+        w = 1.0 + 0j
+        for j, gj, R in zip(others, g, radices):
+            x[j] = np.exp(2j * np.pi * gj / R)
+            w *= x[j]
+        X.append([x[j] for j in J])
+        W.append(w)
+    return J, k0, others, np.array(X, dtype=np.complex128).reshape(len(X), len(J)), np.array(W, dtype=np.complex128)
+
+
+def node_count(photons) -> int:
+    p = np.asarray(photons)
+    J = [j for j in range(len(p)) if p[j] > 0]
+    if not J:
+        return 1
+    k0 = min(J, key=lambda j: (p[j], j))
+    return int(np.prod([int(p[j]) + 1 for j in J if j != k0]))
+
+
+def pgf_extract(fp, z, nodes=None, total=None) -> complex:
+    """G(z) = [x^p] prod_j (B(z) x)_j^{p_j} by the roots-of-unity nodes (mean over them); with
+    a subset of the nodes and ``total`` = the whole node count, that subset's share."""
     J, _, _, X, W = nodes if nodes is not None else extraction_nodes(fp.photons)
     if not J:
         return 1.0 + 0j
@@ -195,25 +243,45 @@ def pgf_extract(fp, z, nodes=None) -> complex:
     s = X @ B.T                                               # s[node, j] = (B x)_j
     pw = np.asarray(fp.photons)[J]
     F = np.prod(s ** pw[None, :], axis=1)
-    return complex(np.mean(W * F))
+    return complex(np.sum(W * F) / (total if total else len(W)))
 
 
-def pgf_grid(fp, radix=None) -> np.ndarray:
-    """G(omega^k) on the roots-of-unity grid of the output groups (default N_l + 1)."""
+def pgf_grid(fp, radix=None, node_range=None) -> np.ndarray:
+    """G(omega^k) on the roots-of-unity grid of the output groups (default N_l + 1); with
+    node_range = (begin, end), only those nodes' share (Gray-code order)."""
     radix = fp.radix if radix is None else np.asarray(radix)
-    nodes = extraction_nodes(fp.photons)
+    total = None
+    if node_range is None:
+        nodes = extraction_nodes(fp.photons)
+    else:
+        nodes = extraction_nodes_range(fp.photons, *node_range)
+        total = node_count(fp.photons)
     G = np.empty(tuple(int(r) for r in radix), dtype=np.complex128)
     for k in itertools.product(*[range(int(r)) for r in radix]):
         z = [np.exp(2j * np.pi * kl / int(r)) for kl, r in zip(k, radix)]
-        G[k] = pgf_extract(fp, z, nodes)
+        G[k] = pgf_extract(fp, z, nodes, total)
     return G
 
 
-def table(fp, oversample: int = 1) -> dict:
-    """Folded table P~(b), 0 <= b_l <= N_l, on the grid oversample (N_l + 1) per axis."""
+def table(fp, oversample: int = 1, node_range=None) -> dict:
+    """Folded table P~(b), 0 <= b_l <= N_l, on the grid oversample (N_l + 1) per axis.
+
+    With node_range = (begin, end): the partial table of those nodes' share G_p of G, in the
+    half-grid form of the inverse DFT - the last axis k <= R/2 only, weight 1 at k = 0 (and
+    k = R/2 for even R) and 2 elsewhere, real part - which is exact for the whole G
+    (G(-k) = conj G(k)); a node range's share alone has no such symmetry, so this is the
+    form whose shares sum to the whole table over a partition of the nodes."""
     from . import dft
     radix = fp.radix * int(oversample)
-    G = pgf_grid(fp, radix)
+    G = pgf_grid(fp, radix, node_range)
+    if node_range is not None:
+        R = int(radix[-1])
+        c = np.zeros(R)
+        c[:R // 2 + 1] = 2.0
+        c[0] = 1.0
+        if R % 2 == 0:
+            c[R // 2] = 1.0
+        G = G * c
     Pc = dft(G, radix)
     sl = tuple(slice(0, int(c) + 1) for c in fp.cutoff)
     return {"P": Pc.real[sl].copy(), "imag_max": float(np.abs(Pc.imag).max()), "G": G}

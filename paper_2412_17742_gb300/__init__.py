@@ -34,7 +34,7 @@ EXPORTED = ["gbsbin_default_options", "gbsbin_plan_create", "gbsbin_plan_set_sta
             "gbsbin_batch_diagnostics", "gbsbin_batch_read_points", "gbsbin_batch_destroy", "gbsbin_moments",
             "gbsbin_fock_plan_create", "gbsbin_fock_plan_set_transfer", "gbsbin_fock_plan_table_size",
             "gbsbin_fock_execute", "gbsbin_fock_execute_host", "gbsbin_fock_diagnostics",
-            "gbsbin_fock_plan_destroy", "gbsbin_cumulants3"]
+            "gbsbin_fock_plan_destroy", "gbsbin_cumulants3", "gbsbin_fock_plan_nodes"]
 
 
 class GbsbinError(RuntimeError):
@@ -126,6 +126,8 @@ def load():
     lib.gbsbin_fock_plan_set_transfer.argtypes = [vp, _cp, vp]
     lib.gbsbin_fock_plan_table_size.argtypes = [vp]
     lib.gbsbin_fock_plan_table_size.restype = ctypes.c_longlong
+    lib.gbsbin_fock_plan_nodes.argtypes = [vp]
+    lib.gbsbin_fock_plan_nodes.restype = ctypes.c_longlong
     lib.gbsbin_fock_execute.argtypes = [vp, vp, vp]
     lib.gbsbin_fock_execute_host.argtypes = [vp, vp, vp]
     lib.gbsbin_fock_diagnostics.argtypes = [vp, ctypes.POINTER(gbsbin_diag), vp]
@@ -585,10 +587,17 @@ class FockPlan:
     precision GBSBIN_FP64 runs the FP64 kernel, GBSBIN_FP32_REFINE the FP32-pair kernel."""
 
     def __init__(self, prob, precision=GBSBIN_FP64, oversample=1, want_diagnostics=True, tile_override=0,
-                 want_timing=False):
-        self.options = make_options(precision, oversample, want_diagnostics, tile_override, want_timing)
+                 want_timing=False, shard=None):
+        """shard = (begin, end): walk only the input nodes [begin, end) (Gray-code order);
+        table() then returns their partial table."""
+        self.options = make_options(precision, oversample, want_diagnostics, tile_override, want_timing,
+                                    shard=shard)
         self.handle = gbsbin_fock_plan_create(prob, self.options)
         self.shape = tuple(int(c) + 1 for c in prob.cutoff)
+
+    def nodes(self):
+        """Input nodes of the whole problem."""
+        return int(load().gbsbin_fock_plan_nodes(self.handle))
 
     def set_transfer(self, T, stream=None):
         gbsbin_fock_plan_set_transfer(self.handle, T, stream)

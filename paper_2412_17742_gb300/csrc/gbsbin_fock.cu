@@ -115,8 +115,8 @@ __global__ void __launch_bounds__(FT) k_fock(const FockArgs a) {
   int since_flush = 0;
 
   for (long long c = blockIdx.y; c < a.nchunks; c += gridDim.y) {
-    const long long i0 = c * a.chunk;
-    const long long i1 = i0 + a.chunk < a.S ? i0 + a.chunk : a.S;
+    const long long i0 = a.x_lo + c * a.chunk;
+    const long long i1 = i0 + a.chunk < a.x_hi ? i0 + a.chunk : a.x_hi;
     // digit lane d (< nd) of every warp: ordinary digit n, Gray digit g, direction
     int R = 1, n = 0, g = 0, dir = 1;
     if (lane < nd) {

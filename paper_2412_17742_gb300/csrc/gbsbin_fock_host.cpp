@@ -140,7 +140,7 @@ int gbsbin_fock_plan_create(const gbsbin_fock_problem* p, const gbsbin_options* 
   if (opt.tile_override != 0 && opt.tile_override != GBSBIN_KERNEL_FOCK_FP64 &&
       opt.tile_override != GBSBIN_KERNEL_FOCK_DF32)
     return GBSBIN_ERR_ARG;
-  if (opt.want_backward || opt.shard_begin != 0 || opt.shard_end != 0) return GBSBIN_ERR_UNSUPPORTED;
+  if (opt.want_backward) return GBSBIN_ERR_UNSUPPORTED;
   const int M = p->M, L = p->L;
   if (L < 1 || L > M) return GBSBIN_ERR_ARG;
   if (L > GBSBIN_FOCK_MAX_GROUPS) return GBSBIN_ERR_UNSUPPORTED;
@@ -207,6 +207,19 @@ int gbsbin_fock_plan_create(const gbsbin_fock_problem* p, const gbsbin_options* 
     a.dstride[d + 1] = a.dstride[d] * a.drad[d];
   }
   a.S = a.dstride[a.nd];
+  // a shard walks the nodes [shard_begin, shard_end) only; its table is the partial sum of
+  // their terms (normalised by the whole node count), so the shards' tables add up
+  a.x_lo = 0;
+  a.x_hi = a.S;
+  if (opt.shard_end != 0 || opt.shard_begin != 0) {
+    if (opt.shard_begin < 0 || opt.shard_end <= opt.shard_begin || opt.shard_end > a.S) {
+      delete P;
+      return GBSBIN_ERR_ARG;
+    }
+    a.x_lo = opt.shard_begin;
+    a.x_hi = opt.shard_end;
+  }
+  const long long nodes = a.x_hi - a.x_lo;
   // output-group grid, as for Gaussian states
   GridDesc& g = a.grid;
   g.L = L;
@@ -255,11 +268,11 @@ int gbsbin_fock_plan_create(const gbsbin_fock_problem* p, const gbsbin_options* 
   const long long cap = (512LL << 20) / (16 * g.n_full);            // parts <= 512 MB
   if (xr > cap) xr = cap;
   if (xr > 65535) xr = 65535;
-  if (xr > (a.S + 31) / 32) xr = (a.S + 31) / 32;
+  if (xr > (nodes + 31) / 32) xr = (nodes + 31) / 32;
   if (xr < 1) xr = 1;
-  a.chunk = (a.S + xr - 1) / xr;
+  a.chunk = (nodes + xr - 1) / xr;
   if (a.chunk > chunk_max) a.chunk = chunk_max;
-  a.nchunks = (a.S + a.chunk - 1) / a.chunk;
+  a.nchunks = (nodes + a.chunk - 1) / a.chunk;
   if (xr > a.nchunks) xr = a.nchunks;
   a.xr = (int)xr;
   P->coef_count = (size_t)(L + 1) * a.nin * a.nin;
@@ -350,6 +363,8 @@ int gbsbin_fock_plan_set_transfer(gbsbin_fock_plan* P, const gbsbin_complex* T, 
 }
 
 long long gbsbin_fock_plan_table_size(const gbsbin_fock_plan* P) { return P ? P->table_size : -1; }
+
+long long gbsbin_fock_plan_nodes(const gbsbin_fock_plan* P) { return P ? P->args.S : -1; }
 
 int gbsbin_fock_execute(gbsbin_fock_plan* P, double* P_out, void* stream) {
   if (!P || !P_out) return GBSBIN_ERR_ARG;

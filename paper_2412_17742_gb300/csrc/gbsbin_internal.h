@@ -167,7 +167,8 @@ struct FockArgs {
   long long dstride[GBSBIN_FOCK_MAX_IN + 1];   // prod_{d' < d} drad[d']
   int roff[GBSBIN_FOCK_MAX_L + 1];   // offset of group l's rows in the table (sum of radices)
   long long S;                       // nodes: dstride[nd]
-  long long chunk, nchunks;          // Gray steps per restart, restarts
+  long long x_lo, x_hi;              // the nodes this plan walks (a shard: a subrange of [0, S))
+  long long chunk, nchunks;          // Gray steps per restart, restarts over [x_lo, x_hi)
   const double2* coef;               // (L + 1) x nin x nin, [m][k][j] (column k contiguous)
   const float4* coef_df;             // the same as (hi re, hi im, lo re, lo im)
   const double2* xtw;                // exp(2 pi i g / drad[d]), g < drad[d], digit after digit

@@ -56,3 +56,31 @@ def sharded_table(prob, precision: int = 0, oversample: int = 1, group=None, str
         with Plan(prob, precision=precision, oversample=oversample, shard=(begin, end)) as p:
             table = p.table(stream)
     return allreduce_table(table, group)
+
+
+def fock_node_count(photons) -> int:
+    """Input nodes of a Fock-input problem: prod over the occupied inputs but the one with the
+    fewest photons (lowest port on ties) of (p_k + 1)."""
+    p = np.asarray(photons)
+    occ = [j for j in range(len(p)) if p[j] > 0]
+    if not occ:
+        return 1
+    held = min(occ, key=lambda j: (p[j], j))
+    return int(np.prod([int(p[j]) + 1 for j in occ if j != held], dtype=np.int64))
+
+
+def fock_sharded_table(prob, precision: int = 0, oversample: int = 1, group=None, stream=None):
+    """The whole Fock-input table, its input nodes shared by the ranks of ``group``: this rank
+    walks its node range on its current CUDA device, then the partial tables are summed."""
+    import torch
+    import torch.distributed as dist
+
+    from . import FockPlan
+    rank, world = dist.get_rank(group), dist.get_world_size(group)
+    begin, end = shard_range(fock_node_count(prob.photons), rank, world)
+    if end <= begin:                       # more ranks than nodes: contribute zeros
+        table = torch.zeros(tuple(int(c) + 1 for c in prob.cutoff), dtype=torch.float64, device="cuda")
+    else:
+        with FockPlan(prob, precision=precision, oversample=oversample, shard=(begin, end)) as p:
+            table = p.table(stream)
+    return allreduce_table(table, group)

@@ -24,12 +24,21 @@ from shard_tables import partial_table_cpu  # noqa: E402
 def main():
     rank, world = int(os.environ["RANK"]), int(os.environ["WORLD_SIZE"])
     out = sys.argv[1]
+    fock_mode = len(sys.argv) > 2 and sys.argv[2] == "fock"
     dist.init_process_group("gloo", init_method="env://", rank=rank, world_size=world)
-    prob = synth.config(0)
-    logq = oracle.binned(prob)["logq"]
-    n_eval = gdist.evaluated_points(prob.cutoff)
-    begin, end = gdist.shard_range(n_eval, rank, world)
-    part = torch.from_numpy(partial_table_cpu(prob, logq, begin, end))
+    if fock_mode:
+        # Fock inputs: the ranks split the input nodes (Gray-code order) and each contributes
+        # the oracle's partial table of its range, standing in for a sharded Fock plan
+        from oracle import fock
+        fp = synth.random_fock_problem(np.random.default_rng(41), 5, [1, 2, 0, 1, 1], 2, 5)
+        begin, end = gdist.shard_range(fock.node_count(fp.photons), rank, world)
+        part = torch.from_numpy(fock.table(fp, node_range=(begin, end))["P"].copy())
+    else:
+        prob = synth.config(0)
+        logq = oracle.binned(prob)["logq"]
+        n_eval = gdist.evaluated_points(prob.cutoff)
+        begin, end = gdist.shard_range(n_eval, rank, world)
+        part = torch.from_numpy(partial_table_cpu(prob, logq, begin, end))
     total = gdist.allreduce_table(part)
     if rank == 0:
         np.save(out, total.numpy())

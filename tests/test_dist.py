@@ -67,3 +67,22 @@ def test_gloo_world_size_2_allreduce(tmp_path):
     assert all(p.returncode == 0 for p in procs), logs
     ref = oracle.binned(synth.config(0))["P"]
     assert np.abs(np.load(out) - ref).max() < 1e-13
+
+
+def test_gloo_world_size_2_fock_node_shards(tmp_path):
+    out = str(tmp_path / "fock_table.npy")
+    env = dict(os.environ, MASTER_ADDR="127.0.0.1", MASTER_PORT=str(_free_port()), WORLD_SIZE="2")
+    procs = [subprocess.Popen([sys.executable, os.path.join(HERE, "_dist_worker.py"), out, "fock"],
+                              env=dict(env, RANK=str(r)), stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
+             for r in range(2)]
+    logs = []
+    for p in procs:
+        try:
+            logs.append(p.communicate(timeout=240)[0].decode(errors="replace"))
+        except subprocess.TimeoutExpired:
+            p.kill()
+            raise
+    assert all(p.returncode == 0 for p in procs), logs
+    from oracle import fock
+    fp = synth.random_fock_problem(np.random.default_rng(41), 5, [1, 2, 0, 1, 1], 2, 5)
+    assert np.abs(np.load(out) - fock.table(fp)["P"]).max() < 1e-14

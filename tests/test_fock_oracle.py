@@ -181,3 +181,28 @@ def test_vacuum_input():
     fp = synth.random_fock_problem(rng, 3, [0, 0, 0], 2, 2)
     P = fock.table(fp)["P"]
     assert P[0, 0] == pytest.approx(1.0, abs=1e-15) and np.abs(P).sum() == pytest.approx(1.0, abs=1e-14)
+
+
+def test_gray_code_walks_every_node_once_one_digit_at_a_time():
+    radices = [3, 2, 4]
+    seen = []
+    prev = None
+    for i in range(24):
+        g = fock.gray_digits(i, radices)
+        assert all(0 <= d < R for d, R in zip(g, radices))
+        if prev is not None:
+            diff = [abs(a - b) for a, b in zip(g, prev)]
+            assert sorted(diff) == [0, 0, 1]
+        seen.append(tuple(g))
+        prev = g
+    assert len(set(seen)) == 24
+
+
+def test_node_shards_sum_to_the_table():
+    rng = np.random.default_rng(91)
+    fp = synth.random_fock_problem(rng, 5, [1, 2, 0, 1, 1], 2, 5)
+    S = fock.node_count(fp.photons)
+    assert S == 3 * 2 * 2
+    full = fock.table(fp)["P"]
+    parts = [fock.table(fp, node_range=(b, e))["P"] for b, e in [(0, 5), (5, 6), (6, 12)]]
+    assert np.abs(sum(parts) - full).max() < 1e-15

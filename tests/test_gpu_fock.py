@@ -126,3 +126,27 @@ def test_fock_set_transfer_and_host_execute(cuda_lib):
         P_host = plan.table_host()
     assert np.array_equal(P_dev, P_host)
     assert np.abs(P_host - fock.table(fp2)["P"]).max() < TOL
+
+
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "df32"])
+def test_fock_node_shards(cuda_lib, precision):
+    # every shard's partial table against the oracle's partial table of the same node range,
+    # and the shards of a partition summing to the whole table
+    rng = np.random.default_rng(303)
+    fp = synth.random_fock_problem(rng, 9, [1, 1, 2, 1, 0, 1, 1, 1, 0], 2, 8)
+    S = fock.node_count(fp.photons)
+    with cuda_lib.FockPlan(fp, precision=precision) as p:
+        assert p.nodes() == S
+        whole = p.table().cpu().numpy()
+    cuts = [0, 1, S // 3, S - 7, S]
+    total = np.zeros_like(whole)
+    for b, e in zip(cuts[:-1], cuts[1:]):
+        with cuda_lib.FockPlan(fp, precision=precision, shard=(b, e)) as p:
+            part = p.table().cpu().numpy()
+        ref = fock.table(fp, node_range=(b, e))["P"]
+        assert np.abs(part - ref).max() < (1e-13 if precision == 0 else TOL)
+        total += part
+    assert np.abs(total - whole).max() < 1e-13
+    for bad in [(-1, 3), (3, 3), (0, S + 1)]:
+        with pytest.raises(cuda_lib.GbsbinError):
+            cuda_lib.FockPlan(fp, precision=precision, shard=bad)
