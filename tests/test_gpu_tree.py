@@ -58,3 +58,33 @@ def test_tree_state_change(cuda_lib):
     assert st == 0 and d["kernel_name"] == "tree_df32"
     sl = tuple(slice(0, int(c) + 1) for c in b.cutoff)
     assert np.abs(P - oracle.binned(b)["P"][sl]).max() < 1e-10
+
+
+HARD = [
+    # strong squeezing: |log det| large, the power-of-two exponents of P and P(1) differ by
+    # odd and even amounts across the grid, windings of several turns
+    ("strong_squeezing", lambda: synth.random_problem(np.random.default_rng(221), 8, 1, 4, [3, 3, 3, 4],
+                                                      r_range=(1.2, 1.7), eta_range=(0.85, 0.99)), 1),
+    ("oversampled", lambda: synth.random_problem(np.random.default_rng(222), 6, 1, 3, [2, 3, 2]), 3),
+    ("last_group_16_rows", lambda: synth.random_problem(np.random.default_rng(223), 12, 2, 3, [3, 2, 4],
+                                                        displaced=True, internal_basis=True), 1),
+]
+
+
+@pytest.mark.parametrize("name,make,oversample", HARD, ids=[c[0] for c in HARD])
+def test_tree_hard_cases(cuda_lib, name, make, oversample):
+    prob = make()
+    with cuda_lib.Plan(prob, precision=1, oversample=oversample) as p:
+        P = p.table().cpu().numpy()
+        st, d = p.diagnostics()
+        lq, _ = cuda_lib.gbsbin_read_points(p.handle, d["n_evaluated"])
+    assert st == 0 and d["kernel_name"] == "tree_df32"
+    radix = prob.radix * oversample
+    res = oracle.binned(prob, radix=radix)
+    sl = tuple(slice(0, int(c) + 1) for c in prob.cutoff)
+    assert np.abs(P - res["P"][sl]).max() < 1e-10
+    dig = cuda_lib.evaluated_point_digits(prob.cutoff, oversample)
+    strides = np.ones(len(radix), dtype=np.int64)
+    for l in range(len(radix) - 2, -1, -1):
+        strides[l] = strides[l + 1] * radix[l + 1]
+    assert np.abs(lq - res["logq"][dig @ strides]).max() < 1e-9
