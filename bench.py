@@ -55,7 +55,7 @@ def algorithmic_flops(n: int, has_gamma: bool) -> float:
 
 
 def tree_work(prob, n_eval: int, has_gamma: bool):
-    """The tree of block eliminations (kernel 11): complex multiply-adds per table.  Level l
+    """The tree of block eliminations (kernels 11 and 12): complex multiply-adds per table.  Level l
     (one node per combination of the first l axes' roots) runs a Gauss-Jordan sweep over nb
     pivot columns of its m x (m + 1) augmented matrix: step kk scales row kk right of the
     pivot and updates the other m - 1 rows there, (m - kk)(m + 1 - kk - 1) multiply-adds,
@@ -301,8 +301,17 @@ def main():
     peak32 = SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
     peak64 = SMS * FP64_FMA_PER_SM_CLK * 2 * SM_MAX_MHZ * 1e6 / 1e12
     issue32 = SMS * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12    # FP32-pipe operations (T/s)
-    achieved64 = flops_pt * d1["n_evaluated"] / (results[0]["kernel_ms"] * 1e-3) / 1e12
+    d0 = results[0]["diag"]
     tree = d1["kernel_name"] == "tree_df32"
+    if d0["kernel_name"] == "tree_fp64":
+        # the same tree in FP64: one complex multiply-add is 4 FP64 FMAs (8 flops)
+        macs64, _ = tree_work(prob, d0["n_evaluated"], has_gamma)
+        achieved64 = 8.0 * macs64 / (results[0]["kernel_ms"] * 1e-3) / 1e12
+        flops64 = {"flops": "tree of block eliminations: 8 x complex multiply-adds per table",
+                   "flops_per_table": 8.0 * macs64}
+    else:
+        achieved64 = flops_pt * d0["n_evaluated"] / (results[0]["kernel_ms"] * 1e-3) / 1e12
+        flops64 = {"flops": "complex LU (8/3) n^3 per evaluated point", "flops_per_point": flops_pt}
     if tree:
         macs, levels = tree_work(prob, d1["n_evaluated"], has_gamma)
         launches_per_step = levels + 2        # level sweeps, leaves, fused DFT + diagnostics
@@ -334,9 +343,11 @@ def main():
         "tables_per_s": world * args.steps / (results[1]["gpu_ms"] * 1e-3),
         "fp64": {"value": out_points[0], "unit": "points/s", "ms_per_step": results[0]["ms_per_step"],
                  "tables_per_s": world * args.steps / (results[0]["gpu_ms"] * 1e-3),
-                 "point_kernel_ms": results[0]["kernel_ms"],
-                 "roofline": {"bound": "alu", "achieved": achieved64, "peak": peak64, "unit": "TFLOP/s",
-                              "frac": achieved64 / peak64, "traffic": None}},
+                 "point_kernel_ms": results[0]["kernel_ms"], "kernel": d0["kernel_name"],
+                 "roofline": dict({"bound": "alu", "achieved": achieved64, "peak": peak64, "unit": "TFLOP/s",
+                                   "frac": achieved64 / peak64, "traffic": _profiled_traffic(d0["kernel_name"]),
+                                   "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 x 2070 MHz"},
+                                  **flops64)},
         "per_point_fp32_refine": {"kernel": dw["kernel_name"], "value": out_points["warp"], "unit": "points/s",
                                   "ms_per_step": results["warp"]["ms_per_step"],
                                   "point_kernel_ms": results["warp"]["kernel_ms"],

@@ -155,7 +155,7 @@ typedef enum {
   GBSBIN_KERNEL_FOCK_FP64 = 9,     /* Fock inputs (gbsbin_fock_*): FP64 throughout           */
   GBSBIN_KERNEL_FOCK_DF32 = 10,    /* Fock inputs: pairs of FP32 (hi + lo, ~46 bits) on the
                                       FMA pipe, running sums flushed to FP64               */
-  GBSBIN_KERNEL_TREE_DF32 = 11     /* L >= 2: rows ordered by group, the grid evaluated as a
+  GBSBIN_KERNEL_TREE_DF32 = 11,    /* L >= 2: rows ordered by group, the grid evaluated as a
                                       tree of block eliminations - depth l holds one reduced
                                       matrix I - D'A' per combination of the first l axes'
                                       roots (the Schur complement after eliminating groups
@@ -165,6 +165,8 @@ typedef enum {
                                       the FMA pipe, FP64 results; chosen automatically for
                                       GBSBIN_FP32_REFINE plans with n <= 64, last group <= 16
                                       rows, no shard and no want_backward                */
+  GBSBIN_KERNEL_TREE_FP64 = 12     /* the same tree in FP64 (DFMA pipe); chosen automatically
+                                      for GBSBIN_FP64 plans under the same conditions      */
 } gbsbin_kernel;
 
 /* Fill *o with defaults: FP64, oversample 1, diagnostics on, automatic kernel. */

@@ -128,4 +128,81 @@ __device__ __forceinline__ float4 df_csqrt(float4 z) {
   return make_float4(fabsf(q.x), sg * s.x, q.x < 0.f ? -q.z : q.z, sg * s.z);
 }
 
+// ----------------------------------------------------- the tree's two arithmetics
+// Element type E (16 bytes either way), the operations the tree kernels use, and a complex
+// scaling by a power of two that returns the exponent taken out.
+struct ArDF {                                        // pairs of FP32 on the FMA pipe
+  using E = float4;
+  static __device__ __forceinline__ E from(double2 v) { return df_from(v); }
+  static __device__ __forceinline__ double2 to(E v) { return df_to(v); }
+  static __device__ __forceinline__ E one() { return make_float4(1.f, 0.f, 0.f, 0.f); }
+  static __device__ __forceinline__ E zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+  static __device__ __forceinline__ E mul(E a, E b) { return df_mul(a, b); }
+  static __device__ __forceinline__ E add(E a, E b) { return df_add(a, b); }
+  static __device__ __forceinline__ E neg(E a) { return df_neg(a); }
+  static __device__ __forceinline__ E fma(E a, E b, E c) { return df_fma(a, b, c); }
+  static __device__ __forceinline__ E fms(E c, E a, E b) { return df_fms(c, a, b); }
+  static __device__ __forceinline__ E recip(E a) { return df_recip(a); }
+  static __device__ __forceinline__ E csqrt(E a) { return df_csqrt(a); }
+  static __device__ __forceinline__ float re(E a) { return a.x; }
+  static __device__ __forceinline__ float im(E a) { return a.y; }
+  static __device__ __forceinline__ int normalise(E& a) {
+    const float mx = fmaxf(fabsf(a.x), fabsf(a.y));
+    if (!(mx > 0.f && mx < 1.0e30f)) return 0;
+    int ex;
+    frexpf(mx, &ex);
+    a = make_float4(ldexpf(a.x, -ex), ldexpf(a.y, -ex), ldexpf(a.z, -ex), ldexpf(a.w, -ex));
+    return ex;
+  }
+};
+
+struct ArF64 {                                       // FP64 throughout
+  using E = double2;
+  static __device__ __forceinline__ E from(double2 v) { return v; }
+  static __device__ __forceinline__ double2 to(E v) { return v; }
+  static __device__ __forceinline__ E one() { return make_double2(1.0, 0.0); }
+  static __device__ __forceinline__ E zero() { return make_double2(0.0, 0.0); }
+  static __device__ __forceinline__ E mul(E a, E b) {
+    return make_double2(::fma(a.x, b.x, -a.y * b.y), ::fma(a.x, b.y, a.y * b.x));
+  }
+  static __device__ __forceinline__ E add(E a, E b) { return make_double2(a.x + b.x, a.y + b.y); }
+  static __device__ __forceinline__ E neg(E a) { return make_double2(-a.x, -a.y); }
+  static __device__ __forceinline__ E fma(E a, E b, E c) {   // c + a b
+    return make_double2(::fma(a.x, b.x, ::fma(-a.y, b.y, c.x)), ::fma(a.x, b.y, ::fma(a.y, b.x, c.y)));
+  }
+  static __device__ __forceinline__ E fms(E c, E a, E b) {   // c - a b
+    return make_double2(::fma(-a.x, b.x, ::fma(a.y, b.y, c.x)), ::fma(-a.x, b.y, ::fma(-a.y, b.x, c.y)));
+  }
+  // 1 / a = conj(a) / |a|^2, the real reciprocal by two Newton steps s <- s (2 - d s) on the
+  // FP32 seed (each doubles the ~24 correct bits): FP64 division is a long sequence on
+  // this GPU's FP64 pipe
+  static __device__ __forceinline__ E recip(E a) {
+    const double d = ::fma(a.x, a.x, a.y * a.y);
+    double s = (double)__frcp_rn((float)d);
+    s = ::fma(s, ::fma(-d, s, 1.0), s);
+    s = ::fma(s, ::fma(-d, s, 1.0), s);
+    return make_double2(a.x * s, -a.y * s);
+  }
+  // principal square root: r = |a|, t = sqrt((r + |x|) / 2), (t, y / (2 t)) for x >= 0,
+  // (|y| / (2 t), sign(y) t) otherwise
+  static __device__ __forceinline__ E csqrt(E a) {
+    const double r = ::sqrt(::fma(a.x, a.x, a.y * a.y));
+    const double t = ::sqrt(0.5 * (r + ::fabs(a.x)));
+    if (!(t > 0.0)) return make_double2(0.0, 0.0);
+    const double q = a.y / (2.0 * t);
+    if (a.x >= 0.0) return make_double2(t, q);
+    return make_double2(::fabs(q), a.y < 0.0 ? -t : t);
+  }
+  static __device__ __forceinline__ float re(E a) { return (float)a.x; }
+  static __device__ __forceinline__ float im(E a) { return (float)a.y; }
+  static __device__ __forceinline__ int normalise(E& a) {
+    const double mx = ::fmax(::fabs(a.x), ::fabs(a.y));
+    if (!(mx > 0.0 && mx < 1.0e300)) return 0;
+    int ex;
+    ::frexp(mx, &ex);
+    a = make_double2(::ldexp(a.x, -ex), ::ldexp(a.y, -ex));
+    return ex;
+  }
+};
+
 }  // namespace gbsbin

@@ -85,7 +85,8 @@ int validate_shape(const gbsbin_problem* p, const gbsbin_options* o) {
   if (!p->sigma1 && (!p->r || !p->T)) return GBSBIN_ERR_ARG;
   if (o->precision != GBSBIN_FP64 && o->precision != GBSBIN_FP32_REFINE) return GBSBIN_ERR_ARG;
   if (o->oversample < 1) return GBSBIN_ERR_ARG;
-  if (o->tile_override < 0 || (o->tile_override > GBSBIN_KERNEL_HESS_FP64 && o->tile_override != GBSBIN_KERNEL_TREE_DF32))
+  if (o->tile_override < 0 || (o->tile_override > GBSBIN_KERNEL_HESS_FP64 && o->tile_override != GBSBIN_KERNEL_TREE_DF32 &&
+                                o->tile_override != GBSBIN_KERNEL_TREE_FP64))
     return GBSBIN_ERR_ARG;
   long long n = 2LL * p->M * p->K;
   if (n > GBSBIN_MAX_N) return GBSBIN_ERR_UNSUPPORTED;
@@ -275,10 +276,13 @@ int dalloc(T** p, size_t count) {
   return check_cuda(e);
 }
 
+// The tree of block eliminations, in pairs of FP32 or in FP64.
+inline bool is_tree(int kernel) { return kernel == GBSBIN_KERNEL_TREE_DF32 || kernel == GBSBIN_KERNEL_TREE_FP64; }
+
 // Layout of the pinned staging buffer for one state upload.
 struct Stage {
   size_t off_XA, off_g, off_Xg, off_XAhi, off_XAlo, off_Xghi, off_Xglo, off_ghi, off_glo, off_XAfix;
-  size_t off_tree;   // tree plans: permuted XA (n x n), X gamma, gamma as FP32 pairs, root path record
+  size_t off_tree;   // tree plans: permuted XA (n x n), X gamma, gamma (FP32 pairs or FP64), root path record
   size_t total;
 };
 Stage stage_layout(int n, bool tree) {
@@ -317,7 +321,7 @@ int upload_hessenberg(gbsbin_plan* P, cudaStream_t stream);
 // Stage the state and enqueue its upload on `stream`.
 int upload_state(gbsbin_plan* P, cudaStream_t stream) {
   const int n = P->n;
-  const bool tree = P->kernel == GBSBIN_KERNEL_TREE_DF32;
+  const bool tree = is_tree(P->kernel);
   Stage s = stage_layout(n, tree);
   // a previous upload may still be reading the staging buffer
   cudaError_t e = cudaStreamSynchronize(stream);
@@ -352,14 +356,23 @@ int upload_state(gbsbin_plan* P, cudaStream_t stream) {
     float4* u0 = c0 + n;
     float4* path = u0 + n;
     const std::vector<int>& pm = P->tree_perm;
+    const bool f64 = P->kernel == GBSBIN_KERNEL_TREE_FP64;
+    // one 16-byte slot per element: (hi re, hi im, lo re, lo im) FP32 pairs, or a double2
+    auto slot = [f64](cd v) {
+      if (!f64) return split4(v);
+      float4 o;
+      const double2 d = make_double2(v.real(), v.imag());
+      std::memcpy(&o, &d, sizeof(o));
+      return o;
+    };
     for (int i = 0; i < n; ++i) {
-      for (int j = 0; j < n; ++j) A0[(size_t)i * n + j] = split4(P->XA[(size_t)pm[i] * n + pm[j]]);
-      c0[i] = split4(P->Xgamma[pm[i]]);
-      u0[i] = split4(P->gamma[pm[i]]);
+      for (int j = 0; j < n; ++j) A0[(size_t)i * n + j] = slot(P->XA[(size_t)pm[i] * n + pm[j]]);
+      c0[i] = slot(P->Xgamma[pm[i]]);
+      u0[i] = slot(P->gamma[pm[i]]);
     }
-    path[0] = make_float4(1.f, 0.f, 0.f, 0.f);        // pivot product
+    path[0] = slot(cd(1.0, 0.0));                       // pivot product
     path[1] = make_float4(0.f, 0.f, 3.0e38f, 0.f);    // argument sum, power of two, min Re pivot
-    path[2] = make_float4(0.f, 0.f, 0.f, 0.f);        // exponent sum
+    path[2] = slot(cd(0.0, 0.0));                       // exponent sum
     // the w = 1 point on the host: unpivoted LU of I - XA in the tree's row order, its pivot
     // product p0 2^e0, argument and winding (each pivot has Re > 0)
     P->tree_g = !P->has_gamma;
@@ -553,6 +566,7 @@ int evaluate_fp64_with_factors(gbsbin_plan* P, cudaStream_t s) {
 // tensor cores.
 inline bool is_blk(int kernel) { return kernel == GBSBIN_KERNEL_BLK_FP32R || kernel == GBSBIN_KERNEL_BLK_TC_FP32R; }
 
+
 // Tree plans: rows ordered by group (stable within a group), the block sizes, and the
 // reduced-matrix sizes and node counts per depth.  Returns the scratch bytes of depths
 // 1 .. L-1, or 0 when the problem does not suit the tree (one group, a level block or the
@@ -727,17 +741,16 @@ static int plan_create_impl(const gbsbin_problem* p, const gbsbin_options* o, gb
   // (batches run their own per-point launches)
   const bool sharded = opt.shard_end != 0 || opt.shard_begin != 0;
   size_t tree_bytes = 0;
-  if (P->kernel == GBSBIN_KERNEL_TREE_DF32 ||
-      (alloc_gws && !opt.tile_override && opt.precision == GBSBIN_FP32_REFINE && p->L >= 2)) {
+  if (is_tree(P->kernel) || (alloc_gws && !opt.tile_override && p->L >= 2)) {
     tree_bytes = (!sharded && !opt.want_backward) ? tree_layout(P) : 0;
-    if (tree_bytes) {
-      P->kernel = GBSBIN_KERNEL_TREE_DF32;
-    } else if (P->kernel == GBSBIN_KERNEL_TREE_DF32) {
+    if (tree_bytes && !is_tree(P->kernel))
+      P->kernel = opt.precision == GBSBIN_FP64 ? GBSBIN_KERNEL_TREE_FP64 : GBSBIN_KERNEL_TREE_DF32;
+    else if (!tree_bytes && is_tree(P->kernel)) {
       delete P;
       return GBSBIN_ERR_UNSUPPORTED;
     }
   }
-  P->P = P->kernel == GBSBIN_KERNEL_HESS_FP64 || P->kernel == GBSBIN_KERNEL_TREE_DF32 ? 1
+  P->P = P->kernel == GBSBIN_KERNEL_HESS_FP64 || is_tree(P->kernel) ? 1
          : P->kernel == GBSBIN_KERNEL_WARP_FP32R ? (n <= 32 ? 1 : 0)
          : is_blk(P->kernel) ? (n <= GBSBIN_BLK_MAX_N ? 1 : 0)
                                                  : points_per_cta(P->kernel, n, p->L);
@@ -759,7 +772,7 @@ static int plan_create_impl(const gbsbin_problem* p, const gbsbin_options* o, gb
     return GBSBIN_ERR_CUDA;
   }
   const size_t nn = (size_t)n * n;
-  Stage sl = stage_layout(n, P->kernel == GBSBIN_KERNEL_TREE_DF32);
+  Stage sl = stage_layout(n, is_tree(P->kernel));
   (void)nn;
   if ((st = dalloc(&P->d_state, sl.total)) || (st = dalloc(&P->d_label, n)) || (st = dalloc(&P->d_logq, g.n_eval)) ||
       (st = dalloc(&P->d_minpiv, g.n_eval)) || (st = dalloc(&P->d_bufA, g.n_full)) ||
@@ -794,13 +807,13 @@ static int plan_create_impl(const gbsbin_problem* p, const gbsbin_options* o, gb
     return st;
   }
   if ((P->kernel == GBSBIN_KERNEL_WARP_FP32R || P->kernel == GBSBIN_KERNEL_HESS_FP64 ||
-       P->kernel == GBSBIN_KERNEL_TREE_DF32) &&
+       is_tree(P->kernel)) &&
       (st = dalloc(&P->d_ldfin, (size_t)6 * g.n_eval))) {
     free_device(P);
     delete P;
     return st;
   }
-  if (P->kernel == GBSBIN_KERNEL_TREE_DF32) {
+  if (is_tree(P->kernel)) {
     if ((st = dalloc(&P->d_tree, tree_bytes))) {
       free_device(P);
       delete P;
@@ -974,7 +987,7 @@ int gbsbin_execute(gbsbin_plan* P, double* P_out, void* stream) {
   PointArgs a = make_point_args(P);
   P->saved_valid = a.lu_store != nullptr;
   if (P->ev0 && cudaEventRecord(P->ev0, s) != cudaSuccess) return GBSBIN_ERR_CUDA;
-  if (P->kernel == GBSBIN_KERNEL_TREE_DF32) {
+  if (is_tree(P->kernel)) {
     TreeArgs t = P->tree;
     t.has_gamma = P->has_gamma;
     t.tw = P->d_tw;
@@ -982,7 +995,7 @@ int gbsbin_execute(gbsbin_plan* P, double* P_out, void* stream) {
     t.ldfin = P->d_ldfin;
     t.minpiv = P->d_minpiv;
     t.gout = P->tree_g ? P->d_bufA : nullptr;
-    if (launch_points_tree(t, s) != cudaSuccess) return GBSBIN_ERR_CUDA;
+    if (launch_points_tree(t, P->kernel == GBSBIN_KERNEL_TREE_FP64, s) != cudaSuccess) return GBSBIN_ERR_CUDA;
     if (P->ev1 && cudaEventRecord(P->ev1, s) != cudaSuccess) return GBSBIN_ERR_CUDA;
     DftArgs d = make_dft_args(P, P_out);
     d.g_ready = P->tree_g ? 1 : 0;
@@ -1031,7 +1044,7 @@ int gbsbin_diagnostics(gbsbin_plan* P, gbsbin_diag* out, void* stream) {
   out->max_imag = h[1];
   out->min_pivot_re = h[2];
   out->n_bad_points = (long long)h[3];
-  out->log_q1_re = (P->kernel == GBSBIN_KERNEL_TREE_DF32 && P->tree_g) ? P->tree_logq0 : h[4];
+  out->log_q1_re = (is_tree(P->kernel) && P->tree_g) ? P->tree_logq0 : h[4];
   out->n_points = P->grid.npts;
   out->n_evaluated = P->grid.n_eval;
   out->table_size = P->table_size;
@@ -1056,7 +1069,7 @@ int gbsbin_read_points(gbsbin_plan* P, double* logq_host, double* minpiv_host, v
   cudaStream_t s = (cudaStream_t)stream;
   const size_t ne = (size_t)P->grid.n_eval;
   // plans whose DFT took G directly left log q unfinished
-  if (P->kernel == GBSBIN_KERNEL_TREE_DF32 && P->tree_g &&
+  if (is_tree(P->kernel) && P->tree_g &&
       launch_finish_logq(P->d_ldfin, P->d_logq, (long long)ne, s) != cudaSuccess)
     return GBSBIN_ERR_CUDA;
   if (cudaMemcpyAsync(logq_host, P->d_logq, ne * sizeof(double2), cudaMemcpyDeviceToHost, s) != cudaSuccess)

@@ -123,10 +123,11 @@ struct DftArgs {
 };
 
 // Tree of block eliminations over the grid (gbsbin_points_tree.cu), in pairs of FP32
-// (float4 = hi re, hi im, lo re, lo im): rows ordered by group; depth l holds one reduced
-// matrix A' per combination of the first l axes' roots (A[l]: nodes x m[l] x m[l],
-// row-major; c, u: the displacement vectors; path: 3 float4 per node).  Depth 0 is the
-// permuted state.  Leaves (depth L - 1, last axis halved) write the unfinished log q of
+// (float4 = hi re, hi im, lo re, lo im) or in FP64 (double2 in the same 16-byte slots):
+// rows ordered by group; depth l holds one reduced matrix A' per combination of the first
+// l axes' roots (A[l]: nodes x m[l] x m[l], row-major; c, u: the displacement vectors;
+// path: 3 slots per node - pivot product, (argument sum, power of two, smallest pivot
+// real part, -) as FP32, exponent sum).  Depth 0 is the permuted state.  Leaves (depth L - 1, last axis halved) write the unfinished log q of
 // every evaluated point to ldfin (FP64).
 struct TreeArgs {
   int has_gamma;
@@ -149,7 +150,7 @@ struct TreeArgs {
 };
 size_t tree_level_smem_bytes(int nb, int m);
 int tree_leaf_threads(int n);   // lanes per leaf (0: no kernel for a last group of n rows)
-cudaError_t launch_points_tree(const TreeArgs& a, cudaStream_t s);
+cudaError_t launch_points_tree(const TreeArgs& a, bool fp64, cudaStream_t s);
 
 // Fock inputs through a lossy circuit (gbsbin_fock.cu).  nin occupied inputs in position
 // order (position 0 is the held input, x = 1; positions 1..nd are the Gray digits); per

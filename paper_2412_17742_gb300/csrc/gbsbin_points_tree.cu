@@ -1,5 +1,5 @@
 // Grid points by a tree of block eliminations (arXiv:2412.17742, Sec. III Eq. q_d on the
-// roots-of-unity grid of Sec. VI), in pairs of FP32.
+// roots-of-unity grid of Sec. VI), in pairs of FP32 or in FP64.
 //
 // Order the rows and columns of K(w) = I - D(w) A (A = XA) by detector group, group 0
 // first (a symmetric permutation: det and the bilinear form below are unchanged, and
@@ -26,9 +26,12 @@
 // sum of the pivots' arguments, the exponent sum and the smallest pivot real part - and
 // leaves write the unfinished form that the inverse DFT's first stage finishes in FP64.
 //
-// Arithmetic: pairs of FP32 (about 46 bits, gbsbin_df.cuh) on the FMA pipe.  The chains
-// here are short and dependent; the FP64 pipe of this GPU issues one 32-lane instruction
-// per ~64 cycles per scheduler, the FMA pipe one per cycle.
+// Arithmetic: every kernel is written once over an arithmetic (gbsbin_df.cuh): pairs of
+// FP32 (about 46 bits) on the FMA pipe, or FP64.  The chains here are short and dependent;
+// the FP64 pipe of this GPU issues one 32-lane instruction per ~64 cycles per scheduler,
+// the FMA pipe one per cycle, so the pairs are the fast form and FP64 the exact-type one.
+// Both store 16-byte elements (float4 hi/lo pairs or double2), so the tree's buffers and
+// its launch shapes are the same.
 #include <cuda_runtime.h>
 
 #include "gbsbin_device.cuh"
@@ -40,72 +43,79 @@ namespace {
 
 constexpr int LT_MAX = 512;      // threads of a level CTA (at most)
 
-// path record (3 float4): [0] pivot product; [1] = (argument sum, power of two, smallest
-// pivot real part, -); [2] exponent sum
-__device__ __forceinline__ void path_pivot(float4* pr, float4 p) {
-  float4 r = df_mul(pr[0], p);
-  const float mx = fmaxf(fabsf(r.x), fabsf(r.y));
-  float e2 = pr[1].y;
-  if (mx > 0.f && mx < 1.0e30f) {
-    int ex;
-    frexpf(mx, &ex);
-    r = make_float4(ldexpf(r.x, -ex), ldexpf(r.y, -ex), ldexpf(r.z, -ex), ldexpf(r.w, -ex));
-    e2 += (float)ex;
-  }
-  pr[0] = r;
-  float mn = fminf(pr[1].z, p.x);
-  if (!(p.x == p.x) || !(p.y == p.y)) mn = -3.0e38f;
-  pr[1] = make_float4(__fadd_rn(pr[1].x, atan2f(p.y, p.x)), e2, mn, 0.f);
+// Path record of a node (48 bytes in both arithmetics): the pivot product scaled by a power
+// of two; (FP32 argument sum, power of two, smallest pivot real part, -); the exponent sum.
+template <class E>
+struct PathRec {
+  E prod;
+  float4 meta;
+  E ex;
+};
+static_assert(sizeof(PathRec<float4>) == 3 * sizeof(float4) && sizeof(PathRec<double2>) == 3 * sizeof(float4),
+              "path records are three 16-byte slots");
+
+template <class Ar>
+__device__ __forceinline__ PathRec<typename Ar::E>* path_at(float4* base, long long node) {
+  return reinterpret_cast<PathRec<typename Ar::E>*>(base + 3 * node);
+}
+template <class Ar>
+__device__ __forceinline__ typename Ar::E* elem(float4* p) {
+  return reinterpret_cast<typename Ar::E*>(p);
 }
 
-__device__ __forceinline__ float4 shfl4(float4 v, int src) {
+// fold one pivot into a record
+template <class Ar>
+__device__ __forceinline__ void path_pivot(PathRec<typename Ar::E>& pr, typename Ar::E p) {
+  typename Ar::E r = Ar::mul(pr.prod, p);
+  const int ex = Ar::normalise(r);
+  pr.prod = r;
+  const float pre = Ar::re(p), pim = Ar::im(p);
+  float mn = fminf(pr.meta.z, pre);
+  if (!(pre == pre) || !(pim == pim)) mn = -3.0e38f;
+  pr.meta = make_float4(__fadd_rn(pr.meta.x, atan2f(pim, pre)), pr.meta.y + (float)ex, mn, 0.f);
+}
+
+__device__ __forceinline__ float4 shfl(float4 v, int src) {
   return make_float4(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src),
                      __shfl_sync(0xffffffffu, v.z, src), __shfl_sync(0xffffffffu, v.w, src));
 }
-__device__ __forceinline__ float4 shfl4_xor(float4 v, int mask) {
+__device__ __forceinline__ double2 shfl(double2 v, int src) {
+  return make_double2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
+}
+__device__ __forceinline__ float4 shfl_xor(float4 v, int mask) {
   return make_float4(__shfl_xor_sync(0xffffffffu, v.x, mask), __shfl_xor_sync(0xffffffffu, v.y, mask),
                      __shfl_xor_sync(0xffffffffu, v.z, mask), __shfl_xor_sync(0xffffffffu, v.w, mask));
+}
+__device__ __forceinline__ double2 shfl_xor(double2 v, int mask) {
+  return make_double2(__shfl_xor_sync(0xffffffffu, v.x, mask), __shfl_xor_sync(0xffffffffu, v.y, mask));
 }
 
 // The path record after a set of pivots, by one full warp: lane t holds pivot t of the set
 // (count <= 32; lanes beyond hold 1).  Product by a butterfly of pair products (each level
 // rescaled by a power of two), argument sum and smallest real part by butterflies too.
 // pr: the parent's record on input, the child's on output (every lane).
-__device__ __forceinline__ void path_warp(float4* pr, float4 piv, bool real) {
-  const int lane = threadIdx.x & 31;
-  float4 p = real ? piv : make_float4(1.f, 0.f, 0.f, 0.f);
-  float arg = real ? atan2f(piv.y, piv.x) : 0.f;
-  float mn = real ? piv.x : 3.0e38f;
-  if (real && (!(piv.x == piv.x) || !(piv.y == piv.y))) mn = -3.0e38f;
+template <class Ar>
+__device__ __forceinline__ void path_warp(PathRec<typename Ar::E>& pr, typename Ar::E piv, bool real) {
+  using E = typename Ar::E;
+  E p = real ? piv : Ar::one();
+  const float pre = Ar::re(piv), pim = Ar::im(piv);
+  float arg = real ? atan2f(pim, pre) : 0.f;
+  float mn = real ? pre : 3.0e38f;
+  if (real && (!(pre == pre) || !(pim == pim))) mn = -3.0e38f;
   float e2 = 0.f;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    p = df_mul(p, shfl4_xor(p, o));
-    const float mx = fmaxf(fabsf(p.x), fabsf(p.y));
-    float eo = __shfl_xor_sync(0xffffffffu, e2, o);
-    e2 += eo;
-    if (mx > 0.f && mx < 1.0e30f) {
-      int ex;
-      frexpf(mx, &ex);
-      p = make_float4(ldexpf(p.x, -ex), ldexpf(p.y, -ex), ldexpf(p.z, -ex), ldexpf(p.w, -ex));
-      e2 += (float)ex;
-    }
+    p = Ar::mul(p, shfl_xor(p, o));
+    e2 += __shfl_xor_sync(0xffffffffu, e2, o);
+    e2 += (float)Ar::normalise(p);
     arg = __fadd_rn(arg, __shfl_xor_sync(0xffffffffu, arg, o));
     mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
   }
-  (void)lane;
   // every lane now holds the same product, exponent, sum and minimum; fold in the parent
-  float4 q = df_mul(pr[0], p);
-  float e = pr[1].y + e2;
-  const float mx = fmaxf(fabsf(q.x), fabsf(q.y));
-  if (mx > 0.f && mx < 1.0e30f) {
-    int ex;
-    frexpf(mx, &ex);
-    q = make_float4(ldexpf(q.x, -ex), ldexpf(q.y, -ex), ldexpf(q.z, -ex), ldexpf(q.w, -ex));
-    e += (float)ex;
-  }
-  pr[0] = q;
-  pr[1] = make_float4(__fadd_rn(pr[1].x, arg), e, fminf(pr[1].z, mn), 0.f);
+  E q = Ar::mul(pr.prod, p);
+  const float e = pr.meta.y + e2 + (float)Ar::normalise(q);
+  pr.prod = q;
+  pr.meta = make_float4(__fadd_rn(pr.meta.x, arg), e, fminf(pr.meta.z, mn), 0.f);
 }
 
 // Level l: one CTA per child (parent, k) of depth l.  Forward elimination of the nb pivot
@@ -120,39 +130,41 @@ __device__ __forceinline__ void path_warp(float4* pr, float4 piv, bool real) {
 // are never scaled (only the Schur complement is needed): step kk subtracts
 // (G[i][kk] / G[kk][kk]) row kk from every row i > kk: one thread forms the pivot's
 // reciprocal, the rows below their multipliers, then every entry one fused multiply-subtract.
+template <class Ar>
 __global__ void __launch_bounds__(LT_MAX) k_tree_level(TreeArgs a, int l) {
-  extern __shared__ __align__(16) float4 gsm[];
+  using E = typename Ar::E;
+  extern __shared__ __align__(16) unsigned char gsm_raw[];
   const int nb = a.nb[l], m = a.m[l], mc = m - nb, cols = m + 1;
   const int rows = a.has_gamma ? m + 1 : m;
-  float4* G = gsm;                                   // rows x cols
-  float4* pv = G + (size_t)rows * cols;              // nb pivots
-  float4* Lm = pv + nb;                              // rows: multipliers of the current step
-  __shared__ float4 s_inv[1];
+  E* G = reinterpret_cast<E*>(gsm_raw);              // rows x cols
+  E* pv = G + (size_t)rows * cols;                   // nb pivots
+  E* Lm = pv + nb;                                   // rows: multipliers of the current step
+  __shared__ E s_inv[1];
   const long long child = blockIdx.x;
   const int R = a.grid.radix[l];
   const long long parent = child / R;
   const int k = (int)(child - parent * R);
-  const float4 w = df_from(grid_root(a.tw, a.grid, l, k));
-  const float4* Ap = a.A[l] + parent * (long long)m * m;
-  const float4* cp = a.c[l] + parent * (long long)m;
-  const float4* up = a.u[l] + parent * (long long)m;
+  const E w = Ar::from(grid_root(a.tw, a.grid, l, k));
+  const E* Ap = elem<Ar>(a.A[l]) + parent * (long long)m * m;
+  const E* cp = elem<Ar>(a.c[l]) + parent * (long long)m;
+  const E* up = elem<Ar>(a.u[l]) + parent * (long long)m;
   const int tid = threadIdx.x, LT = blockDim.x;
-  const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+  const E zero = Ar::zero();
   for (int idx = tid; idx < rows * cols; idx += LT) {
     const int i = idx / cols, s = idx - (idx / cols) * cols;
-    float4 g;
+    E g;
     if (i == m) {                                   // the u row
-      g = s < nb ? df_neg(up[s]) : s < m ? up[s] : zero;
+      g = s < nb ? Ar::neg(up[s]) : s < m ? up[s] : zero;
     } else {
-      const float4 v = s < m ? Ap[(long long)i * m + s] : (a.has_gamma ? cp[i] : zero);
+      const E v = s < m ? Ap[(long long)i * m + s] : (a.has_gamma ? cp[i] : zero);
       if (i < nb) {
-        g = df_mul(w, v);
+        g = Ar::mul(w, v);
         if (s < nb) {
-          g = df_neg(g);
-          if (s == i) g = df_add(g, make_float4(1.f, 0.f, 0.f, 0.f));
+          g = Ar::neg(g);
+          if (s == i) g = Ar::add(g, Ar::one());
         }
       } else {
-        g = s < nb ? df_neg(v) : v;
+        g = s < nb ? Ar::neg(v) : v;
       }
     }
     G[idx] = g;
@@ -160,13 +172,13 @@ __global__ void __launch_bounds__(LT_MAX) k_tree_level(TreeArgs a, int l) {
   for (int kk = 0; kk < nb; ++kk) {
     __syncthreads();                                 // row kk final
     if (tid == 0) {
-      const float4 piv = G[kk * cols + kk];
+      const E piv = G[kk * cols + kk];
       pv[kk] = piv;
-      s_inv[0] = df_recip(piv);
+      s_inv[0] = Ar::recip(piv);
     }
     __syncthreads();
-    const float4 r = s_inv[0];
-    for (int i = kk + 1 + tid; i < rows; i += LT) Lm[i] = df_mul(G[i * cols + kk], r);
+    const E r = s_inv[0];
+    for (int i = kk + 1 + tid; i < rows; i += LT) Lm[i] = Ar::mul(G[i * cols + kk], r);
     __syncthreads();
     // entries (i, s), i in (kk, rows), s in (kk, cols); two independent entries per pass.
     // floor(idx / w_) from a float reciprocal: idx < 2^14 and w_ <= 65, so (idx + 1/2) / w_
@@ -177,43 +189,37 @@ __global__ void __launch_bounds__(LT_MAX) k_tree_level(TreeArgs a, int l) {
       const int idx2 = idx + LT;
       const int i = kk + 1 + (int)(((float)idx + 0.5f) * rw);
       const int sc = kk + 1 + (idx - (i - kk - 1) * w_);
-      const float4 g1 = df_fms(G[i * cols + sc], Lm[i], G[kk * cols + sc]);
+      const E g1 = Ar::fms(G[i * cols + sc], Lm[i], G[kk * cols + sc]);
       if (idx2 < total) {
         const int i2 = kk + 1 + (int)(((float)idx2 + 0.5f) * rw);
         const int s2 = kk + 1 + (idx2 - (i2 - kk - 1) * w_);
-        G[i2 * cols + s2] = df_fms(G[i2 * cols + s2], Lm[i2], G[kk * cols + s2]);
+        G[i2 * cols + s2] = Ar::fms(G[i2 * cols + s2], Lm[i2], G[kk * cols + s2]);
       }
       G[i * cols + sc] = g1;
     }
   }
   __syncthreads();
-  float4* Ac = a.A[l + 1] + child * (long long)mc * mc;
+  E* Ac = elem<Ar>(a.A[l + 1]) + child * (long long)mc * mc;
   for (int idx = tid; idx < mc * mc; idx += LT) {
     const int i = idx / mc, j = idx - (idx / mc) * mc;
     Ac[idx] = G[(nb + i) * cols + nb + j];
   }
   if (a.has_gamma) {
-    float4* cc = a.c[l + 1] + child * (long long)mc;
-    float4* uc = a.u[l + 1] + child * (long long)mc;
+    E* cc = elem<Ar>(a.c[l + 1]) + child * (long long)mc;
+    E* uc = elem<Ar>(a.u[l + 1]) + child * (long long)mc;
     for (int j = tid; j < mc; j += LT) {
       cc[j] = G[(nb + j) * cols + m];
       uc[j] = G[m * cols + nb + j];
     }
   }
   if (tid < 32) {                                    // the child's path record (warp 0)
-    const float4* pp = a.path[l] + parent * 3;
-    float4 pr[3] = {pp[0], pp[1], pp[2]};
+    PathRec<E> pr = *path_at<Ar>(a.path[l], parent);
     for (int t0 = 0; t0 < nb; t0 += 32) {
       const int t = t0 + tid;
-      path_warp(pr, t < nb ? pv[t] : zero, t < nb);
+      path_warp<Ar>(pr, t < nb ? pv[t] : zero, t < nb);
     }
-    if (a.has_gamma) pr[2] = df_add(pr[2], G[m * cols + m]);
-    if (tid == 0) {
-      float4* pc = a.path[l + 1] + child * 3;
-      pc[0] = pr[0];
-      pc[1] = pr[1];
-      pc[2] = pr[2];
-    }
+    if (a.has_gamma) pr.ex = Ar::add(pr.ex, G[m * cols + m]);
+    if (tid == 0) *path_at<Ar>(a.path[l + 1], child) = pr;
   }
 }
 
@@ -224,8 +230,9 @@ __global__ void __launch_bounds__(LT_MAX) k_tree_level(TreeArgs a, int l) {
 // right-hand side with them), so U and L^-1 (w c) come out together; the back substitution
 // then broadcasts one solution entry per step.  Every lane sees every pivot and keeps the
 // path record; the team's first lane writes the point.
-template <int NL>
+template <class Ar, int NL>
 __global__ void __launch_bounds__(128) k_tree_leaf(TreeArgs a) {
+  using E = typename Ar::E;
   constexpr int TEAMS = 32 / NL;
   const int lane = threadIdx.x & 31;
   const int team = lane / NL, r = lane - team * NL;
@@ -236,80 +243,79 @@ __global__ void __launch_bounds__(128) k_tree_leaf(TreeArgs a) {
   const int H = a.grid.half;
   const long long parent = live ? leaf / H : 0;
   const int k = live ? (int)(leaf - parent * H) : 0;
-  const float4 w = df_from(grid_root(a.tw, a.grid, l, k));
-  const float4* Ap = a.A[l] + parent * (long long)NL * NL + (long long)(live ? r : 0) * NL;
-  const float4 one = make_float4(1.f, 0.f, 0.f, 0.f), zero = make_float4(0.f, 0.f, 0.f, 0.f);
-  float4 b[NL];
+  const E w = Ar::from(grid_root(a.tw, a.grid, l, k));
+  const E* Ap = elem<Ar>(a.A[l]) + parent * (long long)NL * NL + (long long)(live ? r : 0) * NL;
+  const E one = Ar::one(), zero = Ar::zero();
+  E b[NL];
 #pragma unroll
   for (int j = 0; j < NL; ++j) {
-    b[j] = df_neg(df_mul(w, Ap[j]));
-    if (j == r) b[j] = df_add(b[j], one);
+    b[j] = Ar::neg(Ar::mul(w, Ap[j]));
+    if (j == r) b[j] = Ar::add(b[j], one);
   }
-  float4 y = zero, u = zero;
+  E y = zero, u = zero;
   if (a.has_gamma) {
-    y = df_mul(w, a.c[l][parent * NL + (live ? r : 0)]);
-    u = a.u[l][parent * NL + (live ? r : 0)];
+    y = Ar::mul(w, elem<Ar>(a.c[l])[parent * NL + (live ? r : 0)]);
+    u = elem<Ar>(a.u[l])[parent * NL + (live ? r : 0)];
   }
-  const float4* pp = a.path[l] + parent * 3;
-  float4 pr[3] = {pp[0], pp[1], pp[2]};
-  float4 myinv = one;
+  PathRec<E> pr = *path_at<Ar>(a.path[l], parent);
+  E myinv = one;
   // the step loop stays rolled (an unrolled copy per step overflows the instruction
   // cache); the row stays in registers, entries left of the step skipped by a uniform test
 #pragma unroll 1
   for (int kk = 0; kk < NL; ++kk) {
     const int src = base + kk;
-    float4 bk = b[0];
+    E bk = b[0];
 #pragma unroll
     for (int j = 1; j < NL; ++j)
       if (j == kk) bk = b[j];
-    const float4 piv = shfl4(bk, src);
-    const float4 ykk = shfl4(y, src);
-    path_pivot(pr, piv);
-    const float4 inv = df_recip(piv);
+    const E piv = shfl(bk, src);
+    const E ykk = shfl(y, src);
+    path_pivot<Ar>(pr, piv);
+    const E inv = Ar::recip(piv);
     if (r == kk) myinv = inv;
     const bool below = r > kk;
-    const float4 li = df_mul(bk, inv);               // used by the rows below only
+    const E li = Ar::mul(bk, inv);                   // used by the rows below only
 #pragma unroll
     for (int j = 1; j < NL; ++j) {
       if (j <= kk) continue;
-      const float4 rj = shfl4(b[j], src);
-      if (below) b[j] = df_fms(b[j], li, rj);
+      const E rj = shfl(b[j], src);
+      if (below) b[j] = Ar::fms(b[j], li, rj);
     }
-    if (below) y = df_fms(y, li, ykk);
+    if (below) y = Ar::fms(y, li, ykk);
   }
-  float4 ex = pr[2];
+  E ex = pr.ex;
   if (a.has_gamma) {                                  // x = U^-1 y, ex += u^T x
-    float4 acc = y, x = zero;
+    E acc = y, x = zero;
 #pragma unroll
     for (int t = NL - 1; t >= 0; --t) {
-      if (r == t) x = df_mul(acc, myinv);
-      const float4 xt = shfl4(x, base + t);
-      if (r < t) acc = df_fms(acc, b[t], xt);
+      if (r == t) x = Ar::mul(acc, myinv);
+      const E xt = shfl(x, base + t);
+      if (r < t) acc = Ar::fms(acc, b[t], xt);
     }
-    float4 part = df_mul(u, x);
+    E part = Ar::mul(u, x);
 #pragma unroll
-    for (int t = 0; t < NL; ++t) ex = df_add(ex, shfl4(part, base + t));
+    for (int t = 0; t < NL; ++t) ex = Ar::add(ex, shfl(part, base + t));
   }
   if (!live || r != 0) return;
   const double LN2 = 0.693147180559945309417232121458;
-  const double2 P = df_to(pr[0]), X = df_to(ex);
+  const double2 P = Ar::to(pr.prod), X = Ar::to(ex);
   double* f = a.ldfin + 6 * leaf;
   f[0] = P.x;
   f[1] = P.y;
-  f[2] = (double)pr[1].x;
-  f[3] = -0.5 * (double)pr[1].y * LN2 + 0.5 * X.x;
+  f[2] = (double)pr.meta.x;
+  f[3] = -0.5 * (double)pr.meta.y * LN2 + 0.5 * X.x;
   f[4] = 0.5 * X.y;
   f[5] = 0.0;
-  a.minpiv[leaf] = (double)pr[1].z;
+  a.minpiv[leaf] = (double)pr.meta.z;
   if (a.gout) {                                      // G = q / q(1) = (P0 / P)^(1/2) 2^((e0 - e)/2) (-1)^w
     const float TWO_PI = 6.28318530717958647692f;
-    const float argP = atan2f(pr[0].y, pr[0].x);
-    const float m = rintf((pr[1].x - argP) / TWO_PI);           // winding of log det at this point
-    const float4 Z = df_mul(df_from(make_double2(a.p0re, a.p0im)), df_recip(pr[0]));
-    const float kz = rintf((atan2f(Z.y, Z.x) - (a.p0arg - argP)) / TWO_PI);
+    const float argP = atan2f(Ar::im(pr.prod), Ar::re(pr.prod));
+    const float m = rintf((pr.meta.x - argP) / TWO_PI);         // winding of log det at this point
+    const E Z = Ar::mul(Ar::from(make_double2(a.p0re, a.p0im)), Ar::recip(pr.prod));
+    const float kz = rintf((atan2f(Ar::im(Z), Ar::re(Z)) - (a.p0arg - argP)) / TWO_PI);
     const int wind = (int)(kz + m - a.m0);
-    double2 g = df_to(df_csqrt(Z));
-    const int d = (int)(a.e0 - pr[1].y);
+    double2 g = Ar::to(Ar::csqrt(Z));
+    const int d = (int)(a.e0 - pr.meta.y);
     if (d & 1) {
       g.x *= 1.41421356237309504880;
       g.y *= 1.41421356237309504880;
@@ -320,13 +326,44 @@ __global__ void __launch_bounds__(128) k_tree_leaf(TreeArgs a) {
   }
 }
 
-template <int NL>
+template <class Ar, int NL>
 cudaError_t launch_leaf(const TreeArgs& a, cudaStream_t s) {
   constexpr int TEAMS = 32 / NL;
   const long long warps = (a.grid.n_eval + TEAMS - 1) / TEAMS;
   const long long blocks = (warps + 3) / 4;
-  k_tree_leaf<NL><<<(unsigned)blocks, 128, 0, s>>>(a);
+  k_tree_leaf<Ar, NL><<<(unsigned)blocks, 128, 0, s>>>(a);
   return cudaGetLastError();
+}
+
+template <class Ar>
+cudaError_t launch_tree(const TreeArgs& a, cudaStream_t s) {
+  cudaError_t err = cudaSuccess;
+  long long nodes = 1;
+  for (int l = 0; l + 1 < a.grid.L; ++l) {
+    const long long children = nodes * a.grid.radix[l];
+    const size_t smem = tree_level_smem_bytes(a.nb[l], a.m[l]);
+    if (smem > 48 * 1024) {
+      err = cudaFuncSetAttribute(k_tree_level<Ar>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (err != cudaSuccess) return err;
+    }
+    const int m = a.m[l], width = m * m;              // entries of the first elimination step
+    const int threads = width >= 1024 ? 512 : width >= 256 ? 256 : 128;
+    k_tree_level<Ar><<<(unsigned)children, threads, smem, s>>>(a, l);
+    err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+    nodes = children;
+  }
+  switch (a.m[a.grid.L - 1]) {
+    case 2: return launch_leaf<Ar, 2>(a, s);
+    case 4: return launch_leaf<Ar, 4>(a, s);
+    case 6: return launch_leaf<Ar, 6>(a, s);
+    case 8: return launch_leaf<Ar, 8>(a, s);
+    case 10: return launch_leaf<Ar, 10>(a, s);
+    case 12: return launch_leaf<Ar, 12>(a, s);
+    case 14: return launch_leaf<Ar, 14>(a, s);
+    case 16: return launch_leaf<Ar, 16>(a, s);
+    default: return cudaErrorInvalidConfiguration;
+  }
 }
 
 }  // namespace
@@ -336,34 +373,8 @@ size_t tree_level_smem_bytes(int nb, int m) { return sizeof(float4) * ((size_t)(
 // Leaf blocks of 2, 4, ..., 16 rows have a kernel instance (0: not supported).
 int tree_leaf_threads(int n) { return (n >= 2 && n <= 16 && n % 2 == 0) ? n : 0; }
 
-cudaError_t launch_points_tree(const TreeArgs& a, cudaStream_t s) {
-  cudaError_t err = cudaSuccess;
-  long long nodes = 1;
-  for (int l = 0; l + 1 < a.grid.L; ++l) {
-    const long long children = nodes * a.grid.radix[l];
-    const size_t smem = tree_level_smem_bytes(a.nb[l], a.m[l]);
-    if (smem > 48 * 1024) {
-      err = cudaFuncSetAttribute(k_tree_level, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (err != cudaSuccess) return err;
-    }
-    const int m = a.m[l], width = m * m;              // entries of the first elimination step
-    const int threads = width >= 1024 ? 512 : width >= 256 ? 256 : 128;
-    k_tree_level<<<(unsigned)children, threads, smem, s>>>(a, l);
-    err = cudaGetLastError();
-    if (err != cudaSuccess) return err;
-    nodes = children;
-  }
-  switch (a.m[a.grid.L - 1]) {
-    case 2: return launch_leaf<2>(a, s);
-    case 4: return launch_leaf<4>(a, s);
-    case 6: return launch_leaf<6>(a, s);
-    case 8: return launch_leaf<8>(a, s);
-    case 10: return launch_leaf<10>(a, s);
-    case 12: return launch_leaf<12>(a, s);
-    case 14: return launch_leaf<14>(a, s);
-    case 16: return launch_leaf<16>(a, s);
-    default: return cudaErrorInvalidConfiguration;
-  }
+cudaError_t launch_points_tree(const TreeArgs& a, bool fp64, cudaStream_t s) {
+  return fp64 ? launch_tree<ArF64>(a, s) : launch_tree<ArDF>(a, s);
 }
 
 }  // namespace gbsbin

@@ -151,11 +151,13 @@ def test_fock_host_validation(gb):
     assert _fock_status(gb, nodes) == 8                                               # 4^30 nodes
 
 
-def test_tree_kernel_validation(gb):
+@pytest.mark.parametrize("tree", [11, 12], ids=["df32", "fp64"])
+def test_tree_kernel_validation(gb, tree):
     one_group = synth.random_problem(np.random.default_rng(7), 4, 1, 1, 3)
-    assert _status(gb, one_group, tile_override=11) == 8                 # the tree needs L >= 2
+    assert _status(gb, one_group, tile_override=tree) == 8               # the tree needs L >= 2
     big = synth.random_problem(np.random.default_rng(8), 40, 1, 2, 2)    # n = 80 > 64
-    assert _status(gb, big, tile_override=11) == 8
-    assert _status(gb, synth.config(1), tile_override=11, want_backward=True) == 8
-    assert _status(gb, synth.config(1), tile_override=11, shard=(0, 10)) == 8
+    assert _status(gb, big, tile_override=tree) == 8
+    assert _status(gb, synth.config(1), tile_override=tree, want_backward=True) == 8
+    assert _status(gb, synth.config(1), tile_override=tree, shard=(0, 10)) == 8
     assert _status(gb, synth.config(1), tile_override=9) == 1            # a Fock kernel id
+    assert _status(gb, synth.config(1), tile_override=13) == 1           # no such kernel
