@@ -99,22 +99,37 @@ __global__ void k_sum_parts(const double2* parts, long long nparts, double pscal
 }
 
 // out[o, b, s] = sum_{k < R} in[o, k, s] tw[(k b) mod R],  b < nout
+// Indices in 32 bits (every array here has at most GBSBIN_MAX_POINTS entries); the terms
+// are loaded four at a time before their multiply-adds, which keep the order k = 0, 1, ...
 __device__ __forceinline__ void stage_axis(const double2* __restrict__ in, double2* __restrict__ out, long long outer,
                                            int R, int nout, long long inner, const double2* __restrict__ tw,
                                            long long t0, long long stride) {
-  const long long total = outer * nout * inner;
-  for (long long t = t0; t < total; t += stride) {
-    long long s = t % inner;
-    long long rest = t / inner;
-    int b = (int)(rest % nout);
-    long long o = rest / nout;
-    const double2* src = in + o * R * inner + s;
+  const unsigned total = (unsigned)(outer * nout * inner), in32 = (unsigned)inner, nout32 = (unsigned)nout;
+  const unsigned R32 = (unsigned)R;
+  for (unsigned t = (unsigned)t0; t < total; t += (unsigned)stride) {
+    const unsigned rest = t / in32, s = t - rest * in32;
+    const unsigned o = rest / nout32, b = rest - o * nout32;
+    const double2* src = in + (size_t)o * R32 * in32 + s;
     double2 acc = make_double2(0.0, 0.0);
-    int idx = 0;
-    for (int k = 0; k < R; ++k) {
-      acc = cfma2(src[(long long)k * inner], tw[idx], acc);
+    unsigned idx = 0;                                // (k b) mod R, b < R
+    unsigned k = 0;
+    for (; k + 4 <= R32; k += 4) {
+      const unsigned i1 = idx + b >= R32 ? idx + b - R32 : idx + b;
+      const unsigned i2 = i1 + b >= R32 ? i1 + b - R32 : i1 + b;
+      const unsigned i3 = i2 + b >= R32 ? i2 + b - R32 : i2 + b;
+      const double2 v0 = src[(size_t)k * in32], v1 = src[(size_t)(k + 1) * in32];
+      const double2 v2 = src[(size_t)(k + 2) * in32], v3 = src[(size_t)(k + 3) * in32];
+      const double2 w0 = tw[idx], w1 = tw[i1], w2 = tw[i2], w3 = tw[i3];
+      acc = cfma2(v0, w0, acc);
+      acc = cfma2(v1, w1, acc);
+      acc = cfma2(v2, w2, acc);
+      acc = cfma2(v3, w3, acc);
+      idx = i3 + b >= R32 ? i3 + b - R32 : i3 + b;
+    }
+    for (; k < R32; ++k) {
+      acc = cfma2(src[(size_t)k * in32], tw[idx], acc);
       idx += b;
-      if (idx >= R) idx -= R;
+      if (idx >= R32) idx -= R32;
     }
     out[t] = acc;
   }
@@ -136,24 +151,35 @@ __device__ __forceinline__ void stage_last_real(const double2* __restrict__ Y, d
                                                 long long outer, int R, int H, int nout, double scale,
                                                 const double2* __restrict__ tw, long long t0, long long stride,
                                                 DiagAcc* acc_out = nullptr) {
-  const long long total = outer * nout;
-  for (long long t = t0; t < total; t += stride) {
-    int b = (int)(t % nout);
-    long long o = t / nout;
-    const double2* row = Y + o * H;
+  // 32-bit indices and four terms loaded ahead, the sum's order unchanged (as stage_axis)
+  const unsigned total = (unsigned)(outer * nout), nout32 = (unsigned)nout, R32 = (unsigned)R;
+  for (unsigned t = (unsigned)t0; t < total; t += (unsigned)stride) {
+    const unsigned o = t / nout32, b = t - o * nout32;
+    const double2* row = Y + (size_t)o * H;
     if (acc_out && b == 0) {                          // the row's self-conjugate entries
       acc_out->im = fmax(acc_out->im, fabs(row[0].y));
       if ((R & 1) == 0) acc_out->im = fmax(acc_out->im, fabs(row[H - 1].y));
     }
     double acc = row[0].x;
-    int idx = b;
-    if (idx >= R) idx -= R;
-    for (int k = 1; k < H; ++k) {
-      double2 y = row[k], w = tw[idx];
-      double re = fma(y.x, w.x, -y.y * w.y);
-      acc += ((2 * k == R) ? 1.0 : 2.0) * re;
+    unsigned idx = b >= R32 ? b - R32 : b;           // (k b) mod R at k = 1
+    int k = 1;
+    for (; k + 4 <= H; k += 4) {
+      const unsigned i1 = idx + b >= R32 ? idx + b - R32 : idx + b;
+      const unsigned i2 = i1 + b >= R32 ? i1 + b - R32 : i1 + b;
+      const unsigned i3 = i2 + b >= R32 ? i2 + b - R32 : i2 + b;
+      const double2 y0 = row[k], y1 = row[k + 1], y2 = row[k + 2], y3 = row[k + 3];
+      const double2 w0 = tw[idx], w1 = tw[i1], w2 = tw[i2], w3 = tw[i3];
+      acc += ((2 * k == R) ? 1.0 : 2.0) * fma(y0.x, w0.x, -y0.y * w0.y);
+      acc += ((2 * (k + 1) == R) ? 1.0 : 2.0) * fma(y1.x, w1.x, -y1.y * w1.y);
+      acc += ((2 * (k + 2) == R) ? 1.0 : 2.0) * fma(y2.x, w2.x, -y2.y * w2.y);
+      acc += ((2 * (k + 3) == R) ? 1.0 : 2.0) * fma(y3.x, w3.x, -y3.y * w3.y);
+      idx = i3 + b >= R32 ? i3 + b - R32 : i3 + b;
+    }
+    for (; k < H; ++k) {
+      const double2 y = row[k], w = tw[idx];
+      acc += ((2 * k == R) ? 1.0 : 2.0) * fma(y.x, w.x, -y.y * w.y);
       idx += b;
-      if (idx >= R) idx -= R;
+      if (idx >= R32) idx -= R32;
     }
     P[t] = acc * scale;
     if (acc_out) acc_out->sum += acc * scale;
@@ -307,7 +333,7 @@ __device__ __forceinline__ void grid_barrier(unsigned* bar) {
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(128) k_dft_fused(DftFused f) {
+__global__ void __launch_bounds__(128, 4) k_dft_fused(DftFused f) {
   const DftArgs& a = f.a;
   // the CTA's k-th item goes to lane k / 4 of warp k mod 4: a CTA's few items use all
   // four schedulers' FP64 units instead of one warp's
