@@ -11,7 +11,8 @@
 // real).  The transform runs axis by axis in FP64: axes 0..L-2 as complex DFTs on the
 // half array, keeping only the N_l + 1 outputs the table needs, then the last axis as a
 // Hermitian (real-output) transform.  For any partial transform Y along the other axes
-// Y(b', R - k) = conj Y(b', k), so the last axis needs only the stored half.
+// Y(b', R - k) = conj Y(b', k), so the last axis needs only the stored half.  Small grids of
+// three or more axes take a two-phase form with one grid barrier (k_dft_blocked).
 #include <cuda_runtime.h>
 
 #include "gbsbin_internal.h"
@@ -38,49 +39,50 @@ __device__ __forceinline__ double2 finish_logq(const double* f) {
 // point kernel left it unfinished).  A shard's plan evaluated point 0 and its slice
 // [e_lo, e_hi) only: G is zero off the slice, so the transform gives the slice's partial
 // table.  Items t0, t0 + stride, ... of the half grid; l0 = log q_0.
+// G at half-grid point t (see stage_normalise); with ldfin, also stores the finished log q.
+__device__ __forceinline__ double2 normalise_one(const double2* logq, const GridDesc& g, const double* __restrict__ ldfin,
+                                                 double2* logq_fin, double2 l0, long long t) {
+  const bool in_slice = t >= g.e_lo && t < g.e_hi;
+  // this plan's index of half-grid point t (-1: not evaluated here)
+  const long long loc = in_slice ? (g.e_lo > 0 ? t - g.e_lo + 1 : t) : (t == 0 ? 0 : -1);
+  if (loc < 0) return make_double2(0.0, 0.0);
+  double2 v;
+  if (ldfin) {
+    v = finish_logq(ldfin + 6 * loc);
+    logq_fin[loc] = v;
+  } else {
+    v = logq[loc];
+  }
+  if (!in_slice) return make_double2(0.0, 0.0);     // point 0 of a later shard: normalisation only
+  double m = exp(v.x - l0.x);
+  double s, c;
+  sincos(v.y - l0.y, &s, &c);
+  return make_double2(m * c, m * s);
+}
+
 __device__ __forceinline__ void stage_normalise(const double2* logq, const GridDesc& g, double2* __restrict__ G,
                                                 const double* __restrict__ ldfin, double2* logq_fin, double2 l0,
                                                 long long t0, long long stride) {
-  for (long long t = t0; t < g.n_full; t += stride) {
-    const bool in_slice = t >= g.e_lo && t < g.e_hi;
-    // this plan's index of half-grid point t (-1: not evaluated here)
-    const long long loc = in_slice ? (g.e_lo > 0 ? t - g.e_lo + 1 : t) : (t == 0 ? 0 : -1);
-    if (loc < 0) {
-      G[t] = make_double2(0.0, 0.0);
-      continue;
-    }
-    double2 v;
-    if (ldfin) {
-      v = finish_logq(ldfin + 6 * loc);
-      logq_fin[loc] = v;
-    } else {
-      v = logq[loc];
-    }
-    if (!in_slice) {                   // point 0 of a later shard: normalisation only
-      G[t] = make_double2(0.0, 0.0);
-      continue;
-    }
-    double m = exp(v.x - l0.x);
-    double s, c;
-    sincos(v.y - l0.y, &s, &c);
-    G[t] = make_double2(m * c, m * s);
-  }
+  for (long long t = t0; t < g.n_full; t += stride) G[t] = normalise_one(logq, g, ldfin, logq_fin, l0, t);
 }
 
 // G given as partial sums over nparts ranges of some inner sum (Fock inputs: node ranges
 // of the input-side extraction): G[t] = pscale sum_r parts[r n_full + t], r ascending.
+__device__ __forceinline__ double2 sum_parts_one(const double2* __restrict__ parts, long long nparts, double pscale,
+                                                 long long n_full, long long t) {
+  double2 acc = make_double2(0.0, 0.0);
+  for (long long r = 0; r < nparts; ++r) {
+    const double2 v = parts[r * n_full + t];
+    acc.x += v.x;
+    acc.y += v.y;
+  }
+  return make_double2(acc.x * pscale, acc.y * pscale);
+}
+
 __device__ __forceinline__ void stage_sum_parts(const double2* __restrict__ parts, long long nparts, double pscale,
                                                 const GridDesc& g, double2* __restrict__ G, long long t0,
                                                 long long stride) {
-  for (long long t = t0; t < g.n_full; t += stride) {
-    double2 acc = make_double2(0.0, 0.0);
-    for (long long r = 0; r < nparts; ++r) {
-      const double2 v = parts[r * g.n_full + t];
-      acc.x += v.x;
-      acc.y += v.y;
-    }
-    G[t] = make_double2(acc.x * pscale, acc.y * pscale);
-  }
+  for (long long t = t0; t < g.n_full; t += stride) G[t] = sum_parts_one(parts, nparts, pscale, g.n_full, t);
 }
 
 __global__ void k_normalise(const double2* logq, GridDesc g, double2* __restrict__ G,
@@ -448,9 +450,223 @@ cudaError_t launch_finish_logq(const double* ldfin, double2* logq, long long n, 
   return cudaGetLastError();
 }
 
+// ------------------------------------------- small grids: two phases, one grid barrier
+// The separable transform needs a global exchange only between axis sets.  Phase 1: CTA per
+// column c (one combination of the indices of axes h..L-1) gathers G[., c] (the prod_{l<h}
+// R_l entries of the leading axes), runs axes 0..h-1 in shared memory and writes
+// Y[b_0..b_{h-1}, c].  One grid barrier.  Phase 2: CTA per row (one combination of the
+// leading outputs b_0..b_{h-1}) reads its contiguous Y row, runs axes h..L-2 and the
+// Hermitian last axis in shared memory, and writes the table row.  Every entry is summed in
+// the same order as by the axis-by-axis stages (the table is bit-identical to theirs); the
+// grid barriers between the axes inside a phase become block barriers.
+struct DftBlocked {
+  DftArgs a;
+  unsigned* bar;
+  int L, h;
+  int R[GBSBIN_MAX_L], nout[GBSBIN_MAX_L], twoff[GBSBIN_MAX_L];
+  int outer[GBSBIN_MAX_L], inner[GBSBIN_MAX_L];   // per axis, within its phase's block
+  int B1, C1, C2, O2;     // phase-1 block entries, columns; phase-2 rows, last-axis rows per row
+  int H, last_R, last_nout, last_twoff, buf;      // buf: entries per shared buffer
+  double scale;
+};
+
+// out[o, b, s] = sum_k in[o, k, s] tw[(k b) mod R] inside one CTA's shared block
+__device__ __forceinline__ void block_axis(const double2* in, double2* out, int outer, int R, int nout, int inner,
+                                           const double2* __restrict__ tw) {
+  const int total = outer * nout * inner;
+  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    const int rest = t / inner, s = t - rest * inner;
+    const int o = rest / nout, b = rest - o * nout;
+    const double2* src = in + o * R * inner + s;
+    double2 acc = make_double2(0.0, 0.0);
+    int idx = 0;
+    for (int k = 0; k < R; ++k) {
+      acc = cfma2(src[k * inner], tw[idx], acc);
+      idx += b;
+      if (idx >= R) idx -= R;
+    }
+    out[t] = acc;
+  }
+}
+
+__global__ void __launch_bounds__(128) k_dft_blocked(DftBlocked f) {
+  extern __shared__ __align__(16) double2 dsm[];
+  const DftArgs& a = f.a;
+  double2* S0 = dsm;
+  double2* S1 = dsm + f.buf;
+  __shared__ double2 s_l0;
+  if (!a.g_ready && !a.parts) {
+    if (threadIdx.x == 0) s_l0 = a.ldfin ? finish_logq(a.ldfin) : a.logq[0];
+    __syncthreads();
+  }
+  // phase 1: axes 0 .. h-1 per column
+  for (int c = blockIdx.x; c < f.C1; c += gridDim.x) {
+    for (int e = threadIdx.x; e < f.B1; e += blockDim.x) {
+      const long long t = (long long)e * f.C1 + c;
+      S0[e] = a.g_ready ? a.bufA[t]
+              : a.parts ? sum_parts_one(a.parts, a.nparts, a.pscale, a.grid.n_full, t)
+                        : normalise_one(a.logq, a.grid, a.ldfin, a.logq_fin, s_l0, t);
+    }
+    __syncthreads();
+    double2* cur = S0;
+    double2* nxt = S1;
+    for (int l = 0; l < f.h; ++l) {
+      block_axis(cur, nxt, f.outer[l], f.R[l], f.nout[l], f.inner[l], a.tw + f.twoff[l]);
+      __syncthreads();
+      double2* t = cur;
+      cur = nxt;
+      nxt = t;
+    }
+    for (int e = threadIdx.x; e < f.C2; e += blockDim.x) a.bufB[(long long)e * f.C1 + c] = cur[e];
+    __syncthreads();
+  }
+  grid_barrier(f.bar);
+  // phase 2: axes h .. L-2, then the last (Hermitian) axis, per row
+  DiagAcc acc{0.0, 0.0, 1.0e300, 0.0};
+  const int R = f.last_R, H = f.H, nout = f.last_nout;
+  const double2* tw = a.tw + f.last_twoff;
+  for (int r = blockIdx.x; r < f.C2; r += gridDim.x) {
+    for (int e = threadIdx.x; e < f.C1; e += blockDim.x) S0[e] = a.bufB[(long long)r * f.C1 + e];
+    __syncthreads();
+    double2* cur = S0;
+    double2* nxt = S1;
+    for (int l = f.h; l < f.L - 1; ++l) {
+      block_axis(cur, nxt, f.outer[l], f.R[l], f.nout[l], f.inner[l], a.tw + f.twoff[l]);
+      __syncthreads();
+      double2* t = cur;
+      cur = nxt;
+      nxt = t;
+    }
+    double* Prow = a.P + (long long)r * f.O2 * nout;
+    for (int t = threadIdx.x; t < f.O2 * nout; t += blockDim.x) {
+      const int o = t / nout, b = t - o * nout;
+      const double2* row = cur + o * H;
+      if (b == 0) {                                   // the row's self-conjugate entries
+        acc.im = fmax(acc.im, fabs(row[0].y));
+        if ((R & 1) == 0) acc.im = fmax(acc.im, fabs(row[H - 1].y));
+      }
+      double v = row[0].x;
+      int idx = b >= R ? b - R : b;
+      for (int k = 1; k < H; ++k) {
+        const double2 y = row[k], w = tw[idx];
+        v += ((2 * k == R) ? 1.0 : 2.0) * fma(y.x, w.x, -y.y * w.y);
+        idx += b;
+        if (idx >= R) idx -= R;
+      }
+      Prow[t] = v * f.scale;
+      acc.sum += v * f.scale;
+    }
+    __syncthreads();
+  }
+  if (a.diag) {
+    const double2* lq = a.g_ready ? nullptr : a.ldfin ? a.logq_fin : a.logq;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; a.minpiv && e < a.grid.n_eval; e += stride) {
+      const double m = a.minpiv[e];
+      const double2 l = lq ? lq[e] : make_double2(0.0, 0.0);
+      if (!((m > 0.0) && isfinite(l.x) && isfinite(l.y))) acc.bad += 1.0;
+      acc.mn = fmin(acc.mn, m);
+    }
+    block_diag(acc, a.diag, blockIdx.x);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      a.diag[4 * GBSBIN_DIAG_SLOTS] = lq ? lq[0].x : 0.0;
+      a.diag[4 * GBSBIN_DIAG_SLOTS + 1] = (double)*(volatile unsigned*)(f.bar + 2);
+      a.diag[4 * GBSBIN_DIAG_SLOTS + 2] = (double)gridDim.x;
+    }
+  }
+}
+
+// The blocked form where it suits: three or more axes, both phases' blocks within
+// kBlockedMaxEntries, and at least kBlockedMinCtas columns and rows (the split h with the
+// most of both); otherwise 0.
+constexpr int kBlockedMaxEntries = 1024;
+constexpr int kBlockedMinCtas = 32;
+static int blocked_split(const GridDesc& g) {
+  const int L = g.L;
+  if (L < 3) return 0;
+  long long d[GBSBIN_MAX_L];
+  for (int l = 0; l < L - 1; ++l) d[l] = g.radix[l];
+  d[L - 1] = g.half;
+  int best = 0;
+  long long best_min = 0;
+  for (int h = 1; h < L; ++h) {
+    long long B1 = 1, C1 = 1, C2 = 1;
+    for (int l = 0; l < h; ++l) {
+      B1 *= d[l];
+      C2 *= g.nout[l];
+    }
+    for (int l = h; l < L; ++l) C1 *= d[l];
+    if (B1 > kBlockedMaxEntries || C1 > kBlockedMaxEntries) continue;
+    const long long mn = C1 < C2 ? C1 : C2;
+    if (mn >= kBlockedMinCtas && mn > best_min) {
+      best = h;
+      best_min = mn;
+    }
+  }
+  return best;
+}
+
+static cudaError_t launch_dft_blocked(const DftArgs& a, int h, unsigned* bar, int num_sms, cudaStream_t s) {
+  const GridDesc& g = a.grid;
+  const int L = g.L;
+  DftBlocked f{};
+  f.a = a;
+  f.bar = bar;
+  f.L = L;
+  f.h = h;
+  int d[GBSBIN_MAX_L];
+  for (int l = 0; l < L - 1; ++l) d[l] = g.radix[l];
+  d[L - 1] = g.half;
+  int twoff = 0;
+  for (int l = 0; l < L; ++l) {
+    f.R[l] = g.radix[l];
+    f.nout[l] = g.nout[l];
+    f.twoff[l] = twoff;
+    twoff += g.radix[l];
+  }
+  // within phase 1 the block is [axes 0..h-1]; within phase 2 [axes h..L-1]; axes before l
+  // in the block already hold outputs
+  for (int l = 0; l < L - 1; ++l) {
+    const int lo = l < h ? 0 : h, hi = l < h ? h : L;
+    int outer = 1, inner = 1;
+    for (int m = lo; m < l; ++m) outer *= g.nout[m];
+    for (int m = l + 1; m < hi; ++m) inner *= d[m];
+    f.outer[l] = outer;
+    f.inner[l] = inner;
+  }
+  f.B1 = 1;
+  f.C1 = 1;
+  f.C2 = 1;
+  f.O2 = 1;
+  for (int l = 0; l < h; ++l) {
+    f.B1 *= d[l];
+    f.C2 *= g.nout[l];
+  }
+  for (int l = h; l < L; ++l) f.C1 *= d[l];
+  for (int l = h; l < L - 1; ++l) f.O2 *= g.nout[l];
+  f.H = g.half;
+  f.last_R = g.radix[L - 1];
+  f.last_nout = g.nout[L - 1];
+  f.last_twoff = f.twoff[L - 1];
+  f.buf = f.B1 > f.C1 ? f.B1 : f.C1;
+  f.scale = 1.0 / (double)g.npts;
+  const size_t smem = 2 * (size_t)f.buf * sizeof(double2);
+  int per_sm = 0;
+  cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dft_blocked, 128, smem);
+  if (err != cudaSuccess) return err;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  long long blocks = f.C1 > f.C2 ? f.C1 : f.C2;     // one column or row per CTA
+  if (blocks > (long long)per_sm * num_sms) blocks = (long long)per_sm * num_sms;
+  if (blocks > GBSBIN_DIAG_SLOTS) blocks = GBSBIN_DIAG_SLOTS;
+  void* params[] = {&f};
+  return cudaLaunchCooperativeKernel((const void*)k_dft_blocked, dim3((unsigned)blocks), dim3(128), params, smem, s);
+}
+
 cudaError_t launch_dft_fused(const DftArgs& a, unsigned* bar, int num_sms, cudaStream_t s) {
   const GridDesc& g = a.grid;
   const int L = g.L;
+  const int h = blocked_split(g);
+  if (h > 0) return launch_dft_blocked(a, h, bar, num_sms, s);
   DftFused f{};
   f.a = a;
   f.bar = bar;

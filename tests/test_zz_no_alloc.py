@@ -49,3 +49,4 @@ def test_noalloc_rejects_grids_beyond_its_scratch(cuda_lib):
     with pytest.raises(gb.GbsbinError) as e:
         gb.gbsbin_table_from_logq_noalloc([20000], 1, dummy, dummy)      # twiddles > 2^14
     assert e.value.status == 8
+
