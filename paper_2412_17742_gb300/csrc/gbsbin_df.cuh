@@ -146,12 +146,20 @@ struct ArDF {                                        // pairs of FP32 on the FMA
   static __device__ __forceinline__ E csqrt(E a) { return df_csqrt(a); }
   static __device__ __forceinline__ float re(E a) { return a.x; }
   static __device__ __forceinline__ float im(E a) { return a.y; }
+  // mx = 2^(ex - 1) f, f in [1, 2): ex from the exponent bits, the scaling by 2^-ex an exact
+  // multiply (ex in [-99, 100] here); subnormal magnitudes take frexpf/ldexpf
   static __device__ __forceinline__ int normalise(E& a) {
     const float mx = fmaxf(fabsf(a.x), fabsf(a.y));
     if (!(mx > 0.f && mx < 1.0e30f)) return 0;
-    int ex;
-    frexpf(mx, &ex);
-    a = make_float4(ldexpf(a.x, -ex), ldexpf(a.y, -ex), ldexpf(a.z, -ex), ldexpf(a.w, -ex));
+    if (mx < 1.0e-30f) {
+      int ex;
+      frexpf(mx, &ex);
+      a = make_float4(ldexpf(a.x, -ex), ldexpf(a.y, -ex), ldexpf(a.z, -ex), ldexpf(a.w, -ex));
+      return ex;
+    }
+    const int ex = (int)((__float_as_uint(mx) >> 23) & 0xffu) - 126;
+    const float sc = __uint_as_float((unsigned)(127 - ex) << 23);
+    a = make_float4(a.x * sc, a.y * sc, a.z * sc, a.w * sc);
     return ex;
   }
 };
@@ -195,12 +203,19 @@ struct ArF64 {                                       // FP64 throughout
   }
   static __device__ __forceinline__ float re(E a) { return (float)a.x; }
   static __device__ __forceinline__ float im(E a) { return (float)a.y; }
+  // as ArDF::normalise, from the FP64 exponent bits (ex in [-996, 997] here)
   static __device__ __forceinline__ int normalise(E& a) {
     const double mx = ::fmax(::fabs(a.x), ::fabs(a.y));
     if (!(mx > 0.0 && mx < 1.0e300)) return 0;
-    int ex;
-    ::frexp(mx, &ex);
-    a = make_double2(::ldexp(a.x, -ex), ::ldexp(a.y, -ex));
+    if (mx < 1.0e-300) {
+      int ex;
+      ::frexp(mx, &ex);
+      a = make_double2(::ldexp(a.x, -ex), ::ldexp(a.y, -ex));
+      return ex;
+    }
+    const int ex = (int)((__double_as_longlong(mx) >> 52) & 0x7ff) - 1022;
+    const double sc = __longlong_as_double((long long)(1023 - ex) << 52);
+    a = make_double2(a.x * sc, a.y * sc);
     return ex;
   }
 };

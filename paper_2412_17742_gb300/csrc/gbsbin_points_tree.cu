@@ -63,18 +63,6 @@ __device__ __forceinline__ typename Ar::E* elem(float4* p) {
   return reinterpret_cast<typename Ar::E*>(p);
 }
 
-// fold one pivot into a record
-template <class Ar>
-__device__ __forceinline__ void path_pivot(PathRec<typename Ar::E>& pr, typename Ar::E p) {
-  typename Ar::E r = Ar::mul(pr.prod, p);
-  const int ex = Ar::normalise(r);
-  pr.prod = r;
-  const float pre = Ar::re(p), pim = Ar::im(p);
-  float mn = fminf(pr.meta.z, pre);
-  if (!(pre == pre) || !(pim == pim)) mn = -3.0e38f;
-  pr.meta = make_float4(__fadd_rn(pr.meta.x, atan2f(pim, pre)), pr.meta.y + (float)ex, mn, 0.f);
-}
-
 __device__ __forceinline__ float4 shfl(float4 v, int src) {
   return make_float4(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src),
                      __shfl_sync(0xffffffffu, v.z, src), __shfl_sync(0xffffffffu, v.w, src));
@@ -228,8 +216,8 @@ __global__ void __launch_bounds__(LT_MAX) k_tree_level(TreeArgs a, int l) {
 // row r of B = I - w A_leaf and of the right-hand side w c in registers.  Step kk
 // broadcasts row kk from its lane; the rows below subtract their multiple of it (the
 // right-hand side with them), so U and L^-1 (w c) come out together; the back substitution
-// then broadcasts one solution entry per step.  Every lane sees every pivot and keeps the
-// path record; the team's first lane writes the point.
+// then broadcasts one solution entry per step.  Lane r keeps pivot r; the team reduces the
+// path record into its first lane, which writes the point.
 template <class Ar, int NL>
 __global__ void __launch_bounds__(128) k_tree_leaf(TreeArgs a) {
   using E = typename Ar::E;
@@ -257,8 +245,7 @@ __global__ void __launch_bounds__(128) k_tree_leaf(TreeArgs a) {
     y = Ar::mul(w, elem<Ar>(a.c[l])[parent * NL + (live ? r : 0)]);
     u = elem<Ar>(a.u[l])[parent * NL + (live ? r : 0)];
   }
-  PathRec<E> pr = *path_at<Ar>(a.path[l], parent);
-  E myinv = one;
+  E myinv = one, mypiv = one;
   // the step loop stays rolled (an unrolled copy per step overflows the instruction
   // cache); the row stays in registers, entries left of the step skipped by a uniform test
 #pragma unroll 1
@@ -270,9 +257,11 @@ __global__ void __launch_bounds__(128) k_tree_leaf(TreeArgs a) {
       if (j == kk) bk = b[j];
     const E piv = shfl(bk, src);
     const E ykk = shfl(y, src);
-    path_pivot<Ar>(pr, piv);
     const E inv = Ar::recip(piv);
-    if (r == kk) myinv = inv;
+    if (r == kk) {
+      myinv = inv;
+      mypiv = piv;
+    }
     const bool below = r > kk;
     const E li = Ar::mul(bk, inv);                   // used by the rows below only
 #pragma unroll
@@ -282,6 +271,34 @@ __global__ void __launch_bounds__(128) k_tree_leaf(TreeArgs a) {
       if (below) b[j] = Ar::fms(b[j], li, rj);
     }
     if (below) y = Ar::fms(y, li, ykk);
+  }
+  // the path record: lane r holds pivot r; a tree over the team (partner r + o, o = 8, 4,
+  // 2, 1) leaves the product (rescaled by powers of two), the argument sum and the smallest
+  // real part in lane 0, which folds in the parent's record
+  PathRec<E> pr = *path_at<Ar>(a.path[l], parent);
+  {
+    E p = mypiv;
+    const float pre = Ar::re(p), pim = Ar::im(p);
+    float arg = atan2f(pim, pre), mn = pre, e2 = 0.f;
+    if (!(pre == pre) || !(pim == pim)) mn = -3.0e38f;
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) {
+      if (o >= NL) continue;
+      const int partner = (lane + o) & 31;
+      const E q = shfl(p, partner);
+      const float qa = __shfl_sync(0xffffffffu, arg, partner), qm = __shfl_sync(0xffffffffu, mn, partner);
+      const float qe = __shfl_sync(0xffffffffu, e2, partner);
+      if (r + o < NL) {
+        p = Ar::mul(p, q);
+        e2 += qe + (float)Ar::normalise(p);
+        arg = __fadd_rn(arg, qa);
+        mn = fminf(mn, qm);
+      }
+    }
+    E prod = Ar::mul(pr.prod, p);
+    const float e = pr.meta.y + e2 + (float)Ar::normalise(prod);
+    pr.prod = prod;
+    pr.meta = make_float4(__fadd_rn(pr.meta.x, arg), e, fminf(pr.meta.z, mn), 0.f);
   }
   E ex = pr.ex;
   if (a.has_gamma) {                                  // x = U^-1 y, ex += u^T x
