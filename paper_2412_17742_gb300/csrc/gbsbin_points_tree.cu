@@ -79,11 +79,12 @@ __device__ __forceinline__ double2 shfl_xor(double2 v, int mask) {
 }
 
 // The path record after a set of pivots, by one full warp: lane t holds pivot t of the set
-// (count <= 32; lanes beyond hold 1).  Product by a butterfly of pair products (each level
-// rescaled by a power of two), argument sum and smallest real part by butterflies too.
-// pr: the parent's record on input, the child's on output (every lane).
+// (count <= span, a power of two <= 32; lanes beyond hold 1).  Product by a butterfly of
+// pair products over aligned groups of span lanes (each level rescaled by a power of two),
+// argument sum and smallest real part by butterflies too.  pr: the parent's record on
+// input, the child's on output (every lane of the first group; all lanes when span = 32).
 template <class Ar>
-__device__ __forceinline__ void path_warp(PathRec<typename Ar::E>& pr, typename Ar::E piv, bool real) {
+__device__ __forceinline__ void path_warp(PathRec<typename Ar::E>& pr, typename Ar::E piv, bool real, int span) {
   using E = typename Ar::E;
   E p = real ? piv : Ar::one();
   const float pre = Ar::re(piv), pim = Ar::im(piv);
@@ -91,8 +92,7 @@ __device__ __forceinline__ void path_warp(PathRec<typename Ar::E>& pr, typename 
   float mn = real ? pre : 3.0e38f;
   if (real && (!(pre == pre) || !(pim == pim))) mn = -3.0e38f;
   float e2 = 0.f;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
+  for (int o = span >> 1; o > 0; o >>= 1) {
     p = Ar::mul(p, shfl_xor(p, o));
     e2 += __shfl_xor_sync(0xffffffffu, e2, o);
     e2 += (float)Ar::normalise(p);
@@ -117,7 +117,9 @@ __device__ __forceinline__ void path_warp(PathRec<typename Ar::E>& pr, typename 
 // eliminating block 0 from a row [a_0 | a_r] gives a_r - a_0 B^-1 [w A_0r | w c_0].  Rows
 // are never scaled (only the Schur complement is needed): step kk subtracts
 // (G[i][kk] / G[kk][kk]) row kk from every row i > kk: one thread forms the pivot's
-// reciprocal, the rows below their multipliers, then every entry one fused multiply-subtract.
+// reciprocal (every lane of warp 0) and the rows below their multipliers (warp 0), then every
+// entry one fused multiply-subtract.  After the sweep warp 0 forms the child's path record
+// while the other warps copy out the child's matrix and vectors.
 template <class Ar>
 __global__ void __launch_bounds__(LT_MAX) k_tree_level(TreeArgs a, int l) {
   using E = typename Ar::E;
@@ -127,7 +129,6 @@ __global__ void __launch_bounds__(LT_MAX) k_tree_level(TreeArgs a, int l) {
   E* G = reinterpret_cast<E*>(gsm_raw);              // rows x cols
   E* pv = G + (size_t)rows * cols;                   // nb pivots
   E* Lm = pv + nb;                                   // rows: multipliers of the current step
-  __shared__ E s_inv[1];
   const long long child = blockIdx.x;
   const int R = a.grid.radix[l];
   const long long parent = child / R;
@@ -159,14 +160,12 @@ __global__ void __launch_bounds__(LT_MAX) k_tree_level(TreeArgs a, int l) {
   }
   for (int kk = 0; kk < nb; ++kk) {
     __syncthreads();                                 // row kk final
-    if (tid == 0) {
-      const E piv = G[kk * cols + kk];
-      pv[kk] = piv;
-      s_inv[0] = Ar::recip(piv);
+    if (tid < 32) {                                  // warp 0: the pivot's reciprocal (every
+      const E piv = G[kk * cols + kk];               // lane) and the rows' multipliers
+      if (tid == 0) pv[kk] = piv;
+      const E r = Ar::recip(piv);
+      for (int i = kk + 1 + tid; i < rows; i += 32) Lm[i] = Ar::mul(G[i * cols + kk], r);
     }
-    __syncthreads();
-    const E r = s_inv[0];
-    for (int i = kk + 1 + tid; i < rows; i += LT) Lm[i] = Ar::mul(G[i * cols + kk], r);
     __syncthreads();
     // entries (i, s), i in (kk, rows), s in (kk, cols); two independent entries per pass.
     // floor(idx / w_) from a float reciprocal: idx < 2^14 and w_ <= 65, so (idx + 1/2) / w_
@@ -187,24 +186,28 @@ __global__ void __launch_bounds__(LT_MAX) k_tree_level(TreeArgs a, int l) {
     }
   }
   __syncthreads();
-  E* Ac = elem<Ar>(a.A[l + 1]) + child * (long long)mc * mc;
-  for (int idx = tid; idx < mc * mc; idx += LT) {
-    const int i = idx / mc, j = idx - (idx / mc) * mc;
-    Ac[idx] = G[(nb + i) * cols + nb + j];
-  }
-  if (a.has_gamma) {
-    E* cc = elem<Ar>(a.c[l + 1]) + child * (long long)mc;
-    E* uc = elem<Ar>(a.u[l + 1]) + child * (long long)mc;
-    for (int j = tid; j < mc; j += LT) {
-      cc[j] = G[(nb + j) * cols + m];
-      uc[j] = G[m * cols + nb + j];
+  if (tid >= 32) {                                   // the child's A', c', u' (warps 1..)
+    const int t = tid - 32, LO = LT - 32;
+    E* Ac = elem<Ar>(a.A[l + 1]) + child * (long long)mc * mc;
+    for (int idx = t; idx < mc * mc; idx += LO) {
+      const int i = idx / mc, j = idx - (idx / mc) * mc;
+      Ac[idx] = G[(nb + i) * cols + nb + j];
     }
-  }
-  if (tid < 32) {                                    // the child's path record (warp 0)
+    if (a.has_gamma) {
+      E* cc = elem<Ar>(a.c[l + 1]) + child * (long long)mc;
+      E* uc = elem<Ar>(a.u[l + 1]) + child * (long long)mc;
+      for (int j = t; j < mc; j += LO) {
+        cc[j] = G[(nb + j) * cols + m];
+        uc[j] = G[m * cols + nb + j];
+      }
+    }
+  } else {                                           // the child's path record (warp 0)
     PathRec<E> pr = *path_at<Ar>(a.path[l], parent);
+    int span = 1;                                    // butterfly over the pivots' lanes only
+    while (span < nb && span < 32) span <<= 1;
     for (int t0 = 0; t0 < nb; t0 += 32) {
       const int t = t0 + tid;
-      path_warp<Ar>(pr, t < nb ? pv[t] : zero, t < nb);
+      path_warp<Ar>(pr, t < nb ? pv[t] : zero, t < nb, span);
     }
     if (a.has_gamma) pr.ex = Ar::add(pr.ex, G[m * cols + m]);
     if (tid == 0) *path_at<Ar>(a.path[l + 1], child) = pr;
