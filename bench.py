@@ -277,9 +277,10 @@ def main():
     host_out = torch.empty(plans[1].shape, dtype=torch.float64).pin_memory()
     args_prob = gb.ProblemArgs(prob)
     n = prob.n
-    h2d = n * n * (16 + 8 + 8 + 16) + n * (16 + 16 + 4 * 8)
     if plans[1].diagnostics(stream)[1]["kernel_name"] == "tree_df32":
-        h2d += (n * n + 2 * n + 3) * 16     # the permuted state as FP32 pairs
+        h2d = (n * n + 2 * n + 3) * 16      # tree plans upload their permuted state (FP32 pairs) alone
+    else:
+        h2d = n * n * (16 + 8 + 8 + 16) + n * (16 + 16 + 4 * 8)
     d2h = int(np.prod(plans[1].shape)) * 8
     for _ in range(3):
         gb.gbsbin_plan_set_state(plans[1].handle, args_prob, stream)

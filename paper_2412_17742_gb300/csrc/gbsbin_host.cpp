@@ -135,20 +135,42 @@ int physical_state(const gbsbin_problem* p, std::vector<cd>& S1, std::vector<cd>
     nn[q] = sh * sh;
     mm[q] = sh * ch;
   }
-  // N_out[a][b] = sum_q conj(Tf[a][q]) n_q Tf[b][q];  Mm_out[a][b] = sum_q Tf[a][q] m_q Tf[b][q]
+  // N_out[a][b] = sum_q conj(Tf[a][q]) n_q Tf[b][q] (Hermitian), Mm_out[a][b] = sum_q
+  // Tf[a][q] m_q Tf[b][q] (symmetric): the b >= a half, on split real/imaginary rows
+  std::vector<double> tr((size_t)MK * MK), ti((size_t)MK * MK), nr((size_t)MK * MK), ni((size_t)MK * MK),
+      mr((size_t)MK * MK), mi((size_t)MK * MK);
+  for (size_t q = 0; q < (size_t)MK * MK; ++q) {
+    const double w_n = nn[q % MK], w_m = mm[q % MK];
+    tr[q] = Tf[q].real();
+    ti[q] = Tf[q].imag();
+    nr[q] = tr[q] * w_n;                            // conj(Tf) n
+    ni[q] = -ti[q] * w_n;
+    mr[q] = tr[q] * w_m;                            // Tf m
+    mi[q] = ti[q] * w_m;
+  }
   S1.assign((size_t)n * n, 0.0);
   for (int a = 0; a < MK; ++a)
-    for (int b = 0; b < MK; ++b) {
-      cd N = 0.0, Mo = 0.0;
+    for (int b = a; b < MK; ++b) {
+      const double *ar = &nr[(size_t)a * MK], *ai = &ni[(size_t)a * MK], *br = &tr[(size_t)b * MK],
+                   *bi = &ti[(size_t)b * MK], *cr = &mr[(size_t)a * MK], *ci = &mi[(size_t)a * MK];
+      double Nr = 0.0, Ni = 0.0, Mr = 0.0, Mi = 0.0;
       for (int q = 0; q < MK; ++q) {
-        cd ta = Tf[(size_t)a * MK + q], tb = Tf[(size_t)b * MK + q];
-        N += std::conj(ta) * nn[q] * tb;
-        Mo += ta * mm[q] * tb;
+        Nr += ar[q] * br[q] - ai[q] * bi[q];
+        Ni += ar[q] * bi[q] + ai[q] * br[q];
+        Mr += cr[q] * br[q] - ci[q] * bi[q];
+        Mi += cr[q] * bi[q] + ci[q] * br[q];
       }
+      const cd N(Nr, Ni), Mo(Mr, Mi);
       S1[(size_t)b * n + a] = N;                     // top-left: N^T
       S1[(size_t)a * n + (MK + b)] = Mo;             // top-right: Mm
       S1[(size_t)(MK + a) * n + b] = std::conj(Mo);  // bottom-left: Mm^*
       S1[(size_t)(MK + a) * n + (MK + b)] = N;       // bottom-right: N
+      if (b != a) {                                  // (b, a): conj(N), Mo
+        S1[(size_t)a * n + b] = std::conj(N);
+        S1[(size_t)b * n + (MK + a)] = Mo;
+        S1[(size_t)(MK + b) * n + a] = std::conj(Mo);
+        S1[(size_t)(MK + b) * n + (MK + a)] = std::conj(N);
+      }
     }
   zbar.assign(n, 0.0);
   if (p->alpha) {
@@ -162,18 +184,29 @@ int physical_state(const gbsbin_problem* p, std::vector<cd>& S1, std::vector<cd>
   return GBSBIN_OK;
 }
 
-// In-place Cholesky of a Hermitian matrix (lower factor); false if not positive definite.
-bool cholesky(std::vector<cd>& A, int n) {
+// In-place Cholesky of a Hermitian matrix (lower factor) held as split real / imaginary
+// row-major arrays; false if not positive definite.  Row j of L: L_jj = sqrt(A_jj -
+// sum_k |L_jk|^2), L_ij = (A_ij - sum_k L_ik conj(L_jk)) / L_jj, k < j (contiguous in k).
+bool cholesky(std::vector<double>& re, std::vector<double>& im, int n) {
   for (int j = 0; j < n; ++j) {
-    double d = A[(size_t)j * n + j].real();
-    for (int k = 0; k < j; ++k) d -= std::norm(A[(size_t)j * n + k]);
+    const double* rj = &re[(size_t)j * n];
+    const double* ij = &im[(size_t)j * n];
+    double d = rj[j];
+    for (int k = 0; k < j; ++k) d -= rj[k] * rj[k] + ij[k] * ij[k];
     if (!(d > 0.0) || !std::isfinite(d)) return false;
-    double ljj = std::sqrt(d);
-    A[(size_t)j * n + j] = ljj;
+    const double ljj = std::sqrt(d);
+    re[(size_t)j * n + j] = ljj;
+    im[(size_t)j * n + j] = 0.0;
     for (int i = j + 1; i < n; ++i) {
-      cd s = A[(size_t)i * n + j];
-      for (int k = 0; k < j; ++k) s -= A[(size_t)i * n + k] * std::conj(A[(size_t)j * n + k]);
-      A[(size_t)i * n + j] = s / ljj;
+      double* ri = &re[(size_t)i * n];
+      double* ii = &im[(size_t)i * n];
+      double sr = ri[j], si = ii[j];
+      for (int k = 0; k < j; ++k) {
+        sr -= ri[k] * rj[k] + ii[k] * ij[k];
+        si -= ii[k] * rj[k] - ri[k] * ij[k];
+      }
+      ri[j] = sr / ljj;
+      ii[j] = si / ljj;
     }
   }
   return true;
@@ -182,38 +215,72 @@ bool cholesky(std::vector<cd>& A, int n) {
 // XA = I - Sigma^{-1}, Xgamma = Sigma^{-1} z-bar, gamma = X Xgamma, Sigma = I + Sigma^(1).
 int adjacency(const std::vector<cd>& S1, const std::vector<cd>& zbar, int n, std::vector<cd>& XA,
               std::vector<cd>& gamma, std::vector<cd>& Xgamma) {
-  double scale = 1.0;
+  double scale2 = 1.0;                               // running max of |a|^2 (squares compared)
   for (int i = 0; i < n; ++i)
     for (int j = 0; j < n; ++j) {
       cd a = S1[(size_t)i * n + j], b = S1[(size_t)j * n + i];
       if (!std::isfinite(a.real()) || !std::isfinite(a.imag())) return GBSBIN_ERR_ARG;
-      scale = std::fmax(scale, std::abs(a));
-      if (std::abs(a - std::conj(b)) > kHermTol * scale) return GBSBIN_ERR_NONPHYSICAL;
+      scale2 = std::fmax(scale2, std::norm(a));
+      if (std::norm(a - std::conj(b)) > kHermTol * kHermTol * scale2) return GBSBIN_ERR_NONPHYSICAL;
     }
   // physicality: Sigma - I/2 = Sigma^(1) + I/2 positive definite <=> ||I - Sigma^{-1}|| < 1
-  std::vector<cd> C(S1);
-  for (int i = 0; i < n; ++i) C[(size_t)i * n + i] += 0.5;
-  if (!cholesky(C, n)) return GBSBIN_ERR_NONPHYSICAL;
+  const size_t nn = (size_t)n * n;
+  std::vector<double> cr(nn), ci(nn);
+  for (size_t q = 0; q < nn; ++q) {
+    cr[q] = S1[q].real();
+    ci[q] = S1[q].imag();
+  }
+  for (int i = 0; i < n; ++i) cr[(size_t)i * n + i] += 0.5;
+  if (!cholesky(cr, ci, n)) return GBSBIN_ERR_NONPHYSICAL;
   // Sigma = C C^H; Sigma^{-1} = C^{-H} C^{-1}
-  C = S1;
-  for (int i = 0; i < n; ++i) C[(size_t)i * n + i] += 1.0;
-  if (!cholesky(C, n)) return GBSBIN_ERR_NONPHYSICAL;
-  std::vector<cd> Ci((size_t)n * n, 0.0);  // C^{-1}, lower triangular
-  for (int j = 0; j < n; ++j) {
-    Ci[(size_t)j * n + j] = 1.0 / C[(size_t)j * n + j];
-    for (int i = j + 1; i < n; ++i) {
-      cd s = 0.0;
-      for (int k = j; k < i; ++k) s += C[(size_t)i * n + k] * Ci[(size_t)k * n + j];
-      Ci[(size_t)i * n + j] = -s / C[(size_t)i * n + i];
+  for (size_t q = 0; q < nn; ++q) {
+    cr[q] = S1[q].real();
+    ci[q] = S1[q].imag();
+  }
+  for (int i = 0; i < n; ++i) cr[(size_t)i * n + i] += 1.0;
+  if (!cholesky(cr, ci, n)) return GBSBIN_ERR_NONPHYSICAL;
+  // X = C^{-1} (lower triangular) row by row: C_ii X_i. = e_i - sum_{k<i} C_ik X_k.
+  std::vector<double> xr(nn, 0.0), xi(nn, 0.0);
+  for (int i = 0; i < n; ++i) {
+    double* ri = &xr[(size_t)i * n];
+    double* ii = &xi[(size_t)i * n];
+    for (int k = 0; k < i; ++k) {
+      const double a = cr[(size_t)i * n + k], b = ci[(size_t)i * n + k];
+      const double* rk = &xr[(size_t)k * n];
+      const double* ik = &xi[(size_t)k * n];
+      for (int j = 0; j <= k; ++j) {
+        ri[j] -= a * rk[j] - b * ik[j];
+        ii[j] -= a * ik[j] + b * rk[j];
+      }
+    }
+    const double cii = cr[(size_t)i * n + i];
+    for (int j = 0; j < i; ++j) {
+      ri[j] /= cii;
+      ii[j] /= cii;
+    }
+    ri[i] = 1.0 / cii;
+  }
+  // S = X^H X (lower half) as a sum over k of rows: S_ij += conj(X_ki) X_kj, j <= i <= k
+  std::vector<double> sr(nn, 0.0), si(nn, 0.0);
+  for (int k = 0; k < n; ++k) {
+    const double* rk = &xr[(size_t)k * n];
+    const double* ik = &xi[(size_t)k * n];
+    for (int i = 0; i <= k; ++i) {
+      const double a = rk[i], b = -ik[i];
+      double* ri = &sr[(size_t)i * n];
+      double* ii = &si[(size_t)i * n];
+      for (int j = 0; j <= i; ++j) {
+        ri[j] += a * rk[j] - b * ik[j];
+        ii[j] += a * ik[j] + b * rk[j];
+      }
     }
   }
-  XA.assign((size_t)n * n, 0.0);
+  XA.assign(nn, 0.0);
   for (int i = 0; i < n; ++i)
     for (int j = 0; j <= i; ++j) {
-      cd s = 0.0;  // (C^{-H} C^{-1})_ij = sum_k conj(Ci[k][i]) Ci[k][j], k >= max(i, j) = i
-      for (int k = i; k < n; ++k) s += std::conj(Ci[(size_t)k * n + i]) * Ci[(size_t)k * n + j];
-      XA[(size_t)i * n + j] = (i == j ? 1.0 : 0.0) - s;
-      if (i != j) XA[(size_t)j * n + i] = -std::conj(s);
+      const cd v(sr[(size_t)i * n + j], si[(size_t)i * n + j]);
+      XA[(size_t)i * n + j] = (i == j ? 1.0 : 0.0) - v;
+      if (i != j) XA[(size_t)j * n + i] = -std::conj(v);
     }
   Xgamma.assign(n, 0.0);
   gamma.assign(n, 0.0);
@@ -337,14 +404,15 @@ int upload_state(gbsbin_plan* P, cudaStream_t stream) {
   float2* ghi = (float2*)(h + s.off_ghi);
   float2* glo = (float2*)(h + s.off_glo);
   longlong2* XAfix = (longlong2*)(h + s.off_XAfix);
-  for (size_t q = 0; q < (size_t)n * n; ++q) {  // the kernels use -XA
+  // the per-point kernels' copies of the state (tree plans read only their own region)
+  const double fix_scale = std::ldexp(1.0, GBSBIN_FIX_BITS);
+  for (size_t q = 0; !tree && q < (size_t)n * n; ++q) {  // the kernels use -XA
     XA[q] = make_double2(-P->XA[q].real(), -P->XA[q].imag());
     split(-P->XA[q], &XAhi[q], &XAlo[q]);
     // |XA_ij| <= ||XA||_2 < 1 for a physical state, so the scaled value fits in 63 bits
-    XAfix[q] = make_longlong2(std::llrint(std::ldexp(-P->XA[q].real(), GBSBIN_FIX_BITS)),
-                              std::llrint(std::ldexp(-P->XA[q].imag(), GBSBIN_FIX_BITS)));
+    XAfix[q] = make_longlong2(std::llrint(-P->XA[q].real() * fix_scale), std::llrint(-P->XA[q].imag() * fix_scale));
   }
-  for (int i = 0; i < n; ++i) {
+  for (int i = 0; !tree && i < n; ++i) {
     g[i] = make_double2(P->gamma[i].real(), P->gamma[i].imag());
     Xg[i] = make_double2(P->Xgamma[i].real(), P->Xgamma[i].imag());
     split(P->Xgamma[i], &Xghi[i], &Xglo[i]);
@@ -377,23 +445,36 @@ int upload_state(gbsbin_plan* P, cudaStream_t stream) {
     // product p0 2^e0, argument and winding (each pivot has Re > 0)
     P->tree_g = !P->has_gamma;
     if (P->tree_g) {
-      std::vector<cd> K((size_t)n * n);
+      // split real / imaginary rows; each pivot's reciprocal once, rows updated contiguously
+      std::vector<double> kr((size_t)n * n), ki((size_t)n * n);
       for (int i = 0; i < n; ++i)
-        for (int j = 0; j < n; ++j) K[(size_t)i * n + j] = (i == j ? 1.0 : 0.0) - P->XA[(size_t)pm[i] * n + pm[j]];
+        for (int j = 0; j < n; ++j) {
+          const cd v = (i == j ? 1.0 : 0.0) - P->XA[(size_t)pm[i] * n + pm[j]];
+          kr[(size_t)i * n + j] = v.real();
+          ki[(size_t)i * n + j] = v.imag();
+        }
       cd prod = 1.0;
       int e0 = 0;
       double args = 0.0;
       for (int k = 0; k < n; ++k) {
-        const cd piv = K[(size_t)k * n + k];
+        const cd piv(kr[(size_t)k * n + k], ki[(size_t)k * n + k]);
         prod *= piv;
         int ex;
         std::frexp(std::max(std::fabs(prod.real()), std::fabs(prod.imag())), &ex);
         prod = cd(std::ldexp(prod.real(), -ex), std::ldexp(prod.imag(), -ex));
         e0 += ex;
         args += std::atan2(piv.imag(), piv.real());
+        const double d = std::norm(piv), pr = piv.real() / d, pi = -piv.imag() / d;   // 1 / piv
+        const double* rk = &kr[(size_t)k * n];
+        const double* ik = &ki[(size_t)k * n];
         for (int i = k + 1; i < n; ++i) {
-          const cd li = K[(size_t)i * n + k] / piv;
-          for (int j = k + 1; j < n; ++j) K[(size_t)i * n + j] -= li * K[(size_t)k * n + j];
+          double* ri = &kr[(size_t)i * n];
+          double* ii = &ki[(size_t)i * n];
+          const double lr = ri[k] * pr - ii[k] * pi, lim = ri[k] * pi + ii[k] * pr;
+          for (int j = k + 1; j < n; ++j) {
+            ri[j] -= lr * rk[j] - lim * ik[j];
+            ii[j] -= lr * ik[j] + lim * rk[j];
+          }
         }
       }
       const double TWO_PI = 6.283185307179586476925286766559;
@@ -406,8 +487,9 @@ int upload_state(gbsbin_plan* P, cudaStream_t stream) {
       P->tree_logq0 = -0.5 * (std::log(std::abs(prod)) + e0 * 0.693147180559945309417232121458);
     }
   }
-  // the device block has the staging layout: one copy
-  e = cudaMemcpyAsync(P->d_state, h, s.total, cudaMemcpyHostToDevice, stream);
+  // the device block has the staging layout: one copy (of the tree region alone for trees)
+  const size_t off = tree ? s.off_tree : 0;
+  e = cudaMemcpyAsync(P->d_state + off, h + off, s.total - off, cudaMemcpyHostToDevice, stream);
   if (e != cudaSuccess) return GBSBIN_ERR_CUDA;
   if (P->kernel == GBSBIN_KERNEL_HESS_FP64) return upload_hessenberg(P, stream);
   return GBSBIN_OK;
