@@ -183,7 +183,10 @@ int gbsbin_plan_create(const gbsbin_problem* p, const gbsbin_options* o, gbsbin_
 /*
  * Replace the state of an existing plan (same M, K, L, cutoffs and grouping; new r, T,
  * alpha, V or sigma1/zbar): redo the host FP64 algebra and enqueue the upload on
- * `stream`.  Same errors as plan_create; ERR_ARG if a shape differs.
+ * `stream`, ordered after the work already enqueued there.  The plan stages uploads in two
+ * pinned buffers used in turn, so the call waits only for the upload two calls back, not
+ * for the stream: the host algebra of the next state overlaps the device work of the
+ * current one.  Same errors as plan_create; ERR_ARG if a shape differs.
  */
 int gbsbin_plan_set_state(gbsbin_plan* plan, const gbsbin_problem* p, void* stream);
 
@@ -205,6 +208,15 @@ int gbsbin_execute(gbsbin_plan* plan, double* P_out, void* stream);
  * on `stream` and the call synchronises it before returning.
  */
 int gbsbin_execute_host(gbsbin_plan* plan, double* P_out_host, void* stream);
+
+/*
+ * As gbsbin_execute_host without the final synchronisation: the execute and the
+ * device-to-host copy are enqueued on `stream` and the call returns.  P_out_host (pinned
+ * memory for an asynchronous copy) holds the table once the stream has reached the copy;
+ * the caller synchronises before reading it and must not reuse it for a later call until
+ * then.  Errors as gbsbin_execute, ERR_ARG for a null pointer.
+ */
+int gbsbin_execute_host_async(gbsbin_plan* plan, double* P_out_host, void* stream);
 
 /*
  * Diagnostics of the last execute on this plan.  Synchronises `stream`.  Returns

@@ -27,7 +27,8 @@ KERNELS = {1: "smem_fp64", 2: "smem_fp32r", 3: "gmem_fp64", 4: "gmem_fp32r", 5: 
            7: "blk_tc_fp32r", 8: "hess_fp64", 9: "fock_fp64", 10: "fock_df32",
            11: "tree_df32", 12: "tree_fp64"}
 EXPORTED = ["gbsbin_default_options", "gbsbin_plan_create", "gbsbin_plan_set_state", "gbsbin_plan_destroy",
-            "gbsbin_plan_table_size", "gbsbin_execute", "gbsbin_execute_host", "gbsbin_diagnostics",
+            "gbsbin_plan_table_size", "gbsbin_execute", "gbsbin_execute_host", "gbsbin_execute_host_async",
+            "gbsbin_diagnostics",
             "gbsbin_strerror", "gbsbin_alu_peak", "gbsbin_read_points", "gbsbin_table_from_logq_noalloc",
             "gbsbin_backward", "gbsbin_autotune", "gbsbin_batch_create", "gbsbin_batch_execute",
             "gbsbin_batch_capture_graph", "gbsbin_batch_replay", "gbsbin_batch_table_size",
@@ -100,6 +101,7 @@ def load():
     lib.gbsbin_plan_table_size.restype = ctypes.c_longlong
     lib.gbsbin_execute.argtypes = [vp, vp, vp]
     lib.gbsbin_execute_host.argtypes = [vp, vp, vp]
+    lib.gbsbin_execute_host_async.argtypes = [vp, vp, vp]
     lib.gbsbin_diagnostics.argtypes = [vp, ctypes.POINTER(gbsbin_diag), vp]
     lib.gbsbin_strerror.argtypes = [ctypes.c_int]
     lib.gbsbin_strerror.restype = ctypes.c_char_p
@@ -133,7 +135,8 @@ def load():
     lib.gbsbin_fock_diagnostics.argtypes = [vp, ctypes.POINTER(gbsbin_diag), vp]
     lib.gbsbin_fock_plan_destroy.argtypes = [vp]
     for f in ("gbsbin_plan_create", "gbsbin_plan_set_state", "gbsbin_plan_destroy", "gbsbin_execute",
-              "gbsbin_execute_host", "gbsbin_diagnostics", "gbsbin_alu_peak", "gbsbin_read_points",
+              "gbsbin_execute_host", "gbsbin_execute_host_async", "gbsbin_diagnostics", "gbsbin_alu_peak",
+              "gbsbin_read_points",
               "gbsbin_table_from_logq_noalloc", "gbsbin_backward", "gbsbin_autotune", "gbsbin_batch_create",
               "gbsbin_batch_execute", "gbsbin_batch_capture_graph", "gbsbin_batch_replay",
               "gbsbin_batch_diagnostics", "gbsbin_batch_read_points", "gbsbin_batch_destroy",
@@ -245,6 +248,13 @@ def gbsbin_execute(plan, P_out, stream=None):
 def gbsbin_execute_host(plan, P_out_host, stream=None):
     """P_out_host: host float64 buffer (numpy array, pinned torch tensor or pointer)."""
     _check(load().gbsbin_execute_host(plan, _ptr(P_out_host), _stream_handle(stream)), "gbsbin_execute_host")
+
+
+def gbsbin_execute_host_async(plan, P_out_host, stream=None):
+    """Enqueue the execute and the copy into P_out_host (pinned host buffer) and return;
+    synchronise the stream before reading P_out_host."""
+    _check(load().gbsbin_execute_host_async(plan, _ptr(P_out_host), _stream_handle(stream)),
+           "gbsbin_execute_host_async")
 
 
 def gbsbin_diagnostics(plan, stream=None):

@@ -66,7 +66,11 @@ struct gbsbin_plan {
   bool saved_valid = false;           // d_lu / d_xs hold the current state's factors
   long long bws_slot_bytes = 0;       // per-SM slot of d_bws (reverse pass and FP64 workspace)
   // pinned staging for uploads
-  void* h_stage = nullptr;
+  // two pinned staging buffers used in turn, each with the event recorded after the copy
+  // that last read it: an upload waits only for the copy two uploads back
+  void* h_stage[2] = {nullptr, nullptr};
+  cudaEvent_t ev_stage[2] = {nullptr, nullptr};
+  int stage_next = 0;
   size_t h_stage_bytes = 0;
 };
 
@@ -324,7 +328,10 @@ void free_device(gbsbin_plan* P) {
                   P->d_diag,  P->d_gws,   P->d_table, P->d_ldfin,  P->d_bar,  P->d_H,    P->d_tree};
   for (void* q : ptrs)
     if (q) cudaFree(q);
-  if (P->h_stage) cudaFreeHost(P->h_stage);
+  for (int b = 0; b < 2; ++b) {
+    if (P->h_stage[b]) cudaFreeHost(P->h_stage[b]);
+    if (P->ev_stage[b]) cudaEventDestroy(P->ev_stage[b]);
+  }
   if (P->ev0) cudaEventDestroy(P->ev0);
   if (P->ev1) cudaEventDestroy(P->ev1);
   void* bw[] = {P->d_lu, P->d_xs, P->d_adjA, P->d_adjB, P->d_bws, P->d_partS, P->d_partg, P->d_outS, P->d_outg};
@@ -390,10 +397,12 @@ int upload_state(gbsbin_plan* P, cudaStream_t stream) {
   const int n = P->n;
   const bool tree = is_tree(P->kernel);
   Stage s = stage_layout(n, tree);
-  // a previous upload may still be reading the staging buffer
-  cudaError_t e = cudaStreamSynchronize(stream);
+  // the copy that last read this staging buffer (two uploads back) must have finished
+  const int sb = P->stage_next;
+  P->stage_next ^= 1;
+  cudaError_t e = cudaEventSynchronize(P->ev_stage[sb]);
   if (e != cudaSuccess) return GBSBIN_ERR_CUDA;
-  char* h = (char*)P->h_stage;
+  char* h = (char*)P->h_stage[sb];
   double2* XA = (double2*)(h + s.off_XA);
   double2* g = (double2*)(h + s.off_g);
   double2* Xg = (double2*)(h + s.off_Xg);
@@ -490,7 +499,7 @@ int upload_state(gbsbin_plan* P, cudaStream_t stream) {
   // the device block has the staging layout: one copy (of the tree region alone for trees)
   const size_t off = tree ? s.off_tree : 0;
   e = cudaMemcpyAsync(P->d_state + off, h + off, s.total - off, cudaMemcpyHostToDevice, stream);
-  if (e != cudaSuccess) return GBSBIN_ERR_CUDA;
+  if (e != cudaSuccess || cudaEventRecord(P->ev_stage[sb], stream) != cudaSuccess) return GBSBIN_ERR_CUDA;
   if (P->kernel == GBSBIN_KERNEL_HESS_FP64) return upload_hessenberg(P, stream);
   return GBSBIN_OK;
 }
@@ -923,11 +932,19 @@ static int plan_create_impl(const gbsbin_problem* p, const gbsbin_options* o, gb
       return e == cudaErrorMemoryAllocation ? GBSBIN_ERR_NOMEM : GBSBIN_ERR_CUDA;
     }
   }
-  if (cudaMallocHost(&P->h_stage, sl.total) != cudaSuccess) {
-    cudaGetLastError();
-    free_device(P);
-    delete P;
-    return GBSBIN_ERR_NOMEM;
+  for (int b = 0; b < 2; ++b) {
+    if (cudaMallocHost(&P->h_stage[b], sl.total) != cudaSuccess) {
+      cudaGetLastError();
+      free_device(P);
+      delete P;
+      return GBSBIN_ERR_NOMEM;
+    }
+    if (cudaEventCreateWithFlags(&P->ev_stage[b], cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      free_device(P);
+      delete P;
+      return GBSBIN_ERR_CUDA;
+    }
   }
   P->h_stage_bytes = sl.total;
   if (opt.want_backward) {
@@ -1093,14 +1110,19 @@ int gbsbin_execute(gbsbin_plan* P, double* P_out, void* stream) {
   return e == cudaSuccess ? GBSBIN_OK : GBSBIN_ERR_CUDA;
 }
 
-int gbsbin_execute_host(gbsbin_plan* P, double* P_out_host, void* stream) {
+int gbsbin_execute_host_async(gbsbin_plan* P, double* P_out_host, void* stream) {
   if (!P || !P_out_host) return GBSBIN_ERR_ARG;
-  cudaStream_t s = (cudaStream_t)stream;
   int st = gbsbin_execute(P, P->d_table, stream);
   if (!st && cudaMemcpyAsync(P_out_host, P->d_table, (size_t)P->table_size * sizeof(double),
-                             cudaMemcpyDeviceToHost, s) != cudaSuccess)
+                             cudaMemcpyDeviceToHost, (cudaStream_t)stream) != cudaSuccess)
     st = GBSBIN_ERR_CUDA;
-  if (cudaStreamSynchronize(s) != cudaSuccess && !st) st = GBSBIN_ERR_CUDA;
+  return st;
+}
+
+int gbsbin_execute_host(gbsbin_plan* P, double* P_out_host, void* stream) {
+  int st = gbsbin_execute_host_async(P, P_out_host, stream);
+  if (st == GBSBIN_ERR_ARG) return st;
+  if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess && !st) st = GBSBIN_ERR_CUDA;
   return st;
 }
 

@@ -195,6 +195,42 @@ def test_execute_host_matches_device(cuda_lib):
     assert np.array_equal(Pd.reshape(-1), Ph)
 
 
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "fp32r"])
+def test_pipelined_state_changes(cuda_lib, precision):
+    # set_state + execute_host_async over alternating states into two pinned buffers with
+    # one synchronisation per pair: every table equals the synchronous one of its state
+    # (the two staging buffers let an upload proceed while the previous table is computed)
+    import torch
+    gb = cuda_lib
+    probs = [synth.config(1), synth.config(1), synth.config(1)]
+    probs[1].r = probs[1].r * 0.9
+    probs[2].r = probs[2].r * 1.05
+    args = [gb.ProblemArgs(q) for q in probs]
+    with gb.Plan(probs[0], precision=precision) as p:
+        ts = gb.gbsbin_plan_table_size(p.handle)
+        sync = []
+        for a in args:
+            gb.gbsbin_plan_set_state(p.handle, a)
+            out = np.zeros(ts)
+            gb.gbsbin_execute_host(p.handle, out)
+            sync.append(out)
+        outs = [torch.zeros(ts, dtype=torch.float64).pin_memory() for _ in range(2)]
+        stream = torch.cuda.current_stream()
+        for step in range(7):
+            k = step % 3
+            gb.gbsbin_plan_set_state(p.handle, args[k], stream)
+            gb.gbsbin_execute_host_async(p.handle, outs[step & 1], stream)
+            if step & 1:
+                torch.cuda.synchronize()
+                for j, kk in ((0, (step - 1) % 3), (1, k)):
+                    assert np.array_equal(outs[j].numpy(), sync[kk]), (step, j)
+        torch.cuda.synchronize()
+        assert np.array_equal(outs[0].numpy(), sync[6 % 3])
+    for q, t in zip(probs, sync):
+        ref, _ = oracle_table(q)
+        assert np.abs(t.reshape(ref.shape) - ref).max() < 1e-10
+
+
 def test_direct_covariance_input(cuda_lib):
     from oracle import state
     prob = synth.random_problem(np.random.default_rng(121), 4, 1, 2, 5, displaced=True)
