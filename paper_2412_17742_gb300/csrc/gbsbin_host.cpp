@@ -1094,7 +1094,8 @@ int gbsbin_execute(gbsbin_plan* P, double* P_out, void* stream) {
     t.ldfin = P->d_ldfin;
     t.minpiv = P->d_minpiv;
     t.gout = P->tree_g ? P->d_bufA : nullptr;
-    if (launch_points_tree(t, P->kernel == GBSBIN_KERNEL_TREE_FP64, s) != cudaSuccess) return GBSBIN_ERR_CUDA;
+    if (launch_points_tree(t, P->kernel == GBSBIN_KERNEL_TREE_FP64, P->num_sms, s) != cudaSuccess)
+      return GBSBIN_ERR_CUDA;
     if (P->ev1 && cudaEventRecord(P->ev1, s) != cudaSuccess) return GBSBIN_ERR_CUDA;
     DftArgs d = make_dft_args(P, P_out);
     d.g_ready = P->tree_g ? 1 : 0;

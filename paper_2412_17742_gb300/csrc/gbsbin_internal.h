@@ -150,7 +150,7 @@ struct TreeArgs {
 };
 size_t tree_level_smem_bytes(int nb, int m);
 int tree_leaf_threads(int n);   // lanes per leaf (0: no kernel for a last group of n rows)
-cudaError_t launch_points_tree(const TreeArgs& a, bool fp64, cudaStream_t s);
+cudaError_t launch_points_tree(const TreeArgs& a, bool fp64, int num_sms, cudaStream_t s);
 
 // Fock inputs through a lossy circuit (gbsbin_fock.cu).  nin occupied inputs in position
 // order (position 0 is the held input, x = 1; positions 1..nd are the Gray digits); per

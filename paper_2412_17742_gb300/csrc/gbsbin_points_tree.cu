@@ -42,6 +42,7 @@ namespace gbsbin {
 namespace {
 
 constexpr int LT_MAX = 512;      // threads of a level CTA (at most)
+constexpr int SPAN_MAX = 4;      // groups one level launch may eliminate
 
 // Path record of a node (48 bytes in both arithmetics): the pivot product scaled by a power
 // of two; (FP32 argument sum, power of two, smallest pivot real part, -); the exponent sum.
@@ -120,20 +121,41 @@ __device__ __forceinline__ void path_warp(PathRec<typename Ar::E>& pr, typename 
 // reciprocal (every lane of warp 0) and the rows below their multipliers (warp 0), then every
 // entry one fused multiply-subtract.  After the sweep warp 0 forms the child's path record
 // while the other warps copy out the child's matrix and vectors.
+//
+// A launch may eliminate span consecutive groups l .. l + span - 1 at once (a node of depth
+// l + span from its ancestor at depth l): the leading block is then those groups' rows, each
+// pivot row scaled by its own group's root, and the Schur complement of that block is the
+// same A'' as after span single-group sweeps (eliminating block 0 and then block 1 of the
+// first Schur complement is eliminating [0 1] at once), with the same pivots.
 template <class Ar>
-__global__ void __launch_bounds__(LT_MAX) k_tree_level(TreeArgs a, int l) {
+__global__ void __launch_bounds__(LT_MAX) k_tree_level(TreeArgs a, int l, int span) {
   using E = typename Ar::E;
   extern __shared__ __align__(16) unsigned char gsm_raw[];
-  const int nb = a.nb[l], m = a.m[l], mc = m - nb, cols = m + 1;
+  // the child's roots, last merged axis fastest in its index, and the pivot-row bounds
+  E wg[SPAN_MAX];
+  int bound[SPAN_MAX];
+  long long rest = blockIdx.x;
+  int nb = 0;
+#pragma unroll
+  for (int g = SPAN_MAX - 1; g >= 0; --g) {
+    if (g < span) {
+      const int R = a.grid.radix[l + g];
+      const long long up = rest / R;
+      wg[g] = Ar::from(grid_root(a.tw, a.grid, l + g, (int)(rest - up * R)));
+      rest = up;
+    }
+  }
+#pragma unroll
+  for (int g = 0; g < SPAN_MAX; ++g) {
+    if (g < span) nb += a.nb[l + g];
+    bound[g] = nb;
+  }
+  const long long child = blockIdx.x, parent = rest;
+  const int m = a.m[l], mc = m - nb, cols = m + 1;
   const int rows = a.has_gamma ? m + 1 : m;
   E* G = reinterpret_cast<E*>(gsm_raw);              // rows x cols
   E* pv = G + (size_t)rows * cols;                   // nb pivots
   E* Lm = pv + nb;                                   // rows: multipliers of the current step
-  const long long child = blockIdx.x;
-  const int R = a.grid.radix[l];
-  const long long parent = child / R;
-  const int k = (int)(child - parent * R);
-  const E w = Ar::from(grid_root(a.tw, a.grid, l, k));
   const E* Ap = elem<Ar>(a.A[l]) + parent * (long long)m * m;
   const E* cp = elem<Ar>(a.c[l]) + parent * (long long)m;
   const E* up = elem<Ar>(a.u[l]) + parent * (long long)m;
@@ -147,6 +169,10 @@ __global__ void __launch_bounds__(LT_MAX) k_tree_level(TreeArgs a, int l) {
     } else {
       const E v = s < m ? Ap[(long long)i * m + s] : (a.has_gamma ? cp[i] : zero);
       if (i < nb) {
+        E w = wg[0];                                 // the root of row i's group
+#pragma unroll
+        for (int q = 1; q < SPAN_MAX; ++q)
+          if (q < span && i >= bound[q - 1]) w = wg[q];
         g = Ar::mul(w, v);
         if (s < nb) {
           g = Ar::neg(g);
@@ -188,14 +214,14 @@ __global__ void __launch_bounds__(LT_MAX) k_tree_level(TreeArgs a, int l) {
   __syncthreads();
   if (tid >= 32) {                                   // the child's A', c', u' (warps 1..)
     const int t = tid - 32, LO = LT - 32;
-    E* Ac = elem<Ar>(a.A[l + 1]) + child * (long long)mc * mc;
+    E* Ac = elem<Ar>(a.A[l + span]) + child * (long long)mc * mc;
     for (int idx = t; idx < mc * mc; idx += LO) {
       const int i = idx / mc, j = idx - (idx / mc) * mc;
       Ac[idx] = G[(nb + i) * cols + nb + j];
     }
     if (a.has_gamma) {
-      E* cc = elem<Ar>(a.c[l + 1]) + child * (long long)mc;
-      E* uc = elem<Ar>(a.u[l + 1]) + child * (long long)mc;
+      E* cc = elem<Ar>(a.c[l + span]) + child * (long long)mc;
+      E* uc = elem<Ar>(a.u[l + span]) + child * (long long)mc;
       for (int j = t; j < mc; j += LO) {
         cc[j] = G[(nb + j) * cols + m];
         uc[j] = G[m * cols + nb + j];
@@ -203,14 +229,14 @@ __global__ void __launch_bounds__(LT_MAX) k_tree_level(TreeArgs a, int l) {
     }
   } else {                                           // the child's path record (warp 0)
     PathRec<E> pr = *path_at<Ar>(a.path[l], parent);
-    int span = 1;                                    // butterfly over the pivots' lanes only
-    while (span < nb && span < 32) span <<= 1;
+    int width = 1;                                   // butterfly over the pivots' lanes only
+    while (width < nb && width < 32) width <<= 1;
     for (int t0 = 0; t0 < nb; t0 += 32) {
       const int t = t0 + tid;
-      path_warp<Ar>(pr, t < nb ? pv[t] : zero, t < nb, span);
+      path_warp<Ar>(pr, t < nb ? pv[t] : zero, t < nb, width);
     }
     if (a.has_gamma) pr.ex = Ar::add(pr.ex, G[m * cols + m]);
-    if (tid == 0) *path_at<Ar>(a.path[l + 1], child) = pr;
+    if (tid == 0) *path_at<Ar>(a.path[l + span], child) = pr;
   }
 }
 
@@ -355,23 +381,33 @@ cudaError_t launch_leaf(const TreeArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// Levels whose children would fill fewer than half the SMs take the next level into the
+// same launch (a level's fixed costs - launch, fill from the parent, copy-out, path record -
+// are then paid once), up to SPAN_MAX groups and while a level remains before the leaves.
 template <class Ar>
-cudaError_t launch_tree(const TreeArgs& a, cudaStream_t s) {
+cudaError_t launch_tree(const TreeArgs& a, int num_sms, cudaStream_t s) {
   cudaError_t err = cudaSuccess;
   long long nodes = 1;
-  for (int l = 0; l + 1 < a.grid.L; ++l) {
-    const long long children = nodes * a.grid.radix[l];
-    const size_t smem = tree_level_smem_bytes(a.nb[l], a.m[l]);
+  for (int l = 0; l + 1 < a.grid.L;) {
+    long long children = nodes * a.grid.radix[l];
+    int span = 1, nb = a.nb[l];
+    while (span < SPAN_MAX && l + span + 1 < a.grid.L && 2 * children < num_sms) {
+      children *= a.grid.radix[l + span];
+      nb += a.nb[l + span];
+      ++span;
+    }
+    const size_t smem = tree_level_smem_bytes(nb, a.m[l]);
     if (smem > 48 * 1024) {
       err = cudaFuncSetAttribute(k_tree_level<Ar>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (err != cudaSuccess) return err;
     }
     const int m = a.m[l], width = m * m;              // entries of the first elimination step
     const int threads = width >= 1024 ? 512 : width >= 256 ? 256 : 128;
-    k_tree_level<Ar><<<(unsigned)children, threads, smem, s>>>(a, l);
+    k_tree_level<Ar><<<(unsigned)children, threads, smem, s>>>(a, l, span);
     err = cudaGetLastError();
     if (err != cudaSuccess) return err;
     nodes = children;
+    l += span;
   }
   switch (a.m[a.grid.L - 1]) {
     case 2: return launch_leaf<Ar, 2>(a, s);
@@ -393,8 +429,8 @@ size_t tree_level_smem_bytes(int nb, int m) { return sizeof(float4) * ((size_t)(
 // Leaf blocks of 2, 4, ..., 16 rows have a kernel instance (0: not supported).
 int tree_leaf_threads(int n) { return (n >= 2 && n <= 16 && n % 2 == 0) ? n : 0; }
 
-cudaError_t launch_points_tree(const TreeArgs& a, bool fp64, cudaStream_t s) {
-  return fp64 ? launch_tree<ArF64>(a, s) : launch_tree<ArDF>(a, s);
+cudaError_t launch_points_tree(const TreeArgs& a, bool fp64, int num_sms, cudaStream_t s) {
+  return fp64 ? launch_tree<ArF64>(a, num_sms, s) : launch_tree<ArDF>(a, num_sms, s);
 }
 
 }  // namespace gbsbin
