@@ -63,7 +63,9 @@ typedef enum {
                                solve whose residual is formed with error-free FP32
                                transformations; FP64 epilogue and DFT.  Where the tree of
                                block eliminations applies (GBSBIN_KERNEL_TREE_DF32), pairs
-                               of FP32 instead of the refinement                            */
+                               of FP32 instead of the refinement, and the inverse DFT in
+                               pairs of FP32 too where its two-phase form applies (three or
+                               more groups on a small grid)                                 */
 } gbsbin_precision;
 
 typedef struct {

@@ -15,6 +15,9 @@
 // three or more axes take a two-phase form with one grid barrier (k_dft_blocked).
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
+#include "gbsbin_df.cuh"
 #include "gbsbin_internal.h"
 
 namespace gbsbin {
@@ -467,21 +470,25 @@ struct DftBlocked {
   int outer[GBSBIN_MAX_L], inner[GBSBIN_MAX_L];   // per axis, within its phase's block
   int B1, C1, C2, O2;     // phase-1 block entries, columns; phase-2 rows, last-axis rows per row
   int H, last_R, last_nout, last_twoff, buf;      // buf: entries per shared buffer
+  int ntw;                                          // twiddles of all axes (staged in shared memory)
   double scale;
 };
 
-// out[o, b, s] = sum_k in[o, k, s] tw[(k b) mod R] inside one CTA's shared block
-__device__ __forceinline__ void block_axis(const double2* in, double2* out, int outer, int R, int nout, int inner,
-                                           const double2* __restrict__ tw) {
+// out[o, b, s] = sum_k in[o, k, s] tw[(k b) mod R] inside one CTA's shared block, in the
+// arithmetic Ar (ArF64::fma is the FP64 complex multiply-add of the axis stages)
+template <class Ar>
+__device__ __forceinline__ void block_axis(const typename Ar::E* in, typename Ar::E* out, int outer, int R, int nout,
+                                           int inner, const typename Ar::E* tw) {
+  using E = typename Ar::E;
   const int total = outer * nout * inner;
   for (int t = threadIdx.x; t < total; t += blockDim.x) {
     const int rest = t / inner, s = t - rest * inner;
     const int o = rest / nout, b = rest - o * nout;
-    const double2* src = in + o * R * inner + s;
-    double2 acc = make_double2(0.0, 0.0);
+    const E* src = in + o * R * inner + s;
+    E acc = Ar::zero();
     int idx = 0;
     for (int k = 0; k < R; ++k) {
-      acc = cfma2(src[k * inner], tw[idx], acc);
+      acc = Ar::fma(src[k * inner], tw[idx], acc);
       idx += b;
       if (idx >= R) idx -= R;
     }
@@ -489,77 +496,59 @@ __device__ __forceinline__ void block_axis(const double2* in, double2* out, int 
   }
 }
 
+// Order-preserving integer key of a double that is not NaN (negative values flipped).
+__device__ __forceinline__ long long order_key(double v) {
+  const long long b = __double_as_longlong(v);
+  return b >= 0 ? b : b ^ 0x7fffffffffffffffll;
+}
+__device__ __forceinline__ double key_value(long long k) {
+  return __longlong_as_double(k >= 0 ? k : k ^ 0x7fffffffffffffffll);
+}
+
+// Per-warp diagnostics partial into slot vb: the sum in FP64, the maximum |Im| (non-negative)
+// and the minimum pivot through their order-preserving integer keys, the count as an
+// integer; no block barrier.
+__device__ __forceinline__ void warp_diag(DiagAcc a, double* __restrict__ part, int vb) {
+  double sum = a.sum;
+  long long im = order_key(a.im), mn = order_key(a.mn);
+  int bad = (int)a.bad;
+  for (int o = 16; o > 0; o >>= 1) {
+    sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    const long long io = __shfl_xor_sync(0xffffffffu, im, o), mo = __shfl_xor_sync(0xffffffffu, mn, o);
+    im = io > im ? io : im;
+    mn = mo < mn ? mo : mn;
+    bad += __shfl_xor_sync(0xffffffffu, bad, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    part[4 * vb] = sum;
+    part[4 * vb + 1] = key_value(im);
+    part[4 * vb + 2] = key_value(mn);
+    part[4 * vb + 3] = (double)bad;
+  }
+}
+
+// Ar = ArF64: every entry summed as by the axis stages (bit-identical tables); Ar = ArDF:
+// the transform in pairs of FP32 (about 46 bits) on the FMA pipe.
+template <class Ar>
 __global__ void __launch_bounds__(128) k_dft_blocked(DftBlocked f) {
-  extern __shared__ __align__(16) double2 dsm[];
+  using E = typename Ar::E;
+  extern __shared__ __align__(16) unsigned char dsm_raw[];
   const DftArgs& a = f.a;
-  double2* S0 = dsm;
-  double2* S1 = dsm + f.buf;
+  E* S0 = reinterpret_cast<E*>(dsm_raw);
+  E* S1 = S0 + f.buf;
+  E* tws = S1 + f.buf;                               // all axes' twiddles
+  E* Y = reinterpret_cast<E*>(a.bufB);               // 16-byte entries either way
+  for (int j = threadIdx.x; j < f.ntw; j += blockDim.x) tws[j] = Ar::from(a.tw[j]);
   __shared__ double2 s_l0;
   if (!a.g_ready && !a.parts) {
     if (threadIdx.x == 0) s_l0 = a.ldfin ? finish_logq(a.ldfin) : a.logq[0];
     __syncthreads();
   }
-  // phase 1: axes 0 .. h-1 per column
-  for (int c = blockIdx.x; c < f.C1; c += gridDim.x) {
-    for (int e = threadIdx.x; e < f.B1; e += blockDim.x) {
-      const long long t = (long long)e * f.C1 + c;
-      S0[e] = a.g_ready ? a.bufA[t]
-              : a.parts ? sum_parts_one(a.parts, a.nparts, a.pscale, a.grid.n_full, t)
-                        : normalise_one(a.logq, a.grid, a.ldfin, a.logq_fin, s_l0, t);
-    }
-    __syncthreads();
-    double2* cur = S0;
-    double2* nxt = S1;
-    for (int l = 0; l < f.h; ++l) {
-      block_axis(cur, nxt, f.outer[l], f.R[l], f.nout[l], f.inner[l], a.tw + f.twoff[l]);
-      __syncthreads();
-      double2* t = cur;
-      cur = nxt;
-      nxt = t;
-    }
-    for (int e = threadIdx.x; e < f.C2; e += blockDim.x) a.bufB[(long long)e * f.C1 + c] = cur[e];
-    __syncthreads();
-  }
-  grid_barrier(f.bar);
-  // phase 2: axes h .. L-2, then the last (Hermitian) axis, per row
+  // the pivots' scan: before phase 1 when nothing it reads is written here (G from the
+  // point kernel), else after the barrier (log q finished in phase 1)
   DiagAcc acc{0.0, 0.0, 1.0e300, 0.0};
-  const int R = f.last_R, H = f.H, nout = f.last_nout;
-  const double2* tw = a.tw + f.last_twoff;
-  for (int r = blockIdx.x; r < f.C2; r += gridDim.x) {
-    for (int e = threadIdx.x; e < f.C1; e += blockDim.x) S0[e] = a.bufB[(long long)r * f.C1 + e];
-    __syncthreads();
-    double2* cur = S0;
-    double2* nxt = S1;
-    for (int l = f.h; l < f.L - 1; ++l) {
-      block_axis(cur, nxt, f.outer[l], f.R[l], f.nout[l], f.inner[l], a.tw + f.twoff[l]);
-      __syncthreads();
-      double2* t = cur;
-      cur = nxt;
-      nxt = t;
-    }
-    double* Prow = a.P + (long long)r * f.O2 * nout;
-    for (int t = threadIdx.x; t < f.O2 * nout; t += blockDim.x) {
-      const int o = t / nout, b = t - o * nout;
-      const double2* row = cur + o * H;
-      if (b == 0) {                                   // the row's self-conjugate entries
-        acc.im = fmax(acc.im, fabs(row[0].y));
-        if ((R & 1) == 0) acc.im = fmax(acc.im, fabs(row[H - 1].y));
-      }
-      double v = row[0].x;
-      int idx = b >= R ? b - R : b;
-      for (int k = 1; k < H; ++k) {
-        const double2 y = row[k], w = tw[idx];
-        v += ((2 * k == R) ? 1.0 : 2.0) * fma(y.x, w.x, -y.y * w.y);
-        idx += b;
-        if (idx >= R) idx -= R;
-      }
-      Prow[t] = v * f.scale;
-      acc.sum += v * f.scale;
-    }
-    __syncthreads();
-  }
-  if (a.diag) {
-    const double2* lq = a.g_ready ? nullptr : a.ldfin ? a.logq_fin : a.logq;
+  const double2* lq = a.g_ready ? nullptr : a.ldfin ? a.logq_fin : a.logq;
+  auto scan = [&]() {
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; a.minpiv && e < a.grid.n_eval; e += stride) {
       const double m = a.minpiv[e];
@@ -567,23 +556,102 @@ __global__ void __launch_bounds__(128) k_dft_blocked(DftBlocked f) {
       if (!((m > 0.0) && isfinite(l.x) && isfinite(l.y))) acc.bad += 1.0;
       acc.mn = fmin(acc.mn, m);
     }
-    block_diag(acc, a.diag, blockIdx.x);
+  };
+  if (a.diag && !lq) scan();
+  // phase 1: axes 0 .. h-1 per column
+  for (int c = blockIdx.x; c < f.C1; c += gridDim.x) {
+    for (int e = threadIdx.x; e < f.B1; e += blockDim.x) {
+      const long long t = (long long)e * f.C1 + c;
+      S0[e] = Ar::from(a.g_ready ? a.bufA[t]
+                       : a.parts ? sum_parts_one(a.parts, a.nparts, a.pscale, a.grid.n_full, t)
+                                 : normalise_one(a.logq, a.grid, a.ldfin, a.logq_fin, s_l0, t));
+    }
+    __syncthreads();
+    E* cur = S0;
+    E* nxt = S1;
+    for (int l = 0; l < f.h; ++l) {
+      block_axis<Ar>(cur, nxt, f.outer[l], f.R[l], f.nout[l], f.inner[l], tws + f.twoff[l]);
+      __syncthreads();
+      E* t = cur;
+      cur = nxt;
+      nxt = t;
+    }
+    for (int e = threadIdx.x; e < f.C2; e += blockDim.x) Y[(long long)e * f.C1 + c] = cur[e];
+    __syncthreads();
+  }
+  grid_barrier(f.bar);
+  if (a.diag && lq) scan();
+  // phase 2: axes h .. L-2, then the last (Hermitian) axis, per row
+  const int R = f.last_R, H = f.H, nout = f.last_nout;
+  const E* tw = tws + f.last_twoff;
+  for (int r = blockIdx.x; r < f.C2; r += gridDim.x) {
+    for (int e = threadIdx.x; e < f.C1; e += blockDim.x) S0[e] = Y[(long long)r * f.C1 + e];
+    __syncthreads();
+    E* cur = S0;
+    E* nxt = S1;
+    for (int l = f.h; l < f.L - 1; ++l) {
+      block_axis<Ar>(cur, nxt, f.outer[l], f.R[l], f.nout[l], f.inner[l], tws + f.twoff[l]);
+      __syncthreads();
+      E* t = cur;
+      cur = nxt;
+      nxt = t;
+    }
+    double* Prow = a.P + (long long)r * f.O2 * nout;
+    for (int t = threadIdx.x; t < f.O2 * nout; t += blockDim.x) {
+      const int o = t / nout, b = t - o * nout;
+      const E* row = cur + o * H;
+      if (b == 0) {                                   // the row's self-conjugate entries
+        acc.im = fmax(acc.im, fabs((double)Ar::im(row[0])));
+        if ((R & 1) == 0) acc.im = fmax(acc.im, fabs((double)Ar::im(row[H - 1])));
+      }
+      int idx = b >= R ? b - R : b;
+      double v;
+      if constexpr (std::is_same<Ar, ArF64>::value) {
+        v = row[0].x;
+        for (int k = 1; k < H; ++k) {
+          const double2 y = row[k], w = tw[idx];
+          v += ((2 * k == R) ? 1.0 : 2.0) * fma(y.x, w.x, -y.y * w.y);
+          idx += b;
+          if (idx >= R) idx -= R;
+        }
+      } else {                                        // Re(row[0] + sum_k c_k row[k] w), c_k = 2 or 1
+        E acc2 = Ar::zero();
+        for (int k = 1; k < H; ++k) {
+          E yw = Ar::mul(row[k], tw[idx]);
+          if (2 * k != R) yw = Ar::add(yw, yw);
+          acc2 = Ar::add(acc2, yw);
+          idx += b;
+          if (idx >= R) idx -= R;
+        }
+        v = Ar::to(Ar::add(row[0], acc2)).x;
+      }
+      Prow[t] = v * f.scale;
+      acc.sum += v * f.scale;
+    }
+    __syncthreads();
+  }
+  if (a.diag) {
+    const int nw = blockDim.x >> 5;
+    warp_diag(acc, a.diag, blockIdx.x * nw + (threadIdx.x >> 5));
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       a.diag[4 * GBSBIN_DIAG_SLOTS] = lq ? lq[0].x : 0.0;
       a.diag[4 * GBSBIN_DIAG_SLOTS + 1] = (double)*(volatile unsigned*)(f.bar + 2);
-      a.diag[4 * GBSBIN_DIAG_SLOTS + 2] = (double)gridDim.x;
+      a.diag[4 * GBSBIN_DIAG_SLOTS + 2] = (double)(gridDim.x * nw);
     }
   }
 }
 
-// The blocked form where it suits: three or more axes, both phases' blocks within
-// kBlockedMaxEntries, and at least kBlockedMinCtas columns and rows (the split h with the
-// most of both); otherwise 0.
+// The blocked form where it suits: three or more axes, both phases' blocks and all axes'
+// twiddles within kBlockedMaxEntries each (48 KB of shared memory at most), and at least
+// kBlockedMinCtas columns and rows (the split h with the most of both); otherwise 0.
 constexpr int kBlockedMaxEntries = 1024;
 constexpr int kBlockedMinCtas = 32;
 static int blocked_split(const GridDesc& g) {
   const int L = g.L;
   if (L < 3) return 0;
+  long long ntw = 0;                                 // the twiddles go to shared memory too
+  for (int l = 0; l < L; ++l) ntw += g.radix[l];
+  if (ntw > kBlockedMaxEntries) return 0;
   long long d[GBSBIN_MAX_L];
   for (int l = 0; l < L - 1; ++l) d[l] = g.radix[l];
   d[L - 1] = g.half;
@@ -606,6 +674,7 @@ static int blocked_split(const GridDesc& g) {
   return best;
 }
 
+template <class Ar>
 static cudaError_t launch_dft_blocked(const DftArgs& a, int h, unsigned* bar, int num_sms, cudaStream_t s) {
   const GridDesc& g = a.grid;
   const int L = g.L;
@@ -649,24 +718,27 @@ static cudaError_t launch_dft_blocked(const DftArgs& a, int h, unsigned* bar, in
   f.last_nout = g.nout[L - 1];
   f.last_twoff = f.twoff[L - 1];
   f.buf = f.B1 > f.C1 ? f.B1 : f.C1;
+  f.ntw = twoff;
   f.scale = 1.0 / (double)g.npts;
-  const size_t smem = 2 * (size_t)f.buf * sizeof(double2);
+  const size_t smem = (2 * (size_t)f.buf + (size_t)f.ntw) * sizeof(double2);
   int per_sm = 0;
-  cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dft_blocked, 128, smem);
+  cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dft_blocked<Ar>, 128, smem);
   if (err != cudaSuccess) return err;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   long long blocks = f.C1 > f.C2 ? f.C1 : f.C2;     // one column or row per CTA
   if (blocks > (long long)per_sm * num_sms) blocks = (long long)per_sm * num_sms;
-  if (blocks > GBSBIN_DIAG_SLOTS) blocks = GBSBIN_DIAG_SLOTS;
+  if (blocks > GBSBIN_DIAG_SLOTS / 4) blocks = GBSBIN_DIAG_SLOTS / 4;   // a partial per warp
   void* params[] = {&f};
-  return cudaLaunchCooperativeKernel((const void*)k_dft_blocked, dim3((unsigned)blocks), dim3(128), params, smem, s);
+  return cudaLaunchCooperativeKernel((const void*)k_dft_blocked<Ar>, dim3((unsigned)blocks), dim3(128), params, smem,
+                                     s);
 }
 
 cudaError_t launch_dft_fused(const DftArgs& a, unsigned* bar, int num_sms, cudaStream_t s) {
   const GridDesc& g = a.grid;
   const int L = g.L;
   const int h = blocked_split(g);
-  if (h > 0) return launch_dft_blocked(a, h, bar, num_sms, s);
+  if (h > 0) return a.df ? launch_dft_blocked<ArDF>(a, h, bar, num_sms, s)
+                         : launch_dft_blocked<ArF64>(a, h, bar, num_sms, s);
   DftFused f{};
   f.a = a;
   f.bar = bar;

@@ -1077,6 +1077,7 @@ static DftArgs make_dft_args(gbsbin_plan* P, double* P_out) {
   d.diag = P->opt.want_diagnostics ? P->d_diag : nullptr;
   d.minpiv = P->d_minpiv;
   d.table_size = P->table_size;
+  d.df = P->kernel == GBSBIN_KERNEL_TREE_DF32 ? 1 : 0;
   return d;
 }
 

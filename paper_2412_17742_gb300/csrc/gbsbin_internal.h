@@ -120,6 +120,8 @@ struct DftArgs {
   double* diag;             // GBSBIN_DIAG_DOUBLES: partial reductions (see above), or nullptr
   const double* minpiv;     // n_eval
   long long table_size;
+  int df;                   // nonzero: the two-phase transform (where it applies) in pairs of
+                            // FP32 (plans whose points are computed in pairs of FP32)
 };
 
 // Tree of block eliminations over the grid (gbsbin_points_tree.cu), in pairs of FP32
