@@ -544,20 +544,22 @@ __global__ void __launch_bounds__(128) k_dft_blocked(DftBlocked f) {
     if (threadIdx.x == 0) s_l0 = a.ldfin ? finish_logq(a.ldfin) : a.logq[0];
     __syncthreads();
   }
-  // the pivots' scan: before phase 1 when nothing it reads is written here (G from the
-  // point kernel), else after the barrier (log q finished in phase 1)
+  // the pivots' scan after phase 1 (log q may be finished there); its first pivot per
+  // thread is loaded now, so that load's latency passes under phase 1
   DiagAcc acc{0.0, 0.0, 1.0e300, 0.0};
   const double2* lq = a.g_ready ? nullptr : a.ldfin ? a.logq_fin : a.logq;
+  const long long e_first = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const bool has_first = a.diag && a.minpiv && e_first < a.grid.n_eval;
+  const double m_first = has_first ? a.minpiv[e_first] : 0.0;
   auto scan = [&]() {
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; a.minpiv && e < a.grid.n_eval; e += stride) {
-      const double m = a.minpiv[e];
+    for (long long e = e_first; a.minpiv && e < a.grid.n_eval; e += stride) {
+      const double m = e == e_first ? m_first : a.minpiv[e];
       const double2 l = lq ? lq[e] : make_double2(0.0, 0.0);
       if (!((m > 0.0) && isfinite(l.x) && isfinite(l.y))) acc.bad += 1.0;
       acc.mn = fmin(acc.mn, m);
     }
   };
-  if (a.diag && !lq) scan();
   // phase 1: axes 0 .. h-1 per column
   for (int c = blockIdx.x; c < f.C1; c += gridDim.x) {
     for (int e = threadIdx.x; e < f.B1; e += blockDim.x) {
@@ -580,7 +582,7 @@ __global__ void __launch_bounds__(128) k_dft_blocked(DftBlocked f) {
     __syncthreads();
   }
   grid_barrier(f.bar);
-  if (a.diag && lq) scan();
+  if (a.diag) scan();
   // phase 2: axes h .. L-2, then the last (Hermitian) axis, per row
   const int R = f.last_R, H = f.H, nout = f.last_nout;
   const E* tw = tws + f.last_twoff;

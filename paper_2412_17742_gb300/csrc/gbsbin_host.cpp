@@ -51,6 +51,7 @@ struct gbsbin_plan {
   double* d_minpiv = nullptr;
   double2 *d_bufA = nullptr, *d_bufB = nullptr;
   double2* d_tw = nullptr;
+  float4* d_twdf = nullptr;           // tree plans: the roots w = conj(twiddle) as pairs of FP32
   double* d_diag = nullptr;
   double* d_table = nullptr;  // device copy of the table for execute_host
   void* d_gws = nullptr;
@@ -324,6 +325,7 @@ int build_state(const gbsbin_problem* p, int n, std::vector<cd>& XA, std::vector
 }
 
 void free_device(gbsbin_plan* P) {
+  if (P->d_twdf) cudaFree(P->d_twdf);
   void* ptrs[] = {P->d_state, P->d_label, P->d_logq,  P->d_minpiv, P->d_bufA, P->d_bufB, P->d_tw,
                   P->d_diag,  P->d_gws,   P->d_table, P->d_ldfin,  P->d_bar,  P->d_H,    P->d_tree};
   for (void* q : ptrs)
@@ -490,6 +492,7 @@ int upload_state(gbsbin_plan* P, cudaStream_t stream) {
       const double arg0 = std::atan2(prod.imag(), prod.real());
       P->tree.p0re = prod.real();
       P->tree.p0im = prod.imag();
+      P->tree.p0df = split4(prod);
       P->tree.p0arg = (float)arg0;
       P->tree.e0 = (float)e0;
       P->tree.m0 = (float)std::nearbyint((args - arg0) / TWO_PI);
@@ -987,6 +990,17 @@ static int plan_create_impl(const gbsbin_problem* p, const gbsbin_options* o, gb
     delete P;
     return GBSBIN_ERR_CUDA;
   }
+  if (is_tree(P->kernel)) {                       // the roots w = conj(twiddle) as FP32 pairs
+    std::vector<float4> twdf((size_t)twn);
+    for (size_t j = 0; j < twdf.size(); ++j) twdf[j] = split4(cd(tw[j].x, -tw[j].y));
+    if (cudaMalloc(&P->d_twdf, twdf.size() * sizeof(float4)) != cudaSuccess ||
+        cudaMemcpy(P->d_twdf, twdf.data(), twdf.size() * sizeof(float4), cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaGetLastError();
+      free_device(P);
+      delete P;
+      return GBSBIN_ERR_CUDA;
+    }
+  }
   st = upload_state(P, 0);
   if (!st && cudaStreamSynchronize(0) != cudaSuccess) st = GBSBIN_ERR_CUDA;
   if (st) {
@@ -1091,6 +1105,7 @@ int gbsbin_execute(gbsbin_plan* P, double* P_out, void* stream) {
     TreeArgs t = P->tree;
     t.has_gamma = P->has_gamma;
     t.tw = P->d_tw;
+    t.twdf = P->d_twdf;
     t.grid = P->grid;
     t.ldfin = P->d_ldfin;
     t.minpiv = P->d_minpiv;

@@ -140,6 +140,8 @@ struct TreeArgs {
   float4* u[GBSBIN_MAX_L];
   float4* path[GBSBIN_MAX_L];
   const double2* tw;
+  const float4* twdf;       // the same roots w = exp(2 pi i k / R_l) as pairs of FP32 (the pair
+                            // kernels read these instead of converting FP64 twiddles)
   GridDesc grid;
   double* ldfin;
   double* minpiv;
@@ -148,6 +150,7 @@ struct TreeArgs {
   // p0arg and winding m0 (log det(I - XA) = log|P0| + e0 log 2 + i (p0arg + 2 pi m0))
   double2* gout;
   double p0re, p0im;
+  float4 p0df;              // p0 as a pair of FP32
   float p0arg, e0, m0;
 };
 size_t tree_level_smem_bytes(int nb, int m);

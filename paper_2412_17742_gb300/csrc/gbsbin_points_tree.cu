@@ -34,6 +34,8 @@
 // its launch shapes are the same.
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "gbsbin_device.cuh"
 #include "gbsbin_df.cuh"
 #include "gbsbin_internal.h"
@@ -62,6 +64,19 @@ __device__ __forceinline__ PathRec<typename Ar::E>* path_at(float4* base, long l
 template <class Ar>
 __device__ __forceinline__ typename Ar::E* elem(float4* p) {
   return reinterpret_cast<typename Ar::E*>(p);
+}
+
+// w = exp(2 pi i k / R_l): from the pairs-of-FP32 table for ArDF (no FP64 conversion), else
+// from the FP64 twiddles
+template <class Ar>
+__device__ __forceinline__ typename Ar::E root_at(const TreeArgs& a, int l, int k) {
+  if constexpr (std::is_same<Ar, ArDF>::value) {
+    int off = 0;
+    for (int q = 0; q < l; ++q) off += a.grid.radix[q];
+    return a.twdf[off + k];
+  } else {
+    return Ar::from(grid_root(a.tw, a.grid, l, k));
+  }
 }
 
 __device__ __forceinline__ float4 shfl(float4 v, int src) {
@@ -141,7 +156,7 @@ __global__ void __launch_bounds__(LT_MAX) k_tree_level(TreeArgs a, int l, int sp
     if (g < span) {
       const int R = a.grid.radix[l + g];
       const long long up = rest / R;
-      wg[g] = Ar::from(grid_root(a.tw, a.grid, l + g, (int)(rest - up * R)));
+      wg[g] = root_at<Ar>(a, l + g, (int)(rest - up * R));
       rest = up;
     }
   }
@@ -260,7 +275,7 @@ __global__ void __launch_bounds__(128) k_tree_leaf(TreeArgs a) {
   const int H = a.grid.half;
   const long long parent = live ? leaf / H : 0;
   const int k = live ? (int)(leaf - parent * H) : 0;
-  const E w = Ar::from(grid_root(a.tw, a.grid, l, k));
+  const E w = root_at<Ar>(a, l, k);
   const E* Ap = elem<Ar>(a.A[l]) + parent * (long long)NL * NL + (long long)(live ? r : 0) * NL;
   const E one = Ar::one(), zero = Ar::zero();
   E b[NL];
@@ -357,18 +372,41 @@ __global__ void __launch_bounds__(128) k_tree_leaf(TreeArgs a) {
     const float TWO_PI = 6.28318530717958647692f;
     const float argP = atan2f(Ar::im(pr.prod), Ar::re(pr.prod));
     const float m = rintf((pr.meta.x - argP) / TWO_PI);         // winding of log det at this point
-    const E Z = Ar::mul(Ar::from(make_double2(a.p0re, a.p0im)), Ar::recip(pr.prod));
+    E p0;
+    if constexpr (std::is_same<Ar, ArDF>::value) p0 = a.p0df;
+    else p0 = Ar::from(make_double2(a.p0re, a.p0im));
+    const E Z = Ar::mul(p0, Ar::recip(pr.prod));
     const float kz = rintf((atan2f(Ar::im(Z), Ar::re(Z)) - (a.p0arg - argP)) / TWO_PI);
     const int wind = (int)(kz + m - a.m0);
-    double2 g = Ar::to(Ar::csqrt(Z));
     const int d = (int)(a.e0 - pr.meta.y);
-    if (d & 1) {
-      g.x *= 1.41421356237309504880;
-      g.y *= 1.41421356237309504880;
-    }
     const int hexp = (d - (d & 1)) / 2;
-    const double sg = (wind & 1) ? -1.0 : 1.0;
-    a.gout[leaf] = make_double2(sg * ldexp(g.x, hexp), sg * ldexp(g.y, hexp));
+    if constexpr (std::is_same<Ar, ArDF>::value) {
+      // sqrt(2) and 2^hexp applied to the pair (exact power-of-two scaling), one conversion
+      E g = Ar::csqrt(Z);
+      if (d & 1) {
+        constexpr double SQ2 = 1.41421356237309504880;
+        constexpr float SQ2_HI = (float)SQ2;
+        constexpr float SQ2_LO = (float)(SQ2 - (double)SQ2_HI);
+        g = Ar::mul(g, make_float4(SQ2_HI, 0.f, SQ2_LO, 0.f));
+      }
+      if (hexp >= -126 && hexp <= 127) {
+        const float sc = __uint_as_float((unsigned)(127 + hexp) << 23) * ((wind & 1) ? -1.f : 1.f);
+        g = make_float4(g.x * sc, g.y * sc, g.z * sc, g.w * sc);
+        a.gout[leaf] = Ar::to(g);
+      } else {
+        const double2 gd = Ar::to(g);
+        const double sg = (wind & 1) ? -1.0 : 1.0;
+        a.gout[leaf] = make_double2(sg * ldexp(gd.x, hexp), sg * ldexp(gd.y, hexp));
+      }
+    } else {
+      double2 g = Ar::to(Ar::csqrt(Z));
+      if (d & 1) {
+        g.x *= 1.41421356237309504880;
+        g.y *= 1.41421356237309504880;
+      }
+      const double sg = (wind & 1) ? -1.0 : 1.0;
+      a.gout[leaf] = make_double2(sg * ldexp(g.x, hexp), sg * ldexp(g.y, hexp));
+    }
   }
 }
 
