@@ -564,9 +564,12 @@ __global__ void __launch_bounds__(128) k_dft_blocked(DftBlocked f) {
   for (int c = blockIdx.x; c < f.C1; c += gridDim.x) {
     for (int e = threadIdx.x; e < f.B1; e += blockDim.x) {
       const long long t = (long long)e * f.C1 + c;
-      S0[e] = Ar::from(a.g_ready ? a.bufA[t]
-                       : a.parts ? sum_parts_one(a.parts, a.nparts, a.pscale, a.grid.n_full, t)
-                                 : normalise_one(a.logq, a.grid, a.ldfin, a.logq_fin, s_l0, t));
+      if (std::is_same<Ar, ArDF>::value && a.g_ready && a.g_df)
+        S0[e] = reinterpret_cast<const E*>(a.bufA)[t];    // G written as a pair
+      else
+        S0[e] = Ar::from(a.g_ready ? a.bufA[t]
+                         : a.parts ? sum_parts_one(a.parts, a.nparts, a.pscale, a.grid.n_full, t)
+                                   : normalise_one(a.logq, a.grid, a.ldfin, a.logq_fin, s_l0, t));
     }
     __syncthreads();
     E* cur = S0;
@@ -675,6 +678,8 @@ static int blocked_split(const GridDesc& g) {
   }
   return best;
 }
+
+int dft_two_phase(const GridDesc& g) { return blocked_split(g) > 0 ? 1 : 0; }
 
 template <class Ar>
 static cudaError_t launch_dft_blocked(const DftArgs& a, int h, unsigned* bar, int num_sms, cudaStream_t s) {

@@ -1110,11 +1110,14 @@ int gbsbin_execute(gbsbin_plan* P, double* P_out, void* stream) {
     t.ldfin = P->d_ldfin;
     t.minpiv = P->d_minpiv;
     t.gout = P->tree_g ? P->d_bufA : nullptr;
+    // pairs plans whose transform runs in pairs take G as pairs (no FP64 round trip)
+    t.gout_df = (P->tree_g && P->kernel == GBSBIN_KERNEL_TREE_DF32 && dft_two_phase(P->grid)) ? 1 : 0;
     if (launch_points_tree(t, P->kernel == GBSBIN_KERNEL_TREE_FP64, P->num_sms, s) != cudaSuccess)
       return GBSBIN_ERR_CUDA;
     if (P->ev1 && cudaEventRecord(P->ev1, s) != cudaSuccess) return GBSBIN_ERR_CUDA;
     DftArgs d = make_dft_args(P, P_out);
     d.g_ready = P->tree_g ? 1 : 0;
+    d.g_df = t.gout_df;
     return launch_dft_fused(d, P->d_bar, P->num_sms, s) == cudaSuccess ? GBSBIN_OK : GBSBIN_ERR_CUDA;
   }
   cudaError_t e = P->kernel == GBSBIN_KERNEL_WARP_FP32R  ? launch_points_warp(a, P->num_sms, s)

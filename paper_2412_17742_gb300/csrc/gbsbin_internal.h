@@ -122,6 +122,7 @@ struct DftArgs {
   long long table_size;
   int df;                   // nonzero: the two-phase transform (where it applies) in pairs of
                             // FP32 (plans whose points are computed in pairs of FP32)
+  int g_df;                 // with g_ready and df: bufA holds G as pairs of FP32 (float4)
 };
 
 // Tree of block eliminations over the grid (gbsbin_points_tree.cu), in pairs of FP32
@@ -149,6 +150,8 @@ struct TreeArgs {
   // the pivot product P0 = p0 2^e0 of I - XA (host FP64, same row order), its argument
   // p0arg and winding m0 (log det(I - XA) = log|P0| + e0 log 2 + i (p0arg + 2 pi m0))
   double2* gout;
+  int gout_df;              // nonzero (pairs plans whose DFT runs in pairs): G stored as a pair
+                            // of FP32 (float4) in the 16-byte slots of gout
   double p0re, p0im;
   float4 p0df;              // p0 as a pair of FP32
   float p0arg, e0, m0;
@@ -219,6 +222,8 @@ cudaError_t launch_finish_logq(const double* ldfin, double2* logq, long long n, 
 // All DFT stages and the diagnostics in one cooperative launch; bar: 4 zeroed unsigned ints
 // of grid-barrier state owned by the caller; diag (if any) holds GBSBIN_DIAG_DOUBLES.
 cudaError_t launch_dft_fused(const DftArgs& a, unsigned* bar, int num_sms, cudaStream_t s);
+// Nonzero when launch_dft_fused takes the two-phase form for this grid.
+int dft_two_phase(const GridDesc& g);
 cudaError_t launch_backward(const BackwardArgs& b, const double* dLdP, cudaStream_t s);
 cudaError_t launch_alu_peak(int fp64, int blocks, float* out_sink, int iters, cudaStream_t s);
 

@@ -392,11 +392,14 @@ __global__ void __launch_bounds__(128) k_tree_leaf(TreeArgs a) {
       if (hexp >= -126 && hexp <= 127) {
         const float sc = __uint_as_float((unsigned)(127 + hexp) << 23) * ((wind & 1) ? -1.f : 1.f);
         g = make_float4(g.x * sc, g.y * sc, g.z * sc, g.w * sc);
-        a.gout[leaf] = Ar::to(g);
+        if (a.gout_df) reinterpret_cast<float4*>(a.gout)[leaf] = g;   // the DFT reads pairs
+        else a.gout[leaf] = Ar::to(g);
       } else {
         const double2 gd = Ar::to(g);
         const double sg = (wind & 1) ? -1.0 : 1.0;
-        a.gout[leaf] = make_double2(sg * ldexp(gd.x, hexp), sg * ldexp(gd.y, hexp));
+        const double2 gv = make_double2(sg * ldexp(gd.x, hexp), sg * ldexp(gd.y, hexp));
+        if (a.gout_df) reinterpret_cast<float4*>(a.gout)[leaf] = Ar::from(gv);
+        else a.gout[leaf] = gv;
       }
     } else {
       double2 g = Ar::to(Ar::csqrt(Z));
