@@ -132,9 +132,11 @@ __device__ __forceinline__ void path_warp(PathRec<typename Ar::E>& pr, typename 
 // leaves the child's A' and c' in the middle rows and (u'^T | u_0^T y) in the last row:
 // eliminating block 0 from a row [a_0 | a_r] gives a_r - a_0 B^-1 [w A_0r | w c_0].  Rows
 // are never scaled (only the Schur complement is needed): step kk subtracts
-// (G[i][kk] / G[kk][kk]) row kk from every row i > kk: one thread forms the pivot's
-// reciprocal (every lane of warp 0) and the rows below their multipliers (warp 0), then every
-// entry one fused multiply-subtract.  After the sweep warp 0 forms the child's path record
+// (G[i][kk] / G[kk][kk]) row kk from every row i > kk, each entry one fused multiply-subtract
+// with its row's multiplier.  The multipliers run one step ahead: in step kk warp 0 updates
+// column kk + 1 and then forms pivot kk + 1's reciprocal (every lane) and step kk + 1's
+// multipliers, while warps 1.. update the columns right of it - one barrier per step, the
+// hand-off off the critical path.  After the sweep warp 0 forms the child's path record
 // while the other warps copy out the child's matrix and vectors.
 //
 // A launch may eliminate span consecutive groups l .. l + span - 1 at once (a node of depth
@@ -142,8 +144,9 @@ __device__ __forceinline__ void path_warp(PathRec<typename Ar::E>& pr, typename 
 // pivot row scaled by its own group's root, and the Schur complement of that block is the
 // same A'' as after span single-group sweeps (eliminating block 0 and then block 1 of the
 // first Schur complement is eliminating [0 1] at once), with the same pivots.
+// (48 registers: five 256-thread CTAs per SM, so a 729-CTA level runs in one wave)
 template <class Ar>
-__global__ void __launch_bounds__(LT_MAX) k_tree_level(TreeArgs a, int l, int span) {
+__global__ void __maxnreg__(48) k_tree_level(TreeArgs a, int l, int span) {
   using E = typename Ar::E;
   extern __shared__ __align__(16) unsigned char gsm_raw[];
   // the child's roots, last merged axis fastest in its index, and the pivot-row bounds
@@ -170,7 +173,7 @@ __global__ void __launch_bounds__(LT_MAX) k_tree_level(TreeArgs a, int l, int sp
   const int rows = a.has_gamma ? m + 1 : m;
   E* G = reinterpret_cast<E*>(gsm_raw);              // rows x cols
   E* pv = G + (size_t)rows * cols;                   // nb pivots
-  E* Lm = pv + nb;                                   // rows: multipliers of the current step
+  E* Lm = pv + nb;                                   // 2 x rows: multipliers, this step and next
   const E* Ap = elem<Ar>(a.A[l]) + parent * (long long)m * m;
   const E* cp = elem<Ar>(a.c[l]) + parent * (long long)m;
   const E* up = elem<Ar>(a.u[l]) + parent * (long long)m;
@@ -199,32 +202,52 @@ __global__ void __launch_bounds__(LT_MAX) k_tree_level(TreeArgs a, int l, int sp
     }
     G[idx] = g;
   }
+  // one step of look-ahead: warp 0 updates column kk + 1 and at once forms pivot kk + 1's
+  // reciprocal and the next multipliers (into the other buffer) while warps 1.. update the
+  // columns right of it; one barrier per step
+  __syncthreads();                                   // the matrix is filled
+  if (tid < 32) {                                    // pivot 0 and its multipliers
+    const E piv = G[0];
+    if (tid == 0) pv[0] = piv;
+    const E r = Ar::recip(piv);
+    for (int i = 1 + tid; i < rows; i += 32) Lm[i] = Ar::mul(G[i * cols], r);
+  }
+  __syncthreads();
   for (int kk = 0; kk < nb; ++kk) {
-    __syncthreads();                                 // row kk final
-    if (tid < 32) {                                  // warp 0: the pivot's reciprocal (every
-      const E piv = G[kk * cols + kk];               // lane) and the rows' multipliers
-      if (tid == 0) pv[kk] = piv;
-      const E r = Ar::recip(piv);
-      for (int i = kk + 1 + tid; i < rows; i += 32) Lm[i] = Ar::mul(G[i * cols + kk], r);
+    const E* Lc = Lm + (kk & 1) * rows;              // this step's multipliers
+    if (tid < 32) {
+      E* Ln = Lm + ((kk + 1) & 1) * rows;
+      const int s1 = kk + 1;
+      for (int i = kk + 1 + tid; i < rows; i += 32)
+        G[i * cols + s1] = Ar::fms(G[i * cols + s1], Lc[i], G[kk * cols + s1]);
+      if (kk + 1 < nb) {
+        __syncwarp();
+        const E piv = G[s1 * cols + s1];
+        if (tid == 0) pv[s1] = piv;
+        const E r = Ar::recip(piv);
+        for (int i = s1 + 1 + tid; i < rows; i += 32) Ln[i] = Ar::mul(G[i * cols + s1], r);
+      }
+    } else {
+      // entries (i, s), i in (kk, rows), s in (kk + 1, cols), over threads 32..; two
+      // independent entries per pass.  floor(idx / w_) from a float reciprocal: idx < 2^14
+      // and w_ <= 65, so (idx + 1/2) / w_ stays more than 1/(2 w_) from an integer
+      const int t = tid - 32, LO = LT - 32;
+      const int w_ = cols - kk - 2, total = (rows - kk - 1) * w_;
+      const float rw = 1.0f / (float)(w_ > 0 ? w_ : 1);
+      for (int idx = t; idx < total; idx += 2 * LO) {
+        const int idx2 = idx + LO;
+        const int i = kk + 1 + (int)(((float)idx + 0.5f) * rw);
+        const int sc = kk + 2 + (idx - (i - kk - 1) * w_);
+        const E g1 = Ar::fms(G[i * cols + sc], Lc[i], G[kk * cols + sc]);
+        if (idx2 < total) {
+          const int i2 = kk + 1 + (int)(((float)idx2 + 0.5f) * rw);
+          const int s2 = kk + 2 + (idx2 - (i2 - kk - 1) * w_);
+          G[i2 * cols + s2] = Ar::fms(G[i2 * cols + s2], Lc[i2], G[kk * cols + s2]);
+        }
+        G[i * cols + sc] = g1;
+      }
     }
     __syncthreads();
-    // entries (i, s), i in (kk, rows), s in (kk, cols); two independent entries per pass.
-    // floor(idx / w_) from a float reciprocal: idx < 2^14 and w_ <= 65, so (idx + 1/2) / w_
-    // stays more than 1/(2 w_) from an integer, far above its rounding
-    const int w_ = cols - kk - 1, total = (rows - kk - 1) * w_;
-    const float rw = 1.0f / (float)w_;
-    for (int idx = tid; idx < total; idx += 2 * LT) {
-      const int idx2 = idx + LT;
-      const int i = kk + 1 + (int)(((float)idx + 0.5f) * rw);
-      const int sc = kk + 1 + (idx - (i - kk - 1) * w_);
-      const E g1 = Ar::fms(G[i * cols + sc], Lm[i], G[kk * cols + sc]);
-      if (idx2 < total) {
-        const int i2 = kk + 1 + (int)(((float)idx2 + 0.5f) * rw);
-        const int s2 = kk + 1 + (idx2 - (i2 - kk - 1) * w_);
-        G[i2 * cols + s2] = Ar::fms(G[i2 * cols + s2], Lm[i2], G[kk * cols + s2]);
-      }
-      G[i * cols + sc] = g1;
-    }
   }
   __syncthreads();
   if (tid >= 32) {                                   // the child's A', c', u' (warps 1..)
@@ -417,8 +440,8 @@ template <class Ar, int NL>
 cudaError_t launch_leaf(const TreeArgs& a, cudaStream_t s) {
   constexpr int TEAMS = 32 / NL;
   const long long warps = (a.grid.n_eval + TEAMS - 1) / TEAMS;
-  const long long blocks = (warps + 3) / 4;
-  k_tree_leaf<Ar, NL><<<(unsigned)blocks, 128, 0, s>>>(a);
+  const long long blocks = (warps + 1) / 2;           // two warps per CTA: spread evenly over SMs
+  k_tree_leaf<Ar, NL><<<(unsigned)blocks, 64, 0, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -465,7 +488,7 @@ cudaError_t launch_tree(const TreeArgs& a, int num_sms, cudaStream_t s) {
 
 }  // namespace
 
-size_t tree_level_smem_bytes(int nb, int m) { return sizeof(float4) * ((size_t)(m + 1) * (m + 1) + nb + m + 1); }
+size_t tree_level_smem_bytes(int nb, int m) { return sizeof(float4) * ((size_t)(m + 1) * (m + 1) + nb + 2 * (m + 1)); }
 
 // Leaf blocks of 2, 4, ..., 16 rows have a kernel instance (0: not supported).
 int tree_leaf_threads(int n) { return (n >= 2 && n <= 16 && n % 2 == 0) ? n : 0; }
