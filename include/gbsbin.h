@@ -361,6 +361,21 @@ int gbsbin_moments(const gbsbin_problem* p, double* mean, double* cov);
 int gbsbin_cumulants3(const gbsbin_problem* p, double* k3);
 
 /*
+ * Exact fourth cumulants of the binned counts (Sec. VI, coarse-grained moments and
+ * cumulants): kappa_{l1 l2 l3 l4} = fourth derivative of log G(e^t) at t = 0.  In
+ * e_l = e^{t_l} - 1, log G = sum_{r >= 1} sum_{m1..mr} C_r(m1..mr) e_m1 ... e_mr with
+ *   C_r(m1..mr) = sum_{i_k in m_k} ( 1/(2r) W_i1i2 W_i2i3 ... W_iri1
+ *                                    + 1/2 v_i1 W_i1i2 ... W_i(r-1)ir u_ir )
+ * (W, u, v as for gbsbin_moments; r = 1..3 are the c, a, b of gbsbin_cumulants3).  Each e_l
+ * depends on t_l alone and every derivative of e^t is 1 at 0, so kappa is the sum over the
+ * set partitions of the four index slots whose blocks each carry a single group of F_r (the
+ * blocks' groups), F_r(m1..mr) = sum over the orders of (m1..mr) of C_r.  Unfolded (no cutoff
+ * enters).  Host only, FP64, O(n^3 + L^4 (n/L)^2); k4: L^4 doubles, row-major, caller-owned
+ * host memory.  Errors: as gbsbin_moments.
+ */
+int gbsbin_cumulants4(const gbsbin_problem* p, double* k4);
+
+/*
  * Fock inputs through a lossy linear circuit (App. C of the paper).  photons[j] >= 0
  * photons enter input port j of the M x M transfer matrix T (T[i*M + j]: output i <- input
  * j, ||T||_2 <= 1), the output ports are grouped as for Gaussian states, and the library

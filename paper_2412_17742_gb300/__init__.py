@@ -35,7 +35,7 @@ EXPORTED = ["gbsbin_default_options", "gbsbin_plan_create", "gbsbin_plan_set_sta
             "gbsbin_batch_diagnostics", "gbsbin_batch_read_points", "gbsbin_batch_destroy", "gbsbin_moments",
             "gbsbin_fock_plan_create", "gbsbin_fock_plan_set_transfer", "gbsbin_fock_plan_table_size",
             "gbsbin_fock_execute", "gbsbin_fock_execute_host", "gbsbin_fock_diagnostics",
-            "gbsbin_fock_plan_destroy", "gbsbin_cumulants3", "gbsbin_fock_plan_nodes"]
+            "gbsbin_fock_plan_destroy", "gbsbin_cumulants3", "gbsbin_cumulants4", "gbsbin_fock_plan_nodes"]
 
 
 class GbsbinError(RuntimeError):
@@ -109,6 +109,8 @@ def load():
     lib.gbsbin_moments.argtypes = [ctypes.POINTER(gbsbin_problem), vp, vp]
     lib.gbsbin_cumulants3.argtypes = [ctypes.POINTER(gbsbin_problem), vp]
     lib.gbsbin_cumulants3.restype = ctypes.c_int
+    lib.gbsbin_cumulants4.argtypes = [ctypes.POINTER(gbsbin_problem), vp]
+    lib.gbsbin_cumulants4.restype = ctypes.c_int
     lib.gbsbin_read_points.argtypes = [vp, vp, vp, vp]
     lib.gbsbin_table_from_logq_noalloc.argtypes = [ctypes.c_int, _ip, ctypes.c_int, vp, vp, vp]
     lib.gbsbin_backward.argtypes = [vp, vp, ctypes.POINTER(gbsbin_grads), vp]
@@ -349,6 +351,16 @@ def gbsbin_cumulants3(prob):
     k3 = np.zeros((L, L, L), dtype=np.float64)
     _check(load().gbsbin_cumulants3(ctypes.byref(args.c), k3.ctypes.data_as(ctypes.c_void_p)), "gbsbin_cumulants3")
     return k3
+
+
+def gbsbin_cumulants4(prob):
+    """Exact fourth cumulants kappa_{l1 l2 l3 l4} of the binned counts (host FP64), an
+    (L, L, L, L) array."""
+    args = ProblemArgs(prob)
+    L = int(len(args.cut))
+    k4 = np.zeros((L, L, L, L), dtype=np.float64)
+    _check(load().gbsbin_cumulants4(ctypes.byref(args.c), k4.ctypes.data_as(ctypes.c_void_p)), "gbsbin_cumulants4")
+    return k4
 
 
 def gbsbin_alu_peak(precision, blocks, stream=None):

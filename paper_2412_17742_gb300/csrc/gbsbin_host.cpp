@@ -1501,6 +1501,164 @@ int gbsbin_cumulants3(const gbsbin_problem* p, double* k3) {
   return GBSBIN_OK;
 }
 
+// Fourth cumulants: the order-1..4 coefficients C_r of log G in e (C_r = tr((EW)^r) / (2r)
+// + 1/2 v^T E (W E)^(r-1) u, summed per group of each index) from block products of W, then
+// the chain rule from e_l = e^{t_l} - 1 (every derivative of e^t is 1 at 0, and e_l depends
+// on t_l alone): kappa_{l1..l4} = sum over the set partitions of the four slots whose blocks
+// each carry one group of F_r(the blocks' groups), F_r the fully symmetrised C_r.
+int gbsbin_cumulants4(const gbsbin_problem* p, double* k4) {
+  if (!p || !k4) return GBSBIN_ERR_ARG;
+  int n = 0;
+  std::vector<int> lab;
+  std::vector<cd> W, u, v;
+  int st = moment_algebra(p, n, lab, W, u, v);
+  if (st) return st;
+  const int L = p->L;
+  std::vector<std::vector<int>> rows(L);             // the rows of each group
+  for (int i = 0; i < n; ++i) rows[lab[i]].push_back(i);
+  // blocks W_ab (rows of a, columns of b), dense row-major
+  auto blk = [&](int a, int b) {
+    std::vector<cd> B(rows[a].size() * rows[b].size());
+    for (size_t i = 0; i < rows[a].size(); ++i)
+      for (size_t j = 0; j < rows[b].size(); ++j) B[i * rows[b].size() + j] = W[(size_t)rows[a][i] * n + rows[b][j]];
+    return B;
+  };
+  std::vector<std::vector<cd>> Wb((size_t)L * L);
+  for (int a = 0; a < L; ++a)
+    for (int b = 0; b < L; ++b) Wb[(size_t)a * L + b] = blk(a, b);
+  auto Wab = [&](int a, int b) -> const std::vector<cd>& { return Wb[(size_t)a * L + b]; };
+  auto sz = [&](int a) { return rows[a].size(); };
+  // X_abc = W_ab W_bc (|a| x |c|)
+  std::vector<std::vector<cd>> X((size_t)L * L * L);
+  for (int a = 0; a < L; ++a)
+    for (int b = 0; b < L; ++b)
+      for (int c = 0; c < L; ++c) {
+        std::vector<cd>& x = X[((size_t)a * L + b) * L + c];
+        x.assign(sz(a) * sz(c), 0.0);
+        const std::vector<cd>& A = Wab(a, b);
+        const std::vector<cd>& B = Wab(b, c);
+        for (size_t i = 0; i < sz(a); ++i)
+          for (size_t k = 0; k < sz(b); ++k) {
+            const cd aik = A[i * sz(b) + k];
+            for (size_t j = 0; j < sz(c); ++j) x[i * sz(c) + j] += aik * B[k * sz(c) + j];
+          }
+      }
+  auto Xabc = [&](int a, int b, int c) -> const std::vector<cd>& { return X[((size_t)a * L + b) * L + c]; };
+  auto vg = [&](int a, size_t i) { return v[rows[a][i]]; };
+  auto ug = [&](int a, size_t i) { return u[rows[a][i]]; };
+  const size_t L2 = (size_t)L * L, L3 = L2 * L;
+  std::vector<cd> C1(L, 0.0), C2(L2, 0.0), C3(L3, 0.0), C4(L3 * L, 0.0);
+  for (int a = 0; a < L; ++a)
+    for (size_t i = 0; i < sz(a); ++i) C1[a] += 0.5 * (Wab(a, a)[i * sz(a) + i] + vg(a, i) * ug(a, i));
+  for (int a = 0; a < L; ++a)
+    for (int b = 0; b < L; ++b) {
+      cd tr = 0.0, vec = 0.0;
+      const std::vector<cd>& A = Wab(a, b);
+      const std::vector<cd>& B = Wab(b, a);
+      for (size_t i = 0; i < sz(a); ++i)
+        for (size_t j = 0; j < sz(b); ++j) {
+          tr += A[i * sz(b) + j] * B[j * sz(a) + i];
+          vec += vg(a, i) * A[i * sz(b) + j] * ug(b, j);
+        }
+      C2[(size_t)a * L + b] = tr / 4.0 + 0.5 * vec;
+    }
+  // q_cd = W_cd u_d (over the rows of c), p_abc = v_a^T X_abc (over the rows of c)
+  std::vector<std::vector<cd>> q(L2), pv(L3);
+  for (int c = 0; c < L; ++c)
+    for (int d = 0; d < L; ++d) {
+      std::vector<cd>& y = q[(size_t)c * L + d];
+      y.assign(sz(c), 0.0);
+      for (size_t i = 0; i < sz(c); ++i)
+        for (size_t j = 0; j < sz(d); ++j) y[i] += Wab(c, d)[i * sz(d) + j] * ug(d, j);
+    }
+  for (int a = 0; a < L; ++a)
+    for (int b = 0; b < L; ++b)
+      for (int c = 0; c < L; ++c) {
+        std::vector<cd>& y = pv[((size_t)a * L + b) * L + c];
+        y.assign(sz(c), 0.0);
+        const std::vector<cd>& x = Xabc(a, b, c);
+        for (size_t i = 0; i < sz(a); ++i)
+          for (size_t j = 0; j < sz(c); ++j) y[j] += vg(a, i) * x[i * sz(c) + j];
+      }
+  for (int a = 0; a < L; ++a)
+    for (int b = 0; b < L; ++b)
+      for (int c = 0; c < L; ++c) {
+        cd tr = 0.0, vec = 0.0;
+        const std::vector<cd>& x = Xabc(a, b, c);
+        const std::vector<cd>& w = Wab(c, a);
+        for (size_t i = 0; i < sz(a); ++i)
+          for (size_t k = 0; k < sz(c); ++k) tr += x[i * sz(c) + k] * w[k * sz(a) + i];
+        const std::vector<cd>& y = pv[((size_t)a * L + b) * L + c];
+        for (size_t k = 0; k < sz(c); ++k) vec += y[k] * ug(c, k);
+        C3[((size_t)a * L + b) * L + c] = tr / 6.0 + 0.5 * vec;
+      }
+  for (int a = 0; a < L; ++a)
+    for (int b = 0; b < L; ++b)
+      for (int c = 0; c < L; ++c)
+        for (int d = 0; d < L; ++d) {
+          // tr(X_abc X_cda) and p_abc . q_cd
+          cd tr = 0.0, vec = 0.0;
+          const std::vector<cd>& x1 = Xabc(a, b, c);
+          const std::vector<cd>& x2 = Xabc(c, d, a);
+          for (size_t i = 0; i < sz(a); ++i)
+            for (size_t k = 0; k < sz(c); ++k) tr += x1[i * sz(c) + k] * x2[k * sz(a) + i];
+          const std::vector<cd>& y = pv[((size_t)a * L + b) * L + c];
+          const std::vector<cd>& z = q[(size_t)c * L + d];
+          for (size_t k = 0; k < sz(c); ++k) vec += y[k] * z[k];
+          C4[(((size_t)a * L + b) * L + c) * L + d] = tr / 8.0 + 0.5 * vec;
+        }
+  // F_r: the r-th mixed partial at e = 0, the sum of C_r over the orders of its indices
+  auto F1 = [&](int a) { return C1[a]; };
+  auto F2 = [&](int a, int b) { return C2[(size_t)a * L + b] + C2[(size_t)b * L + a]; };
+  auto F3 = [&](int a, int b, int c) {
+    const int m[3] = {a, b, c};
+    static const int P3[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+    cd t = 0.0;
+    for (const auto& o : P3) t += C3[((size_t)m[o[0]] * L + m[o[1]]) * L + m[o[2]]];
+    return t;
+  };
+  auto F4 = [&](int a, int b, int c, int d) {
+    int o[4] = {0, 1, 2, 3};
+    const int m[4] = {a, b, c, d};
+    cd t = 0.0;
+    do {
+      t += C4[(((size_t)m[o[0]] * L + m[o[1]]) * L + m[o[2]]) * L + m[o[3]]];
+    } while (std::next_permutation(o, o + 4));
+    return t;
+  };
+  for (int l0 = 0; l0 < L; ++l0)
+    for (int l1 = 0; l1 < L; ++l1)
+      for (int l2 = 0; l2 < L; ++l2)
+        for (int l3 = 0; l3 < L; ++l3) {
+          const int g[4] = {l0, l1, l2, l3};
+          cd kap = F4(l0, l1, l2, l3);                 // four singletons
+          // one pair, two singletons (6 pairs)
+          for (int x = 0; x < 4; ++x)
+            for (int y = x + 1; y < 4; ++y) {
+              if (g[x] != g[y]) continue;
+              int r[2], k = 0;
+              for (int z = 0; z < 4; ++z)
+                if (z != x && z != y) r[k++] = g[z];
+              kap += F3(g[x], r[0], r[1]);
+            }
+          // two pairs (3 ways)
+          const int PP[3][4] = {{0, 1, 2, 3}, {0, 2, 1, 3}, {0, 3, 1, 2}};
+          for (const auto& pp : PP)
+            if (g[pp[0]] == g[pp[1]] && g[pp[2]] == g[pp[3]]) kap += F2(g[pp[0]], g[pp[2]]);
+          // a triple and a singleton (4 ways)
+          for (int z = 0; z < 4; ++z) {
+            int t[3], k = 0;
+            for (int w = 0; w < 4; ++w)
+              if (w != z) t[k++] = g[w];
+            if (t[0] == t[1] && t[1] == t[2]) kap += F2(t[0], g[z]);
+          }
+          // all four in one block
+          if (l0 == l1 && l1 == l2 && l2 == l3) kap += F1(l0);
+          k4[(((size_t)l0 * L + l1) * L + l2) * L + l3] = kap.real();
+        }
+  return GBSBIN_OK;
+}
+
 int gbsbin_alu_peak(int precision, int blocks, double* tflops, void* stream) {
   if (!tflops || blocks <= 0) return GBSBIN_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;

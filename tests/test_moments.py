@@ -1,5 +1,6 @@
-"""Exact binned means and covariances (gbsbin_moments, host FP64, no GPU) against textbook
-single-mode results and against the moments of the oracle's unfolded (oversampled) tables."""
+"""Exact binned means, covariances and third and fourth cumulants (gbsbin_moments,
+gbsbin_cumulants3, gbsbin_cumulants4; host FP64, no GPU) against textbook single-mode results
+and against the central moments of the oracle's unfolded (oversampled) tables."""
 import numpy as np
 import pytest
 
@@ -107,3 +108,56 @@ def test_third_cumulants_against_unfolded_tables(gb, M, K, L, cut, disp, basis):
     # symmetric in its three indices
     for perm in [(0, 2, 1), (1, 0, 2), (2, 1, 0)]:
         assert np.abs(k3 - k3.transpose(perm)).max() < 1e-12
+
+
+# ------------------------------------------------------------------ fourth cumulants
+def test_fourth_cumulant_single_modes(gb):
+    # squeezed vacuum: the fourth derivative of -1/2 log(1 + s - s e^{2t}) at 0 is
+    # 8 s (1 + s)(1 + 6 s + 6 s^2), s = sinh^2 r; coherent state: Poisson (every cumulant is
+    # the mean); a squeezed displaced single mode: the fourth central moment minus 3 var^2
+    # of its photon-number distribution (oracle table, unfolded)
+    r = 0.6
+    s = np.sinh(r) ** 2
+    k4 = gb.gbsbin_cumulants4(_one_mode(r))
+    assert abs(k4[0, 0, 0, 0] - 8 * s * (1 + s) * (1 + 6 * s + 6 * s * s)) < 1e-11
+    a = 0.7 + 0.5j
+    k4 = gb.gbsbin_cumulants4(_one_mode(0.0, a))
+    assert abs(k4[0, 0, 0, 0] - abs(a) ** 2) < 1e-13
+    prob = _one_mode(0.3, 0.4 - 0.2j, eta=0.8)
+    # 32 bins: the squeezed tail is below 1e-16 there, and the table's roundoff weighted by
+    # (b - mean)^4 stays near 1e-10 (a wider table amplifies it, a narrower one truncates)
+    P = oracle.binned(prob, radix=np.array([32]))["P"]
+    b = np.arange(P.shape[0])
+    mu = (P * b).sum()
+    m2, m4 = (P * (b - mu) ** 2).sum(), (P * (b - mu) ** 4).sum()
+    assert abs(gb.gbsbin_cumulants4(prob)[0, 0, 0, 0] - (m4 - 3 * m2 * m2)) < 2e-9
+
+
+def _central(P, L):
+    grids = np.meshgrid(*[np.arange(sz) for sz in P.shape], indexing="ij")
+    mu = [(P * g).sum() for g in grids]
+    return [g - m for g, m in zip(grids, mu)]
+
+
+@pytest.mark.parametrize("M,K,L,cut,disp,basis", [(4, 1, 2, 6, True, False), (3, 2, 2, 5, False, True),
+                                                  (3, 1, 3, 4, True, False), (4, 1, 4, 3, True, False)])
+def test_fourth_cumulants_against_unfolded_tables(gb, M, K, L, cut, disp, basis):
+    # kappa_ijkl = mu_ijkl - mu_ij mu_kl - mu_ik mu_jl - mu_il mu_jk, central moments of the
+    # unfolded table; the first three orders must agree with gbsbin_moments / cumulants3
+    rng = np.random.default_rng(970 + M + K + L)
+    prob = synth.random_problem(rng, M, K, L, cut, displaced=disp, internal_basis=basis, r_range=(0.1, 0.4))
+    k4 = gb.gbsbin_cumulants4(prob)
+    # the table's own accuracy bounds the reference: too few bins truncate the tail, too many
+    # weight the table's roundoff by (b - mean)^4; these oversamplings sit near the optimum
+    over = 6 if L <= 3 else 5
+    P = oracle.binned(prob, radix=prob.radix * over)["P"]
+    d = _central(P, L)
+    c2 = np.array([[(P * d[i] * d[j]).sum() for j in range(L)] for i in range(L)])
+    ref = np.zeros((L,) * 4)
+    for i, j, k, l in np.ndindex(*(L,) * 4):
+        ref[i, j, k, l] = ((P * d[i] * d[j] * d[k] * d[l]).sum()
+                           - c2[i, j] * c2[k, l] - c2[i, k] * c2[j, l] - c2[i, l] * c2[j, k])
+    assert np.abs(k4 - ref).max() < 1e-8 * max(1.0, np.abs(k4).max()), np.abs(k4 - ref).max()
+    # symmetric in its four indices
+    for perm in [(1, 0, 2, 3), (0, 2, 1, 3), (0, 1, 3, 2), (3, 1, 2, 0)]:
+        assert np.abs(k4 - k4.transpose(perm)).max() < 1e-12
