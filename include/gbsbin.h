@@ -376,6 +376,18 @@ int gbsbin_cumulants3(const gbsbin_problem* p, double* k3);
 int gbsbin_cumulants4(const gbsbin_problem* p, double* k4);
 
 /*
+ * Total photon-number distribution Pr(N), N = 0..Nmax, over all detectors (grouping
+ * ignored), by the power series of Sec. IV / App. A: with z = (eta, ..., eta),
+ * log q(eta) = sum_k a_k eta^k, a_k = tr((XA)^k) / (2k) + 1/2 gamma^T (XA)^(k-1) X gamma,
+ * and Pr(N) = Pr(0) [eta^N] exp(sum_k a_k eta^k), Pr(0) = 1 / q(1).  Unfolded (exact up to
+ * rounding; no grid).  A second evaluator beside the roots-of-unity transform of the
+ * one-group plans.  Host only, FP64, O(Nmax n^3) (the powers of XA by repeated
+ * multiplication); P_out: Nmax + 1 doubles, caller-owned host memory.  Errors: ERR_ARG
+ * (Nmax < 0, null pointers), then as gbsbin_moments.
+ */
+int gbsbin_total_photon_series(const gbsbin_problem* p, int Nmax, double* P_out);
+
+/*
  * Fock inputs through a lossy linear circuit (App. C of the paper).  photons[j] >= 0
  * photons enter input port j of the M x M transfer matrix T (T[i*M + j]: output i <- input
  * j, ||T||_2 <= 1), the output ports are grouped as for Gaussian states, and the library

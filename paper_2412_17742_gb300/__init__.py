@@ -35,7 +35,8 @@ EXPORTED = ["gbsbin_default_options", "gbsbin_plan_create", "gbsbin_plan_set_sta
             "gbsbin_batch_diagnostics", "gbsbin_batch_read_points", "gbsbin_batch_destroy", "gbsbin_moments",
             "gbsbin_fock_plan_create", "gbsbin_fock_plan_set_transfer", "gbsbin_fock_plan_table_size",
             "gbsbin_fock_execute", "gbsbin_fock_execute_host", "gbsbin_fock_diagnostics",
-            "gbsbin_fock_plan_destroy", "gbsbin_cumulants3", "gbsbin_cumulants4", "gbsbin_fock_plan_nodes"]
+            "gbsbin_fock_plan_destroy", "gbsbin_cumulants3", "gbsbin_cumulants4", "gbsbin_fock_plan_nodes",
+            "gbsbin_total_photon_series"]
 
 
 class GbsbinError(RuntimeError):
@@ -111,6 +112,8 @@ def load():
     lib.gbsbin_cumulants3.restype = ctypes.c_int
     lib.gbsbin_cumulants4.argtypes = [ctypes.POINTER(gbsbin_problem), vp]
     lib.gbsbin_cumulants4.restype = ctypes.c_int
+    lib.gbsbin_total_photon_series.argtypes = [ctypes.POINTER(gbsbin_problem), ctypes.c_int, vp]
+    lib.gbsbin_total_photon_series.restype = ctypes.c_int
     lib.gbsbin_read_points.argtypes = [vp, vp, vp, vp]
     lib.gbsbin_table_from_logq_noalloc.argtypes = [ctypes.c_int, _ip, ctypes.c_int, vp, vp, vp]
     lib.gbsbin_backward.argtypes = [vp, vp, ctypes.POINTER(gbsbin_grads), vp]
@@ -361,6 +364,15 @@ def gbsbin_cumulants4(prob):
     k4 = np.zeros((L, L, L, L), dtype=np.float64)
     _check(load().gbsbin_cumulants4(ctypes.byref(args.c), k4.ctypes.data_as(ctypes.c_void_p)), "gbsbin_cumulants4")
     return k4
+
+
+def gbsbin_total_photon_series(prob, Nmax):
+    """Total photon-number distribution Pr(N), N = 0..Nmax, by the power series (host FP64)."""
+    args = ProblemArgs(prob)
+    out = np.zeros(int(Nmax) + 1, dtype=np.float64)
+    _check(load().gbsbin_total_photon_series(ctypes.byref(args.c), int(Nmax), out.ctypes.data_as(ctypes.c_void_p)),
+           "gbsbin_total_photon_series")
+    return out
 
 
 def gbsbin_alu_peak(precision, blocks, stream=None):

@@ -1659,6 +1659,84 @@ int gbsbin_cumulants4(const gbsbin_problem* p, double* k4) {
   return GBSBIN_OK;
 }
 
+// Total photon-number distribution by the power series of App. A (a second evaluator beside
+// the roots-of-unity transform): log q(eta) = sum_k a_k eta^k with a_k = tr((XA)^k) / (2k)
+// + 1/2 gamma^T (XA)^(k-1) X gamma; q's Taylor coefficients e_m follow from e = exp(sum a_k
+// eta^k) by m e_m = sum_{k=1}^m k a_k e_{m-k}; Pr(N) = Pr(0) e_N with Pr(0) = 1 / q(1) from an
+// unpivoted LU of I - XA.  Powers of XA by repeated multiplication: O(Nmax n^3), host FP64.
+int gbsbin_total_photon_series(const gbsbin_problem* p, int Nmax, double* P_out) {
+  if (!p || !P_out || Nmax < 0) return GBSBIN_ERR_ARG;
+  gbsbin_options o;
+  gbsbin_default_options(&o);
+  int st = validate_shape(p, &o);
+  if (st) return st;
+  const int n = 2 * p->M * p->K;
+  std::vector<cd> XA, gamma, Xgamma;
+  int has_gamma = 0;
+  st = build_state(p, n, XA, gamma, Xgamma, &has_gamma);
+  if (st) return st;
+  // log q(1) = 1/2 gamma^T (I - XA)^-1 X gamma - 1/2 log det(I - XA), unpivoted LU (every pivot
+  // has Re > 0, so the sum of principal logarithms is the branch of the series)
+  std::vector<cd> K((size_t)n * n);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) K[(size_t)i * n + j] = (i == j ? 1.0 : 0.0) - XA[(size_t)i * n + j];
+  cd logdet = 0.0;
+  std::vector<cd> x(Xgamma);
+  for (int k = 0; k < n; ++k) {
+    const cd piv = K[(size_t)k * n + k];
+    logdet += std::log(piv);
+    for (int i = k + 1; i < n; ++i) {
+      const cd li = K[(size_t)i * n + k] / piv;
+      if (li == cd(0.0)) continue;
+      for (int j = k + 1; j < n; ++j) K[(size_t)i * n + j] -= li * K[(size_t)k * n + j];
+      x[i] -= li * x[k];
+    }
+  }
+  for (int i = n - 1; i >= 0; --i) {                 // x = U^-1 (L^-1 X gamma)
+    cd acc = x[i];
+    for (int j = i + 1; j < n; ++j) acc -= K[(size_t)i * n + j] * x[j];
+    x[i] = acc / K[(size_t)i * n + i];
+  }
+  cd bil = 0.0;
+  for (int i = 0; i < n; ++i) bil += gamma[i] * x[i];
+  const cd logq1 = 0.5 * bil - 0.5 * logdet;
+  // a_k, k = 1..Nmax: traces of M = (XA)^k and w = (XA)^(k-1) X gamma
+  std::vector<cd> a((size_t)Nmax + 1, 0.0), M(XA), T((size_t)n * n), w(Xgamma), w2(n);
+  for (int k = 1; k <= Nmax; ++k) {
+    cd tr = 0.0, g = 0.0;
+    for (int i = 0; i < n; ++i) tr += M[(size_t)i * n + i];
+    for (int i = 0; i < n; ++i) g += gamma[i] * w[i];
+    a[k] = tr / (2.0 * k) + 0.5 * g;
+    if (k == Nmax) break;
+    std::fill(T.begin(), T.end(), cd(0.0));          // M <- M XA
+    for (int i = 0; i < n; ++i)
+      for (int q = 0; q < n; ++q) {
+        const cd m = M[(size_t)i * n + q];
+        if (m == cd(0.0)) continue;
+        const cd* xr = &XA[(size_t)q * n];
+        cd* tr_ = &T[(size_t)i * n];
+        for (int j = 0; j < n; ++j) tr_[j] += m * xr[j];
+      }
+    M.swap(T);
+    for (int i = 0; i < n; ++i) {                    // w <- XA w
+      cd acc = 0.0;
+      for (int j = 0; j < n; ++j) acc += XA[(size_t)i * n + j] * w[j];
+      w2[i] = acc;
+    }
+    w.swap(w2);
+  }
+  std::vector<cd> e((size_t)Nmax + 1, 0.0);
+  e[0] = 1.0;
+  for (int m = 1; m <= Nmax; ++m) {
+    cd acc = 0.0;
+    for (int k = 1; k <= m; ++k) acc += (double)k * a[k] * e[m - k];
+    e[m] = acc / (double)m;
+  }
+  const cd pr0 = std::exp(-logq1);
+  for (int m = 0; m <= Nmax; ++m) P_out[m] = (pr0 * e[m]).real();
+  return GBSBIN_OK;
+}
+
 int gbsbin_alu_peak(int precision, int blocks, double* tflops, void* stream) {
   if (!tflops || blocks <= 0) return GBSBIN_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;

@@ -96,3 +96,17 @@ def test_one_group_state_changes_and_errors(cuda_lib):
             st, d = p.diagnostics()
             assert st == 0 and d["kernel_name"] == "hess_fp64"
             assert np.abs(Pn - oracle.binned(new)["P"]).max() <= 1e-10
+
+
+def test_hessenberg_table_matches_power_series(cuda_lib):
+    # two evaluators of the total photon-number distribution: the roots-of-unity transform
+    # of the one-group plan (Hessenberg kernel) and the power series of App. A (host); the
+    # grid's folding is far below the bound at this squeezing (mean about 2 photons)
+    gb = cuda_lib
+    prob = synth.random_problem(np.random.default_rng(1001), 20, 1, 1, 40, displaced=True, r_range=(0.1, 0.35))
+    with gb.Plan(prob) as p:
+        P = p.table().cpu().numpy()
+        st, d = p.diagnostics()
+    assert st == 0 and d["kernel_name"] == "hess_fp64"
+    ref = gb.gbsbin_total_photon_series(prob, 40)
+    assert np.abs(P - ref).max() < 1e-12
