@@ -388,6 +388,23 @@ int gbsbin_cumulants4(const gbsbin_problem* p, double* k4);
 int gbsbin_total_photon_series(const gbsbin_problem* p, int Nmax, double* P_out);
 
 /*
+ * Joint cumulant <<n_S1 n_S2 ... n_Sr>> of the counts of r distinct groups (bit l of `mask`
+ * selects group l): the coarse-grained loop Montrealer of Sec. VI.  With distinct groups only
+ * the all-singleton set partition enters the chain rule from e = e^t - 1, so
+ *   kappa_S = 1/2 sum over the directed Hamiltonian cycles a -> b -> ... -> a through S of
+ *             tr(W_ab W_bc ... W_za)
+ *           + 1/2 sum over the Hamiltonian paths a -> ... -> z through S of
+ *             v_a^T W_ab ... W_yz u_z
+ * (W, u, v as for gbsbin_moments; W_ab the block of rows of group a, columns of group b);
+ * r = 1, 2, 3, 4 give the mean, the covariance and the distinct-index entries of
+ * gbsbin_cumulants3/4.  Dynamic programming over the subsets of S, O(2^r r^2 (n/r)^3), host
+ * FP64; *kappa: one double.  Errors: ERR_ARG (mask empty or naming a group >= L, null
+ * pointers), ERR_UNSUPPORTED (more than 10 groups, or above ~1 GB of partial products),
+ * then as gbsbin_moments.
+ */
+int gbsbin_cumulant_groups(const gbsbin_problem* p, unsigned mask, double* kappa);
+
+/*
  * Fock inputs through a lossy linear circuit (App. C of the paper).  photons[j] >= 0
  * photons enter input port j of the M x M transfer matrix T (T[i*M + j]: output i <- input
  * j, ||T||_2 <= 1), the output ports are grouped as for Gaussian states, and the library

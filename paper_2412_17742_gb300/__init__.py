@@ -36,7 +36,7 @@ EXPORTED = ["gbsbin_default_options", "gbsbin_plan_create", "gbsbin_plan_set_sta
             "gbsbin_fock_plan_create", "gbsbin_fock_plan_set_transfer", "gbsbin_fock_plan_table_size",
             "gbsbin_fock_execute", "gbsbin_fock_execute_host", "gbsbin_fock_diagnostics",
             "gbsbin_fock_plan_destroy", "gbsbin_cumulants3", "gbsbin_cumulants4", "gbsbin_fock_plan_nodes",
-            "gbsbin_total_photon_series"]
+            "gbsbin_total_photon_series", "gbsbin_cumulant_groups"]
 
 
 class GbsbinError(RuntimeError):
@@ -114,6 +114,8 @@ def load():
     lib.gbsbin_cumulants4.restype = ctypes.c_int
     lib.gbsbin_total_photon_series.argtypes = [ctypes.POINTER(gbsbin_problem), ctypes.c_int, vp]
     lib.gbsbin_total_photon_series.restype = ctypes.c_int
+    lib.gbsbin_cumulant_groups.argtypes = [ctypes.POINTER(gbsbin_problem), ctypes.c_uint, vp]
+    lib.gbsbin_cumulant_groups.restype = ctypes.c_int
     lib.gbsbin_read_points.argtypes = [vp, vp, vp, vp]
     lib.gbsbin_table_from_logq_noalloc.argtypes = [ctypes.c_int, _ip, ctypes.c_int, vp, vp, vp]
     lib.gbsbin_backward.argtypes = [vp, vp, ctypes.POINTER(gbsbin_grads), vp]
@@ -373,6 +375,21 @@ def gbsbin_total_photon_series(prob, Nmax):
     _check(load().gbsbin_total_photon_series(ctypes.byref(args.c), int(Nmax), out.ctypes.data_as(ctypes.c_void_p)),
            "gbsbin_total_photon_series")
     return out
+
+
+def gbsbin_cumulant_groups(prob, groups):
+    """Joint cumulant of the counts of the distinct groups in `groups` (the coarse-grained loop
+    Montrealer; host FP64)."""
+    mask = 0
+    for g in groups:
+        if mask >> int(g) & 1:
+            raise ValueError("groups must be distinct")
+        mask |= 1 << int(g)
+    args = ProblemArgs(prob)
+    out = ctypes.c_double()
+    _check(load().gbsbin_cumulant_groups(ctypes.byref(args.c), ctypes.c_uint(mask), ctypes.byref(out)),
+           "gbsbin_cumulant_groups")
+    return out.value
 
 
 def gbsbin_alu_peak(precision, blocks, stream=None):

@@ -1737,6 +1737,95 @@ int gbsbin_total_photon_series(const gbsbin_problem* p, int Nmax, double* P_out)
   return GBSBIN_OK;
 }
 
+// Joint cumulant of the counts of a set S of distinct groups (the coarse-grained loop
+// Montrealer): with distinct groups only the all-singleton partition enters the chain rule,
+// so kappa_S = sum over the orders of S of C_|S| = 1/2 sum over the directed Hamiltonian
+// cycles through S of tr(W_ab W_bc ... W_za) + 1/2 sum over the Hamiltonian paths of
+// v_a^T W_ab ... W_yz u_z.  Both by dynamic programming over the subsets of S: cycles start
+// at the smallest group of S (one rotation each), paths at any group.
+int gbsbin_cumulant_groups(const gbsbin_problem* p, unsigned mask, double* kappa) {
+  if (!p || !kappa || mask == 0u) return GBSBIN_ERR_ARG;
+  int n = 0;
+  std::vector<int> lab;
+  std::vector<cd> W, u, v;
+  int st = moment_algebra(p, n, lab, W, u, v);
+  if (st) return st;
+  const int L = p->L;
+  if (L > 16 || (mask >> L) != 0u) return GBSBIN_ERR_ARG;
+  std::vector<int> grp;                               // the groups of S, ascending
+  for (int l = 0; l < L; ++l)
+    if (mask >> l & 1u) grp.push_back(l);
+  const int r = (int)grp.size();
+  std::vector<std::vector<int>> rows(L);
+  for (int i = 0; i < n; ++i) rows[lab[i]].push_back(i);
+  auto sz = [&](int g) { return rows[grp[g]].size(); };
+  // 2^r x r blocks of |group 0| x |e| entries: at most ten groups and about 1 GB
+  size_t big = 0;
+  for (int g = 0; g < r; ++g) big = std::max(big, sz(g));
+  if (r > 10 || ((size_t)1 << r) * (size_t)r * sz(0) * big * sizeof(cd) > ((size_t)1 << 30))
+    return GBSBIN_ERR_UNSUPPORTED;
+  auto wblk = [&](int a, int b) {                     // W restricted to S's groups a, b
+    std::vector<cd> B(sz(a) * sz(b));
+    for (size_t i = 0; i < sz(a); ++i)
+      for (size_t j = 0; j < sz(b); ++j) B[i * sz(b) + j] = W[(size_t)rows[grp[a]][i] * n + rows[grp[b]][j]];
+    return B;
+  };
+  std::vector<std::vector<cd>> Wb((size_t)r * r);
+  for (int a = 0; a < r; ++a)
+    for (int b = 0; b < r; ++b) Wb[(size_t)a * r + b] = wblk(a, b);
+  const unsigned full = (1u << r) - 1u;
+  // cycles: Pc[m][e] = sum over paths from group 0 through the set m ending at e of the block
+  // products (|0| x |e|); paths: Qp[m][e] = the same for row vectors starting at v_start
+  std::vector<std::vector<cd>> Pc((size_t)(full + 1) * r), Qp((size_t)(full + 1) * r);
+  Pc[(size_t)1u * r + 0].assign(sz(0) * sz(0), 0.0);
+  for (size_t i = 0; i < sz(0); ++i) Pc[(size_t)1u * r + 0][i * sz(0) + i] = 1.0;
+  for (int a = 0; a < r; ++a) {
+    std::vector<cd>& q = Qp[(size_t)(1u << a) * r + a];
+    q.resize(sz(a));
+    for (size_t i = 0; i < sz(a); ++i) q[i] = v[rows[grp[a]][i]];
+  }
+  for (unsigned m = 1; m <= full; ++m)
+    for (int e = 0; e < r; ++e) {
+      if (!(m >> e & 1u) || m == (1u << e)) continue;
+      const unsigned prev = m & ~(1u << e);
+      std::vector<cd>& pc = Pc[(size_t)m * r + e];
+      std::vector<cd>& qp = Qp[(size_t)m * r + e];
+      for (int b = 0; b < r; ++b) {
+        if (!(prev >> b & 1u)) continue;
+        const std::vector<cd>& B = Wb[(size_t)b * r + e];
+        const std::vector<cd>& P0 = Pc[(size_t)prev * r + b];
+        if ((m & 1u) && !P0.empty() && e != 0) {     // cycles keep group 0 as their start
+          if (pc.empty()) pc.assign(sz(0) * sz(e), 0.0);
+          for (size_t i = 0; i < sz(0); ++i)
+            for (size_t k = 0; k < sz(b); ++k) {
+              const cd x = P0[i * sz(b) + k];
+              if (x == cd(0.0)) continue;
+              for (size_t j = 0; j < sz(e); ++j) pc[i * sz(e) + j] += x * B[k * sz(e) + j];
+            }
+        }
+        const std::vector<cd>& Q0 = Qp[(size_t)prev * r + b];
+        if (!Q0.empty()) {
+          if (qp.empty()) qp.assign(sz(e), 0.0);
+          for (size_t k = 0; k < sz(b); ++k)
+            for (size_t j = 0; j < sz(e); ++j) qp[j] += Q0[k] * B[k * sz(e) + j];
+        }
+      }
+    }
+  cd cyc = 0.0, path = 0.0;
+  for (int e = 0; e < r; ++e) {
+    const std::vector<cd>& pc = Pc[(size_t)full * r + e];
+    if (!pc.empty()) {                                 // close the cycle: tr(P W_e0)
+      const std::vector<cd>& B = Wb[(size_t)e * r + 0];
+      for (size_t i = 0; i < sz(0); ++i)
+        for (size_t k = 0; k < sz(e); ++k) cyc += pc[i * sz(e) + k] * B[k * sz(0) + i];
+    }
+    const std::vector<cd>& qp = Qp[(size_t)full * r + e];
+    for (size_t k = 0; k < qp.size(); ++k) path += qp[k] * u[rows[grp[e]][k]];
+  }
+  *kappa = (0.5 * cyc + 0.5 * path).real();
+  return GBSBIN_OK;
+}
+
 int gbsbin_alu_peak(int precision, int blocks, double* tflops, void* stream) {
   if (!tflops || blocks <= 0) return GBSBIN_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;

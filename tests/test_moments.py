@@ -161,3 +161,49 @@ def test_fourth_cumulants_against_unfolded_tables(gb, M, K, L, cut, disp, basis)
     # symmetric in its four indices
     for perm in [(1, 0, 2, 3), (0, 2, 1, 3), (0, 1, 3, 2), (3, 1, 2, 0)]:
         assert np.abs(k4 - k4.transpose(perm)).max() < 1e-12
+
+
+# ------------------------------------------------------------- joint cumulants of distinct groups
+@pytest.mark.parametrize("M,K,L,disp,basis", [(4, 1, 4, True, False), (6, 2, 3, False, True), (5, 1, 5, True, False)])
+def test_distinct_group_cumulants_match_the_tensors(gb, M, K, L, disp, basis):
+    # orders 1-4 of the loop-Montrealer form against the mean, covariance and the
+    # distinct-index entries of the third and fourth cumulant tensors
+    import itertools
+    rng = np.random.default_rng(1100 + M + K + L)
+    prob = synth.random_problem(rng, M, K, L, 3, displaced=disp, internal_basis=basis, r_range=(0.2, 0.6))
+    mean, cov = gb.gbsbin_moments(prob)
+    k3, k4 = gb.gbsbin_cumulants3(prob), gb.gbsbin_cumulants4(prob)
+    for l in range(L):
+        assert abs(gb.gbsbin_cumulant_groups(prob, [l]) - mean[l]) < 1e-12
+    for a, b in itertools.combinations(range(L), 2):
+        assert abs(gb.gbsbin_cumulant_groups(prob, [a, b]) - cov[a, b]) < 1e-12
+    for t in itertools.combinations(range(L), 3):
+        assert abs(gb.gbsbin_cumulant_groups(prob, t) - k3[t]) < 1e-11
+    for t in itertools.combinations(range(L), 4):
+        assert abs(gb.gbsbin_cumulant_groups(prob, t) - k4[t]) < 1e-11
+
+
+def test_fifth_joint_cumulant_against_unfolded_table(gb):
+    # five groups of one mode: kappa_12345 = mu_12345 - sum over the 10 (pair, triple) splits of
+    # mu_pair mu_triple, central moments of the oracle's unfolded table
+    import itertools
+    rng = np.random.default_rng(1200)
+    prob = synth.random_problem(rng, 5, 1, 5, 2, displaced=True, r_range=(0.15, 0.4))
+    P = oracle.binned(prob, radix=prob.radix * 5)["P"]
+    d = _central(P, 5)
+    mu = lambda idx: (P * np.prod([d[i] for i in idx], axis=0)).sum()
+    ref = mu(range(5))
+    for pair in itertools.combinations(range(5), 2):
+        ref -= mu(pair) * mu([i for i in range(5) if i not in pair])
+    got = gb.gbsbin_cumulant_groups(prob, range(5))
+    assert abs(got - ref) < 1e-8 * max(1.0, abs(ref)), (got, ref)
+
+
+def test_distinct_group_cumulant_errors(gb):
+    prob = synth.random_problem(np.random.default_rng(1300), 3, 1, 3, 2)
+    with pytest.raises(ValueError):
+        gb.gbsbin_cumulant_groups(prob, [1, 1])
+    with pytest.raises(gb.GbsbinError):
+        gb.gbsbin_cumulant_groups(prob, [])
+    with pytest.raises(gb.GbsbinError):
+        gb.gbsbin_cumulant_groups(prob, [3])
