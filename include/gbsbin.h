@@ -405,6 +405,21 @@ int gbsbin_total_photon_series(const gbsbin_problem* p, int Nmax, double* P_out)
 int gbsbin_cumulant_groups(const gbsbin_problem* p, unsigned mask, double* kappa);
 
 /*
+ * Fine-grained Pr(n) (pattern[k] photons in external mode k, k < M) of an undisplaced state
+ * whose internal modes are fully distinguishable (App. D): XA block diagonal over the
+ * internal modes (aligned internal bases, each internal mode carrying one source), every
+ * block B_l of rank <= 2.  By the finite differences at integer points,
+ *   Pr(n) = Pr(0) / prod n_k! sum_{m <= n} prod C(n_k, m_k) (-1)^(N - |m|) f_N(m),
+ * f_N(m) = [eta^N] exp(sum_j p_j eta^j / (2j)), p_j = sum_l (lambda1^j + lambda2^j) with the two
+ * eigenvalues of sqrt(D(m)) B_l sqrt(D(m)) from its trace T and Frobenius norm F,
+ * lambda = T/2 +- sqrt(2F^2 - T^2)/2.  prod (n_k + 1) points, O(K M^2 + K N + N^2) each; the
+ * alternating sum cancels (FP64 loses digits as N grows).  Host only.  Errors: ERR_ARG (null
+ * pointers, a negative count), ERR_UNSUPPORTED (displaced, not block diagonal over internal
+ * modes, or a block of rank above 2), then as gbsbin_moments.
+ */
+int gbsbin_prob_distinguishable(const gbsbin_problem* p, const int* pattern, double* prob);
+
+/*
  * Fock inputs through a lossy linear circuit (App. C of the paper).  photons[j] >= 0
  * photons enter input port j of the M x M transfer matrix T (T[i*M + j]: output i <- input
  * j, ||T||_2 <= 1), the output ports are grouped as for Gaussian states, and the library

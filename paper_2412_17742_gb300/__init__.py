@@ -36,7 +36,7 @@ EXPORTED = ["gbsbin_default_options", "gbsbin_plan_create", "gbsbin_plan_set_sta
             "gbsbin_fock_plan_create", "gbsbin_fock_plan_set_transfer", "gbsbin_fock_plan_table_size",
             "gbsbin_fock_execute", "gbsbin_fock_execute_host", "gbsbin_fock_diagnostics",
             "gbsbin_fock_plan_destroy", "gbsbin_cumulants3", "gbsbin_cumulants4", "gbsbin_fock_plan_nodes",
-            "gbsbin_total_photon_series", "gbsbin_cumulant_groups"]
+            "gbsbin_total_photon_series", "gbsbin_cumulant_groups", "gbsbin_prob_distinguishable"]
 
 
 class GbsbinError(RuntimeError):
@@ -116,6 +116,8 @@ def load():
     lib.gbsbin_total_photon_series.restype = ctypes.c_int
     lib.gbsbin_cumulant_groups.argtypes = [ctypes.POINTER(gbsbin_problem), ctypes.c_uint, vp]
     lib.gbsbin_cumulant_groups.restype = ctypes.c_int
+    lib.gbsbin_prob_distinguishable.argtypes = [ctypes.POINTER(gbsbin_problem), _ip, vp]
+    lib.gbsbin_prob_distinguishable.restype = ctypes.c_int
     lib.gbsbin_read_points.argtypes = [vp, vp, vp, vp]
     lib.gbsbin_table_from_logq_noalloc.argtypes = [ctypes.c_int, _ip, ctypes.c_int, vp, vp, vp]
     lib.gbsbin_backward.argtypes = [vp, vp, ctypes.POINTER(gbsbin_grads), vp]
@@ -389,6 +391,17 @@ def gbsbin_cumulant_groups(prob, groups):
     out = ctypes.c_double()
     _check(load().gbsbin_cumulant_groups(ctypes.byref(args.c), ctypes.c_uint(mask), ctypes.byref(out)),
            "gbsbin_cumulant_groups")
+    return out.value
+
+
+def gbsbin_prob_distinguishable(prob, pattern):
+    """Fine-grained Pr(n) of an undisplaced state with fully distinguishable internal modes
+    (App. D; host FP64)."""
+    pat = np.ascontiguousarray(np.asarray(pattern, dtype=np.int32))
+    args = ProblemArgs(prob)
+    out = ctypes.c_double()
+    _check(load().gbsbin_prob_distinguishable(ctypes.byref(args.c), pat.ctypes.data_as(_ip), ctypes.byref(out)),
+           "gbsbin_prob_distinguishable")
     return out.value
 
 

@@ -1826,6 +1826,128 @@ int gbsbin_cumulant_groups(const gbsbin_problem* p, unsigned mask, double* kappa
   return GBSBIN_OK;
 }
 
+// Fine-grained Pr(n) of an undisplaced state whose internal modes are fully
+// distinguishable (App. D): XA (rows and columns of internal mode l: (j K + l) and
+// (MK + j K + l), j < M) is block diagonal over the internal modes with blocks B_l of rank
+// <= 2.  The finite differences at integer points m <= n give
+//   Pr(n) = Pr(0) / prod n_k! * sum_{m <= n} prod C(n_k, m_k) (-1)^(N - |m|) f_N(m),
+// f_N(m) = [eta^N] exp(sum_j p_j(m) eta^j / (2j)), p_j(m) = tr((D(m) XA)^j) = sum_l
+// (lambda1^j + lambda2^j), the two eigenvalues of sqrt(D) B_l sqrt(D) from its trace T and
+// Frobenius norm F (lambda = T/2 +- sqrt(2 F^2 - T^2)/2), D(m) = diag(m) (+) diag(m).
+int gbsbin_prob_distinguishable(const gbsbin_problem* p, const int* pattern, double* prob) {
+  if (!p || !pattern || !prob) return GBSBIN_ERR_ARG;
+  gbsbin_options o;
+  gbsbin_default_options(&o);
+  int st = validate_shape(p, &o);
+  if (st) return st;
+  const int M = p->M, K = p->K, MK = M * K, n = 2 * MK;
+  int N = 0;
+  for (int k = 0; k < M; ++k) {
+    if (pattern[k] < 0) return GBSBIN_ERR_ARG;
+    N += pattern[k];
+  }
+  std::vector<cd> XA, gamma, Xgamma;
+  int has_gamma = 0;
+  st = build_state(p, n, XA, gamma, Xgamma, &has_gamma);
+  if (st) return st;
+  if (has_gamma) return GBSBIN_ERR_UNSUPPORTED;       // App. D: undisplaced states
+  auto idx = [&](int l, int a) { return a < M ? a * K + l : MK + (a - M) * K + l; };   // a < 2M
+  double scale = 0.0;
+  for (const cd& x : XA) scale = std::max(scale, std::abs(x));
+  // block-diagonal over internal modes?
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      const int li = (i % MK) % K, lj = (j % MK) % K;
+      if (li != lj && std::abs(XA[(size_t)i * n + j]) > 1e-12 * std::max(scale, 1.0)) return GBSBIN_ERR_UNSUPPORTED;
+    }
+  // blocks B_l (2M x 2M); rank <= 2 checked through tr(B^3) and tr(B^4) against the two
+  // eigenvalues from the trace and the Frobenius norm
+  const int m2 = 2 * M;
+  std::vector<std::vector<cd>> B(K, std::vector<cd>((size_t)m2 * m2));
+  for (int l = 0; l < K; ++l)
+    for (int a = 0; a < m2; ++a)
+      for (int b = 0; b < m2; ++b) B[l][(size_t)a * m2 + b] = XA[(size_t)idx(l, a) * n + idx(l, b)];
+  auto eig2 = [&](const std::vector<cd>& Bl, const std::vector<double>& w, double& l1, double& l2) {
+    double T = 0.0, F2 = 0.0;                        // of sqrt(D) B sqrt(D), D = diag(w)
+    for (int a = 0; a < m2; ++a) {
+      T += w[a] * Bl[(size_t)a * m2 + a].real();
+      for (int b = 0; b < m2; ++b) F2 += w[a] * w[b] * std::norm(Bl[(size_t)a * m2 + b]);
+    }
+    const double disc = std::sqrt(std::max(0.0, 2.0 * F2 - T * T));
+    l1 = 0.5 * (T + disc);
+    l2 = 0.5 * (T - disc);
+  };
+  for (int l = 0; l < K; ++l) {
+    std::vector<double> ones(m2, 1.0);
+    double l1, l2;
+    eig2(B[l], ones, l1, l2);
+    std::vector<cd> B2((size_t)m2 * m2, 0.0);
+    for (int a = 0; a < m2; ++a)
+      for (int c = 0; c < m2; ++c)
+        for (int b = 0; b < m2; ++b) B2[(size_t)a * m2 + b] += B[l][(size_t)a * m2 + c] * B[l][(size_t)c * m2 + b];
+    cd t3 = 0.0, t4 = 0.0;
+    for (int a = 0; a < m2; ++a)
+      for (int c = 0; c < m2; ++c) {
+        t3 += B2[(size_t)a * m2 + c] * B[l][(size_t)c * m2 + a];
+        t4 += B2[(size_t)a * m2 + c] * B2[(size_t)c * m2 + a];
+      }
+    const double ref = std::max(1.0, l1 * l1 + l2 * l2);
+    if (std::abs(t3 - (l1 * l1 * l1 + l2 * l2 * l2)) > 1e-9 * ref ||
+        std::abs(t4 - (l1 * l1 * l1 * l1 + l2 * l2 * l2 * l2)) > 1e-9 * ref)
+      return GBSBIN_ERR_UNSUPPORTED;                 // a block of rank above 2
+  }
+  // Pr(0) = sqrt(det(I - XA)), the blocks' determinants det(I - B_l) = (1 - l1)(1 - l2)
+  double pr0 = 1.0;
+  for (int l = 0; l < K; ++l) {
+    std::vector<double> ones(m2, 1.0);
+    double l1, l2;
+    eig2(B[l], ones, l1, l2);
+    pr0 *= std::sqrt((1.0 - l1) * (1.0 - l2));
+  }
+  // the sum over m <= n (mixed radix), each term f_N(m) from the power sums
+  std::vector<int> m(M, 0);
+  std::vector<double> w(m2), ps((size_t)N + 1), e((size_t)N + 1);
+  double total = 0.0;
+  while (true) {
+    int msum = 0;
+    double binom = 1.0;
+    for (int k = 0; k < M; ++k) {
+      msum += m[k];
+      double c = 1.0;                                // C(n_k, m_k)
+      for (int q = 1; q <= m[k]; ++q) c = c * (double)(pattern[k] - m[k] + q) / (double)q;
+      binom *= c;
+      w[k] = w[k + M] = (double)m[k];
+    }
+    std::fill(ps.begin(), ps.end(), 0.0);
+    for (int l = 0; l < K; ++l) {
+      double l1, l2;
+      eig2(B[l], w, l1, l2);
+      double x1 = 1.0, x2 = 1.0;
+      for (int j = 1; j <= N; ++j) {
+        x1 *= l1;
+        x2 *= l2;
+        ps[j] += x1 + x2;
+      }
+    }
+    e[0] = 1.0;                                      // e = exp(sum_j ps_j eta^j / (2j))
+    for (int q = 1; q <= N; ++q) {
+      double acc = 0.0;
+      for (int j = 1; j <= q; ++j) acc += 0.5 * ps[j] * e[q - j];   // j a_j = ps_j / 2
+      e[q] = acc / (double)q;
+    }
+    total += (((N - msum) & 1) ? -1.0 : 1.0) * binom * e[N];
+    int k = 0;                                       // next m
+    while (k < M && m[k] == pattern[k]) m[k++] = 0;
+    if (k == M) break;
+    ++m[k];
+  }
+  double fact = 1.0;
+  for (int k = 0; k < M; ++k)
+    for (int q = 2; q <= pattern[k]; ++q) fact *= (double)q;
+  *prob = pr0 * total / fact;
+  return GBSBIN_OK;
+}
+
 int gbsbin_alu_peak(int precision, int blocks, double* tflops, void* stream) {
   if (!tflops || blocks <= 0) return GBSBIN_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
