@@ -1904,42 +1904,77 @@ int gbsbin_prob_distinguishable(const gbsbin_problem* p, const int* pattern, dou
     eig2(B[l], ones, l1, l2);
     pr0 *= std::sqrt((1.0 - l1) * (1.0 - l2));
   }
-  // the sum over m <= n (mixed radix), each term f_N(m) from the power sums
-  std::vector<int> m(M, 0);
-  std::vector<double> w(m2), ps((size_t)N + 1), e((size_t)N + 1);
-  double total = 0.0;
-  while (true) {
-    int msum = 0;
-    double binom = 1.0;
+  // the sum over m <= n in reflected mixed-radix Gray order (one digit changes by +-1 per
+  // point): per block the trace T = sum_k m_k d_k and F^2 = sum_kj m_k m_j S_kj update in
+  // O(M), F^2(m + s e_k) = F^2(m) + 2 s sum_j m_j S_kj + S_kk (App. D), with
+  // d_k = Re(B_kk + B_k+M,k+M), S_kj = |B_kj|^2 + |B_k+M,j+M|^2 + |B_k+M,j|^2 + |B_k,j+M|^2;
+  // both are recomputed from m every 1024 points (rounding cannot drift)
+  std::vector<double> d((size_t)K * M), S((size_t)K * M * M);
+  for (int l = 0; l < K; ++l)
     for (int k = 0; k < M; ++k) {
-      msum += m[k];
-      double c = 1.0;                                // C(n_k, m_k)
-      for (int q = 1; q <= m[k]; ++q) c = c * (double)(pattern[k] - m[k] + q) / (double)q;
-      binom *= c;
-      w[k] = w[k + M] = (double)m[k];
+      d[(size_t)l * M + k] = B[l][(size_t)k * m2 + k].real() + B[l][(size_t)(k + M) * m2 + k + M].real();
+      for (int jj = 0; jj < M; ++jj)
+        S[((size_t)l * M + k) * M + jj] = std::norm(B[l][(size_t)k * m2 + jj]) +
+                                          std::norm(B[l][(size_t)(k + M) * m2 + jj + M]) +
+                                          std::norm(B[l][(size_t)(k + M) * m2 + jj]) +
+                                          std::norm(B[l][(size_t)k * m2 + jj + M]);
     }
+  std::vector<int> m(M, 0), dir(M, 1);
+  std::vector<double> Tl(K, 0.0), F2l(K, 0.0), ps((size_t)N + 1), e((size_t)N + 1);
+  auto recompute = [&]() {
+    for (int l = 0; l < K; ++l) {
+      double T = 0.0, F2 = 0.0;
+      for (int k = 0; k < M; ++k) {
+        T += m[k] * d[(size_t)l * M + k];
+        for (int jj = 0; jj < M; ++jj) F2 += (double)m[k] * m[jj] * S[((size_t)l * M + k) * M + jj];
+      }
+      Tl[l] = T;
+      F2l[l] = F2;
+    }
+  };
+  double binom = 1.0;                                // prod C(n_k, m_k), m = 0
+  int msum = 0;
+  double total = 0.0;
+  long long count = 0;
+  while (true) {
+    if ((count & 1023) == 0) recompute();
     std::fill(ps.begin(), ps.end(), 0.0);
     for (int l = 0; l < K; ++l) {
-      double l1, l2;
-      eig2(B[l], w, l1, l2);
+      const double disc = std::sqrt(std::max(0.0, 2.0 * F2l[l] - Tl[l] * Tl[l]));
+      const double l1 = 0.5 * (Tl[l] + disc), l2 = 0.5 * (Tl[l] - disc);
       double x1 = 1.0, x2 = 1.0;
-      for (int j = 1; j <= N; ++j) {
+      for (int jj = 1; jj <= N; ++jj) {
         x1 *= l1;
         x2 *= l2;
-        ps[j] += x1 + x2;
+        ps[jj] += x1 + x2;
       }
     }
     e[0] = 1.0;                                      // e = exp(sum_j ps_j eta^j / (2j))
     for (int q = 1; q <= N; ++q) {
       double acc = 0.0;
-      for (int j = 1; j <= q; ++j) acc += 0.5 * ps[j] * e[q - j];   // j a_j = ps_j / 2
+      for (int jj = 1; jj <= q; ++jj) acc += 0.5 * ps[jj] * e[q - jj];   // j a_j = ps_j / 2
       e[q] = acc / (double)q;
     }
     total += (((N - msum) & 1) ? -1.0 : 1.0) * binom * e[N];
-    int k = 0;                                       // next m
-    while (k < M && m[k] == pattern[k]) m[k++] = 0;
+    ++count;
+    int k = 0;                                       // next point: the lowest digit that can move
+    while (k < M && (m[k] + dir[k] < 0 || m[k] + dir[k] > pattern[k])) {
+      dir[k] = -dir[k];
+      ++k;
+    }
     if (k == M) break;
-    ++m[k];
+    const int sgn = dir[k];
+    for (int l = 0; l < K; ++l) {
+      double cross = 0.0;
+      for (int jj = 0; jj < M; ++jj) cross += m[jj] * S[((size_t)l * M + k) * M + jj];
+      F2l[l] += 2.0 * sgn * cross + S[((size_t)l * M + k) * M + k];
+      Tl[l] += sgn * d[(size_t)l * M + k];
+    }
+    // C(n, m + 1) = C(n, m) (n - m) / (m + 1); C(n, m - 1) = C(n, m) m / (n - m + 1)
+    binom *= sgn > 0 ? (double)(pattern[k] - m[k]) / (double)(m[k] + 1)
+                     : (double)m[k] / (double)(pattern[k] - m[k] + 1);
+    m[k] += sgn;
+    msum += sgn;
   }
   double fact = 1.0;
   for (int k = 0; k < M; ++k)

@@ -53,6 +53,17 @@ def test_against_the_oracle_fine_grained_table(gb, seed):
         assert abs(got - table[n]) < 1e-12, (n, got, table[n])
 
 
+def test_gray_order_beyond_the_recompute_period(gb):
+    # 6^4 = 1296 evaluation points: the incremental trace / norm updates run past the
+    # recompute after 1024 points; absolute agreement (the alternating sum of a 20-photon
+    # pattern cancels, and the 24-bin table folds at the 1e-12 level at this squeezing)
+    rng = np.random.default_rng(1600)
+    prob = _distinguishable(rng, 4, 5, r=(0.6, 0.9))
+    table = oracle.binned(prob, radix=np.full(4, 24))["P"]
+    for n in [(5, 5, 5, 5), (5, 4, 3, 5), (2, 5, 5, 1)]:
+        assert abs(gb.gbsbin_prob_distinguishable(prob, list(n)) - table[n]) < 1e-10
+
+
 def test_rejects_other_structures(gb):
     rng = np.random.default_rng(1500)
     indist = synth.random_problem(rng, 3, 1, 3, 2)                 # one internal mode, three sources
