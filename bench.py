@@ -221,9 +221,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the other workloads (n=192 grid, 256-problem batch, n=200 gradient, "
-                         "M=256 total photon number, Fock inputs)")
-    ap.add_argument("--extras", default="n192,batch,n200,e3,fock",
-                    help="comma list of the other workloads to time: n192, batch, n200, e3, fock")
+                         "M=256 total photon number, Fock inputs, App. D fine-grained)")
+    ap.add_argument("--extras", default="n192,batch,n200,e3,fock,appd",
+                    help="comma list of the other workloads to time: n192, batch, n200, e3, fock, appd")
     ap.add_argument("--extra-steps", type=int, default=3)
     args = ap.parse_args()
     if args.impl == "reference":
@@ -440,7 +440,40 @@ def extra_workloads(gb, torch, stream, flush, steps, world, which=("n192", "batc
         out.update(_extra_e3(gb, torch, stream, flush, steps, world))
     if "fock" in which:
         out.update(_extra_fock(gb, torch, stream, flush, steps, world))
+    if "appd" in which:
+        try:
+            out.update(_extra_distinguishable(gb, torch, steps))
+        except Exception as ex:                           # reported, never fatal to the bench line
+            out["appd_distinguishable_m16_ones"] = {"error": str(ex)[:200]}
     return out
+
+
+def _extra_distinguishable(gb, torch, steps):
+    """App. D's fine-grained Pr(n) of a fully distinguishable state (16 sources, each in its own
+    internal mode, r ~ U(0.5, 0.9), lossy Haar interferometer; one photon per detector: 2^16 =
+    65536 evaluation points, N = 16, where the alternating sum keeps its digits): the device
+    sum (one thread per point, FP64) against the host sum in Gray-code order, per call (the
+    device call includes its buffer allocation); both values reported."""
+    rng = np.random.default_rng(1700)
+    M = 16
+    r = np.diag(rng.uniform(0.5, 0.9, M))
+    T = np.sqrt(rng.uniform(0.4, 0.9, M))[:, None] * synth.haar_unitary(M, rng)
+    prob = synth.Problem(M, M, r, T, np.arange(M, dtype=np.int32), np.full(M, 1, np.int32))
+    pattern = [1] * M
+    gb.gbsbin_prob_distinguishable_device(prob, pattern)       # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        dev = gb.gbsbin_prob_distinguishable_device(prob, pattern)
+    t_dev = (time.perf_counter() - t0) / steps
+    t0 = time.perf_counter()
+    host = gb.gbsbin_prob_distinguishable(prob, pattern)
+    t_host = time.perf_counter() - t0
+    pts = 2 ** M
+    return {"appd_distinguishable_m16_ones": {"points": pts, "N": M, "device_ms_per_call": t_dev * 1e3,
+                                           "device_points_per_s": pts / t_dev, "host_ms": t_host * 1e3,
+                                           "host_points_per_s": pts / t_host, "prob_device": dev,
+                                           "prob_host": host, "precision": "fp64"}}
 
 
 def _extra_fock(gb, torch, stream, flush, steps, world):

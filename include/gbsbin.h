@@ -420,6 +420,15 @@ int gbsbin_cumulant_groups(const gbsbin_problem* p, unsigned mask, double* kappa
 int gbsbin_prob_distinguishable(const gbsbin_problem* p, const int* pattern, double* prob);
 
 /*
+ * The same Pr(n) with the sum over the prod (n_k + 1) evaluation points on the GPU: one thread
+ * per point (its digits, the rank-2 blocks' eigenvalues, the power sums and the FP64 series),
+ * fixed-order partial sums; host setup as above.  Synchronous on `stream`; device buffers are
+ * allocated and freed per call.  Errors: as gbsbin_prob_distinguishable, ERR_UNSUPPORTED for N
+ * or M above 64, ERR_NOMEM, ERR_CUDA.
+ */
+int gbsbin_prob_distinguishable_device(const gbsbin_problem* p, const int* pattern, double* prob, void* stream);
+
+/*
  * Fock inputs through a lossy linear circuit (App. C of the paper).  photons[j] >= 0
  * photons enter input port j of the M x M transfer matrix T (T[i*M + j]: output i <- input
  * j, ||T||_2 <= 1), the output ports are grouped as for Gaussian states, and the library

@@ -36,7 +36,8 @@ EXPORTED = ["gbsbin_default_options", "gbsbin_plan_create", "gbsbin_plan_set_sta
             "gbsbin_fock_plan_create", "gbsbin_fock_plan_set_transfer", "gbsbin_fock_plan_table_size",
             "gbsbin_fock_execute", "gbsbin_fock_execute_host", "gbsbin_fock_diagnostics",
             "gbsbin_fock_plan_destroy", "gbsbin_cumulants3", "gbsbin_cumulants4", "gbsbin_fock_plan_nodes",
-            "gbsbin_total_photon_series", "gbsbin_cumulant_groups", "gbsbin_prob_distinguishable"]
+            "gbsbin_total_photon_series", "gbsbin_cumulant_groups", "gbsbin_prob_distinguishable",
+            "gbsbin_prob_distinguishable_device"]
 
 
 class GbsbinError(RuntimeError):
@@ -118,6 +119,8 @@ def load():
     lib.gbsbin_cumulant_groups.restype = ctypes.c_int
     lib.gbsbin_prob_distinguishable.argtypes = [ctypes.POINTER(gbsbin_problem), _ip, vp]
     lib.gbsbin_prob_distinguishable.restype = ctypes.c_int
+    lib.gbsbin_prob_distinguishable_device.argtypes = [ctypes.POINTER(gbsbin_problem), _ip, vp, vp]
+    lib.gbsbin_prob_distinguishable_device.restype = ctypes.c_int
     lib.gbsbin_read_points.argtypes = [vp, vp, vp, vp]
     lib.gbsbin_table_from_logq_noalloc.argtypes = [ctypes.c_int, _ip, ctypes.c_int, vp, vp, vp]
     lib.gbsbin_backward.argtypes = [vp, vp, ctypes.POINTER(gbsbin_grads), vp]
@@ -402,6 +405,17 @@ def gbsbin_prob_distinguishable(prob, pattern):
     out = ctypes.c_double()
     _check(load().gbsbin_prob_distinguishable(ctypes.byref(args.c), pat.ctypes.data_as(_ip), ctypes.byref(out)),
            "gbsbin_prob_distinguishable")
+    return out.value
+
+
+def gbsbin_prob_distinguishable_device(prob, pattern, stream=None):
+    """gbsbin_prob_distinguishable with the sum over the evaluation points on the GPU."""
+    pat = np.ascontiguousarray(np.asarray(pattern, dtype=np.int32))
+    args = ProblemArgs(prob)
+    out = ctypes.c_double()
+    _check(load().gbsbin_prob_distinguishable_device(ctypes.byref(args.c), pat.ctypes.data_as(_ip),
+                                                     ctypes.byref(out), _stream_handle(stream)),
+           "gbsbin_prob_distinguishable_device")
     return out.value
 
 

@@ -1834,7 +1834,7 @@ int gbsbin_cumulant_groups(const gbsbin_problem* p, unsigned mask, double* kappa
 // f_N(m) = [eta^N] exp(sum_j p_j(m) eta^j / (2j)), p_j(m) = tr((D(m) XA)^j) = sum_l
 // (lambda1^j + lambda2^j), the two eigenvalues of sqrt(D) B_l sqrt(D) from its trace T and
 // Frobenius norm F (lambda = T/2 +- sqrt(2 F^2 - T^2)/2), D(m) = diag(m) (+) diag(m).
-int gbsbin_prob_distinguishable(const gbsbin_problem* p, const int* pattern, double* prob) {
+static int dist_eval(const gbsbin_problem* p, const int* pattern, double* prob, bool device, void* stream) {
   if (!p || !pattern || !prob) return GBSBIN_ERR_ARG;
   gbsbin_options o;
   gbsbin_default_options(&o);
@@ -1919,6 +1919,16 @@ int gbsbin_prob_distinguishable(const gbsbin_problem* p, const int* pattern, dou
                                           std::norm(B[l][(size_t)(k + M) * m2 + jj]) +
                                           std::norm(B[l][(size_t)k * m2 + jj + M]);
     }
+  double fact = 1.0;
+  for (int k = 0; k < M; ++k)
+    for (int q = 2; q <= pattern[k]; ++q) fact *= (double)q;
+  if (device) {                                      // one thread per point on the GPU
+    double sum = 0.0;
+    st = distinguishable_sum_device(M, K, N, pattern, d.data(), S.data(), &sum, (cudaStream_t)stream);
+    if (st) return st;
+    *prob = pr0 * sum / fact;
+    return GBSBIN_OK;
+  }
   std::vector<int> m(M, 0), dir(M, 1);
   std::vector<double> Tl(K, 0.0), F2l(K, 0.0), ps((size_t)N + 1), e((size_t)N + 1);
   auto recompute = [&]() {
@@ -1976,11 +1986,16 @@ int gbsbin_prob_distinguishable(const gbsbin_problem* p, const int* pattern, dou
     m[k] += sgn;
     msum += sgn;
   }
-  double fact = 1.0;
-  for (int k = 0; k < M; ++k)
-    for (int q = 2; q <= pattern[k]; ++q) fact *= (double)q;
   *prob = pr0 * total / fact;
   return GBSBIN_OK;
+}
+
+int gbsbin_prob_distinguishable(const gbsbin_problem* p, const int* pattern, double* prob) {
+  return dist_eval(p, pattern, prob, false, nullptr);
+}
+
+int gbsbin_prob_distinguishable_device(const gbsbin_problem* p, const int* pattern, double* prob, void* stream) {
+  return dist_eval(p, pattern, prob, true, stream);
 }
 
 int gbsbin_alu_peak(int precision, int blocks, double* tflops, void* stream) {

@@ -224,6 +224,15 @@ cudaError_t launch_finish_logq(const double* ldfin, double2* logq, long long n, 
 cudaError_t launch_dft_fused(const DftArgs& a, unsigned* bar, int num_sms, cudaStream_t s);
 // Nonzero when launch_dft_fused takes the two-phase form for this grid.
 int dft_two_phase(const GridDesc& g);
+
+// App. D's sum over the evaluation points m <= pattern on the device (gbsbin_distinguishable.cu):
+// d (K x M) and S (K x M x M) the rank-2 blocks' trace and Frobenius-norm coefficients; the
+// signed, binomial-weighted sum of f_N(m) to *total.  Synchronous on s; N <= kDistMaxN and
+// M <= kDistMaxM (else GBSBIN_ERR_UNSUPPORTED).
+constexpr int kDistMaxN = 64;
+constexpr int kDistMaxM = 64;
+int distinguishable_sum_device(int M, int K, int N, const int* pattern, const double* d, const double* S,
+                               double* total, cudaStream_t s);
 cudaError_t launch_backward(const BackwardArgs& b, const double* dLdP, cudaStream_t s);
 cudaError_t launch_alu_peak(int fp64, int blocks, float* out_sink, int iters, cudaStream_t s);
 
