@@ -415,7 +415,8 @@ int gbsbin_cumulant_groups(const gbsbin_problem* p, unsigned mask, double* kappa
  * lambda = T/2 +- sqrt(2F^2 - T^2)/2.  prod (n_k + 1) points, O(K M^2 + K N + N^2) each; the
  * alternating sum cancels (FP64 loses digits as N grows).  Host only.  Errors: ERR_ARG (null
  * pointers, a negative count), ERR_UNSUPPORTED (displaced, not block diagonal over internal
- * modes, or a block of rank above 2), then as gbsbin_moments.
+ * modes, a block of rank above 2, or more than 2^40 evaluation points), then as
+ * gbsbin_moments.
  */
 int gbsbin_prob_distinguishable(const gbsbin_problem* p, const int* pattern, double* prob);
 

@@ -1842,9 +1842,12 @@ static int dist_eval(const gbsbin_problem* p, const int* pattern, double* prob, 
   if (st) return st;
   const int M = p->M, K = p->K, MK = M * K, n = 2 * MK;
   int N = 0;
+  long long npts = 1;                                // evaluation points, at most 2^40
   for (int k = 0; k < M; ++k) {
     if (pattern[k] < 0) return GBSBIN_ERR_ARG;
     N += pattern[k];
+    npts *= (long long)pattern[k] + 1;
+    if (npts > (1ll << 40)) return GBSBIN_ERR_UNSUPPORTED;
   }
   std::vector<cd> XA, gamma, Xgamma;
   int has_gamma = 0;

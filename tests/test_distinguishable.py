@@ -75,3 +75,6 @@ def test_rejects_other_structures(gb):
         gb.gbsbin_prob_distinguishable(disp, [1, 1])
     with pytest.raises(gb.GbsbinError):
         gb.gbsbin_prob_distinguishable(_distinguishable(rng, 2, 2), [1, -1])
+    with pytest.raises(gb.GbsbinError) as e:                         # (2^21)^2 > 2^40 points
+        gb.gbsbin_prob_distinguishable(_distinguishable(rng, 2, 2), [1 << 21, 1 << 21])
+    assert e.value.status == 8
