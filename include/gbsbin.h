@@ -383,7 +383,7 @@ int gbsbin_cumulants4(const gbsbin_problem* p, double* k4);
  * rounding; no grid).  A second evaluator beside the roots-of-unity transform of the
  * one-group plans.  Host only, FP64, O(Nmax n^3) (the powers of XA by repeated
  * multiplication); P_out: Nmax + 1 doubles, caller-owned host memory.  Errors: ERR_ARG
- * (Nmax < 0, null pointers), then as gbsbin_moments.
+ * (Nmax < 0, null pointers), ERR_UNSUPPORTED (Nmax > 2^20), then as gbsbin_moments.
  */
 int gbsbin_total_photon_series(const gbsbin_problem* p, int Nmax, double* P_out);
 

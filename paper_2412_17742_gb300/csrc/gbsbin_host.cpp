@@ -1666,6 +1666,7 @@ int gbsbin_cumulants4(const gbsbin_problem* p, double* k4) {
 // unpivoted LU of I - XA.  Powers of XA by repeated multiplication: O(Nmax n^3), host FP64.
 int gbsbin_total_photon_series(const gbsbin_problem* p, int Nmax, double* P_out) {
   if (!p || !P_out || Nmax < 0) return GBSBIN_ERR_ARG;
+  if (Nmax > (1 << 20)) return GBSBIN_ERR_UNSUPPORTED;
   gbsbin_options o;
   gbsbin_default_options(&o);
   int st = validate_shape(p, &o);

@@ -66,3 +66,6 @@ def test_grouping_is_ignored(gb):
 def test_rejects_bad_input(gb):
     with pytest.raises(gb.GbsbinError):
         gb.gbsbin_total_photon_series(_one_mode(0.5), -1)
+    with pytest.raises(gb.GbsbinError) as e:
+        gb.gbsbin_total_photon_series(_one_mode(0.5), (1 << 20) + 1)
+    assert e.value.status == 8
