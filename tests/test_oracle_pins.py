@@ -322,3 +322,35 @@ def test_nonphysical_state_is_flagged():
     XA = 1.5 * np.eye(n, dtype=complex)
     logq, minre, st = oracle.logq_grid(XA, np.zeros(n, complex), np.zeros(n, np.int32), np.array([3]))
     assert st[0] != 0 and minre[0] < 0
+
+
+# ------------------------------------------ per-point evaluation at chosen grid points
+@pytest.mark.parametrize("radix", [(3, 5), (4, 1, 6), (2, 3, 1, 5), (1, 7), (5, 2, 2, 3)])
+def test_logq_points_matches_grid(radix):
+    # oracle.logq_points maps digit rows to flat grid indices (last axis fastest) and
+    # evaluates the same per-point LU as logq_grid: equal bits at every point, in any
+    # order and with repeats; and, independently of the C code, exp(2 log q) equals
+    # exp(gamma^T K^-1 D X gamma) / det K with K = I - D(w) XA formed by numpy (Sec. III,
+    # Eq. q_d; the square removes the square root's branch)
+    L = len(radix)
+    rng = np.random.default_rng(600 + sum(radix))
+    prob = synth.random_problem(rng, max(L, 3), 2, L, [r - 1 for r in radix], displaced=True,
+                                internal_basis=True, shuffle_bins=True)
+    XA, gamma, labels = oracle.plan(prob)
+    R = np.array(radix, dtype=np.int64)
+    full, minre_full, _ = oracle.logq_grid(XA, gamma, labels, R)
+    npts = int(np.prod(R))
+    flat = np.concatenate([rng.permutation(npts), rng.integers(0, npts, 5)])
+    digits = np.stack(np.unravel_index(flat, tuple(radix)), axis=1)
+    lq, minre, st = oracle.logq_points(XA, gamma, labels, R, digits)
+    assert st.max() == 0
+    assert np.array_equal(lq, full[flat]) and np.array_equal(minre, minre_full[flat])
+    n = XA.shape[0]
+    Xg = np.concatenate([gamma[n // 2:], gamma[:n // 2]])
+    for idx in flat[:6]:
+        k = np.unravel_index(idx, tuple(radix))
+        w = np.array([np.exp(2j * np.pi * k[l] / radix[l]) for l in range(L)])[labels]
+        K = np.eye(n) - w[:, None] * XA
+        sq = np.exp(gamma @ np.linalg.solve(K, w * Xg)) / np.linalg.det(K)
+        got = np.exp(2 * lq[np.where(flat == idx)[0][0]])
+        assert abs(got - sq) <= 1e-12 * abs(sq), (radix, k, got, sq)
