@@ -3,18 +3,21 @@
 
 Metric: generating-function points per second (every point of the roots-of-unity grid
 counts; conjugate symmetry means about half are evaluated) and binned P(b) tables per
-second, for the FP32-arithmetic path (``value``: on this grid the tree of block
-eliminations in pairs of FP32, kernel 11) next to the per-point FP32 + refinement warp
-kernel and the per-point FP64 path, all held to |P - P_oracle| <= 1e-10.
+second, for the FP32-arithmetic path (``value``) next to the FP64 path (``fp64``), both held
+to |P - P_oracle| <= 1e-10 and both as a user gets them (automatic kernel choice).
 
-Workload: M = 16 spatial modes, K = 1, r ~ U(0.5, 1.2), T = diag(sqrt(eta)) U with
-eta ~ U(0.4, 0.9) and Haar U, 4 detector groups of 4, N_l = 8: 9^4 = 6561 grid points of
-32 x 32 complex matrices per table.  One step = one table: every device stage of the path
-(grid phases, the per-point factorisation - shared Schur complements down the tree, or one
-LU per point - log det / exponent epilogue, inverse DFT, diagnostics) with the state
-resident in HBM.  ``e2e`` times the
-public C ABI from host buffers: per step the host FP64 state algebra and upload
-(gbsbin_plan_set_state) plus execute and the copy of the table back (gbsbin_execute_host).
+Workload (the largest single-problem configuration): M = 24 spatial x K = 4 internal
+(Schmidt) modes per source with weights lambda_k ~ exp(-k/2), each source in its own seeded
+Haar internal basis (so the 192 x 192 matrices are dense), T = sqrt(0.6) U with U Haar,
+displacement alpha ~ CN(0, 0.1) on 4 inputs, 3 detector groups of 8, N_l = 20: 21^3 = 9261
+grid points of 192 x 192 complex matrices per table.  One step = one table: every device
+stage of the path (grid phases, the factorisations - shared block eliminations down the
+tree of the grid's axes, or one LU per point - the log det / exponent epilogue, the inverse
+DFT, the diagnostics) with the state resident in HBM.  ``e2e`` times the public C ABI from
+host buffers: per step the host FP64 state algebra and upload (gbsbin_plan_set_state), the
+execute and the copy of the table back.  The n = 32 grid (four groups), the 256-problem
+batch, the n = 200 gradient, the M = 256 total photon number, Fock inputs and App. D are
+timed as extras.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
@@ -36,8 +39,8 @@ sys.path.insert(0, ROOT)
 
 import synth  # noqa: E402
 
-WORKLOAD_INDEX = 1
-WORKLOAD_NAME = "M16_K1_L4_N8_n32_6561pts"
+WORKLOAD_INDEX = 2
+WORKLOAD_NAME = "M24_K4_L3_N20_n192_9261pts"
 L2_FLUSH_BYTES = 256 << 20   # > 129 MB L2
 SMS = 152
 SM_MAX_MHZ = 2070.0
@@ -75,6 +78,38 @@ def tree_work(prob, n_eval: int, has_gamma: bool):
     per_leaf = sum((m - kk) ** 2 for kk in range(m)) + (m * m / 2.0 if has_gamma else 0.0)
     macs += n_eval * per_leaf
     return macs, tree_level_launches(prob.radix, prob.L)
+
+
+def btree_work(prob, n_eval: int, has_gamma: bool, smem_slots: int = 200 * 1024 // 16):
+    """The large-matrix tree (kernels 13 and 14): complex multiply-adds per table, as the library
+    counts them.  Level l eliminates its group's nb pivots in sub-steps of nbs (as many as fit
+    the shared-memory budget: nbs (D + 1) <= 12800 16-byte slots, D the augmented dimension):
+    the pivot rows among themselves, sum (nbs - kk - 1)(D - kk - 1), and each of the other
+    D - nbs rows against them, sum (D - kk - 1); per leaf parent a Householder reduction to
+    Hessenberg form, sum over k of 2 (m - k - 1)(m - k + 1) + 2 m (m - k - 1); per evaluated point
+    the Hessenberg elimination, m^2 / 2 (twice that when displaced)."""
+    rows = [2 * prob.K * int(np.sum(prob.bin_of_mode == l)) for l in range(prob.L)]
+    radix = [int(r) for r in prob.radix]
+    m, nodes, macs = prob.n, 1, 0.0
+    for l in range(prob.L - 1):
+        nodes *= radix[l]
+        D = m + 1
+        cap = smem_slots // (D + 1)
+        nsub = -(-rows[l] // cap)
+        per = -(-rows[l] // nsub)
+        p0 = 0
+        while p0 < rows[l]:
+            nbs = min(per, rows[l] - p0)
+            top = sum((nbs - kk - 1) * (D - kk - 1) for kk in range(nbs))
+            row = sum(D - kk - 1 for kk in range(nbs))
+            macs += nodes * (top + (D - nbs) * row)
+            D -= nbs
+            p0 += nbs
+        m -= rows[l]
+    hess = sum(2.0 * (m - k - 1) * (m - k + 1) + 2.0 * m * (m - k - 1) for k in range(m - 2))
+    macs += nodes * hess
+    macs += n_eval * (2.0 if has_gamma else 1.0) * m * m / 2.0
+    return macs
 
 
 def tree_level_launches(radix, L, num_sms=SMS, span_max=4):
@@ -210,20 +245,60 @@ def run_reference(args):
     return 0
 
 
+def _time_plan(gb, torch, plan, table, stream, flush, steps, world):
+    """CUDA events around `steps` executes of one plan on `stream` (L2 flushed between steps,
+    outside the events), with the library's own point-kernel events read back after each
+    step; max over ranks."""
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    kms = []
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter()
+    st, d = 0, None
+    for s in range(steps):
+        flush.zero_()
+        ev[s][0].record(stream)
+        gb.gbsbin_execute(plan.handle, table, stream)
+        ev[s][1].record(stream)
+        st, d = gb.gbsbin_diagnostics(plan.handle, stream)   # syncs; reads the kernel time
+        kms.append(d["point_kernel_ms"])
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    gpu_ms = sum(a.elapsed_time(b) for a, b in ev)
+    if world > 1:
+        t = torch.tensor([gpu_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        gpu_ms = float(t.item())
+    return {"gpu_ms": gpu_ms, "ms_per_step": gpu_ms / steps, "kernel_ms": float(np.mean(kms)), "status": st,
+            "diag": d, "wall_s": t_wall, "steps": steps}
+
+
+def _side_steps(gb, torch, plan, table, stream, steps, budget_s=8.0):
+    """Steps for a plan timed beside the headline: as many as fit in ~budget_s, at most
+    `steps`, at least 3."""
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    gb.gbsbin_execute(plan.handle, table, stream)
+    torch.cuda.synchronize()
+    one = max(time.perf_counter() - t0, 1e-6)
+    return int(max(3, min(steps, budget_s / one)))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1000)
-    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--e2e-steps", type=int, default=200)
-    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--e2e-steps", type=int, default=50)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip the other workloads (n=192 grid, 256-problem batch, n=200 gradient, "
+                    help="skip the other workloads (n=32 grid, 256-problem batch, n=200 gradient, "
                          "M=256 total photon number, Fock inputs, App. D fine-grained)")
-    ap.add_argument("--extras", default="n192,batch,n200,e3,fock,appd",
-                    help="comma list of the other workloads to time: n192, batch, n200, e3, fock, appd")
+    ap.add_argument("--extras", default="n32,batch,n200,e3,fock,appd",
+                    help="comma list of the other workloads to time: n32, batch, n200, e3, fock, appd")
     ap.add_argument("--extra-steps", type=int, default=3)
     args = ap.parse_args()
     if args.impl == "reference":
@@ -245,11 +320,14 @@ def main():
 
     prob = synth.config(WORKLOAD_INDEX)
     npts = prob.n_points
+    n = prob.n
+    has_gamma = prob.alpha is not None
     stream = torch.cuda.current_stream()
-    # precision 1 on this grid runs the tree of block eliminations (FP32 pairs); the per-point
-    # FP32 + refinement warp kernel and the per-point FP64 kernel are timed beside it
-    plans = {1: gb.Plan(prob, precision=1, want_timing=True), 0: gb.Plan(prob, precision=0, want_timing=True),
-             "warp": gb.Plan(prob, precision=1, want_timing=True, tile_override=5)}
+    # precision 1 (FP32 arithmetic) and precision 0 (FP64) as a user gets them (automatic
+    # kernel choice), and the per-point blocked FP32 + refinement kernel beside them
+    plans = {1: gb.Plan(prob, precision=1, want_timing=True), 0: gb.Plan(prob, precision=0, want_timing=True)}
+    if plans[1].diagnostics(stream)[1]["kernel_name"] != "blk_fp32r":
+        plans["blk"] = gb.Plan(prob, precision=1, want_timing=True, tile_override=6)
     tables = {p: torch.empty(plans[p].shape, dtype=torch.float64, device="cuda") for p in plans}
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
@@ -257,159 +335,171 @@ def main():
                   "int64_mad_wide_tops": gb.gbsbin_alu_peak(2, SMS * 8)}
 
     for p in plans:
-        for _ in range(args.warmup):
+        for _ in range(max(args.warmup, 3)):
             gb.gbsbin_execute(plans[p].handle, tables[p], stream)
     torch.cuda.synchronize()
+    steps = {p: (args.steps if p == 1 else _side_steps(gb, torch, plans[p], tables[p], stream, args.steps))
+             for p in plans}
 
     sampler = ClockSampler(local)
     sampler.start()
-    results = {}
-    for p in (1, 0, "warp"):
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-        kms = []
-        if world > 1:
-            torch.distributed.barrier()
-        torch.cuda.synchronize()
-        t_wall = time.perf_counter()
-        for s in range(args.steps):
-            flush.zero_()
-            ev[s][0].record(stream)
-            gb.gbsbin_execute(plans[p].handle, tables[p], stream)
-            ev[s][1].record(stream)
-            st, d = gb.gbsbin_diagnostics(plans[p].handle, stream)   # syncs; reads kernel time
-            kms.append(d["point_kernel_ms"])
-        torch.cuda.synchronize()
-        t_wall = time.perf_counter() - t_wall
-        gpu_ms = sum(a.elapsed_time(b) for a, b in ev)
-        if world > 1:
-            t = torch.tensor([gpu_ms], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            gpu_ms = float(t.item())
-        results[p] = {"gpu_ms": gpu_ms, "ms_per_step": gpu_ms / args.steps, "kernel_ms": float(np.mean(kms)),
-                      "status": st, "diag": d, "wall_s": t_wall}
+    results = {p: _time_plan(gb, torch, plans[p], tables[p], stream, flush, steps[p], world) for p in plans}
     clocks = sampler.stop()
 
-    # end to end through the C ABI with host buffers
-    host_out = torch.empty(plans[1].shape, dtype=torch.float64).pin_memory()
-    host_outs = [host_out, torch.empty(plans[1].shape, dtype=torch.float64).pin_memory()]
+    # end to end through the C ABI with host buffers: per step the host FP64 state algebra
+    # and upload (gbsbin_plan_set_state), the execute and the copy of the table back
+    host_outs = [torch.empty(plans[1].shape, dtype=torch.float64).pin_memory() for _ in range(2)]
     args_prob = gb.ProblemArgs(prob)
-    n = prob.n
-    if plans[1].diagnostics(stream)[1]["kernel_name"] == "tree_df32":
-        h2d = (n * n + 2 * n + 3) * 16      # tree plans upload their permuted state (FP32 pairs) alone
-    else:
-        h2d = n * n * (16 + 8 + 8 + 16) + n * (16 + 16 + 4 * 8)
+    d1 = results[1]["diag"]
+    h2d = d1["state_upload_bytes"]
     d2h = int(np.prod(plans[1].shape)) * 8
     for _ in range(3):
         gb.gbsbin_plan_set_state(plans[1].handle, args_prob, stream)
-        gb.gbsbin_execute_host(plans[1].handle, host_out, stream)
+        gb.gbsbin_execute_host(plans[1].handle, host_outs[0], stream)
     torch.cuda.synchronize()
+    e2e_steps = max(3, min(args.e2e_steps, int(10.0 / max(results[1]["ms_per_step"] * 1e-3, 1e-6))))
     t0 = time.perf_counter()
-    for _ in range(args.e2e_steps):                   # each call returns with the table on the host
+    for _ in range(e2e_steps):                        # each call returns with the table on the host
         gb.gbsbin_plan_set_state(plans[1].handle, args_prob, stream)
-        gb.gbsbin_execute_host(plans[1].handle, host_out, stream)
+        gb.gbsbin_execute_host(plans[1].handle, host_outs[0], stream)
     torch.cuda.synchronize()
-    e2e_sync_value = world * npts * args.e2e_steps / (time.perf_counter() - t0)
+    e2e_sync_value = world * npts * e2e_steps / (time.perf_counter() - t0)
     # pipelined: the host algebra and upload of step i + 1 overlap the device work of step i
-    # (two pinned staging buffers in the plan, two pinned output buffers here); every step
-    # still uploads its state and copies its table back
     t0 = time.perf_counter()
-    for i in range(args.e2e_steps):
+    for i in range(e2e_steps):
         gb.gbsbin_plan_set_state(plans[1].handle, args_prob, stream)
         gb.gbsbin_execute_host_async(plans[1].handle, host_outs[i & 1], stream)
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    e2e_value = world * npts * args.e2e_steps / e2e_s
+    e2e_value = world * npts * e2e_steps / (time.perf_counter() - t0)
 
-    d1 = results[1]["diag"]
-    dw = results["warp"]["diag"]
-    has_gamma = prob.alpha is not None
-    out_points = {p: world * npts * args.steps / (results[p]["gpu_ms"] * 1e-3) for p in results}
+    out_points = {p: world * npts * results[p]["steps"] / (results[p]["gpu_ms"] * 1e-3) for p in results}
     flops_pt = algorithmic_flops(n, has_gamma)
     peak32 = SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
     peak64 = SMS * FP64_FMA_PER_SM_CLK * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    issue32 = SMS * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12    # FP32-pipe operations (T/s)
-    d0 = results[0]["diag"]
-    tree = d1["kernel_name"] == "tree_df32"
-    if d0["kernel_name"] == "tree_fp64":
-        # the same tree in FP64: one complex multiply-add is 4 FP64 FMAs (8 flops)
-        macs64, _ = tree_work(prob, d0["n_evaluated"], has_gamma)
-        achieved64 = 8.0 * macs64 / (results[0]["kernel_ms"] * 1e-3) / 1e12
-        flops64 = {"flops": "tree of block eliminations: 8 x complex multiply-adds per table",
-                   "flops_per_table": 8.0 * macs64}
-    else:
-        achieved64 = flops_pt * d0["n_evaluated"] / (results[0]["kernel_ms"] * 1e-3) / 1e12
-        flops64 = {"flops": "complex LU (8/3) n^3 per evaluated point", "flops_per_point": flops_pt}
-    if tree:
-        macs, levels = tree_work(prob, d1["n_evaluated"], has_gamma)
-        launches_per_step = levels + 2        # level launches, leaves, the DFT with the diagnostics
-        achieved = 8.0 * macs / (results[1]["kernel_ms"] * 1e-3) / 1e12
-        # one complex multiply-add in FP32 pairs: product 38, sum 22, negation 4 operations
-        pipe_achieved = 64.0 * macs / (results[1]["kernel_ms"] * 1e-3) / 1e12
-        roof_extra = {"flops": "tree of block eliminations: 8 x complex multiply-adds per table",
-                      "flops_per_table": 8.0 * macs, "pipe_ops_per_table": 64.0 * macs,
-                      "pipe_unit": "FP32-pipe operations / s (T)", "pipe_peak": issue32,
-                      "pipe_frac": pipe_achieved / issue32}
-    else:
-        launches_per_step = 2                  # point kernel, fused DFT + diagnostics
-        achieved = flops_pt * d1["n_evaluated"] / (results[1]["kernel_ms"] * 1e-3) / 1e12
-        pipe_achieved = pipe_flops(n, has_gamma, 1) * d1["n_evaluated"] / (results[1]["kernel_ms"] * 1e-3) / 1e12
-        roof_extra = {"flops": "complex LU (8/3) n^3 per evaluated point", "flops_per_point": flops_pt,
-                      "pipe_flops_per_point": pipe_flops(n, has_gamma, 1), "pipe_frac": pipe_achieved / peak32}
-    achieved_w = flops_pt * dw["n_evaluated"] / (results["warp"]["kernel_ms"] * 1e-3) / 1e12
-    pipe_w = pipe_flops(n, has_gamma, 1) * dw["n_evaluated"] / (results["warp"]["kernel_ms"] * 1e-3) / 1e12
-    traffic = _profiled_traffic(d1["kernel_name"])
+    tf32_peak = _measured_peaks().get("bf16_tflops", 1973.9) / 2.0   # dense TF32 = BF16 / 2 (nominal ratio)
+
+    def roofline(p, peak, peak_source):
+        r, d = results[p], results[p]["diag"]
+        achieved = flops_pt * d["n_evaluated"] / (r["kernel_ms"] * 1e-3) / 1e12
+        out = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+               "traffic": _profiled_traffic(d["kernel_name"]), "kernel": d["kernel_name"],
+               "kernel_ms": r["kernel_ms"], "peak_source": peak_source,
+               "flops": "method's per-point work: complex unpivoted LU (8/3) n^3 + 8 n^2 exponent solves, "
+                        "per evaluated point", "flops_per_point": flops_pt, "units_per_launch": d["n_evaluated"]}
+        issued = _issued_work(prob, d, p != 0 and d["kernel_name"] != "gmem_fp64")
+        if issued:
+            name, ops, unit, pk = issued
+            out.update({"issued": name, "issued_rate": ops / (r["kernel_ms"] * 1e-3) / 1e12,
+                        "issued_unit": unit, "issued_peak": pk,
+                        "issued_frac": ops / (r["kernel_ms"] * 1e-3) / 1e12 / pk})
+        stale = _traffic_note(d["kernel_name"])
+        if stale:
+            out["traffic_note"] = stale
+        return out
 
     line = {
         "metric": METRIC, "value": out_points[1], "unit": "points/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": results[1]["ms_per_step"], "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32x2" if tree else "f32+f64refine", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32x2" if d1["kernel_name"].endswith("df32") else "f32+f64refine", "data": "synthetic",
         "config": {"workload": WORKLOAD_NAME, "n": n, "grid_points": npts, "evaluated_points": d1["n_evaluated"],
-                   "bins": prob.L, "cutoff": int(prob.cutoff[0]), "precision": "fp32_refine",
-                   "kernel": d1["kernel_name"],
+                   "bins": prob.L, "cutoff": int(prob.cutoff[0]), "internal_modes": prob.K, "displaced": has_gamma,
+                   "precision": "fp32_refine", "kernel": d1["kernel_name"],
                    "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas{world}"},
-        "tables_per_s": world * args.steps / (results[1]["gpu_ms"] * 1e-3),
+        "tables_per_s": world * results[1]["steps"] / (results[1]["gpu_ms"] * 1e-3),
         "fp64": {"value": out_points[0], "unit": "points/s", "ms_per_step": results[0]["ms_per_step"],
-                 "tables_per_s": world * args.steps / (results[0]["gpu_ms"] * 1e-3),
-                 "point_kernel_ms": results[0]["kernel_ms"], "kernel": d0["kernel_name"],
-                 "roofline": dict({"bound": "alu", "achieved": achieved64, "peak": peak64, "unit": "TFLOP/s",
-                                   "frac": achieved64 / peak64, "traffic": _profiled_traffic(d0["kernel_name"]),
-                                   "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 x 2070 MHz"},
-                                  **flops64)},
-        "per_point_fp32_refine": {"kernel": dw["kernel_name"], "value": out_points["warp"], "unit": "points/s",
-                                  "ms_per_step": results["warp"]["ms_per_step"],
-                                  "point_kernel_ms": results["warp"]["kernel_ms"],
-                                  "roofline": {"bound": "alu", "achieved": achieved_w, "peak": peak32,
-                                               "unit": "TFLOP/s", "frac": achieved_w / peak32,
-                                               "pipe_achieved": pipe_w, "pipe_frac": pipe_w / peak32,
-                                               "traffic": _profiled_traffic(dw["kernel_name"])}},
+                 "steps": results[0]["steps"],
+                 "tables_per_s": world * results[0]["steps"] / (results[0]["gpu_ms"] * 1e-3),
+                 "point_kernel_ms": results[0]["kernel_ms"], "kernel": results[0]["diag"]["kernel_name"],
+                 "roofline": roofline(0, peak64, "derived: 152 SMs x 2 FP64 FMA/clk x 2 x 2070 MHz")},
         "speedup_fp32r_vs_fp64": out_points[1] / out_points[0],
-        "roofline": dict({"bound": "alu", "achieved": achieved, "peak": peak32, "unit": "TFLOP/s",
-                          "frac": achieved / peak32, "traffic": traffic,
-                          "kernel": d1["kernel_name"], "kernel_ms": results[1]["kernel_ms"],
-                          "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
-                          "pipe_achieved": pipe_achieved, "measured_alu_chains": peaks_meas}, **roof_extra),
+        "roofline": dict(roofline(1, peak32, "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"),
+                         tensor_peak=tf32_peak, tensor_frac=None,
+                         tensor_note="TF32 dense peak (measured BF16 burst / 2) for context; the point stage "
+                                     "issues no tensor-core instructions on this path",
+                         measured_alu_chains=peaks_meas),
         "e2e": {"value": e2e_value, "unit": "points/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "steps": e2e_steps,
                 "mode": "pipelined: set_state + execute_host_async per step, one synchronise at the end"},
         "e2e_sync": {"value": e2e_sync_value, "unit": "points/s", "h2d_bytes_per_step": h2d,
                      "d2h_bytes_per_step": d2h, "mode": "set_state + execute_host (synchronous) per step"},
-        "gpu_launches": launches_per_step * args.steps,
+        "gpu_launches": int(d1["launches"]) * args.steps,
         "clocks": clocks,
         "diagnostics": {"sum_P": d1["sum_P"], "min_pivot_re": d1["min_pivot_re"],
                         "bad_points": d1["n_bad_points"], "fp64_sum_P": results[0]["diag"]["sum_P"]},
     }
+    if "blk" in results:
+        rb = results["blk"]
+        line["per_point_fp32_refine"] = {"kernel": rb["diag"]["kernel_name"], "value": out_points["blk"],
+                                         "unit": "points/s", "ms_per_step": rb["ms_per_step"],
+                                         "steps": rb["steps"], "point_kernel_ms": rb["kernel_ms"],
+                                         "roofline": roofline("blk", peak32, "derived FP32 peak")}
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"], errs = cpu_baseline(prob, args.cpu_seconds, tables)
+        line["max_abs_err_vs_oracle"] = errs
     for p in plans.values():
         p.close()
     if not args.no_extras:
         which = {w.strip() for w in args.extras.split(",") if w.strip()}
         line["workloads"] = extra_workloads(gb, torch, stream, flush, args.extra_steps, world, which)
-    if rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"], errs = cpu_baseline(prob, args.cpu_seconds, tables)
-        line["max_abs_err_vs_oracle"] = errs
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def _measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def _issued_work(prob, d, fp32):
+    """The arithmetic-pipe work the kernel issues per launch, where it differs from the
+    method's flops: (description, operations, unit, peak).  Per-point FP32 + refinement
+    kernels: pipe_flops against the FP32 peak.  Trees: complex multiply-adds x 64 FP32-pipe
+    operations (pairs) against the FP32 issue rate, or x 8 flops (FP64) against the FP64 peak."""
+    name = d["kernel_name"]
+    n = prob.n
+    has_gamma = prob.alpha is not None
+    issue32 = SMS * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
+    peak32 = 2 * issue32
+    peak64 = SMS * FP64_FMA_PER_SM_CLK * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    if name in ("tree_df32", "tree_fp64"):
+        macs, _ = tree_work(prob, d["n_evaluated"], has_gamma)
+        if name == "tree_df32":
+            return ("tree complex multiply-adds x 64 FP32-pipe operations", 64.0 * macs, "T ops/s", issue32)
+        return ("tree complex multiply-adds x 8 FP64 flops", 8.0 * macs, "TFLOP/s", peak64)
+    if name in ("btree_df32", "btree_fp64"):
+        macs = btree_work(prob, d["n_evaluated"], has_gamma)
+        if name == "btree_df32":
+            return ("tree complex multiply-adds x 64 FP32-pipe operations", 64.0 * macs, "T ops/s", issue32)
+        return ("tree complex multiply-adds x 8 FP64 flops", 8.0 * macs, "TFLOP/s", peak64)
+    if fp32 and name.endswith("fp32r"):
+        return ("FP32-FMA-slot equivalents x 2 of the LU, exact residual and trace correction",
+                pipe_flops(n, has_gamma, 1) * d["n_evaluated"], "TFLOP/s", peak32)
+    return None
+
+
+def _traffic_note(kernel_name):
+    """Why `traffic` is null, said out loud: no capture of this kernel, or its sources
+    changed since the committed capture (the figure of that capture is quoted)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        entry = json.load(open(path)).get(kernel_name)
+    except (OSError, ValueError):
+        return "no profiles/traffic.json"
+    if not entry:
+        return f"no DRAM capture of {kernel_name} in profiles/traffic.json"
+    try:
+        if _sources_hash(entry["sources"]) != entry["sources_hash"]:
+            return (f"stale: sources changed since the capture (captured "
+                    f"{entry.get('dram_bytes_per_launch', entry.get('dram_bytes_per_table'))} B per launch)")
+    except (OSError, KeyError):
+        return "capture record unreadable"
+    return None
 
 
 def _timed(torch, stream, flush, steps, fn):
@@ -426,12 +516,12 @@ def _timed(torch, stream, flush, steps, fn):
     return total
 
 
-def extra_workloads(gb, torch, stream, flush, steps, world, which=("n192", "batch", "n200", "e3")):
+def extra_workloads(gb, torch, stream, flush, steps, world, which=("n32", "batch", "n200", "e3")):
     """The other workloads, a few steps each: per-table and per-point rates, FP32R next to
     FP64 where both apply."""
     out = {}
-    if "n192" in which:
-        out.update(_extra_n192(gb, torch, stream, flush, steps, world))
+    if "n32" in which:
+        out.update(_extra_n32(gb, torch, stream, flush, max(steps, 200), world))
     if "batch" in which:
         out.update(_extra_batch(gb, torch, stream, flush, steps, world))
     if "n200" in which:
@@ -545,21 +635,31 @@ def _extra_e3(gb, torch, stream, flush, steps, world):
     return {"E3_M256_n512_L1_N170": res}
 
 
-def _extra_n192(gb, torch, stream, flush, steps, world):
-    out = {}
-    # n = 192: 24 modes x 4 internal, displaced, 3 groups, 9261 points
-    prob = synth.config(2)
+def _extra_n32(gb, torch, stream, flush, steps, world):
+    """M = 16, K = 1, four groups of four detectors, N_l = 8: 6561 points of 32 x 32 matrices.
+    FP32 arithmetic (the tree of block eliminations in pairs of FP32), FP64 (the same tree in
+    FP64) and the per-point FP32 + refinement warp kernel, with the tree's own work rate."""
+    prob = synth.config(1)
+    npts = prob.n_points
     res = {}
-    for name, prec, tile in (("fp32_refine", 1, 0), ("fp32_refine_tensor_core_trace", 1, 7), ("fp64", 0, 0)):
+    for name, prec, tile in (("fp32", 1, 0), ("fp64", 0, 0), ("per_point_fp32_refine", 1, 5)):
         with gb.Plan(prob, precision=prec, want_timing=True, tile_override=tile) as p:
             t = torch.empty(p.shape, dtype=torch.float64, device="cuda")
-            gb.gbsbin_execute(p.handle, t, stream)
-            ms = _timed(torch, stream, flush, steps, lambda: gb.gbsbin_execute(p.handle, t, stream))
-            st, d = p.diagnostics(stream)
-            res[name] = {"ms_per_table": ms / steps, "points_per_s": world * prob.n_points * steps / (ms * 1e-3),
-                         "point_kernel_ms": d["point_kernel_ms"], "kernel": d["kernel_name"]}
-    out["M24_K4_L3_N20_n192_9261pts"] = res
-    return out
+            for _ in range(5):
+                gb.gbsbin_execute(p.handle, t, stream)
+            r = _time_plan(gb, torch, p, t, stream, flush, steps, world)
+            d = r["diag"]
+            ent = {"ms_per_table": r["ms_per_step"], "points_per_s": world * npts * steps / (r["gpu_ms"] * 1e-3),
+                   "tables_per_s": world * steps / (r["gpu_ms"] * 1e-3), "point_kernel_ms": r["kernel_ms"],
+                   "kernel": d["kernel_name"], "launches_per_table": d["launches"], "steps": steps}
+            issued = _issued_work(prob, d, prec == 1)
+            if issued:
+                ent.update({"issued": issued[0], "issued_rate": issued[1] / (r["kernel_ms"] * 1e-3) / 1e12,
+                            "issued_unit": issued[2], "issued_frac":
+                            issued[1] / (r["kernel_ms"] * 1e-3) / 1e12 / issued[3]})
+            ent["traffic"] = _profiled_traffic(d["kernel_name"])
+            res[name] = ent
+    return {"M16_K1_L4_N8_n32_6561pts": res}
 
 
 def _extra_batch(gb, torch, stream, flush, steps, world):
@@ -654,7 +754,7 @@ def cpu_baseline(prob, seconds, tables):
         if time.perf_counter() - t0 > seconds:
             break
     dt = time.perf_counter() - t0
-    names = {1: "fp32_refine", 0: "fp64", "warp": "per_point_fp32_refine"}
+    names = {1: "fp32_refine", 0: "fp64", "blk": "per_point_fp32_refine"}
     errs = {names.get(p, str(p)): float(np.abs(tables[p].cpu().numpy() - ref).max()) for p in tables}
     return ({"value": prob.n_points * count / dt, "unit": "points/s", "cores": os.cpu_count(), "kind": "oracle",
              "sample": f"{count} whole {prob.n_points}-point tables in {dt:.1f} s"}, errs)

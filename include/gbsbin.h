@@ -135,6 +135,10 @@ typedef struct {
   int kernel;                /* gbsbin_kernel id used by the last execute                      */
   double log_q1_re;          /* log q(A, gamma, 1) = -log Pr(0), from the w = 1 grid point    */
   double point_kernel_ms;    /* duration of the last point-kernel launch (want_timing), else 0 */
+  long long state_upload_bytes; /* bytes one state upload (plan creation, gbsbin_plan_set_state or
+                                   gbsbin_fock_plan_set_transfer) copies from host to device    */
+  int launches;              /* kernel launches of the last execute (point stage, inverse DFT
+                                with its diagnostics), 0 before the first                       */
 } gbsbin_diag;
 
 typedef enum {
@@ -167,8 +171,23 @@ typedef enum {
                                       the FMA pipe, FP64 results; chosen automatically for
                                       GBSBIN_FP32_REFINE plans with n <= 64, last group <= 16
                                       rows, no shard and no want_backward                */
-  GBSBIN_KERNEL_TREE_FP64 = 12     /* the same tree in FP64 (DFMA pipe); chosen automatically
+  GBSBIN_KERNEL_TREE_FP64 = 12,    /* the same tree in FP64 (DFMA pipe); chosen automatically
                                       for GBSBIN_FP64 plans under the same conditions      */
+  GBSBIN_KERNEL_BTREE_DF32 = 13,   /* L >= 2, large matrices: the same tree of block
+                                      eliminations with the reduced matrices in HBM/L2 - a
+                                      level's pivot rows factored by one CTA per child in
+                                      shared memory, the other rows streamed through
+                                      registers by many CTAs per child - and the last
+                                      group's block I - w A_L of every leaf parent reduced
+                                      once to Hessenberg form (A_L = Q H Q^H), so each grid
+                                      point is an O(m^2) elimination of H - conj(w) I;
+                                      pairs of FP32; chosen automatically for standalone
+                                      GBSBIN_FP32_REFINE plans where kernel 11 does not
+                                      apply and it needs under half the per-point LUs'
+                                      work (last group <= 112 rows, no shard, no
+                                      want_backward)                                       */
+  GBSBIN_KERNEL_BTREE_FP64 = 14    /* the same in FP64; chosen for GBSBIN_FP64 plans under
+                                      the same conditions                                   */
 } gbsbin_kernel;
 
 /* Fill *o with defaults: FP64, oversample 1, diagnostics on, automatic kernel. */

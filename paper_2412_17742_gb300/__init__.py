@@ -25,7 +25,7 @@ GBSBIN_FP64 = 0
 GBSBIN_FP32_REFINE = 1
 KERNELS = {1: "smem_fp64", 2: "smem_fp32r", 3: "gmem_fp64", 4: "gmem_fp32r", 5: "warp_fp32r", 6: "blk_fp32r",
            7: "blk_tc_fp32r", 8: "hess_fp64", 9: "fock_fp64", 10: "fock_df32",
-           11: "tree_df32", 12: "tree_fp64"}
+           11: "tree_df32", 12: "tree_fp64", 13: "btree_df32", 14: "btree_fp64"}
 EXPORTED = ["gbsbin_default_options", "gbsbin_plan_create", "gbsbin_plan_set_state", "gbsbin_plan_destroy",
             "gbsbin_plan_table_size", "gbsbin_execute", "gbsbin_execute_host", "gbsbin_execute_host_async",
             "gbsbin_diagnostics",
@@ -75,7 +75,8 @@ class gbsbin_diag(ctypes.Structure):
     _fields_ = [("sum_P", ctypes.c_double), ("max_imag", ctypes.c_double), ("min_pivot_re", ctypes.c_double),
                 ("n_bad_points", ctypes.c_longlong), ("n_points", ctypes.c_longlong),
                 ("n_evaluated", ctypes.c_longlong), ("table_size", ctypes.c_longlong), ("n", ctypes.c_int),
-                ("kernel", ctypes.c_int), ("log_q1_re", ctypes.c_double), ("point_kernel_ms", ctypes.c_double)]
+                ("kernel", ctypes.c_int), ("log_q1_re", ctypes.c_double), ("point_kernel_ms", ctypes.c_double),
+                ("state_upload_bytes", ctypes.c_longlong), ("launches", ctypes.c_int)]
 
 
 class gbsbin_fock_problem(ctypes.Structure):

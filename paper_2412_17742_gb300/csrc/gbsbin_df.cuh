@@ -128,6 +128,22 @@ __device__ __forceinline__ float4 df_csqrt(float4 z) {
   return make_float4(fabsf(q.x), sg * s.x, q.x < 0.f ? -q.z : q.z, sg * s.z);
 }
 
+// Full-warp shuffles of 16-byte elements (pairs of FP32 or FP64 complex values).
+__device__ __forceinline__ float4 shfl(float4 v, int src) {
+  return make_float4(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src),
+                     __shfl_sync(0xffffffffu, v.z, src), __shfl_sync(0xffffffffu, v.w, src));
+}
+__device__ __forceinline__ double2 shfl(double2 v, int src) {
+  return make_double2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
+}
+__device__ __forceinline__ float4 shfl_xor(float4 v, int mask) {
+  return make_float4(__shfl_xor_sync(0xffffffffu, v.x, mask), __shfl_xor_sync(0xffffffffu, v.y, mask),
+                     __shfl_xor_sync(0xffffffffu, v.z, mask), __shfl_xor_sync(0xffffffffu, v.w, mask));
+}
+__device__ __forceinline__ double2 shfl_xor(double2 v, int mask) {
+  return make_double2(__shfl_xor_sync(0xffffffffu, v.x, mask), __shfl_xor_sync(0xffffffffu, v.y, mask));
+}
+
 // ----------------------------------------------------- the tree's two arithmetics
 // Element type E (16 bytes either way), the operations the tree kernels use, and a complex
 // scaling by a power of two that returns the exponent taken out.
@@ -144,6 +160,14 @@ struct ArDF {                                        // pairs of FP32 on the FMA
   static __device__ __forceinline__ E fms(E c, E a, E b) { return df_fms(c, a, b); }
   static __device__ __forceinline__ E recip(E a) { return df_recip(a); }
   static __device__ __forceinline__ E csqrt(E a) { return df_csqrt(a); }
+  static __device__ __forceinline__ E conj(E a) { return df_conj(a); }
+  // |a|^2 as a real pair; sqrt and reciprocal of a real pair (imaginary parts zero)
+  static __device__ __forceinline__ E norm2(E a) {
+    const float4 x = make_float4(a.x, 0.f, a.z, 0.f), y = make_float4(a.y, 0.f, a.w, 0.f);
+    return df_add(df_mul(x, x), df_mul(y, y));
+  }
+  static __device__ __forceinline__ E rsqrt_real(E a) { return df_rsqrt_root(a); }
+  static __device__ __forceinline__ E rrecip(E a) { return df_rrecip(a); }
   static __device__ __forceinline__ float re(E a) { return a.x; }
   static __device__ __forceinline__ float im(E a) { return a.y; }
   // mx = 2^(ex - 1) f, f in [1, 2): ex from the exponent bits, the scaling by 2^-ex an exact
@@ -201,6 +225,10 @@ struct ArF64 {                                       // FP64 throughout
     if (a.x >= 0.0) return make_double2(t, q);
     return make_double2(::fabs(q), a.y < 0.0 ? -t : t);
   }
+  static __device__ __forceinline__ E conj(E a) { return make_double2(a.x, -a.y); }
+  static __device__ __forceinline__ E norm2(E a) { return make_double2(::fma(a.x, a.x, a.y * a.y), 0.0); }
+  static __device__ __forceinline__ E rsqrt_real(E a) { return make_double2(a.x > 0.0 ? ::sqrt(a.x) : 0.0, 0.0); }
+  static __device__ __forceinline__ E rrecip(E a) { return make_double2(1.0 / a.x, 0.0); }
   static __device__ __forceinline__ float re(E a) { return (float)a.x; }
   static __device__ __forceinline__ float im(E a) { return (float)a.y; }
   // as ArDF::normalise, from the FP64 exponent bits (ex in [-996, 997] here)

@@ -25,6 +25,7 @@ struct gbsbin_fock_plan {
   long long table_size = 0;
   FockArgs args{};
   size_t coef_count = 0;                 // (L + 1) nin^2
+  bool executed = false;                 // an execute has been enqueued
   // device
   unsigned char* d_state = nullptr;      // coef (double2) then coef_df (float4)
   double2* d_xtw = nullptr;
@@ -371,6 +372,7 @@ int gbsbin_fock_execute(gbsbin_fock_plan* P, double* P_out, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
   if (P->ev0 && cudaEventRecord(P->ev0, s) != cudaSuccess) return GBSBIN_ERR_CUDA;
   if (launch_fock(P->args, P->df, P->zt, s) != cudaSuccess) return GBSBIN_ERR_CUDA;
+  P->executed = true;
   if (P->ev1 && cudaEventRecord(P->ev1, s) != cudaSuccess) return GBSBIN_ERR_CUDA;
   DftArgs d{};
   d.grid = P->args.grid;
@@ -423,7 +425,9 @@ int gbsbin_fock_diagnostics(gbsbin_fock_plan* P, gbsbin_diag* out, void* stream)
   out->n = P->args.nin;
   out->kernel = P->kernel;
   out->point_kernel_ms = 0.0;
-  if (P->ev1) {
+  out->state_upload_bytes = (long long)P->state_bytes;
+  out->launches = P->executed ? 2 : 0;            // the Fock kernel and the fused DFT
+  if (P->ev1 && P->executed) {
     float ms = 0.f;
     if (cudaEventSynchronize(P->ev1) != cudaSuccess || cudaEventElapsedTime(&ms, P->ev0, P->ev1) != cudaSuccess) {
       cudaGetLastError();

@@ -46,6 +46,13 @@ struct gbsbin_plan {
   bool tree_g = false;                // undisplaced tree plan: leaves write G, the DFT skips a stage
   double tree_logq0 = 0.0;            // Re log q(1) from the host LU (diagnostics)
   unsigned char* d_tree = nullptr;
+  // large-matrix tree plans (kernels 13, 14): the same row order, depth-0 augmented matrix in
+  // d_state, the other depths, sub-step scratch and Hessenberg leaves in d_tree
+  BTreeArgs btree{};
+  std::vector<BTreeStep> btree_steps;
+  size_t bt_scratch[3] = {0, 0, 0};   // 16-byte slots: each trailing-block buffer, pivot rows, reciprocals
+  int last_launches = 0;              // kernel launches of the last execute
+  long long upload_bytes = 0;         // host-to-device bytes of one state upload
   int* d_label = nullptr;
   double2* d_logq = nullptr;
   double* d_minpiv = nullptr;
@@ -90,8 +97,10 @@ int validate_shape(const gbsbin_problem* p, const gbsbin_options* o) {
   if (!p->sigma1 && (!p->r || !p->T)) return GBSBIN_ERR_ARG;
   if (o->precision != GBSBIN_FP64 && o->precision != GBSBIN_FP32_REFINE) return GBSBIN_ERR_ARG;
   if (o->oversample < 1) return GBSBIN_ERR_ARG;
-  if (o->tile_override < 0 || (o->tile_override > GBSBIN_KERNEL_HESS_FP64 && o->tile_override != GBSBIN_KERNEL_TREE_DF32 &&
-                                o->tile_override != GBSBIN_KERNEL_TREE_FP64))
+  if (o->tile_override < 0 ||
+      (o->tile_override > GBSBIN_KERNEL_HESS_FP64 && o->tile_override != GBSBIN_KERNEL_TREE_DF32 &&
+       o->tile_override != GBSBIN_KERNEL_TREE_FP64 && o->tile_override != GBSBIN_KERNEL_BTREE_DF32 &&
+       o->tile_override != GBSBIN_KERNEL_BTREE_FP64))
     return GBSBIN_ERR_ARG;
   long long n = 2LL * p->M * p->K;
   if (n > GBSBIN_MAX_N) return GBSBIN_ERR_UNSUPPORTED;
@@ -352,8 +361,15 @@ int dalloc(T** p, size_t count) {
   return check_cuda(e);
 }
 
-// The tree of block eliminations, in pairs of FP32 or in FP64.
+// The tree of block eliminations, in pairs of FP32 or in FP64; and its large-matrix form.
 inline bool is_tree(int kernel) { return kernel == GBSBIN_KERNEL_TREE_DF32 || kernel == GBSBIN_KERNEL_TREE_FP64; }
+inline bool is_btree(int kernel) { return kernel == GBSBIN_KERNEL_BTREE_DF32 || kernel == GBSBIN_KERNEL_BTREE_FP64; }
+// 16-byte slots of a tree plan's depth-0 region in the state block
+size_t tree_region_slots(int n, int kernel) {
+  if (is_tree(kernel)) return (size_t)n * n + 2 * (size_t)n + 3;   // permuted XA, X gamma, gamma, path record
+  if (is_btree(kernel)) return (size_t)(n + 1) * (n + 1) + 2;    // augmented matrix, path record
+  return 0;
+}
 
 // Layout of the pinned staging buffer for one state upload.
 struct Stage {
@@ -361,7 +377,7 @@ struct Stage {
   size_t off_tree;   // tree plans: permuted XA (n x n), X gamma, gamma (FP32 pairs or FP64), root path record
   size_t total;
 };
-Stage stage_layout(int n, bool tree) {
+Stage stage_layout(int n, size_t tree_slots) {
   Stage s{};
   size_t nn = (size_t)n * n, o = 0;
   s.off_XA = o;   o += nn * sizeof(double2);
@@ -375,7 +391,7 @@ Stage stage_layout(int n, bool tree) {
   s.off_glo = o;  o += n * sizeof(float2);
   s.off_XAfix = o; o += nn * sizeof(longlong2);
   s.off_tree = o;
-  if (tree) o += (nn + 2 * (size_t)n + 3) * sizeof(float4);
+  o += tree_slots * sizeof(float4);
   s.total = o;
   return s;
 }
@@ -397,8 +413,8 @@ int upload_hessenberg(gbsbin_plan* P, cudaStream_t stream);
 // Stage the state and enqueue its upload on `stream`.
 int upload_state(gbsbin_plan* P, cudaStream_t stream) {
   const int n = P->n;
-  const bool tree = is_tree(P->kernel);
-  Stage s = stage_layout(n, tree);
+  const bool tree = is_tree(P->kernel) || is_btree(P->kernel);
+  Stage s = stage_layout(n, tree_region_slots(n, P->kernel));
   // the copy that last read this staging buffer (two uploads back) must have finished
   const int sb = P->stage_next;
   P->stage_next ^= 1;
@@ -429,7 +445,27 @@ int upload_state(gbsbin_plan* P, cudaStream_t stream) {
     split(P->Xgamma[i], &Xghi[i], &Xglo[i]);
     split(P->gamma[i], &ghi[i], &glo[i]);
   }
-  if (tree) {                                     // depth 0 of the tree: the permuted state
+  if (is_btree(P->kernel)) {                       // depth 0: the permuted augmented matrix
+    float4* A0 = (float4*)(h + s.off_tree);
+    const std::vector<int>& pm = P->tree_perm;
+    const bool f64 = P->kernel == GBSBIN_KERNEL_BTREE_FP64;
+    auto slot = [f64](cd v) {
+      if (!f64) return split4(v);
+      float4 o;
+      const double2 d = make_double2(v.real(), v.imag());
+      std::memcpy(&o, &d, sizeof(o));
+      return o;
+    };
+    const size_t D = (size_t)n + 1;
+    for (int i = 0; i < n; ++i) {
+      for (int j = 0; j < n; ++j) A0[i * D + j] = slot(P->XA[(size_t)pm[i] * n + pm[j]]);
+      A0[i * D + n] = slot(P->Xgamma[pm[i]]);             // c: v = D(w) c
+      A0[n * D + i] = slot(P->gamma[pm[i]]);              // u
+    }
+    A0[n * D + n] = slot(cd(0.0, 0.0));                   // the exponent collected so far
+    A0[D * D] = slot(cd(1.0, 0.0));                       // path record: pivot product
+    A0[D * D + 1] = make_float4(0.f, 0.f, 3.0e38f, 0.f);  // argument sum, power of two, min Re pivot
+  } else if (tree) {                               // depth 0 of the tree: the permuted state
     float4* A0 = (float4*)(h + s.off_tree);
     float4* c0 = A0 + (size_t)n * n;
     float4* u0 = c0 + n;
@@ -501,6 +537,7 @@ int upload_state(gbsbin_plan* P, cudaStream_t stream) {
   }
   // the device block has the staging layout: one copy (of the tree region alone for trees)
   const size_t off = tree ? s.off_tree : 0;
+  P->upload_bytes = (long long)(s.total - off);
   e = cudaMemcpyAsync(P->d_state + off, h + off, s.total - off, cudaMemcpyHostToDevice, stream);
   if (e != cudaSuccess || cudaEventRecord(P->ev_stage[sb], stream) != cudaSuccess) return GBSBIN_ERR_CUDA;
   if (P->kernel == GBSBIN_KERNEL_HESS_FP64) return upload_hessenberg(P, stream);
@@ -574,6 +611,7 @@ int upload_hessenberg(gbsbin_plan* P, cudaStream_t stream) {
   // a pageable source: the call returns once the data are staged, so h may go out of scope
   if (cudaMemcpyAsync(P->d_H, h.data(), h.size() * sizeof(double2), cudaMemcpyHostToDevice, stream) != cudaSuccess)
     return GBSBIN_ERR_CUDA;
+  P->upload_bytes += (long long)(h.size() * sizeof(double2));
   return GBSBIN_OK;
 }
 
@@ -693,6 +731,137 @@ size_t tree_layout(gbsbin_plan* P) {
     bytes += (size_t)nodes * (mc * mc + 2 * mc + 3) * sizeof(float4);
   }
   return bytes <= (2ull << 30) ? bytes : 0;
+}
+
+// Complex multiply-adds of the large-matrix tree for the plan's sub-step list, and of one
+// LU per evaluated point, for choosing between them.
+double btree_macs(const gbsbin_plan* P) {
+  const BTreeArgs& t = P->btree;
+  double macs = 0.0;
+  for (const BTreeStep& st : P->btree_steps) {
+    double children = 1.0;
+    for (int l = 0; l <= st.l; ++l) children *= P->grid.radix[l];
+    double top = 0.0, row = 0.0;
+    for (int kk = 0; kk < st.nbs; ++kk) {
+      top += (double)(st.nbs - kk - 1) * (st.D - kk - 1);
+      row += (double)(st.D - kk - 1);
+    }
+    macs += children * (top + (double)(st.D - st.nbs) * row);
+  }
+  double parents = 1.0;
+  for (int l = 0; l + 1 < P->L; ++l) parents *= P->grid.radix[l];
+  const double m = t.mL;
+  double hess = 0.0;
+  for (int k = 0; k + 2 < t.mL; ++k) hess += 2.0 * (m - k - 1) * (m - k + 1) + 2.0 * m * (m - k - 1);
+  macs += parents * hess;
+  macs += (double)P->grid.n_eval * (P->has_gamma ? 2.0 : 1.0) * m * m / 2.0;
+  return macs;
+}
+
+// Large-matrix tree plans: rows ordered by group (as for kernels 11 and 12), the sub-step
+// list (each level's pivots in as few equal sub-steps as the shared-memory budget allows)
+// and the scratch layout.  Returns the device bytes of depths 1 .. L-1, the sub-step
+// scratch and the Hessenberg leaves, or 0 when the problem does not suit it (one group, a
+// last group above GBSBIN_BT_MAX_HESS rows, scratch above 8 GB).
+size_t btree_layout(gbsbin_plan* P) {
+  const int L = P->L, n = P->n;
+  if (L < 2) return 0;
+  BTreeArgs& t = P->btree;
+  t = BTreeArgs{};
+  P->tree_perm.clear();
+  int nb[GBSBIN_MAX_L], m[GBSBIN_MAX_L];
+  for (int l = 0; l < L; ++l) {
+    nb[l] = 0;
+    for (int q = 0; q < n; ++q)
+      if (P->label[q] == l) {
+        P->tree_perm.push_back(q);
+        ++nb[l];
+      }
+  }
+  int rem = n;
+  for (int l = 0; l < L; ++l) {
+    m[l] = rem;
+    rem -= nb[l];
+  }
+  t.L = L;
+  t.mL = m[L - 1];
+  if (t.mL > GBSBIN_BT_MAX_HESS || t.mL < 1) return 0;
+  P->btree_steps.clear();
+  size_t bytes = 0, tmp_max = 0, u_max = 0, inv_max = 0;
+  long long nodes = 1;
+  for (int l = 0; l + 1 < L; ++l) {
+    const long long children = nodes * P->grid.radix[l];
+    int D = m[l] + 1;
+    const int cap = (int)(GBSBIN_BT_SMEM / sizeof(float4)) / (D + 1);   // pivots per sub-step
+    if (cap < 1) return 0;
+    const int nsub = (nb[l] + cap - 1) / cap;
+    const int per = (nb[l] + nsub - 1) / nsub;
+    for (int p0 = 0; p0 < nb[l]; p0 += per) {
+      BTreeStep st{};
+      st.l = l;
+      st.first = p0 == 0;
+      st.nbg = nb[l];
+      st.nbs = std::min(per, nb[l] - p0);
+      st.D = D;
+      P->btree_steps.push_back(st);
+      u_max = std::max(u_max, (size_t)children * st.nbs * D);
+      inv_max = std::max(inv_max, (size_t)children * st.nbs);
+      D -= st.nbs;
+      if (p0 + st.nbs < nb[l]) tmp_max = std::max(tmp_max, (size_t)children * D * D);
+    }
+    bytes += (size_t)children * (m[l + 1] + 1) * (m[l + 1] + 1) + 2 * (size_t)children;
+    nodes = children;
+  }
+  const size_t hslots = (size_t)nodes * ((size_t)t.mL * t.mL + 2 * (size_t)t.mL + 1);
+  const size_t total = bytes + 2 * tmp_max + u_max + inv_max + hslots;
+  if (total * sizeof(float4) > (8ull << 30)) return 0;
+  P->bt_scratch[0] = tmp_max;
+  P->bt_scratch[1] = u_max;
+  P->bt_scratch[2] = inv_max;
+  return total * sizeof(float4);
+}
+
+// Device pointers of a large-matrix tree plan (the layout of btree_layout) and the sub-step
+// list's inputs and outputs.
+void btree_pointers(gbsbin_plan* P, const Stage& sl) {
+  BTreeArgs& t = P->btree;
+  const int L = P->L, n = P->n;
+  float4* A0 = (float4*)(P->d_state + sl.off_tree);
+  t.mat[0] = A0;
+  t.path[0] = A0 + (size_t)(n + 1) * (n + 1);
+  float4* q = (float4*)P->d_tree;
+  long long nodes = 1;
+  int m = n;
+  for (int l = 0; l + 1 < L; ++l) {
+    nodes *= P->grid.radix[l];
+    int nbl = 0;
+    for (int x : P->label) nbl += x == l;
+    m -= nbl;
+    t.mat[l + 1] = q;
+    q += (size_t)nodes * (m + 1) * (m + 1);
+    t.path[l + 1] = q;
+    q += 2 * (size_t)nodes;
+  }
+  const size_t tmp_max = P->bt_scratch[0], u_max = P->bt_scratch[1], inv_max = P->bt_scratch[2];
+  float4* tmp[2] = {q, q + tmp_max};
+  q += 2 * tmp_max;
+  t.U = q;
+  q += u_max;
+  t.inv = q;
+  q += inv_max;
+  t.H = q;
+  q += (size_t)nodes * t.mL * t.mL;
+  t.hv = q;
+  // sub-step inputs and outputs: a level's later sub-steps read the previous trailing blocks;
+  // the last one writes depth l + 1
+  int cur = 0;
+  for (size_t k = 0; k < P->btree_steps.size(); ++k) {
+    BTreeStep& st = P->btree_steps[k];
+    const bool last = k + 1 == P->btree_steps.size() || P->btree_steps[k + 1].first;
+    st.in = st.first ? nullptr : tmp[cur];
+    if (!st.first) cur ^= 1;
+    st.out = last ? t.mat[st.l + 1] : tmp[cur];
+  }
 }
 
 void tree_pointers(gbsbin_plan* P, const Stage& sl) {
@@ -844,7 +1013,24 @@ static int plan_create_impl(const gbsbin_problem* p, const gbsbin_options* o, gb
       return GBSBIN_ERR_UNSUPPORTED;
     }
   }
-  P->P = P->kernel == GBSBIN_KERNEL_HESS_FP64 || is_tree(P->kernel) ? 1
+  // the large-matrix tree: asked for, or by default for standalone plans of n > 64 where it
+  // needs under half the work of one LU per evaluated point
+  if (is_btree(P->kernel) || (!is_tree(P->kernel) && alloc_gws && !opt.tile_override && p->L >= 2 && n > 64)) {
+    tree_bytes = (!sharded && !opt.want_backward) ? btree_layout(P) : 0;
+    bool take = tree_bytes > 0;
+    if (take && !is_btree(P->kernel))
+      take = btree_macs(P) < 0.5 * (double)g.n_eval * (double)n * (double)n * (double)n / 3.0;
+    if (!take) {
+      tree_bytes = 0;
+      if (is_btree(P->kernel)) {
+        delete P;
+        return GBSBIN_ERR_UNSUPPORTED;
+      }
+    } else if (!is_btree(P->kernel)) {
+      P->kernel = opt.precision == GBSBIN_FP64 ? GBSBIN_KERNEL_BTREE_FP64 : GBSBIN_KERNEL_BTREE_DF32;
+    }
+  }
+  P->P = P->kernel == GBSBIN_KERNEL_HESS_FP64 || is_tree(P->kernel) || is_btree(P->kernel) ? 1
          : P->kernel == GBSBIN_KERNEL_WARP_FP32R ? (n <= 32 ? 1 : 0)
          : is_blk(P->kernel) ? (n <= GBSBIN_BLK_MAX_N ? 1 : 0)
                                                  : points_per_cta(P->kernel, n, p->L);
@@ -866,7 +1052,7 @@ static int plan_create_impl(const gbsbin_problem* p, const gbsbin_options* o, gb
     return GBSBIN_ERR_CUDA;
   }
   const size_t nn = (size_t)n * n;
-  Stage sl = stage_layout(n, is_tree(P->kernel));
+  Stage sl = stage_layout(n, tree_region_slots(n, P->kernel));
   (void)nn;
   if ((st = dalloc(&P->d_state, sl.total)) || (st = dalloc(&P->d_label, n)) || (st = dalloc(&P->d_logq, g.n_eval)) ||
       (st = dalloc(&P->d_minpiv, g.n_eval)) || (st = dalloc(&P->d_bufA, g.n_full)) ||
@@ -901,7 +1087,7 @@ static int plan_create_impl(const gbsbin_problem* p, const gbsbin_options* o, gb
     return st;
   }
   if ((P->kernel == GBSBIN_KERNEL_WARP_FP32R || P->kernel == GBSBIN_KERNEL_HESS_FP64 ||
-       is_tree(P->kernel)) &&
+       is_tree(P->kernel) || is_btree(P->kernel)) &&
       (st = dalloc(&P->d_ldfin, (size_t)6 * g.n_eval))) {
     free_device(P);
     delete P;
@@ -914,6 +1100,14 @@ static int plan_create_impl(const gbsbin_problem* p, const gbsbin_options* o, gb
       return st;
     }
     tree_pointers(P, sl);
+  }
+  if (is_btree(P->kernel)) {
+    if ((st = dalloc(&P->d_tree, tree_bytes))) {
+      free_device(P);
+      delete P;
+      return st;
+    }
+    btree_pointers(P, sl);
   }
   if (P->kernel == GBSBIN_KERNEL_HESS_FP64 && (st = dalloc(&P->d_H, nn + 2 * (size_t)n))) {
     free_device(P);
@@ -990,7 +1184,7 @@ static int plan_create_impl(const gbsbin_problem* p, const gbsbin_options* o, gb
     delete P;
     return GBSBIN_ERR_CUDA;
   }
-  if (is_tree(P->kernel)) {                       // the roots w = conj(twiddle) as FP32 pairs
+  if (is_tree(P->kernel) || is_btree(P->kernel)) {   // the roots w = conj(twiddle) as FP32 pairs
     std::vector<float4> twdf((size_t)twn);
     for (size_t j = 0; j < twdf.size(); ++j) twdf[j] = split4(cd(tw[j].x, -tw[j].y));
     if (cudaMalloc(&P->d_twdf, twdf.size() * sizeof(float4)) != cudaSuccess ||
@@ -1112,19 +1306,39 @@ int gbsbin_execute(gbsbin_plan* P, double* P_out, void* stream) {
     t.gout = P->tree_g ? P->d_bufA : nullptr;
     // pairs plans whose transform runs in pairs take G as pairs (no FP64 round trip)
     t.gout_df = (P->tree_g && P->kernel == GBSBIN_KERNEL_TREE_DF32 && dft_two_phase(P->grid)) ? 1 : 0;
-    if (launch_points_tree(t, P->kernel == GBSBIN_KERNEL_TREE_FP64, P->num_sms, s) != cudaSuccess)
+    int nl = 0;
+    if (launch_points_tree(t, P->kernel == GBSBIN_KERNEL_TREE_FP64, P->num_sms, s, &nl) != cudaSuccess)
       return GBSBIN_ERR_CUDA;
+    P->last_launches = nl + 1;                    // the tree's launches and the fused DFT
     if (P->ev1 && cudaEventRecord(P->ev1, s) != cudaSuccess) return GBSBIN_ERR_CUDA;
     DftArgs d = make_dft_args(P, P_out);
     d.g_ready = P->tree_g ? 1 : 0;
     d.g_df = t.gout_df;
     return launch_dft_fused(d, P->d_bar, P->num_sms, s) == cudaSuccess ? GBSBIN_OK : GBSBIN_ERR_CUDA;
   }
+  if (is_btree(P->kernel)) {
+    BTreeArgs t = P->btree;
+    t.has_gamma = P->has_gamma;
+    t.tw = P->d_tw;
+    t.twdf = P->d_twdf;
+    t.grid = P->grid;
+    t.ldfin = P->d_ldfin;
+    t.minpiv = P->d_minpiv;
+    int nl = 0;
+    if (launch_points_btree(t, P->btree_steps.data(), (int)P->btree_steps.size(),
+                            P->kernel == GBSBIN_KERNEL_BTREE_FP64, P->num_sms, s, &nl) != cudaSuccess)
+      return GBSBIN_ERR_CUDA;
+    P->last_launches = nl + 1;                    // the tree's launches and the fused DFT
+    if (P->ev1 && cudaEventRecord(P->ev1, s) != cudaSuccess) return GBSBIN_ERR_CUDA;
+    return launch_dft_fused(make_dft_args(P, P_out), P->d_bar, P->num_sms, s) == cudaSuccess ? GBSBIN_OK
+                                                                                             : GBSBIN_ERR_CUDA;
+  }
   cudaError_t e = P->kernel == GBSBIN_KERNEL_WARP_FP32R  ? launch_points_warp(a, P->num_sms, s)
                   : P->kernel == GBSBIN_KERNEL_HESS_FP64 ? launch_points_hess(a, PointBatch{}, P->num_sms, s)
                   : is_blk(P->kernel) ? launch_points_blk(a, PointBatch{}, 0, P->num_sms, s, P->kernel == GBSBIN_KERNEL_BLK_TC_FP32R)
                                                          : launch_points(a, P->kernel, P->num_sms, s);
   if (e != cudaSuccess) return GBSBIN_ERR_CUDA;
+  P->last_launches = 2;                           // the point kernel and the fused DFT
   if (P->ev1 && cudaEventRecord(P->ev1, s) != cudaSuccess) return GBSBIN_ERR_CUDA;
   e = launch_dft_fused(make_dft_args(P, P_out), P->d_bar, P->num_sms, s);
   return e == cudaSuccess ? GBSBIN_OK : GBSBIN_ERR_CUDA;
@@ -1175,7 +1389,9 @@ int gbsbin_diagnostics(gbsbin_plan* P, gbsbin_diag* out, void* stream) {
   out->n = P->n;
   out->kernel = P->kernel;
   out->point_kernel_ms = 0.0;
-  if (P->ev1) {
+  out->state_upload_bytes = P->upload_bytes;
+  out->launches = P->last_launches;
+  if (P->ev1 && P->last_launches > 0) {          // the timing events exist once an execute has run
     float ms = 0.f;
     if (cudaEventSynchronize(P->ev1) != cudaSuccess || cudaEventElapsedTime(&ms, P->ev0, P->ev1) != cudaSuccess) {
       cudaGetLastError();

@@ -156,9 +156,48 @@ struct TreeArgs {
   float4 p0df;              // p0 as a pair of FP32
   float p0arg, e0, m0;
 };
+// Tree of block eliminations for large matrices with Hessenberg leaves
+// (gbsbin_points_btree.cu), in pairs of FP32 or FP64 (16-byte elements either way).  Depth d
+// holds one augmented matrix [[A, c], [u^T, ex]] ((m_d + 1)^2 elements) per combination of
+// the first d axes' roots, and a path record (pivot product; FP32 argument sum, power of
+// two, smallest pivot real part).  Level l runs as sub-steps of nbs pivots of its group,
+// each a top launch (CTA per child) and a bottom launch (CTAs per row chunk); the last
+// group's blocks are reduced to Hessenberg form (a CTA per leaf parent) and every evaluated
+// point is an O(m^2) Hessenberg elimination (a warp per point) writing the unfinished log q.
+#define GBSBIN_BT_MAX_HESS 112          // largest last group (shared-memory Householder)
+#define GBSBIN_BT_SMEM (200 * 1024)     // shared-memory budget of one sub-step's pivot rows
+struct BTreeStep {
+  int l;                    // level: the grid axis whose roots this sub-step applies
+  int first;                // first sub-step of the level: input is the parent's matrix at depth l
+  int nbg;                  // rows of the level's group (the G form of the first sub-step)
+  int nbs;                  // pivots eliminated by this sub-step
+  int D;                    // dimension of the input matrix (augmented)
+  const float4* in;         // later sub-steps: the previous trailing blocks, one per child
+  float4* out;              // trailing blocks (D - nbs)^2 per child: depth l + 1 after the last sub-step
+};
+struct BTreeArgs {
+  int L;
+  int has_gamma;
+  int mL;                   // rows of the last group
+  GridDesc grid;
+  const double2* tw;
+  const float4* twdf;
+  float4* mat[GBSBIN_MAX_L];
+  float4* path[GBSBIN_MAX_L];
+  float4* U;                // per child of the current sub-step: nbs x D pivot rows
+  float4* inv;              // per child: nbs reciprocal pivots
+  float4* H;                // per leaf parent: mL x mL Hessenberg form
+  float4* hv;               // per leaf parent: a = Q^T u (mL), b = Q^H c (mL), the exponent so far
+  double* ldfin;
+  double* minpiv;
+};
+size_t btree_step_smem_bytes(int nbs, int D);
+size_t btree_hess_smem_bytes(int m);
+cudaError_t launch_points_btree(const BTreeArgs& a, const BTreeStep* steps, int nsteps, bool fp64, int num_sms,
+                                cudaStream_t s, int* launches);
 size_t tree_level_smem_bytes(int nb, int m);
 int tree_leaf_threads(int n);   // lanes per leaf (0: no kernel for a last group of n rows)
-cudaError_t launch_points_tree(const TreeArgs& a, bool fp64, int num_sms, cudaStream_t s);
+cudaError_t launch_points_tree(const TreeArgs& a, bool fp64, int num_sms, cudaStream_t s, int* launches);
 
 // Fock inputs through a lossy circuit (gbsbin_fock.cu).  nin occupied inputs in position
 // order (position 0 is the held input, x = 1; positions 1..nd are the Gray digits); per

@@ -1,0 +1,545 @@
+// Grid points of large matrices by a tree of block eliminations with Hessenberg leaves
+// (arXiv:2412.17742, Sec. III Eq. q_d on the roots-of-unity grid of Sec. VI), in pairs of
+// FP32 or in FP64.
+//
+// Rows and columns of K(w) = I - D(w) A are ordered by detector group (a symmetric
+// permutation: det, the exponent's bilinear form and the pivots' Re > 0 are unchanged).
+// Eliminating group 0's block leaves a matrix of the same form whose A' depends on w_0 only,
+// so depth l of the tree holds one reduced matrix per combination of the first l axes'
+// roots.  Each node stores the augmented matrix
+//
+//   [ A    c  ]      A: m x m,  c: the right-hand side's coefficients (v = D c),
+//   [ u^T  ex ]      u: the exponent's left vector, ex: the exponent collected so far,
+//
+// and a level turns it, for the child's root w of the group's axis, into
+//
+//   [ I - w A_00   w A_0r   w c_0 ]
+//   [   -A_r0       A_rr     c_r  ]        (the "G form")
+//   [   -u_0^T      u_r^T    ex   ]
+//
+// whose forward elimination over the group's nb pivot columns leaves exactly the child's
+// augmented matrix [[A', c'], [u'^T, ex + u_0^T y]] (A' = A_rr + A_r0 W, W = w B^-1 A_0r,
+// y = w B^-1 c_0): the exponent rides along in the corner.  The pivots are those of the
+// per-point unpivoted LU of the permuted K(w), each with Re > 0.
+//
+// A level runs in sub-steps of nbs pivots (as many as fit in shared memory), each in two
+// launches:
+//   top:    one CTA per child eliminates the nbs pivot rows among themselves in shared
+//           memory (one barrier per step) and writes them with their reciprocal pivots; one
+//           warp folds the pivots into the child's path record;
+//   bottom: several CTAs per child stage those pivot rows in shared memory and stream the
+//           other rows through registers (a warp per row: lane t holds columns t + 32 s),
+//           each eliminated against the pivot rows, and write the trailing block - the next
+//           sub-step's input, or the child's augmented matrix after the level's last one.
+//
+// Leaves.  The last group's block is I - w A_L for every root w of the last axis, so one
+// Householder reduction A_L = Q H Q^H per leaf parent (a CTA per node, the matrix in shared
+// memory) serves all of them: det(I - w A_L) = det(I - w H), and with N = H - conj(w) I =
+// -conj(w) (I - w H) the pivots of I - w H are -w times those of N.  The exponent's leaf term
+// u^T (I - w A_L)^-1 w c = -a^T N^-1 b with a = Q^T u, b = Q^H c (reflectors applied to c and
+// to conj(u) as extra columns).  A warp per evaluated point runs the O(m^2) unpivoted
+// elimination of the Hessenberg matrix N (each step updates the next row only), with the
+// exponent by the recurrences y_{i+1} = b_{i+1} - l_i y_i and z_i = (a_i - s_i) / n_ii,
+// s_j += z_i n_ij, a^T N^-1 b = sum z_i y_i, and writes the point's unfinished log q.  Every
+// pivot of I - w H has Re > 0 (a unitary similarity of the Schur complement I - w A_L, which
+// has a positive-definite Hermitian part), and Sum Log over any unpivoted elimination of a
+// matrix of that class is the branch of log det continuous along (1 - t) I + t K, so the
+// branch is the per-point LU's.
+#include <cuda_runtime.h>
+
+#include <type_traits>
+
+#include "gbsbin_device.cuh"
+#include "gbsbin_df.cuh"
+#include "gbsbin_internal.h"
+
+namespace gbsbin {
+namespace {
+
+constexpr int TOP_THREADS = 512;
+constexpr int BOT_WARPS = 16;
+constexpr int HESS_THREADS = 256;
+constexpr int LEAF_WARPS = 4;
+constexpr int LEAF_SMAX = (GBSBIN_BT_MAX_HESS + 31) / 32;
+
+template <class Ar>
+__device__ __forceinline__ typename Ar::E* elem(float4* p) {
+  return reinterpret_cast<typename Ar::E*>(p);
+}
+template <class Ar>
+__device__ __forceinline__ const typename Ar::E* elem(const float4* p) {
+  return reinterpret_cast<const typename Ar::E*>(p);
+}
+
+// w = exp(2 pi i k / R_l)
+template <class Ar>
+__device__ __forceinline__ typename Ar::E bt_root(const BTreeArgs& a, int l, int k) {
+  if constexpr (std::is_same<Ar, ArDF>::value) {
+    int off = 0;
+    for (int q = 0; q < l; ++q) off += a.grid.radix[q];
+    return a.twdf[off + k];
+  } else {
+    return Ar::from(grid_root(a.tw, a.grid, l, k));
+  }
+}
+
+// Entry (i, s) of a level's G form from the parent's augmented entry v (see the top of the
+// file): the group's rows (i < nbg) are scaled by the root and their group columns become
+// I - w A_00; the other rows have their group columns negated.
+template <class Ar>
+__device__ __forceinline__ typename Ar::E g_form(typename Ar::E v, int i, int s, int nbg, typename Ar::E w) {
+  if (i < nbg) {
+    v = Ar::mul(w, v);
+    if (s < nbg) {
+      v = Ar::neg(v);
+      if (s == i) v = Ar::add(v, Ar::one());
+    }
+  } else if (s < nbg) {
+    v = Ar::neg(v);
+  }
+  return v;
+}
+
+// Path record: the pivot product scaled by a power of two, then (FP32 sum of the pivots'
+// arguments, the power of two, the smallest pivot real part, -).
+template <class E>
+struct BRec {
+  E prod;
+  float4 meta;
+};
+static_assert(sizeof(BRec<float4>) == 2 * sizeof(float4) && sizeof(BRec<double2>) == 2 * sizeof(float4),
+              "path records are two 16-byte slots");
+
+// Fold count pivots (read through piv(k)) into the record rec, by one full warp: each lane
+// multiplies its share, a butterfly combines them.  Every lane returns the new record.
+template <class Ar, class PivFn>
+__device__ __forceinline__ BRec<typename Ar::E> fold_pivots(BRec<typename Ar::E> rec, int count, PivFn piv) {
+  using E = typename Ar::E;
+  const int lane = threadIdx.x & 31;
+  E p = Ar::one();
+  float arg = 0.f, mn = 3.0e38f, e2 = 0.f;
+  int since = 0;
+  for (int k = lane; k < count; k += 32) {
+    const E q = piv(k);
+    const float qr = Ar::re(q), qi = Ar::im(q);
+    arg = __fadd_rn(arg, atan2f(qi, qr));
+    mn = fminf(mn, qr);
+    if (!(qr == qr) || !(qi == qi)) mn = -3.0e38f;
+    p = Ar::mul(p, q);
+    if (++since == 8) {                              // |pivot| <= 2: rescale every 8
+      e2 += (float)Ar::normalise(p);
+      since = 0;
+    }
+  }
+  e2 += (float)Ar::normalise(p);
+  for (int o = 16; o > 0; o >>= 1) {
+    p = Ar::mul(p, shfl_xor(p, o));
+    e2 += __shfl_xor_sync(0xffffffffu, e2, o);
+    e2 += (float)Ar::normalise(p);
+    arg = __fadd_rn(arg, __shfl_xor_sync(0xffffffffu, arg, o));
+    mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+  }
+  BRec<E> out;
+  out.prod = Ar::mul(rec.prod, p);
+  const float e = rec.meta.y + e2 + (float)Ar::normalise(out.prod);
+  out.meta = make_float4(__fadd_rn(rec.meta.x, arg), e, fminf(rec.meta.z, mn), 0.f);
+  return out;
+}
+
+template <class Ar>
+__device__ __forceinline__ BRec<typename Ar::E>* rec_at(float4* base, long long node) {
+  return reinterpret_cast<BRec<typename Ar::E>*>(base + 2 * node);
+}
+
+// Input matrix of a sub-step for a child: the parent's augmented matrix (first sub-step of
+// a level, roots applied on load) or the child's own trailing block.
+template <class Ar>
+__device__ __forceinline__ const typename Ar::E* step_input(const BTreeArgs& a, const BTreeStep& st, long long child,
+                                                            long long parent) {
+  const long long DD = (long long)st.D * st.D;
+  return st.first ? elem<Ar>(a.mat[st.l]) + parent * DD : elem<Ar>(st.in) + child * DD;
+}
+
+// ---------------------------------------------------------------------------- top
+// One CTA per child: the nbs pivot rows (D columns) in shared memory, forward elimination
+// among themselves.  Step kk: every warp forms 1 / u_kk and the multipliers of its own rows
+// (column kk and row kk are not written in step kk), then updates its rows right of kk; one
+// barrier per step.
+template <class Ar>
+__global__ void __launch_bounds__(TOP_THREADS) k_bt_top(BTreeArgs a, BTreeStep st) {
+  using E = typename Ar::E;
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  const int D = st.D, nbs = st.nbs;
+  E* U = reinterpret_cast<E*>(sm_raw);               // nbs x D
+  E* pinv = U + (size_t)nbs * D;                     // nbs
+  const long long child = blockIdx.x;
+  const int R = a.grid.radix[st.l];
+  const long long parent = child / R;
+  const E w = bt_root<Ar>(a, st.l, (int)(child - parent * R));
+  const E* src = step_input<Ar>(a, st, child, parent);
+  const int tid = threadIdx.x, T = blockDim.x, lane = tid & 31, warp = tid >> 5, NW = T >> 5;
+  for (int idx = tid; idx < nbs * D; idx += T) {
+    const int i = idx / D, s = idx - i * D;
+    E v = src[idx];
+    if (st.first) v = g_form<Ar>(v, i, s, st.nbg, w);
+    U[idx] = v;
+  }
+  __syncthreads();
+  for (int kk = 0; kk < nbs; ++kk) {
+    const E* Uk = U + (size_t)kk * D;
+    const E r = Ar::recip(Uk[kk]);
+    if (tid == 0) pinv[kk] = r;
+    for (int i = kk + 1 + warp; i < nbs; i += NW) {
+      E* Ui = U + (size_t)i * D;
+      const E li = Ar::mul(Ui[kk], r);
+      for (int j = kk + 1 + lane; j < D; j += 32) Ui[j] = Ar::fms(Ui[j], li, Uk[j]);
+    }
+    __syncthreads();
+  }
+  E* Ug = elem<Ar>(a.U) + child * (long long)nbs * D;
+  E* pg = elem<Ar>(a.inv) + child * (long long)nbs;
+  for (int idx = tid; idx < nbs * D; idx += T) Ug[idx] = U[idx];
+  for (int k = tid; k < nbs; k += T) pg[k] = pinv[k];
+  if (warp == 0) {
+    const BRec<E> in = st.first ? *rec_at<Ar>(a.path[st.l], parent) : *rec_at<Ar>(a.path[st.l + 1], child);
+    const BRec<E> out = fold_pivots<Ar>(in, nbs, [&](int k) { return U[(size_t)k * D + k]; });
+    if (lane == 0) *rec_at<Ar>(a.path[st.l + 1], child) = out;
+  }
+}
+
+// ---------------------------------------------------------------------------- bottom
+// CTA (child, chunk): the child's nbs pivot rows and reciprocals staged in shared memory;
+// each warp takes rows nbs + chunk * rows_per_cta + warp, + BOT_WARPS, ...: the row in
+// registers (lane t: columns t + 32 s), eliminated against pivot rows 0 .. nbs - 1 in order
+// (the multiplier is the row's current entry kk, broadcast from its lane), then its
+// trailing part (columns nbs ..) written as row - nbs of the output.
+template <class Ar, int SMAX>
+__global__ void __launch_bounds__(BOT_WARPS * 32) k_bt_bottom(BTreeArgs a, BTreeStep st, int chunks,
+                                                               int rows_per_cta) {
+  using E = typename Ar::E;
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  const int D = st.D, nbs = st.nbs, Do = D - nbs;
+  E* U = reinterpret_cast<E*>(sm_raw);
+  E* pinv = U + (size_t)nbs * D;
+  const long long child = blockIdx.x / chunks;
+  const int chunk = (int)(blockIdx.x - child * chunks);
+  const int R = a.grid.radix[st.l];
+  const long long parent = child / R;
+  const E w = bt_root<Ar>(a, st.l, (int)(child - parent * R));
+  const E* src = step_input<Ar>(a, st, child, parent);
+  E* dst = elem<Ar>(st.out) + child * (long long)Do * Do;
+  const E* Ug = elem<Ar>(a.U) + child * (long long)nbs * D;
+  const E* pg = elem<Ar>(a.inv) + child * (long long)nbs;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int idx = tid; idx < nbs * D; idx += blockDim.x) U[idx] = Ug[idx];
+  for (int k = tid; k < nbs; k += blockDim.x) pinv[k] = pg[k];
+  __syncthreads();
+  const int S = (D + 31) >> 5;
+  const int r0 = nbs + chunk * rows_per_cta, r1 = min(D, r0 + rows_per_cta);
+  for (int i = r0 + warp; i < r1; i += BOT_WARPS) {
+    E r[SMAX];
+#pragma unroll
+    for (int s = 0; s < SMAX; ++s) {
+      const int j = lane + 32 * s;
+      E v = Ar::zero();
+      if (s < S && j < D) {
+        v = src[(long long)i * D + j];
+        if (st.first) v = g_form<Ar>(v, i, j, st.nbg, w);
+      }
+      r[s] = v;
+    }
+#pragma unroll
+    for (int sb = 0; sb < SMAX; ++sb) {              // pivot kk = 32 sb + il sits in slot sb of lane il
+      if (32 * sb >= nbs) break;
+      const int kend = min(32, nbs - 32 * sb);
+      for (int il = 0; il < kend; ++il) {
+        const int kk = 32 * sb + il;
+        const E x = shfl(r[sb], il);
+        const E li = Ar::mul(x, pinv[kk]);
+        const E* Uk = U + (size_t)kk * D;
+#pragma unroll
+        for (int s = sb; s < SMAX; ++s) {
+          const int j = lane + 32 * s;
+          if (s < S && j > kk && j < D) r[s] = Ar::fms(r[s], li, Uk[j]);
+        }
+      }
+    }
+    E* drow = dst + (long long)(i - nbs) * Do;
+#pragma unroll
+    for (int s = 0; s < SMAX; ++s) {
+      const int j = lane + 32 * s;
+      if (s < S && j >= nbs && j < D) drow[j - nbs] = r[s];
+    }
+  }
+}
+
+// ------------------------------------------------------------------------- Hessenberg
+// One CTA per leaf parent: the m x m block A_L with c and conj(u) as two extra columns in
+// shared memory (row stride m + 3, odd in 16-byte units), reduced to upper Hessenberg form
+// by Householder reflectors H_k = I - beta v v^H on rows/columns k + 1 .. m - 1
+// (v = x - alpha e_1, alpha = -e^{i arg x_0} ||x||, beta = 2 / ||v||^2), applied from the left
+// to A and the two columns and from the right to A.  Writes H (m x m), a = Q^T u, b = Q^H c
+// and the exponent collected so far (the augmented corner).
+template <class Ar>
+__global__ void __launch_bounds__(HESS_THREADS) k_bt_hess(BTreeArgs a) {
+  using E = typename Ar::E;
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  const int m = a.mL, ld = m + 3, D = m + 1;
+  E* A = reinterpret_cast<E*>(sm_raw);               // m x ld
+  E* v = A + (size_t)m * ld;                         // m
+  E* sv = v + m;                                     // m + 2 (left products per column)
+  E* tv = sv + m + 2;                                // m (right products per row)
+  E* sc = tv + m;                                    // alpha, beta
+  const long long node = blockIdx.x;
+  const E* src = elem<Ar>(a.mat[a.L - 1]) + node * (long long)D * D;
+  const int tid = threadIdx.x, T = blockDim.x, lane = tid & 31, warp = tid >> 5;
+  for (int idx = tid; idx < m * (m + 2); idx += T) {
+    const int i = idx / (m + 2), j = idx - i * (m + 2);
+    E val;
+    if (j < m) val = src[(long long)i * D + j];
+    else if (j == m) val = src[(long long)i * D + m];                 // c
+    else val = Ar::conj(src[(long long)m * D + i]);                    // conj(u)
+    A[(size_t)i * ld + j] = val;
+  }
+  __syncthreads();
+  for (int k = 0; k + 2 < m; ++k) {
+    if (warp == 0) {                                 // the reflector of column k
+      E nrm2 = Ar::zero();
+      for (int i = k + 1 + lane; i < m; i += 32) nrm2 = Ar::add(nrm2, Ar::norm2(A[(size_t)i * ld + k]));
+      for (int o = 16; o > 0; o >>= 1) nrm2 = Ar::add(nrm2, shfl_xor(nrm2, o));
+      const E x0 = A[(size_t)(k + 1) * ld + k];
+      E alpha = Ar::zero(), beta = Ar::zero();
+      if (Ar::re(nrm2) > 0.f) {
+        const E nrm = Ar::rsqrt_real(nrm2);
+        const E ax0 = Ar::rsqrt_real(Ar::norm2(x0));
+        alpha = Ar::re(ax0) > 0.f ? Ar::neg(Ar::mul(x0, Ar::mul(nrm, Ar::rrecip(ax0)))) : Ar::neg(nrm);
+        // ||v||^2 = ||x||^2 - 2 Re(conj(alpha) x0) + |alpha|^2 = 2 (||x||^2 + ||x|| |x0|)
+        const E vn2 = Ar::add(Ar::add(nrm2, nrm2), Ar::add(Ar::mul(nrm, ax0), Ar::mul(nrm, ax0)));
+        beta = Ar::add(Ar::rrecip(vn2), Ar::rrecip(vn2));
+      }
+      for (int i = k + 1 + lane; i < m; i += 32) {
+        E vi = A[(size_t)i * ld + k];
+        if (i == k + 1) vi = Ar::add(vi, Ar::neg(alpha));
+        v[i] = vi;
+      }
+      if (lane == 0) {
+        sc[0] = alpha;
+        sc[1] = beta;
+      }
+    }
+    __syncthreads();
+    const E beta = sc[1];
+    if (Ar::re(beta) > 0.f) {
+      // left: s_j = sum_{i > k} conj(v_i) A_ij for columns j > k and the two extra columns
+      for (int j = k + 1 + tid; j < m + 2; j += T) {
+        E s = Ar::zero();
+        for (int i = k + 1; i < m; ++i) s = Ar::fma(Ar::conj(v[i]), A[(size_t)i * ld + j], s);
+        sv[j] = Ar::mul(beta, s);
+      }
+      __syncthreads();
+      const int wl = m + 2 - (k + 1);
+      for (int idx = tid; idx < (m - k - 1) * wl; idx += T) {
+        const int i = k + 1 + idx / wl, j = k + 1 + idx % wl;
+        A[(size_t)i * ld + j] = Ar::fms(A[(size_t)i * ld + j], v[i], sv[j]);
+      }
+      __syncthreads();
+      // right: t_i = sum_{j > k} A_ij v_j for every row
+      for (int i = tid; i < m; i += T) {
+        E t = Ar::zero();
+        for (int j = k + 1; j < m; ++j) t = Ar::fma(A[(size_t)i * ld + j], v[j], t);
+        tv[i] = Ar::mul(beta, t);
+      }
+      __syncthreads();
+      const int wr = m - (k + 1);
+      for (int idx = tid; idx < m * wr; idx += T) {
+        const int i = idx / wr, j = k + 1 + idx % wr;
+        A[(size_t)i * ld + j] = Ar::fms(A[(size_t)i * ld + j], tv[i], Ar::conj(v[j]));
+      }
+      if (tid == 0) A[(size_t)(k + 1) * ld + k] = sc[0];
+    }
+    __syncthreads();
+  }
+  E* H = elem<Ar>(a.H) + node * (long long)m * m;
+  E* hv = elem<Ar>(a.hv) + node * (long long)(2 * m + 1);
+  for (int idx = tid; idx < m * m; idx += T) {
+    const int i = idx / m, j = idx - i * m;
+    H[idx] = A[(size_t)i * ld + j];
+  }
+  for (int i = tid; i < m; i += T) {
+    hv[i] = Ar::conj(A[(size_t)i * ld + m + 1]);     // a = Q^T u = conj(Q^H conj(u))
+    hv[m + i] = A[(size_t)i * ld + m];               // b = Q^H c
+  }
+  if (tid == 0) hv[2 * m] = src[(long long)m * D + m];   // the exponent so far
+}
+
+// ----------------------------------------------------------------------------- leaves
+// A warp per evaluated point: the Hessenberg elimination of N = H - conj(w) I with the
+// exponent recurrences (see the top of the file).  Lane t holds entries t + 32 s of the
+// current pivot row (and of the running sums s_j); row i + 1 of H is read from L2.
+template <class Ar, bool DISP>
+__global__ void __launch_bounds__(LEAF_WARPS * 32) k_bt_leaf(BTreeArgs a) {
+  using E = typename Ar::E;
+  const int lane = threadIdx.x & 31;
+  const long long leaf = (long long)blockIdx.x * LEAF_WARPS + (threadIdx.x >> 5);
+  if (leaf >= a.grid.n_eval) return;
+  const int m = a.mL, S = (m + 31) >> 5, l = a.grid.L - 1, half = a.grid.half;
+  const long long parent = leaf / half;
+  const E w = bt_root<Ar>(a, l, (int)(leaf - parent * half));
+  const E sg = Ar::conj(w), mw = Ar::neg(w);
+  const E* H = elem<Ar>(a.H) + parent * (long long)m * m;
+  const E* hv = elem<Ar>(a.hv) + parent * (long long)(2 * m + 1);
+  const E* av = hv;
+  const E* bv = hv + m;
+  E r[LEAF_SMAX], sacc[DISP ? LEAF_SMAX : 1];
+#pragma unroll
+  for (int s = 0; s < LEAF_SMAX; ++s) {
+    const int j = lane + 32 * s;
+    E x = Ar::zero();
+    if (s < S && j < m) {
+      x = H[j];
+      if (j == 0) x = Ar::add(x, Ar::neg(sg));
+    }
+    r[s] = x;
+    if constexpr (DISP) sacc[s] = Ar::zero();
+  }
+  E y = DISP ? bv[0] : Ar::zero();
+  E zy = Ar::zero();
+  BRec<E> rec = *rec_at<Ar>(a.path[l], parent);
+  E prod = rec.prod;
+  float e2 = rec.meta.y, args = rec.meta.x, mn = rec.meta.z;
+#pragma unroll
+  for (int sb = 0; sb < LEAF_SMAX; ++sb) {
+    if (sb >= S) break;
+    for (int il = 0; il < 32; ++il) {
+      const int i = 32 * sb + il;
+      if (i >= m) break;
+      const E q = shfl(r[sb], il);                   // pivot of N
+      const E p = Ar::mul(mw, q);                    // pivot of I - w H
+      const E iq = Ar::recip(q);
+      if constexpr (DISP) {
+        const E si = shfl(sacc[sb], il);
+        const E zi = Ar::mul(Ar::add(av[i], Ar::neg(si)), iq);
+        zy = Ar::fma(zi, y, zy);
+#pragma unroll
+        for (int s = sb; s < LEAF_SMAX; ++s) {
+          const int j = lane + 32 * s;
+          if (s < S && j > i && j < m) sacc[s] = Ar::fma(zi, r[s], sacc[s]);
+        }
+      }
+      const float pr = Ar::re(p), pi = Ar::im(p);
+      mn = fminf(mn, pr);
+      if (!(pr == pr) || !(pi == pi)) mn = -3.0e38f;
+      args = __fadd_rn(args, atan2f(pi, pr));
+      prod = Ar::mul(prod, p);
+      if ((il & 7) == 7) e2 += (float)Ar::normalise(prod);
+      if (i == m - 1) break;
+      const E* hrow = H + (long long)(i + 1) * m;
+      const E li = Ar::mul(hrow[i], iq);
+      if constexpr (DISP) y = Ar::fms(bv[i + 1], li, y);
+#pragma unroll
+      for (int s = sb; s < LEAF_SMAX; ++s) {
+        const int j = lane + 32 * s;
+        if (s < S && j > i && j < m) {
+          E h = hrow[j];
+          if (j == i + 1) h = Ar::add(h, Ar::neg(sg));
+          r[s] = Ar::fms(h, li, r[s]);
+        }
+      }
+    }
+  }
+  e2 += (float)Ar::normalise(prod);
+  if (lane != 0) return;
+  // ex = exponent so far + the leaf's term -a^T N^-1 b
+  const E ex = DISP ? Ar::add(hv[2 * m], Ar::neg(zy)) : Ar::zero();
+  const double LN2 = 0.693147180559945309417232121458;
+  const double2 P = Ar::to(prod), X = Ar::to(ex);
+  double* f = a.ldfin + 6 * leaf;
+  f[0] = P.x;
+  f[1] = P.y;
+  f[2] = (double)args;
+  f[3] = -0.5 * (double)e2 * LN2 + 0.5 * X.x;
+  f[4] = 0.5 * X.y;
+  f[5] = 0.0;
+  a.minpiv[leaf] = (double)mn;
+}
+
+// ---------------------------------------------------------------------------- launch
+size_t top_smem(const BTreeStep& st) { return sizeof(float4) * ((size_t)st.nbs * st.D + st.nbs); }
+
+template <class Ar, int SMAX>
+cudaError_t launch_bottom(const BTreeArgs& a, const BTreeStep& st, long long children, int num_sms, cudaStream_t s) {
+  const size_t smem = top_smem(st);
+  cudaError_t err = cudaSuccess;
+  if (smem > 48 * 1024) {
+    err = cudaFuncSetAttribute(k_bt_bottom<Ar, SMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+  }
+  int per_sm = 0;
+  err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bt_bottom<Ar, SMAX>, BOT_WARPS * 32, smem);
+  if (err != cudaSuccess) return err;
+  if (per_sm < 1) per_sm = 1;
+  // chunks of rows per child so that the launch fills every SM's resident CTAs at least once
+  const int rows = st.D - st.nbs;
+  long long want = ((long long)per_sm * num_sms + children - 1) / children;
+  int chunks = (int)std::min<long long>(std::max<long long>(want, 1), (rows + 7) / 8);
+  if (chunks < 1) chunks = 1;
+  const int rows_per_cta = (rows + chunks - 1) / chunks;
+  chunks = (rows + rows_per_cta - 1) / rows_per_cta;
+  k_bt_bottom<Ar, SMAX><<<(unsigned)(children * chunks), BOT_WARPS * 32, smem, s>>>(a, st, chunks, rows_per_cta);
+  return cudaGetLastError();
+}
+
+template <class Ar>
+cudaError_t launch_btree_ar(const BTreeArgs& a, const BTreeStep* steps, int nsteps, int num_sms, cudaStream_t s,
+                            int* launches) {
+  cudaError_t err = cudaSuccess;
+  *launches = 0;
+  for (int q = 0; q < nsteps; ++q) {
+    const BTreeStep& st = steps[q];
+    long long children = 1;
+    for (int l = 0; l <= st.l; ++l) children *= a.grid.radix[l];
+    const size_t smem = top_smem(st);
+    if (smem > 48 * 1024) {
+      err = cudaFuncSetAttribute(k_bt_top<Ar>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (err != cudaSuccess) return err;
+    }
+    k_bt_top<Ar><<<(unsigned)children, TOP_THREADS, smem, s>>>(a, st);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    const int S = (st.D + 31) / 32;
+    err = S <= 4    ? launch_bottom<Ar, 4>(a, st, children, num_sms, s)
+          : S <= 8  ? launch_bottom<Ar, 8>(a, st, children, num_sms, s)
+          : S <= 12 ? launch_bottom<Ar, 12>(a, st, children, num_sms, s)
+                    : launch_bottom<Ar, 17>(a, st, children, num_sms, s);
+    if (err != cudaSuccess) return err;
+    *launches += 2;
+  }
+  long long parents = 1;
+  for (int l = 0; l + 1 < a.grid.L; ++l) parents *= a.grid.radix[l];
+  const size_t hsmem = btree_hess_smem_bytes(a.mL);
+  if (hsmem > 48 * 1024) {
+    err = cudaFuncSetAttribute(k_bt_hess<Ar>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsmem);
+    if (err != cudaSuccess) return err;
+  }
+  k_bt_hess<Ar><<<(unsigned)parents, HESS_THREADS, hsmem, s>>>(a);
+  if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  const long long blocks = (a.grid.n_eval + LEAF_WARPS - 1) / LEAF_WARPS;
+  if (a.has_gamma) k_bt_leaf<Ar, true><<<(unsigned)blocks, LEAF_WARPS * 32, 0, s>>>(a);
+  else k_bt_leaf<Ar, false><<<(unsigned)blocks, LEAF_WARPS * 32, 0, s>>>(a);
+  *launches += 2;
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t btree_step_smem_bytes(int nbs, int D) { return sizeof(float4) * ((size_t)nbs * D + nbs); }
+size_t btree_hess_smem_bytes(int m) {
+  return sizeof(float4) * ((size_t)m * (m + 3) + (size_t)m + (m + 2) + m + 2);
+}
+
+cudaError_t launch_points_btree(const BTreeArgs& a, const BTreeStep* steps, int nsteps, bool fp64, int num_sms,
+                                cudaStream_t s, int* launches) {
+  return fp64 ? launch_btree_ar<ArF64>(a, steps, nsteps, num_sms, s, launches)
+              : launch_btree_ar<ArDF>(a, steps, nsteps, num_sms, s, launches);
+}
+
+}  // namespace gbsbin

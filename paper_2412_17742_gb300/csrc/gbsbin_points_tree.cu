@@ -79,21 +79,6 @@ __device__ __forceinline__ typename Ar::E root_at(const TreeArgs& a, int l, int 
   }
 }
 
-__device__ __forceinline__ float4 shfl(float4 v, int src) {
-  return make_float4(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src),
-                     __shfl_sync(0xffffffffu, v.z, src), __shfl_sync(0xffffffffu, v.w, src));
-}
-__device__ __forceinline__ double2 shfl(double2 v, int src) {
-  return make_double2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
-}
-__device__ __forceinline__ float4 shfl_xor(float4 v, int mask) {
-  return make_float4(__shfl_xor_sync(0xffffffffu, v.x, mask), __shfl_xor_sync(0xffffffffu, v.y, mask),
-                     __shfl_xor_sync(0xffffffffu, v.z, mask), __shfl_xor_sync(0xffffffffu, v.w, mask));
-}
-__device__ __forceinline__ double2 shfl_xor(double2 v, int mask) {
-  return make_double2(__shfl_xor_sync(0xffffffffu, v.x, mask), __shfl_xor_sync(0xffffffffu, v.y, mask));
-}
-
 // The path record after a set of pivots, by one full warp: lane t holds pivot t of the set
 // (count <= span, a power of two <= 32; lanes beyond hold 1).  Product by a butterfly of
 // pair products over aligned groups of span lanes (each level rescaled by a power of two),
@@ -449,8 +434,9 @@ cudaError_t launch_leaf(const TreeArgs& a, cudaStream_t s) {
 // same launch (a level's fixed costs - launch, fill from the parent, copy-out, path record -
 // are then paid once), up to SPAN_MAX groups and while a level remains before the leaves.
 template <class Ar>
-cudaError_t launch_tree(const TreeArgs& a, int num_sms, cudaStream_t s) {
+cudaError_t launch_tree(const TreeArgs& a, int num_sms, cudaStream_t s, int* launches) {
   cudaError_t err = cudaSuccess;
+  *launches = 1;                                      // the leaves
   long long nodes = 1;
   for (int l = 0; l + 1 < a.grid.L;) {
     long long children = nodes * a.grid.radix[l];
@@ -468,6 +454,7 @@ cudaError_t launch_tree(const TreeArgs& a, int num_sms, cudaStream_t s) {
     const int m = a.m[l], width = m * m;              // entries of the first elimination step
     const int threads = width >= 1024 ? 512 : width >= 256 ? 256 : 128;
     k_tree_level<Ar><<<(unsigned)children, threads, smem, s>>>(a, l, span);
+    ++*launches;
     err = cudaGetLastError();
     if (err != cudaSuccess) return err;
     nodes = children;
@@ -493,8 +480,8 @@ size_t tree_level_smem_bytes(int nb, int m) { return sizeof(float4) * ((size_t)(
 // Leaf blocks of 2, 4, ..., 16 rows have a kernel instance (0: not supported).
 int tree_leaf_threads(int n) { return (n >= 2 && n <= 16 && n % 2 == 0) ? n : 0; }
 
-cudaError_t launch_points_tree(const TreeArgs& a, bool fp64, int num_sms, cudaStream_t s) {
-  return fp64 ? launch_tree<ArF64>(a, num_sms, s) : launch_tree<ArDF>(a, num_sms, s);
+cudaError_t launch_points_tree(const TreeArgs& a, bool fp64, int num_sms, cudaStream_t s, int* launches) {
+  return fp64 ? launch_tree<ArF64>(a, num_sms, s, launches) : launch_tree<ArDF>(a, num_sms, s, launches);
 }
 
 }  // namespace gbsbin

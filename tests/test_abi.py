@@ -160,4 +160,15 @@ def test_tree_kernel_validation(gb, tree):
     assert _status(gb, synth.config(1), tile_override=tree, want_backward=True) == 8
     assert _status(gb, synth.config(1), tile_override=tree, shard=(0, 10)) == 8
     assert _status(gb, synth.config(1), tile_override=9) == 1            # a Fock kernel id
-    assert _status(gb, synth.config(1), tile_override=13) == 1           # no such kernel
+    assert _status(gb, synth.config(1), tile_override=15) == 1           # no such kernel
+
+
+@pytest.mark.parametrize("btree", [13, 14], ids=["df32", "fp64"])
+def test_large_tree_validation(gb, btree):
+    # the large-matrix tree's host-side refusals (before any device call)
+    one_group = synth.random_problem(np.random.default_rng(7), 4, 1, 1, 3)
+    assert _status(gb, one_group, tile_override=btree) == 8              # needs L >= 2
+    big_last = synth.random_problem(np.random.default_rng(9), 120, 1, 2, 2)   # last group 120 rows > 112
+    assert _status(gb, big_last, tile_override=btree) == 8
+    assert _status(gb, synth.config(2), tile_override=btree, want_backward=True) == 8
+    assert _status(gb, synth.config(2), tile_override=btree, shard=(0, 10)) == 8

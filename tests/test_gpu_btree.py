@@ -1,0 +1,113 @@
+"""The large-matrix tree of block eliminations with Hessenberg leaves (kernels 13 and 14)
+against the CPU oracle: every table entry (1e-10 absolute) and every evaluated log q (1e-9,
+imaginary part included, so the square-root branch is checked at every point).
+
+Cases cover one and several sub-steps per level (a level's pivots split when its pivot rows
+exceed the shared-memory budget), groups of uneven and shuffled rows, two to four groups,
+a radix-1 axis, an even and a radix-2 last axis, a two-row last group, displaced and
+undisplaced states, internal modes with non-aligned bases, and both arithmetics.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
+LOGQ_TOL = 1e-9
+
+
+def _flat_index(digits, radix):
+    strides = np.ones(len(radix), dtype=np.int64)
+    for l in range(len(radix) - 2, -1, -1):
+        strides[l] = strides[l + 1] * radix[l + 1]
+    return digits @ strides
+
+
+def _problem(seed, M, K, L, cutoff, **kw):
+    return synth.random_problem(np.random.default_rng(seed), M, K, L, cutoff, **kw)
+
+
+CASES = [
+    # n = 96, three groups of 32 rows, one sub-step per level
+    ("n96_l3_disp_basis", lambda: _problem(901, 12, 4, 3, [3, 4, 5], displaced=True, internal_basis=True)),
+    # n = 300, three groups of 100 rows: level 0 in three sub-steps, level 1 in two
+    ("n300_l3_substeps", lambda: _problem(902, 150, 1, 3, [2, 2, 3], displaced=True)),
+    # n = 200, two groups of 100 rows, undisplaced, even last radix
+    ("n200_l2_even", lambda: _problem(903, 100, 1, 2, [4, 5])),
+    # uneven, shuffled groups over four axes, one of radix 1
+    ("n144_l4_shuffled", lambda: _problem(904, 36, 2, 4, [2, 0, 3, 2], displaced=True, shuffle_bins=True,
+                                          internal_basis=True)),
+    # a two-row last group (a single port), radix-2 last axis
+    ("n130_last_group_two_rows", lambda: synth.Problem(
+        65, 1, np.random.default_rng(905).uniform(0.2, 0.9, (65, 1)),
+        np.sqrt(0.8) * synth.haar_unitary(65, np.random.default_rng(906)),
+        np.array([0] * 64 + [1], np.int32), np.array([3, 1], np.int32),
+        alpha=0.3 * np.ones((65, 1), complex))),
+]
+
+
+@pytest.mark.parametrize("kernel", [13, 14], ids=["df32", "fp64"])
+@pytest.mark.parametrize("name,make", CASES, ids=[c[0] for c in CASES])
+def test_btree_matches_oracle(cuda_lib, name, make, kernel):
+    gb = cuda_lib
+    prob = make()
+    with gb.Plan(prob, precision=1 if kernel == 13 else 0, tile_override=kernel) as p:
+        P = p.table().cpu().numpy()
+        st, d = p.diagnostics()
+        lq, mp = gb.gbsbin_read_points(p.handle, d["n_evaluated"])
+    assert d["kernel"] == kernel
+    assert st == 0 and d["n_bad_points"] == 0
+    res = oracle.binned(prob)
+    ref = res["P"]
+    err = float(np.abs(P - ref).max())
+    assert err <= TOL, (name, kernel, err)
+    dig = gb.evaluated_point_digits(prob.cutoff)
+    full = res["logq"][_flat_index(dig, prob.radix)]
+    assert np.abs(lq - full).max() < LOGQ_TOL, (name, kernel, np.abs(lq - full).max())
+    assert abs(d["log_q1_re"] - res["logq"][0].real) < 1e-10
+    assert d["min_pivot_re"] > 0 and np.all(mp > 0)
+    assert d["launches"] >= 4
+
+
+def test_btree_is_default_for_large_grids(cuda_lib):
+    # the n = 192 workload takes the large-matrix tree in both precisions by default, and
+    # repeated executes are bit-identical (no atomics on the path)
+    gb = cuda_lib
+    prob = synth.config(2)
+    for precision, kernel in ((1, "btree_df32"), (0, "btree_fp64")):
+        with gb.Plan(prob, precision=precision) as p:
+            a = p.table().cpu().numpy()
+            b = p.table().cpu().numpy()
+            st, d = p.diagnostics()
+        assert d["kernel_name"] == kernel and st == 0
+        assert np.array_equal(a, b)
+
+
+def test_btree_set_state(cuda_lib):
+    # a new state on an existing plan re-uploads the permuted augmented matrix
+    gb = cuda_lib
+    a = _problem(907, 40, 2, 2, [3, 4], displaced=True, internal_basis=True)
+    b = _problem(907, 40, 2, 2, [3, 4], displaced=True, internal_basis=True)
+    b.r = b.r * 0.8
+    with gb.Plan(a, precision=1, tile_override=13) as p:
+        gb.gbsbin_plan_set_state(p.handle, b)
+        Pb = p.table().cpu().numpy()
+    assert np.abs(Pb - oracle.binned(b)["P"]).max() <= TOL
+
+
+def test_btree_refuses_what_it_cannot_do(cuda_lib):
+    gb = cuda_lib
+    one_group = _problem(908, 40, 1, 1, 5)
+    with pytest.raises(gb.GbsbinError) as e:
+        gb.Plan(one_group, tile_override=14)
+    assert e.value.status == 8
+    big_last = _problem(909, 120, 1, 2, [2, 2])              # last group of 120 rows > 112
+    with pytest.raises(gb.GbsbinError) as e:
+        gb.Plan(big_last, tile_override=13)
+    assert e.value.status == 8
+    with pytest.raises(gb.GbsbinError) as e:                  # no reverse pass on the tree
+        gb.Plan(_problem(910, 40, 2, 2, [2, 2]), tile_override=13, want_backward=True)
+    assert e.value.status == 8
