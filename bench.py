@@ -82,34 +82,45 @@ def tree_work(prob, n_eval: int, has_gamma: bool):
 
 def btree_work(prob, n_eval: int, has_gamma: bool, smem_slots: int = 200 * 1024 // 16):
     """The large-matrix tree (kernels 13 and 14): complex multiply-adds per table, as the library
-    counts them.  Level l eliminates its group's nb pivots in sub-steps of nbs (as many as fit
-    the shared-memory budget: nbs (D + 1) <= 12800 16-byte slots, D the augmented dimension):
-    the pivot rows among themselves, sum (nbs - kk - 1)(D - kk - 1), and each of the other
-    D - nbs rows against them, sum (D - kk - 1); per leaf parent a Householder reduction to
-    Hessenberg form, sum over k of 2 (m - k - 1)(m - k + 1) + 2 m (m - k - 1); per evaluated point
-    the Hessenberg elimination, m^2 / 2 (twice that when displaced)."""
+    counts them.  Conjugate symmetry halves either the last axis (the leaves) or the first
+    (then every level's nodes halve and each leaf covers a point or its conjugate); the
+    library takes the halving with fewer multiply-adds.  Level l eliminates its group's nb
+    pivots in sub-steps of nbs (as many as fit the shared-memory budget: nbs (D + 1) <= 12800
+    16-byte slots, D the augmented dimension): the pivot rows among themselves,
+    sum (nbs - kk - 1)(D - kk - 1), and each of the other D - nbs rows against them,
+    sum (D - kk - 1); per leaf parent a Householder reduction to Hessenberg form, sum over k of
+    2 (m - k - 1)(m - k + 1) + 2 m (m - k - 1); per leaf the Hessenberg elimination, m^2 / 2
+    (twice that when displaced)."""
     rows = [2 * prob.K * int(np.sum(prob.bin_of_mode == l)) for l in range(prob.L)]
     radix = [int(r) for r in prob.radix]
-    m, nodes, macs = prob.n, 1, 0.0
-    for l in range(prob.L - 1):
-        nodes *= radix[l]
-        D = m + 1
-        cap = smem_slots // (D + 1)
-        nsub = -(-rows[l] // cap)
-        per = -(-rows[l] // nsub)
-        p0 = 0
-        while p0 < rows[l]:
-            nbs = min(per, rows[l] - p0)
-            top = sum((nbs - kk - 1) * (D - kk - 1) for kk in range(nbs))
-            row = sum(D - kk - 1 for kk in range(nbs))
-            macs += nodes * (top + (D - nbs) * row)
-            D -= nbs
-            p0 += nbs
-        m -= rows[l]
-    hess = sum(2.0 * (m - k - 1) * (m - k + 1) + 2.0 * m * (m - k - 1) for k in range(m - 2))
-    macs += nodes * hess
-    macs += n_eval * (2.0 if has_gamma else 1.0) * m * m / 2.0
-    return macs
+    best = None
+    for halve_first in (0, 1):
+        cnt = list(radix)
+        if halve_first:
+            cnt[0] = radix[0] // 2 + 1
+        else:
+            cnt[-1] = radix[-1] // 2 + 1
+        m, nodes, macs = prob.n, 1, 0.0
+        for l in range(prob.L - 1):
+            nodes *= cnt[l]
+            D = m + 1
+            cap = smem_slots // (D + 1)
+            nsub = -(-rows[l] // cap)
+            per = -(-rows[l] // nsub)
+            p0 = 0
+            while p0 < rows[l]:
+                nbs = min(per, rows[l] - p0)
+                top = sum((nbs - kk - 1) * (D - kk - 1) for kk in range(nbs))
+                row = sum(D - kk - 1 for kk in range(nbs))
+                macs += nodes * (top + (D - nbs) * row)
+                D -= nbs
+                p0 += nbs
+            m -= rows[l]
+        hess = sum(2.0 * (m - k - 1) * (m - k + 1) + 2.0 * m * (m - k - 1) for k in range(m - 2))
+        macs += nodes * hess
+        macs += nodes * cnt[-1] * (2.0 if has_gamma else 1.0) * m * m / 2.0
+        best = macs if best is None else min(best, macs)
+    return best
 
 
 def tree_level_launches(radix, L, num_sms=SMS, span_max=4):

@@ -733,14 +733,14 @@ size_t tree_layout(gbsbin_plan* P) {
   return bytes <= (2ull << 30) ? bytes : 0;
 }
 
-// Complex multiply-adds of the large-matrix tree for the plan's sub-step list, and of one
-// LU per evaluated point, for choosing between them.
+// Complex multiply-adds of the large-matrix tree for the plan's sub-step list and root
+// counts (for choosing between its two halvings and against one LU per evaluated point).
 double btree_macs(const gbsbin_plan* P) {
   const BTreeArgs& t = P->btree;
   double macs = 0.0;
   for (const BTreeStep& st : P->btree_steps) {
     double children = 1.0;
-    for (int l = 0; l <= st.l; ++l) children *= P->grid.radix[l];
+    for (int l = 0; l <= st.l; ++l) children *= t.cnt[l];
     double top = 0.0, row = 0.0;
     for (int kk = 0; kk < st.nbs; ++kk) {
       top += (double)(st.nbs - kk - 1) * (st.D - kk - 1);
@@ -749,20 +749,65 @@ double btree_macs(const gbsbin_plan* P) {
     macs += children * (top + (double)(st.D - st.nbs) * row);
   }
   double parents = 1.0;
-  for (int l = 0; l + 1 < P->L; ++l) parents *= P->grid.radix[l];
+  for (int l = 0; l + 1 < P->L; ++l) parents *= t.cnt[l];
   const double m = t.mL;
   double hess = 0.0;
   for (int k = 0; k + 2 < t.mL; ++k) hess += 2.0 * (m - k - 1) * (m - k + 1) + 2.0 * m * (m - k - 1);
   macs += parents * hess;
-  macs += (double)P->grid.n_eval * (P->has_gamma ? 2.0 : 1.0) * m * m / 2.0;
+  macs += (double)t.n_leaves * (P->has_gamma ? 2.0 : 1.0) * m * m / 2.0;
   return macs;
 }
 
-// Large-matrix tree plans: rows ordered by group (as for kernels 11 and 12), the sub-step
-// list (each level's pivots in as few equal sub-steps as the shared-memory budget allows)
-// and the scratch layout.  Returns the device bytes of depths 1 .. L-1, the sub-step
-// scratch and the Hessenberg leaves, or 0 when the problem does not suit it (one group, a
-// last group above GBSBIN_BT_MAX_HESS rows, scratch above 8 GB).
+// The sub-step list and scratch sizes of the large-matrix tree for one halving (the last
+// axis, or the first); nb, m: rows of each group and reduced sizes.  Returns the 16-byte
+// slots of device memory it needs.
+size_t btree_configure(gbsbin_plan* P, int halve_first, const int* nb, const int* m) {
+  const int L = P->L;
+  BTreeArgs& t = P->btree;
+  t.halve_first = halve_first;
+  for (int l = 0; l < L; ++l) t.cnt[l] = P->grid.radix[l];
+  if (halve_first) t.cnt[0] = P->grid.radix[0] / 2 + 1;
+  else t.cnt[L - 1] = P->grid.half;
+  t.n_leaves = 1;
+  for (int l = 0; l < L; ++l) t.n_leaves *= t.cnt[l];
+  P->btree_steps.clear();
+  size_t bytes = 0, tmp_max = 0, u_max = 0, inv_max = 0;
+  long long nodes = 1;
+  for (int l = 0; l + 1 < L; ++l) {
+    const long long children = nodes * t.cnt[l];
+    int D = m[l] + 1;
+    const int cap = (int)(GBSBIN_BT_SMEM / sizeof(float4)) / (D + 1);   // pivots per sub-step
+    if (cap < 1) return 0;
+    const int nsub = (nb[l] + cap - 1) / cap;
+    const int per = (nb[l] + nsub - 1) / nsub;
+    for (int p0 = 0; p0 < nb[l]; p0 += per) {
+      BTreeStep st{};
+      st.l = l;
+      st.first = p0 == 0;
+      st.nbg = nb[l];
+      st.nbs = std::min(per, nb[l] - p0);
+      st.D = D;
+      P->btree_steps.push_back(st);
+      u_max = std::max(u_max, (size_t)children * st.nbs * D);
+      inv_max = std::max(inv_max, (size_t)children * st.nbs);
+      D -= st.nbs;
+      if (p0 + st.nbs < nb[l]) tmp_max = std::max(tmp_max, (size_t)children * D * D);
+    }
+    bytes += (size_t)children * (m[l + 1] + 1) * (m[l + 1] + 1) + 2 * (size_t)children;
+    nodes = children;
+  }
+  const size_t hslots = (size_t)nodes * ((size_t)t.mL * t.mL + 2 * (size_t)t.mL + 1);
+  P->bt_scratch[0] = tmp_max;
+  P->bt_scratch[1] = u_max;
+  P->bt_scratch[2] = inv_max;
+  return bytes + 2 * tmp_max + u_max + inv_max + hslots;
+}
+
+// Large-matrix tree plans: rows ordered by group (as for kernels 11 and 12), each level's
+// pivots in as few equal sub-steps as the shared-memory budget allows, and the halving (last
+// axis or first) that needs fewer multiply-adds.  Returns the device bytes of depths
+// 1 .. L-1, the sub-step scratch and the Hessenberg leaves, or 0 when the problem does not
+// suit it (one group, a last group above GBSBIN_BT_MAX_HESS rows, scratch above 8 GB).
 size_t btree_layout(gbsbin_plan* P) {
   const int L = P->L, n = P->n;
   if (L < 2) return 0;
@@ -786,38 +831,19 @@ size_t btree_layout(gbsbin_plan* P) {
   t.L = L;
   t.mL = m[L - 1];
   if (t.mL > GBSBIN_BT_MAX_HESS || t.mL < 1) return 0;
-  P->btree_steps.clear();
-  size_t bytes = 0, tmp_max = 0, u_max = 0, inv_max = 0;
-  long long nodes = 1;
-  for (int l = 0; l + 1 < L; ++l) {
-    const long long children = nodes * P->grid.radix[l];
-    int D = m[l] + 1;
-    const int cap = (int)(GBSBIN_BT_SMEM / sizeof(float4)) / (D + 1);   // pivots per sub-step
-    if (cap < 1) return 0;
-    const int nsub = (nb[l] + cap - 1) / cap;
-    const int per = (nb[l] + nsub - 1) / nsub;
-    for (int p0 = 0; p0 < nb[l]; p0 += per) {
-      BTreeStep st{};
-      st.l = l;
-      st.first = p0 == 0;
-      st.nbg = nb[l];
-      st.nbs = std::min(per, nb[l] - p0);
-      st.D = D;
-      P->btree_steps.push_back(st);
-      u_max = std::max(u_max, (size_t)children * st.nbs * D);
-      inv_max = std::max(inv_max, (size_t)children * st.nbs);
-      D -= st.nbs;
-      if (p0 + st.nbs < nb[l]) tmp_max = std::max(tmp_max, (size_t)children * D * D);
+  int best = -1;
+  double best_macs = 0.0;
+  for (int h = 0; h < 2; ++h) {
+    if (!btree_configure(P, h, nb, m)) continue;
+    const double w = btree_macs(P);
+    if (best < 0 || w < best_macs) {
+      best = h;
+      best_macs = w;
     }
-    bytes += (size_t)children * (m[l + 1] + 1) * (m[l + 1] + 1) + 2 * (size_t)children;
-    nodes = children;
   }
-  const size_t hslots = (size_t)nodes * ((size_t)t.mL * t.mL + 2 * (size_t)t.mL + 1);
-  const size_t total = bytes + 2 * tmp_max + u_max + inv_max + hslots;
+  if (best < 0) return 0;
+  const size_t total = btree_configure(P, best, nb, m);
   if (total * sizeof(float4) > (8ull << 30)) return 0;
-  P->bt_scratch[0] = tmp_max;
-  P->bt_scratch[1] = u_max;
-  P->bt_scratch[2] = inv_max;
   return total * sizeof(float4);
 }
 
@@ -833,7 +859,7 @@ void btree_pointers(gbsbin_plan* P, const Stage& sl) {
   long long nodes = 1;
   int m = n;
   for (int l = 0; l + 1 < L; ++l) {
-    nodes *= P->grid.radix[l];
+    nodes *= t.cnt[l];
     int nbl = 0;
     for (int x : P->label) nbl += x == l;
     m -= nbl;

@@ -179,6 +179,16 @@ struct BTreeArgs {
   int L;
   int has_gamma;
   int mL;                   // rows of the last group
+  int cnt[GBSBIN_MAX_L];    // roots of axis l the tree takes: child = parent * cnt[l] + k.  Either
+                            // every axis in full but the last halved (leaf = evaluated point), or
+                            // the first halved (cnt[0] = radix[0] / 2 + 1) and the rest in full,
+                            // which halves every level's nodes: each leaf k then writes its
+                            // evaluated point when k_{L-1} <= radix[L-1] / 2 and the conjugate
+                            // point -k (conjugated record) when 1 <= k_0 < radix[0] / 2 and
+                            // k_{L-1} = 0 or 2 k_{L-1} >= radix[L-1], so every evaluated point of
+                            // the half grid is written exactly once
+  int halve_first;
+  long long n_leaves;       // leaves: prod cnt[l]
   GridDesc grid;
   const double2* tw;
   const float4* twdf;

@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(TOP_THREADS) k_bt_top(BTreeArgs a, BTreeStep s
   E* U = reinterpret_cast<E*>(sm_raw);               // nbs x D
   E* pinv = U + (size_t)nbs * D;                     // nbs
   const long long child = blockIdx.x;
-  const int R = a.grid.radix[st.l];
+  const int R = a.cnt[st.l];
   const long long parent = child / R;
   const E w = bt_root<Ar>(a, st.l, (int)(child - parent * R));
   const E* src = step_input<Ar>(a, st, child, parent);
@@ -223,7 +223,7 @@ __global__ void __launch_bounds__(BOT_WARPS * 32) k_bt_bottom(BTreeArgs a, BTree
   E* pinv = U + (size_t)nbs * D;
   const long long child = blockIdx.x / chunks;
   const int chunk = (int)(blockIdx.x - child * chunks);
-  const int R = a.grid.radix[st.l];
+  const int R = a.cnt[st.l];
   const long long parent = child / R;
   const E w = bt_root<Ar>(a, st.l, (int)(child - parent * R));
   const E* src = step_input<Ar>(a, st, child, parent);
@@ -278,8 +278,10 @@ __global__ void __launch_bounds__(BOT_WARPS * 32) k_bt_bottom(BTreeArgs a, BTree
 // shared memory (row stride m + 3, odd in 16-byte units), reduced to upper Hessenberg form
 // by Householder reflectors H_k = I - beta v v^H on rows/columns k + 1 .. m - 1
 // (v = x - alpha e_1, alpha = -e^{i arg x_0} ||x||, beta = 2 / ||v||^2), applied from the left
-// to A and the two columns and from the right to A.  Writes H (m x m), a = Q^T u, b = Q^H c
-// and the exponent collected so far (the augmented corner).
+// to A and the two columns and from the right to A.  Each product vector (v^H A per column,
+// A v per row) is formed by g threads per column or row over interleaved index sets, then
+// summed in a fixed order, so the dependent chains are m / g long.  Writes H (m x m),
+// a = Q^T u, b = Q^H c and the exponent collected so far (the augmented corner).
 template <class Ar>
 __global__ void __launch_bounds__(HESS_THREADS) k_bt_hess(BTreeArgs a) {
   using E = typename Ar::E;
@@ -290,6 +292,7 @@ __global__ void __launch_bounds__(HESS_THREADS) k_bt_hess(BTreeArgs a) {
   E* sv = v + m;                                     // m + 2 (left products per column)
   E* tv = sv + m + 2;                                // m (right products per row)
   E* sc = tv + m;                                    // alpha, beta
+  E* part = sc + 2;                                  // HESS_THREADS partial sums
   const long long node = blockIdx.x;
   const E* src = elem<Ar>(a.mat[a.L - 1]) + node * (long long)D * D;
   const int tid = threadIdx.x, T = blockDim.x, lane = tid & 31, warp = tid >> 5;
@@ -330,11 +333,22 @@ __global__ void __launch_bounds__(HESS_THREADS) k_bt_hess(BTreeArgs a) {
     __syncthreads();
     const E beta = sc[1];
     if (Ar::re(beta) > 0.f) {
-      // left: s_j = sum_{i > k} conj(v_i) A_ij for columns j > k and the two extra columns
-      for (int j = k + 1 + tid; j < m + 2; j += T) {
-        E s = Ar::zero();
-        for (int i = k + 1; i < m; ++i) s = Ar::fma(Ar::conj(v[i]), A[(size_t)i * ld + j], s);
-        sv[j] = Ar::mul(beta, s);
+      // left: s_j = beta sum_{i > k} conj(v_i) A_ij, columns j > k and the two extra columns
+      const int nc = m + 1 - k, gl = max(1, min(8, T / nc));
+      {
+        const int c = tid / gl, g = tid - c * gl;
+        if (c < nc) {
+          const int j = k + 1 + c;
+          E s = Ar::zero();
+          for (int i = k + 1 + g; i < m; i += gl) s = Ar::fma(Ar::conj(v[i]), A[(size_t)i * ld + j], s);
+          part[tid] = s;
+        }
+      }
+      __syncthreads();
+      for (int c = tid; c < nc; c += T) {
+        E s = part[c * gl];
+        for (int g = 1; g < gl; ++g) s = Ar::add(s, part[c * gl + g]);
+        sv[k + 1 + c] = Ar::mul(beta, s);
       }
       __syncthreads();
       const int wl = m + 2 - (k + 1);
@@ -343,10 +357,20 @@ __global__ void __launch_bounds__(HESS_THREADS) k_bt_hess(BTreeArgs a) {
         A[(size_t)i * ld + j] = Ar::fms(A[(size_t)i * ld + j], v[i], sv[j]);
       }
       __syncthreads();
-      // right: t_i = sum_{j > k} A_ij v_j for every row
+      // right: t_i = beta sum_{j > k} A_ij v_j, every row
+      const int gr = max(1, min(8, T / m));
+      {
+        const int i = tid / gr, g = tid - i * gr;
+        if (i < m) {
+          E t = Ar::zero();
+          for (int j = k + 1 + g; j < m; j += gr) t = Ar::fma(A[(size_t)i * ld + j], v[j], t);
+          part[tid] = t;
+        }
+      }
+      __syncthreads();
       for (int i = tid; i < m; i += T) {
-        E t = Ar::zero();
-        for (int j = k + 1; j < m; ++j) t = Ar::fma(A[(size_t)i * ld + j], v[j], t);
+        E t = part[i * gr];
+        for (int g = 1; g < gr; ++g) t = Ar::add(t, part[i * gr + g]);
         tv[i] = Ar::mul(beta, t);
       }
       __syncthreads();
@@ -373,38 +397,60 @@ __global__ void __launch_bounds__(HESS_THREADS) k_bt_hess(BTreeArgs a) {
 }
 
 // ----------------------------------------------------------------------------- leaves
-// A warp per evaluated point: the Hessenberg elimination of N = H - conj(w) I with the
-// exponent recurrences (see the top of the file).  Lane t holds entries t + 32 s of the
-// current pivot row (and of the running sums s_j); row i + 1 of H is read from L2.
+// Unfinished log q record of evaluated point e (see the inverse DFT's first stage), or of its
+// conjugate point: log q(-k) = conj log q(k), so the record becomes (conj P, -arguments,
+// Re part, -Im part).
+__device__ __forceinline__ void write_record(const BTreeArgs& a, long long e, double2 P, double args, double r3,
+                                             double r4, double mn, bool conj) {
+  double* f = a.ldfin + 6 * e;
+  f[0] = P.x;
+  f[1] = conj ? -P.y : P.y;
+  f[2] = conj ? -args : args;
+  f[3] = r3;
+  f[4] = conj ? -r4 : r4;
+  f[5] = 0.0;
+  a.minpiv[e] = mn;
+}
+
+// A warp per leaf: the Hessenberg elimination of N = H - conj(w) I with the exponent
+// recurrences (see the top of the file).  Lane t holds entries t + 32 s of the current pivot
+// row (and of the running sums s_j); row i + 1 of H, the subdiagonal entry and b_{i+1} are read
+// from L2 one step ahead of their use.
 template <class Ar, bool DISP>
 __global__ void __launch_bounds__(LEAF_WARPS * 32) k_bt_leaf(BTreeArgs a) {
   using E = typename Ar::E;
   const int lane = threadIdx.x & 31;
   const long long leaf = (long long)blockIdx.x * LEAF_WARPS + (threadIdx.x >> 5);
-  if (leaf >= a.grid.n_eval) return;
-  const int m = a.mL, S = (m + 31) >> 5, l = a.grid.L - 1, half = a.grid.half;
-  const long long parent = leaf / half;
-  const E w = bt_root<Ar>(a, l, (int)(leaf - parent * half));
+  if (leaf >= a.n_leaves) return;
+  const int m = a.mL, S = (m + 31) >> 5, l = a.grid.L - 1;
+  const int kl = a.cnt[l];
+  const long long parent = leaf / kl;
+  const int klast = (int)(leaf - parent * kl);
+  const E w = bt_root<Ar>(a, l, klast);
   const E sg = Ar::conj(w), mw = Ar::neg(w);
   const E* H = elem<Ar>(a.H) + parent * (long long)m * m;
   const E* hv = elem<Ar>(a.hv) + parent * (long long)(2 * m + 1);
   const E* av = hv;
   const E* bv = hv + m;
-  E r[LEAF_SMAX], sacc[DISP ? LEAF_SMAX : 1];
+  E r[LEAF_SMAX], nx[LEAF_SMAX], sacc[DISP ? LEAF_SMAX : 1];
 #pragma unroll
   for (int s = 0; s < LEAF_SMAX; ++s) {
     const int j = lane + 32 * s;
-    E x = Ar::zero();
+    E x = Ar::zero(), y1 = Ar::zero();
     if (s < S && j < m) {
       x = H[j];
       if (j == 0) x = Ar::add(x, Ar::neg(sg));
+      if (m > 1) y1 = H[(long long)m + j];           // row 1, used in step 0
     }
     r[s] = x;
+    nx[s] = y1;
     if constexpr (DISP) sacc[s] = Ar::zero();
   }
+  E hsub = m > 1 ? H[m] : Ar::zero();                // H[1][0]
+  E bnext = (DISP && m > 1) ? bv[1] : Ar::zero();
   E y = DISP ? bv[0] : Ar::zero();
   E zy = Ar::zero();
-  BRec<E> rec = *rec_at<Ar>(a.path[l], parent);
+  const BRec<E> rec = *rec_at<Ar>(a.path[l], parent);
   E prod = rec.prod;
   float e2 = rec.meta.y, args = rec.meta.x, mn = rec.meta.z;
 #pragma unroll
@@ -413,6 +459,19 @@ __global__ void __launch_bounds__(LEAF_WARPS * 32) k_bt_leaf(BTreeArgs a) {
     for (int il = 0; il < 32; ++il) {
       const int i = 32 * sb + il;
       if (i >= m) break;
+      // the next step's row, subdiagonal entry and right-hand side, loaded ahead
+      E nx2[LEAF_SMAX], hsub2 = Ar::zero(), bnext2 = Ar::zero();
+      const bool more = i + 2 < m;
+      const E* hrow2 = H + (long long)(i + 2) * m;
+#pragma unroll
+      for (int s = 0; s < LEAF_SMAX; ++s) {
+        const int j = lane + 32 * s;
+        nx2[s] = (more && s >= sb && s < S && j > i + 1 && j < m) ? hrow2[j] : Ar::zero();
+      }
+      if (more) {
+        hsub2 = hrow2[i + 1];
+        if constexpr (DISP) bnext2 = bv[i + 2];
+      }
       const E q = shfl(r[sb], il);                   // pivot of N
       const E p = Ar::mul(mw, q);                    // pivot of I - w H
       const E iq = Ar::recip(q);
@@ -433,18 +492,21 @@ __global__ void __launch_bounds__(LEAF_WARPS * 32) k_bt_leaf(BTreeArgs a) {
       prod = Ar::mul(prod, p);
       if ((il & 7) == 7) e2 += (float)Ar::normalise(prod);
       if (i == m - 1) break;
-      const E* hrow = H + (long long)(i + 1) * m;
-      const E li = Ar::mul(hrow[i], iq);
-      if constexpr (DISP) y = Ar::fms(bv[i + 1], li, y);
+      const E li = Ar::mul(hsub, iq);
+      if constexpr (DISP) y = Ar::fms(bnext, li, y);
 #pragma unroll
       for (int s = sb; s < LEAF_SMAX; ++s) {
         const int j = lane + 32 * s;
         if (s < S && j > i && j < m) {
-          E h = hrow[j];
+          E h = nx[s];
           if (j == i + 1) h = Ar::add(h, Ar::neg(sg));
           r[s] = Ar::fms(h, li, r[s]);
         }
       }
+#pragma unroll
+      for (int s = 0; s < LEAF_SMAX; ++s) nx[s] = nx2[s];
+      hsub = hsub2;
+      bnext = bnext2;
     }
   }
   e2 += (float)Ar::normalise(prod);
@@ -453,14 +515,33 @@ __global__ void __launch_bounds__(LEAF_WARPS * 32) k_bt_leaf(BTreeArgs a) {
   const E ex = DISP ? Ar::add(hv[2 * m], Ar::neg(zy)) : Ar::zero();
   const double LN2 = 0.693147180559945309417232121458;
   const double2 P = Ar::to(prod), X = Ar::to(ex);
-  double* f = a.ldfin + 6 * leaf;
-  f[0] = P.x;
-  f[1] = P.y;
-  f[2] = (double)args;
-  f[3] = -0.5 * (double)e2 * LN2 + 0.5 * X.x;
-  f[4] = 0.5 * X.y;
-  f[5] = 0.0;
-  a.minpiv[leaf] = (double)mn;
+  const double r3 = -0.5 * (double)e2 * LN2 + 0.5 * X.x, r4 = 0.5 * X.y;
+  if (!a.halve_first) {
+    write_record(a, leaf, P, (double)args, r3, r4, (double)mn, false);
+    return;
+  }
+  // the leaf's digits (cnt radices) -> its evaluated point and, where it is the source, the
+  // conjugate evaluated point
+  const GridDesc& g = a.grid;
+  int dig[GBSBIN_MAX_L];
+  long long rest = leaf;
+  for (int q = g.L - 1; q >= 0; --q) {
+    const long long up = rest / a.cnt[q];
+    dig[q] = (int)(rest - up * a.cnt[q]);
+    rest = up;
+  }
+  const int RL = g.radix[g.L - 1];
+  if (2 * dig[g.L - 1] <= RL) {
+    long long e = 0;
+    for (int q = 0; q + 1 < g.L; ++q) e = e * g.radix[q] + dig[q];
+    write_record(a, e * g.half + dig[g.L - 1], P, (double)args, r3, r4, (double)mn, false);
+  }
+  if (dig[0] >= 1 && 2 * dig[0] < g.radix[0] && (dig[g.L - 1] == 0 || 2 * dig[g.L - 1] >= RL)) {
+    long long e = 0;
+    for (int q = 0; q + 1 < g.L; ++q) e = e * g.radix[q] + (dig[q] == 0 ? 0 : g.radix[q] - dig[q]);
+    const int cl = dig[g.L - 1] == 0 ? 0 : RL - dig[g.L - 1];
+    write_record(a, e * g.half + cl, P, (double)args, r3, r4, (double)mn, true);
+  }
 }
 
 // ---------------------------------------------------------------------------- launch
@@ -497,7 +578,7 @@ cudaError_t launch_btree_ar(const BTreeArgs& a, const BTreeStep* steps, int nste
   for (int q = 0; q < nsteps; ++q) {
     const BTreeStep& st = steps[q];
     long long children = 1;
-    for (int l = 0; l <= st.l; ++l) children *= a.grid.radix[l];
+    for (int l = 0; l <= st.l; ++l) children *= a.cnt[l];
     const size_t smem = top_smem(st);
     if (smem > 48 * 1024) {
       err = cudaFuncSetAttribute(k_bt_top<Ar>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -514,7 +595,7 @@ cudaError_t launch_btree_ar(const BTreeArgs& a, const BTreeStep* steps, int nste
     *launches += 2;
   }
   long long parents = 1;
-  for (int l = 0; l + 1 < a.grid.L; ++l) parents *= a.grid.radix[l];
+  for (int l = 0; l + 1 < a.grid.L; ++l) parents *= a.cnt[l];
   const size_t hsmem = btree_hess_smem_bytes(a.mL);
   if (hsmem > 48 * 1024) {
     err = cudaFuncSetAttribute(k_bt_hess<Ar>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsmem);
@@ -522,7 +603,7 @@ cudaError_t launch_btree_ar(const BTreeArgs& a, const BTreeStep* steps, int nste
   }
   k_bt_hess<Ar><<<(unsigned)parents, HESS_THREADS, hsmem, s>>>(a);
   if ((err = cudaGetLastError()) != cudaSuccess) return err;
-  const long long blocks = (a.grid.n_eval + LEAF_WARPS - 1) / LEAF_WARPS;
+  const long long blocks = (a.n_leaves + LEAF_WARPS - 1) / LEAF_WARPS;
   if (a.has_gamma) k_bt_leaf<Ar, true><<<(unsigned)blocks, LEAF_WARPS * 32, 0, s>>>(a);
   else k_bt_leaf<Ar, false><<<(unsigned)blocks, LEAF_WARPS * 32, 0, s>>>(a);
   *launches += 2;
@@ -533,7 +614,7 @@ cudaError_t launch_btree_ar(const BTreeArgs& a, const BTreeStep* steps, int nste
 
 size_t btree_step_smem_bytes(int nbs, int D) { return sizeof(float4) * ((size_t)nbs * D + nbs); }
 size_t btree_hess_smem_bytes(int m) {
-  return sizeof(float4) * ((size_t)m * (m + 3) + (size_t)m + (m + 2) + m + 2);
+  return sizeof(float4) * ((size_t)m * (m + 3) + (size_t)m + (m + 2) + m + 2 + HESS_THREADS);
 }
 
 cudaError_t launch_points_btree(const BTreeArgs& a, const BTreeStep* steps, int nsteps, bool fp64, int num_sms,
