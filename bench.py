@@ -104,7 +104,7 @@ def btree_work(prob, n_eval: int, has_gamma: bool, smem_slots: int = 200 * 1024 
         for l in range(prob.L - 1):
             nodes *= cnt[l]
             D = m + 1
-            cap = smem_slots // (D + 1)
+            cap = min(128, smem_slots // (D + 1))
             nsub = -(-rows[l] // cap)
             per = -(-rows[l] // nsub)
             p0 = 0

@@ -67,8 +67,39 @@ __device__ __forceinline__ float4 df_conj(float4 a) { return make_float4(a.x, -a
 __device__ __forceinline__ float4 df_neg(float4 a) { return make_float4(-a.x, -a.y, -a.z, -a.w); }
 // c + a b
 __device__ __forceinline__ float4 df_fma(float4 a, float4 b, float4 c) { return df_add(c, df_mul(a, b)); }
-// c - a b
-__device__ __forceinline__ float4 df_fms(float4 c, float4 a, float4 b) { return df_add(c, df_neg(df_mul(a, b))); }
+// c - a b, fused: per component the two hi x hi products exactly (TwoProduct by FMA), each
+// subtracted from c's hi part by a TwoSum, the rounding errors, c's lo part and the cross
+// terms gathered in FP32, one renormalisation (the product is never renormalised on its own)
+__device__ __forceinline__ float4 df_fms(float4 c, float4 a, float4 b) {
+  // real: c - (a.re b.re - a.im b.im)
+  const float p1 = __fmul_rn(a.x, b.x), e1 = fmaf(a.x, b.x, -p1);
+  const float p2 = __fmul_rn(a.y, b.y), e2 = fmaf(a.y, b.y, -p2);
+  float s, t1, s2, t2;
+  two_sum(c.x, -p1, s, t1);
+  two_sum(s, p2, s2, t2);
+  float er = __fadd_rn(__fadd_rn(t1, t2), c.z);
+  er = __fadd_rn(__fsub_rn(er, e1), e2);
+  er = fmaf(-a.x, b.z, er);
+  er = fmaf(-a.z, b.x, er);
+  er = fmaf(a.y, b.w, er);
+  er = fmaf(a.w, b.y, er);
+  // imaginary: c - (a.re b.im + a.im b.re)
+  const float p3 = __fmul_rn(a.x, b.y), e3 = fmaf(a.x, b.y, -p3);
+  const float p4 = __fmul_rn(a.y, b.x), e4 = fmaf(a.y, b.x, -p4);
+  float u, t3, u2, t4;
+  two_sum(c.y, -p3, u, t3);
+  two_sum(u, -p4, u2, t4);
+  float ei = __fadd_rn(__fadd_rn(t3, t4), c.w);
+  ei = __fsub_rn(__fsub_rn(ei, e3), e4);
+  ei = fmaf(-a.x, b.w, ei);
+  ei = fmaf(-a.w, b.x, ei);
+  ei = fmaf(-a.y, b.z, ei);
+  ei = fmaf(-a.z, b.y, ei);
+  float4 r;
+  fast_two_sum(s2, er, r.x, r.z);
+  fast_two_sum(u2, ei, r.y, r.w);
+  return r;
+}
 
 // 1 / a for a nonzero pair a: d = |a|^2 as a real pair, s = 1/d from the FP32 seed s0 =
 // 1/hi(d) by one Newton step s = s0 + s0 (1 - d s0) (the residual 1 - d s0 formed with an

@@ -776,7 +776,7 @@ size_t btree_configure(gbsbin_plan* P, int halve_first, const int* nb, const int
   for (int l = 0; l + 1 < L; ++l) {
     const long long children = nodes * t.cnt[l];
     int D = m[l] + 1;
-    const int cap = (int)(GBSBIN_BT_SMEM / sizeof(float4)) / (D + 1);   // pivots per sub-step
+    const int cap = std::min(GBSBIN_BT_MAX_NBS, (int)(GBSBIN_BT_SMEM / sizeof(float4)) / (D + 1));   // pivots per sub-step
     if (cap < 1) return 0;
     const int nsub = (nb[l] + cap - 1) / cap;
     const int per = (nb[l] + nsub - 1) / nsub;

@@ -166,6 +166,7 @@ struct TreeArgs {
 // point is an O(m^2) Hessenberg elimination (a warp per point) writing the unfinished log q.
 #define GBSBIN_BT_MAX_HESS 112          // largest last group (shared-memory Householder)
 #define GBSBIN_BT_SMEM (200 * 1024)     // shared-memory budget of one sub-step's pivot rows
+#define GBSBIN_BT_MAX_NBS 128           // pivots of one sub-step (at most)
 struct BTreeStep {
   int l;                    // level: the grid axis whose roots this sub-step applies
   int first;                // first sub-step of the level: input is the parent's matrix at depth l

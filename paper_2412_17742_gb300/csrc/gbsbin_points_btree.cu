@@ -47,6 +47,7 @@
 // branch is the per-point LU's.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <type_traits>
 
 #include "gbsbin_device.cuh"
@@ -161,115 +162,153 @@ __device__ __forceinline__ const typename Ar::E* step_input(const BTreeArgs& a, 
 }
 
 // ---------------------------------------------------------------------------- top
-// One CTA per child: the nbs pivot rows (D columns) in shared memory, forward elimination
-// among themselves.  Step kk: every warp forms 1 / u_kk and the multipliers of its own rows
-// (column kk and row kk are not written in step kk), then updates its rows right of kk; one
-// barrier per step.
+// CTA (child, part): the nbs pivot rows in shared memory - their first nbs columns (the pivot
+// block) and the part's share of the columns right of it (every column when parts = 1; the
+// parts split the right-hand columns when a level has few children, each redoing the pivot
+// block) - and their forward elimination among themselves.  Step kk: every warp forms
+// 1 / u_kk and the multipliers of its own rows (column kk and row kk are not written in step
+// kk), then updates its rows right of kk; one barrier per step.  Part 0 also writes the pivot
+// block, the reciprocal pivots and the child's path record.
 template <class Ar>
-__global__ void __launch_bounds__(TOP_THREADS) k_bt_top(BTreeArgs a, BTreeStep st) {
+__global__ void __launch_bounds__(TOP_THREADS) k_bt_top(BTreeArgs a, BTreeStep st, int parts, int W) {
   using E = typename Ar::E;
   extern __shared__ __align__(16) unsigned char sm_raw[];
-  const int D = st.D, nbs = st.nbs;
-  E* U = reinterpret_cast<E*>(sm_raw);               // nbs x D
-  E* pinv = U + (size_t)nbs * D;                     // nbs
-  const long long child = blockIdx.x;
+  const int D = st.D, nbs = st.nbs;                  // W: right-hand columns per part, (parts - 1) W < D - nbs
+  const long long child = blockIdx.x / parts;
+  const int part = (int)(blockIdx.x - child * parts);
+  const int c0 = nbs + part * W, c1 = min(D, c0 + W);  // this part's right-hand columns
+  const int Dl = nbs + (c1 - c0);                    // local columns: pivot block, then the share
+  E* U = reinterpret_cast<E*>(sm_raw);               // nbs x Dl
+  E* pinv = U + (size_t)nbs * Dl;                    // nbs
   const int R = a.cnt[st.l];
   const long long parent = child / R;
   const E w = bt_root<Ar>(a, st.l, (int)(child - parent * R));
   const E* src = step_input<Ar>(a, st, child, parent);
   const int tid = threadIdx.x, T = blockDim.x, lane = tid & 31, warp = tid >> 5, NW = T >> 5;
-  for (int idx = tid; idx < nbs * D; idx += T) {
-    const int i = idx / D, s = idx - i * D;
-    E v = src[idx];
-    if (st.first) v = g_form<Ar>(v, i, s, st.nbg, w);
+  for (int idx = tid; idx < nbs * Dl; idx += T) {
+    const int i = idx / Dl, c = idx - i * Dl;
+    const int g = c < nbs ? c : c0 + (c - nbs);
+    E v = src[(long long)i * D + g];
+    if (st.first) v = g_form<Ar>(v, i, g, st.nbg, w);
     U[idx] = v;
   }
   __syncthreads();
   for (int kk = 0; kk < nbs; ++kk) {
-    const E* Uk = U + (size_t)kk * D;
+    const E* Uk = U + (size_t)kk * Dl;
     const E r = Ar::recip(Uk[kk]);
     if (tid == 0) pinv[kk] = r;
     for (int i = kk + 1 + warp; i < nbs; i += NW) {
-      E* Ui = U + (size_t)i * D;
+      E* Ui = U + (size_t)i * Dl;
       const E li = Ar::mul(Ui[kk], r);
-      for (int j = kk + 1 + lane; j < D; j += 32) Ui[j] = Ar::fms(Ui[j], li, Uk[j]);
+      for (int j = kk + 1 + lane; j < Dl; j += 32) Ui[j] = Ar::fms(Ui[j], li, Uk[j]);
     }
     __syncthreads();
   }
   E* Ug = elem<Ar>(a.U) + child * (long long)nbs * D;
+  for (int idx = tid; idx < nbs * Dl; idx += T) {
+    const int i = idx / Dl, c = idx - i * Dl;
+    if (c >= nbs) Ug[(long long)i * D + c0 + (c - nbs)] = U[idx];
+    else if (part == 0) Ug[(long long)i * D + c] = U[idx];
+  }
+  if (part != 0) return;
   E* pg = elem<Ar>(a.inv) + child * (long long)nbs;
-  for (int idx = tid; idx < nbs * D; idx += T) Ug[idx] = U[idx];
   for (int k = tid; k < nbs; k += T) pg[k] = pinv[k];
   if (warp == 0) {
     const BRec<E> in = st.first ? *rec_at<Ar>(a.path[st.l], parent) : *rec_at<Ar>(a.path[st.l + 1], child);
-    const BRec<E> out = fold_pivots<Ar>(in, nbs, [&](int k) { return U[(size_t)k * D + k]; });
+    const BRec<E> out = fold_pivots<Ar>(in, nbs, [&](int k) { return U[(size_t)k * Dl + k]; });
     if (lane == 0) *rec_at<Ar>(a.path[st.l + 1], child) = out;
   }
 }
 
 // ---------------------------------------------------------------------------- bottom
-// CTA (child, chunk): the child's nbs pivot rows and reciprocals staged in shared memory;
-// each warp takes rows nbs + chunk * rows_per_cta + warp, + BOT_WARPS, ...: the row in
-// registers (lane t: columns t + 32 s), eliminated against pivot rows 0 .. nbs - 1 in order
-// (the multiplier is the row's current entry kk, broadcast from its lane), then its
-// trailing part (columns nbs ..) written as row - nbs of the output.
+// The other rows of every child, D - nbs per child, taken as one sequence (child-major) and
+// split evenly over the CTAs (one per resident slot): a CTA walks its share child by child,
+// staging each child's nbs pivot rows and reciprocals in shared memory.  A warp per row: the
+// row's first Dm columns in registers (lane t: columns t + 32 s), eliminated against pivot
+// rows 0 .. nbs - 1 in order (the multiplier is the row's current entry kk, broadcast from
+// its lane; lane kk mod 32 keeps it), then the trailing part (columns nbs ..) written as row
+// - nbs of the output.  Columns Dm .. D - 1 (a short tail, such as the augmented column when
+// D = 32 s + 1) need no register slot: each is its initial value minus the dot product of the
+// kept multipliers with the pivot rows' entries, summed over the lanes by a fixed butterfly.
 template <class Ar, int SMAX>
-__global__ void __launch_bounds__(BOT_WARPS * 32) k_bt_bottom(BTreeArgs a, BTreeStep st, int chunks,
-                                                               int rows_per_cta) {
+__global__ void __launch_bounds__(BOT_WARPS * 32) k_bt_bottom(BTreeArgs a, BTreeStep st, int Dm, long long rows_total) {
   using E = typename Ar::E;
+  constexpr int LMS = GBSBIN_BT_MAX_NBS / 32;          // register slots of the multipliers
   extern __shared__ __align__(16) unsigned char sm_raw[];
-  const int D = st.D, nbs = st.nbs, Do = D - nbs;
+  const int D = st.D, nbs = st.nbs, Do = D - nbs, S = (Dm + 31) >> 5;
   E* U = reinterpret_cast<E*>(sm_raw);
   E* pinv = U + (size_t)nbs * D;
-  const long long child = blockIdx.x / chunks;
-  const int chunk = (int)(blockIdx.x - child * chunks);
   const int R = a.cnt[st.l];
-  const long long parent = child / R;
-  const E w = bt_root<Ar>(a, st.l, (int)(child - parent * R));
-  const E* src = step_input<Ar>(a, st, child, parent);
-  E* dst = elem<Ar>(st.out) + child * (long long)Do * Do;
-  const E* Ug = elem<Ar>(a.U) + child * (long long)nbs * D;
-  const E* pg = elem<Ar>(a.inv) + child * (long long)nbs;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int idx = tid; idx < nbs * D; idx += blockDim.x) U[idx] = Ug[idx];
-  for (int k = tid; k < nbs; k += blockDim.x) pinv[k] = pg[k];
-  __syncthreads();
-  const int S = (D + 31) >> 5;
-  const int r0 = nbs + chunk * rows_per_cta, r1 = min(D, r0 + rows_per_cta);
-  for (int i = r0 + warp; i < r1; i += BOT_WARPS) {
-    E r[SMAX];
+  const long long g0 = rows_total * blockIdx.x / gridDim.x, g1 = rows_total * (blockIdx.x + 1) / gridDim.x;
+  for (long long gs = g0; gs < g1;) {
+    const long long child = gs / Do;
+    const long long ge = min(g1, (child + 1) * Do);  // this child's rows in the share
+    const long long parent = child / R;
+    const E w = bt_root<Ar>(a, st.l, (int)(child - parent * R));
+    const E* src = step_input<Ar>(a, st, child, parent);
+    E* dst = elem<Ar>(st.out) + child * (long long)Do * Do;
+    const E* Ug = elem<Ar>(a.U) + child * (long long)nbs * D;
+    const E* pg = elem<Ar>(a.inv) + child * (long long)nbs;
+    __syncthreads();                                 // the previous child's rows are done
+    for (int idx = tid; idx < nbs * D; idx += blockDim.x) U[idx] = Ug[idx];
+    for (int k = tid; k < nbs; k += blockDim.x) pinv[k] = pg[k];
+    __syncthreads();
+    for (long long gr = gs + warp; gr < ge; gr += BOT_WARPS) {
+      const int i = nbs + (int)(gr - child * Do);
+      const E* srow = src + (long long)i * D;
+      E r[SMAX], lm[LMS];
 #pragma unroll
-    for (int s = 0; s < SMAX; ++s) {
-      const int j = lane + 32 * s;
-      E v = Ar::zero();
-      if (s < S && j < D) {
-        v = src[(long long)i * D + j];
-        if (st.first) v = g_form<Ar>(v, i, j, st.nbg, w);
+      for (int s = 0; s < SMAX; ++s) {
+        const int j = lane + 32 * s;
+        E v = Ar::zero();
+        if (s < S && j < Dm) {
+          v = srow[j];
+          if (st.first) v = g_form<Ar>(v, i, j, st.nbg, w);
+        }
+        r[s] = v;
       }
-      r[s] = v;
-    }
 #pragma unroll
-    for (int sb = 0; sb < SMAX; ++sb) {              // pivot kk = 32 sb + il sits in slot sb of lane il
-      if (32 * sb >= nbs) break;
-      const int kend = min(32, nbs - 32 * sb);
-      for (int il = 0; il < kend; ++il) {
-        const int kk = 32 * sb + il;
-        const E x = shfl(r[sb], il);
-        const E li = Ar::mul(x, pinv[kk]);
-        const E* Uk = U + (size_t)kk * D;
+      for (int s = 0; s < LMS; ++s) lm[s] = Ar::zero();
 #pragma unroll
-        for (int s = sb; s < SMAX; ++s) {
-          const int j = lane + 32 * s;
-          if (s < S && j > kk && j < D) r[s] = Ar::fms(r[s], li, Uk[j]);
+      for (int sb = 0; sb < SMAX; ++sb) {            // pivot kk = 32 sb + il sits in slot sb of lane il
+        if (32 * sb >= nbs) break;
+        const int kend = min(32, nbs - 32 * sb);
+        for (int il = 0; il < kend; ++il) {
+          const int kk = 32 * sb + il;
+          const E x = shfl(r[sb], il);
+          const E li = Ar::mul(x, pinv[kk]);
+          if (sb < LMS && lane == il) lm[sb < LMS ? sb : 0] = li;
+          const E* Uk = U + (size_t)kk * D;
+#pragma unroll
+          for (int s = sb; s < SMAX; ++s) {
+            const int j = lane + 32 * s;
+            if (s < S && j > kk && j < Dm) r[s] = Ar::fms(r[s], li, Uk[j]);
+          }
+        }
+      }
+      E* drow = dst + (long long)(i - nbs) * Do;
+#pragma unroll
+      for (int s = 0; s < SMAX; ++s) {
+        const int j = lane + 32 * s;
+        if (s < S && j >= nbs && j < Dm) drow[j - nbs] = r[s];
+      }
+      for (int t = Dm; t < D; ++t) {                 // the tail: initial value - sum_kk l_kk U[kk][t]
+        E acc = Ar::zero();
+#pragma unroll
+        for (int s = 0; s < LMS; ++s) {
+          const int kk = lane + 32 * s;
+          if (kk < nbs) acc = Ar::fma(lm[s], U[(size_t)kk * D + t], acc);
+        }
+        for (int o = 16; o > 0; o >>= 1) acc = Ar::add(acc, shfl_xor(acc, o));
+        if (lane == 0) {
+          E v = srow[t];
+          if (st.first) v = g_form<Ar>(v, i, t, st.nbg, w);
+          drow[t - nbs] = Ar::add(v, Ar::neg(acc));
         }
       }
     }
-    E* drow = dst + (long long)(i - nbs) * Do;
-#pragma unroll
-    for (int s = 0; s < SMAX; ++s) {
-      const int j = lane + 32 * s;
-      if (s < S && j >= nbs && j < D) drow[j - nbs] = r[s];
-    }
+    gs = ge;
   }
 }
 
@@ -417,7 +456,7 @@ __device__ __forceinline__ void write_record(const BTreeArgs& a, long long e, do
 // row (and of the running sums s_j); row i + 1 of H, the subdiagonal entry and b_{i+1} are read
 // from L2 one step ahead of their use.
 template <class Ar, bool DISP>
-__global__ void __launch_bounds__(LEAF_WARPS * 32) k_bt_leaf(BTreeArgs a) {
+__global__ void __launch_bounds__(LEAF_WARPS * 32, 4) k_bt_leaf(BTreeArgs a) {
   using E = typename Ar::E;
   const int lane = threadIdx.x & 31;
   const long long leaf = (long long)blockIdx.x * LEAF_WARPS + (threadIdx.x >> 5);
@@ -451,8 +490,12 @@ __global__ void __launch_bounds__(LEAF_WARPS * 32) k_bt_leaf(BTreeArgs a) {
   E y = DISP ? bv[0] : Ar::zero();
   E zy = Ar::zero();
   const BRec<E> rec = *rec_at<Ar>(a.path[l], parent);
-  E prod = rec.prod;
-  float e2 = rec.meta.y, args = rec.meta.x, mn = rec.meta.z;
+  // the leaf's own pivot product lp (scaled by powers of two) and its windings around 0: each
+  // pivot turns lp by less than pi/2 (Re > 0), so a turn across the negative real axis has
+  // both ends in the left half-plane and shows as a sign change of Im lp there
+  E lp = Ar::one();
+  int wind = 0;
+  float e2 = rec.meta.y, mn = rec.meta.z;
 #pragma unroll
   for (int sb = 0; sb < LEAF_SMAX; ++sb) {
     if (sb >= S) break;
@@ -488,9 +531,11 @@ __global__ void __launch_bounds__(LEAF_WARPS * 32) k_bt_leaf(BTreeArgs a) {
       const float pr = Ar::re(p), pi = Ar::im(p);
       mn = fminf(mn, pr);
       if (!(pr == pr) || !(pi == pi)) mn = -3.0e38f;
-      args = __fadd_rn(args, atan2f(pi, pr));
-      prod = Ar::mul(prod, p);
-      if ((il & 7) == 7) e2 += (float)Ar::normalise(prod);
+      const float x0 = Ar::re(lp), y0 = Ar::im(lp);
+      lp = Ar::mul(lp, p);
+      const float x1 = Ar::re(lp), y1 = Ar::im(lp);
+      if (x0 < 0.f && x1 < 0.f) wind += (y0 >= 0.f && y1 < 0.f) ? 1 : (y0 < 0.f && y1 >= 0.f) ? -1 : 0;
+      if ((il & 7) == 7) e2 += (float)Ar::normalise(lp);
       if (i == m - 1) break;
       const E li = Ar::mul(hsub, iq);
       if constexpr (DISP) y = Ar::fms(bnext, li, y);
@@ -509,8 +554,12 @@ __global__ void __launch_bounds__(LEAF_WARPS * 32) k_bt_leaf(BTreeArgs a) {
       bnext = bnext2;
     }
   }
-  e2 += (float)Ar::normalise(prod);
+  e2 += (float)Ar::normalise(lp);
   if (lane != 0) return;
+  const float TWO_PI = 6.28318530717958647692f;
+  const float args = __fadd_rn(rec.meta.x, atan2f(Ar::im(lp), Ar::re(lp)) + TWO_PI * (float)wind);
+  E prod = Ar::mul(rec.prod, lp);
+  e2 += (float)Ar::normalise(prod);
   // ex = exponent so far + the leaf's term -a^T N^-1 b
   const E ex = DISP ? Ar::add(hv[2 * m], Ar::neg(zy)) : Ar::zero();
   const double LN2 = 0.693147180559945309417232121458;
@@ -547,8 +596,18 @@ __global__ void __launch_bounds__(LEAF_WARPS * 32) k_bt_leaf(BTreeArgs a) {
 // ---------------------------------------------------------------------------- launch
 size_t top_smem(const BTreeStep& st) { return sizeof(float4) * ((size_t)st.nbs * st.D + st.nbs); }
 
+// Columns of the bottom rows kept in registers: all D, or D rounded down to a multiple of 32
+// when the rest (the tail) is cheaper as dot products of the kept multipliers (~280 pair
+// operations per tail column against 64 per pivot for a register slot).
+int bottom_main_columns(int D, int nbs) {
+  const int tail = D % 32;
+  if (tail == 0 || D - tail <= nbs || tail * 280 >= nbs * 64) return D;
+  return D - tail;
+}
+
 template <class Ar, int SMAX>
-cudaError_t launch_bottom(const BTreeArgs& a, const BTreeStep& st, long long children, int num_sms, cudaStream_t s) {
+cudaError_t launch_bottom(const BTreeArgs& a, const BTreeStep& st, long long children, int Dm, int num_sms,
+                          cudaStream_t s) {
   const size_t smem = top_smem(st);
   cudaError_t err = cudaSuccess;
   if (smem > 48 * 1024) {
@@ -559,14 +618,10 @@ cudaError_t launch_bottom(const BTreeArgs& a, const BTreeStep& st, long long chi
   err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bt_bottom<Ar, SMAX>, BOT_WARPS * 32, smem);
   if (err != cudaSuccess) return err;
   if (per_sm < 1) per_sm = 1;
-  // chunks of rows per child so that the launch fills every SM's resident CTAs at least once
-  const int rows = st.D - st.nbs;
-  long long want = ((long long)per_sm * num_sms + children - 1) / children;
-  int chunks = (int)std::min<long long>(std::max<long long>(want, 1), (rows + 7) / 8);
-  if (chunks < 1) chunks = 1;
-  const int rows_per_cta = (rows + chunks - 1) / chunks;
-  chunks = (rows + rows_per_cta - 1) / rows_per_cta;
-  k_bt_bottom<Ar, SMAX><<<(unsigned)(children * chunks), BOT_WARPS * 32, smem, s>>>(a, st, chunks, rows_per_cta);
+  // one CTA per resident slot, each with an even share of all children's rows
+  const long long rows = children * (long long)(st.D - st.nbs);
+  const long long grid = std::min<long long>((long long)per_sm * num_sms, rows);
+  k_bt_bottom<Ar, SMAX><<<(unsigned)grid, BOT_WARPS * 32, smem, s>>>(a, st, Dm, rows);
   return cudaGetLastError();
 }
 
@@ -579,18 +634,28 @@ cudaError_t launch_btree_ar(const BTreeArgs& a, const BTreeStep* steps, int nste
     const BTreeStep& st = steps[q];
     long long children = 1;
     for (int l = 0; l <= st.l; ++l) children *= a.cnt[l];
-    const size_t smem = top_smem(st);
+    // few children: split the pivot rows' right-hand columns over several CTAs per child
+    const int X = st.D - st.nbs;
+    int parts = 1;
+    if (2 * children < num_sms) {
+      const long long want = (num_sms + children - 1) / children;
+      parts = (int)std::max<long long>(1, std::min<long long>(want, (X + 15) / 16));
+    }
+    const int Wp = (X + parts - 1) / parts;
+    parts = (X + Wp - 1) / Wp;                        // no empty part: (parts - 1) Wp < X
+    const size_t smem = btree_step_smem_bytes(st.nbs, st.nbs + Wp);
     if (smem > 48 * 1024) {
       err = cudaFuncSetAttribute(k_bt_top<Ar>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (err != cudaSuccess) return err;
     }
-    k_bt_top<Ar><<<(unsigned)children, TOP_THREADS, smem, s>>>(a, st);
+    k_bt_top<Ar><<<(unsigned)(children * parts), TOP_THREADS, smem, s>>>(a, st, parts, Wp);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
-    const int S = (st.D + 31) / 32;
-    err = S <= 4    ? launch_bottom<Ar, 4>(a, st, children, num_sms, s)
-          : S <= 8  ? launch_bottom<Ar, 8>(a, st, children, num_sms, s)
-          : S <= 12 ? launch_bottom<Ar, 12>(a, st, children, num_sms, s)
-                    : launch_bottom<Ar, 17>(a, st, children, num_sms, s);
+    const int Dm = bottom_main_columns(st.D, st.nbs);
+    const int S = (Dm + 31) / 32;
+    err = S <= 4    ? launch_bottom<Ar, 4>(a, st, children, Dm, num_sms, s)
+          : S <= 8  ? launch_bottom<Ar, 8>(a, st, children, Dm, num_sms, s)
+          : S <= 12 ? launch_bottom<Ar, 12>(a, st, children, Dm, num_sms, s)
+                    : launch_bottom<Ar, 17>(a, st, children, Dm, num_sms, s);
     if (err != cudaSuccess) return err;
     *launches += 2;
   }
