@@ -552,9 +552,9 @@ def extra_workloads(gb, torch, stream, flush, steps, world, which=("n32", "batch
 def _extra_distinguishable(gb, torch, steps):
     """App. D's fine-grained Pr(n) of a fully distinguishable state (16 sources, each in its own
     internal mode, r ~ U(0.5, 0.9), lossy Haar interferometer; one photon per detector: 2^16 =
-    65536 evaluation points, N = 16, where the alternating sum keeps its digits): the device
-    sum (one thread per point, FP64) against the host sum in Gray-code order, per call (the
-    device call includes its buffer allocation); both values reported."""
+    65536 evaluation points, N = 16): the device sum (one thread per point, FP64, compensated)
+    against the host sum in Gray-code order, per call (the device call includes its buffer
+    allocation); both values with their rounding-error estimates."""
     rng = np.random.default_rng(1700)
     M = 16
     r = np.diag(rng.uniform(0.5, 0.9, M))
@@ -565,16 +565,17 @@ def _extra_distinguishable(gb, torch, steps):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(steps):
-        dev = gb.gbsbin_prob_distinguishable_device(prob, pattern)
+        dev, dev_err = gb.gbsbin_prob_distinguishable_device(prob, pattern, with_error=True)
     t_dev = (time.perf_counter() - t0) / steps
     t0 = time.perf_counter()
-    host = gb.gbsbin_prob_distinguishable(prob, pattern)
+    host, host_err = gb.gbsbin_prob_distinguishable(prob, pattern, with_error=True)
     t_host = time.perf_counter() - t0
     pts = 2 ** M
     return {"appd_distinguishable_m16_ones": {"points": pts, "N": M, "device_ms_per_call": t_dev * 1e3,
                                            "device_points_per_s": pts / t_dev, "host_ms": t_host * 1e3,
                                            "host_points_per_s": pts / t_host, "prob_device": dev,
-                                           "prob_host": host, "precision": "fp64"}}
+                                           "prob_device_abs_err_estimate": dev_err, "prob_host": host,
+                                           "prob_host_abs_err_estimate": host_err, "precision": "fp64"}}
 
 
 def _extra_fock(gb, torch, stream, flush, steps, world):

@@ -51,7 +51,10 @@ typedef enum {
   GBSBIN_ERR_NUMERIC = 7,      /* a pivot with Re u_ii <= 0 or a non-finite value at some
                                   grid point (see gbsbin_diagnostics)                      */
   GBSBIN_ERR_UNSUPPORTED = 8,  /* size beyond what this build supports (n > GBSBIN_MAX_N)   */
-  GBSBIN_ERR_TIMEOUT = 9       /* a bounded device-side wait gave up                        */
+  GBSBIN_ERR_TIMEOUT = 9,      /* a bounded device-side wait gave up                        */
+  GBSBIN_ERR_PRECISION = 10    /* the result lost its significant digits to cancellation (its
+                                  rounding-error estimate exceeds 1e-3 of it); the value is
+                                  still written                                           */
 } gbsbin_status;
 
 #define GBSBIN_MAX_N 512                 /* largest matrix size n = 2 M K            */
@@ -431,22 +434,29 @@ int gbsbin_cumulant_groups(const gbsbin_problem* p, unsigned mask, double* kappa
  *   Pr(n) = Pr(0) / prod n_k! sum_{m <= n} prod C(n_k, m_k) (-1)^(N - |m|) f_N(m),
  * f_N(m) = [eta^N] exp(sum_j p_j eta^j / (2j)), p_j = sum_l (lambda1^j + lambda2^j) with the two
  * eigenvalues of sqrt(D(m)) B_l sqrt(D(m)) from its trace T and Frobenius norm F,
- * lambda = T/2 +- sqrt(2F^2 - T^2)/2.  prod (n_k + 1) points, O(K M^2 + K N + N^2) each; the
- * alternating sum cancels (FP64 loses digits as N grows).  Host only.  Errors: ERR_ARG (null
- * pointers, a negative count), ERR_UNSUPPORTED (displaced, not block diagonal over internal
- * modes, a block of rank above 2, or more than 2^40 evaluation points), then as
- * gbsbin_moments.
+ * lambda = T/2 +- sqrt(2F^2 - T^2)/2.  prod (n_k + 1) points, O(K M^2 + K N + N^2) each.  The
+ * alternating sum cancels, more as N grows: it is summed with Neumaier compensation next to
+ * the sum of the terms' magnitudes, and abs_err (may be NULL) receives the estimate
+ * (N + 16) eps Pr(0) / prod n_k! x sum |terms| of the result's absolute rounding error.  Host
+ * only.  Errors: ERR_ARG (null pointers, a negative count), ERR_UNSUPPORTED (displaced, not
+ * block diagonal over internal modes, a block of rank above 2, or more than 2^40 evaluation
+ * points), then as gbsbin_moments; ERR_PRECISION when that estimate exceeds 1e-3 of |Pr(n)|
+ * (the value is still written: fewer than three significant digits are left).
  */
-int gbsbin_prob_distinguishable(const gbsbin_problem* p, const int* pattern, double* prob);
+int gbsbin_prob_distinguishable(const gbsbin_problem* p, const int* pattern, double* prob, double* abs_err);
 
 /*
  * The same Pr(n) with the sum over the prod (n_k + 1) evaluation points on the GPU: one thread
  * per point (its digits, the rank-2 blocks' eigenvalues, the power sums and the FP64 series),
- * fixed-order partial sums; host setup as above.  Synchronous on `stream`; device buffers are
- * allocated and freed per call.  Errors: as gbsbin_prob_distinguishable, ERR_UNSUPPORTED for N
- * or M above 64, ERR_NOMEM, ERR_CUDA.
+ * compensated per thread and per CTA, the CTAs' partials added in a fixed order on the host;
+ * host setup as above.  The points run in launches of at most ~2e10 estimated FP64 operations
+ * (about 20 ms each on this GPU), so no launch runs long on a shared device.  Synchronous on
+ * `stream`; device buffers are allocated and freed per call.  Errors: as
+ * gbsbin_prob_distinguishable, ERR_UNSUPPORTED for N or M above 64 or more than ~3e13
+ * estimated operations in all (about 30 s), ERR_NOMEM, ERR_CUDA.
  */
-int gbsbin_prob_distinguishable_device(const gbsbin_problem* p, const int* pattern, double* prob, void* stream);
+int gbsbin_prob_distinguishable_device(const gbsbin_problem* p, const int* pattern, double* prob, double* abs_err,
+                                       void* stream);
 
 /*
  * Fock inputs through a lossy linear circuit (App. C of the paper).  photons[j] >= 0

@@ -13,6 +13,9 @@ Pieces:
   unpivoted LU, and a direct, compensated inverse DFT; plain C, FP64, OpenMP over points.
 * :mod:`oracle.lhaf` - brute-force loop Hafnians, Fock probabilities and binned sums
   (Sec. II, Eq. gbs_probability_distribution; Sec. VI, Eq. coarse_grained_prob).
+* :func:`distinguishable_ones` - one photon per port for fully distinguishable sources (App. D's
+  limit), from the sources' closed-form output generating functions by a positive subset
+  dynamic programme (``gbs_oracle.c``).
 
 Every function here is pinned by ``-m "not gpu"`` tests (brute force, closed forms,
 invariants); none is "parity unpinned".
@@ -62,6 +65,8 @@ def _load():
         lib.oracle_logq_points.restype = ctypes.c_int
         lib.oracle_dft.argtypes = [ctypes.c_int, ip, dp, dp]
         lib.oracle_dft.restype = ctypes.c_int
+        lib.oracle_distinguishable_ones.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, dp]
+        lib.oracle_distinguishable_ones.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -161,6 +166,44 @@ def unfolded(prob, oversample: int = 4, nthreads: int = 0) -> np.ndarray:
     P = binned(prob, radix, nthreads)["P"]
     sl = tuple(slice(0, int(c) + 1) for c in prob.cutoff)
     return P[sl]
+
+
+def squeezed_pgf_taylor(r: float, y0: float, order: int) -> np.ndarray:
+    """Taylor coefficients a_j, j <= order, of a single-mode squeezed vacuum's photon-number
+    generating function g(y) = (1 - tanh^2(r) y^2)^(-1/2) / cosh r (Sec. II) about y = y0.
+    With u(x) = 1 - t^2 (y0 + x)^2 = u0 + u1 x + u2 x^2, the power w = u^(-1/2) follows from
+    J. C. P. Miller's recurrence n u0 w_n = sum_{k=1}^{min(n,2)} (k (p + 1) - n) u_k w_{n-k},
+    p = -1/2."""
+    t2 = np.tanh(r) ** 2
+    u = [1.0 - t2 * y0 * y0, -2.0 * t2 * y0, -t2]
+    p = -0.5
+    w = np.zeros(order + 1)
+    w[0] = u[0] ** p
+    for n in range(1, order + 1):
+        acc = 0.0
+        for k in (1, 2):
+            if k <= n:
+                acc += (k * (p + 1.0) - n) * u[k] * w[n - k]
+        w[n] = acc / (n * u[0])
+    return w / np.cosh(r)
+
+
+def distinguishable_ones(r, T) -> float:
+    """Probability of one photon on every output port for fully distinguishable sources
+    (App. D's limit: source s in its own internal mode), r[s] the squeezing of source s and
+    T (ports x sources) the lossy transfer matrix: the coefficient of z_1 ... z_M in
+    prod_s g_s(1 - P_s + sum_k |T_ks|^2 z_k), by the positive subset dynamic programme of
+    ``oracle_distinguishable_ones`` (``gbs_oracle.c``)."""
+    T = np.asarray(T)
+    M, S = T.shape
+    pk = np.ascontiguousarray(np.abs(T) ** 2, dtype=np.float64)
+    a = np.ascontiguousarray(np.stack([squeezed_pgf_taylor(float(r[s]), 1.0 - pk[:, s].sum(), M)
+                                       for s in range(S)]), dtype=np.float64)
+    out = ctypes.c_double()
+    rc = _load().oracle_distinguishable_ones(M, S, _dp(pk), _dp(a), ctypes.byref(out))
+    if rc != 0:
+        raise RuntimeError(f"oracle_distinguishable_ones failed: {rc}")
+    return out.value
 
 
 def logdet_series(XA, d, terms: int) -> complex:

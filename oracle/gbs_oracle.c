@@ -256,3 +256,64 @@ int oracle_dft(int L, const int *radix, const double *in_, double *out_) {
   free(b);
   return OR_OK;
 }
+
+/*
+ * Fully distinguishable sources (App. D, its limit of one source per internal mode): source
+ * s is a single-mode squeezed vacuum whose photons leave on output port k with probability
+ * p[k*S + s] = |T_ks|^2 and are lost otherwise, independently of the other sources.  Its
+ * output generating function is g_s(1 - P_s + sum_k p_ks z_k), P_s = sum_k p_ks, with
+ * g_s(y) = sum_j a[s*(M+1) + j] (y - (1 - P_s))^j given as Taylor coefficients, and the
+ * joint one is the product over sources.  The probability of one photon on every one of the
+ * M ports is the coefficient of z_1 ... z_M: each source covers a subset T of the ports, with
+ * coefficient a_{s,|T|} |T|! prod_{k in T} p_ks, so a dynamic programme over the subsets of
+ * covered ports (sources added one at a time, every subset of the uncovered ports tried)
+ * sums only positive terms.  O(S 3^M); M <= 24.
+ */
+int oracle_distinguishable_ones(int M, int S, const double *p, const double *a, double *out) {
+  if (M < 1 || M > 24 || S < 1) return OR_ERR_ARG;
+  const long full = 1L << M;
+  double *dp = (double *)calloc(full, sizeof(double));
+  double *nx = (double *)malloc(full * sizeof(double));
+  double *f = (double *)malloc(full * sizeof(double));
+  if (!dp || !nx || !f) {
+    free(dp);
+    free(nx);
+    free(f);
+    return OR_ERR_NOMEM;
+  }
+  dp[0] = 1.0;
+  double fact[25];
+  fact[0] = 1.0;
+  for (int j = 1; j <= 24; ++j) fact[j] = fact[j - 1] * j;
+  for (int s = 0; s < S; ++s) {
+    /* f(T) = a_{s,|T|} |T|! prod_{k in T} p_ks */
+    for (long T = 0; T < full; ++T) {
+      double prod = 1.0;
+      int size = 0;
+      for (int k = 0; k < M; ++k)
+        if (T >> k & 1) {
+          prod *= p[(long)k * S + s];
+          ++size;
+        }
+      f[T] = a[(long)s * (M + 1) + size] * fact[size] * prod;
+    }
+    /* nx(U) = sum over T subset of U of dp(U \ T) f(T) */
+#pragma omp parallel for schedule(dynamic, 64)
+    for (long U = 0; U < full; ++U) {
+      double acc = 0.0;
+      for (long T = U;; T = (T - 1) & U) {
+        acc += dp[U ^ T] * f[T];
+        if (T == 0) break;
+      }
+      nx[U] = acc;
+    }
+    double *t = dp;
+    dp = nx;
+    nx = t;
+  }
+  *out = dp[full - 1];
+  free(dp);
+  free(nx);
+  free(f);
+  return OR_OK;
+}

@@ -118,9 +118,9 @@ def load():
     lib.gbsbin_total_photon_series.restype = ctypes.c_int
     lib.gbsbin_cumulant_groups.argtypes = [ctypes.POINTER(gbsbin_problem), ctypes.c_uint, vp]
     lib.gbsbin_cumulant_groups.restype = ctypes.c_int
-    lib.gbsbin_prob_distinguishable.argtypes = [ctypes.POINTER(gbsbin_problem), _ip, vp]
+    lib.gbsbin_prob_distinguishable.argtypes = [ctypes.POINTER(gbsbin_problem), _ip, vp, vp]
     lib.gbsbin_prob_distinguishable.restype = ctypes.c_int
-    lib.gbsbin_prob_distinguishable_device.argtypes = [ctypes.POINTER(gbsbin_problem), _ip, vp, vp]
+    lib.gbsbin_prob_distinguishable_device.argtypes = [ctypes.POINTER(gbsbin_problem), _ip, vp, vp, vp]
     lib.gbsbin_prob_distinguishable_device.restype = ctypes.c_int
     lib.gbsbin_read_points.argtypes = [vp, vp, vp, vp]
     lib.gbsbin_table_from_logq_noalloc.argtypes = [ctypes.c_int, _ip, ctypes.c_int, vp, vp, vp]
@@ -398,26 +398,39 @@ def gbsbin_cumulant_groups(prob, groups):
     return out.value
 
 
-def gbsbin_prob_distinguishable(prob, pattern):
+GBSBIN_ERR_PRECISION = 10
+
+
+def _dist_result(status, where, out, err, with_error):
+    """Value (and error estimate) of an App. D call; a result that lost its digits to
+    cancellation raises GbsbinError(GBSBIN_ERR_PRECISION) carrying ``value`` and ``abs_err``."""
+    if status == GBSBIN_ERR_PRECISION:
+        e = GbsbinError(status, where)
+        e.value, e.abs_err = out.value, err.value
+        raise e
+    _check(status, where)
+    return (out.value, err.value) if with_error else out.value
+
+
+def gbsbin_prob_distinguishable(prob, pattern, with_error=False):
     """Fine-grained Pr(n) of an undisplaced state with fully distinguishable internal modes
-    (App. D; host FP64)."""
+    (App. D; host FP64).  with_error: also return the estimate of its absolute rounding error."""
     pat = np.ascontiguousarray(np.asarray(pattern, dtype=np.int32))
     args = ProblemArgs(prob)
-    out = ctypes.c_double()
-    _check(load().gbsbin_prob_distinguishable(ctypes.byref(args.c), pat.ctypes.data_as(_ip), ctypes.byref(out)),
-           "gbsbin_prob_distinguishable")
-    return out.value
+    out, err = ctypes.c_double(), ctypes.c_double()
+    st = load().gbsbin_prob_distinguishable(ctypes.byref(args.c), pat.ctypes.data_as(_ip), ctypes.byref(out),
+                                            ctypes.byref(err))
+    return _dist_result(st, "gbsbin_prob_distinguishable", out, err, with_error)
 
 
-def gbsbin_prob_distinguishable_device(prob, pattern, stream=None):
+def gbsbin_prob_distinguishable_device(prob, pattern, stream=None, with_error=False):
     """gbsbin_prob_distinguishable with the sum over the evaluation points on the GPU."""
     pat = np.ascontiguousarray(np.asarray(pattern, dtype=np.int32))
     args = ProblemArgs(prob)
-    out = ctypes.c_double()
-    _check(load().gbsbin_prob_distinguishable_device(ctypes.byref(args.c), pat.ctypes.data_as(_ip),
-                                                     ctypes.byref(out), _stream_handle(stream)),
-           "gbsbin_prob_distinguishable_device")
-    return out.value
+    out, err = ctypes.c_double(), ctypes.c_double()
+    st = load().gbsbin_prob_distinguishable_device(ctypes.byref(args.c), pat.ctypes.data_as(_ip), ctypes.byref(out),
+                                                   ctypes.byref(err), _stream_handle(stream))
+    return _dist_result(st, "gbsbin_prob_distinguishable_device", out, err, with_error)
 
 
 def gbsbin_alu_peak(precision, blocks, stream=None):

@@ -7,10 +7,15 @@
 // one thread per point (grid-stride): the digits of m, per rank-2 block l its trace
 // T = sum_k m_k d_lk and squared Frobenius norm F^2 = sum_kj m_k m_j S_lkj, the two eigenvalues
 // T/2 +- sqrt(2 F^2 - T^2)/2, the power sums and the series coefficient.  FP64 throughout (the
-// alternating sum cancels).  Each CTA reduces its threads' terms in a fixed order into its own
-// partial; the host adds the partials in order.
+// alternating sum cancels): each thread sums its terms with Neumaier compensation, each CTA
+// reduces its threads' (sum, error) pairs by TwoSum in a fixed order into its own partial, and
+// the host adds the partials in order, compensated; the terms' magnitudes are summed alongside
+// for the caller's error estimate.  The points run in launches of a bounded number of points
+// (a bounded amount of FP64 work each).
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <cmath>
 #include <vector>
 
 #include "gbsbin_internal.h"
@@ -22,20 +27,26 @@ constexpr int kThreads = 128;
 
 struct DistArgs {
   int M, K, N, nmax;
-  long long npts;          // prod (n_k + 1)
+  long long p0, p1;        // this launch's points [p0, p1) of prod (n_k + 1)
   const int* radix;        // M: n_k + 1
   const double* d;         // K x M
   const double* S;         // K x M x M
   const double* binom;     // M x (nmax + 1): C(n_k, m), m <= n_k
-  double* partial;         // gridDim.x
+  double* partial;         // 3 x gridDim.x: sum, its rounding error, sum of magnitudes
 };
+
+__device__ __forceinline__ void two_sum_d(double a, double b, double& s, double& e) {
+  s = __dadd_rn(a, b);
+  const double bb = __dsub_rn(s, a);
+  e = __dadd_rn(__dsub_rn(a, __dsub_rn(s, bb)), __dsub_rn(b, bb));
+}
 
 __global__ void __launch_bounds__(kThreads) k_distinguishable(DistArgs a) {
   double ps[kDistMaxN + 1], e[kDistMaxN + 1];
   int m[kDistMaxM];
-  double acc = 0.0;
+  double acc = 0.0, comp = 0.0, mag = 0.0;
   const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < a.npts; t += stride) {
+  for (long long t = a.p0 + blockIdx.x * (long long)blockDim.x + threadIdx.x; t < a.p1; t += stride) {
     long long rest = t;
     int msum = 0;
     double bin = 1.0;
@@ -74,22 +85,39 @@ __global__ void __launch_bounds__(kThreads) k_distinguishable(DistArgs a) {
       for (int j = 1; j <= q; ++j) s += 0.5 * ps[j] * e[q - j];
       e[q] = s / q;
     }
-    acc += (((a.N - msum) & 1) ? -1.0 : 1.0) * bin * e[a.N];
+    const double term = (((a.N - msum) & 1) ? -1.0 : 1.0) * bin * e[a.N];
+    double sn, er;
+    two_sum_d(acc, term, sn, er);
+    acc = sn;
+    comp += er;
+    mag += fabs(term);
   }
-  __shared__ double sh[kThreads];
+  __shared__ double sh[kThreads], se[kThreads], sm[kThreads];
   sh[threadIdx.x] = acc;
+  se[threadIdx.x] = comp;
+  sm[threadIdx.x] = mag;
   __syncthreads();
   for (int o = kThreads / 2; o > 0; o >>= 1) {
-    if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    if ((int)threadIdx.x < o) {
+      double sn, er;
+      two_sum_d(sh[threadIdx.x], sh[threadIdx.x + o], sn, er);
+      sh[threadIdx.x] = sn;
+      se[threadIdx.x] += se[threadIdx.x + o] + er;
+      sm[threadIdx.x] += sm[threadIdx.x + o];
+    }
     __syncthreads();
   }
-  if (threadIdx.x == 0) a.partial[blockIdx.x] = sh[0];
+  if (threadIdx.x == 0) {
+    a.partial[blockIdx.x] = sh[0];
+    a.partial[gridDim.x + blockIdx.x] = se[0];
+    a.partial[2 * gridDim.x + blockIdx.x] = sm[0];
+  }
 }
 
 }  // namespace
 
 int distinguishable_sum_device(int M, int K, int N, const int* pattern, const double* d, const double* S,
-                               double* total, cudaStream_t s) {
+                               double* total, double* abs_total, cudaStream_t s) {
   if (M > kDistMaxM || N > kDistMaxN) return GBSBIN_ERR_UNSUPPORTED;
   int nmax = 0;
   long long npts = 1;
@@ -100,6 +128,11 @@ int distinguishable_sum_device(int M, int K, int N, const int* pattern, const do
     npts *= radix[k];
     if (npts > (1ll << 40)) return GBSBIN_ERR_UNSUPPORTED;
   }
+  // FP64 operations per point: digits and binomials, per block the trace and the norm's double
+  // sum and the power sums, the series recurrence
+  const double per_point = 4.0 * M + (double)K * (2.0 * M * M + 2.0 * M + 4.0 * N + 20.0) + (double)N * N + 4.0 * N;
+  if (per_point * (double)npts > kDistMaxFlops) return GBSBIN_ERR_UNSUPPORTED;
+  const long long chunk = std::max<long long>(kThreads, (long long)(kDistChunkFlops / per_point));
   std::vector<double> binom((size_t)M * (nmax + 1), 0.0);
   for (int k = 0; k < M; ++k) {
     double c = 1.0;
@@ -113,8 +146,7 @@ int distinguishable_sum_device(int M, int K, int N, const int* pattern, const do
     cudaGetLastError();
     return GBSBIN_ERR_CUDA;
   }
-  long long blocks = (npts + kThreads - 1) / kThreads;
-  if (blocks > 8ll * sms) blocks = 8ll * sms;
+  const long long max_blocks = 8ll * sms;
   int* d_radix = nullptr;
   double *d_d = nullptr, *d_S = nullptr, *d_binom = nullptr, *d_part = nullptr;
   auto release = [&]() {
@@ -127,33 +159,47 @@ int distinguishable_sum_device(int M, int K, int N, const int* pattern, const do
   if (cudaMalloc(&d_radix, sizeof(int) * M) != cudaSuccess || cudaMalloc(&d_d, sizeof(double) * K * M) != cudaSuccess ||
       cudaMalloc(&d_S, sizeof(double) * (size_t)K * M * M) != cudaSuccess ||
       cudaMalloc(&d_binom, sizeof(double) * binom.size()) != cudaSuccess ||
-      cudaMalloc(&d_part, sizeof(double) * blocks) != cudaSuccess) {
+      cudaMalloc(&d_part, sizeof(double) * 3 * max_blocks) != cudaSuccess) {
     cudaGetLastError();
     release();
     return GBSBIN_ERR_NOMEM;
   }
-  std::vector<double> part((size_t)blocks);
+  std::vector<double> part((size_t)(3 * max_blocks));
   cudaError_t err = cudaMemcpyAsync(d_radix, radix.data(), sizeof(int) * M, cudaMemcpyHostToDevice, s);
   if (err == cudaSuccess) err = cudaMemcpyAsync(d_d, d, sizeof(double) * K * M, cudaMemcpyHostToDevice, s);
   if (err == cudaSuccess) err = cudaMemcpyAsync(d_S, S, sizeof(double) * (size_t)K * M * M, cudaMemcpyHostToDevice, s);
   if (err == cudaSuccess)
     err = cudaMemcpyAsync(d_binom, binom.data(), sizeof(double) * binom.size(), cudaMemcpyHostToDevice, s);
-  if (err == cudaSuccess) {
-    DistArgs a{M, K, N, nmax, npts, d_radix, d_d, d_S, d_binom, d_part};
+  double sum = 0.0, comp = 0.0, mag = 0.0;           // the partials, Neumaier-compensated, in order
+  auto add = [&](double v) {
+    const double t = sum + v;
+    comp += std::fabs(sum) >= std::fabs(v) ? (sum - t) + v : (v - t) + sum;
+    sum = t;
+  };
+  for (long long p0 = 0; err == cudaSuccess && p0 < npts; p0 += chunk) {
+    const long long p1 = std::min(npts, p0 + chunk);
+    long long blocks = (p1 - p0 + kThreads - 1) / kThreads;
+    if (blocks > max_blocks) blocks = max_blocks;
+    DistArgs a{M, K, N, nmax, p0, p1, d_radix, d_d, d_S, d_binom, d_part};
     k_distinguishable<<<(unsigned)blocks, kThreads, 0, s>>>(a);
     err = cudaGetLastError();
+    if (err == cudaSuccess)
+      err = cudaMemcpyAsync(part.data(), d_part, sizeof(double) * 3 * blocks, cudaMemcpyDeviceToHost, s);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+    if (err == cudaSuccess)
+      for (long long b = 0; b < blocks; ++b) {       // fixed order
+        add(part[b]);
+        comp += part[blocks + b];
+        mag += part[2 * blocks + b];
+      }
   }
-  if (err == cudaSuccess)
-    err = cudaMemcpyAsync(part.data(), d_part, sizeof(double) * blocks, cudaMemcpyDeviceToHost, s);
-  if (err == cudaSuccess) err = cudaStreamSynchronize(s);
   release();
   if (err != cudaSuccess) {
     cudaGetLastError();
     return GBSBIN_ERR_CUDA;
   }
-  double sum = 0.0;
-  for (double v : part) sum += v;                    // fixed order
-  *total = sum;
+  *total = sum + comp;
+  *abs_total = mag;
   return GBSBIN_OK;
 }
 

@@ -952,6 +952,7 @@ const char* gbsbin_strerror(int status) {
     case GBSBIN_ERR_NUMERIC: return "non-positive or non-finite pivot at some grid point";
     case GBSBIN_ERR_UNSUPPORTED: return "size not supported by this build";
     case GBSBIN_ERR_TIMEOUT: return "bounded device wait timed out";
+    case GBSBIN_ERR_PRECISION: return "result lost its significant digits to cancellation (value still written)";
   }
   return "unknown status";
 }
@@ -2077,7 +2078,20 @@ int gbsbin_cumulant_groups(const gbsbin_problem* p, unsigned mask, double* kappa
 // f_N(m) = [eta^N] exp(sum_j p_j(m) eta^j / (2j)), p_j(m) = tr((D(m) XA)^j) = sum_l
 // (lambda1^j + lambda2^j), the two eigenvalues of sqrt(D) B_l sqrt(D) from its trace T and
 // Frobenius norm F (lambda = T/2 +- sqrt(2 F^2 - T^2)/2), D(m) = diag(m) (+) diag(m).
-static int dist_eval(const gbsbin_problem* p, const int* pattern, double* prob, bool device, void* stream) {
+// The App. D sum's result: Pr(n) = Pr(0) / n! x sum, an estimate of its absolute rounding
+// error from the sum of the terms' magnitudes (each term carries ~N + 16 roundings of its own
+// size: the power sums, the series recurrence, the binomial weight), and the status: the
+// value has fewer than three significant digits left when that estimate exceeds 1e-3 of it.
+static int dist_finish(double pr0, double fact, double sum, double abs_sum, int N, double* prob, double* abs_err) {
+  const double scale = pr0 / fact;
+  const double err = (double)(N + 16) * 2.220446049250313e-16 * abs_sum * scale;
+  *prob = scale * sum;
+  if (abs_err) *abs_err = err;
+  return err > 1e-3 * std::fabs(*prob) ? GBSBIN_ERR_PRECISION : GBSBIN_OK;
+}
+
+static int dist_eval(const gbsbin_problem* p, const int* pattern, double* prob, double* abs_err, bool device,
+                     void* stream) {
   if (!p || !pattern || !prob) return GBSBIN_ERR_ARG;
   gbsbin_options o;
   gbsbin_default_options(&o);
@@ -2169,11 +2183,10 @@ static int dist_eval(const gbsbin_problem* p, const int* pattern, double* prob, 
   for (int k = 0; k < M; ++k)
     for (int q = 2; q <= pattern[k]; ++q) fact *= (double)q;
   if (device) {                                      // one thread per point on the GPU
-    double sum = 0.0;
-    st = distinguishable_sum_device(M, K, N, pattern, d.data(), S.data(), &sum, (cudaStream_t)stream);
+    double sum = 0.0, abs_sum = 0.0;
+    st = distinguishable_sum_device(M, K, N, pattern, d.data(), S.data(), &sum, &abs_sum, (cudaStream_t)stream);
     if (st) return st;
-    *prob = pr0 * sum / fact;
-    return GBSBIN_OK;
+    return dist_finish(pr0, fact, sum, abs_sum, N, prob, abs_err);
   }
   std::vector<int> m(M, 0), dir(M, 1);
   std::vector<double> Tl(K, 0.0), F2l(K, 0.0), ps((size_t)N + 1), e((size_t)N + 1);
@@ -2190,7 +2203,7 @@ static int dist_eval(const gbsbin_problem* p, const int* pattern, double* prob, 
   };
   double binom = 1.0;                                // prod C(n_k, m_k), m = 0
   int msum = 0;
-  double total = 0.0;
+  double total = 0.0, comp = 0.0, abs_sum = 0.0;     // Neumaier-compensated signed sum
   long long count = 0;
   while (true) {
     if ((count & 1023) == 0) recompute();
@@ -2211,7 +2224,11 @@ static int dist_eval(const gbsbin_problem* p, const int* pattern, double* prob, 
       for (int jj = 1; jj <= q; ++jj) acc += 0.5 * ps[jj] * e[q - jj];   // j a_j = ps_j / 2
       e[q] = acc / (double)q;
     }
-    total += (((N - msum) & 1) ? -1.0 : 1.0) * binom * e[N];
+    const double term = (((N - msum) & 1) ? -1.0 : 1.0) * binom * e[N];
+    const double t = total + term;
+    comp += std::fabs(total) >= std::fabs(term) ? (total - t) + term : (term - t) + total;
+    total = t;
+    abs_sum += std::fabs(term);
     ++count;
     int k = 0;                                       // next point: the lowest digit that can move
     while (k < M && (m[k] + dir[k] < 0 || m[k] + dir[k] > pattern[k])) {
@@ -2232,16 +2249,16 @@ static int dist_eval(const gbsbin_problem* p, const int* pattern, double* prob, 
     m[k] += sgn;
     msum += sgn;
   }
-  *prob = pr0 * total / fact;
-  return GBSBIN_OK;
+  return dist_finish(pr0, fact, total + comp, abs_sum, N, prob, abs_err);
 }
 
-int gbsbin_prob_distinguishable(const gbsbin_problem* p, const int* pattern, double* prob) {
-  return dist_eval(p, pattern, prob, false, nullptr);
+int gbsbin_prob_distinguishable(const gbsbin_problem* p, const int* pattern, double* prob, double* abs_err) {
+  return dist_eval(p, pattern, prob, abs_err, false, nullptr);
 }
 
-int gbsbin_prob_distinguishable_device(const gbsbin_problem* p, const int* pattern, double* prob, void* stream) {
-  return dist_eval(p, pattern, prob, true, stream);
+int gbsbin_prob_distinguishable_device(const gbsbin_problem* p, const int* pattern, double* prob, double* abs_err,
+                                       void* stream) {
+  return dist_eval(p, pattern, prob, abs_err, true, stream);
 }
 
 int gbsbin_alu_peak(int precision, int blocks, double* tflops, void* stream) {

@@ -277,12 +277,16 @@ int dft_two_phase(const GridDesc& g);
 
 // App. D's sum over the evaluation points m <= pattern on the device (gbsbin_distinguishable.cu):
 // d (K x M) and S (K x M x M) the rank-2 blocks' trace and Frobenius-norm coefficients; the
-// signed, binomial-weighted sum of f_N(m) to *total.  Synchronous on s; N <= kDistMaxN and
-// M <= kDistMaxM (else GBSBIN_ERR_UNSUPPORTED).
+// signed, binomial-weighted sum of f_N(m) to *total (compensated) and the sum of the terms'
+// magnitudes to *abs_total.  Launches of at most kDistChunkFlops estimated FP64 work each,
+// synchronous on s; N <= kDistMaxN, M <= kDistMaxM and the whole sum at most kDistMaxFlops
+// (else GBSBIN_ERR_UNSUPPORTED).
 constexpr int kDistMaxN = 64;
 constexpr int kDistMaxM = 64;
+constexpr double kDistChunkFlops = 2e10;   // ~20 ms of FP64 work per launch on this GPU
+constexpr double kDistMaxFlops = 3e13;     // ~30 s
 int distinguishable_sum_device(int M, int K, int N, const int* pattern, const double* d, const double* S,
-                               double* total, cudaStream_t s);
+                               double* total, double* abs_total, cudaStream_t s);
 cudaError_t launch_backward(const BackwardArgs& b, const double* dLdP, cudaStream_t s);
 cudaError_t launch_alu_peak(int fp64, int blocks, float* out_sink, int iters, cudaStream_t s);
 

@@ -55,13 +55,44 @@ def test_against_the_oracle_fine_grained_table(gb, seed):
 
 def test_gray_order_beyond_the_recompute_period(gb):
     # 6^4 = 1296 evaluation points: the incremental trace / norm updates run past the
-    # recompute after 1024 points; absolute agreement (the alternating sum of a 20-photon
-    # pattern cancels, and the 24-bin table folds at the 1e-12 level at this squeezing)
+    # recompute after 1024 points.  Each value lies within its own rounding-error estimate of
+    # an unfolded oracle table (40 bins per detector), and a 20-photon pattern whose
+    # alternating sum keeps fewer than three digits reports GBSBIN_ERR_PRECISION
     rng = np.random.default_rng(1600)
     prob = _distinguishable(rng, 4, 5, r=(0.6, 0.9))
-    table = oracle.binned(prob, radix=np.full(4, 24))["P"]
-    for n in [(5, 5, 5, 5), (5, 4, 3, 5), (2, 5, 5, 1)]:
-        assert abs(gb.gbsbin_prob_distinguishable(prob, list(n)) - table[n]) < 1e-10
+    table = oracle.binned(prob, radix=np.full(4, 40))["P"]
+    for n in [(5, 4, 3, 5), (2, 5, 5, 1), (2, 2, 2, 2)]:
+        v, err = gb.gbsbin_prob_distinguishable(prob, list(n), with_error=True)
+        assert err < 1e-3 * v and abs(v - table[n]) <= err + 1e-15, (n, v, err, table[n])
+    with pytest.raises(gb.GbsbinError) as e:
+        gb.gbsbin_prob_distinguishable(prob, [5, 5, 5, 5])
+    assert e.value.status == 10 and abs(e.value.value - table[5, 5, 5, 5]) <= e.value.abs_err
+
+
+def test_cancelled_sum_is_flagged(gb):
+    # 5^8 evaluation points, 32 photons: the alternating sum loses every digit (its rounded
+    # value is even negative); the call says so instead of returning a probability
+    big = _distinguishable(np.random.default_rng(1700), 8, 4, r=(0.2, 0.4))
+    with pytest.raises(gb.GbsbinError) as e:
+        gb.gbsbin_prob_distinguishable(big, [4] * 8)
+    assert e.value.status == 10 and abs(e.value.value) <= e.value.abs_err
+
+
+def _m16_all_ones():
+    rng = np.random.default_rng(1700)
+    M = 16
+    r = rng.uniform(0.5, 0.9, M)
+    T = np.sqrt(rng.uniform(0.4, 0.9, M))[:, None] * synth.haar_unitary(M, rng)
+    return synth.Problem(M, M, np.diag(r), T, np.arange(M, dtype=np.int32), np.full(M, 1, np.int32)), r, T
+
+
+def test_ones_pattern_against_the_independent_sum(gb):
+    # 16 sources, one photon per detector (2^16 evaluation points): App. D's alternating sum
+    # against the positive subset sum of the sources' closed-form output distributions
+    prob, r, T = _m16_all_ones()
+    ref = oracle.distinguishable_ones(r, T)
+    v, err = gb.gbsbin_prob_distinguishable(prob, [1] * 16, with_error=True)
+    assert abs(v - ref) <= err and err < 1e-4 * ref, (v, ref, err)
 
 
 def test_rejects_other_structures(gb):

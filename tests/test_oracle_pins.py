@@ -354,3 +354,31 @@ def test_logq_points_matches_grid(radix):
         sq = np.exp(gamma @ np.linalg.solve(K, w * Xg)) / np.linalg.det(K)
         got = np.exp(2 * lq[np.where(flat == idx)[0][0]])
         assert abs(got - sq) <= 1e-12 * abs(sq), (radix, k, got, sq)
+
+
+# ------------------------------------- fully distinguishable sources, one photon per port
+def test_squeezed_pgf_taylor_matches_series():
+    # Taylor coefficients of the single-mode squeezed vacuum's generating function about y0
+    # against the direct sum_n P(n) C(n, j) y0^(n - j) with P(2k) = tanh^2k(r) (2k)! /
+    # (4^k k!^2 cosh r)
+    for r, y0 in ((0.7, 0.35), (0.3, 0.0), (1.1, 0.8)):
+        t = math.tanh(r)
+        P = np.zeros(400)
+        for k in range(200):
+            P[2 * k] = math.exp(2 * k * math.log(t) + math.lgamma(2 * k + 1) - k * math.log(4.0)
+                                - 2 * math.lgamma(k + 1)) / math.cosh(r)
+        a = oracle.squeezed_pgf_taylor(r, y0, 8)
+        ref = [sum(P[n] * math.comb(n, j) * y0 ** (n - j) for n in range(j, 400)) for j in range(9)]
+        assert np.abs(a - ref).max() < 1e-13
+
+
+@pytest.mark.parametrize("M", [1, 2, 3, 4])
+def test_distinguishable_ones_matches_the_generic_oracle(M):
+    # sources each in their own internal mode through a lossy interferometer: the positive
+    # subset sum against the generic oracle's unfolded table (one group per detector)
+    rng = np.random.default_rng(40 + M)
+    r = rng.uniform(0.3, 0.8, M)
+    T = np.sqrt(rng.uniform(0.4, 0.9, M))[:, None] * synth.haar_unitary(M, rng)
+    prob = synth.Problem(M, M, np.diag(r), T, np.arange(M, dtype=np.int32), np.full(M, 1, np.int32))
+    table = oracle.binned(prob, radix=np.full(M, 48 if M <= 3 else 28))["P"]
+    assert abs(oracle.distinguishable_ones(r, T) - table[(1,) * M]) < 1e-12 * max(1.0, M)
