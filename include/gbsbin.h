@@ -85,7 +85,9 @@ typedef struct {
                              w = 1, for the normalisation) and returns the PARTIAL table of
                              their terms; the tables of shards that partition [0, n_evaluated)
                              sum to the whole table (the DFT is linear).  0, 0 = whole grid.
-                             Not for batches or gbsbin_backward (ERR_UNSUPPORTED).          */
+                             gbsbin_backward on a shard's plan gives the gradient of its
+                             partial table: the shards' gradients sum to the whole gradient.
+                             Not for batches (ERR_UNSUPPORTED).                             */
 } gbsbin_options;
 
 /*

@@ -1,5 +1,7 @@
 // Reverse mode through the binned distribution: dL/dP(b) -> dL/dXA, dL/dgamma
-// (the host then chains to Sigma^(1), z-bar and the physical parameters).
+// (the host then chains to Sigma^(1), z-bar and the physical parameters).  A shard's plan
+// (a slice of the evaluated half grid) gives the gradient of its partial table: the slices'
+// gradients sum to the whole one.
 //
 // Forward (per evaluated point k, arXiv:2412.17742 Sec. III Eq. q_d with the grouping of
 // Sec. VI):  M_k = conj(D_k) - XA,  x_k = M_k^{-1} X gamma,
@@ -56,7 +58,9 @@ __global__ void k_real_to_complex(const double* __restrict__ in, long long n, do
     out[t] = make_double2(in[t], 0.0);
 }
 
-// a_k = c_k gbar_k G_k / N (gbar still unscaled), per evaluated point
+// a_k = c_k gbar_k G_k / N (gbar still unscaled, over the whole half grid), per evaluated
+// point of this plan; a shard's point 0 outside its slice only normalises (a = 0 there, so
+// beta_0 = -sum of the slice's a_k)
 __global__ void k_adj_weights(const double2* __restrict__ gbar, const double2* __restrict__ logq, GridDesc g,
                               double2* __restrict__ a) {
   const double2 l0 = logq[0];
@@ -64,14 +68,19 @@ __global__ void k_adj_weights(const double2* __restrict__ gbar, const double2* _
   const int R = g.radix[g.L - 1];
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < g.n_eval;
        e += (long long)gridDim.x * blockDim.x) {
-    const int klast = (int)(e % g.half);
+    if (e == 0 && g.e_lo > 0) {
+      a[e] = make_double2(0.0, 0.0);
+      continue;
+    }
+    const long long t = global_point(e, g);
+    const int klast = (int)(t % g.half);
     const double c = (klast == 0 || 2 * klast == R) ? 1.0 : 2.0;
     double2 v = logq[e];
     double m = exp(v.x - l0.x);
     double s, co;
     sincos(v.y - l0.y, &s, &co);
     double2 G = make_double2(m * co, m * s);
-    double2 gb = gbar[e];
+    double2 gb = gbar[t];
     a[e] = make_double2(c * scale * (gb.x * G.x - gb.y * G.y), c * scale * (gb.x * G.y + gb.y * G.x));
   }
 }

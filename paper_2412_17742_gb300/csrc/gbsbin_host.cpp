@@ -51,6 +51,8 @@ struct gbsbin_plan {
   BTreeArgs btree{};
   std::vector<BTreeStep> btree_steps;
   size_t bt_scratch[3] = {0, 0, 0};   // 16-byte slots: each trailing-block buffer, pivot rows, reciprocals
+  cd logq1 = 0.0;                     // sharded large-matrix tree plans: log q(1) of the state (host FP64)
+  double logq1_minpiv = 1.0;          // and the smallest real part of its pivots
   int last_launches = 0;              // kernel launches of the last execute
   long long upload_bytes = 0;         // host-to-device bytes of one state upload
   int* d_label = nullptr;
@@ -445,6 +447,36 @@ int upload_state(gbsbin_plan* P, cudaStream_t stream) {
     split(P->Xgamma[i], &Xghi[i], &Xglo[i]);
     split(P->gamma[i], &ghi[i], &glo[i]);
   }
+  if (is_btree(P->kernel) && P->grid.e_lo > 0) {   // a shard without point 0: log q(1) on the host
+    // K = I - XA, unpivoted LU (every pivot has Re > 0), x = K^-1 X gamma,
+    // log q(1) = 1/2 gamma^T x - 1/2 sum Log u_ii  (Sec. III, Eq. q_d at w = 1)
+    std::vector<cd> K((size_t)n * n);
+    std::vector<cd> x(P->Xgamma);
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) K[(size_t)i * n + j] = (i == j ? 1.0 : 0.0) - P->XA[(size_t)i * n + j];
+    cd ld = 0.0;
+    double mn = 1e300;
+    for (int k = 0; k < n; ++k) {
+      const cd piv = K[(size_t)k * n + k];
+      ld += std::log(piv);
+      mn = std::min(mn, piv.real());
+      for (int i = k + 1; i < n; ++i) {
+        const cd l = K[(size_t)i * n + k] / piv;
+        if (l == cd(0.0)) continue;
+        for (int j = k + 1; j < n; ++j) K[(size_t)i * n + j] -= l * K[(size_t)k * n + j];
+        x[i] -= l * x[k];
+      }
+    }
+    for (int i = n - 1; i >= 0; --i) {
+      cd s = x[i];
+      for (int j = i + 1; j < n; ++j) s -= K[(size_t)i * n + j] * x[j];
+      x[i] = s / K[(size_t)i * n + i];
+    }
+    cd gx = 0.0;
+    for (int i = 0; i < n; ++i) gx += P->gamma[i] * x[i];
+    P->logq1 = 0.5 * gx - 0.5 * ld;
+    P->logq1_minpiv = mn;
+  }
   if (is_btree(P->kernel)) {                       // depth 0: the permuted augmented matrix
     float4* A0 = (float4*)(h + s.off_tree);
     const std::vector<int>& pm = P->tree_perm;
@@ -764,10 +796,20 @@ double btree_macs(const gbsbin_plan* P) {
 size_t btree_configure(gbsbin_plan* P, int halve_first, const int* nb, const int* m) {
   const int L = P->L;
   BTreeArgs& t = P->btree;
+  const GridDesc& g = P->grid;
   t.halve_first = halve_first;
-  for (int l = 0; l < L; ++l) t.cnt[l] = P->grid.radix[l];
-  if (halve_first) t.cnt[0] = P->grid.radix[0] / 2 + 1;
-  else t.cnt[L - 1] = P->grid.half;
+  for (int l = 0; l < L; ++l) t.cnt[l] = g.radix[l];
+  t.k0_lo = 0;
+  if (halve_first) {
+    t.cnt[0] = g.radix[0] / 2 + 1;
+  } else {
+    t.cnt[L - 1] = g.half;
+    if (g.e_lo != 0 || g.e_hi != g.n_full) {        // a shard: the level-0 roots covering its slice
+      const long long per_k0 = g.n_full / g.radix[0];
+      t.k0_lo = (int)(g.e_lo / per_k0);
+      t.cnt[0] = (int)((g.e_hi + per_k0 - 1) / per_k0) - t.k0_lo;
+    }
+  }
   t.n_leaves = 1;
   for (int l = 0; l < L; ++l) t.n_leaves *= t.cnt[l];
   P->btree_steps.clear();
@@ -833,7 +875,8 @@ size_t btree_layout(gbsbin_plan* P) {
   if (t.mL > GBSBIN_BT_MAX_HESS || t.mL < 1) return 0;
   int best = -1;
   double best_macs = 0.0;
-  for (int h = 0; h < 2; ++h) {
+  const bool shard = P->grid.e_lo != 0 || P->grid.e_hi != P->grid.n_full;
+  for (int h = 0; h < (shard ? 1 : 2); ++h) {       // a shard keeps the last axis halved
     if (!btree_configure(P, h, nb, m)) continue;
     const double w = btree_macs(P);
     if (best < 0 || w < best_macs) {
@@ -1008,10 +1051,6 @@ static int plan_create_impl(const gbsbin_problem* p, const gbsbin_options* o, gb
       delete P;
       return GBSBIN_ERR_ARG;
     }
-    if (opt.want_backward) {
-      delete P;
-      return GBSBIN_ERR_UNSUPPORTED;
-    }
     g.e_lo = opt.shard_begin;
     g.e_hi = opt.shard_end;
     g.n_eval = (g.e_hi - g.e_lo) + (g.e_lo > 0 ? 1 : 0);
@@ -1043,7 +1082,7 @@ static int plan_create_impl(const gbsbin_problem* p, const gbsbin_options* o, gb
   // the large-matrix tree: asked for, or by default for standalone plans of n > 64 where it
   // needs under half the work of one LU per evaluated point
   if (is_btree(P->kernel) || (!is_tree(P->kernel) && alloc_gws && !opt.tile_override && p->L >= 2 && n > 64)) {
-    tree_bytes = (!sharded && !opt.want_backward) ? btree_layout(P) : 0;
+    tree_bytes = !opt.want_backward ? btree_layout(P) : 0;
     bool take = tree_bytes > 0;
     if (take && !is_btree(P->kernel))
       take = btree_macs(P) < 0.5 * (double)g.n_eval * (double)n * (double)n * (double)n / 3.0;
@@ -1172,7 +1211,7 @@ static int plan_create_impl(const gbsbin_problem* p, const gbsbin_options* o, gb
   }
   P->h_stage_bytes = sl.total;
   if (opt.want_backward) {
-    const size_t ne = (size_t)g.n_eval, adj = (size_t)std::max<long long>(P->table_size, g.n_eval);
+    const size_t ne = (size_t)g.n_eval, adj = (size_t)std::max<long long>(P->table_size, g.n_full);
     const size_t parts = (size_t)P->num_sms;
     P->bws_slot_bytes = ((long long)points_matrix_bytes(GBSBIN_KERNEL_GMEM_FP64, n, 1) + 255) / 256 * 256;
     if ((st = dalloc(&P->d_lu, ne * nn)) || (st = dalloc(&P->d_xs, ne * n)) || (st = dalloc(&P->d_adjA, adj)) ||
@@ -1351,6 +1390,9 @@ int gbsbin_execute(gbsbin_plan* P, double* P_out, void* stream) {
     t.grid = P->grid;
     t.ldfin = P->d_ldfin;
     t.minpiv = P->d_minpiv;
+    t.q1re = P->logq1.real();
+    t.q1im = P->logq1.imag();
+    t.q1minpiv = P->logq1_minpiv;
     int nl = 0;
     if (launch_points_btree(t, P->btree_steps.data(), (int)P->btree_steps.size(),
                             P->kernel == GBSBIN_KERNEL_BTREE_FP64, P->num_sms, s, &nl) != cudaSuccess)

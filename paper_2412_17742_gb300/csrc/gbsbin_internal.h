@@ -190,6 +190,12 @@ struct BTreeArgs {
                             // the half grid is written exactly once
   int halve_first;
   long long n_leaves;       // leaves: prod cnt[l]
+  // a shard (last axis halved): level 0 takes the roots k0_lo .. k0_lo + cnt[0] - 1, and the
+  // leaves write only the evaluated points of the grid's slice [e_lo, e_hi) (grid), at their
+  // local index; with e_lo > 0 the first leaf also writes point 0's record from log q(1),
+  // computed on the host
+  int k0_lo;
+  double q1re, q1im, q1minpiv;
   GridDesc grid;
   const double2* tw;
   const float4* twdf;

@@ -72,9 +72,10 @@ __device__ __forceinline__ const typename Ar::E* elem(const float4* p) {
   return reinterpret_cast<const typename Ar::E*>(p);
 }
 
-// w = exp(2 pi i k / R_l)
+// w = exp(2 pi i k / R_l) (k counted from k0_lo on axis 0 of a shard)
 template <class Ar>
 __device__ __forceinline__ typename Ar::E bt_root(const BTreeArgs& a, int l, int k) {
+  if (l == 0) k += a.k0_lo;
   if constexpr (std::is_same<Ar, ArDF>::value) {
     int off = 0;
     for (int q = 0; q < l; ++q) off += a.grid.radix[q];
@@ -566,7 +567,18 @@ __global__ void __launch_bounds__(LEAF_WARPS * 32, 4) k_bt_leaf(BTreeArgs a) {
   const double2 P = Ar::to(prod), X = Ar::to(ex);
   const double r3 = -0.5 * (double)e2 * LN2 + 0.5 * X.x, r4 = 0.5 * X.y;
   if (!a.halve_first) {
-    write_record(a, leaf, P, (double)args, r3, r4, (double)mn, false);
+    const GridDesc& g = a.grid;
+    if (g.e_lo == 0 && g.e_hi == g.n_full) {
+      write_record(a, leaf, P, (double)args, r3, r4, (double)mn, false);
+    } else {                                         // a shard: its slice only, local indices
+      long long inner = 1;                           // evaluated points per level-0 root
+      for (int q = 1; q + 1 < g.L; ++q) inner *= g.radix[q];
+      const long long e = leaf + (long long)a.k0_lo * inner * g.half;
+      if (e >= g.e_lo && e < g.e_hi)
+        write_record(a, e - g.e_lo + (g.e_lo > 0 ? 1 : 0), P, (double)args, r3, r4, (double)mn, false);
+      if (leaf == 0 && g.e_lo > 0)                   // point 0 (w = 1), for the normalisation
+        write_record(a, 0, make_double2(1.0, 0.0), 0.0, a.q1re, a.q1im, a.q1minpiv, false);
+    }
     return;
   }
   // the leaf's digits (cnt radices) -> its evaluated point and, where it is the source, the

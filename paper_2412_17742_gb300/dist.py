@@ -12,7 +12,14 @@ Two ways to share the work, both without a collective on the point path:
   (``sharded_table``).
 
 Slices of the half grid keep every conjugate pair G(w^-k) = conj G(w^k) on one rank: the
-half grid holds one representative of each pair.
+half grid holds one representative of each pair.  Where the large-matrix tree of block
+eliminations serves the plan, a shard runs the subtrees of the first axis's roots that cover
+its slice.
+
+Gradients (``ShardedPlan.backward``): each rank's plan gives the gradient of its partial
+table; the partial tables sum to the table, so the gradients sum to the gradient - one
+all-reduce of each requested gradient array (the chain from the n x n adjoint to the
+physical parameters is linear and the same on every rank).
 """
 from __future__ import annotations
 
@@ -56,6 +63,64 @@ def sharded_table(prob, precision: int = 0, oversample: int = 1, group=None, str
         with Plan(prob, precision=precision, oversample=oversample, shard=(begin, end)) as p:
             table = p.table(stream)
     return allreduce_table(table, group)
+
+
+def allreduce_grads(grads, group=None):
+    """Sum the ranks' partial gradients (a dict of numpy arrays, as Plan.backward returns) in
+    place: one all-reduce per array (complex arrays as their real and imaginary parts)."""
+    import torch
+    import torch.distributed as dist
+    for key in sorted(grads):
+        a = np.ascontiguousarray(grads[key])
+        t = torch.from_numpy(a.view(np.float64) if np.iscomplexobj(a) else a.astype(np.float64)).clone()
+        dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
+        v = t.numpy()
+        grads[key] = v.view(np.complex128).reshape(a.shape) if np.iscomplexobj(a) else v.reshape(a.shape)
+    return grads
+
+
+class ShardedPlan:
+    """One problem's grid shared by the ranks of ``group``: this rank's plan evaluates its
+    slice of the evaluated half grid on its current CUDA device.  ``table()`` returns the whole
+    table (partial tables all-reduced); ``backward(dL_dP, want)`` the whole gradient (partial
+    gradients all-reduced) for the state of the last ``table()``."""
+
+    def __init__(self, prob, precision: int = 0, oversample: int = 1, want_backward: bool = False, group=None):
+        import torch.distributed as dist
+
+        from . import Plan
+        self.group = group
+        rank, world = dist.get_rank(group), dist.get_world_size(group)
+        self.shape = tuple(int(c) + 1 for c in prob.cutoff)
+        self.begin, self.end = shard_range(evaluated_points(prob.cutoff, oversample), rank, world)
+        self.plan = None
+        if self.end > self.begin:
+            self.plan = Plan(prob, precision=precision, oversample=oversample, want_backward=want_backward,
+                             shard=(self.begin, self.end))
+
+    def table(self, stream=None):
+        import torch
+        if self.plan is None:              # more ranks than points: contribute zeros
+            t = torch.zeros(self.shape, dtype=torch.float64, device="cuda")
+        else:
+            t = self.plan.table(stream)
+        return allreduce_table(t, self.group)
+
+    def backward(self, dL_dP, want=("r", "T", "alpha", "V"), stream=None):
+        if self.plan is None:
+            raise RuntimeError("a rank without points has no gradient to contribute")
+        return allreduce_grads(self.plan.backward(dL_dP, stream, want), self.group)
+
+    def close(self):
+        if self.plan is not None:
+            self.plan.close()
+            self.plan = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 def fock_node_count(photons) -> int:

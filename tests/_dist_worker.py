@@ -2,7 +2,9 @@
 
 Each rank builds the partial table of its shard of the evaluated half grid on the CPU from
 the oracle's per-point log q (standing in for the device's partial table), the ranks sum
-them with paper_2412_17742_gb300.dist.allreduce_table, and rank 0 saves the result.
+them with paper_2412_17742_gb300.dist.allreduce_table, and rank 0 saves the result; in the
+"fock" mode the same over Fock-input node ranges, in the "grad" mode the partial gradients of
+a linear loss summed with paper_2412_17742_gb300.dist.allreduce_grads.
 """
 import os
 import sys
@@ -21,11 +23,40 @@ from paper_2412_17742_gb300 import dist as gdist  # noqa: E402
 from shard_tables import partial_table_cpu  # noqa: E402
 
 
+def partial_loss_gradient(prob, pbar, begin, end, h=1e-6):
+    """d/dr of sum_b pbar(b) P_[begin, end)(b) by central differences of the oracle."""
+    g = np.zeros(prob.r.shape)
+    for idx in np.ndindex(*prob.r.shape):
+        vals = []
+        for sgn in (1.0, -1.0):
+            q = synth.Problem(prob.M, prob.K, prob.r.copy(), prob.T.copy(), prob.bin_of_mode, prob.cutoff)
+            q.r[idx] += sgn * h
+            vals.append(float((partial_table_cpu(q, oracle.binned(q)["logq"], begin, end) * pbar).sum()))
+        g[idx] = (vals[0] - vals[1]) / (2 * h)
+    return g
+
+
 def main():
     rank, world = int(os.environ["RANK"]), int(os.environ["WORLD_SIZE"])
     out = sys.argv[1]
     fock_mode = len(sys.argv) > 2 and sys.argv[2] == "fock"
+    grad_mode = len(sys.argv) > 2 and sys.argv[2] == "grad"
     dist.init_process_group("gloo", init_method="env://", rank=rank, world_size=world)
+    if grad_mode:
+        # gradients: each rank's partial gradient (central differences of the oracle's partial
+        # table of its shard, standing in for a sharded plan's reverse pass), summed by
+        # paper_2412_17742_gb300.dist.allreduce_grads
+        prob = synth.config(0)
+        n_eval = gdist.evaluated_points(prob.cutoff)
+        begin, end = gdist.shard_range(n_eval, rank, world)
+        pbar = np.random.default_rng(7).standard_normal(tuple(int(c) + 1 for c in prob.cutoff))
+        grads = {"r": partial_loss_gradient(prob, pbar, begin, end)}
+        total = gdist.allreduce_grads(grads)
+        if rank == 0:
+            np.save(out, total["r"])
+        dist.barrier()
+        dist.destroy_process_group()
+        return
     if fock_mode:
         # Fock inputs: the ranks split the input nodes (Gray-code order) and each contributes
         # the oracle's partial table of its range, standing in for a sharded Fock plan

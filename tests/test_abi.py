@@ -171,4 +171,3 @@ def test_large_tree_validation(gb, btree):
     big_last = synth.random_problem(np.random.default_rng(9), 120, 1, 2, 2)   # last group 120 rows > 112
     assert _status(gb, big_last, tile_override=btree) == 8
     assert _status(gb, synth.config(2), tile_override=btree, want_backward=True) == 8
-    assert _status(gb, synth.config(2), tile_override=btree, shard=(0, 10)) == 8

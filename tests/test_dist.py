@@ -86,3 +86,26 @@ def test_gloo_world_size_2_fock_node_shards(tmp_path):
     from oracle import fock
     fp = synth.random_fock_problem(np.random.default_rng(41), 5, [1, 2, 0, 1, 1], 2, 5)
     assert np.abs(np.load(out) - fock.table(fp)["P"]).max() < 1e-14
+
+
+def test_gloo_world_size_2_partial_gradients(tmp_path):
+    # each rank's gradient of its partial table (a sharded plan's reverse pass) summed by one
+    # all-reduce per array equals the gradient of the whole table
+    out = str(tmp_path / "grad.npy")
+    env = dict(os.environ, MASTER_ADDR="127.0.0.1", MASTER_PORT=str(_free_port()), WORLD_SIZE="2")
+    procs = [subprocess.Popen([sys.executable, os.path.join(HERE, "_dist_worker.py"), out, "grad"],
+                              env=dict(env, RANK=str(r)), stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
+             for r in range(2)]
+    logs = []
+    for p in procs:
+        try:
+            logs.append(p.communicate(timeout=240)[0].decode(errors="replace"))
+        except subprocess.TimeoutExpired:
+            p.kill()
+            raise
+    assert all(p.returncode == 0 for p in procs), logs
+    from _dist_worker import partial_loss_gradient
+    prob = synth.config(0)
+    pbar = np.random.default_rng(7).standard_normal(tuple(int(c) + 1 for c in prob.cutoff))
+    whole = partial_loss_gradient(prob, pbar, 0, gdist.evaluated_points(prob.cutoff))
+    assert np.abs(np.load(out) - whole).max() < 1e-8
