@@ -1001,16 +1001,18 @@ const char* gbsbin_strerror(int status) {
 }
 
 static int plan_create_impl(const gbsbin_problem* p, const gbsbin_options* o, gbsbin_plan** out, int p_override,
-                            bool alloc_gws);
+                            bool alloc_gws, bool allow_tree);
 
 int gbsbin_plan_create(const gbsbin_problem* p, const gbsbin_options* o, gbsbin_plan** out) {
-  return plan_create_impl(p, o, out, 0, true);
+  return plan_create_impl(p, o, out, 0, true, true);
 }
 
 // p_override > 0 forces the points per CTA (autotuning); alloc_gws = false leaves the
-// workspace to a batch that shares one across its problems.
+// workspace to a batch that shares one across its problems; allow_tree lets the automatic
+// choice take a tree of block eliminations (standalone plans, and batch problems large enough
+// to run apart from the batch's per-point launches).
 static int plan_create_impl(const gbsbin_problem* p, const gbsbin_options* o, gbsbin_plan** out, int p_override,
-                            bool alloc_gws) {
+                            bool alloc_gws, bool allow_tree) {
   if (!out) return GBSBIN_ERR_ARG;
   *out = nullptr;
   gbsbin_options opt;
@@ -1070,7 +1072,7 @@ static int plan_create_impl(const gbsbin_problem* p, const gbsbin_options* o, gb
   // (batches run their own per-point launches)
   const bool sharded = opt.shard_end != 0 || opt.shard_begin != 0;
   size_t tree_bytes = 0;
-  if (is_tree(P->kernel) || (alloc_gws && !opt.tile_override && p->L >= 2)) {
+  if (is_tree(P->kernel) || (allow_tree && !opt.tile_override && p->L >= 2)) {
     tree_bytes = (!sharded && !opt.want_backward) ? tree_layout(P) : 0;
     if (tree_bytes && !is_tree(P->kernel))
       P->kernel = opt.precision == GBSBIN_FP64 ? GBSBIN_KERNEL_TREE_FP64 : GBSBIN_KERNEL_TREE_DF32;
@@ -1081,7 +1083,7 @@ static int plan_create_impl(const gbsbin_problem* p, const gbsbin_options* o, gb
   }
   // the large-matrix tree: asked for, or by default for standalone plans of n > 64 where it
   // needs under half the work of one LU per evaluated point
-  if (is_btree(P->kernel) || (!is_tree(P->kernel) && alloc_gws && !opt.tile_override && p->L >= 2 && n > 64)) {
+  if (is_btree(P->kernel) || (!is_tree(P->kernel) && allow_tree && !opt.tile_override && p->L >= 2 && n > 64)) {
     tree_bytes = !opt.want_backward ? btree_layout(P) : 0;
     bool take = tree_bytes > 0;
     if (take && !is_btree(P->kernel))
@@ -2402,7 +2404,7 @@ int tune_size(int n, int precision, TuneVal* best) {
     o.tile_override = c.kernel;
     o.want_diagnostics = 0;
     gbsbin_plan* P = nullptr;
-    if (plan_create_impl(&pr, &o, &P, c.P, true) != GBSBIN_OK) continue;
+    if (plan_create_impl(&pr, &o, &P, c.P, true, false) != GBSBIN_OK) continue;
     PointArgs a = make_point_args(P);
     float best_ms = 1e30f;
     for (int rep = 0; rep < 3; ++rep) {
@@ -2457,6 +2459,7 @@ int autotune_lookup(int n, int precision, TuneVal* out) {
 // ================================================================== batches
 struct gbsbin_batch {
   std::vector<gbsbin_plan*> plans;
+  std::vector<char> own;              // problem i runs its own plan's launches (a tree), not the queue
   struct Class {
     int kernel = 0, threads = 0, np = 0;
     size_t smem = 0;
@@ -2502,6 +2505,11 @@ int batch_launch(gbsbin_batch* B, double* const* P_out, cudaStream_t s) {
   }
   for (size_t i = 0; i < B->plans.size(); ++i) {
     if (!P_out[i]) return GBSBIN_ERR_ARG;
+    if (B->own[i]) {                                 // a tree: its own launches and DFT
+      const int st = gbsbin_execute(B->plans[i], P_out[i], s);
+      if (st) return st;
+      continue;
+    }
     if (launch_dft_fused(make_dft_args(B->plans[i], P_out[i]), B->plans[i]->d_bar, B->num_sms, s) != cudaSuccess)
       return GBSBIN_ERR_CUDA;
   }
@@ -2543,12 +2551,34 @@ int gbsbin_batch_create(const gbsbin_problem* probs, int nprob, const gbsbin_opt
     return GBSBIN_ERR_CUDA;
   }
   B->plans.assign(nprob, nullptr);
+  B->own.assign(nprob, 0);
   std::vector<PointArgs> args(nprob);
   std::map<std::tuple<int, int, int>, int> class_of;
   for (int i = 0; i < nprob; ++i) {
     gbsbin_options oi = opt;
     int p_override = 0;
     const int n = 2 * probs[i].M * probs[i].K;
+    // problems whose per-point LUs would take ~50 us or more of the batch run a tree of block
+    // eliminations of their own where one suits them (the automatic choice of a standalone
+    // plan), outside the per-point job queue
+    if (!opt.tile_override && probs[i].L >= 2 && n <= GBSBIN_MAX_N) {
+      double evald = 1.0;
+      for (int l = 0; l < probs[i].L; ++l) {
+        const double R = (double)opt.oversample * (probs[i].cutoff[l] + 1);
+        evald *= l + 1 < probs[i].L ? R : std::floor(R / 2) + 1;
+      }
+      if (evald * n * (double)n * n / 3.0 >= 2e7) {
+        gbsbin_plan* T = nullptr;
+        const int st = plan_create_impl(&probs[i], &opt, &T, 0, false, true);
+        if (st == GBSBIN_OK && (is_tree(T->kernel) || is_btree(T->kernel))) {
+          B->plans[i] = T;
+          B->own[i] = 1;
+          args[i] = make_point_args(T);
+          continue;
+        }
+        if (T) gbsbin_plan_destroy(T);
+      }
+    }
     // one-group problems keep the Hessenberg path whatever the size's tuning
     const bool one_group = probs[i].L == 1;
     if (autotune && !opt.tile_override && n <= GBSBIN_MAX_N && !one_group) {
@@ -2561,8 +2591,9 @@ int gbsbin_batch_create(const gbsbin_problem* probs, int nprob, const gbsbin_opt
       oi.tile_override = v.kernel;
       p_override = v.P;
     }
-    int st = plan_create_impl(&probs[i], &oi, &B->plans[i], p_override, false);
-    if (st == GBSBIN_ERR_UNSUPPORTED && p_override) st = plan_create_impl(&probs[i], &opt, &B->plans[i], 0, false);
+    int st = plan_create_impl(&probs[i], &oi, &B->plans[i], p_override, false, false);
+    if (st == GBSBIN_ERR_UNSUPPORTED && p_override)
+      st = plan_create_impl(&probs[i], &opt, &B->plans[i], 0, false, false);
     if (st) {
       batch_free(B);
       return st;

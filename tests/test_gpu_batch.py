@@ -90,3 +90,36 @@ def test_full_batched_workload_sampled(cuda_lib):
             ref, _, _ = oracle.logq_points(XA, gamma, labels, p.radix, dig[pick])
             assert np.abs(lq[pick] - ref).max() < 1e-9, (i, p.n)
         assert all(float(o.sum()) == pytest.approx(1.0, abs=1e-10) for o in outs)
+
+
+def test_batch_problems_on_trees(cuda_lib):
+    # problems large enough to run apart from the per-point queue take a tree of their own
+    # (the small tree for n <= 64, the large-matrix tree above), beside per-point problems;
+    # every table against the oracle, and the same tables from a captured graph
+    import torch
+    gb = cuda_lib
+    rng = np.random.default_rng(703)
+    probs = [synth.random_problem(rng, 16, 2, 4, [4, 4, 4, 4], displaced=True),            # n = 64, small tree
+             synth.random_problem(rng, 16, 3, 3, [6, 6, 6], displaced=True, internal_basis=True),   # n = 96, large
+             synth.random_problem(rng, 4, 1, 2, [5, 4]),                                    # n = 8, queue
+             synth.random_problem(rng, 60, 1, 2, [3, 2], displaced=True)]                   # n = 120, queue
+    for precision, small, large in ((1, "tree_df32", "btree_df32"), (0, "tree_fp64", "btree_fp64")):
+        with gb.Batch(probs, precision=precision) as b:
+            ref = [t.clone() for t in b.execute()]
+            kinds = [b.diagnostics(i)[1]["kernel_name"] for i in range(len(probs))]
+            assert kinds[0] == small and kinds[1] == large, kinds
+            assert "tree" not in kinds[2] and "tree" not in kinds[3], kinds
+            for i, p in enumerate(probs):
+                st, d = b.diagnostics(i)
+                assert st == 0 and d["n_bad_points"] == 0
+                assert np.abs(ref[i].cpu().numpy() - oracle.binned(p)["P"]).max() <= 1e-10, (i, precision)
+            torch.cuda.synchronize()
+            s = torch.cuda.Stream()
+            for t in b.outputs:
+                t.zero_()
+            torch.cuda.synchronize()
+            b.capture(s)
+            b.replay(s)
+            s.synchronize()
+            for t, r in zip(b.outputs, ref):
+                assert torch.equal(t, r)
