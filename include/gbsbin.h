@@ -191,8 +191,10 @@ typedef enum {
                                       apply and it needs under half the per-point LUs'
                                       work (last group <= 112 rows, no shard, no
                                       want_backward)                                       */
-  GBSBIN_KERNEL_BTREE_FP64 = 14    /* the same in FP64; chosen for GBSBIN_FP64 plans under
+  GBSBIN_KERNEL_BTREE_FP64 = 14,   /* the same in FP64; chosen for GBSBIN_FP64 plans under
                                       the same conditions                                   */
+  GBSBIN_KERNEL_HERALD_FP64 = 15   /* heralded states (gbsbin_herald_*): CTA per point, FP64;
+                                      not a choice for gbsbin_plan_create                   */
 } gbsbin_kernel;
 
 /* Fill *o with defaults: FP64, oversample 1, diagnostics on, automatic kernel. */
@@ -524,6 +526,76 @@ int gbsbin_fock_execute(gbsbin_fock_plan* plan, double* P_out, void* stream);
 int gbsbin_fock_execute_host(gbsbin_fock_plan* plan, double* P_out_host, void* stream);
 int gbsbin_fock_diagnostics(gbsbin_fock_plan* plan, gbsbin_diag* out, void* stream);
 int gbsbin_fock_plan_destroy(gbsbin_fock_plan* plan);
+/*
+ * Heralded states (Sec. VII of the paper, Eqs. heralded_state_internal and
+ * lhaf_heralded_offd_internal_1).  The M*K modes of a Gaussian state (state fields of
+ * gbsbin_problem as for gbsbin_plan_create; its bin_of_mode, L and cutoff are ignored) take a
+ * role each: role[m] = l in [0, L) - mode m belongs to heralding group l (a photon-number-
+ * resolving detector, or a group of them whose counts are summed); GBSBIN_HERALD_TRACED - the
+ * mode is discarded (traced out); GBSBIN_HERALD_KEPT - the mode carries the heralded state.
+ * For every heralding outcome b (0 <= b_l <= cutoff[l]) the library returns the unnormalised
+ * heralded state restricted to Fock indices <= fock_cutoff on each kept mode,
+ *   rho(b) = sum over heralding patterns n with group counts b of Tr_traced <n| rho |n>,
+ * and its trace over all kept
+ * photon numbers, Pr(b) (the probability of outcome b; rho(b) / Pr(b) is the normalised
+ * state).  Method: with A = X (I - Sigma^{-1}) and gamma as for the binned tables, the sum
+ * over heralding and traced photon numbers weighted by w^n / n! is a complex-Gaussian
+ * expectation, so that
+ *   <v| rho(b) |u> = Pr(0) sqrt(u! v!) [w^b][x^u y^v] exp(xi^T M(w) xi / 2 + l(w)^T xi + e(w))
+ *                  / sqrt(det(I - X D(w) A_DD)),
+ * xi = (x, y) on the kept modes' two halves, M(w), l(w), e(w) from one solve with the
+ * heralding and traced block I - X D(w) A_DD (w = 1 on traced modes), and the coefficient of
+ * w^b by an inverse DFT over the grid w_l = exp(2 pi i k_l / R_l), R_l = oversample
+ * (cutoff[l] + 1) (folded: photon numbers beyond R_l - 1 alias onto b, as for the binned
+ * tables; oversample to unfold).  Pr(b) is the binned table of the heralding groups with
+ * every other mode traced.  The Taylor coefficients of the kept modes follow from the
+ * recurrence (p_i + 1) c_{p + e_i} = l_i c_p + sum_j M_ij c_{p - e_j} and are exact (no
+ * folding) up to fock_cutoff.
+ * Layout of rho_out: element [b_0 .. b_{L-1}][u_1 .. u_k][v_1 .. v_k] = <v| rho(b) |u> (the
+ * conjugate of <u| rho(b) |v>), the last index fastest, u_i / v_i the ket / bra Fock index of
+ * the i-th kept mode (in mode order), each of extent
+ * fock_cutoff + 1: table_size = prod (cutoff[l] + 1) x (fock_cutoff + 1)^(2k) complex values;
+ * prob_out: prod (cutoff[l] + 1) doubles.  FP64 throughout (kernel 15).
+ * Limits: 2 x (modes not kept) and 2 M K at most GBSBIN_HERALD_MAX_MODES2, at most
+ * GBSBIN_HERALD_MAX_KEPT kept modes (at least one), (fock_cutoff + 1)^(2k) at most
+ * GBSBIN_HERALD_MAX_COEF (ERR_UNSUPPORTED); grid as for gbsbin_plan_create (ERR_CUTOFF).
+ * Errors: ERR_ARG (null pointers, a role outside [-2, L), L < 1, fock_cutoff < 0, options
+ * other than precision GBSBIN_FP64 / oversample / want_timing / want_diagnostics), ERR_PARTITION (a heralding group
+ * without modes), ERR_NONPHYSICAL as for plan creation.  Options: oversample, want_timing
+ * (point_kernel_ms of gbsbin_herald_diagnostics: all its launches).  All arrays host memory read
+ * during the call.  gbsbin_herald_diagnostics: sum_P = sum of Pr(b) over the table,
+ * min_pivot_re / n_bad_points over both eliminations of every point (n_bad_points > 0 makes
+ * execute's results unreliable; the diagnostics call returns ERR_NUMERIC then), n_points =
+ * n_evaluated = grid points, table_size as gbsbin_herald_table_size, n = 2 M K, kernel 15,
+ * log_q1_re = -log Pr(0).
+ */
+#define GBSBIN_HERALD_TRACED (-1)
+#define GBSBIN_HERALD_KEPT (-2)
+#define GBSBIN_HERALD_MAX_MODES2 96
+#define GBSBIN_HERALD_MAX_KEPT 4
+#define GBSBIN_HERALD_MAX_COEF (1 << 20)
+typedef struct {
+  gbsbin_problem state;
+  const int* role;     /* [M*K], external-major mode order (port i, internal k: i*K + k) */
+  int L;
+  const int* cutoff;   /* [L] */
+  int fock_cutoff;
+} gbsbin_herald_problem;
+typedef struct gbsbin_herald_plan gbsbin_herald_plan;
+int gbsbin_herald_plan_create(const gbsbin_herald_problem* p, const gbsbin_options* o, gbsbin_herald_plan** out);
+/* Complex elements of rho_out (-1 if plan is NULL); prob_out has table_size / (fock_cutoff
+ * + 1)^(2k) entries. */
+long long gbsbin_herald_table_size(const gbsbin_herald_plan* plan);
+long long gbsbin_herald_prob_size(const gbsbin_herald_plan* plan);
+/* rho_out, prob_out device memory; asynchronous on `stream` (1 + L launches: the points, then the
+ * inverse DFT one heralding axis at a time). */
+int gbsbin_herald_execute(gbsbin_herald_plan* plan, gbsbin_complex* rho_out, double* prob_out, void* stream);
+/* The same into host memory; synchronises `stream`. */
+int gbsbin_herald_execute_host(gbsbin_herald_plan* plan, gbsbin_complex* rho_out_host, double* prob_out_host,
+                               void* stream);
+int gbsbin_herald_diagnostics(gbsbin_herald_plan* plan, gbsbin_diag* out, void* stream);
+int gbsbin_herald_plan_destroy(gbsbin_herald_plan* plan);
+
 /* Static description of a status code. */
 const char* gbsbin_strerror(int status);
 

@@ -25,7 +25,7 @@ GBSBIN_FP64 = 0
 GBSBIN_FP32_REFINE = 1
 KERNELS = {1: "smem_fp64", 2: "smem_fp32r", 3: "gmem_fp64", 4: "gmem_fp32r", 5: "warp_fp32r", 6: "blk_fp32r",
            7: "blk_tc_fp32r", 8: "hess_fp64", 9: "fock_fp64", 10: "fock_df32",
-           11: "tree_df32", 12: "tree_fp64", 13: "btree_df32", 14: "btree_fp64"}
+           11: "tree_df32", 12: "tree_fp64", 13: "btree_df32", 14: "btree_fp64", 15: "herald_fp64"}
 EXPORTED = ["gbsbin_default_options", "gbsbin_plan_create", "gbsbin_plan_set_state", "gbsbin_plan_destroy",
             "gbsbin_plan_table_size", "gbsbin_execute", "gbsbin_execute_host", "gbsbin_execute_host_async",
             "gbsbin_diagnostics",
@@ -37,7 +37,11 @@ EXPORTED = ["gbsbin_default_options", "gbsbin_plan_create", "gbsbin_plan_set_sta
             "gbsbin_fock_execute", "gbsbin_fock_execute_host", "gbsbin_fock_diagnostics",
             "gbsbin_fock_plan_destroy", "gbsbin_cumulants3", "gbsbin_cumulants4", "gbsbin_fock_plan_nodes",
             "gbsbin_total_photon_series", "gbsbin_cumulant_groups", "gbsbin_prob_distinguishable",
-            "gbsbin_prob_distinguishable_device"]
+            "gbsbin_prob_distinguishable_device", "gbsbin_herald_plan_create", "gbsbin_herald_table_size",
+            "gbsbin_herald_prob_size", "gbsbin_herald_execute", "gbsbin_herald_execute_host",
+            "gbsbin_herald_diagnostics", "gbsbin_herald_plan_destroy"]
+GBSBIN_HERALD_TRACED = -1
+GBSBIN_HERALD_KEPT = -2
 
 
 class GbsbinError(RuntimeError):
@@ -82,6 +86,11 @@ class gbsbin_diag(ctypes.Structure):
 class gbsbin_fock_problem(ctypes.Structure):
     _fields_ = [("M", ctypes.c_int), ("T", _cp), ("photons", _ip), ("bin_of_mode", _ip), ("L", ctypes.c_int),
                 ("cutoff", _ip)]
+
+
+class gbsbin_herald_problem(ctypes.Structure):
+    _fields_ = [("state", gbsbin_problem), ("role", _ip), ("L", ctypes.c_int), ("cutoff", _ip),
+                ("fock_cutoff", ctypes.c_int)]
 
 
 def load():
@@ -147,6 +156,19 @@ def load():
     lib.gbsbin_fock_execute_host.argtypes = [vp, vp, vp]
     lib.gbsbin_fock_diagnostics.argtypes = [vp, ctypes.POINTER(gbsbin_diag), vp]
     lib.gbsbin_fock_plan_destroy.argtypes = [vp]
+    hp = ctypes.POINTER(gbsbin_herald_problem)
+    lib.gbsbin_herald_plan_create.argtypes = [hp, ctypes.POINTER(gbsbin_options), ctypes.POINTER(vp)]
+    lib.gbsbin_herald_table_size.argtypes = [vp]
+    lib.gbsbin_herald_table_size.restype = ctypes.c_longlong
+    lib.gbsbin_herald_prob_size.argtypes = [vp]
+    lib.gbsbin_herald_prob_size.restype = ctypes.c_longlong
+    lib.gbsbin_herald_execute.argtypes = [vp, vp, vp, vp]
+    lib.gbsbin_herald_execute_host.argtypes = [vp, vp, vp, vp]
+    lib.gbsbin_herald_diagnostics.argtypes = [vp, ctypes.POINTER(gbsbin_diag), vp]
+    lib.gbsbin_herald_plan_destroy.argtypes = [vp]
+    for f in ("gbsbin_herald_plan_create", "gbsbin_herald_execute", "gbsbin_herald_execute_host",
+              "gbsbin_herald_diagnostics", "gbsbin_herald_plan_destroy"):
+        getattr(lib, f).restype = ctypes.c_int
     for f in ("gbsbin_plan_create", "gbsbin_plan_set_state", "gbsbin_plan_destroy", "gbsbin_execute",
               "gbsbin_execute_host", "gbsbin_execute_host_async", "gbsbin_diagnostics", "gbsbin_alu_peak",
               "gbsbin_read_points",
@@ -712,6 +734,115 @@ class FockPlan:
     def close(self):
         if self.handle is not None:
             gbsbin_fock_plan_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------------ heralded states (Sec. VII)
+class HeraldProblemArgs:
+    """Marshals a state (M, K and r, T, optional alpha, V - or sigma1, optional zbar), the
+    per-mode roles (heralding group >= 0, GBSBIN_HERALD_TRACED, GBSBIN_HERALD_KEPT), the
+    heralding cutoffs and the kept modes' Fock cutoff into a gbsbin_herald_problem."""
+
+    class _State:
+        def __init__(self, st):
+            self.__dict__.update({k: getattr(st, k, None) for k in ("M", "K", "r", "T", "alpha", "V", "sigma1",
+                                                                     "zbar")})
+            self.bin_of_mode = [0] * int(st.M)     # ignored by the library
+            self.cutoff = [0]
+
+    def __init__(self, state, roles, cutoff, fock_cutoff):
+        self.state = ProblemArgs(self._State(state))
+        self.roles = np.ascontiguousarray(np.asarray(roles, dtype=np.int32))
+        self.cut = np.ascontiguousarray(np.asarray(cutoff, dtype=np.int32))
+        self.c = gbsbin_herald_problem(self.state.c, self.roles.ctypes.data_as(_ip), int(len(self.cut)),
+                                       self.cut.ctypes.data_as(_ip), int(fock_cutoff))
+
+
+def gbsbin_herald_plan_create(state, roles, cutoff, fock_cutoff, options=None):
+    args = HeraldProblemArgs(state, roles, cutoff, fock_cutoff)
+    opts = options if options is not None else gbsbin_default_options()
+    h = ctypes.c_void_p()
+    _check(load().gbsbin_herald_plan_create(ctypes.byref(args.c), ctypes.byref(opts), ctypes.byref(h)),
+           "gbsbin_herald_plan_create")
+    return h
+
+
+def gbsbin_herald_table_size(plan):
+    return int(load().gbsbin_herald_table_size(plan))
+
+
+def gbsbin_herald_prob_size(plan):
+    return int(load().gbsbin_herald_prob_size(plan))
+
+
+def gbsbin_herald_execute(plan, rho_out, prob_out, stream=None):
+    _check(load().gbsbin_herald_execute(plan, _ptr(rho_out), _ptr(prob_out), _stream_handle(stream)),
+           "gbsbin_herald_execute")
+
+
+def gbsbin_herald_execute_host(plan, rho_host, prob_host, stream=None):
+    _check(load().gbsbin_herald_execute_host(plan, _ptr(rho_host), _ptr(prob_host), _stream_handle(stream)),
+           "gbsbin_herald_execute_host")
+
+
+def gbsbin_herald_diagnostics(plan, stream=None):
+    d = gbsbin_diag()
+    st = load().gbsbin_herald_diagnostics(plan, ctypes.byref(d), _stream_handle(stream))
+    out = {f: getattr(d, f) for f, _ in gbsbin_diag._fields_}
+    out["kernel_name"] = KERNELS.get(out["kernel"], "?")
+    out["status"] = st
+    return out
+
+
+def gbsbin_herald_plan_destroy(plan):
+    _check(load().gbsbin_herald_plan_destroy(plan), "gbsbin_herald_plan_destroy")
+
+
+class HeraldPlan:
+    """Owning wrapper: ``with HeraldPlan(state, roles, cutoff, fock_cutoff) as h: rho, pr = h.states()``.
+
+    ``rho[b..., u..., v...] = <v| rho(b) |u>`` (unnormalised; ``pr[b]`` = Pr(b) its trace over all
+    kept photon numbers)."""
+
+    def __init__(self, state, roles, cutoff, fock_cutoff, oversample=1, want_timing=False):
+        self.options = make_options(GBSBIN_FP64, oversample, True, 0, want_timing)
+        self.handle = gbsbin_herald_plan_create(state, roles, cutoff, fock_cutoff, self.options)
+        nk = int(sum(1 for r in roles if int(r) == GBSBIN_HERALD_KEPT))
+        self.prob_shape = tuple(int(c) + 1 for c in cutoff)
+        self.shape = self.prob_shape + (int(fock_cutoff) + 1,) * (2 * nk)
+
+    def states(self, stream=None):
+        """Execute into new CUDA tensors: rho (complex128, ``shape``) and Pr(b) (float64)."""
+        import torch
+        rho = torch.empty(self.shape, dtype=torch.complex128, device="cuda")
+        pr = torch.empty(self.prob_shape, dtype=torch.float64, device="cuda")
+        gbsbin_herald_execute(self.handle, rho, pr, stream)
+        return rho, pr
+
+    def states_host(self, stream=None):
+        rho = np.empty(self.shape, dtype=np.complex128)
+        pr = np.empty(self.prob_shape, dtype=np.float64)
+        gbsbin_herald_execute_host(self.handle, rho, pr, stream)
+        return rho, pr
+
+    def diagnostics(self, stream=None):
+        return gbsbin_herald_diagnostics(self.handle, stream)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            gbsbin_herald_plan_destroy(self.handle)
             self.handle = None
 
     def __enter__(self):

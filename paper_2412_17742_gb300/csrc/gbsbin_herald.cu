@@ -1,0 +1,292 @@
+// Heralded (conditional) states of a Gaussian state (arXiv:2412.17742, Sec. VII, Eqs.
+// heralded_state_internal and lhaf_heralded_offd_internal_1), from the generating function.
+//
+// The modes are heralding (group l), traced or kept.  With lhaf(A_p, gamma_p) the p-th
+// derivative of exp(xi^T A xi / 2 + gamma^T xi) at 0, the sum over the heralding and traced
+// photon patterns with weights w^n / n! is the complex-Gaussian expectation of that
+// exponential with xi = sqrt(w) (alpha, conj alpha) on those modes, and the kept modes' Fock
+// indices (u on the first half, v on the second) are Taylor coefficients of the rest:
+//
+//   sum_{n, t} lhaf(A_{(n,t,u)+(n,t,v)}, ...) w^n / (n! t!) = u! v! [x^u y^v] F(w; x, y),
+//   F = exp(xi_F^T M xi_F / 2 + l^T xi_F + e) / sqrt(det(I - X D(w) A_DD)),
+//   N = (I - X D(w) A_DD)^-1 X D(w),  M = A_FF + A_DF^T N A_DF,  l = gamma_F + A_DF^T N gamma_D,
+//   e = gamma_D^T N gamma_D / 2,
+//
+// D the heralding and traced indices (both halves; w = 1 on traced modes), F the kept ones.
+// Hence <v|rho(b)|u> = Pr(0) sqrt(u! v!) [w^b][x^u y^v] F.  Per point of the roots-of-unity grid
+// over the heralding groups a CTA eliminates I - X D(w) A_DD without pivoting (a principal
+// block of I - D(w) XA with ||XA|| < 1: every pivot has Re > 0 and Sum Log is the branch of
+// the square root continuous from w = 0), solves for the kept modes' columns and gamma_D,
+// forms M, l, e, and the Taylor coefficients of exp(xi^T M xi / 2 + l^T xi) by
+// (p_i + 1) c_{p + e_i} = l_i c_p + sum_j M_ij c_{p - e_j} (shells of equal total degree in
+// parallel); the same CTA also evaluates the heralding probability's generating function,
+// every non-heralding mode traced.  An inverse DFT over the grid, one axis per launch, then
+// extracts [w^b] for every coefficient.  FP64 throughout.
+#include <cuda_runtime.h>
+
+#include "gbsbin_device.cuh"
+#include "gbsbin_internal.h"
+
+namespace gbsbin {
+namespace {
+
+constexpr int HT = 256;
+
+__device__ __forceinline__ double2 cadd2(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 cneg2(double2 a) { return make_double2(-a.x, -a.y); }
+
+// Root of the group of mode m at grid point k (1 for a non-heralding mode).
+__device__ __forceinline__ double2 mode_root(const HeraldArgs& a, long long k, int m) {
+  const int l = a.role[m];
+  if (l < 0) return make_double2(1.0, 0.0);
+  long long rest = k;
+  int d = 0;
+  for (int q = a.L - 1; q >= 0; --q) {
+    const long long up = rest / a.radix[q];
+    if (q == l) d = (int)(rest - up * a.radix[q]);
+    rest = up;
+  }
+  int off = 0;
+  for (int q = 0; q < l; ++q) off += a.radix[q];
+  const double2 t = a.tw[off + d];                   // exp(-2 pi i d / R)
+  return make_double2(t.x, -t.y);
+}
+
+// Unpivoted elimination of the nr x nr block of G (row stride ld) with ncol right-hand-side
+// columns after it, then back substitution: the columns become the block's inverse times
+// themselves.  Returns sum Log(pivots) (each Re > 0) and the smallest pivot real part in
+// thread 0's registers; all threads call it.
+__device__ void solve_block(double2* G, int nr, int ncol, int ld, double2* ldet, double* minre) {
+  const int tid = threadIdx.x, T = blockDim.x;
+  const int cols = nr + ncol;
+  double2 lsum = make_double2(0.0, 0.0);
+  double mn = 1e300;
+  for (int k = 0; k < nr; ++k) {
+    const double2 piv = G[k * ld + k];
+    const double2 r = crecip(piv);
+    if (tid == 0) {
+      lsum = cadd2(lsum, make_double2(0.5 * log(fma(piv.x, piv.x, piv.y * piv.y)), atan2(piv.y, piv.x)));
+      mn = fmin(mn, piv.x);
+      if (!(piv.x == piv.x) || !(piv.y == piv.y)) mn = -1e300;
+    }
+    const int w = cols - k - 1;
+    for (int idx = tid; idx < (nr - k - 1) * w; idx += T) {
+      const int i = k + 1 + idx / w, j = k + 1 + idx % w;
+      const double2 li = cmul(G[i * ld + k], r);
+      G[i * ld + j] = cfnma(G[i * ld + j], li, G[k * ld + j]);
+    }
+    __syncthreads();
+  }
+  for (int k = nr - 1; k >= 0; --k) {                // x_k = (rhs_k - sum_{j > k} u_kj x_j) / u_kk
+    const double2 r = crecip(G[k * ld + k]);
+    for (int c = tid; c < ncol; c += T) {
+      double2 s = G[k * ld + nr + c];
+      for (int j = k + 1; j < nr; ++j) s = cfnma(s, G[k * ld + j], G[j * ld + nr + c]);
+      G[k * ld + nr + c] = cmul(s, r);
+    }
+    __syncthreads();
+  }
+  *ldet = lsum;
+  *minre = mn;
+}
+
+__global__ void __launch_bounds__(HT) k_herald_points(HeraldArgs a) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  const long long k = blockIdx.x;
+  const int nd = a.nd, nf = a.nf, n2 = a.n2, tid = threadIdx.x, T = blockDim.x;
+  const int cols = nd + nf + 1;
+  const size_t gsz = (size_t)nd * cols > (size_t)n2 * (n2 + 1) ? (size_t)nd * cols : (size_t)n2 * (n2 + 1);
+  double2* G = reinterpret_cast<double2*>(sm_raw);   // nd x cols (the kept solve), then n2 x (n2 + 1)
+  double2* Mq = G + gsz;                              // nf x nf
+  double2* lq = Mq + nf * nf;                         // nf
+  double2* sc = lq + nf;                              // e, log det, e_all, log det_all
+  // I - X D(w) A_DD with the right-hand sides X D(w) [A_DF | gamma_D]; row i of X D A is
+  // w_{partner(i)} A_{partner(i), .}
+  for (int idx = tid; idx < nd * cols; idx += T) {
+    const int i = idx / cols, j = idx - (idx / cols) * cols;
+    const int pi = a.dpart[i];                        // X partner of row i within D
+    const double2 w = mode_root(a, k, a.dmode[pi]);
+    double2 v;
+    if (j < nd) v = cneg2(cmul(w, a.ADD[(size_t)pi * nd + j]));
+    else if (j < nd + nf) v = cmul(w, a.ADF[(size_t)pi * nf + (j - nd)]);
+    else v = cmul(w, a.gD[pi]);
+    if (j == i) v.x += 1.0;
+    G[idx] = v;
+  }
+  __syncthreads();
+  double2 ld;
+  double mn;
+  solve_block(G, nd, nf + 1, cols, &ld, &mn);
+  // M = A_FF + A_DF^T Y_F, l = gamma_F + A_DF^T y, e = gamma_D^T y / 2
+  for (int idx = tid; idx < nf * (nf + 1); idx += T) {
+    const int i = idx / (nf + 1), c = idx - (idx / (nf + 1)) * (nf + 1);
+    double2 s = c < nf ? a.AFF[i * nf + c] : a.gF[i];
+    for (int d = 0; d < nd; ++d) s = cadd2(s, cmul(a.ADF[(size_t)d * nf + i], G[d * cols + nd + c]));
+    if (c < nf) Mq[i * nf + c] = s;
+    else lq[i] = s;
+  }
+  if (tid == 0) {
+    double2 e = make_double2(0.0, 0.0);
+    for (int d = 0; d < nd; ++d) e = cadd2(e, cmul(a.gD[d], G[d * cols + nd + nf]));
+    sc[0] = make_double2(0.5 * e.x, 0.5 * e.y);
+    sc[1] = ld;
+  }
+  __syncthreads();
+  // the heralding probability: I - X D(w) A over every mode (w = 1 off the heralding groups),
+  // right-hand side X D(w) gamma
+  {
+    const int cn = n2 + 1;
+    for (int idx = tid; idx < n2 * cn; idx += T) {
+      const int i = idx / cn, j = idx - (idx / cn) * cn;
+      const int pi = i < n2 / 2 ? i + n2 / 2 : i - n2 / 2;
+      const double2 w = mode_root(a, k, pi % (n2 / 2));
+      double2 v = j < n2 ? cneg2(cmul(w, a.Aall[(size_t)pi * n2 + j])) : cmul(w, a.gall[pi]);
+      if (j == i) v.x += 1.0;
+      G[idx] = v;
+    }
+    __syncthreads();
+    double2 lda;
+    double mna;
+    solve_block(G, n2, 1, cn, &lda, &mna);
+    if (tid == 0) {
+      double2 e = make_double2(0.0, 0.0);
+      for (int d = 0; d < n2; ++d) e = cadd2(e, cmul(a.gall[d], G[d * cn + n2]));
+      const double re = 0.5 * e.x - 0.5 * lda.x, im = 0.5 * e.y - 0.5 * lda.y;
+      const double m = exp(re);
+      double s, c;
+      sincos(im, &s, &c);
+      a.gcoef[(size_t)k * (a.ncoef + 1) + a.ncoef] = make_double2(m * c, m * s);
+      a.minpiv[k] = fmin(mn, mna);
+    }
+    __syncthreads();
+  }
+  // Taylor coefficients by shells of total degree; the tensor lives in global memory (this
+  // point's slot of ncoef + 1 entries, the last the heralding probability's value), index
+  // p = sum_i p_i (c + 1)^(nf - 1 - i)
+  double2* C = a.gcoef + (size_t)k * (a.ncoef + 1);
+  const int cp1 = a.cut + 1;
+  const double2 e = sc[0], l0 = sc[1];
+  const double m0 = exp(e.x - 0.5 * l0.x);
+  double s0, c0;
+  sincos(e.y - 0.5 * l0.y, &s0, &c0);
+  if (tid == 0) C[0] = make_double2(m0 * c0, m0 * s0);   // exp(e) / sqrt(det) times c_0 = 1
+  __syncthreads();
+  for (int shell = 1; shell <= nf * a.cut; ++shell) {
+    for (long long q = tid; q < a.ncoef; q += T) {
+      int p[GBSBIN_HERALD_MAX_F];
+      long long rest = q;
+      int tot = 0;
+      for (int i = nf - 1; i >= 0; --i) {
+        p[i] = (int)(rest % cp1);
+        rest /= cp1;
+        tot += p[i];
+      }
+      if (tot != shell) continue;
+      int i0 = 0;
+      while (p[i0] == 0) ++i0;
+      long long stride_i0 = 1;
+      for (int i = nf - 1; i > i0; --i) stride_i0 *= cp1;
+      const long long qm = q - stride_i0;             // p - e_i0
+      double2 val = cmul(lq[i0], C[qm]);
+      long long stride_j = 1;
+      for (int j = nf - 1; j >= 0; --j) {
+        const int pj = p[j] - (j == i0 ? 1 : 0);
+        if (pj > 0) val = cadd2(val, cmul(Mq[i0 * nf + j], C[qm - stride_j]));
+        stride_j *= cp1;
+      }
+      const double inv = 1.0 / (double)p[i0];
+      C[q] = make_double2(val.x * inv, val.y * inv);
+    }
+    __syncthreads();
+  }
+}
+
+// One axis of the inverse DFT over the heralding grid: out[pre][b][post][ch] = sum over
+// k < R_l of in[pre][k][post][ch] exp(-2 pi i k b / R_l), b < nout_l (pre runs over the
+// axes already transformed, extent nout; post over the later ones, extent radix; ch over the
+// ncoef Taylor coefficients and the heralding probability's value).  One thread per output
+// element, consecutive threads on consecutive channels (coalesced reads of the input).  The
+// last axis scales by Pr(0) / N (and prod sqrt(p_i!) per coefficient) and writes rho and
+// Pr(b).
+__global__ void k_herald_dft_axis(HeraldArgs a, int l, const double2* __restrict__ in, double2* __restrict__ out,
+                                  double2* __restrict__ rho, double* __restrict__ prob) {
+  const long long nch = a.ncoef + 1;
+  long long pre = 1, post = 1;
+  for (int q = 0; q < l; ++q) pre *= a.nout[q];
+  for (int q = l + 1; q < a.L; ++q) post *= a.radix[q];
+  const int R = a.radix[l], nb = a.nout[l];
+  int off = 0;
+  for (int q = 0; q < l; ++q) off += a.radix[q];
+  const bool last = l == a.L - 1;
+  const long long total = pre * nb * post * nch;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    long long rest = t;
+    const long long ch = rest % nch;
+    rest /= nch;
+    const long long pi = rest % post;
+    rest /= post;
+    const int b = (int)(rest % nb);
+    const long long pr = rest / nb;
+    const double2* src = in + ((pr * R) * post + pi) * nch + ch;
+    const long long step = post * nch;
+    double2 acc = make_double2(0.0, 0.0);
+    int idx = 0;                                     // k b mod R, advanced by b per k
+    for (int k = 0; k < R; ++k) {
+      acc = cadd2(acc, cmul(src[(long long)k * step], a.tw[off + idx]));
+      idx += b;
+      if (idx >= R) idx -= R;
+    }
+    if (!last) {
+      out[((pr * nb + b) * post + pi) * nch + ch] = acc;
+      continue;
+    }
+    const long long cell = pr * nb + b;              // post = 1 on the last axis
+    const double s = a.pr0 / (double)a.npts;
+    if (ch < a.ncoef) {
+      const double f = s * a.chscale[ch];
+      rho[cell * a.ncoef + ch] = make_double2(acc.x * f, acc.y * f);
+    } else {
+      prob[cell] = acc.x * s;
+      a.prob_own[cell] = acc.x * s;
+    }
+  }
+}
+
+}  // namespace
+
+size_t herald_smem_bytes(int nd, int nf, int n2) {
+  const size_t a = (size_t)nd * (nd + nf + 1), b = (size_t)n2 * (n2 + 1);
+  return sizeof(double2) * ((a > b ? a : b) + (size_t)nf * nf + nf + 4);
+}
+
+cudaError_t launch_herald(const HeraldArgs& a, double2* out, double* prob, cudaStream_t s) {
+  const size_t smem = herald_smem_bytes(a.nd, a.nf, a.n2);
+  cudaError_t err = cudaSuccess;
+  if (smem > 48 * 1024) {
+    err = cudaFuncSetAttribute(k_herald_points, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+  }
+  k_herald_points<<<(unsigned)a.npts, HT, smem, s>>>(a);
+  if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  // axis by axis, ping-pong between the coefficient slots and the scratch buffer (each
+  // output is at most as large as its input)
+  const long long nch = a.ncoef + 1;
+  long long pre = 1;
+  const double2* in = a.gcoef;
+  for (int l = 0; l < a.L; ++l) {
+    long long post = 1;
+    for (int q = l + 1; q < a.L; ++q) post *= a.radix[q];
+    const long long work = pre * a.nout[l] * post * nch;
+    long long blocks = (work + 255) / 256;
+    if (blocks > 65535) blocks = 65535;
+    double2* o = (in == a.gcoef) ? a.scratch : a.gcoef;
+    k_herald_dft_axis<<<(unsigned)blocks, 256, 0, s>>>(a, l, in, o, out, prob);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    in = o;
+    pre *= a.nout[l];
+  }
+  return cudaSuccess;
+}
+
+}  // namespace gbsbin

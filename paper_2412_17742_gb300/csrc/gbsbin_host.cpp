@@ -10,6 +10,7 @@
 #include <new>
 #include <vector>
 
+#include "gbsbin_host_state.h"
 #include "gbsbin_internal.h"
 
 using cd = std::complex<double>;
@@ -447,36 +448,8 @@ int upload_state(gbsbin_plan* P, cudaStream_t stream) {
     split(P->Xgamma[i], &Xghi[i], &Xglo[i]);
     split(P->gamma[i], &ghi[i], &glo[i]);
   }
-  if (is_btree(P->kernel) && P->grid.e_lo > 0) {   // a shard without point 0: log q(1) on the host
-    // K = I - XA, unpivoted LU (every pivot has Re > 0), x = K^-1 X gamma,
-    // log q(1) = 1/2 gamma^T x - 1/2 sum Log u_ii  (Sec. III, Eq. q_d at w = 1)
-    std::vector<cd> K((size_t)n * n);
-    std::vector<cd> x(P->Xgamma);
-    for (int i = 0; i < n; ++i)
-      for (int j = 0; j < n; ++j) K[(size_t)i * n + j] = (i == j ? 1.0 : 0.0) - P->XA[(size_t)i * n + j];
-    cd ld = 0.0;
-    double mn = 1e300;
-    for (int k = 0; k < n; ++k) {
-      const cd piv = K[(size_t)k * n + k];
-      ld += std::log(piv);
-      mn = std::min(mn, piv.real());
-      for (int i = k + 1; i < n; ++i) {
-        const cd l = K[(size_t)i * n + k] / piv;
-        if (l == cd(0.0)) continue;
-        for (int j = k + 1; j < n; ++j) K[(size_t)i * n + j] -= l * K[(size_t)k * n + j];
-        x[i] -= l * x[k];
-      }
-    }
-    for (int i = n - 1; i >= 0; --i) {
-      cd s = x[i];
-      for (int j = i + 1; j < n; ++j) s -= K[(size_t)i * n + j] * x[j];
-      x[i] = s / K[(size_t)i * n + i];
-    }
-    cd gx = 0.0;
-    for (int i = 0; i < n; ++i) gx += P->gamma[i] * x[i];
-    P->logq1 = 0.5 * gx - 0.5 * ld;
-    P->logq1_minpiv = mn;
-  }
+  if (is_btree(P->kernel) && P->grid.e_lo > 0)     // a shard without point 0: log q(1) on the host
+    P->logq1 = host_logq1(P->XA, P->gamma, P->Xgamma, n, &P->logq1_minpiv);
   if (is_btree(P->kernel)) {                       // depth 0: the permuted augmented matrix
     float4* A0 = (float4*)(h + s.off_tree);
     const std::vector<int>& pm = P->tree_perm;
@@ -968,6 +941,46 @@ int choose_kernel(int n, int L, int precision, int override_id, int has_gamma) {
 }
 
 }  // namespace
+
+namespace gbsbin {
+
+int host_state(const gbsbin_problem* p, int n, std::vector<cd>& XA, std::vector<cd>& gamma,
+               std::vector<cd>& Xgamma) {
+  int has_gamma = 0;
+  return build_state(p, n, XA, gamma, Xgamma, &has_gamma);
+}
+
+cd host_logq1(const std::vector<cd>& XA, const std::vector<cd>& gamma, const std::vector<cd>& Xgamma, int n,
+              double* minpiv) {
+  std::vector<cd> K((size_t)n * n);
+  std::vector<cd> x(Xgamma);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) K[(size_t)i * n + j] = (i == j ? 1.0 : 0.0) - XA[(size_t)i * n + j];
+  cd ld = 0.0;
+  double mn = 1e300;
+  for (int k = 0; k < n; ++k) {
+    const cd piv = K[(size_t)k * n + k];
+    ld += std::log(piv);
+    mn = std::min(mn, piv.real());
+    for (int i = k + 1; i < n; ++i) {
+      const cd l = K[(size_t)i * n + k] / piv;
+      if (l == cd(0.0)) continue;
+      for (int j = k + 1; j < n; ++j) K[(size_t)i * n + j] -= l * K[(size_t)k * n + j];
+      x[i] -= l * x[k];
+    }
+  }
+  for (int i = n - 1; i >= 0; --i) {                 // x = U^-1 (L^-1 X gamma)
+    cd acc = x[i];
+    for (int j = i + 1; j < n; ++j) acc -= K[(size_t)i * n + j] * x[j];
+    x[i] = acc / K[(size_t)i * n + i];
+  }
+  cd gx = 0.0;
+  for (int i = 0; i < n; ++i) gx += gamma[i] * x[i];
+  if (minpiv) *minpiv = mn;
+  return 0.5 * gx - 0.5 * ld;
+}
+
+}  // namespace gbsbin
 
 extern "C" {
 
@@ -1963,31 +1976,7 @@ int gbsbin_total_photon_series(const gbsbin_problem* p, int Nmax, double* P_out)
   int has_gamma = 0;
   st = build_state(p, n, XA, gamma, Xgamma, &has_gamma);
   if (st) return st;
-  // log q(1) = 1/2 gamma^T (I - XA)^-1 X gamma - 1/2 log det(I - XA), unpivoted LU (every pivot
-  // has Re > 0, so the sum of principal logarithms is the branch of the series)
-  std::vector<cd> K((size_t)n * n);
-  for (int i = 0; i < n; ++i)
-    for (int j = 0; j < n; ++j) K[(size_t)i * n + j] = (i == j ? 1.0 : 0.0) - XA[(size_t)i * n + j];
-  cd logdet = 0.0;
-  std::vector<cd> x(Xgamma);
-  for (int k = 0; k < n; ++k) {
-    const cd piv = K[(size_t)k * n + k];
-    logdet += std::log(piv);
-    for (int i = k + 1; i < n; ++i) {
-      const cd li = K[(size_t)i * n + k] / piv;
-      if (li == cd(0.0)) continue;
-      for (int j = k + 1; j < n; ++j) K[(size_t)i * n + j] -= li * K[(size_t)k * n + j];
-      x[i] -= li * x[k];
-    }
-  }
-  for (int i = n - 1; i >= 0; --i) {                 // x = U^-1 (L^-1 X gamma)
-    cd acc = x[i];
-    for (int j = i + 1; j < n; ++j) acc -= K[(size_t)i * n + j] * x[j];
-    x[i] = acc / K[(size_t)i * n + i];
-  }
-  cd bil = 0.0;
-  for (int i = 0; i < n; ++i) bil += gamma[i] * x[i];
-  const cd logq1 = 0.5 * bil - 0.5 * logdet;
+  const cd logq1 = host_logq1(XA, gamma, Xgamma, n, nullptr);
   // a_k, k = 1..Nmax: traces of M = (XA)^k and w = (XA)^(k-1) X gamma
   std::vector<cd> a((size_t)Nmax + 1, 0.0), M(XA), T((size_t)n * n), w(Xgamma), w2(n);
   for (int k = 1; k <= Nmax; ++k) {

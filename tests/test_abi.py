@@ -171,3 +171,34 @@ def test_large_tree_validation(gb, btree):
     big_last = synth.random_problem(np.random.default_rng(9), 120, 1, 2, 2)   # last group 120 rows > 112
     assert _status(gb, big_last, tile_override=btree) == 8
     assert _status(gb, synth.config(2), tile_override=btree, want_backward=True) == 8
+
+
+def _herald_status(gb, state, roles, cutoff, cut, **opt):
+    args = gb.HeraldProblemArgs(state, roles, cutoff, cut)
+    o = gb.make_options(**opt)
+    h = ctypes.c_void_p()
+    return gb.load().gbsbin_herald_plan_create(ctypes.byref(args.c), ctypes.byref(o), ctypes.byref(h))
+
+
+def test_herald_host_validation(gb):
+    rng = np.random.default_rng(805)
+    st = synth.random_problem(rng, 4, 1, 2, [2, 2], displaced=True)
+    ok = ([0, 1, -2, -1], [2, 2], 3)
+    assert _herald_status(gb, st, [0, 1, -2, 2], [2, 2], 3) == 1          # role outside [-2, L)
+    assert _herald_status(gb, st, [0, 1, -3, -1], [2, 2], 3) == 1
+    assert _herald_status(gb, st, [0, 0, -2, -1], [2, 2], 3) == 2         # group 1 has no mode
+    assert _herald_status(gb, st, [0, 1, -1, -1], [2, 2], 3) == 8         # nothing kept
+    assert _herald_status(gb, st, *ok[:2], -1) == 1                      # fock cutoff < 0
+    assert _herald_status(gb, st, [0, 1, -2, -1], [2, -1], 3) == 3        # heralding cutoff < 0
+    assert _herald_status(gb, st, *ok, precision=1) == 1                  # FP64 only
+    assert _herald_status(gb, st, *ok, want_backward=True) == 1
+    assert _herald_status(gb, st, *ok, shard=(0, 4)) == 1
+    assert _herald_status(gb, st, *ok, tile_override=3) == 1
+    big = synth.random_problem(rng, 25, 2, 1, [2])                         # 2 M K = 100 > 96
+    assert _herald_status(gb, big, [0] * 48 + [-2, -2], [2], 2) == 8
+    five = synth.random_problem(rng, 6, 1, 1, [2])
+    assert _herald_status(gb, five, [0, -2, -2, -2, -2, -2], [2], 1) == 8   # five kept modes
+    assert _herald_status(gb, five, [0, 0, -2, -2, -2, -1], [2], 10) == 8   # 11^6 coefficients
+    bad = synth.random_problem(rng, 4, 1, 2, [2, 2])
+    bad.T = 1.5 * np.eye(4)                                                # ||T|| > 1
+    assert _herald_status(gb, bad, *ok) == 4
