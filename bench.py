@@ -696,32 +696,70 @@ def _extra_batch(gb, torch, stream, flush, steps, world):
 
 
 def _extra_n200(gb, torch, stream, flush, steps, world):
+    """n = 200 (100 modes, two groups of 50, 81 x 81 grid): the negative log-likelihood of a
+    count table, forward table + reverse pass to the adjacency adjoints, in FP32 pairs and in
+    FP64, timed with CUDA events on the launching stream (gbsbin_backward_device is
+    asynchronous), L2 flushed between steps.  The reverse pass's per-point kernel (the blocked
+    Gauss-Jordan inverse, n^3 complex multiply-adds per evaluated point) is timed by the
+    library's own events; its roofline counts 8 n^3 flops per point (the method's work)
+    against the derived peak of its pipe, and for the pairs also 64 FP32-pipe operations per
+    complex multiply-add against the FP32 issue rate.  The host-chained gradient to the
+    physical parameters (gbsbin_backward, synchronous) is timed by wall clock beside it."""
     out = {}
-    # n = 200: 100 modes, 2 groups of 50, 81 x 81 grid; NLL of a count table, forward + gradient
     prob = synth.config(4)
-    with gb.Plan(prob, precision=0, want_backward=True) as p:
-        t = torch.empty(p.shape, dtype=torch.float64, device="cuda")
-        gb.gbsbin_execute(p.handle, t, stream)
-        torch.cuda.synchronize()
-        rng = np.random.default_rng(0)
-        Pn = np.clip(t.cpu().numpy(), 1e-300, None)
-        counts = torch.from_numpy(rng.multinomial(10 ** 6, (Pn / Pn.sum()).reshape(-1)).reshape(Pn.shape)
-                                  .astype(np.float64)).cuda()
-
-        def step():
+    n = prob.n
+    issue32 = SMS * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
+    peak32 = 2 * issue32
+    peak64 = SMS * FP64_FMA_PER_SM_CLK * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    rng = np.random.default_rng(0)
+    counts = None
+    for precision, name in ((1, "fp32_pairs"), (0, "fp64")):
+        with gb.Plan(prob, precision=precision, want_backward=True, want_timing=True) as p:
+            t = torch.empty(p.shape, dtype=torch.float64, device="cuda")
+            S = torch.empty((n, n), dtype=torch.complex128, device="cuda")
+            g = torch.empty((n,), dtype=torch.complex128, device="cuda")
             gb.gbsbin_execute(p.handle, t, stream)
-            dLdP = -counts / t
-            p.backward(dLdP, stream, want=("r", "T"))
-        step()
-        t0 = time.perf_counter()
-        for _ in range(steps):
-            step()
-        torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        out["M100_K1_L2_N80_n200_gradient"] = {"ms_per_forward_backward": dt / steps * 1e3,
-                                               "points_per_s": world * prob.n_points * steps / dt,
-                                               "precision": "fp64", "timer": "wall clock (backward syncs)"}
-    return out
+            torch.cuda.synchronize()
+            if counts is None:
+                Pn = np.clip(t.cpu().numpy(), 1e-300, None)
+                counts = torch.from_numpy(rng.multinomial(10 ** 6, (Pn / Pn.sum()).reshape(-1))
+                                          .reshape(Pn.shape).astype(np.float64)).cuda()
+            dLdP = torch.empty_like(t)
+
+            def step():
+                gb.gbsbin_execute(p.handle, t, stream)
+                with torch.cuda.stream(stream):
+                    torch.div(-counts, t, out=dLdP)
+                gb.gbsbin_backward_device(p.handle, dLdP, S, g, stream)
+            for _ in range(2):
+                step()
+            ms = _timed(torch, stream, flush, steps, step) / steps
+            st, d = p.diagnostics(stream)
+            bms = d["backward_kernel_ms"]
+            flops = 8.0 * n ** 3 * d["n_evaluated"]
+            peak, pname = (peak32, "derived FP32") if precision else (peak64, "derived FP64")
+            ach = flops / (bms * 1e-3) / 1e12
+            entry = {"ms_per_forward_backward": ms, "points_per_s": world * prob.n_points / (ms * 1e-3),
+                     "backward_kernel_ms": bms, "forward_point_kernel_ms": d["point_kernel_ms"],
+                     "kernel": "k_backward_gj (blocked Gauss-Jordan, recomputed per point)",
+                     "timer": "CUDA events on the launching stream, L2 flushed",
+                     "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                                  "frac": ach / peak, "peak_source": pname,
+                                  "work": "8 n^3 flops per evaluated point (inverse)"}}
+            if precision:
+                ops = 64.0 * n ** 3 * d["n_evaluated"] / (bms * 1e-3) / 1e12
+                entry["issued"] = {"achieved": ops, "peak": issue32, "unit": "T ops/s", "frac": ops / issue32,
+                                   "work": "complex multiply-adds x 64 FP32-pipe operations (pairs)"}
+            t0 = time.perf_counter()
+            wsteps = max(1, steps // 2)
+            for _ in range(wsteps):
+                gb.gbsbin_execute(p.handle, t, stream)
+                with torch.cuda.stream(stream):
+                    torch.div(-counts, t, out=dLdP)
+                p.backward(dLdP, stream, want=("r", "T"))
+            entry["ms_per_forward_backward_host_chain"] = (time.perf_counter() - t0) / wsteps * 1e3
+            out[name] = entry
+    return {"M100_K1_L2_N80_n200_gradient": out}
 
 
 def _sources_hash(paths):

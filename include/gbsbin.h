@@ -78,8 +78,8 @@ typedef struct {
   int tile_override;      /* 0 = automatic kernel choice; otherwise a gbsbin_kernel id      */
   int want_timing;        /* nonzero: execute records CUDA events around the point kernel on
                              its stream; gbsbin_diagnostics reports the elapsed time         */
-  int want_backward;      /* nonzero: allocate what gbsbin_backward needs; FP64 executes then
-                             keep the LU factors and exponent solutions of every point      */
+  int want_backward;      /* nonzero: allocate what gbsbin_backward needs (one n x n
+                             workspace per SM; no per-point storage)                       */
   long long shard_begin;  /* shard_end > 0: this plan evaluates only the evaluated points    */
   long long shard_end;    /* e in [shard_begin, shard_end) of the half grid (plus point 0,
                              w = 1, for the normalisation) and returns the PARTIAL table of
@@ -144,6 +144,8 @@ typedef struct {
                                    gbsbin_fock_plan_set_transfer) copies from host to device    */
   int launches;              /* kernel launches of the last execute (point stage, inverse DFT
                                 with its diagnostics), 0 before the first                       */
+  double backward_kernel_ms; /* duration of the last reverse pass's per-point kernel (plans with
+                                want_timing and want_backward), else 0                          */
 } gbsbin_diag;
 
 typedef enum {
@@ -314,13 +316,27 @@ typedef struct {
  * Reverse pass for the plan's current state (no counterpart in the paper, which leaves
  * differentiability to future work; the adjoint follows from d log det A = tr(A^{-1} dA)).
  * dL_dP: device, table_size doubles, dL/dP(b) for the table of the last execute.  Needs a
- * plan created with want_backward.  It reuses the LU factors stored by the last FP64
- * execute of the current state; otherwise (FP32R plan, or state changed since) it first
- * re-evaluates the grid in FP64 with the factors kept.  Synchronises `stream`.
+ * plan created with want_backward.  Nothing of the forward is kept but log q at the
+ * evaluated points: each point's matrix M = conj(D(w)) - XA is rebuilt and inverted in place
+ * (blocked Gauss-Jordan without pivoting, n^3 complex multiply-adds per point, in a per-SM
+ * workspace of n^2 entries) in FP64 for GBSBIN_FP64 plans and in pairs of FP32 (~46 bits)
+ * for GBSBIN_FP32_REFINE plans; if the state changed since the last execute, an execute
+ * (into the plan's own table) runs first.  Synchronises `stream`.
  * Errors: ERR_ARG (NULL plan/dL_dP/g, plan without want_backward, physical gradients
- * requested for a direct-covariance problem), ERR_CUDA, ERR_NOMEM.
+ * requested for a direct-covariance problem), ERR_NUMERIC (a non-finite adjoint),
+ * ERR_CUDA, ERR_NOMEM.
  */
 int gbsbin_backward(gbsbin_plan* plan, const double* dL_dP, gbsbin_grads* g, void* stream);
+
+/*
+ * The same reverse pass up to the adjoints of the adjacency data, on the device and
+ * asynchronous: S = dL_dXA (n*n, row-major) and s = dL_dgamma (n), device buffers, such that
+ * dL = Re( sum_ij S_ij dXA_ij + sum_i s_i dgamma_i ) with the entries of XA = I - Sigma^{-1}
+ * and gamma treated as independent (the gradient in the d/dRe + i d/dIm convention above is
+ * conj(S), conj(s)); the caller chains them further.  Errors: ERR_ARG, ERR_CUDA.
+ */
+int gbsbin_backward_device(gbsbin_plan* plan, const double* dL_dP, gbsbin_complex* dL_dXA, gbsbin_complex* dL_dgamma,
+                           void* stream);
 
 /*
  * Measured autotuning of the point kernel (no counterpart in the paper): for matrix size

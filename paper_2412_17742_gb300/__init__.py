@@ -30,7 +30,7 @@ EXPORTED = ["gbsbin_default_options", "gbsbin_plan_create", "gbsbin_plan_set_sta
             "gbsbin_plan_table_size", "gbsbin_execute", "gbsbin_execute_host", "gbsbin_execute_host_async",
             "gbsbin_diagnostics",
             "gbsbin_strerror", "gbsbin_alu_peak", "gbsbin_read_points", "gbsbin_table_from_logq_noalloc",
-            "gbsbin_backward", "gbsbin_autotune", "gbsbin_batch_create", "gbsbin_batch_execute",
+            "gbsbin_backward", "gbsbin_backward_device", "gbsbin_autotune", "gbsbin_batch_create", "gbsbin_batch_execute",
             "gbsbin_batch_capture_graph", "gbsbin_batch_replay", "gbsbin_batch_table_size",
             "gbsbin_batch_diagnostics", "gbsbin_batch_read_points", "gbsbin_batch_destroy", "gbsbin_moments",
             "gbsbin_fock_plan_create", "gbsbin_fock_plan_set_transfer", "gbsbin_fock_plan_table_size",
@@ -80,7 +80,8 @@ class gbsbin_diag(ctypes.Structure):
                 ("n_bad_points", ctypes.c_longlong), ("n_points", ctypes.c_longlong),
                 ("n_evaluated", ctypes.c_longlong), ("table_size", ctypes.c_longlong), ("n", ctypes.c_int),
                 ("kernel", ctypes.c_int), ("log_q1_re", ctypes.c_double), ("point_kernel_ms", ctypes.c_double),
-                ("state_upload_bytes", ctypes.c_longlong), ("launches", ctypes.c_int)]
+                ("state_upload_bytes", ctypes.c_longlong), ("launches", ctypes.c_int),
+                ("backward_kernel_ms", ctypes.c_double)]
 
 
 class gbsbin_fock_problem(ctypes.Structure):
@@ -134,6 +135,8 @@ def load():
     lib.gbsbin_read_points.argtypes = [vp, vp, vp, vp]
     lib.gbsbin_table_from_logq_noalloc.argtypes = [ctypes.c_int, _ip, ctypes.c_int, vp, vp, vp]
     lib.gbsbin_backward.argtypes = [vp, vp, ctypes.POINTER(gbsbin_grads), vp]
+    lib.gbsbin_backward_device.argtypes = [vp, vp, vp, vp, vp]
+    lib.gbsbin_backward_device.restype = ctypes.c_int
     lib.gbsbin_autotune.argtypes = [ctypes.c_int, ctypes.c_int, _ip, _ip, _dp]
     lib.gbsbin_batch_create.argtypes = [ctypes.POINTER(gbsbin_problem), ctypes.c_int, ctypes.POINTER(gbsbin_options),
                                         ctypes.c_int, ctypes.POINTER(vp)]
@@ -354,6 +357,13 @@ def gbsbin_backward(plan, dL_dP, M, K, n, stream=None, want=("r", "T", "alpha", 
     return res
 
 
+def gbsbin_backward_device(plan, dL_dP, dL_dXA, dL_dgamma, stream=None):
+    """Asynchronous reverse pass to the adjacency adjoints S (n x n) and s (n), device buffers
+    of complex128: dL = Re(sum S_ij dXA_ij + sum s_i dgamma_i)."""
+    _check(load().gbsbin_backward_device(plan, _ptr(dL_dP), _ptr(dL_dXA), _ptr(dL_dgamma), _stream_handle(stream)),
+           "gbsbin_backward_device")
+
+
 def gbsbin_autotune(n, precision):
     """Returns (kernel id, points per CTA, microseconds per evaluated point)."""
     k, p, us = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
@@ -479,6 +489,14 @@ class Plan:
     def backward(self, dL_dP, stream=None, want=("r", "T", "alpha", "V", "sigma1", "zbar")):
         """Gradients of L for the plan's current state given dL/dP (CUDA float64 tensor)."""
         return gbsbin_backward(self.handle, dL_dP, self.M, self.K, self.n, stream, want)
+
+    def backward_device(self, dL_dP, stream=None):
+        """Adjacency adjoints (S, s) as new CUDA complex128 tensors, asynchronously."""
+        import torch
+        S = torch.empty((self.n, self.n), dtype=torch.complex128, device="cuda")
+        g = torch.empty((self.n,), dtype=torch.complex128, device="cuda")
+        gbsbin_backward_device(self.handle, dL_dP, S, g, stream)
+        return S, g
 
     def table(self, stream=None):
         """Execute into a new CUDA float64 tensor shaped (N_1+1, ..., N_L+1)."""

@@ -16,12 +16,19 @@
 //   d log q = 1/2 sum_ij (y_i x_j + (M^{-1})_ji) dXA_ij + 1/2 (x + X y)^T dgamma
 // so dL/dXA (bilinear) = 1/2 sum_k beta_k (y_k x_k^T + M_k^{-T}) and
 //    dL/dgamma        = 1/2 sum_k beta_k (x_k + X y_k).
-// M_k^{-1} comes from the LU factors the FP64 forward stored: U^{-1} column by column,
-// then X L = U^{-1} from the right.  All FP64; one CTA per SM, each accumulating its
-// points into its own partial, reduced over CTAs in a fixed order (deterministic).
+// Nothing of the forward is stored but log q: each point's M_k is rebuilt from -XA and the
+// point's roots and inverted in place by a blocked Gauss-Jordan elimination without pivoting
+// (its pivots are those of the forward's unpivoted LU), nb pivots per step: the nb x nb
+// diagonal block inverted in shared memory, the block's rows multiplied by that inverse, and
+// a rank-nb update of the rest streamed through registers in 4 x 4 tiles - n^3 complex
+// multiply-adds per point, the same as LU plus inverse from stored factors, in the plan's
+// arithmetic: FP64, or pairs of FP32 (~46 bits) on the FMA pipe for FP32-refine plans.  One
+// CTA per SM, its matrix in an L2-resident slot, each accumulating its points into its own
+// partials, reduced over CTAs in FP64 in a fixed order (deterministic).
 #include <cuda_runtime.h>
 
 #include "gbsbin_device.cuh"
+#include "gbsbin_df.cuh"
 #include "gbsbin_internal.h"
 
 namespace gbsbin {
@@ -110,94 +117,186 @@ __global__ void k_adj_beta0(double2* __restrict__ a, long long n) {
   }
 }
 
-// Per point: W = M^{-1} from the stored L\U; accumulate into this CTA's partials.
-template <int NT>
-__global__ void __launch_bounds__(NT) k_backward_points(BackwardArgs b) {
+// Per point: W = M^{-1} by blocked Gauss-Jordan; accumulate into this CTA's partials (S
+// transposed: ST[j][i] = S[i][j], so that the term M^{-T} reads W row by row).
+constexpr int kGjThreads = 256;
+constexpr int kGjTile = 4;
+
+template <class Ar>
+__global__ void __launch_bounds__(kGjThreads) k_backward_gj(BackwardArgs b) {
+  using E = typename Ar::E;
   extern __shared__ __align__(16) unsigned char smem[];
-  const int n = b.n, tid = threadIdx.x;
-  double2* vec = (double2*)smem;
-  double2* t_i = vec;          // n: scratch per row
-  double2* lcol = vec + n;     // n: saved L column
-  double2* y = vec + 2 * n;    // n
-  double2* x = vec + 3 * n;    // n
-  double2* W = (double2*)((char*)b.ws + (size_t)blockIdx.x * (size_t)b.ws_slot_bytes);
-  double2* S = b.partS + (size_t)blockIdx.x * n * n;
-  double2* sg = b.partg + (size_t)blockIdx.x * n;
-  for (int t = tid; t < n * n; t += NT) S[t] = make_double2(0.0, 0.0);
-  for (int t = tid; t < n; t += NT) sg[t] = make_double2(0.0, 0.0);
-  __syncthreads();
+  const int n = b.n, nbm = b.nb, tid = threadIdx.x, NT = kGjThreads;
+  const GridDesc& g = b.grid;
+  E* Pc = reinterpret_cast<E*>(smem);                 // n x nbm: W[:, B], rows of B zero
+  E* Rx = Pc + (size_t)n * nbm;                       // nbm x n: inv(W_BB) W[B, :]
+  E* Dg = Rx + (size_t)nbm * n;                       // bs x bs: W_BB, inverted in place
+  E* gE = Dg + nbm * nbm;                             // n: gamma
+  E* xgE = gE + n;                                    // n: X gamma
+  E* xv = xgE + n;                                    // n: x = W X gamma
+  E* yv = xv + n;                                     // n: y = W^T gamma
+  double2* wr = reinterpret_cast<double2*>(yv + n);   // L: this point's roots
+  E* W = reinterpret_cast<E*>(reinterpret_cast<char*>(b.ws) + (size_t)blockIdx.x * (size_t)b.ws_slot_bytes);
+  E* ST = reinterpret_cast<E*>(b.partS) + (size_t)blockIdx.x * n * n;
+  E* sg = reinterpret_cast<E*>(b.partg) + (size_t)blockIdx.x * n;
+  for (int t = tid; t < n * n; t += NT) ST[t] = Ar::zero();
+  for (int t = tid; t < n; t += NT) {
+    sg[t] = Ar::zero();
+    gE[t] = Ar::from(b.gamma[t]);
+    xgE[t] = Ar::from(b.Xgamma[t]);
+  }
+  const int tcols = (n + kGjTile - 1) / kGjTile, ntiles = tcols * tcols;
 
   for (long long e = blockIdx.x; e < b.n_eval; e += gridDim.x) {
     const double2 beta = b.beta[e];
     if (beta.x == 0.0 && beta.y == 0.0) continue;  // no contribution
-    const double2* F = b.lu_store + (size_t)e * n * n;
-    for (int t = tid; t < n * n; t += NT) W[t] = F[t];
-    for (int t = tid; t < n; t += NT) x[t] = b.x_store[(size_t)e * n + t];
+    if (tid < g.L) wr[tid] = grid_root(b.tw, g, tid, point_digit(e, g, tid));
     __syncthreads();
-    // U^{-1} in place, column by column: Uinv[0:j, j] = -Uinv[0:j, 0:j] U[0:j, j] / u_jj
-    for (int j = 0; j < n; ++j) {
-      const double2 inv = crecip(W[(size_t)j * n + j]);
-      for (int i = tid; i < j; i += NT) {
-        double2 s = make_double2(0.0, 0.0);
-        for (int k = i; k < j; ++k) {
-          double2 a = W[(size_t)i * n + k], u = W[(size_t)k * n + j];
-          s.x = fma(a.x, u.x, fma(-a.y, u.y, s.x));
-          s.y = fma(a.x, u.y, fma(a.y, u.x, s.y));
+    for (int t = tid; t < n * n; t += NT) {          // M = conj(D) - XA
+      const int i = t / n;
+      double2 v = b.NXA[t];
+      if (i * n + i == t) {
+        const double2 d = wr[b.label[i]];
+        v.x += d.x;
+        v.y -= d.y;
+      }
+      W[t] = Ar::from(v);
+    }
+    __syncthreads();
+    for (int K = 0; K < n; K += nbm) {
+      const int bs = min(nbm, n - K);
+      for (int t = tid; t < n * bs; t += NT) {
+        const int i = t / bs, c = t - (t / bs) * bs;
+        Pc[i * nbm + c] = (i >= K && i < K + bs) ? Ar::zero() : W[(size_t)i * n + K + c];
+      }
+      for (int t = tid; t < bs * n; t += NT) Rx[t] = W[(size_t)K * n + t];   // rows K .. K + bs - 1
+      if (tid < bs * bs) Dg[tid] = W[(size_t)(K + tid / bs) * n + K + tid % bs];
+      __syncthreads();
+      // inv(W_BB) by unpivoted Gauss-Jordan, one element per thread
+      for (int k = 0; k < bs; ++k) {
+        E nv = Ar::zero();
+        if (tid < bs * bs) {
+          const int i = tid / bs, j = tid - (tid / bs) * bs;
+          const E p = Ar::recip(Dg[k * bs + k]);
+          if (i == k && j == k) nv = p;
+          else if (i == k) nv = Ar::mul(Dg[k * bs + j], p);
+          else if (j == k) nv = Ar::neg(Ar::mul(Dg[i * bs + k], p));
+          else nv = Ar::fms(Dg[tid], Ar::mul(Dg[i * bs + k], p), Dg[k * bs + j]);
         }
-        t_i[i] = s;
+        __syncthreads();
+        if (tid < bs * bs) Dg[tid] = nv;
+        __syncthreads();
+      }
+      // Rx = inv(W_BB) W[B, :] outside the block's columns, inv(W_BB) on them
+      for (int j = tid; j < n; j += NT) {
+        if (j >= K && j < K + bs) {
+          for (int r = 0; r < bs; ++r) Rx[r * n + j] = Dg[r * bs + (j - K)];
+          continue;
+        }
+        E col[GBSBIN_BWD_MAX_NB];
+#pragma unroll
+        for (int c = 0; c < GBSBIN_BWD_MAX_NB; ++c)
+          if (c < bs) col[c] = Rx[c * n + j];
+        for (int r = 0; r < bs; ++r) {
+          E acc = Ar::zero();
+#pragma unroll
+          for (int c = 0; c < GBSBIN_BWD_MAX_NB; ++c)
+            if (c < bs) acc = Ar::fma(Dg[r * bs + c], col[c], acc);
+          Rx[r * n + j] = acc;
+        }
       }
       __syncthreads();
-      for (int i = tid; i < j; i += NT) {
-        double2 s = cmul(t_i[i], inv);
-        W[(size_t)i * n + j] = make_double2(-s.x, -s.y);
+      // W[i][j] = (j in B ? 0 : W[i][j]) - sum_c Pc[i][c] Rx[c][j] for i outside B; Rx[i - K][j]
+      // for the block's rows
+      for (int tt = tid; tt < ntiles; tt += NT) {
+        const int i0 = (tt / tcols) * kGjTile, j0 = (tt - (tt / tcols) * tcols) * kGjTile;
+        E acc[kGjTile][kGjTile];
+#pragma unroll
+        for (int r = 0; r < kGjTile; ++r)
+#pragma unroll
+          for (int q = 0; q < kGjTile; ++q) {
+            const int i = i0 + r, j = j0 + q;
+            acc[r][q] = (i < n && j < n && (j < K || j >= K + bs)) ? W[(size_t)i * n + j] : Ar::zero();
+          }
+        for (int c = 0; c < bs; ++c) {
+          E pv[kGjTile], rv[kGjTile];
+#pragma unroll
+          for (int r = 0; r < kGjTile; ++r) pv[r] = i0 + r < n ? Pc[(i0 + r) * nbm + c] : Ar::zero();
+#pragma unroll
+          for (int q = 0; q < kGjTile; ++q) rv[q] = j0 + q < n ? Rx[c * n + j0 + q] : Ar::zero();
+#pragma unroll
+          for (int r = 0; r < kGjTile; ++r)
+#pragma unroll
+            for (int q = 0; q < kGjTile; ++q) acc[r][q] = Ar::fms(acc[r][q], pv[r], rv[q]);
+        }
+#pragma unroll
+        for (int r = 0; r < kGjTile; ++r)
+#pragma unroll
+          for (int q = 0; q < kGjTile; ++q) {
+            const int i = i0 + r, j = j0 + q;
+            if (i >= n || j >= n) continue;
+            W[(size_t)i * n + j] = (i >= K && i < K + bs) ? Rx[(i - K) * n + j] : acc[r][q];
+          }
       }
-      if (tid == 0) W[(size_t)j * n + j] = inv;
       __syncthreads();
     }
-    // X L = Uinv, columns from the right: X[:, j] = Uinv[:, j] - sum_{k > j} X[:, k] L[k][j]
-    for (int j = n - 2; j >= 0; --j) {
-      for (int k = j + 1 + tid; k < n; k += NT) lcol[k] = W[(size_t)k * n + j];
-      __syncthreads();
-      for (int i = tid; i < n; i += NT) {
-        double2 s = i <= j ? W[(size_t)i * n + j] : make_double2(0.0, 0.0);
-        for (int k = j + 1; k < n; ++k) s = cfnma(s, W[(size_t)i * n + k], lcol[k]);
-        W[(size_t)i * n + j] = s;
+    // x = W X gamma (a warp per row), y = W^T gamma (a thread per column)
+    {
+      const int lane = tid & 31, warp = tid >> 5;
+      for (int i = warp; i < n; i += NT / 32) {
+        E acc = Ar::zero();
+        for (int j = lane; j < n; j += 32) acc = Ar::fma(W[(size_t)i * n + j], xgE[j], acc);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc = Ar::add(acc, shfl_xor(acc, o));
+        if (lane == 0) xv[i] = acc;
       }
-      __syncthreads();
-    }
-    // y = M^{-T} gamma
-    for (int i = tid; i < n; i += NT) {
-      double2 s = make_double2(0.0, 0.0);
-      for (int j = 0; j < n; ++j) {
-        double2 m = W[(size_t)j * n + i], g = b.gamma[j];
-        s.x = fma(m.x, g.x, fma(-m.y, g.y, s.x));
-        s.y = fma(m.x, g.y, fma(m.y, g.x, s.y));
+      for (int j = tid; j < n; j += NT) {
+        E acc = Ar::zero();
+        for (int i = 0; i < n; ++i) acc = Ar::fma(W[(size_t)i * n + j], gE[i], acc);
+        yv[j] = acc;
       }
-      y[i] = s;
     }
     __syncthreads();
-    // S += beta/2 (y x^T + M^{-T});  sg += beta/2 (x + X y)
-    const double2 hb = cscale(beta, 0.5);
+    // ST[j][i] += beta/2 (y_i x_j + W[j][i]);  sg += beta/2 (x + X y)
+    const E hb = Ar::from(make_double2(0.5 * beta.x, 0.5 * beta.y));
     for (int t = tid; t < n * n; t += NT) {
-      const int i = t / n, j = t - i * n;
-      double2 v = cadd(cmul(y[i], x[j]), W[(size_t)j * n + i]);
-      S[t] = cadd(S[t], cmul(hb, v));
+      const int j = t / n, i = t - (t / n) * n;
+      ST[t] = Ar::fma(hb, Ar::fma(yv[i], xv[j], W[t]), ST[t]);
     }
     const int h = n / 2;
-    for (int i = tid; i < n; i += NT) sg[i] = cadd(sg[i], cmul(hb, cadd(x[i], y[i < h ? i + h : i - h])));
+    for (int i = tid; i < n; i += NT) sg[i] = Ar::fma(hb, Ar::add(xv[i], yv[i < h ? i + h : i - h]), sg[i]);
     __syncthreads();
   }
 }
 
-// outS[t] = sum over CTAs c of partS[c][t] (fixed order)
-__global__ void k_backward_reduce(const double2* __restrict__ part, int nparts, long long len, double2* __restrict__ out) {
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < len;
+// outS[i][j] = sum over CTAs c of ST_c[j][i], outg[i] = sum_c sg_c[i] (FP64, fixed order)
+template <class Ar>
+__global__ void k_backward_reduce(const void* __restrict__ partS, const void* __restrict__ partg, int nparts, int n,
+                                  double2* __restrict__ outS, double2* __restrict__ outg) {
+  using E = typename Ar::E;
+  const E* pS = reinterpret_cast<const E*>(partS);
+  const E* pg = reinterpret_cast<const E*>(partg);
+  const long long nn = (long long)n * n;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nn + n;
        t += (long long)gridDim.x * blockDim.x) {
     double2 s = make_double2(0.0, 0.0);
-    for (int c = 0; c < nparts; ++c) s = cadd(s, part[(size_t)c * len + t]);
-    out[t] = s;
+    if (t < nn) {
+      const long long i = t / n, j = t - (t / n) * n;
+      for (int c = 0; c < nparts; ++c) s = cadd(s, Ar::to(pS[(size_t)c * nn + j * n + i]));
+      outS[t] = s;
+    } else {
+      const long long i = t - nn;
+      for (int c = 0; c < nparts; ++c) s = cadd(s, Ar::to(pg[(size_t)c * n + i]));
+      outg[i] = s;
+    }
   }
 }
+
+size_t backward_smem_bytes(int n, int nb) {
+  return (size_t)16 * ((size_t)2 * n * nb + (size_t)nb * nb + 4 * (size_t)n) + sizeof(double2) * GBSBIN_MAX_L;
+}
+
+int backward_block(int n) { return n <= 320 ? GBSBIN_BWD_MAX_NB : GBSBIN_BWD_MAX_NB / 2; }
 
 static unsigned nblk(long long work, int threads) {
   long long b = (work + threads - 1) / threads;
@@ -248,16 +347,24 @@ cudaError_t launch_backward(const BackwardArgs& b, const double* dLdP, cudaStrea
   if ((err = cudaGetLastError()) != cudaSuccess) return err;
   BackwardArgs bb = b;
   bb.beta = nxt;
-  const int NT = 256;
-  size_t smem = (size_t)4 * b.n * sizeof(double2);
-  err = cudaFuncSetAttribute(k_backward_points<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (err != cudaSuccess) return err;
-  k_backward_points<NT><<<b.nparts, NT, smem, s>>>(bb);
+  const size_t smem = backward_smem_bytes(b.n, b.nb);
+  if (b.ev0 && (err = cudaEventRecord(b.ev0, s)) != cudaSuccess) return err;
+  if (b.df) {
+    err = cudaFuncSetAttribute(k_backward_gj<ArDF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    k_backward_gj<ArDF><<<b.nparts, kGjThreads, smem, s>>>(bb);
+  } else {
+    err = cudaFuncSetAttribute(k_backward_gj<ArF64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    k_backward_gj<ArF64><<<b.nparts, kGjThreads, smem, s>>>(bb);
+  }
   if ((err = cudaGetLastError()) != cudaSuccess) return err;
-  const long long nn = (long long)b.n * b.n;
-  k_backward_reduce<<<nblk(nn, 256), 256, 0, s>>>(b.partS, b.nparts, nn, b.outS);
-  if ((err = cudaGetLastError()) != cudaSuccess) return err;
-  k_backward_reduce<<<nblk(b.n, 256), 256, 0, s>>>(b.partg, b.nparts, b.n, b.outg);
+  if (b.ev1 && (err = cudaEventRecord(b.ev1, s)) != cudaSuccess) return err;
+  const long long work = (long long)b.n * b.n + b.n;
+  if (b.df)
+    k_backward_reduce<ArDF><<<nblk(work, 256), 256, 0, s>>>(b.partS, b.partg, b.nparts, b.n, b.outS, b.outg);
+  else
+    k_backward_reduce<ArF64><<<nblk(work, 256), 256, 0, s>>>(b.partS, b.partg, b.nparts, b.n, b.outS, b.outg);
   return cudaGetLastError();
 }
 

@@ -72,10 +72,12 @@ struct gbsbin_plan {
   std::vector<double> r;
   std::vector<cd> T, alpha, V, zbar;
   bool has_alpha = false, has_V = false;
-  double2 *d_lu = nullptr, *d_xs = nullptr, *d_adjA = nullptr, *d_adjB = nullptr, *d_bws = nullptr;
+  double2 *d_adjA = nullptr, *d_adjB = nullptr, *d_bws = nullptr;
   double2 *d_partS = nullptr, *d_partg = nullptr, *d_outS = nullptr, *d_outg = nullptr;
-  bool saved_valid = false;           // d_lu / d_xs hold the current state's factors
-  long long bws_slot_bytes = 0;       // per-SM slot of d_bws (reverse pass and FP64 workspace)
+  bool logq_valid = false;            // d_logq holds the current state's log q (an execute ran)
+  long long bws_slot_bytes = 0;       // per-SM slot of d_bws (the reverse pass's matrices)
+  cudaEvent_t ev_b0 = nullptr, ev_b1 = nullptr;   // want_timing: around the reverse per-point kernel
+  bool backward_ran = false;
   // pinned staging for uploads
   // two pinned staging buffers used in turn, each with the event recorded after the copy
   // that last read it: an upload waits only for the copy two uploads back
@@ -348,7 +350,9 @@ void free_device(gbsbin_plan* P) {
   }
   if (P->ev0) cudaEventDestroy(P->ev0);
   if (P->ev1) cudaEventDestroy(P->ev1);
-  void* bw[] = {P->d_lu, P->d_xs, P->d_adjA, P->d_adjB, P->d_bws, P->d_partS, P->d_partg, P->d_outS, P->d_outg};
+  if (P->ev_b0) cudaEventDestroy(P->ev_b0);
+  if (P->ev_b1) cudaEventDestroy(P->ev_b1);
+  void* bw[] = {P->d_adjA, P->d_adjB, P->d_bws, P->d_partS, P->d_partg, P->d_outS, P->d_outg};
   for (void* q : bw)
     if (q) cudaFree(q);
 }
@@ -417,6 +421,7 @@ int upload_hessenberg(gbsbin_plan* P, cudaStream_t stream);
 int upload_state(gbsbin_plan* P, cudaStream_t stream) {
   const int n = P->n;
   const bool tree = is_tree(P->kernel) || is_btree(P->kernel);
+  const bool per_point = !tree || P->opt.want_backward;   // the reverse pass reads -XA, gamma, X gamma
   Stage s = stage_layout(n, tree_region_slots(n, P->kernel));
   // the copy that last read this staging buffer (two uploads back) must have finished
   const int sb = P->stage_next;
@@ -434,15 +439,16 @@ int upload_state(gbsbin_plan* P, cudaStream_t stream) {
   float2* ghi = (float2*)(h + s.off_ghi);
   float2* glo = (float2*)(h + s.off_glo);
   longlong2* XAfix = (longlong2*)(h + s.off_XAfix);
-  // the per-point kernels' copies of the state (tree plans read only their own region)
+  // the per-point kernels' copies of the state (tree plans read only their own region, and
+  // their reverse pass the FP64 copies)
   const double fix_scale = std::ldexp(1.0, GBSBIN_FIX_BITS);
-  for (size_t q = 0; !tree && q < (size_t)n * n; ++q) {  // the kernels use -XA
+  for (size_t q = 0; per_point && q < (size_t)n * n; ++q) {  // the kernels use -XA
     XA[q] = make_double2(-P->XA[q].real(), -P->XA[q].imag());
     split(-P->XA[q], &XAhi[q], &XAlo[q]);
     // |XA_ij| <= ||XA||_2 < 1 for a physical state, so the scaled value fits in 63 bits
     XAfix[q] = make_longlong2(std::llrint(-P->XA[q].real() * fix_scale), std::llrint(-P->XA[q].imag() * fix_scale));
   }
-  for (int i = 0; !tree && i < n; ++i) {
+  for (int i = 0; per_point && i < n; ++i) {
     g[i] = make_double2(P->gamma[i].real(), P->gamma[i].imag());
     Xg[i] = make_double2(P->Xgamma[i].real(), P->Xgamma[i].imag());
     split(P->Xgamma[i], &Xghi[i], &Xglo[i]);
@@ -540,8 +546,9 @@ int upload_state(gbsbin_plan* P, cudaStream_t stream) {
       P->tree_logq0 = -0.5 * (std::log(std::abs(prod)) + e0 * 0.693147180559945309417232121458);
     }
   }
-  // the device block has the staging layout: one copy (of the tree region alone for trees)
-  const size_t off = tree ? s.off_tree : 0;
+  // the device block has the staging layout: one copy (of the tree region alone for trees
+  // without a reverse pass)
+  const size_t off = per_point ? 0 : s.off_tree;
   P->upload_bytes = (long long)(s.total - off);
   e = cudaMemcpyAsync(P->d_state + off, h + off, s.total - off, cudaMemcpyHostToDevice, stream);
   if (e != cudaSuccess || cudaEventRecord(P->ev_stage[sb], stream) != cudaSuccess) return GBSBIN_ERR_CUDA;
@@ -664,41 +671,6 @@ std::vector<cd> transpose(const std::vector<cd>& A, int n) {
 
 // Launch the FP64 point kernel for the current state with the LU factors and exponent
 // solutions kept for the reverse pass.
-int evaluate_fp64_with_factors(gbsbin_plan* P, cudaStream_t s) {
-  const int n = P->n;
-  int kernel = points_per_cta(GBSBIN_KERNEL_SMEM_FP64, n, P->L) > 0 ? GBSBIN_KERNEL_SMEM_FP64 : GBSBIN_KERNEL_GMEM_FP64;
-  PointArgs a{};
-  a.n = n;
-  a.has_gamma = P->has_gamma;
-  a.P = kernel == GBSBIN_KERNEL_GMEM_FP64 ? 1 : points_per_cta(kernel, n, P->L);
-  a.logP = 0;
-  while ((1 << a.logP) < a.P) ++a.logP;
-  a.NXA = P->d_NXA;
-  a.Xgamma = P->d_Xgamma;
-  a.gamma = P->d_gamma;
-  a.NXA_hi = P->d_NXA_hi;
-  a.NXA_lo = P->d_NXA_lo;
-  a.NXA_fix = P->d_NXA_fix;
-  a.Xg_hi = P->d_Xg_hi;
-  a.Xg_lo = P->d_Xg_lo;
-  a.g_hi = P->d_g_hi;
-  a.g_lo = P->d_g_lo;
-  a.label = P->d_label;
-  a.tw = P->d_tw;
-  a.grid = P->grid;
-  a.logq = P->d_logq;
-  a.minpiv = P->d_minpiv;
-  a.lu_store = P->d_lu;
-  a.x_store = P->d_xs;
-  if (kernel == GBSBIN_KERNEL_GMEM_FP64) {  // the reverse-pass slots double as the forward workspace
-    a.gws = P->d_bws;
-    a.gws_slot_bytes = P->bws_slot_bytes;
-  }
-  if (launch_points(a, kernel, P->num_sms, s) != cudaSuccess) return GBSBIN_ERR_CUDA;
-  P->saved_valid = true;
-  return GBSBIN_OK;
-}
-
 // The blocked FP32 + refinement kernel, with its trace updates on the CUDA cores or on the
 // tensor cores.
 inline bool is_blk(int kernel) { return kernel == GBSBIN_KERNEL_BLK_FP32R || kernel == GBSBIN_KERNEL_BLK_TC_FP32R; }
@@ -1086,7 +1058,7 @@ static int plan_create_impl(const gbsbin_problem* p, const gbsbin_options* o, gb
   const bool sharded = opt.shard_end != 0 || opt.shard_begin != 0;
   size_t tree_bytes = 0;
   if (is_tree(P->kernel) || (allow_tree && !opt.tile_override && p->L >= 2)) {
-    tree_bytes = (!sharded && !opt.want_backward) ? tree_layout(P) : 0;
+    tree_bytes = !sharded ? tree_layout(P) : 0;
     if (tree_bytes && !is_tree(P->kernel))
       P->kernel = opt.precision == GBSBIN_FP64 ? GBSBIN_KERNEL_TREE_FP64 : GBSBIN_KERNEL_TREE_DF32;
     else if (!tree_bytes && is_tree(P->kernel)) {
@@ -1097,7 +1069,7 @@ static int plan_create_impl(const gbsbin_problem* p, const gbsbin_options* o, gb
   // the large-matrix tree: asked for, or by default for standalone plans of n > 64 where it
   // needs under half the work of one LU per evaluated point
   if (is_btree(P->kernel) || (!is_tree(P->kernel) && allow_tree && !opt.tile_override && p->L >= 2 && n > 64)) {
-    tree_bytes = !opt.want_backward ? btree_layout(P) : 0;
+    tree_bytes = btree_layout(P);
     bool take = tree_bytes > 0;
     if (take && !is_btree(P->kernel))
       take = btree_macs(P) < 0.5 * (double)g.n_eval * (double)n * (double)n * (double)n / 3.0;
@@ -1226,10 +1198,10 @@ static int plan_create_impl(const gbsbin_problem* p, const gbsbin_options* o, gb
   }
   P->h_stage_bytes = sl.total;
   if (opt.want_backward) {
-    const size_t ne = (size_t)g.n_eval, adj = (size_t)std::max<long long>(P->table_size, g.n_full);
+    const size_t adj = (size_t)std::max<long long>(P->table_size, g.n_full);
     const size_t parts = (size_t)P->num_sms;
-    P->bws_slot_bytes = ((long long)points_matrix_bytes(GBSBIN_KERNEL_GMEM_FP64, n, 1) + 255) / 256 * 256;
-    if ((st = dalloc(&P->d_lu, ne * nn)) || (st = dalloc(&P->d_xs, ne * n)) || (st = dalloc(&P->d_adjA, adj)) ||
+    P->bws_slot_bytes = ((long long)nn * 16 + 255) / 256 * 256;
+    if ((st = dalloc(&P->d_adjA, adj)) ||
         (st = dalloc(&P->d_adjB, adj)) ||
         (st = dalloc(&P->d_bws, parts * (size_t)P->bws_slot_bytes / sizeof(double2))) ||
         (st = dalloc(&P->d_partS, parts * nn)) || (st = dalloc(&P->d_partg, parts * n)) ||
@@ -1240,7 +1212,8 @@ static int plan_create_impl(const gbsbin_problem* p, const gbsbin_options* o, gb
     }
   }
   if (opt.want_timing &&
-      (cudaEventCreate(&P->ev0) != cudaSuccess || cudaEventCreate(&P->ev1) != cudaSuccess)) {
+      (cudaEventCreate(&P->ev0) != cudaSuccess || cudaEventCreate(&P->ev1) != cudaSuccess ||
+       (opt.want_backward && (cudaEventCreate(&P->ev_b0) != cudaSuccess || cudaEventCreate(&P->ev_b1) != cudaSuccess)))) {
     cudaGetLastError();
     free_device(P);
     delete P;
@@ -1302,7 +1275,7 @@ int gbsbin_plan_set_state(gbsbin_plan* P, const gbsbin_problem* p, void* stream)
   st = build_state(p, P->n, XA, gamma, Xgamma, &has_gamma, &zbar);
   if (st) return st;
   record_inputs(P, p);
-  P->saved_valid = false;
+  P->logq_valid = false;
   P->zbar.swap(zbar);
   P->XA.swap(XA);
   P->gamma.swap(gamma);
@@ -1347,9 +1320,6 @@ static PointArgs make_point_args(gbsbin_plan* P) {
   a.gws_slot_bytes = P->gws_slot_bytes;
   a.ldfin = P->d_ldfin;
   a.H = P->d_H;
-  const bool save = P->opt.want_backward && (P->kernel == GBSBIN_KERNEL_SMEM_FP64 || P->kernel == GBSBIN_KERNEL_GMEM_FP64);
-  a.lu_store = save ? P->d_lu : nullptr;
-  a.x_store = save ? P->d_xs : nullptr;
   return a;
 }
 
@@ -1374,7 +1344,7 @@ int gbsbin_execute(gbsbin_plan* P, double* P_out, void* stream) {
   if (!P || !P_out) return GBSBIN_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   PointArgs a = make_point_args(P);
-  P->saved_valid = a.lu_store != nullptr;
+  P->logq_valid = true;
   if (P->ev0 && cudaEventRecord(P->ev0, s) != cudaSuccess) return GBSBIN_ERR_CUDA;
   if (is_tree(P->kernel)) {
     TreeArgs t = P->tree;
@@ -1483,6 +1453,16 @@ int gbsbin_diagnostics(gbsbin_plan* P, gbsbin_diag* out, void* stream) {
     }
     out->point_kernel_ms = ms;
   }
+  out->backward_kernel_ms = 0.0;
+  if (P->ev_b1 && P->backward_ran) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(P->ev_b1) != cudaSuccess ||
+        cudaEventElapsedTime(&ms, P->ev_b0, P->ev_b1) != cudaSuccess) {
+      cudaGetLastError();
+      return GBSBIN_ERR_CUDA;
+    }
+    out->backward_kernel_ms = ms;
+  }
   if (!P->opt.want_diagnostics) return GBSBIN_OK;
   if (part[4 * GBSBIN_DIAG_SLOTS + 1] != 0.0) return GBSBIN_ERR_CUDA;   // a grid barrier gave up waiting
   return out->n_bad_points > 0 ? GBSBIN_ERR_NUMERIC : GBSBIN_OK;
@@ -1505,20 +1485,22 @@ int gbsbin_read_points(gbsbin_plan* P, double* logq_host, double* minpiv_host, v
 }
 
 
-int gbsbin_backward(gbsbin_plan* P, const double* dLdP, gbsbin_grads* g, void* stream) {
-  if (!P || !dLdP || !g) return GBSBIN_ERR_ARG;
-  if (!P->opt.want_backward) return GBSBIN_ERR_ARG;
-  if ((g->d_r || g->d_T || g->d_alpha || g->d_V) && !P->physical) return GBSBIN_ERR_ARG;
-  cudaStream_t s = (cudaStream_t)stream;
-  const int n = P->n, MK = n / 2, M = P->M, K = P->K;
+// Enqueue the reverse pass to the bilinear adjoints d_outS (n x n) and d_outg (n).
+static int backward_enqueue(gbsbin_plan* P, const double* dLdP, cudaStream_t s) {
   int st = GBSBIN_OK;
-  if (!P->saved_valid && (st = evaluate_fp64_with_factors(P, s))) return st;
+  if (!P->logq_valid && (st = gbsbin_execute(P, P->d_table, s))) return st;   // log q of the current state
+  if (is_tree(P->kernel) && P->tree_g &&        // the tree's DFT took G directly: finish log q
+      launch_finish_logq(P->d_ldfin, P->d_logq, P->grid.n_eval, s) != cudaSuccess)
+    return GBSBIN_ERR_CUDA;
   BackwardArgs b{};
-  b.n = n;
+  b.n = P->n;
+  b.df = P->opt.precision == GBSBIN_FP32_REFINE ? 1 : 0;
+  b.nb = backward_block(P->n);
   b.grid = P->grid;
   b.n_eval = P->grid.n_eval;
-  b.lu_store = P->d_lu;
-  b.x_store = P->d_xs;
+  b.NXA = P->d_NXA;
+  b.Xgamma = P->d_Xgamma;
+  b.label = P->d_label;
   b.gamma = P->d_gamma;
   b.logq = P->d_logq;
   b.tw = P->d_tw;
@@ -1531,12 +1513,47 @@ int gbsbin_backward(gbsbin_plan* P, const double* dLdP, gbsbin_grads* g, void* s
   b.nparts = P->num_sms;
   b.outS = P->d_outS;
   b.outg = P->d_outg;
-  if (launch_backward(b, dLdP, s) != cudaSuccess) return GBSBIN_ERR_CUDA;
+  b.ev0 = P->ev_b0;
+  b.ev1 = P->ev_b1;
+  if (launch_backward(b, dLdP, s) != cudaSuccess) {
+    cudaGetLastError();
+    return GBSBIN_ERR_CUDA;
+  }
+  P->backward_ran = true;
+  return GBSBIN_OK;
+}
+
+int gbsbin_backward_device(gbsbin_plan* P, const double* dLdP, gbsbin_complex* dL_dXA, gbsbin_complex* dL_dgamma,
+                           void* stream) {
+  if (!P || !dLdP || !dL_dXA || !dL_dgamma) return GBSBIN_ERR_ARG;
+  if (!P->opt.want_backward) return GBSBIN_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  int st = backward_enqueue(P, dLdP, s);
+  if (st) return st;
+  const size_t n = (size_t)P->n;
+  if (cudaMemcpyAsync(dL_dXA, P->d_outS, n * n * sizeof(double2), cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(dL_dgamma, P->d_outg, n * sizeof(double2), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    return GBSBIN_ERR_CUDA;
+  return GBSBIN_OK;
+}
+
+int gbsbin_backward(gbsbin_plan* P, const double* dLdP, gbsbin_grads* g, void* stream) {
+  if (!P || !dLdP || !g) return GBSBIN_ERR_ARG;
+  if (!P->opt.want_backward) return GBSBIN_ERR_ARG;
+  if ((g->d_r || g->d_T || g->d_alpha || g->d_V) && !P->physical) return GBSBIN_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int n = P->n, MK = n / 2, M = P->M, K = P->K;
+  int st = backward_enqueue(P, dLdP, s);
+  if (st) return st;
   std::vector<double2> hS((size_t)n * n), hg(n);
   if (cudaMemcpyAsync(hS.data(), P->d_outS, hS.size() * sizeof(double2), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaMemcpyAsync(hg.data(), P->d_outg, hg.size() * sizeof(double2), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)
     return GBSBIN_ERR_CUDA;
+  for (size_t q = 0; q < hS.size(); ++q)
+    if (!std::isfinite(hS[q].x) || !std::isfinite(hS[q].y)) return GBSBIN_ERR_NUMERIC;
+  for (int i = 0; i < n; ++i)
+    if (!std::isfinite(hg[i].x) || !std::isfinite(hg[i].y)) return GBSBIN_ERR_NUMERIC;
 
   // dL = Re( sum_ij S_ij dXA_ij + sum_i s_i dgamma_i ) with XA = I - Sigma^{-1},
   // gamma = X Sigma^{-1} zbar:  dL = Re tr(B dSigma) + Re v^T dzbar, where

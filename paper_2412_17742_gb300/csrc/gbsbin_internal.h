@@ -60,8 +60,6 @@ struct PointArgs {
   double* minpiv;           // n_eval outputs: min_i Re u_ii
   void* gws;                // L2-resident workspace for the global-memory variants
   long long gws_slot_bytes; // bytes of one CTA's slot
-  double2* lu_store;        // FP64 kernels only, or nullptr: n_eval x n*n LU factors of M
-  double2* x_store;         // n_eval x n: x = M^{-1} X gamma
   double* ldfin;            // warp kernel only: n_eval x 6 doubles (the product of the
                             // pivots d_i u'_ii re/im, the FP32 sum of their arguments, the
                             // rest of log q re/im, unused); log q is finished by the DFT
@@ -81,26 +79,33 @@ struct PointBatch {
   unsigned long long* queue;
 };
 
+#define GBSBIN_BWD_MAX_NB 16         // pivots per blocked Gauss-Jordan step (n <= 320; 8 above)
 struct BackwardArgs {
   int n;
+  int df;                   // nonzero: the per-point inverse in pairs of FP32, else FP64
+  int nb;                   // pivots per Gauss-Jordan step (backward_block(n))
   GridDesc grid;
   long long n_eval;
-  const double2* lu_store;  // n_eval x n*n
-  const double2* x_store;   // n_eval x n
+  const double2* NXA;       // n*n: -XA
+  const double2* Xgamma;    // n
+  const int* label;         // n: detector group of each row
   const double2* gamma;     // n
   const double2* logq;      // n_eval
   const double2* tw;        // twiddles, as for the DFT
   double2* bufA;            // max(table, n_eval) complex scratch
   double2* bufB;            // max(table, n_eval) complex scratch
   const double2* beta;      // set by the launcher
-  void* ws;                 // nparts slots of n*n complex
+  void* ws;                 // nparts slots of n*n complex (16 bytes an entry)
   long long ws_slot_bytes;
-  double2* partS;           // nparts x n*n
-  double2* partg;           // nparts x n
+  void* partS;              // nparts x n*n, 16 bytes an entry (FP64 or FP32 pairs), transposed
+  void* partg;              // nparts x n, the same
   int nparts;
   double2* outS;            // n*n: dL/dXA (bilinear)
   double2* outg;            // n: dL/dgamma (bilinear)
+  cudaEvent_t ev0, ev1;     // optional: recorded around the per-point kernel
 };
+size_t backward_smem_bytes(int n, int nb);
+int backward_block(int n);
 
 struct DftArgs {
   GridDesc grid;

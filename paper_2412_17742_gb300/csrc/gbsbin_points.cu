@@ -103,12 +103,6 @@ __device__ __forceinline__ void group_fp64(const PointArgs& a, const long long e
       }
       __syncthreads();
     }
-    if (a.lu_store) {  // factors for the reverse pass
-      for (int t = tid; t < P * n * n; t += NT) {
-        int p = t & (P - 1), r = t >> logP;
-        if (e0 + p < a.grid.n_eval) a.lu_store[(size_t)(e0 + p) * n * n + r] = A[(size_t)p * S + r];
-      }
-    }
     // per point: log det and exponent, one warp per point
     for (int p = warp; p < P; p += nwarps) {
       const long long e = e0 + p;
@@ -141,11 +135,6 @@ __device__ __forceinline__ void group_fp64(const PointArgs& a, const long long e
           si += g.x * x[i].y + g.y * x[i].x;
         }
         expo = make_double2(warp_sum_d(sr), warp_sum_d(si));
-      }
-      if (a.x_store && e < a.grid.n_eval) {
-        const int lane = tid & 31;
-        for (int i = lane; i < n; i += 32)
-          a.x_store[(size_t)e * n + i] = a.has_gamma ? xv[(size_t)p * n + i] : make_double2(0.0, 0.0);
       }
       if ((tid & 31) == 0 && e < a.grid.n_eval) {
         a.logq[e] = make_double2(0.5 * expo.x - 0.5 * ld.x, 0.5 * expo.y - 0.5 * ld.y);

@@ -157,7 +157,6 @@ def test_tree_kernel_validation(gb, tree):
     assert _status(gb, one_group, tile_override=tree) == 8               # the tree needs L >= 2
     big = synth.random_problem(np.random.default_rng(8), 40, 1, 2, 2)    # n = 80 > 64
     assert _status(gb, big, tile_override=tree) == 8
-    assert _status(gb, synth.config(1), tile_override=tree, want_backward=True) == 8
     assert _status(gb, synth.config(1), tile_override=tree, shard=(0, 10)) == 8
     assert _status(gb, synth.config(1), tile_override=9) == 1            # a Fock kernel id
     assert _status(gb, synth.config(1), tile_override=15) == 1           # no such kernel
@@ -170,7 +169,6 @@ def test_large_tree_validation(gb, btree):
     assert _status(gb, one_group, tile_override=btree) == 8              # needs L >= 2
     big_last = synth.random_problem(np.random.default_rng(9), 120, 1, 2, 2)   # last group 120 rows > 112
     assert _status(gb, big_last, tile_override=btree) == 8
-    assert _status(gb, synth.config(2), tile_override=btree, want_backward=True) == 8
 
 
 def _herald_status(gb, state, roles, cutoff, cut, **opt):

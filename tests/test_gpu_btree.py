@@ -108,6 +108,29 @@ def test_btree_refuses_what_it_cannot_do(cuda_lib):
     with pytest.raises(gb.GbsbinError) as e:
         gb.Plan(big_last, tile_override=13)
     assert e.value.status == 8
-    with pytest.raises(gb.GbsbinError) as e:                  # no reverse pass on the tree
-        gb.Plan(_problem(910, 40, 2, 2, [2, 2]), tile_override=13, want_backward=True)
-    assert e.value.status == 8
+
+
+@pytest.mark.parametrize("precision,small,large", [(1, "tree_df32", "btree_df32"), (0, "tree_fp64", "btree_fp64")],
+                         ids=["fp32pairs", "fp64"])
+def test_trees_run_the_forward_of_a_reverse_pass(cuda_lib, precision, small, large):
+    # plans with a reverse pass keep the tree for their forward (the reverse pass needs only
+    # log q): the gradient matches a per-point plan's (the same recomputed reverse pass), for the
+    # small tree (undisplaced: its DFT takes G, log q finished for the reverse pass) and the
+    # large-matrix tree
+    import torch
+    gb = cuda_lib
+    cases = [(_problem(911, 8, 2, 2, [4, 5], displaced=False), small, 4),     # n = 32
+             (_problem(912, 40, 2, 2, [3, 4]), large, 6)]                      # n = 160
+    for prob, kind, per_point in cases:
+        rng = np.random.default_rng(913)
+        pbar = torch.from_numpy(rng.standard_normal(tuple(int(c) + 1 for c in prob.cutoff))).cuda()
+        grads = []
+        for tile in (0, per_point if precision else 3):
+            with gb.Plan(prob, precision=precision, want_backward=True, tile_override=tile) as p:
+                p.table()
+                st, d = p.diagnostics()
+                assert st == 0 and (d["kernel_name"] == kind) == (tile == 0), d["kernel_name"]
+                grads.append(p.backward(pbar, want=("r", "T", "sigma1")))
+        for k in grads[0]:
+            scale = max(1.0, float(np.abs(grads[1][k]).max()))
+            assert np.abs(grads[0][k] - grads[1][k]).max() < 1e-10 * scale, (kind, k)

@@ -62,13 +62,12 @@ def test_whole_table_matches_oracle(cuda_lib, oracle_tables, index, precision):
     assert abs(d["sum_P"] - ref.sum()) < 1e-10
 
 
-def test_full_grid_negative_log_likelihood_gradient(cuda_lib, oracle_tables):
-    # n = 200 on the full 81 x 81 grid: the NLL of 10^6 multinomial draws from the oracle's
-    # table; its gradient along a random direction in the 100 squeezings and along the
-    # transmission eta of T = sqrt(eta) U, against Richardson-extrapolated central
-    # differences of the oracle (the NLL is ~1e7 in size, so h cannot be tiny)
-    import torch
-    gb = cuda_lib
+@pytest.fixture(scope="module")
+def nll_reference(oracle_tables):
+    """The n = 200 negative log-likelihood of 10^6 multinomial draws from the oracle's table,
+    and its Richardson-extrapolated central differences (oracle only) along a random direction
+    in the 100 squeezings and along the transmission eta of T = sqrt(eta) U (the NLL is ~1e7
+    in size, so h cannot be tiny)."""
     prob, res = oracle_tables(4)
     rng = np.random.default_rng(504)
     P0 = np.clip(res["P"], 0, None)
@@ -77,11 +76,6 @@ def test_full_grid_negative_log_likelihood_gradient(cuda_lib, oracle_tables):
     def nll(q):
         P = oracle.binned(q)["P"]
         return float(-(counts * np.log(P)).sum())
-
-    with gb.Plan(prob, want_backward=True) as p:
-        Pg = p.table()
-        dLdP = torch.from_numpy(-counts / Pg.cpu().numpy()).cuda()
-        g = p.backward(dLdP, want=("r", "T"))
 
     def copy_prob(q):
         return synth.Problem(q.M, q.K, q.r.copy(), q.T.copy(), q.bin_of_mode.copy(), q.cutoff.copy(),
@@ -98,16 +92,31 @@ def test_full_grid_negative_log_likelihood_gradient(cuda_lib, oracle_tables):
         q = copy_prob(prob)
         q.r = prob.r + hh * dr
         return q
-    f = richardson(shift_r)
-    got = float((g["r"] * dr).sum())
-    assert abs(got - f) <= 1e-4 + 1e-6 * abs(f), (got, f)
     eta = prob.notes["eta"]
-    dT = prob.T / (2 * eta)                       # T = sqrt(eta) U  =>  dT/deta = T / (2 eta)
-    got = float(np.real(np.sum(np.conj(g["T"]) * dT)))
 
     def shift_eta(hh):
         q = copy_prob(prob)
         q.T = np.sqrt((eta + hh) / eta) * prob.T
         return q
-    f = richardson(shift_eta)
+    return dict(prob=prob, counts=counts, dr=dr, f_r=richardson(shift_r), f_eta=richardson(shift_eta),
+                dT=prob.T / (2 * eta))      # T = sqrt(eta) U  =>  dT/deta = T / (2 eta)
+
+
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "fp32pairs"])
+def test_full_grid_negative_log_likelihood_gradient(cuda_lib, nll_reference, precision):
+    # n = 200 on the full 81 x 81 grid: the reverse pass (per-point inverse recomputed, FP64 or
+    # pairs of FP32) along the two directions of the reference differences
+    import torch
+    gb = cuda_lib
+    ref = nll_reference
+    prob, counts = ref["prob"], ref["counts"]
+    with gb.Plan(prob, precision=precision, want_backward=True) as p:
+        Pg = p.table()
+        dLdP = torch.from_numpy(-counts / Pg.cpu().numpy()).cuda()
+        g = p.backward(dLdP, want=("r", "T"))
+    got = float((g["r"] * ref["dr"]).sum())
+    f = ref["f_r"]
+    assert abs(got - f) <= 1e-4 + 1e-6 * abs(f), (got, f)
+    got = float(np.real(np.sum(np.conj(g["T"]) * ref["dT"])))
+    f = ref["f_eta"]
     assert abs(got - f) <= 1e-4 + 1e-6 * abs(f), (got, f)

@@ -218,3 +218,41 @@ def test_autograd_function_matches(cuda_lib):
     assert np.allclose(T.grad.numpy(), g["T"], rtol=0, atol=1e-12)
     assert np.allclose(a.grad.numpy(), g["alpha"], rtol=0, atol=1e-12)
     assert close(float(r.grad[1, 0]), fd(prob, pbar.cpu().numpy(), "r", (1, 0), "re"))
+
+
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "fp32pairs"])
+@pytest.mark.parametrize("M,K,cutoff", [(21, 1, [3, 4]), (3, 7, [2, 3]), (171, 1, [1, 2])],
+                         ids=["n42_ragged_block", "n42_internal", "n342_block8"])
+def test_device_adjoints_along_a_physical_direction(cuda_lib, precision, M, K, cutoff):
+    # the asynchronous adjoints S = dL/dXA, s = dL/dgamma (bilinear) against central differences
+    # of the oracle along a direction in the squeezings: dL = Re(sum S dXA + sum s dgamma), with
+    # dXA, dgamma the state algebra's own differences.  n = 42 runs blocks of 16, 16 and 10
+    # pivots, n = 342 blocks of 8 with a ragged 4 x 4 tile edge
+    import torch
+    gb = cuda_lib
+    rng = np.random.default_rng(505 + M)
+    prob = synth.random_problem(rng, M, K, len(cutoff), cutoff, displaced=True, internal_basis=K > 1)
+    pbar = rng.standard_normal(tuple(int(c) + 1 for c in cutoff))
+    dr = rng.standard_normal(prob.r.shape)
+    h = 1e-5
+
+    def shifted(t):
+        q = copy_prob(prob)
+        q.r = prob.r + t * dr
+        return q
+    adj = [state.adjacency(*state.sigma1_zbar(shifted(t))) for t in (h, -h)]
+    dXA = (adj[0][0] - adj[1][0]) / (2 * h)
+    dg = (adj[0][1] - adj[1][1]) / (2 * h)
+    f = (oracle_loss(shifted(h), pbar) - oracle_loss(shifted(-h), pbar)) / (2 * h)
+    with gb.Plan(prob, precision=precision, want_backward=True, want_timing=True) as p:
+        p.table()
+        S, s = p.backward_device(torch.from_numpy(pbar).cuda())
+        torch.cuda.synchronize()
+        st, d = p.diagnostics()
+        assert st == 0 and d["backward_kernel_ms"] > 0
+        g = p.backward(torch.from_numpy(pbar).cuda(), want=("r",))
+    S, s = S.cpu().numpy(), s.cpu().numpy()
+    got = float(np.real(np.sum(S * dXA) + np.sum(s * dg)))
+    assert abs(got - f) <= 1e-7 + 1e-6 * abs(f), (got, f)
+    chained = float((g["r"] * dr).sum())
+    assert abs(chained - got) <= 1e-9 + 1e-9 * abs(got), (chained, got)
