@@ -308,7 +308,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the other workloads (n=32 grid, 256-problem batch, n=200 gradient, "
                          "M=256 total photon number, Fock inputs, App. D fine-grained)")
-    ap.add_argument("--extras", default="n32,batch,n200,e3,fock,appd",
+    ap.add_argument("--extras", default="n32,batch,n200,e3,fock,herald,appd",
                     help="comma list of the other workloads to time: n32, batch, n200, e3, fock, appd")
     ap.add_argument("--extra-steps", type=int, default=3)
     args = ap.parse_args()
@@ -541,12 +541,46 @@ def extra_workloads(gb, torch, stream, flush, steps, world, which=("n32", "batch
         out.update(_extra_e3(gb, torch, stream, flush, steps, world))
     if "fock" in which:
         out.update(_extra_fock(gb, torch, stream, flush, steps, world))
+    if "herald" in which:
+        out.update(_extra_herald(gb, torch, stream, flush, steps, world))
     if "appd" in which:
         try:
             out.update(_extra_distinguishable(gb, torch, steps))
         except Exception as ex:                           # reported, never fatal to the bench line
             out["appd_distinguishable_m16_ones"] = {"error": str(ex)[:200]}
     return out
+
+
+def _extra_herald(gb, torch, stream, flush, steps, world):
+    """Heralded states (Sec. VII): the Fock-state source of Sec. VIII (two ports x two spectral
+    modes, spectral purity 0.9, no loss; one port heralds with its spectral modes summed, cutoff
+    3, the kept mode to Fock cutoff 15, 16-fold oversampled grid of 64 points) and a larger one
+    (16 ports x 2 internal modes, two heralding groups of six ports, cutoff 8 each: 81 points;
+    two kept modes to Fock cutoff 6: 2401 coefficients per point), per execute (the point
+    kernel and the inverse DFT over the heralding axes), CUDA events, L2 flushed; and the
+    fidelity of the heralded single photon from the GPU's own state."""
+    out = {}
+    cases = [("fock_source_p0.9", synth.fock_heralding_source(0.9, 1.0), synth.FOCK_HERALD_ROLES, [3], 15, 16)]
+    prob, roles, cut, fc = synth.herald_config()
+    cases.append(("m16_k2_two_groups_two_kept", prob, roles, cut, fc, 1))
+    for name, prob, roles, cut, fc, over in cases:
+        with gb.HeraldPlan(prob, roles, cut, fc, oversample=over) as h:
+            rho = torch.empty(h.shape, dtype=torch.complex128, device="cuda")
+            pr = torch.empty(h.prob_shape, dtype=torch.float64, device="cuda")
+            run = lambda: gb.gbsbin_herald_execute(h.handle, rho, pr, stream)
+            for _ in range(3):
+                run()
+            k = max(steps, 20)
+            ms = _timed(torch, stream, flush, k, run) / k
+            d = h.diagnostics(stream)
+            entry = {"ms_per_execute": ms, "grid_points": d["n_points"], "rho_elements": d["table_size"],
+                     "points_per_s": world * d["n_points"] / (ms * 1e-3), "launches": d["launches"],
+                     "sum_Pr": d["sum_P"], "status": d["status"]}
+            if name.startswith("fock"):
+                r, p = rho.cpu().numpy(), pr.cpu().numpy()
+                entry["fidelity_n1"] = float(np.sqrt((r[1, 1, 1] / p[1]).real))
+            out[name] = entry
+    return {"herald": out}
 
 
 def _extra_distinguishable(gb, torch, steps):

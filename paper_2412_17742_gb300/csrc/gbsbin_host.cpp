@@ -168,7 +168,9 @@ int physical_state(const gbsbin_problem* p, std::vector<cd>& S1, std::vector<cd>
     mi[q] = ti[q] * w_m;
   }
   S1.assign((size_t)n * n, 0.0);
-  for (int a = 0; a < MK; ++a)
+  // every unordered pair {a, b} belongs to the thread of min(a, b): rows dealt cyclically
+  parallel_run(MK >= 32 ? host_threads() : 1, [&](int t, int nt) {
+  for (int a = t; a < MK; a += nt)
     for (int b = a; b < MK; ++b) {
       const double *ar = &nr[(size_t)a * MK], *ai = &ni[(size_t)a * MK], *br = &tr[(size_t)b * MK],
                    *bi = &ti[(size_t)b * MK], *cr = &mr[(size_t)a * MK], *ci = &mi[(size_t)a * MK];
@@ -191,6 +193,7 @@ int physical_state(const gbsbin_problem* p, std::vector<cd>& S1, std::vector<cd>
         S1[(size_t)(MK + b) * n + (MK + a)] = std::conj(N);
       }
     }
+  });
   zbar.assign(n, 0.0);
   if (p->alpha) {
     for (int a = 0; a < MK; ++a) {
@@ -203,30 +206,89 @@ int physical_state(const gbsbin_problem* p, std::vector<cd>& S1, std::vector<cd>
   return GBSBIN_OK;
 }
 
-// In-place Cholesky of a Hermitian matrix (lower factor) held as split real / imaginary
-// row-major arrays; false if not positive definite.  Row j of L: L_jj = sqrt(A_jj -
-// sum_k |L_jk|^2), L_ij = (A_ij - sum_k L_ik conj(L_jk)) / L_jj, k < j (contiguous in k).
-bool cholesky(std::vector<double>& re, std::vector<double>& im, int n) {
-  for (int j = 0; j < n; ++j) {
-    const double* rj = &re[(size_t)j * n];
-    const double* ij = &im[(size_t)j * n];
-    double d = rj[j];
-    for (int k = 0; k < j; ++k) d -= rj[k] * rj[k] + ij[k] * ij[k];
-    if (!(d > 0.0) || !std::isfinite(d)) return false;
-    const double ljj = std::sqrt(d);
-    re[(size_t)j * n + j] = ljj;
-    im[(size_t)j * n + j] = 0.0;
-    for (int i = j + 1; i < n; ++i) {
-      double* ri = &re[(size_t)i * n];
-      double* ii = &im[(size_t)i * n];
-      double sr = ri[j], si = ii[j];
-      for (int k = 0; k < j; ++k) {
-        sr -= ri[k] * rj[k] + ii[k] * ij[k];
-        si -= ii[k] * rj[k] - ri[k] * ij[k];
-      }
-      ri[j] = sr / ljj;
-      ii[j] = si / ljj;
+// Complex dot products over split real / imaginary rows: MODE 0: sum a_k b_k,
+// 1: sum a_k conj(b_k), 2: sum conj(a_k) b_k.
+template <int MODE>
+inline void cdot(const double* __restrict__ ar, const double* __restrict__ ai, const double* __restrict__ br,
+                 const double* __restrict__ bi, int len, double* re, double* im) {
+  double r = 0.0, m = 0.0;
+  for (int k = 0; k < len; ++k) {
+    if (MODE == 0) {
+      r += ar[k] * br[k] - ai[k] * bi[k];
+      m += ar[k] * bi[k] + ai[k] * br[k];
+    } else if (MODE == 1) {
+      r += ar[k] * br[k] + ai[k] * bi[k];
+      m += ai[k] * br[k] - ar[k] * bi[k];
+    } else {
+      r += ar[k] * br[k] + ai[k] * bi[k];
+      m += ar[k] * bi[k] - ai[k] * br[k];
     }
+  }
+  *re = r;
+  *im = m;
+}
+
+// In-place Cholesky of a Hermitian matrix (lower factor) held as split real / imaginary
+// row-major arrays; false if not positive definite.  Blocked right-looking: per block of B
+// columns the diagonal block is factored on one thread (L_jj = sqrt(A_jj - sum_k |L_jk|^2),
+// L_ij = (A_ij - sum_k L_ik conj(L_jk)) / L_jj over the block's earlier columns), then the
+// rows below are solved against it and the trailing matrix updated, A_ij -= sum over the
+// block of L_ik conj(L_jk), both in parallel over rows (dealt cyclically).
+bool cholesky(std::vector<double>& re, std::vector<double>& im, int n) {
+  const int B = 48;
+  const int nt = n >= 96 ? host_threads() : 1;
+  for (int k0 = 0; k0 < n; k0 += B) {
+    const int k1 = std::min(n, k0 + B);
+    for (int j = k0; j < k1; ++j) {
+      const double* rj = &re[(size_t)j * n];
+      const double* ij = &im[(size_t)j * n];
+      double d = rj[j];
+      for (int k = k0; k < j; ++k) d -= rj[k] * rj[k] + ij[k] * ij[k];
+      if (!(d > 0.0) || !std::isfinite(d)) return false;
+      const double ljj = std::sqrt(d);
+      re[(size_t)j * n + j] = ljj;
+      im[(size_t)j * n + j] = 0.0;
+      for (int i = j + 1; i < k1; ++i) {
+        double* ri = &re[(size_t)i * n];
+        double* ii = &im[(size_t)i * n];
+        double sr = ri[j], si = ii[j];
+        for (int k = k0; k < j; ++k) {
+          sr -= ri[k] * rj[k] + ii[k] * ij[k];
+          si -= ii[k] * rj[k] - ri[k] * ij[k];
+        }
+        ri[j] = sr / ljj;
+        ii[j] = si / ljj;
+      }
+    }
+    if (k1 == n) break;
+    parallel_run(nt, [&](int t, int nth) {            // rows below the block: L_i,[k0,k1)
+      for (int i = k1 + t; i < n; i += nth) {
+        double* ri = &re[(size_t)i * n];
+        double* ii = &im[(size_t)i * n];
+        for (int j = k0; j < k1; ++j) {
+          const double* rj = &re[(size_t)j * n];
+          const double* ij = &im[(size_t)j * n];
+          double sr, si;
+          cdot<1>(ri + k0, ii + k0, rj + k0, ij + k0, j - k0, &sr, &si);
+          ri[j] = (ri[j] - sr) / rj[j];
+          ii[j] = (ii[j] - si) / rj[j];
+        }
+      }
+    });
+    parallel_run(nt, [&](int t, int nth) {            // trailing update of the lower triangle
+      for (int i = k1 + t; i < n; i += nth) {
+        double* ri = &re[(size_t)i * n];
+        double* ii = &im[(size_t)i * n];
+        for (int j = k1; j <= i; ++j) {
+          const double* rj = &re[(size_t)j * n];
+          const double* ij = &im[(size_t)j * n];
+          double sr, si;
+          cdot<1>(ri + k0, ii + k0, rj + k0, ij + k0, k1 - k0, &sr, &si);
+          ri[j] -= sr;
+          ii[j] -= si;
+        }
+      }
+    });
   }
   return true;
 }
@@ -258,42 +320,44 @@ int adjacency(const std::vector<cd>& S1, const std::vector<cd>& zbar, int n, std
   }
   for (int i = 0; i < n; ++i) cr[(size_t)i * n + i] += 1.0;
   if (!cholesky(cr, ci, n)) return GBSBIN_ERR_NONPHYSICAL;
-  // X = C^{-1} (lower triangular) row by row: C_ii X_i. = e_i - sum_{k<i} C_ik X_k.
+  // X = C^{-1} (lower triangular) column by column, stored transposed (xr, xi row j = column
+  // j of X): X_jj = 1 / C_jj, X_ij = -(sum_{j <= k < i} C_ik X_kj) / C_ii; columns in parallel,
+  // dealt cyclically from the longest
+  const int nt = n >= 96 ? host_threads() : 1;
   std::vector<double> xr(nn, 0.0), xi(nn, 0.0);
-  for (int i = 0; i < n; ++i) {
-    double* ri = &xr[(size_t)i * n];
-    double* ii = &xi[(size_t)i * n];
-    for (int k = 0; k < i; ++k) {
-      const double a = cr[(size_t)i * n + k], b = ci[(size_t)i * n + k];
-      const double* rk = &xr[(size_t)k * n];
-      const double* ik = &xi[(size_t)k * n];
-      for (int j = 0; j <= k; ++j) {
-        ri[j] -= a * rk[j] - b * ik[j];
-        ii[j] -= a * ik[j] + b * rk[j];
+  parallel_run(nt, [&](int t, int nth) {
+    for (int j = t; j < n; j += nth) {
+      double* xrj = &xr[(size_t)j * n];
+      double* xij = &xi[(size_t)j * n];
+      xrj[j] = 1.0 / cr[(size_t)j * n + j];
+      for (int i = j + 1; i < n; ++i) {
+        const double* ci_r = &cr[(size_t)i * n];
+        const double* ci_i = &ci[(size_t)i * n];
+        double sr, si;
+        cdot<0>(ci_r + j, ci_i + j, xrj + j, xij + j, i - j, &sr, &si);
+        const double cii = ci_r[i];
+        xrj[i] = -sr / cii;
+        xij[i] = -si / cii;
       }
     }
-    const double cii = cr[(size_t)i * n + i];
-    for (int j = 0; j < i; ++j) {
-      ri[j] /= cii;
-      ii[j] /= cii;
-    }
-    ri[i] = 1.0 / cii;
-  }
-  // S = X^H X (lower half) as a sum over k of rows: S_ij += conj(X_ki) X_kj, j <= i <= k
+  });
+  // S = X^H X (lower half): S_ij = sum_{k >= i} conj(X_ki) X_kj, j <= i - dot products of the
+  // stored columns i and j over k >= i; rows in parallel
   std::vector<double> sr(nn, 0.0), si(nn, 0.0);
-  for (int k = 0; k < n; ++k) {
-    const double* rk = &xr[(size_t)k * n];
-    const double* ik = &xi[(size_t)k * n];
-    for (int i = 0; i <= k; ++i) {
-      const double a = rk[i], b = -ik[i];
-      double* ri = &sr[(size_t)i * n];
-      double* ii = &si[(size_t)i * n];
+  parallel_run(nt, [&](int t, int nth) {
+    for (int i = t; i < n; i += nth) {
+      const double* ar = &xr[(size_t)i * n];
+      const double* ai = &xi[(size_t)i * n];
       for (int j = 0; j <= i; ++j) {
-        ri[j] += a * rk[j] - b * ik[j];
-        ii[j] += a * ik[j] + b * rk[j];
+        const double* br = &xr[(size_t)j * n];
+        const double* bi = &xi[(size_t)j * n];
+        double vr, vi;
+        cdot<2>(ar + i, ai + i, br + i, bi + i, n - i, &vr, &vi);
+        sr[(size_t)i * n + j] = vr;
+        si[(size_t)i * n + j] = vi;
       }
     }
-  }
+  });
   XA.assign(nn, 0.0);
   for (int i = 0; i < n; ++i)
     for (int j = 0; j <= i; ++j) {

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <complex>
+#include <functional>
 #include <vector>
 
 #include "../../include/gbsbin.h"
@@ -23,5 +24,12 @@ int host_state(const gbsbin_problem* p, int n, std::vector<std::complex<double>>
 std::complex<double> host_logq1(const std::vector<std::complex<double>>& XA,
                                 const std::vector<std::complex<double>>& gamma,
                                 const std::vector<std::complex<double>>& Xgamma, int n, double* minpiv);
+
+// Host threads the state algebra uses: the hardware concurrency capped at 16, or the
+// environment variable GBSBIN_HOST_THREADS.
+int host_threads();
+// fn(t, nthreads) for t = 0 .. nthreads - 1 on the pool's threads (the caller runs t = 0);
+// returns when every call has returned.  One job at a time.
+void parallel_run(int nthreads, const std::function<void(int, int)>& fn);
 
 }  // namespace gbsbin

@@ -222,3 +222,43 @@ def random_fock_problem(rng: np.random.Generator, M: int, photons, L: int, cutof
         lab = rng.permutation(lab).astype(np.int32)
     cut = np.array(np.broadcast_to(np.asarray(cutoff, dtype=np.int32), (L,)), dtype=np.int32)
     return FockProblem(M, T, np.asarray(photons, dtype=np.int32), lab, cut, name=f"fock_rand_m{M}_l{L}")
+
+
+# ------------------------------------------------------------------ heralded states (Sec. VII-VIII)
+FOCK_HERALD_ROLES = [0, 0, -2, -1]   # port 0 (both spectral modes) heralds; port 1: mode 2 kept, mode 3 traced
+
+
+def fock_heralding_source(p: float, eta: float, xi: float = 1.1) -> Problem:
+    """Sec. VIII's Fock-state source: two ports x two spectral modes, squeezing xi in spectral
+    mode 1 and xi' with tanh^2 xi' = ((1 - p)/p) tanh^2 xi in mode 2 (Eq.
+    relation_between_sqz_par, spectral purity p), through T = sqrt(eta) U with U the balanced
+    beam splitter (1/sqrt 2) [[1, i], [i, 1]] (Eq. beam_splitter_unitary).  Roles
+    FOCK_HERALD_ROLES: port 0 heralds with both spectral modes summed, spectral mode 1 of port 1
+    is kept, its mode 2 traced."""
+    xi2 = np.arctanh(np.sqrt((1 - p) / p) * np.tanh(xi)) if p < 1 else 0.0
+    r = np.array([[xi, xi2], [xi, xi2]])
+    T = np.sqrt(eta) * np.array([[1, 1j], [1j, 1]]) / np.sqrt(2)
+    return Problem(2, 2, r, T, np.array([0, 1], np.int32), np.array([8, 8], np.int32))
+
+
+def herald_config(seed: int = 17):
+    """A larger heralding workload: 16 ports x 2 internal modes (64 x 64 matrices), displaced,
+    non-aligned internal bases, Haar T with loss; two heralding groups of six ports each (both
+    internal modes summed), cutoff 8 per group (81 grid points); the first internal mode of
+    ports 12 and 13 kept (Fock cutoff 6: 7^4 coefficients per point), the rest traced.
+    Returns (problem, roles, heralding cutoffs, Fock cutoff)."""
+    rng = np.random.default_rng(seed)
+    prob = random_problem(rng, 16, 2, 2, [8, 8], displaced=True, internal_basis=True, r_range=(0.4, 0.9),
+                          eta_range=(0.6, 0.9))
+    roles = []
+    for port in range(16):
+        for k in range(2):
+            if port < 6:
+                roles.append(0)
+            elif port < 12:
+                roles.append(1)
+            elif port in (12, 13) and k == 0:
+                roles.append(-2)
+            else:
+                roles.append(-1)
+    return prob, roles, [8, 8], 6

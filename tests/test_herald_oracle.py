@@ -16,16 +16,10 @@ GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "fock_heralding_fidel
 
 
 def fock_setup(p, eta, xi=1.1):
-    """Sec. VIII's Fock-state source: two ports x two spectral modes, tanh^2 xi' =
-    ((1 - p)/p) tanh^2 xi (Eq. relation_between_sqz_par), T = sqrt(eta) U with the balanced
-    beam splitter of Eq. beam_splitter_unitary."""
-    xi2 = np.arctanh(np.sqrt((1 - p) / p) * np.tanh(xi)) if p < 1 else 0.0
-    r = np.array([[xi, xi2], [xi, xi2]])
-    T = np.sqrt(eta) * np.array([[1, 1j], [1j, 1]]) / np.sqrt(2)
-    return synth.Problem(2, 2, r, T, np.array([0, 1], np.int32), np.array([8, 8], np.int32))
+    return synth.fock_heralding_source(p, eta, xi)
 
 
-FOCK_ROLES = [0, 0, -2, -1]   # port 0 (both spectral modes) heralds; port 1: mode 2 kept, mode 3 traced
+FOCK_ROLES = synth.FOCK_HERALD_ROLES
 
 
 CASES = [

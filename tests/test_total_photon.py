@@ -69,3 +69,28 @@ def test_rejects_bad_input(gb):
     with pytest.raises(gb.GbsbinError) as e:
         gb.gbsbin_total_photon_series(_one_mode(0.5), (1 << 20) + 1)
     assert e.value.status == 8
+
+
+@pytest.mark.parametrize("M,K", [(60, 1), (32, 2)], ids=["n120", "n128_internal"])
+def test_large_states_on_the_threaded_host_algebra(gb, M, K):
+    # n >= 96 runs the blocked, threaded Cholesky, triangular inverse and Gram product of the
+    # host state algebra; the series it feeds matches the oracle's unfolded one-group table,
+    # with the library's thread count and with one thread (bit-identical: every entry is
+    # summed in the same order whatever the thread count)
+    import subprocess
+    import sys
+    rng = np.random.default_rng(960 + M)
+    prob = synth.random_problem(rng, M, K, 1, 12, displaced=True, internal_basis=K > 1, r_range=(0.1, 0.3),
+                                eta_range=(0.2, 0.4))
+    P = gb.gbsbin_total_photon_series(prob, 12)
+    ref = oracle.binned(prob, radix=[64])["P"][:13]
+    assert np.abs(P - ref).max() < 1e-12, np.abs(P - ref).max()
+    code = ("import sys, numpy as np; sys.path[:0] = sys.argv[1:3]; import synth, paper_2412_17742_gb300 as gb; "
+            f"p = synth.random_problem(np.random.default_rng({960 + M}), {M}, {K}, 1, 12, displaced=True, "
+            f"internal_basis={K > 1}, r_range=(0.1, 0.3), eta_range=(0.2, 0.4)); "
+            "sys.stdout.write(gb.gbsbin_total_photon_series(p, 12).tobytes().hex())")
+    import os
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, "-c", code, root, os.path.join(root, "tests")], check=True,
+                         capture_output=True, text=True, env=dict(os.environ, GBSBIN_HOST_THREADS="1")).stdout
+    assert np.array_equal(np.frombuffer(bytes.fromhex(out), dtype=np.float64), P)
