@@ -144,8 +144,10 @@ typedef struct {
                                    gbsbin_fock_plan_set_transfer) copies from host to device    */
   int launches;              /* kernel launches of the last execute (point stage, inverse DFT
                                 with its diagnostics), 0 before the first                       */
-  double backward_kernel_ms; /* duration of the last reverse pass's per-point kernel (plans with
-                                want_timing and want_backward), else 0                          */
+  double backward_kernel_ms; /* duration of the last reverse pass's per-point (or per-tree)
+                                kernels (plans with want_timing and want_backward), else 0      */
+  int backward_path;         /* how the plan's reverse pass runs: 0 no reverse pass, 1 one
+                                inverse per evaluated point, 2 along the large-matrix tree      */
 } gbsbin_diag;
 
 typedef enum {
@@ -320,8 +322,12 @@ typedef struct {
  * evaluated points: each point's matrix M = conj(D(w)) - XA is rebuilt and inverted in place
  * (blocked Gauss-Jordan without pivoting, n^3 complex multiply-adds per point, in a per-SM
  * workspace of n^2 entries) in FP64 for GBSBIN_FP64 plans and in pairs of FP32 (~46 bits)
- * for GBSBIN_FP32_REFINE plans; if the state changed since the last execute, an execute
- * (into the plan's own table) runs first.  Synchronises `stream`.
+ * for GBSBIN_FP32_REFINE plans.  Plans on the large-matrix tree (kernels 13, 14; no shard)
+ * instead go along the tree where that needs under half the work: per combination of the
+ * first L-1 axes' roots the inverse of the leading groups' block and its products with the
+ * rest, per evaluated point only the inverse of the last group's Schur complement
+ * (gbsbin_diag.backward_path says which).  If the state changed since the last execute, an
+ * execute (into the plan's own table) runs first.  Synchronises `stream`.
  * Errors: ERR_ARG (NULL plan/dL_dP/g, plan without want_backward, physical gradients
  * requested for a direct-covariance problem), ERR_NUMERIC (a non-finite adjoint),
  * ERR_CUDA, ERR_NOMEM.

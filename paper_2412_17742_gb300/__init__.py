@@ -81,7 +81,7 @@ class gbsbin_diag(ctypes.Structure):
                 ("n_evaluated", ctypes.c_longlong), ("table_size", ctypes.c_longlong), ("n", ctypes.c_int),
                 ("kernel", ctypes.c_int), ("log_q1_re", ctypes.c_double), ("point_kernel_ms", ctypes.c_double),
                 ("state_upload_bytes", ctypes.c_longlong), ("launches", ctypes.c_int),
-                ("backward_kernel_ms", ctypes.c_double)]
+                ("backward_kernel_ms", ctypes.c_double), ("backward_path", ctypes.c_int)]
 
 
 class gbsbin_fock_problem(ctypes.Structure):

@@ -29,6 +29,8 @@
 
 #include "gbsbin_device.cuh"
 #include "gbsbin_df.cuh"
+#include "gbsbin_backward_tree.h"
+#include "gbsbin_gj.cuh"
 #include "gbsbin_internal.h"
 
 namespace gbsbin {
@@ -120,7 +122,6 @@ __global__ void k_adj_beta0(double2* __restrict__ a, long long n) {
 // Per point: W = M^{-1} by blocked Gauss-Jordan; accumulate into this CTA's partials (S
 // transposed: ST[j][i] = S[i][j], so that the term M^{-T} reads W row by row).
 constexpr int kGjThreads = 256;
-constexpr int kGjTile = 4;
 
 template <class Ar>
 __global__ void __launch_bounds__(kGjThreads) k_backward_gj(BackwardArgs b) {
@@ -145,7 +146,6 @@ __global__ void __launch_bounds__(kGjThreads) k_backward_gj(BackwardArgs b) {
     gE[t] = Ar::from(b.gamma[t]);
     xgE[t] = Ar::from(b.Xgamma[t]);
   }
-  const int tcols = (n + kGjTile - 1) / kGjTile, ntiles = tcols * tcols;
 
   for (long long e = blockIdx.x; e < b.n_eval; e += gridDim.x) {
     const double2 beta = b.beta[e];
@@ -163,83 +163,7 @@ __global__ void __launch_bounds__(kGjThreads) k_backward_gj(BackwardArgs b) {
       W[t] = Ar::from(v);
     }
     __syncthreads();
-    for (int K = 0; K < n; K += nbm) {
-      const int bs = min(nbm, n - K);
-      for (int t = tid; t < n * bs; t += NT) {
-        const int i = t / bs, c = t - (t / bs) * bs;
-        Pc[i * nbm + c] = (i >= K && i < K + bs) ? Ar::zero() : W[(size_t)i * n + K + c];
-      }
-      for (int t = tid; t < bs * n; t += NT) Rx[t] = W[(size_t)K * n + t];   // rows K .. K + bs - 1
-      if (tid < bs * bs) Dg[tid] = W[(size_t)(K + tid / bs) * n + K + tid % bs];
-      __syncthreads();
-      // inv(W_BB) by unpivoted Gauss-Jordan, one element per thread
-      for (int k = 0; k < bs; ++k) {
-        E nv = Ar::zero();
-        if (tid < bs * bs) {
-          const int i = tid / bs, j = tid - (tid / bs) * bs;
-          const E p = Ar::recip(Dg[k * bs + k]);
-          if (i == k && j == k) nv = p;
-          else if (i == k) nv = Ar::mul(Dg[k * bs + j], p);
-          else if (j == k) nv = Ar::neg(Ar::mul(Dg[i * bs + k], p));
-          else nv = Ar::fms(Dg[tid], Ar::mul(Dg[i * bs + k], p), Dg[k * bs + j]);
-        }
-        __syncthreads();
-        if (tid < bs * bs) Dg[tid] = nv;
-        __syncthreads();
-      }
-      // Rx = inv(W_BB) W[B, :] outside the block's columns, inv(W_BB) on them
-      for (int j = tid; j < n; j += NT) {
-        if (j >= K && j < K + bs) {
-          for (int r = 0; r < bs; ++r) Rx[r * n + j] = Dg[r * bs + (j - K)];
-          continue;
-        }
-        E col[GBSBIN_BWD_MAX_NB];
-#pragma unroll
-        for (int c = 0; c < GBSBIN_BWD_MAX_NB; ++c)
-          if (c < bs) col[c] = Rx[c * n + j];
-        for (int r = 0; r < bs; ++r) {
-          E acc = Ar::zero();
-#pragma unroll
-          for (int c = 0; c < GBSBIN_BWD_MAX_NB; ++c)
-            if (c < bs) acc = Ar::fma(Dg[r * bs + c], col[c], acc);
-          Rx[r * n + j] = acc;
-        }
-      }
-      __syncthreads();
-      // W[i][j] = (j in B ? 0 : W[i][j]) - sum_c Pc[i][c] Rx[c][j] for i outside B; Rx[i - K][j]
-      // for the block's rows
-      for (int tt = tid; tt < ntiles; tt += NT) {
-        const int i0 = (tt / tcols) * kGjTile, j0 = (tt - (tt / tcols) * tcols) * kGjTile;
-        E acc[kGjTile][kGjTile];
-#pragma unroll
-        for (int r = 0; r < kGjTile; ++r)
-#pragma unroll
-          for (int q = 0; q < kGjTile; ++q) {
-            const int i = i0 + r, j = j0 + q;
-            acc[r][q] = (i < n && j < n && (j < K || j >= K + bs)) ? W[(size_t)i * n + j] : Ar::zero();
-          }
-        for (int c = 0; c < bs; ++c) {
-          E pv[kGjTile], rv[kGjTile];
-#pragma unroll
-          for (int r = 0; r < kGjTile; ++r) pv[r] = i0 + r < n ? Pc[(i0 + r) * nbm + c] : Ar::zero();
-#pragma unroll
-          for (int q = 0; q < kGjTile; ++q) rv[q] = j0 + q < n ? Rx[c * n + j0 + q] : Ar::zero();
-#pragma unroll
-          for (int r = 0; r < kGjTile; ++r)
-#pragma unroll
-            for (int q = 0; q < kGjTile; ++q) acc[r][q] = Ar::fms(acc[r][q], pv[r], rv[q]);
-        }
-#pragma unroll
-        for (int r = 0; r < kGjTile; ++r)
-#pragma unroll
-          for (int q = 0; q < kGjTile; ++q) {
-            const int i = i0 + r, j = j0 + q;
-            if (i >= n || j >= n) continue;
-            W[(size_t)i * n + j] = (i >= K && i < K + bs) ? Rx[(i - K) * n + j] : acc[r][q];
-          }
-      }
-      __syncthreads();
-    }
+    gj_invert<Ar>(W, n, n, nbm, Pc, Rx, Dg);
     // x = W X gamma (a warp per row), y = W^T gamma (a thread per column)
     {
       const int lane = tid & 31, warp = tid >> 5;
@@ -305,7 +229,8 @@ static unsigned nblk(long long work, int threads) {
   return (unsigned)b;
 }
 
-cudaError_t launch_backward(const BackwardArgs& b, const double* dLdP, cudaStream_t s) {
+cudaError_t launch_backward_weights(const BackwardArgs& b, const double* dLdP, cudaStream_t s,
+                                    const double2** beta) {
   const GridDesc& g = b.grid;
   const int L = g.L;
   // gbar = adjoint DFT of dL/dP: table dims nout -> evaluated dims (radix..., half)
@@ -345,27 +270,44 @@ cudaError_t launch_backward(const BackwardArgs& b, const double* dLdP, cudaStrea
   if ((err = cudaGetLastError()) != cudaSuccess) return err;
   k_adj_beta0<<<1, 1024, 0, s>>>(nxt, g.n_eval);
   if ((err = cudaGetLastError()) != cudaSuccess) return err;
-  BackwardArgs bb = b;
-  bb.beta = nxt;
+  *beta = nxt;
+  return cudaSuccess;
+}
+
+cudaError_t launch_backward_reduce(const BackwardArgs& b, int nparts, cudaStream_t s) {
+  const long long work = (long long)b.n * b.n + b.n;
+  if (b.df)
+    k_backward_reduce<ArDF><<<nblk(work, 256), 256, 0, s>>>(b.partS, b.partg, nparts, b.n, b.outS, b.outg);
+  else
+    k_backward_reduce<ArF64><<<nblk(work, 256), 256, 0, s>>>(b.partS, b.partg, nparts, b.n, b.outS, b.outg);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_backward_points(const BackwardArgs& b, cudaStream_t s) {
+  cudaError_t err;
   const size_t smem = backward_smem_bytes(b.n, b.nb);
   if (b.ev0 && (err = cudaEventRecord(b.ev0, s)) != cudaSuccess) return err;
   if (b.df) {
     err = cudaFuncSetAttribute(k_backward_gj<ArDF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
-    k_backward_gj<ArDF><<<b.nparts, kGjThreads, smem, s>>>(bb);
+    k_backward_gj<ArDF><<<b.nparts, kGjThreads, smem, s>>>(b);
   } else {
     err = cudaFuncSetAttribute(k_backward_gj<ArF64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
-    k_backward_gj<ArF64><<<b.nparts, kGjThreads, smem, s>>>(bb);
+    k_backward_gj<ArF64><<<b.nparts, kGjThreads, smem, s>>>(b);
   }
   if ((err = cudaGetLastError()) != cudaSuccess) return err;
   if (b.ev1 && (err = cudaEventRecord(b.ev1, s)) != cudaSuccess) return err;
-  const long long work = (long long)b.n * b.n + b.n;
-  if (b.df)
-    k_backward_reduce<ArDF><<<nblk(work, 256), 256, 0, s>>>(b.partS, b.partg, b.nparts, b.n, b.outS, b.outg);
-  else
-    k_backward_reduce<ArF64><<<nblk(work, 256), 256, 0, s>>>(b.partS, b.partg, b.nparts, b.n, b.outS, b.outg);
-  return cudaGetLastError();
+  return launch_backward_reduce(b, b.nparts, s);
+}
+
+cudaError_t launch_backward(const BackwardArgs& b, const double* dLdP, cudaStream_t s) {
+  const double2* beta = nullptr;
+  cudaError_t err = launch_backward_weights(b, dLdP, s, &beta);
+  if (err != cudaSuccess) return err;
+  BackwardArgs bb = b;
+  bb.beta = beta;
+  return launch_backward_points(bb, s);
 }
 
 }  // namespace gbsbin

@@ -426,6 +426,7 @@ int gbsbin_fock_diagnostics(gbsbin_fock_plan* P, gbsbin_diag* out, void* stream)
   out->kernel = P->kernel;
   out->point_kernel_ms = 0.0;
   out->backward_kernel_ms = 0.0;
+  out->backward_path = 0;
   out->state_upload_bytes = (long long)P->state_bytes;
   out->launches = P->executed ? 2 : 0;            // the Fock kernel and the fused DFT
   if (P->ev1 && P->executed) {

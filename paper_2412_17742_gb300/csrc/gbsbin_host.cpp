@@ -10,6 +10,7 @@
 #include <new>
 #include <vector>
 
+#include "gbsbin_backward_tree.h"
 #include "gbsbin_host_state.h"
 #include "gbsbin_internal.h"
 
@@ -78,6 +79,11 @@ struct gbsbin_plan {
   long long bws_slot_bytes = 0;       // per-SM slot of d_bws (the reverse pass's matrices)
   cudaEvent_t ev_b0 = nullptr, ev_b1 = nullptr;   // want_timing: around the reverse per-point kernel
   bool backward_ran = false;
+  // reverse pass along the large-matrix tree (non-shard tree plans where it pays)
+  bool bwd_tree = false;
+  BwdTree bt{};
+  long long bt_parents = 0, bt_wave = 0;
+  unsigned char* d_bt = nullptr;      // parent buffers of one wave, leaf partials, pinv
   // pinned staging for uploads
   // two pinned staging buffers used in turn, each with the event recorded after the copy
   // that last read it: an upload waits only for the copy two uploads back
@@ -416,7 +422,7 @@ void free_device(gbsbin_plan* P) {
   if (P->ev1) cudaEventDestroy(P->ev1);
   if (P->ev_b0) cudaEventDestroy(P->ev_b0);
   if (P->ev_b1) cudaEventDestroy(P->ev_b1);
-  void* bw[] = {P->d_adjA, P->d_adjB, P->d_bws, P->d_partS, P->d_partg, P->d_outS, P->d_outg};
+  void* bw[] = {P->d_adjA, P->d_adjB, P->d_bws, P->d_partS, P->d_partg, P->d_outS, P->d_outg, P->d_bt};
   for (void* q : bw)
     if (q) cudaFree(q);
 }
@@ -714,16 +720,29 @@ void record_inputs(gbsbin_plan* P, const gbsbin_problem* p) {
 
 // ------------------------------------------------------------ reverse-pass helpers
 // C = A B for n x n row-major complex matrices (i, k, j loop order).
+// C = A B (n x n, complex, row-major): rows of C in parallel on the host threads, each row
+// accumulated over k in order with the products written out in real arithmetic (the library's
+// complex operator would guard every product against infinities).
 void matmul(const std::vector<cd>& A, const std::vector<cd>& B, std::vector<cd>& C, int n) {
   C.assign((size_t)n * n, 0.0);
-  for (int i = 0; i < n; ++i)
-    for (int k = 0; k < n; ++k) {
-      const cd a = A[(size_t)i * n + k];
-      if (a == cd(0.0)) continue;
-      const cd* b = &B[(size_t)k * n];
-      cd* c = &C[(size_t)i * n];
-      for (int j = 0; j < n; ++j) c[j] += a * b[j];
+  const double* a = reinterpret_cast<const double*>(A.data());
+  const double* b = reinterpret_cast<const double*>(B.data());
+  double* c = reinterpret_cast<double*>(C.data());
+  parallel_run(n >= 64 ? host_threads() : 1, [&](int t, int nt) {
+    for (int i = t; i < n; i += nt) {
+      double* ci = c + (size_t)2 * i * n;
+      for (int k = 0; k < n; ++k) {
+        const double ar = a[2 * ((size_t)i * n + k)], ai = a[2 * ((size_t)i * n + k) + 1];
+        if (ar == 0.0 && ai == 0.0) continue;
+        const double* bk = b + (size_t)2 * k * n;
+        for (int j = 0; j < n; ++j) {
+          const double br = bk[2 * j], bi = bk[2 * j + 1];
+          ci[2 * j] += ar * br - ai * bi;
+          ci[2 * j + 1] += ar * bi + ai * br;
+        }
+      }
     }
+  });
 }
 
 std::vector<cd> transpose(const std::vector<cd>& A, int n) {
@@ -733,8 +752,6 @@ std::vector<cd> transpose(const std::vector<cd>& A, int n) {
   return T;
 }
 
-// Launch the FP64 point kernel for the current state with the LU factors and exponent
-// solutions kept for the reverse pass.
 // The blocked FP32 + refinement kernel, with its trace updates on the CUDA cores or on the
 // tensor cores.
 inline bool is_blk(int kernel) { return kernel == GBSBIN_KERNEL_BLK_FP32R || kernel == GBSBIN_KERNEL_BLK_TC_FP32R; }
@@ -964,6 +981,64 @@ void tree_pointers(gbsbin_plan* P, const Stage& sl) {
     t.path[l + 1] = q;
     q += (size_t)nodes * 3;
   }
+}
+
+// The reverse pass along the large-matrix tree (gbsbin_backward_tree.cu): E = the rows of
+// groups 0 .. L-2, F = the last group's; per parent the inverse of M_EE and its products, per
+// leaf the inverse of the mF x mF Schur complement.  Taken when its multiply-adds are under
+// half those of one n x n inverse per evaluated point; parents in waves whose buffers stay
+// within 512 MB.
+int backward_tree_setup(gbsbin_plan* P) {
+  const int n = P->n, L = P->L;
+  if (L < 2) return GBSBIN_OK;
+  int mF = 0;
+  for (int x : P->label) mF += x == L - 1;
+  const int mE = n - mF;
+  const GridDesc& g = P->grid;
+  const long long parents = g.npts / g.radix[L - 1], half = g.half;
+  const double E = mE, F = mF;
+  const double per_parent = E * E * E + 2.0 * E * E * F + E * F * F + (F * F * E + E * E * F + E * F * F);
+  const double tree = (double)parents * per_parent + (double)g.n_eval * F * F * F;
+  if (!(tree < 0.5 * (double)g.n_eval * (double)n * n * n)) return GBSBIN_OK;
+  BwdTree& t = P->bt;
+  t.L = L;
+  t.mE = mE;
+  t.mF = mF;
+  t.D = n + 1;
+  t.A0 = P->btree.mat[0];
+  t.half = half;
+  t.pstride = (long long)n * n + 2LL * n;
+  t.lstride = 2LL * mF * mF + 2LL * mF + 1;
+  int off = 0;
+  for (int l = 0; l < L; ++l) {
+    t.goff[l] = off;
+    for (int x : P->label) off += x == l;
+  }
+  t.goff[L] = off;
+  const long long budget = 512LL << 20;
+  const long long wave = std::max(1LL, std::min(parents, budget / (t.pstride * 16)));
+  t.per = (int)((wave * half + P->num_sms - 1) / P->num_sms);
+  t.maxspan = (int)((t.per - 1) / half + 2);
+  t.nparts = (int)std::min<long long>(parents, P->num_sms);
+  const size_t pbuf = (size_t)wave * t.pstride * 16;
+  const size_t part = (size_t)P->num_sms * t.maxspan * t.lstride * 16;
+  const size_t pinv = ((size_t)n * sizeof(int) + 15) / 16 * 16;
+  int st = dalloc(&P->d_bt, pbuf + part + pinv);
+  if (st) return st;
+  t.pbuf = P->d_bt;
+  t.part = P->d_bt + pbuf;
+  std::vector<int> inv(n);
+  for (int a = 0; a < n; ++a) inv[P->tree_perm[a]] = a;
+  int* d_pinv = reinterpret_cast<int*>(P->d_bt + pbuf + part);
+  if (cudaMemcpy(d_pinv, inv.data(), n * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaGetLastError();
+    return GBSBIN_ERR_CUDA;
+  }
+  t.pinv = d_pinv;
+  P->bt_parents = parents;
+  P->bt_wave = wave;
+  P->bwd_tree = true;
+  return GBSBIN_OK;
 }
 
 int choose_kernel(int n, int L, int precision, int override_id, int has_gamma) {
@@ -1275,6 +1350,11 @@ static int plan_create_impl(const gbsbin_problem* p, const gbsbin_options* o, gb
       return st;
     }
   }
+  if (opt.want_backward && is_btree(P->kernel) && !sharded && (st = backward_tree_setup(P))) {
+    free_device(P);
+    delete P;
+    return st;
+  }
   if (opt.want_timing &&
       (cudaEventCreate(&P->ev0) != cudaSuccess || cudaEventCreate(&P->ev1) != cudaSuccess ||
        (opt.want_backward && (cudaEventCreate(&P->ev_b0) != cudaSuccess || cudaEventCreate(&P->ev_b1) != cudaSuccess)))) {
@@ -1518,6 +1598,7 @@ int gbsbin_diagnostics(gbsbin_plan* P, gbsbin_diag* out, void* stream) {
     out->point_kernel_ms = ms;
   }
   out->backward_kernel_ms = 0.0;
+  out->backward_path = !P->opt.want_backward ? 0 : P->bwd_tree ? 2 : 1;
   if (P->ev_b1 && P->backward_ran) {
     float ms = 0.f;
     if (cudaEventSynchronize(P->ev_b1) != cudaSuccess ||
@@ -1579,7 +1660,23 @@ static int backward_enqueue(gbsbin_plan* P, const double* dLdP, cudaStream_t s) 
   b.outg = P->d_outg;
   b.ev0 = P->ev_b0;
   b.ev1 = P->ev_b1;
-  if (launch_backward(b, dLdP, s) != cudaSuccess) {
+  cudaError_t e;
+  if (!P->bwd_tree) {
+    e = launch_backward(b, dLdP, s);
+  } else {                                          // along the tree, parents in waves
+    e = launch_backward_weights(b, dLdP, s, &b.beta);
+    if (e == cudaSuccess && b.ev0) e = cudaEventRecord(b.ev0, s);
+    for (long long p0 = 0; e == cudaSuccess && p0 < P->bt_parents; p0 += P->bt_wave) {
+      BwdTree t = P->bt;
+      t.p0 = p0;
+      t.p1 = std::min(P->bt_parents, p0 + P->bt_wave);
+      t.zero_partials = p0 == 0;
+      e = launch_backward_tree_wave(b, t, s);
+    }
+    if (e == cudaSuccess && b.ev1) e = cudaEventRecord(b.ev1, s);
+    if (e == cudaSuccess) e = launch_backward_reduce(b, P->bt.nparts, s);
+  }
+  if (e != cudaSuccess) {
     cudaGetLastError();
     return GBSBIN_ERR_CUDA;
   }
