@@ -19,13 +19,16 @@
 // the square root continuous from w = 0), solves for the kept modes' columns and gamma_D,
 // forms M, l, e, and the Taylor coefficients of exp(xi^T M xi / 2 + l^T xi) by
 // (p_i + 1) c_{p + e_i} = l_i c_p + sum_j M_ij c_{p - e_j} (shells of equal total degree in
-// parallel); the same CTA also evaluates the heralding probability's generating function,
-// every non-heralding mode traced.  An inverse DFT over the grid, one axis per launch, then
-// extracts [w^b] for every coefficient.  FP64 throughout.
+// parallel, from a table of each coefficient's neighbours).  The heralding probability's
+// generating function (every non-heralding mode traced, w = 1 on the kept ones) continues the
+// same elimination into the kept block: its Schur complement is I - X_F M, so it is
+// exp(e + l^T (I - X_F M)^{-1} X_F l / 2) / sqrt(det(I - X D A_DD) det(I - X_F M)), the
+// branch Sum Log of the pivots of the whole unpivoted elimination.  An inverse DFT over the
+// grid, one axis per launch, then extracts [w^b] for every coefficient.  FP64 throughout.
 #include <cuda_runtime.h>
 
 #include "gbsbin_device.cuh"
-#include "gbsbin_internal.h"
+#include "gbsbin_herald.h"
 
 namespace gbsbin {
 namespace {
@@ -35,27 +38,11 @@ constexpr int HT = 256;
 __device__ __forceinline__ double2 cadd2(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ double2 cneg2(double2 a) { return make_double2(-a.x, -a.y); }
 
-// Root of the group of mode m at grid point k (1 for a non-heralding mode).
-__device__ __forceinline__ double2 mode_root(const HeraldArgs& a, long long k, int m) {
-  const int l = a.role[m];
-  if (l < 0) return make_double2(1.0, 0.0);
-  long long rest = k;
-  int d = 0;
-  for (int q = a.L - 1; q >= 0; --q) {
-    const long long up = rest / a.radix[q];
-    if (q == l) d = (int)(rest - up * a.radix[q]);
-    rest = up;
-  }
-  int off = 0;
-  for (int q = 0; q < l; ++q) off += a.radix[q];
-  const double2 t = a.tw[off + d];                   // exp(-2 pi i d / R)
-  return make_double2(t.x, -t.y);
-}
-
 // Unpivoted elimination of the nr x nr block of G (row stride ld) with ncol right-hand-side
-// columns after it, then back substitution: the columns become the block's inverse times
-// themselves.  Returns sum Log(pivots) (each Re > 0) and the smallest pivot real part in
-// thread 0's registers; all threads call it.
+// columns after it, then back substitution (column by column: each solved entry updates the
+// rows above it in parallel): the columns become the block's inverse times themselves.
+// Returns sum Log(pivots) (each Re > 0) and the smallest pivot real part in thread 0's
+// registers; all threads call it.
 __device__ void solve_block(double2* G, int nr, int ncol, int ld, double2* ldet, double* minre) {
   const int tid = threadIdx.x, T = blockDim.x;
   const int cols = nr + ncol;
@@ -77,12 +64,12 @@ __device__ void solve_block(double2* G, int nr, int ncol, int ld, double2* ldet,
     }
     __syncthreads();
   }
-  for (int k = nr - 1; k >= 0; --k) {                // x_k = (rhs_k - sum_{j > k} u_kj x_j) / u_kk
-    const double2 r = crecip(G[k * ld + k]);
-    for (int c = tid; c < ncol; c += T) {
-      double2 s = G[k * ld + nr + c];
-      for (int j = k + 1; j < nr; ++j) s = cfnma(s, G[k * ld + j], G[j * ld + nr + c]);
-      G[k * ld + nr + c] = cmul(s, r);
+  for (int k = nr - 1; k >= 0; --k) {                // x_k = rhs_k / u_kk; rhs_i -= u_ik x_k, i < k
+    if (tid < ncol) G[k * ld + nr + tid] = cmul(G[k * ld + nr + tid], crecip(G[k * ld + k]));
+    __syncthreads();
+    for (int idx = tid; idx < k * ncol; idx += T) {
+      const int i = idx / ncol, c = idx - (idx / ncol) * ncol;
+      G[i * ld + nr + c] = cfnma(G[i * ld + nr + c], G[i * ld + k], G[k * ld + nr + c]);
     }
     __syncthreads();
   }
@@ -93,19 +80,32 @@ __device__ void solve_block(double2* G, int nr, int ncol, int ld, double2* ldet,
 __global__ void __launch_bounds__(HT) k_herald_points(HeraldArgs a) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   const long long k = blockIdx.x;
-  const int nd = a.nd, nf = a.nf, n2 = a.n2, tid = threadIdx.x, T = blockDim.x;
+  const int nd = a.nd, nf = a.nf, tid = threadIdx.x, T = blockDim.x;
   const int cols = nd + nf + 1;
-  const size_t gsz = (size_t)nd * cols > (size_t)n2 * (n2 + 1) ? (size_t)nd * cols : (size_t)n2 * (n2 + 1);
-  double2* G = reinterpret_cast<double2*>(sm_raw);   // nd x cols (the kept solve), then n2 x (n2 + 1)
-  double2* Mq = G + gsz;                              // nf x nf
+  double2* G = reinterpret_cast<double2*>(sm_raw);   // nd x cols
+  double2* Mq = G + (size_t)nd * cols;                // nf x nf
   double2* lq = Mq + nf * nf;                         // nf
-  double2* sc = lq + nf;                              // e, log det, e_all, log det_all
+  double2* sc = lq + nf;                              // e, log det
+  double2* wg = sc + 2;                               // the heralding groups' roots at this point
+  double2* wd = wg + GBSBIN_MAX_L;                    // the root of each D row's mode
+  if (tid < a.L) {                                    // digit of group tid, w = exp(2 pi i d / R)
+    long long rest = k;
+    for (int q = a.L - 1; q > tid; --q) rest /= a.radix[q];
+    const int d = (int)(rest % a.radix[tid]);
+    int off = 0;
+    for (int q = 0; q < tid; ++q) off += a.radix[q];
+    const double2 t = a.tw[off + d];
+    wg[tid] = make_double2(t.x, -t.y);
+  }
+  __syncthreads();
+  for (int i = tid; i < nd; i += T) wd[i] = a.dgroup[i] >= 0 ? wg[a.dgroup[i]] : make_double2(1.0, 0.0);
+  __syncthreads();
   // I - X D(w) A_DD with the right-hand sides X D(w) [A_DF | gamma_D]; row i of X D A is
   // w_{partner(i)} A_{partner(i), .}
   for (int idx = tid; idx < nd * cols; idx += T) {
     const int i = idx / cols, j = idx - (idx / cols) * cols;
     const int pi = a.dpart[i];                        // X partner of row i within D
-    const double2 w = mode_root(a, k, a.dmode[pi]);
+    const double2 w = wd[pi];
     double2 v;
     if (j < nd) v = cneg2(cmul(w, a.ADD[(size_t)pi * nd + j]));
     else if (j < nd + nf) v = cmul(w, a.ADF[(size_t)pi * nf + (j - nd)]);
@@ -132,39 +132,48 @@ __global__ void __launch_bounds__(HT) k_herald_points(HeraldArgs a) {
     sc[1] = ld;
   }
   __syncthreads();
-  // the heralding probability: I - X D(w) A over every mode (w = 1 off the heralding groups),
-  // right-hand side X D(w) gamma
-  {
-    const int cn = n2 + 1;
-    for (int idx = tid; idx < n2 * cn; idx += T) {
-      const int i = idx / cn, j = idx - (idx / cn) * cn;
-      const int pi = i < n2 / 2 ? i + n2 / 2 : i - n2 / 2;
-      const double2 w = mode_root(a, k, pi % (n2 / 2));
-      double2 v = j < n2 ? cneg2(cmul(w, a.Aall[(size_t)pi * n2 + j])) : cmul(w, a.gall[pi]);
-      if (j == i) v.x += 1.0;
-      G[idx] = v;
+  // the heralding probability's value: the kept block's Schur complement I - X_F M (X_F swaps
+  // the kept modes' halves) with the right-hand side X_F l, eliminated by one thread
+  if (tid == 0) {
+    const int h = nf / 2;
+    double2 Tm[GBSBIN_HERALD_MAX_F][GBSBIN_HERALD_MAX_F + 1];
+    for (int i = 0; i < nf; ++i) {
+      const int pi = i < h ? i + h : i - h;
+      for (int j = 0; j < nf; ++j) Tm[i][j] = cneg2(Mq[pi * nf + j]);
+      Tm[i][i].x += 1.0;
+      Tm[i][nf] = lq[pi];
     }
-    __syncthreads();
-    double2 lda;
-    double mna;
-    solve_block(G, n2, 1, cn, &lda, &mna);
-    if (tid == 0) {
-      double2 e = make_double2(0.0, 0.0);
-      for (int d = 0; d < n2; ++d) e = cadd2(e, cmul(a.gall[d], G[d * cn + n2]));
-      const double re = 0.5 * e.x - 0.5 * lda.x, im = 0.5 * e.y - 0.5 * lda.y;
-      const double m = exp(re);
-      double s, c;
-      sincos(im, &s, &c);
-      a.gcoef[(size_t)k * (a.ncoef + 1) + a.ncoef] = make_double2(m * c, m * s);
-      a.minpiv[k] = fmin(mn, mna);
+    double2 lf = make_double2(0.0, 0.0);
+    double mnf = 1e300;
+    for (int c = 0; c < nf; ++c) {
+      const double2 piv = Tm[c][c];
+      lf = cadd2(lf, make_double2(0.5 * log(fma(piv.x, piv.x, piv.y * piv.y)), atan2(piv.y, piv.x)));
+      mnf = fmin(mnf, piv.x);
+      if (!(piv.x == piv.x) || !(piv.y == piv.y)) mnf = -1e300;
+      const double2 r = crecip(piv);
+      for (int i = c + 1; i < nf; ++i) {
+        const double2 li = cmul(Tm[i][c], r);
+        for (int j = c + 1; j <= nf; ++j) Tm[i][j] = cfnma(Tm[i][j], li, Tm[c][j]);
+      }
     }
-    __syncthreads();
+    double2 y[GBSBIN_HERALD_MAX_F];
+    for (int i = nf - 1; i >= 0; --i) {
+      double2 s = Tm[i][nf];
+      for (int j = i + 1; j < nf; ++j) s = cfnma(s, Tm[i][j], y[j]);
+      y[i] = cmul(s, crecip(Tm[i][i]));
+    }
+    double2 ly = make_double2(0.0, 0.0);
+    for (int i = 0; i < nf; ++i) ly = cadd2(ly, cmul(lq[i], y[i]));
+    const double re = sc[0].x + 0.5 * ly.x - 0.5 * (ld.x + lf.x), im = sc[0].y + 0.5 * ly.y - 0.5 * (ld.y + lf.y);
+    const double m = exp(re);
+    double s, c;
+    sincos(im, &s, &c);
+    a.gcoef[(size_t)k * (a.ncoef + 1) + a.ncoef] = make_double2(m * c, m * s);
+    a.minpiv[k] = fmin(mn, mnf);
   }
-  // Taylor coefficients by shells of total degree; the tensor lives in global memory (this
-  // point's slot of ncoef + 1 entries, the last the heralding probability's value), index
-  // p = sum_i p_i (c + 1)^(nf - 1 - i)
+  // Taylor coefficients by shells of total degree, in this point's slot of ncoef + 1 entries
+  // (index p = sum_i p_i (c + 1)^(nf - 1 - i)), from the plan's table of neighbours
   double2* C = a.gcoef + (size_t)k * (a.ncoef + 1);
-  const int cp1 = a.cut + 1;
   const double2 e = sc[0], l0 = sc[1];
   const double m0 = exp(e.x - 0.5 * l0.x);
   double s0, c0;
@@ -172,30 +181,14 @@ __global__ void __launch_bounds__(HT) k_herald_points(HeraldArgs a) {
   if (tid == 0) C[0] = make_double2(m0 * c0, m0 * s0);   // exp(e) / sqrt(det) times c_0 = 1
   __syncthreads();
   for (int shell = 1; shell <= nf * a.cut; ++shell) {
-    for (long long q = tid; q < a.ncoef; q += T) {
-      int p[GBSBIN_HERALD_MAX_F];
-      long long rest = q;
-      int tot = 0;
-      for (int i = nf - 1; i >= 0; --i) {
-        p[i] = (int)(rest % cp1);
-        rest /= cp1;
-        tot += p[i];
-      }
-      if (tot != shell) continue;
-      int i0 = 0;
-      while (p[i0] == 0) ++i0;
-      long long stride_i0 = 1;
-      for (int i = nf - 1; i > i0; --i) stride_i0 *= cp1;
-      const long long qm = q - stride_i0;             // p - e_i0
-      double2 val = cmul(lq[i0], C[qm]);
-      long long stride_j = 1;
-      for (int j = nf - 1; j >= 0; --j) {
-        const int pj = p[j] - (j == i0 ? 1 : 0);
-        if (pj > 0) val = cadd2(val, cmul(Mq[i0 * nf + j], C[qm - stride_j]));
-        stride_j *= cp1;
-      }
-      const double inv = 1.0 / (double)p[i0];
-      C[q] = make_double2(val.x * inv, val.y * inv);
+    for (int t = a.shell[shell] + tid; t < a.shell[shell + 1]; t += T) {
+      const int i0 = a.ti0[t];
+      double2 val = cmul(lq[i0], C[a.tqm[t]]);
+      const int* nb = a.tnb + (size_t)t * nf;
+      for (int j = 0; j < nf; ++j)
+        if (nb[j] >= 0) val = cadd2(val, cmul(Mq[i0 * nf + j], C[nb[j]]));
+      const double inv = 1.0 / (double)a.tp[t];
+      C[a.tq[t]] = make_double2(val.x * inv, val.y * inv);
     }
     __syncthreads();
   }
@@ -256,8 +249,8 @@ __global__ void k_herald_dft_axis(HeraldArgs a, int l, const double2* __restrict
 }  // namespace
 
 size_t herald_smem_bytes(int nd, int nf, int n2) {
-  const size_t a = (size_t)nd * (nd + nf + 1), b = (size_t)n2 * (n2 + 1);
-  return sizeof(double2) * ((a > b ? a : b) + (size_t)nf * nf + nf + 4);
+  (void)n2;
+  return sizeof(double2) * ((size_t)nd * (nd + nf + 1) + (size_t)nf * nf + nf + 2 + GBSBIN_MAX_L + nd);
 }
 
 cudaError_t launch_herald(const HeraldArgs& a, double2* out, double* prob, cudaStream_t s) {

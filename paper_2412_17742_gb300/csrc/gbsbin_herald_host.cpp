@@ -7,8 +7,8 @@
 #include <new>
 #include <vector>
 
+#include "gbsbin_herald.h"
 #include "gbsbin_host_state.h"
-#include "gbsbin_internal.h"
 
 using cd = std::complex<double>;
 using namespace gbsbin;
@@ -155,12 +155,48 @@ int gbsbin_herald_plan_create(const gbsbin_herald_problem* p, const gbsbin_optio
     for (int j = 0; j < nf; ++j) AFF[(size_t)i * nf + j] = A[(size_t)F[i] * n2 + F[j]];
     gF[i] = gamma[F[i]];
   }
-  std::vector<int> dpart(nd), dmode(nd);
+  std::vector<int> dpart(nd), dgroup(nd);
   const int hd = nd / 2;
   for (int i = 0; i < nd; ++i) {
     dpart[i] = i < hd ? i + hd : i - hd;
-    dmode[i] = Dm[i % hd];
+    dgroup[i] = p->role[Dm[i % hd]] >= 0 ? p->role[Dm[i % hd]] : -1;
   }
+  // the Taylor coefficients in order of total degree, each with its predecessor p - e_i0 (i0
+  // its first non-zero digit) and that predecessor's neighbours p - e_i0 - e_j
+  const int cp1 = cut + 1, nsh = nf * cut;
+  std::vector<std::vector<int>> by_shell((size_t)nsh + 1);
+  for (long long q = 1; q < ncoef; ++q) {
+    long long r = q;
+    int tot = 0;
+    for (int i = 0; i < nf; ++i) {
+      tot += (int)(r % cp1);
+      r /= cp1;
+    }
+    by_shell[tot].push_back((int)q);
+  }
+  std::vector<int> shell((size_t)nsh + 2, 0), tq, tqm, ti0, tp, tnb;
+  std::vector<long long> stride(nf);
+  stride[nf - 1] = 1;
+  for (int i = nf - 2; i >= 0; --i) stride[i] = stride[i + 1] * cp1;
+  for (int sh = 1; sh <= nsh; ++sh) {
+    shell[sh] = (int)tq.size();
+    for (int q : by_shell[sh]) {
+      int dig[GBSBIN_HERALD_MAX_F];
+      for (int i = 0; i < nf; ++i) dig[i] = (int)((q / stride[i]) % cp1);
+      int i0 = 0;
+      while (dig[i0] == 0) ++i0;
+      const long long qm = q - stride[i0];
+      tq.push_back(q);
+      tqm.push_back((int)qm);
+      ti0.push_back(i0);
+      tp.push_back(dig[i0]);
+      for (int j = 0; j < nf; ++j) {
+        const int dj = dig[j] - (j == i0 ? 1 : 0);
+        tnb.push_back(dj > 0 ? (int)(qm - stride[j]) : -1);
+      }
+    }
+  }
+  shell[nsh + 1] = (int)tq.size();
   const double TWO_PI = 6.283185307179586476925286766559;
   std::vector<double2> tw((size_t)rsum);
   for (int l = 0, off = 0; l < L; off += a.radix[l], ++l)
@@ -186,21 +222,23 @@ int gbsbin_herald_plan_create(const gbsbin_herald_problem* p, const gbsbin_optio
   a.pr0 = std::exp(-lq1.real());
 
   Blob b;
-  std::vector<int> role(p->role, p->role + nm);
-  const size_t o_role = b.put(role.data(), role.size() * sizeof(int));
+  const size_t o_dgroup = b.put(dgroup.data(), dgroup.size() * sizeof(int));
   const size_t o_dpart = b.put(dpart.data(), dpart.size() * sizeof(int));
-  const size_t o_dmode = b.put(dmode.data(), dmode.size() * sizeof(int));
   const size_t o_tw = b.put(tw.data(), tw.size() * sizeof(double2));
   const std::vector<double2> vADD = to_d2(ADD), vADF = to_d2(ADF), vAFF = to_d2(AFF), vgD = to_d2(gD),
-                             vgF = to_d2(gF), vA = to_d2(A), vg = to_d2(gamma);
+                             vgF = to_d2(gF);
   const size_t o_ADD = b.put(vADD.data(), vADD.size() * sizeof(double2));
   const size_t o_ADF = b.put(vADF.data(), vADF.size() * sizeof(double2));
   const size_t o_AFF = b.put(vAFF.data(), vAFF.size() * sizeof(double2));
   const size_t o_gD = b.put(vgD.data(), vgD.size() * sizeof(double2));
   const size_t o_gF = b.put(vgF.data(), vgF.size() * sizeof(double2));
-  const size_t o_A = b.put(vA.data(), vA.size() * sizeof(double2));
-  const size_t o_g = b.put(vg.data(), vg.size() * sizeof(double2));
   const size_t o_chs = b.put(chs.data(), chs.size() * sizeof(double));
+  const size_t o_shell = b.put(shell.data(), shell.size() * sizeof(int));
+  const size_t o_tq = b.put(tq.data(), tq.size() * sizeof(int));
+  const size_t o_tqm = b.put(tqm.data(), tqm.size() * sizeof(int));
+  const size_t o_ti0 = b.put(ti0.data(), ti0.size() * sizeof(int));
+  const size_t o_tp = b.put(tp.data(), tp.size() * sizeof(int));
+  const size_t o_tnb = b.put(tnb.data(), tnb.size() * sizeof(int));
 
   gbsbin_herald_plan* P = new (std::nothrow) gbsbin_herald_plan();
   if (!P) return GBSBIN_ERR_NOMEM;
@@ -225,18 +263,21 @@ int gbsbin_herald_plan_create(const gbsbin_herald_problem* p, const gbsbin_optio
     return GBSBIN_ERR_CUDA;
   }
   unsigned char* c = P->d_const;
-  a.role = reinterpret_cast<const int*>(c + o_role);
+  a.dgroup = reinterpret_cast<const int*>(c + o_dgroup);
   a.dpart = reinterpret_cast<const int*>(c + o_dpart);
-  a.dmode = reinterpret_cast<const int*>(c + o_dmode);
   a.tw = reinterpret_cast<const double2*>(c + o_tw);
   a.ADD = reinterpret_cast<const double2*>(c + o_ADD);
   a.ADF = reinterpret_cast<const double2*>(c + o_ADF);
   a.AFF = reinterpret_cast<const double2*>(c + o_AFF);
   a.gD = reinterpret_cast<const double2*>(c + o_gD);
   a.gF = reinterpret_cast<const double2*>(c + o_gF);
-  a.Aall = reinterpret_cast<const double2*>(c + o_A);
-  a.gall = reinterpret_cast<const double2*>(c + o_g);
   a.chscale = reinterpret_cast<const double*>(c + o_chs);
+  a.shell = reinterpret_cast<const int*>(c + o_shell);
+  a.tq = reinterpret_cast<const int*>(c + o_tq);
+  a.tqm = reinterpret_cast<const int*>(c + o_tqm);
+  a.ti0 = reinterpret_cast<const int*>(c + o_ti0);
+  a.tp = reinterpret_cast<const int*>(c + o_tp);
+  a.tnb = reinterpret_cast<const int*>(c + o_tnb);
   a.gcoef = P->d_gcoef;
   a.scratch = P->d_scratch;
   a.minpiv = P->d_minpiv;

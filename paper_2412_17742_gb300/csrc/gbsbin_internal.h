@@ -255,38 +255,6 @@ size_t fock_smem_bytes(int nin, int L, int rsum);
 int fock_ctas_per_sm(bool df, int zt, size_t smem);      // 0: does not fit
 cudaError_t launch_fock(const FockArgs& a, bool df, int zt, cudaStream_t s);
 
-// Heralded states (gbsbin_herald.cu).  D: the heralding and traced modes' indices (first
-// halves, then second halves, nd in all), F: the kept modes' (nf); A = X XA blocks row-major.
-#define GBSBIN_HERALD_MAX_F (2 * GBSBIN_HERALD_MAX_KEPT)
-struct HeraldArgs {
-  int L, nd, nf, n2, cut;
-  int radix[GBSBIN_MAX_L];           // oversample (cutoff + 1) per heralding group
-  int nout[GBSBIN_MAX_L];            // cutoff + 1
-  long long npts;                    // prod radix
-  long long ncoef;                   // (cut + 1)^nf
-  long long table;                   // prod nout
-  double pr0;                        // Pr(0) of the whole state
-  const int* role;                   // per mode: heralding group, or < 0 (traced, kept)
-  const int* dpart;                  // [nd] the X partner of D index i (within D)
-  const int* dmode;                  // [nd] the mode of D index i
-  const double2* tw;                 // exp(-2 pi i d / radix[l]), d < radix[l], group after group
-  const double2* ADD;                // nd x nd
-  const double2* ADF;                // nd x nf
-  const double2* AFF;                // nf x nf
-  const double2* gD;                 // nd
-  const double2* gF;                 // nf
-  const double2* Aall;               // n2 x n2 (every mode)
-  const double2* gall;               // n2
-  const double* chscale;             // [ncoef] prod_i sqrt(p_i!)
-  double2* gcoef;                    // npts x (ncoef + 1): Taylor coefficients at each point, then
-                                     // the heralding probability's generating function
-  double2* scratch;                  // npts x (ncoef + 1): the inverse DFT's other buffer
-  double* minpiv;                    // npts: smallest pivot real part of both eliminations
-  double* prob_own;                  // table: the plan's copy of Pr(b) (diagnostics)
-};
-size_t herald_smem_bytes(int nd, int nf, int n2);
-cudaError_t launch_herald(const HeraldArgs& a, double2* out, double* prob, cudaStream_t s);
-
 // Kernel launchers (return the launch error).
 cudaError_t launch_points(const PointArgs& a, int kernel, int num_sms, cudaStream_t s);
 cudaError_t launch_points_warp(const PointArgs& a, int num_sms, cudaStream_t s);
