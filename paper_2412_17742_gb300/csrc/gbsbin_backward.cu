@@ -137,6 +137,7 @@ __global__ void __launch_bounds__(kGjThreads) k_backward_gj(BackwardArgs b) {
   E* xv = xgE + n;                                    // n: x = W X gamma
   E* yv = xv + n;                                     // n: y = W^T gamma
   double2* wr = reinterpret_cast<double2*>(yv + n);   // L: this point's roots
+  E* Rn = b.rn ? reinterpret_cast<E*>(wr + GBSBIN_MAX_L) : nullptr;   // nb x n, if it fits
   E* W = reinterpret_cast<E*>(reinterpret_cast<char*>(b.ws) + (size_t)blockIdx.x * (size_t)b.ws_slot_bytes);
   E* ST = reinterpret_cast<E*>(b.partS) + (size_t)blockIdx.x * n * n;
   E* sg = reinterpret_cast<E*>(b.partg) + (size_t)blockIdx.x * n;
@@ -163,7 +164,7 @@ __global__ void __launch_bounds__(kGjThreads) k_backward_gj(BackwardArgs b) {
       W[t] = Ar::from(v);
     }
     __syncthreads();
-    gj_invert<Ar>(W, n, n, nbm, Pc, Rx, Dg);
+    gj_invert<Ar>(W, n, n, nbm, Pc, Rx, Dg, Rn);
     // x = W X gamma (a warp per row), y = W^T gamma (a thread per column)
     {
       const int lane = tid & 31, warp = tid >> 5;
@@ -218,6 +219,13 @@ __global__ void k_backward_reduce(const void* __restrict__ partS, const void* __
 
 size_t backward_smem_bytes(int n, int nb) {
   return (size_t)16 * ((size_t)2 * n * nb + (size_t)nb * nb + 4 * (size_t)n) + sizeof(double2) * GBSBIN_MAX_L;
+}
+
+// The shared memory with the block-row buffer (nb x n) where it fits, else without; *rn says which.
+static size_t backward_smem_choice(int n, int nb, int* rn) {
+  const size_t base = backward_smem_bytes(n, nb), with = base + (size_t)16 * nb * n;
+  *rn = with <= 226 * 1024 ? 1 : 0;
+  return *rn ? with : base;
 }
 
 int backward_block(int n) { return n <= 320 ? GBSBIN_BWD_MAX_NB : GBSBIN_BWD_MAX_NB / 2; }
@@ -283,9 +291,10 @@ cudaError_t launch_backward_reduce(const BackwardArgs& b, int nparts, cudaStream
   return cudaGetLastError();
 }
 
-cudaError_t launch_backward_points(const BackwardArgs& b, cudaStream_t s) {
+cudaError_t launch_backward_points(const BackwardArgs& b0, cudaStream_t s) {
   cudaError_t err;
-  const size_t smem = backward_smem_bytes(b.n, b.nb);
+  BackwardArgs b = b0;
+  const size_t smem = backward_smem_choice(b.n, b.nb, &b.rn);
   if (b.ev0 && (err = cudaEventRecord(b.ev0, s)) != cudaSuccess) return err;
   if (b.df) {
     err = cudaFuncSetAttribute(k_backward_gj<ArDF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -32,6 +32,11 @@ namespace {
 
 constexpr int kBtThreads = 256;
 
+// The block-row buffer (nb x n) after the kernels' other shared arrays.
+__host__ __device__ __forceinline__ size_t backward_tree_rn_offset(int n, int nb) {
+  return (size_t)16 * ((size_t)2 * n * nb + (size_t)nb * nb + 4 * (size_t)n + 1) + sizeof(double2) * GBSBIN_MAX_L;
+}
+
 struct Parent {                    // the parent's slot in pbuf
   template <class E>
   __device__ static void map(E* P, int mE, int mF, E** A, E** U, E** V, E** C, E** aE, E** eE, E** cF, E** dF) {
@@ -79,7 +84,7 @@ __global__ void __launch_bounds__(kBtThreads) k_bwdt_parent(BackwardArgs b, BwdT
       A[q] = v;
     }
     __syncthreads();
-    gj_invert<Ar>(A, mE, mE, nb, Pc, Rx, Dg);
+    gj_invert<Ar>(A, mE, mE, nb, Pc, Rx, Dg, t.rn ? reinterpret_cast<E*>(smem + backward_tree_rn_offset(n, nb)) : nullptr);
     // U = -A XA_EF, V = -XA_FE A, C = XA_FF - XA_FE U
     gemm_staged<Ar>(U, mF, A, mE, 1, A0 + mE, D, 1, mE, mF, mE, false, true, nb, Pc, Rx);
     gemm_staged<Ar>(V, mE, A0 + (size_t)mE * D, D, 1, A, mE, 1, mF, mE, mE, false, true, nb, Pc, Rx);
@@ -124,6 +129,7 @@ __global__ void __launch_bounds__(kBtThreads) k_bwdt_leaf(BackwardArgs b, BwdTre
   E* dFs = cFs + mF;
   E* sv = dFs + mF;
   E* tv = sv + mF;
+  E* Rnb = reinterpret_cast<E*>(smem + backward_tree_rn_offset(n, nb));
   E* W = reinterpret_cast<E*>(reinterpret_cast<char*>(b.ws) + (size_t)blockIdx.x * (size_t)b.ws_slot_bytes);
   const long long nleaves = (t.p1 - t.p0) * t.half;
   const long long l0 = (long long)blockIdx.x * t.per, l1 = min(l0 + t.per, nleaves);
@@ -161,7 +167,7 @@ __global__ void __launch_bounds__(kBtThreads) k_bwdt_leaf(BackwardArgs b, BwdTre
       W[q] = v;
     }
     __syncthreads();
-    gj_invert<Ar>(W, mF, mF, nb, Pc, Rx, Dg);
+    gj_invert<Ar>(W, mF, mF, nb, Pc, Rx, Dg, t.rn ? Rnb : nullptr);
     {                                                  // s = inv(S) c_F (warp per row), t = inv(S)^T d_F
       const int lane = tid & 31, warp = tid >> 5;
       for (int i = warp; i < mF; i += NT / 32) {
@@ -289,8 +295,11 @@ __global__ void __launch_bounds__(kBtThreads) k_bwdt_assemble(BackwardArgs b, Bw
 }
 
 template <class Ar>
-cudaError_t tree_wave(const BackwardArgs& b, const BwdTree& t, cudaStream_t s) {
-  const size_t smem = backward_tree_smem_bytes(b.n, b.nb);
+cudaError_t tree_wave(const BackwardArgs& b, const BwdTree& t0, cudaStream_t s) {
+  BwdTree t = t0;
+  const size_t base = backward_tree_smem_bytes(b.n, b.nb), with = base + (size_t)16 * b.nb * b.n;
+  t.rn = with <= 226 * 1024 ? 1 : 0;
+  const size_t smem = t.rn ? with : base;
   cudaError_t err;
   if ((err = cudaFuncSetAttribute(k_bwdt_parent<Ar>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
           cudaSuccess ||

@@ -28,6 +28,7 @@ struct BwdTree {
   int maxspan;              // parents one leaf CTA can touch
   int nparts;               // CTAs of the assembly launch (its partials)
   int zero_partials;        // first wave: the assembly zeroes its partials
+  int rn;                   // the kernels' shared memory holds the block-row buffer (nb x n)
 };
 
 // Adjoint of the inverse DFT and the per-point weights beta (into b.bufB); *beta receives it.

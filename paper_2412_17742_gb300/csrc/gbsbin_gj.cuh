@@ -3,7 +3,10 @@
 // blocked Gauss-Jordan elimination without pivoting, and a staged product C (+)= +-A B with
 // strided operands.  Both stage nb-wide panels in shared memory (Pc: m x nb, Rx: nb x m,
 // Dg: nb x nb) and update the matrix in 4 x 4 register tiles.  Every thread of the CTA calls
-// them; they end with a barrier.
+// them; they end with a barrier.  A thread's 4 x 4 tile takes four consecutive rows and four
+// columns tcols apart (tcols = ceil(columns / 4)), so that the threads of a warp read
+// consecutive 16-byte entries of the staged rows (no shared-memory bank conflicts) and of the
+// matrix (coalesced).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -19,10 +22,11 @@ constexpr int kGjMaxNb = 16;
 // block W_BB is inverted in shared memory (one element per thread per pivot: the scalar rule
 // w'_kk = 1/p, w'_kj = w_kj/p, w'_ik = -w_ik/p, w'_ij = w_ij - w_ik w_kj/p), the block's rows
 // become inv(W_BB) W_BJ, and the rest takes W_IJ - W_IB inv(W_BB) W_BJ with W_IB <- -W_IB inv(W_BB).
-// The pivots are those of the unpivoted LU of W.  nb <= kGjMaxNb, nb^2 <= blockDim.x.
+// The pivots are those of the unpivoted LU of W.  nb <= kGjMaxNb, nb^2 <= blockDim.x.  Rn (nb x m,
+// may be null) takes inv(W_BB) W_BJ one entry per thread; without it a thread forms a column.
 template <class Ar>
 __device__ void gj_invert(typename Ar::E* W, int m, int ld, int nbm, typename Ar::E* Pc, typename Ar::E* Rx,
-                          typename Ar::E* Dg) {
+                          typename Ar::E* Dg, typename Ar::E* Rn) {
   using E = typename Ar::E;
   const int tid = threadIdx.x, NT = blockDim.x;
   const int tcols = (m + kGjTile - 1) / kGjTile, ntiles = tcols * tcols;
@@ -52,32 +56,48 @@ __device__ void gj_invert(typename Ar::E* W, int m, int ld, int nbm, typename Ar
       if (tid < bs * bs) Dg[tid] = nv;
       __syncthreads();
     }
-    for (int j = tid; j < m; j += NT) {
-      if (j >= K && j < K + bs) {
-        for (int r = 0; r < bs; ++r) Rx[r * m + j] = Dg[r * bs + (j - K)];
-        continue;
-      }
-      E col[kGjMaxNb];
-#pragma unroll
-      for (int c = 0; c < kGjMaxNb; ++c)
-        if (c < bs) col[c] = Rx[c * m + j];
-      for (int r = 0; r < bs; ++r) {
+    // the block's rows: inv(W_BB) W[B, :] outside the block's columns, inv(W_BB) on them
+    E* Rb = Rx;
+    if (Rn) {                                          // one entry per thread into Rn
+      for (int t = tid; t < bs * m; t += NT) {
+        const int r = t / m, j = t - (t / m) * m;
+        if (j >= K && j < K + bs) {
+          Rn[t] = Dg[r * bs + (j - K)];
+          continue;
+        }
         E acc = Ar::zero();
+        for (int c = 0; c < bs; ++c) acc = Ar::fma(Dg[r * bs + c], Rx[c * m + j], acc);
+        Rn[t] = acc;
+      }
+      Rb = Rn;
+    } else {                                           // a column per thread, in place
+      for (int j = tid; j < m; j += NT) {
+        if (j >= K && j < K + bs) {
+          for (int r = 0; r < bs; ++r) Rx[r * m + j] = Dg[r * bs + (j - K)];
+          continue;
+        }
+        E col[kGjMaxNb];
 #pragma unroll
         for (int c = 0; c < kGjMaxNb; ++c)
-          if (c < bs) acc = Ar::fma(Dg[r * bs + c], col[c], acc);
-        Rx[r * m + j] = acc;
+          if (c < bs) col[c] = Rx[c * m + j];
+        for (int r = 0; r < bs; ++r) {
+          E acc = Ar::zero();
+#pragma unroll
+          for (int c = 0; c < kGjMaxNb; ++c)
+            if (c < bs) acc = Ar::fma(Dg[r * bs + c], col[c], acc);
+          Rx[r * m + j] = acc;
+        }
       }
     }
     __syncthreads();
     for (int tt = tid; tt < ntiles; tt += NT) {
-      const int i0 = (tt / tcols) * kGjTile, j0 = (tt - (tt / tcols) * tcols) * kGjTile;
+      const int i0 = (tt / tcols) * kGjTile, jt = tt - (tt / tcols) * tcols;
       E acc[kGjTile][kGjTile];
 #pragma unroll
       for (int r = 0; r < kGjTile; ++r)
 #pragma unroll
         for (int q = 0; q < kGjTile; ++q) {
-          const int i = i0 + r, j = j0 + q;
+          const int i = i0 + r, j = jt + q * tcols;
           acc[r][q] = (i < m && j < m && (j < K || j >= K + bs)) ? W[(size_t)i * ld + j] : Ar::zero();
         }
       for (int c = 0; c < bs; ++c) {
@@ -85,7 +105,7 @@ __device__ void gj_invert(typename Ar::E* W, int m, int ld, int nbm, typename Ar
 #pragma unroll
         for (int r = 0; r < kGjTile; ++r) pv[r] = i0 + r < m ? Pc[(i0 + r) * nbm + c] : Ar::zero();
 #pragma unroll
-        for (int q = 0; q < kGjTile; ++q) rv[q] = j0 + q < m ? Rx[c * m + j0 + q] : Ar::zero();
+        for (int q = 0; q < kGjTile; ++q) rv[q] = jt + q * tcols < m ? Rb[c * m + jt + q * tcols] : Ar::zero();
 #pragma unroll
         for (int r = 0; r < kGjTile; ++r)
 #pragma unroll
@@ -95,9 +115,9 @@ __device__ void gj_invert(typename Ar::E* W, int m, int ld, int nbm, typename Ar
       for (int r = 0; r < kGjTile; ++r)
 #pragma unroll
         for (int q = 0; q < kGjTile; ++q) {
-          const int i = i0 + r, j = j0 + q;
+          const int i = i0 + r, j = jt + q * tcols;
           if (i >= m || j >= m) continue;
-          W[(size_t)i * ld + j] = (i >= K && i < K + bs) ? Rx[(i - K) * m + j] : acc[r][q];
+          W[(size_t)i * ld + j] = (i >= K && i < K + bs) ? Rb[(i - K) * m + j] : acc[r][q];
         }
     }
     __syncthreads();
@@ -134,13 +154,13 @@ __device__ void gemm_staged(typename Ar::E* C, int ldc, const typename Ar::E* A,
     __syncthreads();
     const bool first = K == 0 && !acc;
     for (int tt = tid; tt < ntiles; tt += NT) {
-      const int i0 = (tt / tcols) * kGjTile, j0 = (tt - (tt / tcols) * tcols) * kGjTile;
+      const int i0 = (tt / tcols) * kGjTile, jt = tt - (tt / tcols) * tcols;
       E cv[kGjTile][kGjTile];
 #pragma unroll
       for (int r = 0; r < kGjTile; ++r)
 #pragma unroll
         for (int q = 0; q < kGjTile; ++q) {
-          const int i = i0 + r, j = j0 + q;
+          const int i = i0 + r, j = jt + q * tcols;
           cv[r][q] = (!first && i < m && j < n) ? C[(size_t)i * ldc + j] : Ar::zero();
         }
       for (int c = 0; c < bs; ++c) {
@@ -148,7 +168,7 @@ __device__ void gemm_staged(typename Ar::E* C, int ldc, const typename Ar::E* A,
 #pragma unroll
         for (int r = 0; r < kGjTile; ++r) av[r] = i0 + r < m ? As[(i0 + r) * kb + c] : Ar::zero();
 #pragma unroll
-        for (int q = 0; q < kGjTile; ++q) bv[q] = j0 + q < n ? Bs[c * n + j0 + q] : Ar::zero();
+        for (int q = 0; q < kGjTile; ++q) bv[q] = jt + q * tcols < n ? Bs[c * n + jt + q * tcols] : Ar::zero();
 #pragma unroll
         for (int r = 0; r < kGjTile; ++r)
 #pragma unroll
@@ -158,7 +178,7 @@ __device__ void gemm_staged(typename Ar::E* C, int ldc, const typename Ar::E* A,
       for (int r = 0; r < kGjTile; ++r)
 #pragma unroll
         for (int q = 0; q < kGjTile; ++q) {
-          const int i = i0 + r, j = j0 + q;
+          const int i = i0 + r, j = jt + q * tcols;
           if (i < m && j < n) C[(size_t)i * ldc + j] = cv[r][q];
         }
     }

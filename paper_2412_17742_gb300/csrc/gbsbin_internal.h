@@ -84,6 +84,7 @@ struct BackwardArgs {
   int n;
   int df;                   // nonzero: the per-point inverse in pairs of FP32, else FP64
   int nb;                   // pivots per Gauss-Jordan step (backward_block(n))
+  int rn;                   // set by the launcher: shared memory holds the block-row buffer
   GridDesc grid;
   long long n_eval;
   const double2* NXA;       // n*n: -XA
