@@ -179,7 +179,7 @@ typedef enum {
                                       of the permuted matrix; pairs of FP32 (~46 bits) on
                                       the FMA pipe, FP64 results; chosen automatically for
                                       GBSBIN_FP32_REFINE plans with n <= 64, last group <= 16
-                                      rows, no shard and no want_backward                */
+                                      rows and no shard                                    */
   GBSBIN_KERNEL_TREE_FP64 = 12,    /* the same tree in FP64 (DFMA pipe); chosen automatically
                                       for GBSBIN_FP64 plans under the same conditions      */
   GBSBIN_KERNEL_BTREE_DF32 = 13,   /* L >= 2, large matrices: the same tree of block
@@ -193,8 +193,8 @@ typedef enum {
                                       pairs of FP32; chosen automatically for standalone
                                       GBSBIN_FP32_REFINE plans where kernel 11 does not
                                       apply and it needs under half the per-point LUs'
-                                      work (last group <= 112 rows, no shard, no
-                                      want_backward)                                       */
+                                      work (last group <= 116 rows); a shard runs the
+                                      first-axis subtrees that cover its slice          */
   GBSBIN_KERNEL_BTREE_FP64 = 14,   /* the same in FP64; chosen for GBSBIN_FP64 plans under
                                       the same conditions                                   */
   GBSBIN_KERNEL_HERALD_FP64 = 15   /* heralded states (gbsbin_herald_*): CTA per point, FP64;

@@ -46,6 +46,12 @@ CASES = [
         np.sqrt(0.8) * synth.haar_unitary(65, np.random.default_rng(906)),
         np.array([0] * 64 + [1], np.int32), np.array([3, 1], np.int32),
         alpha=0.3 * np.ones((65, 1), complex))),
+    # the largest last group the shared-memory Householder reduction takes: 116 rows (n = 232)
+    ("n232_last_group_116_rows", lambda: synth.Problem(
+        116, 1, np.random.default_rng(907).uniform(0.2, 0.7, (116, 1)),
+        np.sqrt(0.7) * synth.haar_unitary(116, np.random.default_rng(908)),
+        np.array([0] * 58 + [1] * 58, np.int32), np.array([2, 3], np.int32),
+        alpha=0.2 * np.ones((116, 1), complex))),
 ]
 
 
@@ -104,7 +110,7 @@ def test_btree_refuses_what_it_cannot_do(cuda_lib):
     with pytest.raises(gb.GbsbinError) as e:
         gb.Plan(one_group, tile_override=14)
     assert e.value.status == 8
-    big_last = _problem(909, 120, 1, 2, [2, 2])              # last group of 120 rows > 112
+    big_last = _problem(909, 120, 1, 2, [2, 2])              # last group of 120 rows > 116
     with pytest.raises(gb.GbsbinError) as e:
         gb.Plan(big_last, tile_override=13)
     assert e.value.status == 8
