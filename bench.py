@@ -660,15 +660,16 @@ def _extra_fock(gb, torch, stream, flush, steps, world):
 def _extra_e3(gb, torch, stream, flush, steps, world):
     """Total photon number of the largest uniform-loss setup of Sec. VIII: M = 256 (n = 512),
     xi = 0.89, eta = 0.36, Haar U, one detector group, N_max = 170: the one-group Hessenberg
-    path against the general FP64 LU kernel on the same table."""
+    path in pairs of FP32 and in FP64 against the general FP64 LU kernel on the same table."""
     M, Nmax, xi, eta = 256, 170, 0.89, 0.36
     prob = synth.Problem(M, 1, np.full((M, 1), xi), np.sqrt(eta) * synth.haar_unitary(M, np.random.default_rng(61)),
                          np.zeros(M, np.int32), np.array([Nmax], np.int32))
     res = {}
     tables = {}
-    for name, tile in (("hessenberg_fp64", 0), ("general_lu_fp64", 3)):
+    for name, precision, tile in (("hessenberg_fp32_pairs", 1, 0), ("hessenberg_fp64", 0, 0),
+                                  ("general_lu_fp64", 0, 3)):
         t0 = time.perf_counter()
-        with gb.Plan(prob, precision=0, want_timing=True, tile_override=tile) as p:
+        with gb.Plan(prob, precision=precision, want_timing=True, tile_override=tile) as p:
             plan_s = time.perf_counter() - t0
             t = torch.empty(p.shape, dtype=torch.float64, device="cuda")
             gb.gbsbin_execute(p.handle, t, stream)
@@ -678,6 +679,7 @@ def _extra_e3(gb, torch, stream, flush, steps, world):
             res[name] = {"ms_per_table": ms / steps, "point_kernel_ms": d["point_kernel_ms"],
                          "kernel": d["kernel_name"], "plan_create_s": plan_s, "status": st}
     res["max_abs_diff"] = float(np.abs(tables["hessenberg_fp64"] - tables["general_lu_fp64"]).max())
+    res["max_abs_diff_pairs"] = float(np.abs(tables["hessenberg_fp32_pairs"] - tables["general_lu_fp64"]).max())
     return {"E3_M256_n512_L1_N170": res}
 
 

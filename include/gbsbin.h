@@ -166,7 +166,7 @@ typedef enum {
                                       XA = Q H Q^H per state (host) serves every point,
                                       O(n^2) per point (warp per point, FP64), displacement
                                       through Q^T gamma and Q^H X gamma; chosen
-                                      automatically for L = 1                              */
+                                      automatically for GBSBIN_FP64 plans with L = 1       */
   GBSBIN_KERNEL_FOCK_FP64 = 9,     /* Fock inputs (gbsbin_fock_*): FP64 throughout           */
   GBSBIN_KERNEL_FOCK_DF32 = 10,    /* Fock inputs: pairs of FP32 (hi + lo, ~46 bits) on the
                                       FMA pipe, running sums flushed to FP64               */
@@ -197,8 +197,11 @@ typedef enum {
                                       first-axis subtrees that cover its slice          */
   GBSBIN_KERNEL_BTREE_FP64 = 14,   /* the same in FP64; chosen for GBSBIN_FP64 plans under
                                       the same conditions                                   */
-  GBSBIN_KERNEL_HERALD_FP64 = 15   /* heralded states (gbsbin_herald_*): CTA per point, FP64;
+  GBSBIN_KERNEL_HERALD_FP64 = 15,  /* heralded states (gbsbin_herald_*): CTA per point, FP64;
                                       not a choice for gbsbin_plan_create                   */
+  GBSBIN_KERNEL_HESS_DF32 = 16     /* as 8 in pairs of FP32 on the FMA pipe (H, a, c stored as
+                                      pairs; FP64 results); chosen automatically for
+                                      GBSBIN_FP32_REFINE plans with L = 1, also in batches   */
 } gbsbin_kernel;
 
 /* Fill *o with defaults: FP64, oversample 1, diagnostics on, automatic kernel. */

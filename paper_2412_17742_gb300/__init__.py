@@ -25,7 +25,8 @@ GBSBIN_FP64 = 0
 GBSBIN_FP32_REFINE = 1
 KERNELS = {1: "smem_fp64", 2: "smem_fp32r", 3: "gmem_fp64", 4: "gmem_fp32r", 5: "warp_fp32r", 6: "blk_fp32r",
            7: "blk_tc_fp32r", 8: "hess_fp64", 9: "fock_fp64", 10: "fock_df32",
-           11: "tree_df32", 12: "tree_fp64", 13: "btree_df32", 14: "btree_fp64", 15: "herald_fp64"}
+           11: "tree_df32", 12: "tree_fp64", 13: "btree_df32", 14: "btree_fp64", 15: "herald_fp64",
+           16: "hess_df32"}
 EXPORTED = ["gbsbin_default_options", "gbsbin_plan_create", "gbsbin_plan_set_state", "gbsbin_plan_destroy",
             "gbsbin_plan_table_size", "gbsbin_execute", "gbsbin_execute_host", "gbsbin_execute_host_async",
             "gbsbin_diagnostics",

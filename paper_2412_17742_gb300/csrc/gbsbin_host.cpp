@@ -111,7 +111,7 @@ int validate_shape(const gbsbin_problem* p, const gbsbin_options* o) {
   if (o->tile_override < 0 ||
       (o->tile_override > GBSBIN_KERNEL_HESS_FP64 && o->tile_override != GBSBIN_KERNEL_TREE_DF32 &&
        o->tile_override != GBSBIN_KERNEL_TREE_FP64 && o->tile_override != GBSBIN_KERNEL_BTREE_DF32 &&
-       o->tile_override != GBSBIN_KERNEL_BTREE_FP64))
+       o->tile_override != GBSBIN_KERNEL_BTREE_FP64 && o->tile_override != GBSBIN_KERNEL_HESS_DF32))
     return GBSBIN_ERR_ARG;
   long long n = 2LL * p->M * p->K;
   if (n > GBSBIN_MAX_N) return GBSBIN_ERR_UNSUPPORTED;
@@ -440,6 +440,7 @@ int dalloc(T** p, size_t count) {
 
 // The tree of block eliminations, in pairs of FP32 or in FP64; and its large-matrix form.
 inline bool is_tree(int kernel) { return kernel == GBSBIN_KERNEL_TREE_DF32 || kernel == GBSBIN_KERNEL_TREE_FP64; }
+inline bool is_hess(int kernel) { return kernel == GBSBIN_KERNEL_HESS_FP64 || kernel == GBSBIN_KERNEL_HESS_DF32; }
 inline bool is_btree(int kernel) { return kernel == GBSBIN_KERNEL_BTREE_DF32 || kernel == GBSBIN_KERNEL_BTREE_FP64; }
 // 16-byte slots of a tree plan's depth-0 region in the state block
 size_t tree_region_slots(int n, int kernel) {
@@ -622,7 +623,7 @@ int upload_state(gbsbin_plan* P, cudaStream_t stream) {
   P->upload_bytes = (long long)(s.total - off);
   e = cudaMemcpyAsync(P->d_state + off, h + off, s.total - off, cudaMemcpyHostToDevice, stream);
   if (e != cudaSuccess || cudaEventRecord(P->ev_stage[sb], stream) != cudaSuccess) return GBSBIN_ERR_CUDA;
-  if (P->kernel == GBSBIN_KERNEL_HESS_FP64) return upload_hessenberg(P, stream);
+  if (is_hess(P->kernel)) return upload_hessenberg(P, stream);
   return GBSBIN_OK;
 }
 
@@ -690,6 +691,11 @@ int upload_hessenberg(gbsbin_plan* P, cudaStream_t stream) {
     h[(size_t)n * n + i] = make_double2(ga[i].real(), -ga[i].imag());
     h[(size_t)n * n + n + i] = make_double2(c[i].real(), c[i].imag());
   }
+  if (P->kernel == GBSBIN_KERNEL_HESS_DF32)        // pairs of FP32 in the same 16-byte slots
+    for (size_t q = 0; q < h.size(); ++q) {
+      const float4 f = split4(cd(h[q].x, h[q].y));
+      std::memcpy(&h[q], &f, sizeof(f));
+    }
   // a pageable source: the call returns once the data are staged, so h may go out of scope
   if (cudaMemcpyAsync(P->d_H, h.data(), h.size() * sizeof(double2), cudaMemcpyHostToDevice, stream) != cudaSuccess)
     return GBSBIN_ERR_CUDA;
@@ -1043,7 +1049,7 @@ int backward_tree_setup(gbsbin_plan* P) {
 
 int choose_kernel(int n, int L, int precision, int override_id, int has_gamma) {
   if (override_id) return override_id;
-  if (L == 1) return GBSBIN_KERNEL_HESS_FP64;   // one group
+  if (L == 1) return precision == GBSBIN_FP32_REFINE ? GBSBIN_KERNEL_HESS_DF32 : GBSBIN_KERNEL_HESS_FP64;   // one group
   if (precision == GBSBIN_FP32_REFINE && n <= 32) return GBSBIN_KERNEL_WARP_FP32R;
   if (precision == GBSBIN_FP32_REFINE && n > GBSBIN_SMEM_MAX_N && n <= GBSBIN_BLK_MAX_N) return GBSBIN_KERNEL_BLK_FP32R;
   if (precision == GBSBIN_FP64)
@@ -1188,7 +1194,7 @@ static int plan_create_impl(const gbsbin_problem* p, const gbsbin_options* o, gb
   }
   record_inputs(P, p);
   P->kernel = choose_kernel(n, p->L, opt.precision, opt.tile_override, P->has_gamma);
-  if (P->kernel == GBSBIN_KERNEL_HESS_FP64 && p->L != 1) {
+  if (is_hess(P->kernel) && p->L != 1) {
     delete P;
     return GBSBIN_ERR_UNSUPPORTED;
   }
@@ -1222,7 +1228,7 @@ static int plan_create_impl(const gbsbin_problem* p, const gbsbin_options* o, gb
       P->kernel = opt.precision == GBSBIN_FP64 ? GBSBIN_KERNEL_BTREE_FP64 : GBSBIN_KERNEL_BTREE_DF32;
     }
   }
-  P->P = P->kernel == GBSBIN_KERNEL_HESS_FP64 || is_tree(P->kernel) || is_btree(P->kernel) ? 1
+  P->P = is_hess(P->kernel) || is_tree(P->kernel) || is_btree(P->kernel) ? 1
          : P->kernel == GBSBIN_KERNEL_WARP_FP32R ? (n <= 32 ? 1 : 0)
          : is_blk(P->kernel) ? (n <= GBSBIN_BLK_MAX_N ? 1 : 0)
                                                  : points_per_cta(P->kernel, n, p->L);
@@ -1278,7 +1284,7 @@ static int plan_create_impl(const gbsbin_problem* p, const gbsbin_options* o, gb
     delete P;
     return st;
   }
-  if ((P->kernel == GBSBIN_KERNEL_WARP_FP32R || P->kernel == GBSBIN_KERNEL_HESS_FP64 ||
+  if ((P->kernel == GBSBIN_KERNEL_WARP_FP32R || is_hess(P->kernel) ||
        is_tree(P->kernel) || is_btree(P->kernel)) &&
       (st = dalloc(&P->d_ldfin, (size_t)6 * g.n_eval))) {
     free_device(P);
@@ -1301,7 +1307,7 @@ static int plan_create_impl(const gbsbin_problem* p, const gbsbin_options* o, gb
     }
     btree_pointers(P, sl);
   }
-  if (P->kernel == GBSBIN_KERNEL_HESS_FP64 && (st = dalloc(&P->d_H, nn + 2 * (size_t)n))) {
+  if (is_hess(P->kernel) && (st = dalloc(&P->d_H, nn + 2 * (size_t)n))) {
     free_device(P);
     delete P;
     return st;
@@ -1532,7 +1538,7 @@ int gbsbin_execute(gbsbin_plan* P, double* P_out, void* stream) {
                                                                                              : GBSBIN_ERR_CUDA;
   }
   cudaError_t e = P->kernel == GBSBIN_KERNEL_WARP_FP32R  ? launch_points_warp(a, P->num_sms, s)
-                  : P->kernel == GBSBIN_KERNEL_HESS_FP64 ? launch_points_hess(a, PointBatch{}, P->num_sms, s)
+                  : is_hess(P->kernel) ? launch_points_hess(a, PointBatch{}, P->num_sms, s, P->kernel == GBSBIN_KERNEL_HESS_DF32)
                   : is_blk(P->kernel) ? launch_points_blk(a, PointBatch{}, 0, P->num_sms, s, P->kernel == GBSBIN_KERNEL_BLK_TC_FP32R)
                                                          : launch_points(a, P->kernel, P->num_sms, s);
   if (e != cudaSuccess) return GBSBIN_ERR_CUDA;
@@ -2665,7 +2671,7 @@ int batch_launch(gbsbin_batch* B, double* const* P_out, cudaStream_t s) {
     if (cudaMemsetAsync(B->d_queue + c, 0, sizeof(unsigned long long), s) != cudaSuccess) return GBSBIN_ERR_CUDA;
     PointBatch pb{B->d_probs, C.d_jobs, (long long)C.jobs.size(), B->d_queue + c};
     cudaError_t e = C.kernel == GBSBIN_KERNEL_WARP_FP32R  ? launch_points_warp_batch(pb, C.np, B->num_sms, s)
-                    : C.kernel == GBSBIN_KERNEL_HESS_FP64 ? launch_points_hess(PointArgs{}, pb, B->num_sms, s)
+                    : is_hess(C.kernel) ? launch_points_hess(PointArgs{}, pb, B->num_sms, s, C.kernel == GBSBIN_KERNEL_HESS_DF32)
                     : is_blk(C.kernel) ? launch_points_blk(PointArgs{}, pb, C.smem, B->num_sms, s, C.kernel == GBSBIN_KERNEL_BLK_TC_FP32R)
                                                           : launch_points_batch(pb, C.kernel, C.threads, C.smem, B->num_sms, s);
     if (e != cudaSuccess) return GBSBIN_ERR_CUDA;
@@ -2767,7 +2773,7 @@ int gbsbin_batch_create(const gbsbin_problem* probs, int nprob, const gbsbin_opt
     }
     gbsbin_plan* P = B->plans[i];
     args[i] = make_point_args(P);
-    const int threads = (P->kernel == GBSBIN_KERNEL_WARP_FP32R || P->kernel == GBSBIN_KERNEL_HESS_FP64) ? 128
+    const int threads = (P->kernel == GBSBIN_KERNEL_WARP_FP32R || is_hess(P->kernel)) ? 128
                         : is_blk(P->kernel) ? 256
                                                                : points_threads(P->kernel, P->n);
     // warp kernel: padded size class; blocked kernel: problems whose shared memory allows
@@ -2784,7 +2790,7 @@ int gbsbin_batch_create(const gbsbin_problem* probs, int nprob, const gbsbin_opt
       B->classes.back().np = np;
     }
     auto& C = B->classes[class_of[key]];
-    const int group = (P->kernel == GBSBIN_KERNEL_WARP_FP32R || P->kernel == GBSBIN_KERNEL_HESS_FP64) ? 4 : P->P;
+    const int group = (P->kernel == GBSBIN_KERNEL_WARP_FP32R || is_hess(P->kernel)) ? 4 : P->P;
     for (long long e0 = 0; e0 < P->grid.n_eval; e0 += group) C.jobs.push_back(PointJob{i, 0, e0});
     if (P->kernel == GBSBIN_KERNEL_SMEM_FP64 || P->kernel == GBSBIN_KERNEL_SMEM_FP32R ||
         P->kernel == GBSBIN_KERNEL_GMEM_FP64 || P->kernel == GBSBIN_KERNEL_GMEM_FP32R)

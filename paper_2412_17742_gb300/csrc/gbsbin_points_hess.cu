@@ -18,14 +18,19 @@
 // appear (z_i = (a_i - s_i) / u_ii, then s_j += z_i u_ij for j > i), so a^T N^{-1} c =
 // sum_i z_i y_i needs no stored factors.
 //
-// One warp per point, FP64: lane t holds entries j = lane + 32 s of the current pivot row
-// (and of the running sums s) in registers (s < 16, n <= 512); row i + 1 of H - conj(w) I is
-// read from the L2-resident H.  log q = 1/2 gamma^T x - 1/2 log det K is left unfinished as
+// One warp per point: lane t holds entries j = lane + 32 s of the current pivot row (and of
+// the running sums s) in registers (s < 16, n <= 512); row i + 1 of H - conj(w) I is read
+// from the L2-resident H.  log q = 1/2 gamma^T x - 1/2 log det K is left unfinished as
 // (product of pivots with its power of two, FP32 sum of their arguments, the rest), finished
-// one point per thread by the DFT's first stage.
+// one point per thread by the DFT's first stage.  The arithmetic class Ar is FP64 (kernel 8)
+// or pairs of FP32 on the FMA pipe (kernel 16, with H, a and c stored as pairs; the pivot
+// product renormalised every four pivots to stay in FP32's exponent range).
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "gbsbin_device.cuh"
+#include "gbsbin_df.cuh"
 #include "gbsbin_internal.h"
 
 namespace gbsbin {
@@ -34,115 +39,105 @@ namespace {
 constexpr int HW = 4;                         // warps (points) per CTA
 constexpr int SMAX = GBSBIN_MAX_N / 32;       // row slots per lane
 
-__device__ __forceinline__ double2 shfl_d2(double2 v, int src) {
-  return make_double2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
-}
-
-// 2^-ex scaling of z with ex the binary exponent of max(|re|, |im|); returns ex.
-__device__ __forceinline__ int renormalise(double2& z) {
-  const double m = fmax(fabs(z.x), fabs(z.y));
-  if (!(m > 0.0) || !(m < 1.0e300)) return 0;
-  const int ex = ((__double2hiint(m) >> 20) & 0x7ff) - 1022;   // m in [2^(ex-1), 2^ex)
-  const double sc = __hiloint2double((1023 - ex) << 20, 0);    // 2^-ex
-  z.x *= sc;
-  z.y *= sc;
-  return ex;
-}
-
-template <bool DISP>
+template <class Ar, bool DISP>
 __device__ void hess_point(const PointArgs& a, long long e) {
+  using E = typename Ar::E;
   const int n = a.n, lane = threadIdx.x & 31;
   const int S = (n + 31) >> 5;
-  const double2 w = grid_root(a.tw, a.grid, 0, point_digit(e, a.grid, 0));
-  const double2 sg = make_double2(w.x, -w.y);                  // conj(w)
-  const double2 mw = make_double2(-w.x, -w.y);                 // pivots of B = -w x pivots here
-  const double2* H = a.H;
-  const double2* av = H + (size_t)n * n;        // a = Q^T gamma
-  const double2* cv = av + n;                   // c = Q^H X gamma
-  constexpr bool disp = DISP;
+  const double2 wd = grid_root(a.tw, a.grid, 0, point_digit(e, a.grid, 0));
+  const E sg = Ar::from(make_double2(wd.x, -wd.y));             // conj(w)
+  const E mw = Ar::from(make_double2(-wd.x, -wd.y));            // pivots of B = -w x pivots here
+  const E* H = reinterpret_cast<const E*>(a.H);
+  const E* av = H + (size_t)n * n;              // a = Q^T gamma
+  const E* cv = av + n;                         // c = Q^H X gamma
   // row 0 of H - conj(w) I (the running sums only for displaced states)
-  double2 r[SMAX], sacc[DISP ? SMAX : 1];
+  E r[SMAX], sacc[DISP ? SMAX : 1];
 #pragma unroll
   for (int s = 0; s < SMAX; ++s) {
     const int j = lane + 32 * s;
-    double2 v = make_double2(0.0, 0.0);
+    E v = Ar::zero();
     if (s < S && j < n) {
       v = H[j];
-      if (j == 0) v = make_double2(v.x - sg.x, v.y - sg.y);
+      if (j == 0) v = Ar::add(v, Ar::neg(sg));
     }
     r[s] = v;
-    if constexpr (DISP) sacc[s] = make_double2(0.0, 0.0);
+    if constexpr (DISP) sacc[s] = Ar::zero();
   }
-  double2 y = disp ? cv[0] : make_double2(0.0, 0.0);
-  double2 zy = make_double2(0.0, 0.0);          // sum_i z_i y_i
-  double2 prod = make_double2(1.0, 0.0);
+  E y = DISP ? cv[0] : Ar::zero();
+  E zy = Ar::zero();                            // sum_i z_i y_i
+  E prod = Ar::one();
   int e2 = 0;
   float args = 0.0f;
-  double mn = 1.0e300;
+  constexpr bool f64 = std::is_same<Ar, ArF64>::value;
+  using MinT = typename std::conditional<f64, double, float>::type;
+  MinT mn = f64 ? (MinT)1.0e300 : (MinT)3.0e38f;   // FP64 plans: the exact pivot; pairs: its hi part
+  bool bad = false;
 #pragma unroll
   for (int sb = 0; sb < SMAX; ++sb) {           // pivot i = 32 sb + il sits in slot sb of lane il
     if (sb >= S) break;
     for (int il = 0; il < 32; ++il) {
       const int i = 32 * sb + il;
       if (i >= n) break;
-      const double2 q = shfl_d2(r[sb], il);     // pivot of H - conj(w) I
-      const double2 p = cmul(mw, q);            // pivot of B = I - w H
-      const double2 iq = crecip(q);
+      const E q = shfl(r[sb], il);              // pivot of H - conj(w) I
+      const E p = Ar::mul(mw, q);               // pivot of B = I - w H
+      const E iq = Ar::recip(q);
       if constexpr (DISP) {                     // z_i, then the running sums of later columns
-        const double2 si = shfl_d2(sacc[sb], il);
-        const double2 ai = av[i];
-        const double2 zi = cmul(make_double2(ai.x - si.x, ai.y - si.y), iq);
-        zy = make_double2(zy.x + (zi.x * y.x - zi.y * y.y), zy.y + (zi.x * y.y + zi.y * y.x));
+        const E si = shfl(sacc[sb], il);
+        const E zi = Ar::mul(Ar::add(av[i], Ar::neg(si)), iq);
+        zy = Ar::fma(zi, y, zy);
 #pragma unroll
         for (int s = 0; s < SMAX; ++s) {
           const int j = lane + 32 * s;
-          if (s < S && j > i && j < n) sacc[s] = make_double2(sacc[s].x + (zi.x * r[s].x - zi.y * r[s].y),
-                                                              sacc[s].y + (zi.x * r[s].y + zi.y * r[s].x));
+          if (s < S && j > i && j < n) sacc[s] = Ar::fma(zi, r[s], sacc[s]);
         }
       }
-      mn = fmin(mn, p.x);
-      if (!(p.x == p.x) || !(p.y == p.y)) mn = -1.0e300;
-      args += atan2f((float)p.y, (float)p.x);
-      prod = cmul(prod, p);
+      const float pr = Ar::re(p), pi = Ar::im(p);
+      if constexpr (f64) mn = fmin(mn, (double)Ar::to(p).x);
+      else mn = fminf(mn, pr);
+      if (!(pr == pr) || !(pi == pi)) bad = true;
+      args += atan2f(pi, pr);
+      prod = Ar::mul(prod, p);
+      if ((i & 3) == 3) e2 += Ar::normalise(prod);   // |prod| stays in range
       if (i == n - 1) break;
       // row i + 1: its only entry left of the diagonal is H[i+1][i]; l = that / q
-      const double2* hrow = H + (size_t)(i + 1) * n;
-      const double2 l = cmul(hrow[i], iq);
-      if constexpr (DISP) y = cfnma(cv[i + 1], l, y);   // y_{i+1} = c_{i+1} - l_i y_i
+      const E* hrow = H + (size_t)(i + 1) * n;
+      const E l = Ar::mul(hrow[i], iq);
+      if constexpr (DISP) y = Ar::fms(cv[i + 1], l, y);   // y_{i+1} = c_{i+1} - l_i y_i
 #pragma unroll
       for (int s = 0; s < SMAX; ++s) {
         const int j = lane + 32 * s;
         if (s < S && j > i && j < n) {
-          double2 h = hrow[j];
-          if (j == i + 1) h = make_double2(h.x - sg.x, h.y - sg.y);
-          r[s] = cfnma(h, l, r[s]);
+          E h = hrow[j];
+          if (j == i + 1) h = Ar::add(h, Ar::neg(sg));
+          r[s] = Ar::fms(h, l, r[s]);
         }
       }
     }
-    e2 += renormalise(prod);                    // every 32 pivots: |prod| stays in range
   }
+  e2 += Ar::normalise(prod);
   if (lane == 0) {
     const double LN2 = 0.693147180559945309417232121458;
+    const double2 pd = Ar::to(prod), zd = Ar::to(zy);
     double* f = a.ldfin + 6 * e;
-    f[0] = prod.x;
-    f[1] = prod.y;
+    f[0] = pd.x;
+    f[1] = pd.y;
     f[2] = (double)args;
     // log q = 1/2 gamma^T x - 1/2 log det K, gamma^T x = -sum_i z_i y_i
-    f[3] = -0.5 * (double)e2 * LN2 - 0.5 * zy.x;
-    f[4] = -0.5 * zy.y;
+    f[3] = -0.5 * (double)e2 * LN2 - 0.5 * zd.x;
+    f[4] = -0.5 * zd.y;
     f[5] = 0.0;
-    a.minpiv[e] = mn;
+    a.minpiv[e] = bad ? -1.0e300 : (double)mn;
   }
 }
 
 // MODE 0 / 1: one problem, undisplaced / displaced (each with its own register budget);
 // MODE 2: a batch job queue, displacement decided per problem.
-template <int MODE>
+template <class Ar, int MODE>
 __global__ void __launch_bounds__(HW * 32) k_points_hess(PointArgs a0, PointBatch batch) {
   const int warp = threadIdx.x >> 5;
   if constexpr (MODE < 2) {
     for (long long e = (long long)blockIdx.x * HW + warp; e < a0.grid.n_eval; e += (long long)gridDim.x * HW)
-      hess_point<MODE == 1>(a0, e);
+      hess_point<Ar, MODE == 1>(a0, e);
   } else {
     __shared__ PointArgs sa;
     __shared__ long long sj;
@@ -156,31 +151,36 @@ __global__ void __launch_bounds__(HW * 32) k_points_hess(PointArgs a0, PointBatc
       const long long j = sj;
       if (j >= batch.njobs) break;
       const long long e = batch.jobs[j].e0 + warp;
-      if (e < sa.grid.n_eval) sa.has_gamma ? hess_point<true>(sa, e) : hess_point<false>(sa, e);
+      if (e < sa.grid.n_eval) sa.has_gamma ? hess_point<Ar, true>(sa, e) : hess_point<Ar, false>(sa, e);
       __syncthreads();
     }
   }
 }
 
-template <int MODE>
+template <class Ar, int MODE>
 cudaError_t launch_hess_mode(const PointArgs& a, const PointBatch& batch, int num_sms, cudaStream_t s) {
   int per_sm = 0;
-  cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_points_hess<MODE>, HW * 32, 0);
+  cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_points_hess<Ar, MODE>, HW * 32, 0);
   if (err != cudaSuccess) return err;
   if (per_sm < 1) per_sm = 1;
   const long long groups = batch.probs ? batch.njobs : (a.grid.n_eval + HW - 1) / HW;
   long long grid = (long long)per_sm * num_sms;
   if (grid > groups) grid = groups;
   if (grid < 1) grid = 1;
-  k_points_hess<MODE><<<(unsigned)grid, HW * 32, 0, s>>>(a, batch);
+  k_points_hess<Ar, MODE><<<(unsigned)grid, HW * 32, 0, s>>>(a, batch);
   return cudaGetLastError();
+}
+
+template <class Ar>
+cudaError_t launch_hess_ar(const PointArgs& a, const PointBatch& batch, int num_sms, cudaStream_t s) {
+  if (batch.probs) return launch_hess_mode<Ar, 2>(a, batch, num_sms, s);
+  return a.has_gamma ? launch_hess_mode<Ar, 1>(a, batch, num_sms, s) : launch_hess_mode<Ar, 0>(a, batch, num_sms, s);
 }
 
 }  // namespace
 
-cudaError_t launch_points_hess(const PointArgs& a, const PointBatch& batch, int num_sms, cudaStream_t s) {
-  if (batch.probs) return launch_hess_mode<2>(a, batch, num_sms, s);
-  return a.has_gamma ? launch_hess_mode<1>(a, batch, num_sms, s) : launch_hess_mode<0>(a, batch, num_sms, s);
+cudaError_t launch_points_hess(const PointArgs& a, const PointBatch& batch, int num_sms, cudaStream_t s, bool df) {
+  return df ? launch_hess_ar<ArDF>(a, batch, num_sms, s) : launch_hess_ar<ArF64>(a, batch, num_sms, s);
 }
 
 }  // namespace gbsbin
