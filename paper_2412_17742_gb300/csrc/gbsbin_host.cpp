@@ -1211,9 +1211,10 @@ static int plan_create_impl(const gbsbin_problem* p, const gbsbin_options* o, gb
       return GBSBIN_ERR_UNSUPPORTED;
     }
   }
-  // the large-matrix tree: asked for, or by default for standalone plans of n > 64 where it
-  // needs under half the work of one LU per evaluated point
-  if (is_btree(P->kernel) || (!is_tree(P->kernel) && allow_tree && !opt.tile_override && p->L >= 2 && n > 64)) {
+  // the large-matrix tree: asked for, or by default for standalone plans the small tree does
+  // not take (n > 64, or a last group above 16 rows) where it needs under half the work of one
+  // LU per evaluated point
+  if (is_btree(P->kernel) || (!is_tree(P->kernel) && allow_tree && !opt.tile_override && p->L >= 2)) {
     tree_bytes = btree_layout(P);
     bool take = tree_bytes > 0;
     if (take && !is_btree(P->kernel))

@@ -46,6 +46,8 @@ CASES = [
         np.sqrt(0.8) * synth.haar_unitary(65, np.random.default_rng(906)),
         np.array([0] * 64 + [1], np.int32), np.array([3, 1], np.int32),
         alpha=0.3 * np.ones((65, 1), complex))),
+    # n = 60, three groups of 20 rows: too large a last group for the small tree
+    ("n60_l3_last_group_20_rows", lambda: _problem(909, 30, 1, 3, [4, 3, 5], displaced=True)),
     # the largest last group the shared-memory Householder reduction takes: 116 rows (n = 232)
     ("n232_last_group_116_rows", lambda: synth.Problem(
         116, 1, np.random.default_rng(907).uniform(0.2, 0.7, (116, 1)),
@@ -140,3 +142,16 @@ def test_trees_run_the_forward_of_a_reverse_pass(cuda_lib, precision, small, lar
         for k in grads[0]:
             scale = max(1.0, float(np.abs(grads[1][k]).max()))
             assert np.abs(grads[0][k] - grads[1][k]).max() < 1e-10 * scale, (kind, k)
+
+
+def test_default_choice_for_small_matrices_with_large_groups(cuda_lib):
+    # n = 60 with 20-row groups: the small tree does not apply (last group above 16 rows), the
+    # large-matrix tree is the default in both arithmetics
+    gb = cuda_lib
+    prob = _problem(910, 30, 1, 3, [4, 3, 5], displaced=True)
+    for precision, name in ((1, "btree_df32"), (0, "btree_fp64")):
+        with gb.Plan(prob, precision=precision) as p:
+            P = p.table().cpu().numpy()
+            st, d = p.diagnostics()
+        assert st == 0 and d["kernel_name"] == name, d["kernel_name"]
+        assert np.abs(P - oracle.binned(prob)["P"]).max() <= 1e-10
