@@ -76,6 +76,9 @@ struct gbsbin_plan {
   double2 *d_adjA = nullptr, *d_adjB = nullptr, *d_bws = nullptr;
   double2 *d_partS = nullptr, *d_partg = nullptr, *d_outS = nullptr, *d_outg = nullptr;
   bool logq_valid = false;            // d_logq holds the current state's log q (an execute ran)
+  bool dft_plain = false;             // tree plans inside a batch: the inverse DFT as ordinary
+                                      // launches (several trees run at once on side streams, and
+                                      // cooperative launches are not run concurrently)
   long long bws_slot_bytes = 0;       // per-SM slot of d_bws (the reverse pass's matrices)
   cudaEvent_t ev_b0 = nullptr, ev_b1 = nullptr;   // want_timing: around the reverse per-point kernel
   bool backward_ran = false;
@@ -1514,6 +1517,10 @@ int gbsbin_execute(gbsbin_plan* P, double* P_out, void* stream) {
     P->last_launches = nl + 1;                    // the tree's launches and the fused DFT
     if (P->ev1 && cudaEventRecord(P->ev1, s) != cudaSuccess) return GBSBIN_ERR_CUDA;
     DftArgs d = make_dft_args(P, P_out);
+    if (P->dft_plain) {                           // G again from the leaves' records (ldfin)
+      P->last_launches = nl + 2 + P->grid.L + (P->opt.want_diagnostics ? 1 : 0);
+      return launch_dft(d, s) == cudaSuccess ? GBSBIN_OK : GBSBIN_ERR_CUDA;
+    }
     d.g_ready = P->tree_g ? 1 : 0;
     d.g_df = t.gout_df;
     return launch_dft_fused(d, P->d_bar, P->num_sms, s) == cudaSuccess ? GBSBIN_OK : GBSBIN_ERR_CUDA;
@@ -1535,6 +1542,10 @@ int gbsbin_execute(gbsbin_plan* P, double* P_out, void* stream) {
       return GBSBIN_ERR_CUDA;
     P->last_launches = nl + 1;                    // the tree's launches and the fused DFT
     if (P->ev1 && cudaEventRecord(P->ev1, s) != cudaSuccess) return GBSBIN_ERR_CUDA;
+    if (P->dft_plain) {
+      P->last_launches = nl + 1 + P->grid.L + (P->opt.want_diagnostics ? 1 : 0);
+      return launch_dft(make_dft_args(P, P_out), s) == cudaSuccess ? GBSBIN_OK : GBSBIN_ERR_CUDA;
+    }
     return launch_dft_fused(make_dft_args(P, P_out), P->d_bar, P->num_sms, s) == cudaSuccess ? GBSBIN_OK
                                                                                              : GBSBIN_ERR_CUDA;
   }
@@ -2648,6 +2659,12 @@ struct gbsbin_batch {
   int num_sms = 0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
+  // the tree problems, largest first, dealt round-robin to side streams that fork from and
+  // join back to the caller's stream with events (also inside a captured graph)
+  std::vector<int> tree_order;
+  std::vector<cudaStream_t> side;
+  std::vector<cudaEvent_t> ev_join;
+  cudaEvent_t ev_fork = nullptr;
 };
 
 namespace {
@@ -2660,6 +2677,11 @@ void batch_free(gbsbin_batch* B) {
   if (B->d_probs) cudaFree(B->d_probs);
   if (B->d_queue) cudaFree(B->d_queue);
   if (B->d_gws) cudaFree(B->d_gws);
+  for (cudaStream_t st : B->side)
+    if (st) cudaStreamDestroy(st);
+  for (cudaEvent_t ev : B->ev_join)
+    if (ev) cudaEventDestroy(ev);
+  if (B->ev_fork) cudaEventDestroy(B->ev_fork);
   for (gbsbin_plan* P : B->plans)
     if (P) gbsbin_plan_destroy(P);
   delete B;
@@ -2677,16 +2699,28 @@ int batch_launch(gbsbin_batch* B, double* const* P_out, cudaStream_t s) {
                                                           : launch_points_batch(pb, C.kernel, C.threads, C.smem, B->num_sms, s);
     if (e != cudaSuccess) return GBSBIN_ERR_CUDA;
   }
-  for (size_t i = 0; i < B->plans.size(); ++i) {
+  for (size_t i = 0; i < B->plans.size(); ++i)
     if (!P_out[i]) return GBSBIN_ERR_ARG;
-    if (B->own[i]) {                                 // a tree: its own launches and DFT
-      const int st = gbsbin_execute(B->plans[i], P_out[i], s);
-      if (st) return st;
-      continue;
-    }
+  // the trees on the side streams (after everything enqueued so far on s), the per-point
+  // problems' transforms on s meanwhile, then s waits for every side stream
+  const int ns = (int)B->side.size();
+  if (ns > 0 && cudaEventRecord(B->ev_fork, s) != cudaSuccess) return GBSBIN_ERR_CUDA;
+  for (int k = 0; k < ns; ++k)
+    if (cudaStreamWaitEvent(B->side[k], B->ev_fork, 0) != cudaSuccess) return GBSBIN_ERR_CUDA;
+  for (size_t q = 0; q < B->tree_order.size(); ++q) {
+    const int i = B->tree_order[q];
+    const int st = gbsbin_execute(B->plans[i], P_out[i], ns > 0 ? B->side[q % ns] : s);
+    if (st) return st;
+  }
+  for (size_t i = 0; i < B->plans.size(); ++i) {
+    if (B->own[i]) continue;
     if (launch_dft_fused(make_dft_args(B->plans[i], P_out[i]), B->plans[i]->d_bar, B->num_sms, s) != cudaSuccess)
       return GBSBIN_ERR_CUDA;
   }
+  for (int k = 0; k < ns; ++k)
+    if (cudaEventRecord(B->ev_join[k], B->side[k]) != cudaSuccess ||
+        cudaStreamWaitEvent(s, B->ev_join[k], 0) != cudaSuccess)
+      return GBSBIN_ERR_CUDA;
   return GBSBIN_OK;
 }
 
@@ -2747,6 +2781,7 @@ int gbsbin_batch_create(const gbsbin_problem* probs, int nprob, const gbsbin_opt
         if (st == GBSBIN_OK && (is_tree(T->kernel) || is_btree(T->kernel))) {
           B->plans[i] = T;
           B->own[i] = 1;
+          T->dft_plain = true;
           args[i] = make_point_args(T);
           continue;
         }
@@ -2835,6 +2870,27 @@ int gbsbin_batch_create(const gbsbin_problem* probs, int nprob, const gbsbin_opt
     cudaGetLastError();
     batch_free(B);
     return GBSBIN_ERR_NOMEM;
+  }
+  // tree problems, largest per-point work first, over up to eight side streams
+  std::vector<std::pair<double, int>> trees;
+  for (int i = 0; i < nprob; ++i)
+    if (B->own[i]) {
+      const gbsbin_plan* P = B->plans[i];
+      trees.emplace_back(-(double)P->grid.n_eval * P->n * P->n * P->n, i);
+    }
+  std::sort(trees.begin(), trees.end());
+  for (auto& t : trees) B->tree_order.push_back(t.second);
+  const int ns = (int)std::min<size_t>(8, trees.size());
+  B->side.assign(ns, nullptr);
+  B->ev_join.assign(ns, nullptr);
+  bool ok = ns == 0 || cudaEventCreateWithFlags(&B->ev_fork, cudaEventDisableTiming) == cudaSuccess;
+  for (int k = 0; ok && k < ns; ++k)
+    ok = cudaStreamCreateWithFlags(&B->side[k], cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&B->ev_join[k], cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    batch_free(B);
+    return GBSBIN_ERR_CUDA;
   }
   *out = B;
   return GBSBIN_OK;
