@@ -2688,6 +2688,19 @@ void batch_free(gbsbin_batch* B) {
 }
 
 int batch_launch(gbsbin_batch* B, double* const* P_out, cudaStream_t s) {
+  for (size_t i = 0; i < B->plans.size(); ++i)
+    if (!P_out[i]) return GBSBIN_ERR_ARG;
+  // the trees on the side streams from the start, beside the per-point classes' persistent
+  // launches and the per-point problems' transforms on s; then s waits for every side stream
+  const int ns = (int)B->side.size();
+  if (ns > 0 && cudaEventRecord(B->ev_fork, s) != cudaSuccess) return GBSBIN_ERR_CUDA;
+  for (int k = 0; k < ns; ++k)
+    if (cudaStreamWaitEvent(B->side[k], B->ev_fork, 0) != cudaSuccess) return GBSBIN_ERR_CUDA;
+  for (size_t q = 0; q < B->tree_order.size(); ++q) {
+    const int i = B->tree_order[q];
+    const int st = gbsbin_execute(B->plans[i], P_out[i], ns > 0 ? B->side[q % ns] : s);
+    if (st) return st;
+  }
   for (size_t c = 0; c < B->classes.size(); ++c) {
     auto& C = B->classes[c];
     if (C.jobs.empty()) continue;
@@ -2698,19 +2711,6 @@ int batch_launch(gbsbin_batch* B, double* const* P_out, cudaStream_t s) {
                     : is_blk(C.kernel) ? launch_points_blk(PointArgs{}, pb, C.smem, B->num_sms, s, C.kernel == GBSBIN_KERNEL_BLK_TC_FP32R)
                                                           : launch_points_batch(pb, C.kernel, C.threads, C.smem, B->num_sms, s);
     if (e != cudaSuccess) return GBSBIN_ERR_CUDA;
-  }
-  for (size_t i = 0; i < B->plans.size(); ++i)
-    if (!P_out[i]) return GBSBIN_ERR_ARG;
-  // the trees on the side streams (after everything enqueued so far on s), the per-point
-  // problems' transforms on s meanwhile, then s waits for every side stream
-  const int ns = (int)B->side.size();
-  if (ns > 0 && cudaEventRecord(B->ev_fork, s) != cudaSuccess) return GBSBIN_ERR_CUDA;
-  for (int k = 0; k < ns; ++k)
-    if (cudaStreamWaitEvent(B->side[k], B->ev_fork, 0) != cudaSuccess) return GBSBIN_ERR_CUDA;
-  for (size_t q = 0; q < B->tree_order.size(); ++q) {
-    const int i = B->tree_order[q];
-    const int st = gbsbin_execute(B->plans[i], P_out[i], ns > 0 ? B->side[q % ns] : s);
-    if (st) return st;
   }
   for (size_t i = 0; i < B->plans.size(); ++i) {
     if (B->own[i]) continue;
