@@ -742,7 +742,7 @@ def backward_work(prob, d):
         return (float(n) ** 3 * d["n_evaluated"], "k_backward_gj (blocked Gauss-Jordan, per point)",
                 "n^3 complex multiply-adds per evaluated point (inverse) x 8 flops")
     labels = np.repeat(np.asarray(prob.bin_of_mode), prob.K)
-    mF = float(np.sum(labels == prob.L - 1))
+    mF = 2.0 * float(np.sum(labels == prob.L - 1))      # rows: both halves of each mode
     mE = float(n) - mF
     parents = float(np.prod(prob.radix[:-1]))
     per_parent = mE ** 3 + 2 * mE * mE * mF + mE * mF * mF + (mF * mF * mE + mE * mE * mF + mE * mF * mF)
