@@ -43,19 +43,47 @@ __device__ __forceinline__ double2 cneg2(double2 a) { return make_double2(-a.x, 
 // rows above it in parallel): the columns become the block's inverse times themselves.
 // Returns sum Log(pivots) (each Re > 0) and the smallest pivot real part in thread 0's
 // registers; all threads call it.
+// Sum Log of a sequence of pivots (each Re > 0) without a log or an atan2 per pivot (FP64
+// transcendentals are slow on this GPU): the running product, renormalised by powers of two,
+// and the FP32 sum of the pivots' arguments, which fixes the winding of the product's argument
+// (each argument lies in (-pi/2, pi/2); the FP32 sum errs by far less than pi).
+struct LogDet {
+  double2 prod = make_double2(1.0, 0.0);
+  int e2 = 0, count = 0;
+  float args = 0.f;
+  double mn = 1e300;
+  __device__ void add(double2 p) {
+    prod = cmul(prod, p);
+    args += atan2f((float)p.y, (float)p.x);
+    mn = fmin(mn, p.x);
+    if (!(p.x == p.x) || !(p.y == p.y)) mn = -1e300;
+    if ((++count & 7) == 0) renorm();
+  }
+  __device__ void renorm() {
+    const double m = fmax(fabs(prod.x), fabs(prod.y));
+    if (!(m > 0.0) || !(m < 1e300)) return;
+    const int ex = (int)((__double_as_longlong(m) >> 52) & 0x7ff) - 1022;
+    const double sc = __longlong_as_double((long long)(1023 - ex) << 52);
+    prod = make_double2(prod.x * sc, prod.y * sc);
+    e2 += ex;
+  }
+  __device__ double2 value() {
+    renorm();
+    const double TWO_PI = 6.283185307179586476925286766559, LN2 = 0.693147180559945309417232121458;
+    const double a0 = atan2(prod.y, prod.x);
+    const double wind = rint(((double)args - a0) / TWO_PI);
+    return make_double2(0.5 * log(fma(prod.x, prod.x, prod.y * prod.y)) + e2 * LN2, a0 + TWO_PI * wind);
+  }
+};
+
 __device__ void solve_block(double2* G, int nr, int ncol, int ld, double2* ldet, double* minre) {
   const int tid = threadIdx.x, T = blockDim.x;
   const int cols = nr + ncol;
-  double2 lsum = make_double2(0.0, 0.0);
-  double mn = 1e300;
+  LogDet acc;
   for (int k = 0; k < nr; ++k) {
     const double2 piv = G[k * ld + k];
     const double2 r = crecip(piv);
-    if (tid == 0) {
-      lsum = cadd2(lsum, make_double2(0.5 * log(fma(piv.x, piv.x, piv.y * piv.y)), atan2(piv.y, piv.x)));
-      mn = fmin(mn, piv.x);
-      if (!(piv.x == piv.x) || !(piv.y == piv.y)) mn = -1e300;
-    }
+    if (tid == 0) acc.add(piv);
     const int w = cols - k - 1;
     for (int idx = tid; idx < (nr - k - 1) * w; idx += T) {
       const int i = k + 1 + idx / w, j = k + 1 + idx % w;
@@ -73,8 +101,10 @@ __device__ void solve_block(double2* G, int nr, int ncol, int ld, double2* ldet,
     }
     __syncthreads();
   }
-  *ldet = lsum;
-  *minre = mn;
+  if (tid == 0) {
+    *ldet = acc.value();
+    *minre = acc.mn;
+  }
 }
 
 __global__ void __launch_bounds__(HT) k_herald_points(HeraldArgs a) {
@@ -143,13 +173,10 @@ __global__ void __launch_bounds__(HT) k_herald_points(HeraldArgs a) {
       Tm[i][i].x += 1.0;
       Tm[i][nf] = lq[pi];
     }
-    double2 lf = make_double2(0.0, 0.0);
-    double mnf = 1e300;
+    LogDet accf;
     for (int c = 0; c < nf; ++c) {
       const double2 piv = Tm[c][c];
-      lf = cadd2(lf, make_double2(0.5 * log(fma(piv.x, piv.x, piv.y * piv.y)), atan2(piv.y, piv.x)));
-      mnf = fmin(mnf, piv.x);
-      if (!(piv.x == piv.x) || !(piv.y == piv.y)) mnf = -1e300;
+      accf.add(piv);
       const double2 r = crecip(piv);
       for (int i = c + 1; i < nf; ++i) {
         const double2 li = cmul(Tm[i][c], r);
@@ -164,6 +191,8 @@ __global__ void __launch_bounds__(HT) k_herald_points(HeraldArgs a) {
     }
     double2 ly = make_double2(0.0, 0.0);
     for (int i = 0; i < nf; ++i) ly = cadd2(ly, cmul(lq[i], y[i]));
+    const double2 lf = accf.value();
+    const double mnf = accf.mn;
     const double re = sc[0].x + 0.5 * ly.x - 0.5 * (ld.x + lf.x), im = sc[0].y + 0.5 * ly.y - 0.5 * (ld.y + lf.y);
     const double m = exp(re);
     double s, c;
