@@ -118,19 +118,23 @@ __global__ void __launch_bounds__(kBtThreads) k_bwdt_parent(BackwardArgs b, BwdT
 // Leaves: CTA c takes leaves [c per, (c + 1) per) of the wave (parent-major); per leaf
 // inv(S(w)), s, t and the sums into the slot of (c, parent).
 template <class Ar>
-__global__ void __launch_bounds__(kBtThreads) k_bwdt_leaf(BackwardArgs b, BwdTree t) {
+__global__ void __launch_bounds__(kBwdLeafThreads, 2) k_bwdt_leaf(BackwardArgs b, BwdTree t) {
   using E = typename Ar::E;
   extern __shared__ __align__(16) unsigned char smem[];
-  const int n = b.n, nb = b.nb, mE = t.mE, mF = t.mF, tid = threadIdx.x, NT = kBtThreads;
+  // shared memory sized by mF (backward_leaf_smem_bytes): two CTAs of four warps per SM, so
+  // that one leaf's barriers overlap another's arithmetic
+  const int mE = t.mE, mF = t.mF, nb = kBwdLeafNb, tid = threadIdx.x, NT = kBwdLeafThreads;
   E* Pc = reinterpret_cast<E*>(smem);
-  E* Rx = Pc + (size_t)n * nb;
-  E* Dg = Rx + (size_t)nb * n;
+  E* Rx = Pc + (size_t)mF * nb;
+  E* Rnb = Rx + (size_t)nb * mF;
+  E* Dg = Rnb + (size_t)nb * mF;
   E* cFs = Dg + nb * nb;
   E* dFs = cFs + mF;
   E* sv = dFs + mF;
   E* tv = sv + mF;
-  E* Rnb = reinterpret_cast<E*>(smem + backward_tree_rn_offset(n, nb));
-  E* W = reinterpret_cast<E*>(reinterpret_cast<char*>(b.ws) + (size_t)blockIdx.x * (size_t)b.ws_slot_bytes);
+  const int per_slot = t.leaf_ctas > b.nparts ? 2 : 1;   // leaf CTAs sharing one n x n slot
+  E* W = reinterpret_cast<E*>(reinterpret_cast<char*>(b.ws) + (size_t)(blockIdx.x / per_slot) * (size_t)b.ws_slot_bytes) +
+         (size_t)(blockIdx.x % per_slot) * mF * mF;
   const long long nleaves = (t.p1 - t.p0) * t.half;
   const long long l0 = (long long)blockIdx.x * t.per, l1 = min(l0 + t.per, nleaves);
   const long long pfirst = l0 / t.half;
@@ -167,7 +171,7 @@ __global__ void __launch_bounds__(kBtThreads) k_bwdt_leaf(BackwardArgs b, BwdTre
       W[q] = v;
     }
     __syncthreads();
-    gj_invert<Ar>(W, mF, mF, nb, Pc, Rx, Dg, t.rn ? Rnb : nullptr);
+    gj_invert<Ar>(W, mF, mF, nb, Pc, Rx, Dg, Rnb);
     {                                                  // s = inv(S) c_F (warp per row), t = inv(S)^T d_F
       const int lane = tid & 31, warp = tid >> 5;
       for (int i = warp; i < mF; i += NT / 32) {
@@ -303,8 +307,6 @@ cudaError_t tree_wave(const BackwardArgs& b, const BwdTree& t0, cudaStream_t s) 
   cudaError_t err;
   if ((err = cudaFuncSetAttribute(k_bwdt_parent<Ar>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
           cudaSuccess ||
-      (err = cudaFuncSetAttribute(k_bwdt_leaf<Ar>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
-          cudaSuccess ||
       (err = cudaFuncSetAttribute(k_bwdt_assemble<Ar>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
           cudaSuccess)
     return err;
@@ -314,13 +316,21 @@ cudaError_t tree_wave(const BackwardArgs& b, const BwdTree& t0, cudaStream_t s) 
   if ((err = cudaGetLastError()) != cudaSuccess) return err;
   const long long nleaves = parents * t.half;
   const long long gl = (nleaves + t.per - 1) / t.per;
-  k_bwdt_leaf<Ar><<<(unsigned)gl, kBtThreads, smem, s>>>(b, t);
+  const size_t lsmem = backward_leaf_smem_bytes(t.mF);
+  if ((err = cudaFuncSetAttribute(k_bwdt_leaf<Ar>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsmem)) !=
+      cudaSuccess)
+    return err;
+  k_bwdt_leaf<Ar><<<(unsigned)gl, kBwdLeafThreads, lsmem, s>>>(b, t);
   if ((err = cudaGetLastError()) != cudaSuccess) return err;
   k_bwdt_assemble<Ar><<<(unsigned)t.nparts, kBtThreads, smem, s>>>(b, t);
   return cudaGetLastError();
 }
 
 }  // namespace
+
+size_t backward_leaf_smem_bytes(int mF) {
+  return (size_t)16 * ((size_t)3 * mF * kBwdLeafNb + (size_t)kBwdLeafNb * kBwdLeafNb + 4 * (size_t)mF);
+}
 
 size_t backward_tree_smem_bytes(int n, int nb) {
   return (size_t)16 * ((size_t)2 * n * nb + (size_t)nb * nb + 4 * (size_t)n + 1) + sizeof(double2) * GBSBIN_MAX_L;

@@ -29,7 +29,11 @@ struct BwdTree {
   int nparts;               // CTAs of the assembly launch (its partials)
   int zero_partials;        // first wave: the assembly zeroes its partials
   int rn;                   // the kernels' shared memory holds the block-row buffer (nb x n)
+  int leaf_ctas;            // CTAs of the leaf launch: two per SM (128 threads each) where two
+                            // mF x mF slots fit in an SM's n x n workspace slot, else one
 };
+constexpr int kBwdLeafThreads = 128;
+constexpr int kBwdLeafNb = 8;             // pivots per Gauss-Jordan step in the leaves (nb^2 <= 128)
 
 // Adjoint of the inverse DFT and the per-point weights beta (into b.bufB); *beta receives it.
 cudaError_t launch_backward_weights(const BackwardArgs& b, const double* dLdP, cudaStream_t s, const double2** beta);
@@ -41,5 +45,6 @@ cudaError_t launch_backward_tree_wave(const BackwardArgs& b, const BwdTree& t, c
 // outS, outg from the first nparts partials.
 cudaError_t launch_backward_reduce(const BackwardArgs& b, int nparts, cudaStream_t s);
 size_t backward_tree_smem_bytes(int n, int nb);
+size_t backward_leaf_smem_bytes(int mF);
 
 }  // namespace gbsbin

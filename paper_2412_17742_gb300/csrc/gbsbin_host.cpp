@@ -1026,11 +1026,13 @@ int backward_tree_setup(gbsbin_plan* P) {
   t.goff[L] = off;
   const long long budget = 512LL << 20;
   const long long wave = std::max(1LL, std::min(parents, budget / (t.pstride * 16)));
-  t.per = (int)((wave * half + P->num_sms - 1) / P->num_sms);
+  // leaves: two CTAs per SM where two mF x mF matrices fit in an SM's n x n slot
+  t.leaf_ctas = 2LL * mF * mF <= (long long)n * n ? 2 * P->num_sms : P->num_sms;
+  t.per = (int)((wave * half + t.leaf_ctas - 1) / t.leaf_ctas);
   t.maxspan = (int)((t.per - 1) / half + 2);
   t.nparts = (int)std::min<long long>(parents, P->num_sms);
   const size_t pbuf = (size_t)wave * t.pstride * 16;
-  const size_t part = (size_t)P->num_sms * t.maxspan * t.lstride * 16;
+  const size_t part = (size_t)t.leaf_ctas * t.maxspan * t.lstride * 16;
   const size_t pinv = ((size_t)n * sizeof(int) + 15) / 16 * 16;
   int st = dalloc(&P->d_bt, pbuf + part + pinv);
   if (st) return st;
