@@ -48,6 +48,8 @@ CASES = [
         alpha=0.3 * np.ones((65, 1), complex))),
     # n = 60, three groups of 20 rows: too large a last group for the small tree
     ("n60_l3_last_group_20_rows", lambda: _problem(909, 30, 1, 3, [4, 3, 5], displaced=True)),
+    # the largest matrix the library takes: n = 512, five groups of ~102 rows (five levels)
+    ("n512_l5_max", lambda: _problem(911, 256, 1, 5, [1, 1, 2, 1, 2], displaced=True, r_range=(0.1, 0.4))),
     # the largest last group the shared-memory Householder reduction takes: 116 rows (n = 232)
     ("n232_last_group_116_rows", lambda: synth.Problem(
         116, 1, np.random.default_rng(907).uniform(0.2, 0.7, (116, 1)),
