@@ -308,8 +308,8 @@ def main():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the other workloads (n=32 grid, 256-problem batch, n=200 gradient, "
                          "M=256 total photon number, Fock inputs, App. D fine-grained)")
-    ap.add_argument("--extras", default="n32,batch,n200,e3,fock,herald,appd",
-                    help="comma list of the other workloads to time: n32, batch, n200, e3, fock, appd")
+    ap.add_argument("--extras", default="n32,batch,n200,e3,fock,herald,moments,appd",
+                    help="comma list of the other workloads to time: n32, batch, n200, e3, fock, herald, moments, appd")
     ap.add_argument("--extra-steps", type=int, default=3)
     args = ap.parse_args()
     if args.impl == "reference":
@@ -543,6 +543,8 @@ def extra_workloads(gb, torch, stream, flush, steps, world, which=("n32", "batch
         out.update(_extra_fock(gb, torch, stream, flush, steps, world))
     if "herald" in which:
         out.update(_extra_herald(gb, torch, stream, flush, steps, world))
+    if "moments" in which:
+        out.update(_extra_moments(gb, torch, steps))
     if "appd" in which:
         try:
             out.update(_extra_distinguishable(gb, torch, steps))
@@ -581,6 +583,44 @@ def _extra_herald(gb, torch, stream, flush, steps, world):
                 entry["fidelity_n1"] = float(np.sqrt((r[1, 1, 1] / p[1]).real))
             out[name] = entry
     return {"herald": out}
+
+
+def _extra_moments(gb, torch, steps):
+    """Cumulant tensors of orders 1-4 of the binned counts on the GPU (FP64) for the n = 192
+    workload (three groups) and n = 512 (M = 256, eight groups): the device time of the launches
+    (CUDA events inside the call), the whole call (host state algebra, uploads, allocation), the
+    host evaluators' time for the same four tensors, and the largest relative difference.
+    Roofline on the complex multiply-adds: n^2 (n + 32) / 2 for the Hermitian Y_b (the tiles on
+    and above the diagonal) and L^2 n^2 / 2 for the C_4 traces, x 8 FP64 flops, against the
+    derived FP64 peak."""
+    out = {}
+    rng = np.random.default_rng(77)
+    cases = [("n192_L3", synth.config(2)),
+             ("n512_L8", synth.random_problem(rng, 256, 1, 8, 2, displaced=True, r_range=(0.3, 0.9)))]
+    peak64 = SMS * FP64_FMA_PER_SM_CLK * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    for name, prob in cases:
+        gb.gbsbin_cumulants_device(prob)                       # warm-up
+        k = max(3, min(steps, 10))
+        dev_ms, t0 = [], time.perf_counter()
+        for _ in range(k):
+            outs, ms = gb.gbsbin_cumulants_device(prob, with_time=True)
+            dev_ms.append(ms)
+        call_ms = (time.perf_counter() - t0) / k * 1e3
+        entry = {"n": 2 * prob.M * prob.K, "groups": int(prob.L), "device_ms": float(np.median(dev_ms)),
+                 "call_ms": call_ms, "precision": "fp64"}
+        n, L = entry["n"], entry["groups"]
+        flops = 8.0 * (n * n * (n + 32) / 2.0 + L * L * n * n / 2.0)
+        entry["roofline"] = {"bound": "alu", "achieved": flops / (entry["device_ms"] * 1e-3) / 1e12, "peak": peak64,
+                             "unit": "TFLOP/s", "peak_source": "derived FP64 peak"}
+        entry["roofline"]["frac"] = entry["roofline"]["achieved"] / peak64
+        if n <= 192:
+            t0 = time.perf_counter()
+            mean, cov = gb.gbsbin_moments(prob)
+            host = [mean, cov, gb.gbsbin_cumulants3(prob), gb.gbsbin_cumulants4(prob)]
+            entry["host_ms"] = (time.perf_counter() - t0) * 1e3
+            entry["max_rel_diff_vs_host"] = max(float(np.abs(a - b).max() / np.abs(b).max()) for a, b in zip(outs, host))
+        out[name] = entry
+    return {"cumulants_device": out}
 
 
 def _extra_distinguishable(gb, torch, steps):

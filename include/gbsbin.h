@@ -427,6 +427,35 @@ int gbsbin_cumulants3(const gbsbin_problem* p, double* k3);
 int gbsbin_cumulants4(const gbsbin_problem* p, double* k4);
 
 /*
+ * The cumulants of gbsbin_moments, gbsbin_cumulants3 and gbsbin_cumulants4 (Sec. VI,
+ * coarse-grained moments and cumulants) computed on the GPU, FP64 throughout.  With
+ * XA = I - Sigma^{-1}, R = (I - XA)^{-1} = Sigma, so W = XA R = Sigma^(1) (Hermitian),
+ * u = R X gamma = X gamma + W X gamma and v = R^T gamma = gamma + W^T gamma: no inverse is
+ * formed.  The host builds and validates the state as for gbsbin_plan_create and sorts the rows
+ * by group; the device then forms (C_r as for gbsbin_cumulants4; W_ab the block of rows of
+ * group a, columns of group b):
+ *   u, v;
+ *   for order >= 3, Y_b = W_{:,b} W_{:,b}^H per group b (Hermitian: the 32 x 32 tiles on and
+ *     above the diagonal, the depth split into slices where the tiles alone leave SMs idle);
+ *   for order 4, q_d = W_{:,d} u_d and p_ab = v_a^T Y_b[a rows, :];
+ *   C_1 .. C_order, one CTA per coefficient, each a fixed-order sum over one block:
+ *     C_3(a,b,c) = sum_{i in a, k in c} Y_b[i,k] (1/6 conj(W_ik) + 1/2 v_i u_k),
+ *     C_4(a,b,c,d) = 1/8 sum_{i in a, k in c} Y_b[i,k] conj(Y_d[i,k]) + 1/2 sum_{k in c} p_ab[k] q_d[k]
+ *     (one CTA for (a,b,c,d) and (a,d,c,b), whose traces are conjugate);
+ *   kappa by the chain rule of e = e^t - 1 over the set partitions of the slots, a thread per
+ *     entry.
+ * The highest non-null output sets the order: mean (L doubles), cov (L x L), k3 (L^3), k4 (L^4),
+ * row-major, caller-owned host memory; lower orders may be null.  Work ~n^3/2 complex
+ * multiply-adds for the Y_b and ~L^2 n^2/2 for the C_4 traces; device memory up to
+ * (1 + 2 L) n^2 x 16 bytes, allocated and freed per call.  Synchronous on `stream`.
+ * *kernel_ms (may be NULL) receives the device time of the launches by CUDA events (uploads and
+ * the final copies excluded).  Errors: ERR_ARG (p NULL or every output NULL), ERR_UNSUPPORTED
+ * (L > 16), then as gbsbin_moments, ERR_NOMEM, ERR_CUDA.
+ */
+int gbsbin_cumulants_device(const gbsbin_problem* p, double* mean, double* cov, double* k3, double* k4,
+                            double* kernel_ms, void* stream);
+
+/*
  * Total photon-number distribution Pr(N), N = 0..Nmax, over all detectors (grouping
  * ignored), by the power series of Sec. IV / App. A: with z = (eta, ..., eta),
  * log q(eta) = sum_k a_k eta^k, a_k = tr((XA)^k) / (2k) + 1/2 gamma^T (XA)^(k-1) X gamma,

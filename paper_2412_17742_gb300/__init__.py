@@ -38,7 +38,7 @@ EXPORTED = ["gbsbin_default_options", "gbsbin_plan_create", "gbsbin_plan_set_sta
             "gbsbin_fock_execute", "gbsbin_fock_execute_host", "gbsbin_fock_diagnostics",
             "gbsbin_fock_plan_destroy", "gbsbin_cumulants3", "gbsbin_cumulants4", "gbsbin_fock_plan_nodes",
             "gbsbin_total_photon_series", "gbsbin_cumulant_groups", "gbsbin_prob_distinguishable",
-            "gbsbin_prob_distinguishable_device", "gbsbin_herald_plan_create", "gbsbin_herald_table_size",
+            "gbsbin_prob_distinguishable_device", "gbsbin_cumulants_device", "gbsbin_herald_plan_create", "gbsbin_herald_table_size",
             "gbsbin_herald_prob_size", "gbsbin_herald_execute", "gbsbin_herald_execute_host",
             "gbsbin_herald_diagnostics", "gbsbin_herald_plan_destroy"]
 GBSBIN_HERALD_TRACED = -1
@@ -133,6 +133,8 @@ def load():
     lib.gbsbin_prob_distinguishable.restype = ctypes.c_int
     lib.gbsbin_prob_distinguishable_device.argtypes = [ctypes.POINTER(gbsbin_problem), _ip, vp, vp, vp]
     lib.gbsbin_prob_distinguishable_device.restype = ctypes.c_int
+    lib.gbsbin_cumulants_device.argtypes = [ctypes.POINTER(gbsbin_problem), vp, vp, vp, vp, vp, vp]
+    lib.gbsbin_cumulants_device.restype = ctypes.c_int
     lib.gbsbin_read_points.argtypes = [vp, vp, vp, vp]
     lib.gbsbin_table_from_logq_noalloc.argtypes = [ctypes.c_int, _ip, ctypes.c_int, vp, vp, vp]
     lib.gbsbin_backward.argtypes = [vp, vp, ctypes.POINTER(gbsbin_grads), vp]
@@ -405,6 +407,22 @@ def gbsbin_cumulants4(prob):
     k4 = np.zeros((L, L, L, L), dtype=np.float64)
     _check(load().gbsbin_cumulants4(ctypes.byref(args.c), k4.ctypes.data_as(ctypes.c_void_p)), "gbsbin_cumulants4")
     return k4
+
+
+def gbsbin_cumulants_device(prob, order=4, stream=None, with_time=False):
+    """Cumulant tensors of orders 1..order of the binned counts on the GPU (FP64): the list
+    [mean (L,), cov (L, L), k3 (L, L, L), k4 (L, L, L, L)][:order]; with_time also returns the
+    device time of the launches in ms."""
+    if not 1 <= int(order) <= 4:
+        raise ValueError("order must be 1..4")
+    args = ProblemArgs(prob)
+    L = int(len(args.cut))
+    outs = [np.zeros((L,) * r, dtype=np.float64) for r in range(1, int(order) + 1)]
+    ptrs = [o.ctypes.data_as(ctypes.c_void_p) for o in outs] + [None] * (4 - len(outs))
+    ms = ctypes.c_double()
+    _check(load().gbsbin_cumulants_device(ctypes.byref(args.c), *ptrs, ctypes.byref(ms), _stream_handle(stream)),
+           "gbsbin_cumulants_device")
+    return (outs, ms.value) if with_time else outs
 
 
 def gbsbin_total_photon_series(prob, Nmax):

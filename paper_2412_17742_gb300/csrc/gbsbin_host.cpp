@@ -13,6 +13,7 @@
 #include "gbsbin_backward_tree.h"
 #include "gbsbin_host_state.h"
 #include "gbsbin_internal.h"
+#include "gbsbin_moments.h"
 
 using cd = std::complex<double>;
 using namespace gbsbin;
@@ -390,7 +391,8 @@ int adjacency(const std::vector<cd>& S1, const std::vector<cd>& zbar, int n, std
 }
 
 int build_state(const gbsbin_problem* p, int n, std::vector<cd>& XA, std::vector<cd>& gamma,
-                std::vector<cd>& Xgamma, int* has_gamma, std::vector<cd>* zbar_out = nullptr) {
+                std::vector<cd>& Xgamma, int* has_gamma, std::vector<cd>* zbar_out = nullptr,
+                std::vector<cd>* s1_out = nullptr) {
   std::vector<cd> S1, zbar;
   if (p->sigma1) {
     S1.resize((size_t)n * n);
@@ -405,6 +407,7 @@ int build_state(const gbsbin_problem* p, int n, std::vector<cd>& XA, std::vector
   int st = adjacency(S1, zbar, n, XA, gamma, Xgamma);
   if (st) return st;
   if (zbar_out) *zbar_out = zbar;
+  if (s1_out) s1_out->swap(S1);
   *has_gamma = 0;
   for (int i = 0; i < n; ++i)
     if (gamma[i] != cd(0.0)) *has_gamma = 1;
@@ -2155,6 +2158,47 @@ int gbsbin_cumulants4(const gbsbin_problem* p, double* k4) {
           k4[(((size_t)l0 * L + l1) * L + l2) * L + l3] = kap.real();
         }
   return GBSBIN_OK;
+}
+
+// The cumulants of orders 1-4 on the GPU: the host state algebra (validation included), the
+// rows sorted by group, then gbsbin_moments.cu's launches.  With XA = I - Sigma^{-1} (Sigma =
+// I + Sigma^(1)), R = (I - XA)^{-1} = Sigma and W = XA R = Sigma^(1): the device starts from
+// Sigma^(1), made exactly Hermitian ((S + S^H) / 2; the state was validated Hermitian).
+int gbsbin_cumulants_device(const gbsbin_problem* p, double* mean, double* cov, double* k3, double* k4,
+                            double* kernel_ms, void* stream) {
+  if (!p) return GBSBIN_ERR_ARG;
+  const int order = k4 ? 4 : k3 ? 3 : cov ? 2 : mean ? 1 : 0;
+  if (order == 0) return GBSBIN_ERR_ARG;
+  gbsbin_options o;
+  gbsbin_default_options(&o);
+  int st = validate_shape(p, &o);
+  if (st) return st;
+  if (p->L > GBSBIN_MOM_MAX_L) return GBSBIN_ERR_UNSUPPORTED;
+  const int MK = p->M * p->K, n = 2 * MK, L = p->L;
+  std::vector<cd> XA, gamma, Xgamma, S1;
+  int has_gamma = 0;
+  if ((st = build_state(p, n, XA, gamma, Xgamma, &has_gamma, nullptr, &S1))) return st;
+  std::vector<int> perm, goff(L + 1, 0);
+  for (int l = 0; l < L; ++l) {
+    goff[l] = (int)perm.size();
+    for (int i = 0; i < n; ++i)
+      if (p->bin_of_mode[(i % MK) / p->K] == l) perm.push_back(i);
+  }
+  goff[L] = n;
+  std::vector<cd> Wp((size_t)n * n), gp(n), Xgp(n);
+  for (int a = 0; a < n; ++a) {
+    for (int b = 0; b < n; ++b)
+      Wp[(size_t)a * n + b] = 0.5 * (S1[(size_t)perm[a] * n + perm[b]] + std::conj(S1[(size_t)perm[b] * n + perm[a]]));
+    gp[a] = gamma[perm[a]];
+    Xgp[a] = Xgamma[perm[a]];
+  }
+  double* out[4] = {mean, cov, k3, k4};
+  float ms = 0.f;
+  st = cumulants_device(n, L, goff.data(), reinterpret_cast<const double*>(Wp.data()),
+                        reinterpret_cast<const double*>(gp.data()), reinterpret_cast<const double*>(Xgp.data()), order,
+                        out, (cudaStream_t)stream, kernel_ms ? &ms : nullptr);
+  if (!st && kernel_ms) *kernel_ms = ms;
+  return st;
 }
 
 // Total photon-number distribution by the power series of App. A (a second evaluator beside
