@@ -193,7 +193,8 @@ typedef enum {
                                       pairs of FP32; chosen automatically for standalone
                                       GBSBIN_FP32_REFINE plans where kernel 11 does not
                                       apply and it needs under half the per-point LUs'
-                                      work (last group <= 116 rows); a shard runs the
+                                      work (last group <= 192 rows; above 116 the
+                                      Hessenberg reduction works through L2); a shard runs the
                                       first-axis subtrees that cover its slice          */
   GBSBIN_KERNEL_BTREE_FP64 = 14,   /* the same in FP64; chosen for GBSBIN_FP64 plans under
                                       the same conditions                                   */

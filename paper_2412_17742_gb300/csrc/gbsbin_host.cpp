@@ -887,7 +887,7 @@ size_t btree_configure(gbsbin_plan* P, int halve_first, const int* nb, const int
 // pivots in as few equal sub-steps as the shared-memory budget allows, and the halving (last
 // axis or first) that needs fewer multiply-adds.  Returns the device bytes of depths
 // 1 .. L-1, the sub-step scratch and the Hessenberg leaves, or 0 when the problem does not
-// suit it (one group, a last group above GBSBIN_BT_MAX_HESS rows, scratch above 8 GB).
+// suit it (one group, a last group above GBSBIN_BT_MAX_LAST rows, scratch above 8 GB).
 size_t btree_layout(gbsbin_plan* P) {
   const int L = P->L, n = P->n;
   if (L < 2) return 0;
@@ -910,7 +910,7 @@ size_t btree_layout(gbsbin_plan* P) {
   }
   t.L = L;
   t.mL = m[L - 1];
-  if (t.mL > GBSBIN_BT_MAX_HESS || t.mL < 1) return 0;
+  if (t.mL > GBSBIN_BT_MAX_LAST || t.mL < 1) return 0;
   int best = -1;
   double best_macs = 0.0;
   const bool shard = P->grid.e_lo != 0 || P->grid.e_hi != P->grid.n_full;

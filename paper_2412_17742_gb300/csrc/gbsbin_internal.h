@@ -170,7 +170,9 @@ struct TreeArgs {
 // each a top launch (CTA per child) and a bottom launch (CTAs per row chunk); the last
 // group's blocks are reduced to Hessenberg form (a CTA per leaf parent) and every evaluated
 // point is an O(m^2) Hessenberg elimination (a warp per point) writing the unfinished log q.
-#define GBSBIN_BT_MAX_HESS 116          // largest last group (shared-memory Householder: 225 KB at 116)
+#define GBSBIN_BT_MAX_HESS 116          // largest last group reduced in shared memory (225 KB at 116)
+#define GBSBIN_BT_MAX_LAST 192          // largest last group (above 116 rows the reduction works
+                                        // in the plan's Hessenberg buffer, through L2)
 #define GBSBIN_BT_SMEM (200 * 1024)     // shared-memory budget of one sub-step's pivot rows
 #define GBSBIN_BT_MAX_NBS 128           // pivots of one sub-step (at most)
 struct BTreeStep {

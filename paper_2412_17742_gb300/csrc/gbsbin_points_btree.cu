@@ -61,7 +61,8 @@ constexpr int TOP_THREADS = 512;
 constexpr int BOT_WARPS = 16;
 constexpr int HESS_THREADS = 256;
 constexpr int LEAF_WARPS = 4;
-constexpr int LEAF_SMAX = (GBSBIN_BT_MAX_HESS + 31) / 32;
+constexpr int LEAF_SMAX = (GBSBIN_BT_MAX_HESS + 31) / 32;       // leaves of last groups <= 128 rows
+constexpr int LEAF_SMAX_BIG = (GBSBIN_BT_MAX_LAST + 31) / 32;   // and above
 
 template <class Ar>
 __device__ __forceinline__ typename Ar::E* elem(float4* p) {
@@ -315,25 +316,36 @@ __global__ void __launch_bounds__(BOT_WARPS * 32) k_bt_bottom(BTreeArgs a, BTree
 
 // ------------------------------------------------------------------------- Hessenberg
 // One CTA per leaf parent: the m x m block A_L with c and conj(u) as two extra columns in
-// shared memory (row stride m + 3, odd in 16-byte units), reduced to upper Hessenberg form
+// shared memory (row stride m + 3, odd in 16-byte units), or, for GM (m above
+// GBSBIN_BT_MAX_HESS), A_L in the node's slot of the Hessenberg buffer H (row stride m, read and
+// written through L2) with the two columns in shared memory, reduced to upper Hessenberg form
 // by Householder reflectors H_k = I - beta v v^H on rows/columns k + 1 .. m - 1
 // (v = x - alpha e_1, alpha = -e^{i arg x_0} ||x||, beta = 2 / ||v||^2), applied from the left
 // to A and the two columns and from the right to A.  Each product vector (v^H A per column,
 // A v per row) is formed by g threads per column or row over interleaved index sets, then
 // summed in a fixed order, so the dependent chains are m / g long.  Writes H (m x m),
 // a = Q^T u, b = Q^H c and the exponent collected so far (the augmented corner).
-template <class Ar>
+template <class Ar, bool GM>
 __global__ void __launch_bounds__(HESS_THREADS) k_bt_hess(BTreeArgs a) {
   using E = typename Ar::E;
   extern __shared__ __align__(16) unsigned char sm_raw[];
-  const int m = a.mL, ld = m + 3, D = m + 1;
-  E* A = reinterpret_cast<E*>(sm_raw);               // m x ld
-  E* v = A + (size_t)m * ld;                         // m
+  const int m = a.mL, ld = GM ? m : m + 3, D = m + 1;
+  const long long node = blockIdx.x;
+  E* const Hn = elem<Ar>(a.H) + node * (long long)m * m;
+  E* A = GM ? Hn : reinterpret_cast<E*>(sm_raw);     // m x ld (+ the two columns in shared memory)
+  E* v = GM ? reinterpret_cast<E*>(sm_raw) : A + (size_t)m * ld;   // m
   E* sv = v + m;                                     // m + 2 (left products per column)
   E* tv = sv + m + 2;                                // m (right products per row)
   E* sc = tv + m;                                    // alpha, beta
   E* part = sc + 2;                                  // HESS_THREADS partial sums
-  const long long node = blockIdx.x;
+  E* X = part + HESS_THREADS;                        // GM: c and conj(u), m x 2
+  // entry (i, j) of the augmented block, j < m + 2
+  auto at = [&](int i, int j) -> E& {
+    if constexpr (GM) {
+      if (j >= m) return X[2 * i + (j - m)];
+    }
+    return A[(size_t)i * ld + j];
+  };
   const E* src = elem<Ar>(a.mat[a.L - 1]) + node * (long long)D * D;
   const int tid = threadIdx.x, T = blockDim.x, lane = tid & 31, warp = tid >> 5;
   for (int idx = tid; idx < m * (m + 2); idx += T) {
@@ -342,15 +354,15 @@ __global__ void __launch_bounds__(HESS_THREADS) k_bt_hess(BTreeArgs a) {
     if (j < m) val = src[(long long)i * D + j];
     else if (j == m) val = src[(long long)i * D + m];                 // c
     else val = Ar::conj(src[(long long)m * D + i]);                    // conj(u)
-    A[(size_t)i * ld + j] = val;
+    at(i, j) = val;
   }
   __syncthreads();
   for (int k = 0; k + 2 < m; ++k) {
     if (warp == 0) {                                 // the reflector of column k
       E nrm2 = Ar::zero();
-      for (int i = k + 1 + lane; i < m; i += 32) nrm2 = Ar::add(nrm2, Ar::norm2(A[(size_t)i * ld + k]));
+      for (int i = k + 1 + lane; i < m; i += 32) nrm2 = Ar::add(nrm2, Ar::norm2(at(i, k)));
       for (int o = 16; o > 0; o >>= 1) nrm2 = Ar::add(nrm2, shfl_xor(nrm2, o));
-      const E x0 = A[(size_t)(k + 1) * ld + k];
+      const E x0 = at(k + 1, k);
       E alpha = Ar::zero(), beta = Ar::zero();
       if (Ar::re(nrm2) > 0.f) {
         const E nrm = Ar::rsqrt_real(nrm2);
@@ -361,7 +373,7 @@ __global__ void __launch_bounds__(HESS_THREADS) k_bt_hess(BTreeArgs a) {
         beta = Ar::add(Ar::rrecip(vn2), Ar::rrecip(vn2));
       }
       for (int i = k + 1 + lane; i < m; i += 32) {
-        E vi = A[(size_t)i * ld + k];
+        E vi = at(i, k);
         if (i == k + 1) vi = Ar::add(vi, Ar::neg(alpha));
         v[i] = vi;
       }
@@ -380,7 +392,7 @@ __global__ void __launch_bounds__(HESS_THREADS) k_bt_hess(BTreeArgs a) {
         if (c < nc) {
           const int j = k + 1 + c;
           E s = Ar::zero();
-          for (int i = k + 1 + g; i < m; i += gl) s = Ar::fma(Ar::conj(v[i]), A[(size_t)i * ld + j], s);
+          for (int i = k + 1 + g; i < m; i += gl) s = Ar::fma(Ar::conj(v[i]), at(i, j), s);
           part[tid] = s;
         }
       }
@@ -394,7 +406,7 @@ __global__ void __launch_bounds__(HESS_THREADS) k_bt_hess(BTreeArgs a) {
       const int wl = m + 2 - (k + 1);
       for (int idx = tid; idx < (m - k - 1) * wl; idx += T) {
         const int i = k + 1 + idx / wl, j = k + 1 + idx % wl;
-        A[(size_t)i * ld + j] = Ar::fms(A[(size_t)i * ld + j], v[i], sv[j]);
+        at(i, j) = Ar::fms(at(i, j), v[i], sv[j]);
       }
       __syncthreads();
       // right: t_i = beta sum_{j > k} A_ij v_j, every row
@@ -403,7 +415,7 @@ __global__ void __launch_bounds__(HESS_THREADS) k_bt_hess(BTreeArgs a) {
         const int i = tid / gr, g = tid - i * gr;
         if (i < m) {
           E t = Ar::zero();
-          for (int j = k + 1 + g; j < m; j += gr) t = Ar::fma(A[(size_t)i * ld + j], v[j], t);
+          for (int j = k + 1 + g; j < m; j += gr) t = Ar::fma(at(i, j), v[j], t);
           part[tid] = t;
         }
       }
@@ -417,21 +429,21 @@ __global__ void __launch_bounds__(HESS_THREADS) k_bt_hess(BTreeArgs a) {
       const int wr = m - (k + 1);
       for (int idx = tid; idx < m * wr; idx += T) {
         const int i = idx / wr, j = k + 1 + idx % wr;
-        A[(size_t)i * ld + j] = Ar::fms(A[(size_t)i * ld + j], tv[i], Ar::conj(v[j]));
+        at(i, j) = Ar::fms(at(i, j), tv[i], Ar::conj(v[j]));
       }
-      if (tid == 0) A[(size_t)(k + 1) * ld + k] = sc[0];
+      if (tid == 0) at(k + 1, k) = sc[0];
     }
     __syncthreads();
   }
-  E* H = elem<Ar>(a.H) + node * (long long)m * m;
   E* hv = elem<Ar>(a.hv) + node * (long long)(2 * m + 1);
-  for (int idx = tid; idx < m * m; idx += T) {
-    const int i = idx / m, j = idx - i * m;
-    H[idx] = A[(size_t)i * ld + j];
-  }
+  if constexpr (!GM)                                 // (GM: the reduction ran in place)
+    for (int idx = tid; idx < m * m; idx += T) {
+      const int i = idx / m, j = idx - i * m;
+      Hn[idx] = at(i, j);
+    }
   for (int i = tid; i < m; i += T) {
-    hv[i] = Ar::conj(A[(size_t)i * ld + m + 1]);     // a = Q^T u = conj(Q^H conj(u))
-    hv[m + i] = A[(size_t)i * ld + m];               // b = Q^H c
+    hv[i] = Ar::conj(at(i, m + 1));     // a = Q^T u = conj(Q^H conj(u))
+    hv[m + i] = at(i, m);               // b = Q^H c
   }
   if (tid == 0) hv[2 * m] = src[(long long)m * D + m];   // the exponent so far
 }
@@ -456,8 +468,8 @@ __device__ __forceinline__ void write_record(const BTreeArgs& a, long long e, do
 // recurrences (see the top of the file).  Lane t holds entries t + 32 s of the current pivot
 // row (and of the running sums s_j); row i + 1 of H, the subdiagonal entry and b_{i+1} are read
 // from L2 one step ahead of their use.
-template <class Ar, bool DISP>
-__global__ void __launch_bounds__(LEAF_WARPS * 32, 4) k_bt_leaf(BTreeArgs a) {
+template <class Ar, bool DISP, int SMX>
+__global__ void __launch_bounds__(LEAF_WARPS * 32, SMX <= LEAF_SMAX ? 4 : 2) k_bt_leaf(BTreeArgs a) {
   using E = typename Ar::E;
   const int lane = threadIdx.x & 31;
   const long long leaf = (long long)blockIdx.x * LEAF_WARPS + (threadIdx.x >> 5);
@@ -472,9 +484,9 @@ __global__ void __launch_bounds__(LEAF_WARPS * 32, 4) k_bt_leaf(BTreeArgs a) {
   const E* hv = elem<Ar>(a.hv) + parent * (long long)(2 * m + 1);
   const E* av = hv;
   const E* bv = hv + m;
-  E r[LEAF_SMAX], nx[LEAF_SMAX], sacc[DISP ? LEAF_SMAX : 1];
+  E r[SMX], nx[SMX], sacc[DISP ? SMX : 1];
 #pragma unroll
-  for (int s = 0; s < LEAF_SMAX; ++s) {
+  for (int s = 0; s < SMX; ++s) {
     const int j = lane + 32 * s;
     E x = Ar::zero(), y1 = Ar::zero();
     if (s < S && j < m) {
@@ -498,17 +510,17 @@ __global__ void __launch_bounds__(LEAF_WARPS * 32, 4) k_bt_leaf(BTreeArgs a) {
   int wind = 0;
   float e2 = rec.meta.y, mn = rec.meta.z;
 #pragma unroll
-  for (int sb = 0; sb < LEAF_SMAX; ++sb) {
+  for (int sb = 0; sb < SMX; ++sb) {
     if (sb >= S) break;
     for (int il = 0; il < 32; ++il) {
       const int i = 32 * sb + il;
       if (i >= m) break;
       // the next step's row, subdiagonal entry and right-hand side, loaded ahead
-      E nx2[LEAF_SMAX], hsub2 = Ar::zero(), bnext2 = Ar::zero();
+      E nx2[SMX], hsub2 = Ar::zero(), bnext2 = Ar::zero();
       const bool more = i + 2 < m;
       const E* hrow2 = H + (long long)(i + 2) * m;
 #pragma unroll
-      for (int s = 0; s < LEAF_SMAX; ++s) {
+      for (int s = 0; s < SMX; ++s) {
         const int j = lane + 32 * s;
         nx2[s] = (more && s >= sb && s < S && j > i + 1 && j < m) ? hrow2[j] : Ar::zero();
       }
@@ -524,7 +536,7 @@ __global__ void __launch_bounds__(LEAF_WARPS * 32, 4) k_bt_leaf(BTreeArgs a) {
         const E zi = Ar::mul(Ar::add(av[i], Ar::neg(si)), iq);
         zy = Ar::fma(zi, y, zy);
 #pragma unroll
-        for (int s = sb; s < LEAF_SMAX; ++s) {
+        for (int s = sb; s < SMX; ++s) {
           const int j = lane + 32 * s;
           if (s < S && j > i && j < m) sacc[s] = Ar::fma(zi, r[s], sacc[s]);
         }
@@ -541,7 +553,7 @@ __global__ void __launch_bounds__(LEAF_WARPS * 32, 4) k_bt_leaf(BTreeArgs a) {
       const E li = Ar::mul(hsub, iq);
       if constexpr (DISP) y = Ar::fms(bnext, li, y);
 #pragma unroll
-      for (int s = sb; s < LEAF_SMAX; ++s) {
+      for (int s = sb; s < SMX; ++s) {
         const int j = lane + 32 * s;
         if (s < S && j > i && j < m) {
           E h = nx[s];
@@ -550,7 +562,7 @@ __global__ void __launch_bounds__(LEAF_WARPS * 32, 4) k_bt_leaf(BTreeArgs a) {
         }
       }
 #pragma unroll
-      for (int s = 0; s < LEAF_SMAX; ++s) nx[s] = nx2[s];
+      for (int s = 0; s < SMX; ++s) nx[s] = nx2[s];
       hsub = hsub2;
       bnext = bnext2;
     }
@@ -674,15 +686,24 @@ cudaError_t launch_btree_ar(const BTreeArgs& a, const BTreeStep* steps, int nste
   long long parents = 1;
   for (int l = 0; l + 1 < a.grid.L; ++l) parents *= a.cnt[l];
   const size_t hsmem = btree_hess_smem_bytes(a.mL);
-  if (hsmem > 48 * 1024) {
-    err = cudaFuncSetAttribute(k_bt_hess<Ar>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsmem);
-    if (err != cudaSuccess) return err;
+  if (a.mL <= GBSBIN_BT_MAX_HESS) {
+    if (hsmem > 48 * 1024) {
+      err = cudaFuncSetAttribute(k_bt_hess<Ar, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsmem);
+      if (err != cudaSuccess) return err;
+    }
+    k_bt_hess<Ar, false><<<(unsigned)parents, HESS_THREADS, hsmem, s>>>(a);
+  } else {
+    k_bt_hess<Ar, true><<<(unsigned)parents, HESS_THREADS, hsmem, s>>>(a);
   }
-  k_bt_hess<Ar><<<(unsigned)parents, HESS_THREADS, hsmem, s>>>(a);
   if ((err = cudaGetLastError()) != cudaSuccess) return err;
   const long long blocks = (a.n_leaves + LEAF_WARPS - 1) / LEAF_WARPS;
-  if (a.has_gamma) k_bt_leaf<Ar, true><<<(unsigned)blocks, LEAF_WARPS * 32, 0, s>>>(a);
-  else k_bt_leaf<Ar, false><<<(unsigned)blocks, LEAF_WARPS * 32, 0, s>>>(a);
+  if (a.mL <= 32 * LEAF_SMAX) {
+    if (a.has_gamma) k_bt_leaf<Ar, true, LEAF_SMAX><<<(unsigned)blocks, LEAF_WARPS * 32, 0, s>>>(a);
+    else k_bt_leaf<Ar, false, LEAF_SMAX><<<(unsigned)blocks, LEAF_WARPS * 32, 0, s>>>(a);
+  } else {
+    if (a.has_gamma) k_bt_leaf<Ar, true, LEAF_SMAX_BIG><<<(unsigned)blocks, LEAF_WARPS * 32, 0, s>>>(a);
+    else k_bt_leaf<Ar, false, LEAF_SMAX_BIG><<<(unsigned)blocks, LEAF_WARPS * 32, 0, s>>>(a);
+  }
   *launches += 2;
   return cudaGetLastError();
 }
@@ -691,7 +712,9 @@ cudaError_t launch_btree_ar(const BTreeArgs& a, const BTreeStep* steps, int nste
 
 size_t btree_step_smem_bytes(int nbs, int D) { return sizeof(float4) * ((size_t)nbs * D + nbs); }
 size_t btree_hess_smem_bytes(int m) {
-  return sizeof(float4) * ((size_t)m * (m + 3) + (size_t)m + (m + 2) + m + 2 + HESS_THREADS);
+  const size_t vecs = (size_t)m + (m + 2) + m + 2 + HESS_THREADS;
+  if (m > GBSBIN_BT_MAX_HESS) return sizeof(float4) * (vecs + 2 * (size_t)m);   // the block in H
+  return sizeof(float4) * ((size_t)m * (m + 3) + vecs);
 }
 
 cudaError_t launch_points_btree(const BTreeArgs& a, const BTreeStep* steps, int nsteps, bool fp64, int num_sms,

@@ -56,6 +56,19 @@ CASES = [
         np.sqrt(0.7) * synth.haar_unitary(116, np.random.default_rng(908)),
         np.array([0] * 58 + [1] * 58, np.int32), np.array([2, 3], np.int32),
         alpha=0.2 * np.ones((116, 1), complex))),
+    # last groups above 116 rows: the Householder reduction in the Hessenberg buffer through L2,
+    # leaves with six register slots per lane; n = 282 with groups of 144 and 138 rows, and the
+    # largest last group, 192 rows (n = 224)
+    ("n282_last_group_138_rows", lambda: synth.Problem(
+        141, 1, np.random.default_rng(912).uniform(0.2, 0.6, (141, 1)),
+        np.sqrt(0.6) * synth.haar_unitary(141, np.random.default_rng(913)),
+        np.array([0] * 72 + [1] * 69, np.int32), np.array([2, 3], np.int32),
+        alpha=0.2 * np.ones((141, 1), complex))),
+    ("n224_last_group_192_rows", lambda: synth.Problem(
+        112, 1, np.random.default_rng(914).uniform(0.2, 0.6, (112, 1)),
+        np.sqrt(0.6) * synth.haar_unitary(112, np.random.default_rng(915)),
+        np.array([0] * 16 + [1] * 96, np.int32), np.array([3, 2], np.int32),
+        alpha=0.2 * np.ones((112, 1), complex))),
 ]
 
 
@@ -114,7 +127,9 @@ def test_btree_refuses_what_it_cannot_do(cuda_lib):
     with pytest.raises(gb.GbsbinError) as e:
         gb.Plan(one_group, tile_override=14)
     assert e.value.status == 8
-    big_last = _problem(909, 120, 1, 2, [2, 2])              # last group of 120 rows > 116
+    big_last = synth.Problem(                                # last group of 194 rows > 192
+        100, 1, np.full((100, 1), 0.3), np.sqrt(0.7) * synth.haar_unitary(100, np.random.default_rng(909)),
+        np.array([0] * 3 + [1] * 97, np.int32), np.array([2, 2], np.int32))
     with pytest.raises(gb.GbsbinError) as e:
         gb.Plan(big_last, tile_override=13)
     assert e.value.status == 8
@@ -157,3 +172,30 @@ def test_default_choice_for_small_matrices_with_large_groups(cuda_lib):
             st, d = p.diagnostics()
         assert st == 0 and d["kernel_name"] == name, d["kernel_name"]
         assert np.abs(P - oracle.binned(prob)["P"]).max() <= 1e-10
+
+
+def test_default_choice_above_the_shared_memory_householder(cuda_lib):
+    # n = 282 with groups of 144 and 138 rows on a 21 x 21 grid (the shape of the 256-problem
+    # batch's largest per-point problem): the large-matrix tree is now the default in both
+    # arithmetics; log q at sampled evaluated points against the oracle one by one, the table's
+    # total and the two arithmetics' tables against each other
+    gb = cuda_lib
+    prob = synth.Problem(
+        141, 1, np.random.default_rng(916).uniform(0.3, 0.9, (141, 1)),
+        np.sqrt(0.6) * synth.haar_unitary(141, np.random.default_rng(917)),
+        np.array([0] * 72 + [1] * 69, np.int32), np.array([20, 20], np.int32),
+        alpha=0.2 * np.ones((141, 1), complex))
+    XA, gamma, labels = oracle.plan(prob)
+    dig = gb.evaluated_point_digits(prob.cutoff)
+    pick = np.concatenate([[0, 1, len(dig) - 1], np.random.default_rng(918).choice(len(dig), 9, replace=False)])
+    ref, _, _ = oracle.logq_points(XA, gamma, labels, prob.radix, dig[pick])
+    tables = []
+    for precision, name in ((1, "btree_df32"), (0, "btree_fp64")):
+        with gb.Plan(prob, precision=precision) as p:
+            tables.append(p.table().cpu().numpy())
+            st, d = p.diagnostics()
+            lq, mp = gb.gbsbin_read_points(p.handle, d["n_evaluated"])
+        assert st == 0 and d["kernel_name"] == name, d["kernel_name"]
+        assert d["n_bad_points"] == 0 and abs(tables[-1].sum() - 1.0) < 1e-10
+        assert np.abs(lq[pick] - ref).max() < LOGQ_TOL
+    assert np.abs(tables[0] - tables[1]).max() < 1e-10
