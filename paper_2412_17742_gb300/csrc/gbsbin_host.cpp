@@ -6,6 +6,7 @@
 #include <cmath>
 #include <complex>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -1555,7 +1556,7 @@ int gbsbin_execute(gbsbin_plan* P, double* P_out, void* stream) {
                                                                                              : GBSBIN_ERR_CUDA;
   }
   cudaError_t e = P->kernel == GBSBIN_KERNEL_WARP_FP32R  ? launch_points_warp(a, P->num_sms, s)
-                  : is_hess(P->kernel) ? launch_points_hess(a, PointBatch{}, P->num_sms, s, P->kernel == GBSBIN_KERNEL_HESS_DF32)
+                  : is_hess(P->kernel) ? launch_points_hess(a, PointBatch{}, 0, P->num_sms, s, P->kernel == GBSBIN_KERNEL_HESS_DF32)
                   : is_blk(P->kernel) ? launch_points_blk(a, PointBatch{}, 0, P->num_sms, s, P->kernel == GBSBIN_KERNEL_BLK_TC_FP32R)
                                                          : launch_points(a, P->kernel, P->num_sms, s);
   if (e != cudaSuccess) return GBSBIN_ERR_CUDA;
@@ -2733,6 +2734,17 @@ void batch_free(gbsbin_batch* B) {
   delete B;
 }
 
+// Side streams of a batch's tree problems: 8, or the environment variable
+// GBSBIN_BATCH_STREAMS (1 .. 64).
+int batch_side_streams() {
+  static const int n = [] {
+    int v = 8;
+    if (const char* e = std::getenv("GBSBIN_BATCH_STREAMS")) v = std::atoi(e);
+    return std::max(1, std::min(v, 64));
+  }();
+  return n;
+}
+
 int batch_launch(gbsbin_batch* B, double* const* P_out, cudaStream_t s) {
   for (size_t i = 0; i < B->plans.size(); ++i)
     if (!P_out[i]) return GBSBIN_ERR_ARG;
@@ -2753,7 +2765,7 @@ int batch_launch(gbsbin_batch* B, double* const* P_out, cudaStream_t s) {
     if (cudaMemsetAsync(B->d_queue + c, 0, sizeof(unsigned long long), s) != cudaSuccess) return GBSBIN_ERR_CUDA;
     PointBatch pb{B->d_probs, C.d_jobs, (long long)C.jobs.size(), B->d_queue + c};
     cudaError_t e = C.kernel == GBSBIN_KERNEL_WARP_FP32R  ? launch_points_warp_batch(pb, C.np, B->num_sms, s)
-                    : is_hess(C.kernel) ? launch_points_hess(PointArgs{}, pb, B->num_sms, s, C.kernel == GBSBIN_KERNEL_HESS_DF32)
+                    : is_hess(C.kernel) ? launch_points_hess(PointArgs{}, pb, C.np, B->num_sms, s, C.kernel == GBSBIN_KERNEL_HESS_DF32)
                     : is_blk(C.kernel) ? launch_points_blk(PointArgs{}, pb, C.smem, B->num_sms, s, C.kernel == GBSBIN_KERNEL_BLK_TC_FP32R)
                                                           : launch_points_batch(pb, C.kernel, C.threads, C.smem, B->num_sms, s);
     if (e != cudaSuccess) return GBSBIN_ERR_CUDA;
@@ -2859,9 +2871,11 @@ int gbsbin_batch_create(const gbsbin_problem* probs, int nprob, const gbsbin_opt
                         : is_blk(P->kernel) ? 256
                                                                : points_threads(P->kernel, P->n);
     // warp kernel: padded size class; blocked kernel: problems whose shared memory allows
-    // two CTAs per SM run apart from the larger ones (a class launches with its largest need)
+    // two CTAs per SM run apart from the larger ones (a class launches with its largest need);
+    // Hessenberg kernels: the row slots per lane of the instantiation
     const int np = P->kernel == GBSBIN_KERNEL_WARP_FP32R ? (P->n <= 8 ? 8 : P->n <= 16 ? 16 : 32)
                    : is_blk(P->kernel) ? points_blk_ctas_per_sm(P->n)
+                   : is_hess(P->kernel) ? hess_slots(P->n)
                                                           : 0;
     auto key = std::make_tuple(P->kernel, threads, np);
     if (!class_of.count(key)) {
@@ -2917,7 +2931,7 @@ int gbsbin_batch_create(const gbsbin_problem* probs, int nprob, const gbsbin_opt
     batch_free(B);
     return GBSBIN_ERR_NOMEM;
   }
-  // tree problems, largest per-point work first, over up to eight side streams
+  // tree problems, largest per-point work first, over up to batch_side_streams() side streams
   std::vector<std::pair<double, int>> trees;
   for (int i = 0; i < nprob; ++i)
     if (B->own[i]) {
@@ -2926,7 +2940,7 @@ int gbsbin_batch_create(const gbsbin_problem* probs, int nprob, const gbsbin_opt
     }
   std::sort(trees.begin(), trees.end());
   for (auto& t : trees) B->tree_order.push_back(t.second);
-  const int ns = (int)std::min<size_t>(8, trees.size());
+  const int ns = (int)std::min<size_t>((size_t)batch_side_streams(), trees.size());
   B->side.assign(ns, nullptr);
   B->ev_join.assign(ns, nullptr);
   bool ok = ns == 0 || cudaEventCreateWithFlags(&B->ev_fork, cudaEventDisableTiming) == cudaSuccess;

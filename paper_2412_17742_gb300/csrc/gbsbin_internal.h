@@ -274,7 +274,11 @@ cudaError_t launch_points_blk(const PointArgs& a, const PointBatch& batch, size_
                               cudaStream_t s, bool tensor_cores);
 // One-group (L = 1) undisplaced kernel (gbsbin_points_hess.cu): warp per point, four
 // points per CTA; batch jobs are groups of four consecutive points of one problem.
-cudaError_t launch_points_hess(const PointArgs& a, const PointBatch& batch, int num_sms, cudaStream_t s, bool df);
+// slots: row slots per lane of the instantiation (hess_slots(n) for the largest n it serves;
+// 0: from a.n)
+cudaError_t launch_points_hess(const PointArgs& a, const PointBatch& batch, int slots, int num_sms, cudaStream_t s,
+                               bool df);
+int hess_slots(int n);
 size_t points_smem_bytes(int kernel, int n, int P, int L);
 size_t points_matrix_bytes(int kernel, int n, int P);
 int points_per_cta(int kernel, int n, int L);
