@@ -28,6 +28,8 @@
 // product renormalised every four pivots to stay in FP32's exponent range).
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include <type_traits>
 
 #include "gbsbin_device.cuh"
@@ -234,9 +236,145 @@ cudaError_t launch_hess_slots(const PointArgs& a, const PointBatch& batch, int s
   }
 }
 
+// A CTA per point, for grids with too few points to fill the GPU with a warp each (the
+// warp kernel then runs one warp per SM at most and waits on every step's L2 reads): thread t
+// holds entries j = t + HC_T s of the current pivot row (and of the running sums s_j).  Step i
+// reads the pivot's broadcast (q_i, l_i = H[i+1][i] / q_i, z_i = (a_i - s_i) / q_i), updates
+// the thread's entries j > i (s_j += z_i r_j, then r_j = N[i+1][j] - l_i r_j), and the owner of
+// entry i + 1 forms the next broadcast, with H[i+2][i+1] and a_{i+1} loaded at the start of the
+// step; one barrier per step, the broadcast double-buffered.  Row i + 2 is loaded during step
+// i.  Thread 0 keeps the scalar recurrences (the pivot product and its windings, y, z^T y).
+constexpr int HC_T = 128;
+constexpr int HC_S = GBSBIN_MAX_N / HC_T;
+
+template <class Ar, bool DISP>
+__global__ void __launch_bounds__(HC_T) k_points_hess_cta(PointArgs a) {
+  using E = typename Ar::E;
+  __shared__ E bc[2][3];                        // q, l, z of the step (by parity)
+  const int n = a.n, t = threadIdx.x;
+  const E* H = reinterpret_cast<const E*>(a.H);
+  const E* av = H + (size_t)n * n;
+  const E* cv = av + n;
+  constexpr bool f64 = std::is_same<Ar, ArF64>::value;
+  using MinT = typename std::conditional<f64, double, float>::type;
+  for (long long e = blockIdx.x; e < a.grid.n_eval; e += gridDim.x) {
+    const double2 wd = grid_root(a.tw, a.grid, 0, point_digit(e, a.grid, 0));
+    const E sg = Ar::from(make_double2(wd.x, -wd.y));   // conj(w)
+    const E mw = Ar::from(make_double2(-wd.x, -wd.y));
+    E r[HC_S], nx[HC_S], sacc[DISP ? HC_S : 1];
+#pragma unroll
+    for (int s = 0; s < HC_S; ++s) {
+      const int j = t + HC_T * s;
+      E v = Ar::zero(), v1 = Ar::zero();
+      if (j < n) {
+        v = H[j];
+        if (j == 0) v = Ar::add(v, Ar::neg(sg));
+        if (n > 1 && j >= 1) v1 = H[(size_t)n + j];
+      }
+      r[s] = v;
+      nx[s] = v1;
+      if constexpr (DISP) sacc[s] = Ar::zero();
+    }
+    if (t == 0) {                               // step 0's broadcast
+      const E iq = Ar::recip(r[0]);
+      bc[0][0] = r[0];
+      bc[0][1] = n > 1 ? Ar::mul(H[n], iq) : Ar::zero();
+      bc[0][2] = DISP ? Ar::mul(av[0], iq) : Ar::zero();
+    }
+    __syncthreads();
+    E y = DISP ? cv[0] : Ar::zero(), zy = Ar::zero(), prod = Ar::one();
+    int e2 = 0, wind = 0;
+    MinT mn = f64 ? (MinT)1.0e300 : (MinT)3.0e38f;
+    bool bad = false;
+    for (int i = 0; i < n; ++i) {
+      const int b = i & 1;
+      const E q = bc[b][0], l = bc[b][1], z = bc[b][2];
+      const int o = (i + 1) % HC_T, os = (i + 1) / HC_T;
+      E hs = Ar::zero(), an = Ar::zero();
+      if (t == o && i + 2 < n) hs = H[(size_t)(i + 2) * n + i + 1];
+      if (DISP && t == o && i + 1 < n) an = av[i + 1];
+      if (t == 0) {                             // the scalar recurrences
+        const E p = Ar::mul(mw, q);
+        const float pr = Ar::re(p), pi = Ar::im(p);
+        if constexpr (f64) mn = fmin(mn, (double)Ar::to(p).x);
+        else mn = fminf(mn, pr);
+        if (!(pr == pr) || !(pi == pi)) bad = true;
+        const float x0 = Ar::re(prod), y0 = Ar::im(prod);
+        prod = Ar::mul(prod, p);
+        const float x1 = Ar::re(prod), y1 = Ar::im(prod);
+        if (x0 < 0.f && x1 < 0.f) wind += (y0 >= 0.f && y1 < 0.f) ? 1 : (y0 < 0.f && y1 >= 0.f) ? -1 : 0;
+        if ((i & 3) == 3) e2 += Ar::normalise(prod);
+        if constexpr (DISP) {
+          zy = Ar::fma(z, y, zy);
+          if (i + 1 < n) y = Ar::fms(cv[i + 1], l, y);   // y_{i+1} = c_{i+1} - l_i y_i
+        }
+      }
+      if (i == n - 1) break;
+      // row i + 2, for the next step
+      E nx2[HC_S];
+      const E* hrow2 = H + (size_t)(i + 2) * n;
+#pragma unroll
+      for (int s = 0; s < HC_S; ++s) {
+        const int j = t + HC_T * s;
+        nx2[s] = (i + 2 < n && j > i + 1 && j < n) ? hrow2[j] : Ar::zero();
+      }
+#pragma unroll
+      for (int s = 0; s < HC_S; ++s) {
+        const int j = t + HC_T * s;
+        if (j > i && j < n) {
+          if constexpr (DISP) sacc[s] = Ar::fma(z, r[s], sacc[s]);
+          E h = nx[s];
+          if (j == i + 1) h = Ar::add(h, Ar::neg(sg));
+          r[s] = Ar::fms(h, l, r[s]);
+        }
+      }
+      if (t == o) {                             // the next step's broadcast
+        E q1 = r[0], s1 = Ar::zero();
+#pragma unroll
+        for (int s = 0; s < HC_S; ++s)
+          if (s == os) {
+            q1 = r[s];
+            if constexpr (DISP) s1 = sacc[s];
+          }
+        const E iq = Ar::recip(q1);
+        bc[b ^ 1][0] = q1;
+        bc[b ^ 1][1] = Ar::mul(hs, iq);
+        bc[b ^ 1][2] = DISP ? Ar::mul(Ar::add(an, Ar::neg(s1)), iq) : Ar::zero();
+      }
+#pragma unroll
+      for (int s = 0; s < HC_S; ++s) nx[s] = nx2[s];
+      __syncthreads();
+    }
+    if (t == 0) {
+      e2 += Ar::normalise(prod);
+      const double LN2 = 0.693147180559945309417232121458;
+      const double TWO_PI = 6.28318530717958647692;
+      const double2 pd = Ar::to(prod), zd = Ar::to(zy);
+      double* f = a.ldfin + 6 * e;
+      f[0] = pd.x;
+      f[1] = pd.y;
+      f[2] = (double)atan2f(Ar::im(prod), Ar::re(prod)) + TWO_PI * (double)wind;
+      f[3] = -0.5 * (double)e2 * LN2 - 0.5 * zd.x;
+      f[4] = -0.5 * zd.y;
+      f[5] = 0.0;
+      a.minpiv[e] = bad ? -1.0e300 : (double)mn;
+    }
+    __syncthreads();                            // the broadcast buffer is reused by the next point
+  }
+}
+
+template <class Ar>
+cudaError_t launch_hess_cta(const PointArgs& a, int num_sms, cudaStream_t s) {
+  const long long grid = std::min<long long>(a.grid.n_eval, 4LL * num_sms);
+  if (a.has_gamma) k_points_hess_cta<Ar, true><<<(unsigned)grid, HC_T, 0, s>>>(a);
+  else k_points_hess_cta<Ar, false><<<(unsigned)grid, HC_T, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
 template <class Ar>
 cudaError_t launch_hess_ar(const PointArgs& a, const PointBatch& batch, int slots, int num_sms, cudaStream_t s) {
   if (batch.probs) return launch_hess_slots<Ar, 2>(a, batch, slots, num_sms, s);
+  if (a.n >= 128 && a.grid.n_eval < 4LL * num_sms) return launch_hess_cta<Ar>(a, num_sms, s);
   return a.has_gamma ? launch_hess_slots<Ar, 1>(a, batch, slots, num_sms, s)
                      : launch_hess_slots<Ar, 0>(a, batch, slots, num_sms, s);
 }

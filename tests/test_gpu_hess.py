@@ -113,3 +113,28 @@ def test_hessenberg_table_matches_power_series(cuda_lib):
     assert st == 0 and d["kernel_name"] == "hess_fp64"
     ref = gb.gbsbin_total_photon_series(prob, 40)
     assert np.abs(P - ref).max() < 1e-12
+
+
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "fp32pairs"])
+@pytest.mark.parametrize("M,cut,disp", [(80, 1400, True), (200, 1300, False)])
+def test_one_group_large_grids(cuda_lib, M, cut, disp, precision):
+    # grids with enough points for a warp per point (n = 160 and n = 400, 700 and 651 evaluated
+    # points: the 8- and 12-slot instantiations); the small-grid cases above run a CTA per
+    # point from n = 128 on.  log q at sampled points against the oracle one by one, the
+    # table's total and sign, and the two arithmetics' tables against each other
+    gb = cuda_lib
+    prob = synth.random_problem(np.random.default_rng(530 + M), M, 1, 1, cut, displaced=disp, r_range=(0.2, 0.7))
+    with gb.Plan(prob, precision=precision) as p:
+        P = p.table().cpu().numpy()
+        st, d = p.diagnostics()
+        lq, mp = gb.gbsbin_read_points(p.handle, d["n_evaluated"])
+    assert st == 0 and d["kernel_name"] == ("hess_df32" if precision else "hess_fp64") and d["n_bad_points"] == 0
+    assert abs(P.sum() - 1.0) < 1e-10 and P.min() > -1e-10
+    XA, gamma, labels = oracle.plan(prob)
+    dig = gb.evaluated_point_digits(prob.cutoff)
+    pick = np.concatenate([[0, 1, len(dig) - 1], np.random.default_rng(M).choice(len(dig), 9, replace=False)])
+    ref, _, _ = oracle.logq_points(XA, gamma, labels, prob.radix, dig[pick])
+    assert np.abs(lq[pick] - ref).max() < 1e-9
+    with gb.Plan(prob, precision=1 - precision) as p:
+        Q = p.table().cpu().numpy()
+    assert np.abs(P - Q).max() < 1e-10
