@@ -167,7 +167,8 @@ def test_large_tree_validation(gb, btree):
     # the large-matrix tree's host-side refusals (before any device call)
     one_group = synth.random_problem(np.random.default_rng(7), 4, 1, 1, 3)
     assert _status(gb, one_group, tile_override=btree) == 8              # needs L >= 2
-    big_last = synth.random_problem(np.random.default_rng(9), 120, 1, 2, 2)   # last group 120 rows > 116
+    big_last = synth.random_problem(np.random.default_rng(9), 100, 1, 2, 2)   # last group 194 rows > 192
+    big_last.bin_of_mode = np.array([0] * 3 + [1] * 97, np.int32)
     assert _status(gb, big_last, tile_override=btree) == 8
 
 
