@@ -243,7 +243,8 @@ cudaError_t launch_hess_slots(const PointArgs& a, const PointBatch& batch, int s
 // the thread's entries j > i (s_j += z_i r_j, then r_j = N[i+1][j] - l_i r_j), and the owner of
 // entry i + 1 forms the next broadcast, with H[i+2][i+1] and a_{i+1} loaded at the start of the
 // step; one barrier per step, the broadcast double-buffered.  Row i + 2 is loaded during step
-// i.  Thread 0 keeps the scalar recurrences (the pivot product and its windings, y, z^T y).
+// i into the register set the step after it reads (two sets alternating).  Thread 0 keeps the
+// scalar recurrences (the pivot product and its windings, y, z^T y).
 constexpr int HC_T = 128;
 constexpr int HC_S = GBSBIN_MAX_N / HC_T;
 
@@ -286,7 +287,9 @@ __global__ void __launch_bounds__(HC_T) k_points_hess_cta(PointArgs a) {
     int e2 = 0, wind = 0;
     MinT mn = f64 ? (MinT)1.0e300 : (MinT)3.0e38f;
     bool bad = false;
-    for (int i = 0; i < n; ++i) {
+    // step i: row i + 1 in cur, row i + 2 loaded into nxt (two register sets alternating, so a
+    // row's loads are waited for a whole step later); returns true after the last pivot
+    auto step = [&](int i, E (&cur)[HC_S], E (&nxt)[HC_S]) -> bool {
       const int b = i & 1;
       const E q = bc[b][0], l = bc[b][1], z = bc[b][2];
       const int o = (i + 1) % HC_T, os = (i + 1) / HC_T;
@@ -309,21 +312,20 @@ __global__ void __launch_bounds__(HC_T) k_points_hess_cta(PointArgs a) {
           if (i + 1 < n) y = Ar::fms(cv[i + 1], l, y);   // y_{i+1} = c_{i+1} - l_i y_i
         }
       }
-      if (i == n - 1) break;
+      if (i == n - 1) return true;
       // row i + 2, for the next step
-      E nx2[HC_S];
       const E* hrow2 = H + (size_t)(i + 2) * n;
 #pragma unroll
       for (int s = 0; s < HC_S; ++s) {
         const int j = t + HC_T * s;
-        nx2[s] = (i + 2 < n && j > i + 1 && j < n) ? hrow2[j] : Ar::zero();
+        nxt[s] = (i + 2 < n && j > i + 1 && j < n) ? hrow2[j] : Ar::zero();
       }
 #pragma unroll
       for (int s = 0; s < HC_S; ++s) {
         const int j = t + HC_T * s;
         if (j > i && j < n) {
           if constexpr (DISP) sacc[s] = Ar::fma(z, r[s], sacc[s]);
-          E h = nx[s];
+          E h = cur[s];
           if (j == i + 1) h = Ar::add(h, Ar::neg(sg));
           r[s] = Ar::fms(h, l, r[s]);
         }
@@ -341,9 +343,13 @@ __global__ void __launch_bounds__(HC_T) k_points_hess_cta(PointArgs a) {
         bc[b ^ 1][1] = Ar::mul(hs, iq);
         bc[b ^ 1][2] = DISP ? Ar::mul(Ar::add(an, Ar::neg(s1)), iq) : Ar::zero();
       }
-#pragma unroll
-      for (int s = 0; s < HC_S; ++s) nx[s] = nx2[s];
       __syncthreads();
+      return false;
+    };
+    E nxb[HC_S];
+    for (int i = 0; i < n; i += 2) {
+      if (step(i, nx, nxb)) break;
+      if (step(i + 1, nxb, nx)) break;
     }
     if (t == 0) {
       e2 += Ar::normalise(prod);
