@@ -37,6 +37,9 @@ CASES = [
     ("n160_l2_uneven", lambda: _problem(1102, 80, 1, 2, [4, 5], bins=[0] * 30 + [1] * 50, displaced=True)),
     # n = 200, two undisplaced groups of 100, one parent per first-axis root
     ("n200_l2", lambda: _problem(1103, 100, 1, 2, [6, 6])),
+    # n = 240, a last group of 140 rows: the forward's Householder reduction through L2
+    ("n240_last_group_140_rows", lambda: _problem(1104, 120, 1, 2, [5, 9], bins=[0] * 50 + [1] * 70,
+                                                  displaced=True, r_range=(0.2, 0.6))),
 ]
 
 
