@@ -118,3 +118,17 @@ def test_largest_matrix(gb):
     assert np.abs(k2 - k2.T).max() < 1e-12 * np.abs(k2).max()
     assert np.abs(k3 - k3.transpose(2, 0, 1)).max() < 1e-12 * np.abs(k3).max()
     assert np.all(np.linalg.eigvalsh(k2) > 0)
+
+
+def test_sixteen_groups_match_host(gb):
+    # the largest group count (L = 16, one port per group, n = 32): every coefficient launch and
+    # the chain rule at their largest grids, against the host evaluators
+    rng = np.random.default_rng(4343)
+    prob = synth.random_problem(rng, 16, 1, 16, 2, displaced=True, r_range=(0.3, 0.8))
+    prob.bin_of_mode = np.arange(16, dtype=np.int32)
+    outs = gb.gbsbin_cumulants_device(prob)
+    mean, cov = gb.gbsbin_moments(prob)
+    host = [mean, cov, gb.gbsbin_cumulants3(prob), gb.gbsbin_cumulants4(prob)]
+    for r, (dev, ref) in enumerate(zip(outs, host), start=1):
+        assert dev.shape == (16,) * r
+        assert np.abs(dev - ref).max() < 1e-11 * np.abs(ref).max(), (r, np.abs(dev - ref).max())
