@@ -32,7 +32,6 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
-#include <vector>
 
 #include "gbsbin_df.cuh"
 #include "gbsbin_moments.h"
