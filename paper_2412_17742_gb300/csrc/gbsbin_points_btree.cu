@@ -469,7 +469,7 @@ __device__ __forceinline__ void write_record(const BTreeArgs& a, long long e, do
 // row (and of the running sums s_j); row i + 1 of H, the subdiagonal entry and b_{i+1} are read
 // from L2 one step ahead of their use.
 template <class Ar, bool DISP, int SMX>
-__global__ void __launch_bounds__(LEAF_WARPS * 32, SMX <= LEAF_SMAX ? 4 : 2) k_bt_leaf(BTreeArgs a) {
+__global__ void __launch_bounds__(LEAF_WARPS * 32, SMX <= LEAF_SMAX ? (DISP ? 3 : 4) : 2) k_bt_leaf(BTreeArgs a) {
   using E = typename Ar::E;
   const int lane = threadIdx.x & 31;
   const long long leaf = (long long)blockIdx.x * LEAF_WARPS + (threadIdx.x >> 5);
