@@ -123,3 +123,35 @@ def test_batch_problems_on_trees(cuda_lib):
             s.synchronize()
             for t, r in zip(b.outputs, ref):
                 assert torch.equal(t, r)
+
+
+def test_full_batched_workload_whole_tables(cuda_lib):
+    # the 256-problem workload in both arithmetics: whole tables against the oracle element by
+    # element (1e-10) for the 48 problems cheapest for the oracle and, in every kernel class the
+    # batch uses, that class's cheapest problem (the trees, the one-group Hessenberg kernels and
+    # the per-point kernels); log q at sampled points of 24 further problems one by one
+    gb = cuda_lib
+    probs = synth.batch_config()
+    cost = sorted((p.n_points * (2 * p.M * p.K) ** 3, i) for i, p in enumerate(probs))
+    for precision in (1, 0):
+        with gb.Batch(probs, precision=precision) as b:
+            outs = [t.cpu().numpy() for t in b.execute()]
+            kinds = [b.diagnostics(i)[1]["kernel_name"] for i in range(len(probs))]
+            pick = {i for _, i in cost[:48]}
+            for kind in set(kinds):
+                pick.add(min((c, i) for c, i in cost if kinds[i] == kind)[1])
+            for i in sorted(pick):
+                err = float(np.abs(outs[i] - oracle.binned(probs[i])["P"]).max())
+                assert err <= 1e-10, (i, kinds[i], precision, err)
+            rng = np.random.default_rng(704 + precision)
+            rest = [i for i in range(len(probs)) if i not in pick]
+            for i in rng.choice(rest, 24, replace=False):
+                p = probs[i]
+                st, d = b.diagnostics(i)
+                lq, _ = b.read_points(i, d["n_evaluated"])
+                dig = gb.evaluated_point_digits(p.cutoff)
+                sel = np.concatenate([[0, len(dig) - 1], rng.choice(len(dig), 4, replace=False)])
+                XA, gamma, labels = oracle.plan(p)
+                ref, _, _ = oracle.logq_points(XA, gamma, labels, p.radix, dig[sel])
+                assert np.abs(lq[sel] - ref).max() < 1e-9, (i, kinds[i], precision)
+        assert len(set(kinds)) >= 4, set(kinds)
