@@ -116,11 +116,11 @@ def test_hessenberg_table_matches_power_series(cuda_lib):
 
 
 @pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "fp32pairs"])
-@pytest.mark.parametrize("M,cut,disp", [(80, 1400, True), (200, 1300, False)])
+@pytest.mark.parametrize("M,cut,disp", [(80, 1400, True), (150, 1300, True), (200, 1300, False)])
 def test_one_group_large_grids(cuda_lib, M, cut, disp, precision):
-    # grids with enough points for a warp per point (n = 160 and n = 400, 700 and 651 evaluated
-    # points: the 8- and 12-slot instantiations); the small-grid cases above run a CTA per
-    # point from n = 128 on.  log q at sampled points against the oracle one by one, the
+    # grids with enough points for a warp per point (n = 160, 300 and 400 with 701, 651 and 651
+    # evaluated points: the 8-, 12- and 16-slot instantiations); the small-grid cases above run a
+    # CTA per point from n = 128 on.  log q at sampled points against the oracle one by one, the
     # table's total and sign, and the two arithmetics' tables against each other
     gb = cuda_lib
     prob = synth.random_problem(np.random.default_rng(530 + M), M, 1, 1, cut, displaced=disp, r_range=(0.2, 0.7))
