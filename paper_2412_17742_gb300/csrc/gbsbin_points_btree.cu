@@ -34,7 +34,8 @@
 //
 // Leaves.  The last group's block is I - w A_L for every root w of the last axis, so one
 // Householder reduction A_L = Q H Q^H per leaf parent (a CTA per node, the matrix in shared
-// memory) serves all of them: det(I - w A_L) = det(I - w H), and with N = H - conj(w) I =
+// memory, or for last groups above GBSBIN_BT_MAX_HESS rows in the node's slot of the Hessenberg
+// buffer through L2) serves all of them: det(I - w A_L) = det(I - w H), and with N = H - conj(w) I =
 // -conj(w) (I - w H) the pivots of I - w H are -w times those of N.  The exponent's leaf term
 // u^T (I - w A_L)^-1 w c = -a^T N^-1 b with a = Q^T u, b = Q^H c (reflectors applied to c and
 // to conj(u) as extra columns).  A warp per evaluated point runs the O(m^2) unpivoted
