@@ -608,6 +608,13 @@ def _extra_moments(gb, torch, steps):
         call_ms = (time.perf_counter() - t0) / k * 1e3
         entry = {"n": 2 * prob.M * prob.K, "groups": int(prob.L), "device_ms": float(np.median(dev_ms)),
                  "call_ms": call_ms, "precision": "fp64"}
+        gb.gbsbin_cumulants_device(prob, precision=gb.GBSBIN_FP32_REFINE)
+        pair_ms = [gb.gbsbin_cumulants_device(prob, precision=gb.GBSBIN_FP32_REFINE, with_time=True)[1]
+                   for _ in range(k)]
+        pairs = gb.gbsbin_cumulants_device(prob, precision=gb.GBSBIN_FP32_REFINE)
+        entry["fp32_pairs"] = {"device_ms": float(np.median(pair_ms)),
+                               "max_rel_diff_vs_fp64": max(float(np.abs(a - b).max() / np.abs(b).max())
+                                                           for a, b in zip(pairs, outs))}
         n, L = entry["n"], entry["groups"]
         flops = 8.0 * (n * n * (n + 32) / 2.0 + L * L * n * n / 2.0)
         entry["roofline"] = {"bound": "alu", "achieved": flops / (entry["device_ms"] * 1e-3) / 1e12, "peak": peak64,

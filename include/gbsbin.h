@@ -429,7 +429,9 @@ int gbsbin_cumulants4(const gbsbin_problem* p, double* k4);
 
 /*
  * The cumulants of gbsbin_moments, gbsbin_cumulants3 and gbsbin_cumulants4 (Sec. VI,
- * coarse-grained moments and cumulants) computed on the GPU, FP64 throughout.  With
+ * coarse-grained moments and cumulants) computed on the GPU.  precision GBSBIN_FP64: every
+ * device step in FP64; GBSBIN_FP32_REFINE: the products and block sums in pairs of FP32 on the
+ * FMA pipe (~46 bits), the chain rule in FP64.  With
  * XA = I - Sigma^{-1}, R = (I - XA)^{-1} = Sigma, so W = XA R = Sigma^(1) (Hermitian),
  * u = R X gamma = X gamma + W X gamma and v = R^T gamma = gamma + W^T gamma: no inverse is
  * formed.  The host builds and validates the state as for gbsbin_plan_create and sorts the rows
@@ -450,10 +452,10 @@ int gbsbin_cumulants4(const gbsbin_problem* p, double* k4);
  * multiply-adds for the Y_b and ~L^2 n^2/2 for the C_4 traces; device memory up to
  * (1 + 2 L) n^2 x 16 bytes, allocated and freed per call.  Synchronous on `stream`.
  * *kernel_ms (may be NULL) receives the device time of the launches by CUDA events (uploads and
- * the final copies excluded).  Errors: ERR_ARG (p NULL or every output NULL), ERR_UNSUPPORTED
- * (L > 16), then as gbsbin_moments, ERR_NOMEM, ERR_CUDA.
+ * the final copies excluded).  Errors: ERR_ARG (p NULL, every output NULL, or another
+ * precision), ERR_UNSUPPORTED (L > 16), then as gbsbin_moments, ERR_NOMEM, ERR_CUDA.
  */
-int gbsbin_cumulants_device(const gbsbin_problem* p, double* mean, double* cov, double* k3, double* k4,
+int gbsbin_cumulants_device(const gbsbin_problem* p, int precision, double* mean, double* cov, double* k3, double* k4,
                             double* kernel_ms, void* stream);
 
 /*

@@ -133,7 +133,7 @@ def load():
     lib.gbsbin_prob_distinguishable.restype = ctypes.c_int
     lib.gbsbin_prob_distinguishable_device.argtypes = [ctypes.POINTER(gbsbin_problem), _ip, vp, vp, vp]
     lib.gbsbin_prob_distinguishable_device.restype = ctypes.c_int
-    lib.gbsbin_cumulants_device.argtypes = [ctypes.POINTER(gbsbin_problem), vp, vp, vp, vp, vp, vp]
+    lib.gbsbin_cumulants_device.argtypes = [ctypes.POINTER(gbsbin_problem), ctypes.c_int, vp, vp, vp, vp, vp, vp]
     lib.gbsbin_cumulants_device.restype = ctypes.c_int
     lib.gbsbin_read_points.argtypes = [vp, vp, vp, vp]
     lib.gbsbin_table_from_logq_noalloc.argtypes = [ctypes.c_int, _ip, ctypes.c_int, vp, vp, vp]
@@ -409,10 +409,11 @@ def gbsbin_cumulants4(prob):
     return k4
 
 
-def gbsbin_cumulants_device(prob, order=4, stream=None, with_time=False):
-    """Cumulant tensors of orders 1..order of the binned counts on the GPU (FP64): the list
-    [mean (L,), cov (L, L), k3 (L, L, L), k4 (L, L, L, L)][:order]; with_time also returns the
-    device time of the launches in ms."""
+def gbsbin_cumulants_device(prob, order=4, precision=GBSBIN_FP64, stream=None, with_time=False):
+    """Cumulant tensors of orders 1..order of the binned counts on the GPU (FP64, or the
+    products in pairs of FP32 with GBSBIN_FP32_REFINE): the list [mean (L,), cov (L, L),
+    k3 (L, L, L), k4 (L, L, L, L)][:order]; with_time also returns the device time of the
+    launches in ms."""
     if not 1 <= int(order) <= 4:
         raise ValueError("order must be 1..4")
     args = ProblemArgs(prob)
@@ -420,7 +421,8 @@ def gbsbin_cumulants_device(prob, order=4, stream=None, with_time=False):
     outs = [np.zeros((L,) * r, dtype=np.float64) for r in range(1, int(order) + 1)]
     ptrs = [o.ctypes.data_as(ctypes.c_void_p) for o in outs] + [None] * (4 - len(outs))
     ms = ctypes.c_double()
-    _check(load().gbsbin_cumulants_device(ctypes.byref(args.c), *ptrs, ctypes.byref(ms), _stream_handle(stream)),
+    _check(load().gbsbin_cumulants_device(ctypes.byref(args.c), int(precision), *ptrs, ctypes.byref(ms),
+                                          _stream_handle(stream)),
            "gbsbin_cumulants_device")
     return (outs, ms.value) if with_time else outs
 

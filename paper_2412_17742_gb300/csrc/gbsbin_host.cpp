@@ -2165,9 +2165,9 @@ int gbsbin_cumulants4(const gbsbin_problem* p, double* k4) {
 // rows sorted by group, then gbsbin_moments.cu's launches.  With XA = I - Sigma^{-1} (Sigma =
 // I + Sigma^(1)), R = (I - XA)^{-1} = Sigma and W = XA R = Sigma^(1): the device starts from
 // Sigma^(1), made exactly Hermitian ((S + S^H) / 2; the state was validated Hermitian).
-int gbsbin_cumulants_device(const gbsbin_problem* p, double* mean, double* cov, double* k3, double* k4,
+int gbsbin_cumulants_device(const gbsbin_problem* p, int precision, double* mean, double* cov, double* k3, double* k4,
                             double* kernel_ms, void* stream) {
-  if (!p) return GBSBIN_ERR_ARG;
+  if (!p || (precision != GBSBIN_FP64 && precision != GBSBIN_FP32_REFINE)) return GBSBIN_ERR_ARG;
   const int order = k4 ? 4 : k3 ? 3 : cov ? 2 : mean ? 1 : 0;
   if (order == 0) return GBSBIN_ERR_ARG;
   gbsbin_options o;
@@ -2197,7 +2197,7 @@ int gbsbin_cumulants_device(const gbsbin_problem* p, double* mean, double* cov, 
   float ms = 0.f;
   st = cumulants_device(n, L, goff.data(), reinterpret_cast<const double*>(Wp.data()),
                         reinterpret_cast<const double*>(gp.data()), reinterpret_cast<const double*>(Xgp.data()), order,
-                        out, (cudaStream_t)stream, kernel_ms ? &ms : nullptr);
+                        precision == GBSBIN_FP32_REFINE, out, (cudaStream_t)stream, kernel_ms ? &ms : nullptr);
   if (!st && kernel_ms) *kernel_ms = ms;
   return st;
 }

@@ -32,6 +32,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "gbsbin_df.cuh"
 #include "gbsbin_moments.h"
@@ -39,26 +40,26 @@
 namespace gbsbin {
 namespace {
 
-using E = double2;
-using Ar = ArF64;
-
 constexpr int kMomThreads = 256;
 constexpr int kGemmTile = 32;         // C tile of the products (2 x 2 entries per thread)
 constexpr int kGemmK = 16;
 
-__device__ __forceinline__ E cconj(E a) { return make_double2(a.x, -a.y); }
-__device__ __forceinline__ E scale(E a, double s) { return make_double2(s * a.x, s * a.y); }
+// The kernels run in an arithmetic class Ar (gbsbin_df.cuh): ArF64, or ArDF (pairs of FP32 on
+// the FMA pipe, ~46 bits); the coefficients leave them as FP64 for the chain rule.
+template <class Ar>
+__device__ __forceinline__ typename Ar::E scale(typename Ar::E a, double s) {
+  return Ar::mul(a, Ar::from(make_double2(s, 0.0)));
+}
 
-__device__ __forceinline__ E warp_sum(E v) {
+template <class Ar>
+__device__ __forceinline__ typename Ar::E warp_sum(typename Ar::E v) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
-    v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
-  }
+  for (int o = 16; o > 0; o >>= 1) v = Ar::add(v, shfl_xor(v, o));
   return v;
 }
 
 // Fixed-order CTA sum; every thread returns the total.
+template <class Ar, class E>
 __device__ E block_sum(E v, E* red) {
   red[threadIdx.x] = v;
   __syncthreads();
@@ -72,6 +73,7 @@ __device__ E block_sum(E v, E* red) {
 }
 
 // u_i = Xg_i + sum_k W_ik Xg_k, v_i = g_i + sum_k W_ki g_k = g_i + sum_k conj(W_ik) g_k
+template <class Ar, class E = typename Ar::E>
 __global__ void __launch_bounds__(kMomThreads) k_mom_uv(const E* W, const E* Xg, const E* g, E* u, E* v, int n) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int i = blockIdx.x * (kMomThreads / 32) + warp;
@@ -80,10 +82,10 @@ __global__ void __launch_bounds__(kMomThreads) k_mom_uv(const E* W, const E* Xg,
   for (int k = lane; k < n; k += 32) {
     const E w = W[(size_t)i * n + k];
     au = Ar::fma(w, Xg[k], au);
-    av = Ar::fma(cconj(w), g[k], av);
+    av = Ar::fma(Ar::conj(w), g[k], av);
   }
-  au = warp_sum(au);
-  av = warp_sum(av);
+  au = warp_sum<Ar>(au);
+  av = warp_sum<Ar>(av);
   if (lane == 0) {
     u[i] = Ar::add(Xg[i], au);
     v[i] = Ar::add(g[i], av);
@@ -95,6 +97,7 @@ __global__ void __launch_bounds__(kMomThreads) k_mom_uv(const E* W, const E* Xg,
 // conj(W[j, k]), k in the slice.  A thread owns rows 2 tr, 2 tr + 1 and columns tc, tc + 16 of
 // the tile.  With S = 1 the tile goes straight to Y_b and, off the diagonal, its conjugate
 // transpose below it.
+template <class E>
 struct YArgs {
   E* P;                    // Y (S = 1) or the slices, n^2 apart
   const E* W;
@@ -102,7 +105,9 @@ struct YArgs {
   int n, S;
 };
 
-__global__ void __launch_bounds__(kMomThreads) k_mom_gram(YArgs g) {
+template <class Ar>
+__global__ void __launch_bounds__(kMomThreads) k_mom_gram(YArgs<typename Ar::E> g) {
+  using E = typename Ar::E;
   if (blockIdx.x < blockIdx.y) return;
   __shared__ E As[kGemmTile * kGemmK];
   __shared__ E Bs[kGemmK * kGemmTile];
@@ -120,7 +125,7 @@ __global__ void __launch_bounds__(kMomThreads) k_mom_gram(YArgs g) {
       const int r = e / kGemmK, c = e % kGemmK;
       As[e] = (i0 + r < n && c < kc) ? g.W[(size_t)(i0 + r) * n + kk + c] : Ar::zero();
       // Bs[c][r] = conj(W[j0 + r, kk + c])
-      Bs[c * kGemmTile + r] = (j0 + r < n && c < kc) ? cconj(g.W[(size_t)(j0 + r) * n + kk + c]) : Ar::zero();
+      Bs[c * kGemmTile + r] = (j0 + r < n && c < kc) ? Ar::conj(g.W[(size_t)(j0 + r) * n + kk + c]) : Ar::zero();
     }
     __syncthreads();
 #pragma unroll 4
@@ -143,13 +148,14 @@ __global__ void __launch_bounds__(kMomThreads) k_mom_gram(YArgs g) {
       const int i = i0 + 2 * tr + x, j = j0 + tc + 16 * y;
       if (i < n && j < n) {
         P[(size_t)i * n + j] = acc[x][y];
-        if (mirror) P[(size_t)j * n + i] = cconj(acc[x][y]);
+        if (mirror) P[(size_t)j * n + i] = Ar::conj(acc[x][y]);
       }
     }
 }
 
 // Y_b(i, j) = sum_s P_{b,s}(i, j) in order s = 0 .. S-1 for tiles on or above the diagonal,
 // conj(Y_b(j, i)) below it
+template <class Ar, class E = typename Ar::E>
 __global__ void __launch_bounds__(kMomThreads) k_mom_sum_slices(E* Y, const E* P, int S, int n, int L) {
   const long long nn = (long long)n * n, total = nn * L;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
@@ -159,8 +165,15 @@ __global__ void __launch_bounds__(kMomThreads) k_mom_sum_slices(E* Y, const E* P
     const long long src = upper ? x : (long long)j * n + i;
     E acc = Ar::zero();
     for (int sl = 0; sl < S; ++sl) acc = Ar::add(acc, P[(b * S + sl) * nn + src]);
-    Y[b * nn + x] = upper ? acc : cconj(acc);
+    Y[b * nn + x] = upper ? acc : Ar::conj(acc);
   }
+}
+
+// In place: the FP64 values uploaded into a buffer of Ar::E (16 bytes either way) in Ar.
+template <class Ar>
+__global__ void __launch_bounds__(kMomThreads) k_mom_from_f64(typename Ar::E* buf, long long count) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < count; e += (long long)gridDim.x * blockDim.x)
+    buf[e] = Ar::from(reinterpret_cast<const double2*>(buf)[e]);
 }
 
 // Slices of the depth so that the launch has about one CTA per SM at least (each slice >= 32 deep).
@@ -171,6 +184,7 @@ int gemm_slices(long long ctas, int kmin, int sms) {
 }
 
 // q_d[k] = sum_{j in d} W_kj u_j (a warp per (d, k))
+template <class Ar, class E = typename Ar::E>
 __global__ void __launch_bounds__(kMomThreads) k_mom_q(const E* W, const E* u, E* q, const int* goff, int n, int L) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const long long t = (long long)blockIdx.x * (kMomThreads / 32) + warp;
@@ -178,7 +192,7 @@ __global__ void __launch_bounds__(kMomThreads) k_mom_q(const E* W, const E* u, E
   const int d = (int)(t / n), k = (int)(t - (long long)d * n);
   E acc = Ar::zero();
   for (int j = goff[d] + lane; j < goff[d + 1]; j += 32) acc = Ar::fma(W[(size_t)k * n + j], u[j], acc);
-  acc = warp_sum(acc);
+  acc = warp_sum<Ar>(acc);
   if (lane == 0) q[t] = acc;
 }
 
@@ -186,8 +200,9 @@ __global__ void __launch_bounds__(kMomThreads) k_mom_q(const E* W, const E* u, E
 // p + (a (L + 1) + b) n: blockIdx.y = a (L + 1) + b when Y was formed, else blockIdx.y = a and
 // b = L only.  A lane per k, the CTA's eight warps over the rows of a, their partials added in
 // order.
-__global__ void __launch_bounds__(kMomThreads) k_mom_p(const E* Y, const E* W, const E* v, E* p, const int* goff,
-                                                       int n, int L) {
+template <class Ar, class E = typename Ar::E>
+__global__ void __launch_bounds__(kMomThreads) k_mom_p(const E* Y, const E* W, const E* v, E* p, const int* goff, int n,
+                                                       int L) {
   __shared__ E red[kMomThreads];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int k = blockIdx.x * 32 + lane;
@@ -206,6 +221,7 @@ __global__ void __launch_bounds__(kMomThreads) k_mom_p(const E* Y, const E* W, c
   }
 }
 
+template <class E>
 struct CoefArgs {
   int n, L, order;
   const int* goff;
@@ -222,7 +238,9 @@ struct CoefArgs {
 //   C1[a]     = 1/2 sum_{i in a} (W_ii + v_i u_i)
 //   C2[a,b]   = 1/4 sum_{i in a, j in b} |W_ij|^2 + 1/2 sum_{j in b} p_aL[j] u_j
 //   C3[a,b,c] = 1/6 sum_{i in a, k in c} Y_b[i,k] conj(W_ik) + 1/2 sum_{k in c} p_ab[k] u_k
-__global__ void __launch_bounds__(kMomThreads) k_mom_coef(CoefArgs a) {
+template <class Ar>
+__global__ void __launch_bounds__(kMomThreads) k_mom_coef(CoefArgs<typename Ar::E> a) {
+  using E = typename Ar::E;
   __shared__ E red[kMomThreads];
   const int n = a.n, L = a.L;
   int g0 = 0, g1 = 0, g2 = 0;
@@ -243,8 +261,8 @@ __global__ void __launch_bounds__(kMomThreads) k_mom_coef(CoefArgs a) {
     E acc = Ar::zero();
     for (int i = ga + threadIdx.x; i < ga + na; i += kMomThreads)
       acc = Ar::add(acc, Ar::add(a.W[(size_t)i * n + i], Ar::mul(a.v[i], a.u[i])));
-    acc = block_sum(acc, red);
-    if (threadIdx.x == 0) a.out[blockIdx.x] = scale(acc, 0.5);
+    acc = block_sum<Ar>(acc, red);
+    if (threadIdx.x == 0) a.out[blockIdx.x] = scale<Ar>(acc, 0.5);
     return;
   }
   const int hc = a.order == 2 ? g1 : g2;
@@ -255,18 +273,20 @@ __global__ void __launch_bounds__(kMomThreads) k_mom_coef(CoefArgs a) {
   for (long long e = threadIdx.x; e < cnt; e += kMomThreads) {
     const size_t x = (size_t)(ga + (int)(e / nc)) * n + gc + (int)(e - (e / nc) * nc);
     const E w = a.W[x];
-    if (a.order == 2) tr.x = ::fma(w.x, w.x, ::fma(w.y, w.y, tr.x));
-    else tr = Ar::fma(Yb[x], cconj(w), tr);
+    if (a.order == 2) tr = Ar::fma(w, Ar::conj(w), tr);   // |W_ij|^2
+    else tr = Ar::fma(Yb[x], Ar::conj(w), tr);
   }
   const E* pv = a.p + ((size_t)g0 * (L + 1) + (a.order == 2 ? L : g1)) * n;
   for (int k = gc + threadIdx.x; k < gc + nc; k += kMomThreads) vec = Ar::fma(pv[k], a.u[k], vec);
-  tr = block_sum(tr, red);
-  vec = block_sum(vec, red);
-  if (threadIdx.x == 0) a.out[blockIdx.x] = Ar::add(scale(tr, a.order == 2 ? 0.25 : 1.0 / 6.0), scale(vec, 0.5));
+  tr = block_sum<Ar>(tr, red);
+  vec = block_sum<Ar>(vec, red);
+  if (threadIdx.x == 0) a.out[blockIdx.x] = Ar::add(scale<Ar>(tr, a.order == 2 ? 0.25 : 1.0 / 6.0), scale<Ar>(vec, 0.5));
 }
 
 // Order 4: one CTA per (a, c, b <= d) writes C4[a,b,c,d] and C4[a,d,c,b].
-__global__ void __launch_bounds__(kMomThreads) k_mom_coef4(CoefArgs a) {
+template <class Ar>
+__global__ void __launch_bounds__(kMomThreads) k_mom_coef4(CoefArgs<typename Ar::E> a) {
+  using E = typename Ar::E;
   __shared__ E red[kMomThreads];
   const int n = a.n, L = a.L, npair = L * (L + 1) / 2;
   const int ac = blockIdx.x / npair;
@@ -286,7 +306,7 @@ __global__ void __launch_bounds__(kMomThreads) k_mom_coef4(CoefArgs a) {
   const long long cnt = (long long)na * nc;
   for (long long e = threadIdx.x; e < cnt; e += kMomThreads) {
     const size_t x = (size_t)(ga + (int)(e / nc)) * n + gc + (int)(e - (e / nc) * nc);
-    tr = Ar::fma(Yb[x], cconj(Yd[x]), tr);
+    tr = Ar::fma(Yb[x], Ar::conj(Yd[x]), tr);
   }
   // the vector terms: sum_{k in c} p_ab[k] q_d[k] and sum_{k in c} p_ad[k] q_b[k]
   const E* pab = a.p + ((size_t)ga0 * (L + 1) + b) * n;
@@ -295,16 +315,17 @@ __global__ void __launch_bounds__(kMomThreads) k_mom_coef4(CoefArgs a) {
     s1 = Ar::fma(pab[k], a.q[(size_t)d * n + k], s1);
     s2 = Ar::fma(pad[k], a.q[(size_t)b * n + k], s2);
   }
-  tr = block_sum(tr, red);
-  s1 = block_sum(s1, red);
-  s2 = block_sum(s2, red);
+  tr = block_sum<Ar>(tr, red);
+  s1 = block_sum<Ar>(s1, red);
+  s2 = block_sum<Ar>(s2, red);
   if (threadIdx.x == 0) {
     const long long base = (long long)ga0 * L * L * L + (long long)gc0 * L;
-    a.out[base + (long long)b * L * L + d] = Ar::add(scale(tr, 0.125), scale(s1, 0.5));
-    if (b != d) a.out[base + (long long)d * L * L + b] = Ar::add(scale(cconj(tr), 0.125), scale(s2, 0.5));
+    a.out[base + (long long)b * L * L + d] = Ar::add(scale<Ar>(tr, 0.125), scale<Ar>(s1, 0.5));
+    if (b != d) a.out[base + (long long)d * L * L + b] = Ar::add(scale<Ar>(Ar::conj(tr), 0.125), scale<Ar>(s2, 0.5));
   }
 }
 
+template <class E>
 struct KappaArgs {
   int L, order;
   const E* C[5];           // C[r]: L^r coefficients (C[0] unused)
@@ -312,17 +333,18 @@ struct KappaArgs {
 };
 
 // F_r(h_1..h_r): C_r summed over all r! orders of its indices (Heap's algorithm)
-__device__ E F_sym(const KappaArgs& a, int r, const int* h) {
+template <class Ar>
+__device__ double2 F_sym(const KappaArgs<typename Ar::E>& a, int r, const int* h) {
   const int L = a.L;
-  if (r == 1) return a.C[1][h[0]];
+  if (r == 1) return Ar::to(a.C[1][h[0]]);
   int o[4] = {0, 1, 2, 3};
   int c[4] = {0, 0, 0, 0};
   auto term = [&]() {
     long long idx = 0;
     for (int x = 0; x < r; ++x) idx = idx * L + h[o[x]];
-    return a.C[r][idx];
+    return Ar::to(a.C[r][idx]);
   };
-  E s = term();
+  double2 s = term();
   int i = 1;
   while (i < r) {
     if (c[i] < i) {
@@ -330,7 +352,7 @@ __device__ E F_sym(const KappaArgs& a, int r, const int* h) {
       const int tmp = o[sw];
       o[sw] = o[i];
       o[i] = tmp;
-      s = Ar::add(s, term());
+      s = ArF64::add(s, term());
       ++c[i];
       i = 1;
     } else {
@@ -345,7 +367,8 @@ __device__ E F_sym(const KappaArgs& a, int r, const int* h) {
 // restricted growth strings: a block label per slot) whose blocks carry one group each.  A warp
 // per entry: every lane walks the partitions, lane p evaluates those with index = p (mod 32),
 // and the lanes' terms are added by a fixed butterfly.
-__global__ void k_mom_kappa(KappaArgs a) {
+template <class Ar>
+__global__ void k_mom_kappa(KappaArgs<typename Ar::E> a) {
   const int L = a.L, lane = threadIdx.x & 31;
   long long t = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   double* out = a.kappa;
@@ -364,7 +387,7 @@ __global__ void k_mom_kappa(KappaArgs a) {
     g[s] = (int)(x % L);
     x /= L;
   }
-  E kap = Ar::zero();
+  double2 kap = ArF64::zero();
   int lab[4] = {0, 0, 0, 0};
   for (int idx = 0;; ++idx) {
     if ((idx & 31) == lane) {
@@ -376,7 +399,7 @@ __global__ void k_mom_kappa(KappaArgs a) {
         if (bg[lab[s]] < 0) bg[lab[s]] = g[s];
         else if (bg[lab[s]] != g[s]) ok = false;
       }
-      if (ok) kap = Ar::add(kap, F_sym(a, nblk, bg));
+      if (ok) kap = ArF64::add(kap, F_sym<Ar>(a, nblk, bg));
     }
     // next restricted growth string: lab[0] = 0, lab[s] <= 1 + max(lab[0..s-1])
     int s = r - 1;
@@ -391,15 +414,15 @@ __global__ void k_mom_kappa(KappaArgs a) {
     }
     if (s < 1) break;
   }
-  kap = warp_sum(kap);
+  kap = warp_sum<ArF64>(kap);
   if (lane == 0) out[t] = kap.x;
 }
 
-}  // namespace
-
-int cumulants_device(int n, int L, const int* goff, const double* W, const double* gamma, const double* Xgamma,
-                     int order, double* const* kappa, cudaStream_t s, float* ms) {
-  if (order < 1 || order > 4 || L < 1 || L > GBSBIN_MOM_MAX_L || n < 1) return GBSBIN_ERR_ARG;
+template <class Ar>
+int cumulants_run(int n, int L, const int* goff, const double* W, const double* gamma, const double* Xgamma, int order,
+                  double* const* kappa, cudaStream_t s, float* ms) {
+  using E = typename Ar::E;
+  static_assert(sizeof(E) == sizeof(double2), "the FP64 uploads share the buffers");
   const size_t nn = (size_t)n * n;
   long long Lp[5] = {1, L, (long long)L * L, (long long)L * L * L, (long long)L * L * L * L};
   int dev = 0, sms = 0;
@@ -456,28 +479,33 @@ int cumulants_device(int n, int L, const int* goff, const double* W, const doubl
   if (err == cudaSuccess && ms) err = cudaEventRecord(e0, s);
   if (err == cudaSuccess) {
     const int wpb = kMomThreads / 32;
-    k_mom_uv<<<(n + wpb - 1) / wpb, kMomThreads, 0, s>>>(dW, dXg, dg, du, dv, n);
+    if (!std::is_same<Ar, ArF64>::value) {           // the uploads into the arithmetic's format
+      k_mom_from_f64<Ar><<<(unsigned)std::min<size_t>((nn + kMomThreads - 1) / kMomThreads, 4096), kMomThreads, 0, s>>>(
+          dW, (long long)nn);
+      k_mom_from_f64<Ar><<<1, kMomThreads, 0, s>>>(dg, 2LL * n);   // gamma and X gamma (adjacent)
+    }
+    k_mom_uv<Ar><<<(n + wpb - 1) / wpb, kMomThreads, 0, s>>>(dW, dXg, dg, du, dv, n);
     if (order >= 3) {
-      YArgs ya{SY > 1 ? Pb : Y, dW, dgoff, n, SY};
-      k_mom_gram<<<dim3(gt, gt, L * SY), kMomThreads, 0, s>>>(ya);
+      YArgs<E> ya{SY > 1 ? Pb : Y, dW, dgoff, n, SY};
+      k_mom_gram<Ar><<<dim3(gt, gt, L * SY), kMomThreads, 0, s>>>(ya);
       if (SY > 1)
-        k_mom_sum_slices<<<(unsigned)std::min<size_t>((nn * L + kMomThreads - 1) / kMomThreads, 8 * (size_t)sms),
+        k_mom_sum_slices<Ar><<<(unsigned)std::min<size_t>((nn * L + kMomThreads - 1) / kMomThreads, 8 * (size_t)sms),
                            kMomThreads, 0, s>>>(Y, Pb, SY, n, L);
     }
-    if (order >= 4) k_mom_q<<<(unsigned)(((long long)L * n + wpb - 1) / wpb), kMomThreads, 0, s>>>(dW, du, dq, dgoff, n, L);
+    if (order >= 4) k_mom_q<Ar><<<(unsigned)(((long long)L * n + wpb - 1) / wpb), kMomThreads, 0, s>>>(dW, du, dq, dgoff, n, L);
     if (order >= 2)
-      k_mom_p<<<dim3((n + 31) / 32, order >= 3 ? L * (L + 1) : L), kMomThreads, 0, s>>>(order >= 3 ? Y : nullptr, dW, dv,
+      k_mom_p<Ar><<<dim3((n + 31) / 32, order >= 3 ? L * (L + 1) : L), kMomThreads, 0, s>>>(order >= 3 ? Y : nullptr, dW, dv,
                                                                                            dp, dgoff, n, L);
     for (int r = 1; r <= std::min(order, 3); ++r) {
-      CoefArgs ca{n, L, r, dgoff, dW, Y, du, dv, dq, dp, dC[r]};
-      k_mom_coef<<<(unsigned)Lp[r], kMomThreads, 0, s>>>(ca);
+      CoefArgs<E> ca{n, L, r, dgoff, dW, Y, du, dv, dq, dp, dC[r]};
+      k_mom_coef<Ar><<<(unsigned)Lp[r], kMomThreads, 0, s>>>(ca);
     }
     if (order >= 4) {
-      CoefArgs ca{n, L, 4, dgoff, dW, Y, du, dv, dq, dp, dC[4]};
-      k_mom_coef4<<<(unsigned)(Lp[2] * (L * (L + 1) / 2)), kMomThreads, 0, s>>>(ca);
+      CoefArgs<E> ca{n, L, 4, dgoff, dW, Y, du, dv, dq, dp, dC[4]};
+      k_mom_coef4<Ar><<<(unsigned)(Lp[2] * (L * (L + 1) / 2)), kMomThreads, 0, s>>>(ca);
     }
-    KappaArgs ka{L, order, {nullptr, dC[1], dC[2], dC[3], dC[4]}, dk};
-    k_mom_kappa<<<(unsigned)((kwords + 3) / 4), 128, 0, s>>>(ka);
+    KappaArgs<E> ka{L, order, {nullptr, dC[1], dC[2], dC[3], dC[4]}, dk};
+    k_mom_kappa<Ar><<<(unsigned)((kwords + 3) / 4), 128, 0, s>>>(ka);
     err = cudaGetLastError();
   }
   if (err == cudaSuccess && ms) err = cudaEventRecord(e1, s);
@@ -500,6 +528,15 @@ int cumulants_device(int n, int L, const int* goff, const double* W, const doubl
     return GBSBIN_ERR_CUDA;
   }
   return GBSBIN_OK;
+}
+
+}  // namespace
+
+int cumulants_device(int n, int L, const int* goff, const double* W, const double* gamma, const double* Xgamma,
+                     int order, bool pairs, double* const* kappa, cudaStream_t s, float* ms) {
+  if (order < 1 || order > 4 || L < 1 || L > GBSBIN_MOM_MAX_L || n < 1) return GBSBIN_ERR_ARG;
+  return pairs ? cumulants_run<ArDF>(n, L, goff, W, gamma, Xgamma, order, kappa, s, ms)
+               : cumulants_run<ArF64>(n, L, goff, W, gamma, Xgamma, order, kappa, s, ms);
 }
 
 }  // namespace gbsbin

@@ -15,7 +15,8 @@ namespace gbsbin {
 // For r = 1 .. order, kappa[r - 1] (host memory, L^r doubles, row-major; may be null) receives
 // the r-th cumulant tensor of the counts.  Device buffers are allocated and freed per call;
 // synchronous on s.  *ms (may be null) receives the device time of the launches (CUDA events).
+// pairs: the products and block sums in pairs of FP32 (~46 bits) instead of FP64.
 int cumulants_device(int n, int L, const int* goff, const double* W, const double* gamma, const double* Xgamma,
-                     int order, double* const* kappa, cudaStream_t s, float* ms);
+                     int order, bool pairs, double* const* kappa, cudaStream_t s, float* ms);
 
 }  // namespace gbsbin

@@ -1,6 +1,7 @@
 """Cumulants of orders 1-4 of the binned counts on the GPU (gbsbin_cumulants_device, Sec. VI
-coarse-grained moments and cumulants) against textbook single-mode results, the central
-moments of the oracle's unfolded tables, and the host evaluators at the library's sizes."""
+coarse-grained moments and cumulants; FP64, and the products in pairs of FP32) against textbook
+single-mode results, the central moments of the oracle's unfolded tables, and the host
+evaluators at the library's sizes."""
 import numpy as np
 import pytest
 
@@ -47,14 +48,15 @@ def _central(P):
     return mu, [g - m for g, m in zip(grids, mu)]
 
 
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "fp32pairs"])
 @pytest.mark.parametrize("M,K,L,cut,disp,basis", [(4, 1, 2, 6, True, False), (3, 2, 2, 5, False, True),
                                                   (3, 1, 3, 4, True, False), (4, 1, 4, 3, True, False)])
-def test_against_unfolded_tables(gb, M, K, L, cut, disp, basis):
+def test_against_unfolded_tables(gb, M, K, L, cut, disp, basis, precision):
     # the cumulants are the central-moment combinations of the oracle's unfolded table:
     # kappa_ij = mu_ij, kappa_ijk = mu_ijk, kappa_ijkl = mu_ijkl - mu_ij mu_kl - mu_ik mu_jl - mu_il mu_jk
     rng = np.random.default_rng(970 + M + K + L)
     prob = synth.random_problem(rng, M, K, L, cut, displaced=disp, internal_basis=basis, r_range=(0.1, 0.4))
-    k1, k2, k3, k4 = gb.gbsbin_cumulants_device(prob)
+    k1, k2, k3, k4 = gb.gbsbin_cumulants_device(prob, precision=precision)
     over = 6 if L <= 3 else 5
     P = oracle.binned(prob, radix=prob.radix * over)["P"]
     mu, d = _central(P)
@@ -74,8 +76,9 @@ def test_against_unfolded_tables(gb, M, K, L, cut, disp, basis):
         assert np.abs(k4 - k4.transpose(perm)).max() < 1e-12 * max(1.0, np.abs(k4).max())
 
 
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "fp32pairs"])
 @pytest.mark.parametrize("case", ["n192", "ragged"])
-def test_library_sizes_match_host(gb, case):
+def test_library_sizes_match_host(gb, case, precision):
     # the n = 192 workload (24 ports x 4 internal modes, three groups of 64 rows) and a ragged
     # n = 152 case (five groups of uneven size, a last 32-pivot block of 24 rows) against the
     # host evaluators (an FP64 Gauss-Jordan inverse and plain loops), relative to each tensor's
@@ -86,7 +89,7 @@ def test_library_sizes_match_host(gb, case):
         rng = np.random.default_rng(4242)
         prob = synth.random_problem(rng, 38, 2, 5, 3, displaced=True, internal_basis=True, r_range=(0.4, 1.0))
         prob.bin_of_mode = np.array(rng.permutation(np.arange(38) % 5), np.int32)
-    outs = gb.gbsbin_cumulants_device(prob)
+    outs = gb.gbsbin_cumulants_device(prob, precision=precision)
     mean, cov = gb.gbsbin_moments(prob)
     host = [mean, cov, gb.gbsbin_cumulants3(prob), gb.gbsbin_cumulants4(prob)]
     for r, (dev, ref) in enumerate(zip(outs, host), start=1):
@@ -120,15 +123,22 @@ def test_largest_matrix(gb):
     assert np.all(np.linalg.eigvalsh(k2) > 0)
 
 
-def test_sixteen_groups_match_host(gb):
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "fp32pairs"])
+def test_sixteen_groups_match_host(gb, precision):
     # the largest group count (L = 16, one port per group, n = 32): every coefficient launch and
     # the chain rule at their largest grids, against the host evaluators
     rng = np.random.default_rng(4343)
     prob = synth.random_problem(rng, 16, 1, 16, 2, displaced=True, r_range=(0.3, 0.8))
     prob.bin_of_mode = np.arange(16, dtype=np.int32)
-    outs = gb.gbsbin_cumulants_device(prob)
+    outs = gb.gbsbin_cumulants_device(prob, precision=precision)
     mean, cov = gb.gbsbin_moments(prob)
     host = [mean, cov, gb.gbsbin_cumulants3(prob), gb.gbsbin_cumulants4(prob)]
     for r, (dev, ref) in enumerate(zip(outs, host), start=1):
         assert dev.shape == (16,) * r
         assert np.abs(dev - ref).max() < 1e-11 * np.abs(ref).max(), (r, np.abs(dev - ref).max())
+
+
+def test_rejects_other_precisions(gb):
+    with pytest.raises(gb.GbsbinError) as e:
+        gb.gbsbin_cumulants_device(_one_mode(0.5), precision=2)
+    assert e.value.status == 1
